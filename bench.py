@@ -1,0 +1,418 @@
+#!/usr/bin/env python
+"""Benchmark of the compressed staged state-vector loop on GB300.
+
+Workload (default): 28-qubit QFT of a seeded random basis state followed by
+4 x (RZ on every qubit, CX ladder) — 626 gates, complex64 state (2 GiB raw),
+SV blocks of 2^22 amplitudes, inner size 2, gates fused to k = 5 qubits,
+eps = 1e-3 (eb = eps * 2^-14 per real/imaginary part).
+
+One step = one qsim_run of the whole circuit through the C ABI: initial
+store, then per stage decompress -> fused gate passes -> sizing ->
+reservation -> compress for every SV group. Metric: amplitude-gate updates/s
+= 2^n * (gates before fusion) / time, with the compression ratio
+8 * 2^n / (peak compressed store over stages) and the fidelity bound reported
+beside it.
+
+  value  — K steps, plan and inputs already resident, CUDA events on the
+           caller's stream (the library joins its streams back to it);
+  e2e    — K steps from host data through the public API: plan from the host
+           gate list (matrices uploaded), run, read sampled amplitudes and
+           the statistics back to the host.
+The working set (2 GiB state, ~1 GB compressed) is larger than L2 (129 MB),
+so no explicit flush is done between steps.
+
+`--impl reference` times the CPU oracle (complex128 staged simulation + scalar
+codec) on a bounded sample of the same workload on the host cores.
+
+For N > 1 (torchrun), every rank runs an independent replica (weak scaling);
+the per-rank times are reduced with MAX and rank 0 prints the line.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+FP32_LANES_PER_SM = 128
+NUM_SMS = 152
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="fp32", choices=["fp32", "tf32", "bf16x3"])
+    ap.add_argument("--n", type=int, default=28)
+    ap.add_argument("--m", type=int, default=22)
+    ap.add_argument("--inner", type=int, default=2)
+    ap.add_argument("--k", type=int, default=5)
+    ap.add_argument("--streams", type=int, default=2)
+    ap.add_argument("--eps", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle sample")
+    ap.add_argument("--no-profile", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args):
+    from paper_2410_14088_gb300 import inputs
+    return inputs.qft_rz_cx(args.n, 4, args.seed)
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, \
+        "fallback"
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if not self.proc:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for name, v in zip(names, r[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        out.update(sm_mhz=statistics.median(sm) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                   reasons=sorted(reasons), samples=len(rows))
+        return out
+
+
+# --------------------------------------------------------------------------
+# CPU oracle sample (the reference arm and the cpu_baseline key)
+# --------------------------------------------------------------------------
+class OracleSampler:
+    """Bounded sample of the CPU oracle on the benchmark workload: complex128
+    gate updates on the full state in circuit order (continuing across
+    calls), plus QSZ1 encode + decode of SV blocks. The full-run time is
+    modelled as (time per gate) x gates + (time per block) x blocks x stages."""
+
+    def __init__(self, args):
+        import numpy as np
+
+        import oracle
+        from oracle.partition import partition
+
+        self.np, self.oracle = np, oracle
+        self.circ = workload(args)
+        self.n, self.m = self.circ.n, args.m
+        self.eb = args.eps * 2.0 ** (-self.n / 2)
+        self.stages = partition(self.circ.gates, self.n, self.m, args.inner)
+        self.psi = oracle.basis_state(self.n, self.circ.init_basis)
+        self.next_gate = 0
+        self.next_block = 0
+        self.t_gates = self.t_codec = 0.0
+        self.gates_done = self.blocks_done = 0
+
+    def step(self, budget_s, record=True):
+        t0 = time.perf_counter()
+        g = b = 0
+        while time.perf_counter() - t0 < 0.7 * budget_s or g == 0:
+            gi = self.next_gate % len(self.circ.gates)
+            self.oracle.apply_gate(self.psi, self.n, self.circ.gates[gi])
+            self.next_gate += 1
+            g += 1
+        t1 = time.perf_counter()
+        nblocks = 1 << (self.n - self.m)
+        while time.perf_counter() - t1 < 0.3 * budget_s or b == 0:
+            j = self.next_block % nblocks
+            blk = self.psi[2 * (j << self.m): 2 * ((j + 1) << self.m)].astype(self.np.float32)
+            self.oracle.qsz_decode(self.oracle.qsz_encode(blk, self.m, self.eb), self.m)
+            self.next_block += 1
+            b += 1
+        t2 = time.perf_counter()
+        if record:
+            self.t_gates += t1 - t0
+            self.t_codec += t2 - t1
+            self.gates_done += g
+            self.blocks_done += b
+
+    def result(self):
+        per_gate = self.t_gates / max(1, self.gates_done)
+        per_block = self.t_codec / max(1, self.blocks_done)
+        nblocks = 1 << (self.n - self.m)
+        total = per_gate * len(self.circ.gates) + per_block * nblocks * len(self.stages)
+        ups = (1 << self.n) * len(self.circ.gates) / total
+        threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+        sample = (f"{self.gates_done} complex128 gate updates of the full 2^{self.n} state "
+                  f"({self.t_gates:.1f} s) and {self.blocks_done} QSZ1 encode+decode of 2^{self.m}-amplitude "
+                  f"blocks ({self.t_codec:.1f} s); full run modelled as per-gate time x {len(self.circ.gates)} "
+                  f"gates + per-block codec time x {nblocks} blocks x {len(self.stages)} stages")
+        return ups, sample, threads, total
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    smp = OracleSampler(args)
+    per_step = max(2.0, args.cpu_seconds / max(1, args.steps))
+    for _ in range(args.warmup):
+        smp.step(0.5, record=False)
+    for _ in range(args.steps):
+        smp.step(per_step)
+    ups, sample, threads, total = smp.result()
+    line = {
+        "impl": "reference", "metric": "amplitude-gate updates/s incl. codec & compression ratio at fidelity>=0.99",
+        "value": ups, "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": config_dict(args),
+        "cpu_baseline": {"value": ups, "unit": "updates/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "e2e": {"value": ups, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def config_dict(args):
+    return {"workload": f"qft{args.n}+4x(rz,cx-ladder), m={args.m}, inner={args.inner}, k={args.k}, "
+                        f"eps={args.eps:g}, prec={args.prec}",
+            "n_qubits": args.n, "gates": 626 if args.n == 28 else None, "block_log2": args.m, "inner": args.inner,
+            "k": args.k, "eps": args.eps, "prec": args.prec, "streams": args.streams,
+            "l2_policy": "working set (2 GiB state, ~1 GB compressed) > L2 (129 MB); no flush"}
+
+
+# --------------------------------------------------------------------------
+# our arm
+# --------------------------------------------------------------------------
+def run_ours(args, rank, world, dist):
+    import numpy as np
+    import torch
+
+    from paper_2410_14088_gb300 import qsim
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    prec = {"fp32": qsim.PREC_FP32, "tf32": qsim.PREC_TF32, "bf16x3": qsim.PREC_BF16X3}[args.prec]
+    circ = workload(args)
+    G = len(circ.gates)
+    n = circ.n
+    kw = dict(m=args.m, inner=args.inner, k=args.k, eps=args.eps, prec=prec, streams=args.streams)
+    plan = qsim.plan_stages(circ, **kw)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- warm-up ----
+    for _ in range(args.warmup):
+        st = qsim.run(plan)
+        del st
+    barrier()
+
+    # ---- timed: value (inputs resident) ----
+    qsim.profile_enable(not args.no_profile)
+    sampler = ClockSampler(dev)
+    sampler.start()
+    launches0 = qsim.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    kstats_acc = {}
+    stats = []
+    for _ in range(args.steps):
+        st = qsim.run(plan)
+        stats.append(st.stats.as_dict())
+        for k, v in st.kernel_stats().items():
+            a = kstats_acc.setdefault(k, {"launches": 0, "seconds": 0.0, "alg_bytes": 0.0, "alg_flops": 0.0})
+            for f in a:
+                a[f] += v[f]
+        del st
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    qsim.profile_enable(False)
+    launches = qsim.launch_count() - launches0
+    t_ms = ev0.elapsed_time(ev1)
+    t_max = t_ms
+    if dist is not None:
+        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ups = world * args.steps * (1 << n) * G / (t_max * 1e-3)
+
+    # ---- timed: e2e through the public API from host data ----
+    idx = np.arange(0, 1 << n, (1 << n) // 4096, dtype=np.uint64)[:4096]
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h2d = d2h = 0
+    for _ in range(args.steps):
+        p2 = qsim.plan_stages(circ, **kw)
+        st = qsim.run(p2)
+        amps = st.amplitudes(idx)
+        h2d += st.stats.h2d_bytes + idx.nbytes
+        d2h += st.stats.d2h_bytes + amps.nbytes
+        del st, p2
+    e1.record(stream)
+    barrier()
+    te_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([te_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te_ms = float(t.item())
+    e2e = world * args.steps * (1 << n) * G / (te_ms * 1e-3)
+
+    if rank != 0:
+        return
+    last = stats[-1]
+    peaks, peaks_kind = load_peaks()
+    sm_max = peaks.get("sm_max_mhz", 2070.0)
+    fp32_peak_tflops = NUM_SMS * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    # dominant kernel by event-timed total
+    roofline = None
+    kernels = {}
+    if kstats_acc:
+        dom = max(kstats_acc, key=lambda k: kstats_acc[k]["seconds"])
+        for k, v in kstats_acc.items():
+            kernels[k] = {"launches": v["launches"], "ms_per_launch": 1e3 * v["seconds"] / max(1, v["launches"]),
+                          "share": v["seconds"] / max(1e-12, sum(x["seconds"] for x in kstats_acc.values())),
+                          "GBps": v["alg_bytes"] / max(1e-12, v["seconds"]) / 1e9,
+                          "TFLOPps": v["alg_flops"] / max(1e-12, v["seconds"]) / 1e12}
+        d = kstats_acc[dom]
+        per_launch_s = d["seconds"] / max(1, d["launches"])
+        gbps = d["alg_bytes"] / max(1e-12, d["seconds"]) / 1e9
+        tflops = d["alg_flops"] / max(1e-12, d["seconds"]) / 1e12
+        hbm_frac = gbps / peaks["hbm_gbs"]
+        if dom == "gate_pass" and args.prec == "fp32" and tflops / fp32_peak_tflops > hbm_frac:
+            roofline = {"kernel": dom, "bound": "alu", "achieved": tflops, "peak": fp32_peak_tflops,
+                        "unit": "TFLOP/s", "frac": tflops / fp32_peak_tflops,
+                        "peak_source": f"derived: {NUM_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
+                        "hbm_frac_of_measured": hbm_frac}
+        else:
+            roofline = {"kernel": dom, "bound": "hbm", "achieved": gbps, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                        "frac": hbm_frac, "peak_source": f"{peaks_kind} hbm_gbs"}
+        roofline["traffic"] = traffic_for(dom, d["alg_bytes"] / max(1, d["launches"]))
+        roofline["ms_per_launch"] = per_launch_s * 1e3
+    cr = 8.0 * (1 << n) / max(1, last["peak_store_bytes"])
+    line = {
+        "metric": "amplitude-gate updates/s incl. codec & compression ratio at fidelity>=0.99",
+        "value": ups, "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": config_dict(args),
+        "compression_ratio": cr, "compression_ratio_vs_complex128": 2 * cr,
+        "fidelity_lower_bound": last["fidelity_lower_bound"], "norm_sq": last["norm_sq"],
+        "stages": last["nstages"], "plan_seconds": plan.stats()["plan_seconds"],
+        "e2e": {"value": e2e, "unit": "updates/s", "h2d_bytes_per_step": h2d // args.steps,
+                "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "kernels": kernels,
+        "clocks": clocks,
+        "peaks": peaks_kind,
+    }
+    if not args.no_cpu_baseline:
+        smp = OracleSampler(args)
+        smp.step(0.5, record=False)
+        for _ in range(3):
+            smp.step(args.cpu_seconds / 3)
+        cups, sample, threads, _ = smp.result()
+        line["cpu_baseline"] = {"value": cups, "unit": "updates/s", "cores": threads, "kind": "oracle",
+                                "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
+def traffic_for(kernel, alg_bytes_per_launch):
+    """DRAM bytes per launch from the committed ncu summary, scaled to this
+    launch size; None when no capture matches the kernel's current source."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    import hashlib
+    with open(path) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            parts = line.split()
+            if len(parts) < 5 or parts[0] != kernel:
+                continue
+            src, digest, dram_bytes, alg_bytes = parts[1], parts[2], float(parts[3]), float(parts[4])
+            sp = os.path.join(ROOT, src)
+            if not os.path.exists(sp):
+                return None
+            if hashlib.sha256(open(sp, "rb").read()).hexdigest()[:16] != digest:
+                return None  # kernel changed since the counters were taken
+            return dram_bytes / alg_bytes * alg_bytes_per_launch
+    return None
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    run_ours(args, rank, world, dist)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

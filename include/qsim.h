@@ -1,0 +1,267 @@
+/*
+ * qsim.h — C ABI of libqsim, a compressed full-state quantum circuit simulator
+ * for one GB300 (sm_103a), after BMQSim (arXiv 2410.14088).
+ *
+ * The problem statement follows the paper: a circuit, an SV block size and an
+ * inner size are turned into stages offline (Sec. 4.1, Algorithm 1), and the
+ * state is then simulated stage by stage with every SV block kept compressed
+ * between stages (Sec. 4 overview, Sec. 4.2). Where the paper compresses with a
+ * closed library under a point-wise relative bound (Sec. 4.3), this library
+ * uses its own format, QSZ1, under the point-wise absolute bound
+ * eb = eps * 2^(-n/2) on the real and imaginary part of every amplitude.
+ *
+ * Conventions
+ *   - Qubit q is bit q of the amplitude index (little-endian, Sec. 2.1).
+ *   - Amplitudes are complex64, interleaved (re, im) float32, unless stated.
+ *   - Every call returns 0 (QSIM_OK) or a negative QSIM_E_* code; no C++
+ *     exception crosses this boundary. qsim_last_error() gives a message for
+ *     the calling thread's last failure.
+ *   - Device pointers are plain CUDA device addresses (or mapped pinned host
+ *     addresses) of the current device. Streams are cudaStream_t passed as
+ *     void*; NULL is the legacy default stream.
+ *   - The caller owns every buffer it passes in. Handles (qsim_plan,
+ *     qsim_state) are owned by the library until the matching *_free.
+ */
+#ifndef QSIM_H
+#define QSIM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define QSIM_OK 0
+#define QSIM_E_INVALID -1     /* bad argument: qubit, size, NaN/Inf, m/k range */
+#define QSIM_E_NOMEM -2       /* device or pinned-host allocation failed / tiers full */
+#define QSIM_E_CAPACITY -3    /* output buffer too small (needed size reported) */
+#define QSIM_E_CORRUPT -4     /* malformed compressed stream */
+#define QSIM_E_RANGE -5       /* |x| / 2^e >= 2^30: value out of the codec's range */
+#define QSIM_E_UNSUPPORTED -6 /* non-diagonal gate with more global qubits than max(i,2) */
+#define QSIM_E_TIMEOUT -7     /* a bounded device-side wait gave up */
+#define QSIM_E_CUDA -8        /* CUDA runtime error */
+
+/* ---- gates --------------------------------------------------------------- */
+#define QSIM_GATE_DIAG 1u      /* optional hint; diagonality is detected from u */
+#define QSIM_GATE_PHASEFLIP 2u /* amplitude |basis> times -1; u = NULL, nq/q ignored */
+
+/*
+ * One gate (Sec. 2.1 gives the 1- and 2-qubit update; any nq <= 6 is taken).
+ * u: 2^nq x 2^nq row-major complex128 as (re, im) double pairs; q[0] is the
+ * least-significant bit of the row/column index. u must be unitary (checked
+ * to 1e-8) and is copied by qsim_plan_stages.
+ */
+typedef struct qsim_gate {
+    uint32_t nq;
+    uint32_t flags;
+    uint32_t q[6];
+    uint64_t basis;
+    const double *u;
+} qsim_gate;
+
+/* ---- configuration -------------------------------------------------------- */
+#define QSIM_PREC_FP32 0u   /* fused gates on FP32 CUDA cores */
+#define QSIM_PREC_TF32 1u   /* fused gates on tensor cores, TF32 inputs, FP32 accumulate */
+#define QSIM_PREC_BF16X3 2u /* tensor cores, 3-way split BF16 inputs, FP32 accumulate */
+
+#define QSIM_MODE_STREAMS 0u    /* SV groups round-robin over CUDA streams (Sec. 4.2) */
+#define QSIM_MODE_PERSISTENT 1u /* one persistent kernel per stage over a group queue */
+
+#define QSIM_CODEC_QSZ1 0u /* compressed blocks (the method) */
+#define QSIM_CODEC_NONE 1u /* raw complex64 blocks: the no-compression comparison run */
+
+#define QSIM_SIZING_EXACT 0u   /* a sizing pass computes each block's exact size first */
+#define QSIM_SIZING_PREDICT 1u /* learned size predictor reserves space; overflow re-encodes */
+
+typedef struct qsim_config {
+    uint32_t m;           /* log2 amplitudes per SV block (the paper's b), 5..26 */
+    uint32_t inner;       /* inner size i (Sec. 4.1); threshold = max(i, 2) */
+    uint32_t k;           /* max fused gate width, 1..6 */
+    uint32_t prec;        /* QSIM_PREC_* */
+    uint32_t mode;        /* QSIM_MODE_* */
+    uint32_t streams;     /* CUDA streams in QSIM_MODE_STREAMS (1..16) */
+    uint32_t sizing;      /* QSIM_SIZING_* */
+    uint32_t diag_exempt; /* 1: diagonal gates never count as global (off = paper) */
+    uint32_t codec;       /* QSIM_CODEC_* */
+    uint32_t graph;       /* 1: capture each run's stage loop in a CUDA graph (persistent mode) */
+    uint32_t tile_bits;   /* log2 amplitudes per shared-memory tile, 0 = default */
+    uint32_t reserved0;
+    double eps;           /* eb = eps * 2^(-n/2) */
+    uint64_t device_tier_cap_bytes; /* bytes of compressed blocks kept on the device; 0 = no cap */
+    uint64_t init_basis;  /* initial basis state |init_basis> (Sec. 4.2 initialisation) */
+    double predictor_margin; /* predictor reservation = 2^pred * (1 + margin) */
+    uint64_t reserved[6];
+} qsim_config;
+
+/* Fill *cfg with defaults: m 20, inner 2, k 4, FP32, streams mode, 2 streams,
+ * exact sizing, eps 1e-3, QSZ1, no cap, |0...0>. */
+void qsim_config_default(qsim_config *cfg);
+
+/* ---- planning (host only) ------------------------------------------------ */
+typedef struct qsim_plan qsim_plan;
+
+/*
+ * Canonicalise the gates, cut the circuit into stages with Algorithm 1
+ * (Sec. 4.1: a gate joins the current stage unless the distinct global
+ * qubits — bits >= m — of stage plus gate would exceed max(inner, 2)), fuse
+ * each stage's gates greedily into dense ops of at most k qubits, and lay the
+ * ops out in shared-memory tile passes. Host work only; the gate matrices are
+ * uploaded by qsim_run.
+ * Errors: INVALID (n outside 5..40, m > n, bad qubit, non-unitary u, k < a
+ * gate's width), UNSUPPORTED (a non-diagonal gate whose global qubits alone
+ * exceed the threshold), NOMEM.
+ */
+int qsim_plan_stages(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_config *cfg,
+                     qsim_plan **out);
+
+/* Number of stages; if stage_inner_masks is not NULL it receives, per stage,
+ * a mask whose bit j is set when global qubit m + j is an inner index. */
+int qsim_plan_info(const qsim_plan *plan, size_t *nstages, uint32_t *stage_inner_masks);
+
+/* Gates [*first, *first + *count) of the input form stage `stage`. */
+int qsim_plan_stage_gates(const qsim_plan *plan, size_t stage, size_t *first, size_t *count);
+
+typedef struct qsim_plan_stats {
+    uint64_t nstages, ngates, dense_ops, diag_ops, phaseflip_ops, passes;
+    uint64_t max_working_log2; /* log2 amplitudes of the largest working vector */
+    double plan_seconds;
+} qsim_plan_stats;
+int qsim_plan_get_stats(const qsim_plan *plan, qsim_plan_stats *out);
+
+/* Introspection of a stage's fused ops (what the gate passes apply). */
+typedef struct qsim_op_info {
+    uint32_t type;      /* 0 dense matrix, 1 diagonal phases, 2 phase flip */
+    uint32_t nq;        /* qubits of the op (0 for a phase flip) */
+    uint32_t qubits[6]; /* full qubit ids; matrix bit j <-> qubits[j] */
+    uint32_t ngates;    /* input gates folded into the op */
+    uint32_t pass;      /* index of the shared-memory tile pass within the stage */
+    uint64_t basis;     /* phase flip: the flipped basis state */
+    const double *u;    /* dense: 2^nq x 2^nq complex128 row-major; diagonal: 2^nq complex128;
+                           owned by the plan */
+} qsim_op_info;
+
+/* *count receives the number of ops of `stage`; if ops is not NULL it must
+ * hold *count entries on input (capacity) and receives them. */
+int qsim_plan_stage_ops(const qsim_plan *plan, size_t stage, size_t *count, qsim_op_info *ops);
+
+void qsim_plan_free(qsim_plan *plan);
+
+/* ---- simulation ------------------------------------------------------------ */
+typedef struct qsim_state qsim_state;
+
+typedef struct qsim_stats {
+    double seconds;          /* device time of the run (CUDA events), init included */
+    double err_norm_sum;     /* sum over stages of ||delta_s|| (codec error, FP64) */
+    double err_sq_total;     /* sum over stages of ||delta_s||^2 */
+    double norm_sq;          /* ||psi_sim||^2 after the last stage */
+    uint64_t nstages, groups, kernel_launches;
+    uint64_t peak_store_bytes;     /* max over stages of the summed stream bytes (Sec. 5.4) */
+    uint64_t peak_reserved_bytes;  /* max over stages of the reserved slot bytes */
+    uint64_t final_store_bytes;
+    uint64_t host_tier_peak_bytes; /* max over stages of bytes placed in pinned host memory */
+    uint64_t overflow_blocks;      /* predictor under-estimates that were re-encoded */
+    uint64_t blocks_encoded;
+    double fidelity_lower_bound;   /* (1 + |b|^2 - E^2) / (2|b|), E = err_norm_sum */
+    uint64_t h2d_bytes;            /* host->device bytes copied by the run (plan upload included) */
+    uint64_t d2h_bytes;            /* device->host bytes copied by the run (statistics) */
+} qsim_stats;
+
+/*
+ * Run the plan from |init_basis>. Work is ordered on cuda_stream (and on the
+ * library's own streams, joined back to it); the call returns once the run
+ * is complete and *stats (nullable) is filled. *out receives a state handle
+ * owning the final compressed store.
+ * Errors: NOMEM (tiers full), RANGE, TIMEOUT, CUDA, INVALID.
+ */
+int qsim_run(const qsim_plan *plan, void *cuda_stream, qsim_state **out, qsim_stats *stats);
+
+/* Per-stage record of a finished run: stream bytes after the stage, reserved
+ * bytes, ||delta_s||^2 of the codec error injected by the stage. */
+int qsim_state_stage_stats(const qsim_state *st, size_t stage, uint64_t *store_bytes,
+                           uint64_t *reserved_bytes, double *err_sq);
+
+/* ---- readout -------------------------------------------------------------- */
+
+/* Gather `count` amplitudes by index into out_interleaved (HOST, 2*count
+ * floats). Only the blocks holding them are decompressed. */
+int qsim_amplitudes(const qsim_state *st, const uint64_t *idx, size_t count, float *out_interleaved);
+
+/* Fidelity |<ref|sim>| / (||ref|| ||sim||) (Sec. 5.3 definition, normalised),
+ * reduced in FP64 on the GPU. ref: 2^n complex128 interleaved, host or
+ * device pointer. */
+int qsim_fidelity(const qsim_state *st, const double *ref_interleaved, double *f);
+
+/* ||psi_sim||^2 in FP64 on the GPU. */
+int qsim_state_norm(const qsim_state *st, double *norm_sq);
+
+/* Decompress the whole state into d_out (device, 2^n complex64). */
+int qsim_state_decompress(const qsim_state *st, float *d_out, void *cuda_stream);
+
+/* Copy block `block`'s compressed stream to host_out (cap bytes); *bytes gets
+ * its size (also when cap is too small: CAPACITY). */
+int qsim_state_block_stream(const qsim_state *st, uint64_t block, void *host_out, size_t cap,
+                            size_t *bytes);
+
+void qsim_state_free(qsim_state *st);
+
+/* ---- single-block codec (the bit-exactness surface) --------------------- */
+
+/* Worst-case QSZ1 stream size for a block of 2^m amplitudes:
+ * 32 + pad16(4 (nframes+1)) + nframes (pad16(2C) + 8F), F = min(4096, 2^m). */
+size_t qsim_worst_case_bytes(uint32_t m);
+
+/*
+ * Compress one block of 2^m complex64 amplitudes (d_amps, device) under the
+ * absolute bound eb into d_out (device, cap bytes). The call synchronises
+ * cuda_stream and writes the stream size to *out_bytes (host). Every
+ * reconstructed component is within eb of the input.
+ * Errors: INVALID (m outside 5..26, eb out of range, NaN/Inf input), RANGE,
+ * CAPACITY (cap too small; *out_bytes = the size needed), CUDA.
+ * Calls from several host threads are serialised inside the library.
+ */
+int qsim_compress_block(const float *d_amps, uint32_t m, double eb, void *d_out, size_t cap,
+                        size_t *out_bytes, void *cuda_stream);
+
+/*
+ * Decompress a QSZ1 stream (d_in, device, in_bytes) into d_amps (device,
+ * 2^m complex64). Synchronises cuda_stream to report the status.
+ * Errors: INVALID, CORRUPT (bad magic/header/offsets/widths), CUDA.
+ */
+int qsim_decompress_block(const void *d_in, size_t in_bytes, float *d_amps, uint32_t m,
+                          void *cuda_stream);
+
+/* ---- per-kernel timing ---------------------------------------------------- */
+
+/* When enabled, qsim_run brackets every kernel launch with CUDA events on the
+ * stream it is launched on; the per-kernel totals of a run are then read with
+ * qsim_state_kernel_stats. Algorithmic bytes/flops are the run's useful
+ * traffic/work per kernel (compressed bytes read or written, 8 bytes per
+ * amplitude per pass over the working vector, 8 * 2^k flops per amplitude per
+ * dense k-qubit op). */
+void qsim_profile_enable(int on);
+
+typedef struct qsim_kernel_stat {
+    char name[32];
+    uint64_t launches;
+    double seconds;   /* sum of event-timed launch durations */
+    double alg_bytes; /* algorithmic DRAM bytes over the run */
+    double alg_flops; /* algorithmic flops over the run */
+} qsim_kernel_stat;
+
+int qsim_state_kernel_stats(const qsim_state *st, qsim_kernel_stat *out, size_t cap, size_t *count);
+
+/* ---- misc ------------------------------------------------------------------ */
+const char *qsim_last_error(void);
+
+/* Number of kernels this library launched in this process so far. */
+uint64_t qsim_kernel_launch_count(void);
+
+/* Release cached device/pinned buffers held by the library for reuse. */
+void qsim_release_cached_memory(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* QSIM_H */

@@ -1,0 +1,86 @@
+// Types and launchers of the block codec and the block pool (device side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qsim_internal.h"
+
+namespace qsim {
+
+// a compressed block to read
+struct BlockRef {
+    const uint8_t *ptr;
+    uint64_t bytes;
+};
+
+// one entry of the block table (where block b's current stream lives)
+struct BlockSlot {
+    uint8_t *ptr;
+    uint64_t bytes;
+    uint32_t tier;  // 0 device, 1 pinned host
+    uint32_t pad;
+};
+
+// where an encoder writes block j of a group
+struct EncTarget {
+    uint8_t *ptr;
+    uint64_t cap;
+    uint32_t tier;
+    uint32_t pad;
+};
+
+struct EncResult {
+    uint64_t total;      // stream bytes (also computed when the slot overflowed)
+    uint32_t overflow;   // 1 if the stream did not fit the reserved slot
+    uint32_t pad;
+    double err_sq;       // sum (x - x')^2 over the block
+    double norm_sq;      // sum x'^2 over the block
+};
+
+// per-stage running totals, updated by the encoder
+struct StageAccum {
+    uint64_t store_bytes;
+    uint64_t reserved_bytes;
+    uint64_t host_bytes;
+    uint64_t blocks;
+    uint64_t overflow_blocks;
+    uint64_t pad;
+    double err_sq;
+    double norm_sq;
+};
+
+// a bump arena (device memory, or mapped pinned host memory)
+struct ArenaDev {
+    uint8_t *base;
+    uint64_t cap;
+    uint64_t *bump;  // device counter
+};
+
+// look-back scratch of the encoder
+struct LookbackScratch {
+    uint64_t *state;    // one status word per frame
+    uint32_t *ticket;
+    uint32_t *done;
+    uint32_t *epoch;
+};
+
+void count_launch();
+
+void launch_decode(const BlockRef *in, uint32_t nblocks, int m, float2 *wv, uint32_t *hist, int *status,
+                   cudaStream_t s);
+void launch_encode(const float2 *wv, uint32_t nblocks, int m, int e, const EncTarget *tgt, EncResult *res,
+                   int only_overflowed, const uint32_t *ids, BlockSlot *table, StageAccum *acc,
+                   const LookbackScratch &scr, int *status, cudaStream_t s);
+void launch_encode_size(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, int *status,
+                        cudaStream_t s);
+void launch_reserve(uint32_t nblocks, const uint64_t *need, uint64_t add_const, const float *pred_log2,
+                    double margin, uint64_t worst, const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt,
+                    EncResult *res, int retry_overflowed, int *status, cudaStream_t s);
+void launch_copy_out(const float2 *wv, uint32_t nblocks, int m, const EncTarget *tgt, const uint32_t *ids,
+                     BlockSlot *table, StageAccum *acc, int *status, cudaStream_t s);
+void launch_copy_in(const BlockRef *in, uint32_t nblocks, int m, float2 *wv, int *status, cudaStream_t s);
+void launch_gather_refs(const BlockSlot *table, const uint32_t *ids, uint32_t count, BlockRef *out,
+                        cudaStream_t s);
+
+}  // namespace qsim

@@ -1,0 +1,1337 @@
+// Stage engine, two-tier block pool, readout and the C ABI (host side).
+//
+// Execution follows the paper's transfer-concealed workflow (Sec. 4.2): every
+// SV group of a stage goes through decompress -> update -> compress on one CUDA
+// stream, and groups are dealt round-robin to the streams so that the codec,
+// the gate passes and (for the pinned-host tier) the link traffic of different
+// groups overlap. A group is the 2^|inner| blocks sharing the stage's outer
+// global bits (Sec. 4.1); consecutive groups are batched into one launch per
+// kernel so that small blocks still fill the GPU.
+//
+// Compressed blocks live in bump arenas: a device arena and, when the device
+// tier is capped or full, a mapped pinned-host arena (the two memory levels of
+// Sec. 4.4, with pinned host memory standing in for the SSD tier). Each stage
+// reads the arena written by the previous stage and writes the other one, so
+// the memory held is the compressed input plus output of one stage. Slots are
+// reserved on the device (atomic bump), so no host round trip is needed
+// between the sizing and the encoding of a block.
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cmath>
+#include <map>
+#include <mutex>
+#include <vector>
+
+#include "codec.cuh"
+#include "device_common.cuh"
+#include "gates.cuh"
+#include "qsim_internal.h"
+
+namespace qsim {
+
+// ---------------------------------------------------------------------------
+// errors, counters
+// ---------------------------------------------------------------------------
+static thread_local char g_err[512] = "";
+static std::atomic<uint64_t> g_launches{0};
+
+int set_error(int code, const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+    return code;
+}
+void clear_error() { g_err[0] = 0; }
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+// ---------------------------------------------------------------------------
+// optional per-kernel event timing (events reused across runs)
+// ---------------------------------------------------------------------------
+static std::atomic<int> g_profile{0};
+enum ProfCat { P_DECODE = 0, P_PASS, P_ENCODE_SIZE, P_RESERVE, P_ENCODE, P_GATHER, P_COPY_IN, P_COPY_OUT, P_INIT,
+               P_NCAT };
+static const char *kProfNames[P_NCAT] = {"decode", "gate_pass", "encode_size", "reserve", "encode",
+                                         "gather_refs", "copy_in", "copy_out", "init"};
+
+struct Profiler {
+    bool on = false;
+    struct Rec {
+        int cat;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+    size_t used = 0;
+    static std::vector<cudaEvent_t> &pool() {
+        static std::vector<cudaEvent_t> *p = new std::vector<cudaEvent_t>();
+        return *p;
+    }
+    cudaEvent_t get() {
+        auto &P = pool();
+        if (used < P.size()) return P[used++];
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        P.push_back(e);
+        ++used;
+        return e;
+    }
+    void begin(int cat, cudaStream_t s) {
+        if (!on) return;
+        Rec r{cat, get(), nullptr};
+        cudaEventRecord(r.a, s);
+        recs.push_back(r);
+    }
+    void end(cudaStream_t s) {
+        if (!on) return;
+        recs.back().b = get();
+        cudaEventRecord(recs.back().b, s);
+    }
+    // after synchronisation
+    void collect(double secs[P_NCAT], uint64_t launches[P_NCAT]) {
+        for (int c = 0; c < P_NCAT; ++c) { secs[c] = 0; launches[c] = 0; }
+        for (const Rec &r : recs) {
+            float ms = 0;
+            if (cudaEventElapsedTime(&ms, r.a, r.b) == cudaSuccess) {
+                secs[r.cat] += ms * 1e-3;
+                launches[r.cat] += 1;
+            }
+        }
+        cudaGetLastError();
+    }
+};
+
+#define CUDA_TRY(expr)                                                                      \
+    do {                                                                                    \
+        cudaError_t _e = (expr);                                                            \
+        if (_e != cudaSuccess)                                                              \
+            return set_error(_e == cudaErrorMemoryAllocation ? QSIM_E_NOMEM : QSIM_E_CUDA,  \
+                             "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// caching allocator (device and pinned host), exact-size reuse
+// ---------------------------------------------------------------------------
+struct Cache {
+    std::mutex mu;
+    std::multimap<size_t, void *> dev_free, host_free;
+    std::map<void *, size_t> dev_live, host_live;
+};
+static Cache &cache() {
+    static Cache *c = new Cache();
+    return *c;
+}
+
+static int dev_alloc(void **p, size_t bytes) {
+    bytes = (bytes + 255) & ~size_t(255);
+    Cache &c = cache();
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        auto it = c.dev_free.find(bytes);
+        if (it != c.dev_free.end()) {
+            *p = it->second;
+            c.dev_free.erase(it);
+            c.dev_live[*p] = bytes;
+            return QSIM_OK;
+        }
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        // drop cached blocks and retry once
+        qsim_release_cached_memory();
+        e = cudaMalloc(p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QSIM_E_NOMEM, "cudaMalloc(%zu) failed", bytes);
+        }
+    }
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.dev_live[*p] = bytes;
+    return QSIM_OK;
+}
+
+static void dev_free(void *p) {
+    if (!p) return;
+    Cache &c = cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.dev_live.find(p);
+    if (it == c.dev_live.end()) return;
+    c.dev_free.emplace(it->second, p);
+    c.dev_live.erase(it);
+}
+
+static int host_alloc(void **p, size_t bytes) {
+    bytes = (bytes + 4095) & ~size_t(4095);
+    Cache &c = cache();
+    {
+        std::lock_guard<std::mutex> lk(c.mu);
+        auto it = c.host_free.find(bytes);
+        if (it != c.host_free.end()) {
+            *p = it->second;
+            c.host_free.erase(it);
+            c.host_live[*p] = bytes;
+            return QSIM_OK;
+        }
+    }
+    cudaError_t e = cudaHostAlloc(p, bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return set_error(QSIM_E_NOMEM, "cudaHostAlloc(%zu) failed", bytes);
+    }
+    std::lock_guard<std::mutex> lk(c.mu);
+    c.host_live[*p] = bytes;
+    return QSIM_OK;
+}
+
+static void host_free(void *p) {
+    if (!p) return;
+    Cache &c = cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    auto it = c.host_live.find(p);
+    if (it == c.host_live.end()) return;
+    c.host_free.emplace(it->second, p);
+    c.host_live.erase(it);
+}
+
+template <class T>
+struct DevBuf {
+    T *p = nullptr;
+    size_t n = 0;
+    int alloc(size_t count) {
+        release();
+        n = count;
+        if (!count) return QSIM_OK;
+        return dev_alloc(reinterpret_cast<void **>(&p), count * sizeof(T));
+    }
+    void release() {
+        dev_free(p);
+        p = nullptr;
+        n = 0;
+    }
+    ~DevBuf() { release(); }
+};
+
+// ---------------------------------------------------------------------------
+// per-device context: status word and the single-block codec scratch
+// ---------------------------------------------------------------------------
+struct DeviceCtx {
+    std::mutex mu;  // serialises the single-block entry points
+    int *status = nullptr;
+    uint64_t *lb_state = nullptr;
+    uint32_t *lb_ctr = nullptr;  // ticket, done, epoch
+    EncTarget *tgt = nullptr;
+    EncResult *res = nullptr;
+    BlockRef *ref = nullptr;
+    bool ready = false;
+};
+
+static DeviceCtx &device_ctx(int dev) {
+    static DeviceCtx ctx[16];
+    return ctx[dev & 15];
+}
+
+static int ensure_device_ctx(DeviceCtx &c) {
+    if (c.ready) return QSIM_OK;
+    const size_t max_frames = size_t(1) << (kQszMaxM - kQszMaxFrameLog);
+    CUDA_TRY(cudaMalloc(&c.status, 256));
+    CUDA_TRY(cudaMalloc(&c.lb_state, max_frames * sizeof(uint64_t)));
+    CUDA_TRY(cudaMalloc(&c.lb_ctr, 256));
+    CUDA_TRY(cudaMalloc(&c.tgt, sizeof(EncTarget)));
+    CUDA_TRY(cudaMalloc(&c.res, sizeof(EncResult)));
+    CUDA_TRY(cudaMalloc(&c.ref, sizeof(BlockRef)));
+    CUDA_TRY(cudaMemset(c.status, 0, 256));
+    CUDA_TRY(cudaMemset(c.lb_state, 0, max_frames * sizeof(uint64_t)));
+    CUDA_TRY(cudaMemset(c.lb_ctr, 0, 256));
+    c.ready = true;
+    return QSIM_OK;
+}
+
+static LookbackScratch make_scratch(uint64_t *state, uint32_t *ctr) {
+    LookbackScratch s;
+    s.state = state;
+    s.ticket = ctr;
+    s.done = ctr + 1;
+    s.epoch = ctr + 2;
+    return s;
+}
+
+static int read_status(int *d_status, cudaStream_t s) {
+    int h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, d_status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (h) {
+        CUDA_TRY(cudaMemsetAsync(d_status, 0, sizeof(int), s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    return h;
+}
+
+static const char *status_text(int code) {
+    switch (code) {
+        case QSIM_E_INVALID: return "non-finite input value";
+        case QSIM_E_RANGE: return "value out of the codec range (|x|/2^e >= 2^30)";
+        case QSIM_E_CORRUPT: return "corrupt compressed stream";
+        case QSIM_E_NOMEM: return "compressed-block tiers are full";
+        case QSIM_E_TIMEOUT: return "a bounded device wait gave up";
+        default: return "device error";
+    }
+}
+
+// ---------------------------------------------------------------------------
+// plan upload: pass/op descriptors, matrices, group layouts
+// ---------------------------------------------------------------------------
+struct StageDev {
+    uint32_t W, G;              // working bits, blocks per group
+    uint32_t ngroups;
+    uint32_t pass_begin, npasses;
+    std::vector<PassDev> passes_host;
+};
+
+struct PlanDev {
+    bool ready = false;
+    int device = -1;
+    DevBuf<PassDev> passes;
+    DevBuf<OpDev> ops;
+    DevBuf<float2> mats;
+    DevBuf<uint32_t> ids;     // per stage: 2^c block ids, group-major
+    DevBuf<uint64_t> gbase;   // per stage: per group outer bits
+    std::vector<StageDev> stages;
+    std::vector<size_t> ids_off, gbase_off;
+    uint64_t upload_bytes = 0;
+    bool counted = false;  // upload bytes reported by the first run that used it
+};
+
+static std::mutex g_plan_mu;
+static std::map<const qsim_plan *, PlanDev *> g_plan_dev;
+
+static void order_complement(OpDev &od, uint32_t T) {
+    bool is_t[16] = {false};
+    for (uint32_t j = 0; j < od.k; ++j) is_t[od.tq[j]] = true;
+    std::vector<uint32_t> comp;
+    for (uint32_t t = 0; t < T; ++t)
+        if (!is_t[t]) comp.push_back(t);
+    // lane bits: one complement bit per bank residue (tile bit t lands on bank bit t % 4)
+    std::vector<uint32_t> first, rest;
+    bool have[4] = {false, false, false, false};
+    for (uint32_t t : comp) {
+        if (!have[t % 4] && first.size() < 4) {
+            have[t % 4] = true;
+            first.push_back(t);
+        } else {
+            rest.push_back(t);
+        }
+    }
+    uint32_t i = 0;
+    for (uint32_t t : first) od.comp[i++] = t;
+    for (uint32_t t : rest) od.comp[i++] = t;
+    for (; i < 16; ++i) od.comp[i] = 0;
+}
+
+static int upload_plan(const qsim_plan *p, PlanDev **out) {
+    int dev;
+    CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plan_dev.find(p);
+    if (it != g_plan_dev.end() && it->second->device == dev) {
+        *out = it->second;
+        return QSIM_OK;
+    }
+    PlanDev *pd = new PlanDev();
+    pd->device = dev;
+    const uint32_t n = p->n, m = p->cfg.m, c = n - m;
+    std::vector<PassDev> passes;
+    std::vector<OpDev> ops;
+    std::vector<float2> mats;
+    std::vector<uint32_t> ids;
+    std::vector<uint64_t> gbases;
+    for (const Stage &st : p->stages) {
+        StageDev sd;
+        sd.W = st.W;
+        sd.G = 1u << st.inner.size();
+        sd.ngroups = 1u << (c - st.inner.size());
+        sd.pass_begin = passes.size();
+        sd.npasses = st.passes.size();
+        std::vector<uint32_t> outer;
+        uint64_t outer_mask = 0;
+        for (uint32_t q = m; q < n; ++q)
+            if (std::find(st.inner.begin(), st.inner.end(), q) == st.inner.end()) {
+                outer.push_back(q);
+                outer_mask |= 1ull << q;
+            }
+        pd->ids_off.push_back(ids.size());
+        pd->gbase_off.push_back(gbases.size());
+        for (uint64_t g = 0; g < sd.ngroups; ++g) {
+            uint64_t gb = 0;
+            for (size_t t = 0; t < outer.size(); ++t) gb |= ((g >> t) & 1ull) << outer[t];
+            gbases.push_back(gb);
+            for (uint64_t j = 0; j < sd.G; ++j) {
+                uint64_t full = gb;
+                for (size_t t = 0; t < st.inner.size(); ++t) full |= ((j >> t) & 1ull) << st.inner[t];
+                ids.push_back(uint32_t(full >> m));
+            }
+        }
+        for (const Pass &ps : st.passes) {
+            PassDev P{};
+            P.T = ps.T;
+            uint32_t L = 0;
+            while (L < ps.T && ps.tile_pos[L] == L) ++L;
+            P.L = L;
+            P.nout = st.W - ps.T;
+            for (uint32_t t = 0; t < ps.T; ++t) P.tile_pos[t] = ps.tile_pos[t];
+            uint32_t o = 0;
+            uint64_t om = 0;
+            for (uint32_t b = 0; b < st.W; ++b) {
+                bool in_tile = false;
+                for (uint32_t t = 0; t < ps.T; ++t) in_tile |= ps.tile_pos[t] == b;
+                if (!in_tile) {
+                    P.out_pos[o++] = b;
+                    om |= 1ull << b;
+                }
+            }
+            P.out_mask = om;
+            P.op_begin = ops.size();
+            P.op_count = ps.ops.size();
+            P.mat_elems = 0;
+            for (uint32_t oi : ps.ops) {
+                const Op &op = st.ops[oi];
+                OpDev od{};
+                od.type = op.type;
+                od.k = op.k;
+                if (op.type == OP_DENSE) {
+                    for (uint32_t j = 0; j < op.k; ++j) {
+                        uint32_t t = 0;
+                        while (ps.tile_pos[t] != op.wq[j]) ++t;
+                        od.tq[j] = t;
+                    }
+                    order_complement(od, ps.T);
+                    od.mat = mats.size();
+                    for (const cd &v : op.u) mats.push_back(make_float2(float(v.real()), float(v.imag())));
+                    P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << (2 * op.k));
+                } else if (op.type == OP_DIAG) {
+                    for (uint32_t j = 0; j < op.k; ++j) {
+                        uint32_t q = op.fq[j];
+                        if (q < m) {
+                            od.dsrc[j] = q;
+                        } else {
+                            auto f = std::find(st.inner.begin(), st.inner.end(), q);
+                            od.dsrc[j] = f != st.inner.end() ? uint32_t(m + (f - st.inner.begin())) : 64 + q;
+                        }
+                    }
+                    od.mat = mats.size();
+                    for (const cd &v : op.u) mats.push_back(make_float2(float(v.real()), float(v.imag())));
+                    P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << op.k);
+                } else {
+                    od.basis_in_stage = 1;
+                    od.basis_outer = op.basis & outer_mask;
+                    uint64_t w = op.basis & ((1ull << m) - 1);
+                    for (size_t t = 0; t < st.inner.size(); ++t)
+                        w |= ((op.basis >> st.inner[t]) & 1ull) << (m + t);
+                    od.basis_w = w;
+                }
+                ops.push_back(od);
+            }
+            P.mat_elems = (P.mat_elems + 1) & ~1u;
+            sd.passes_host.push_back(P);
+            passes.push_back(P);
+        }
+        pd->stages.push_back(std::move(sd));
+    }
+    if (mats.empty()) mats.push_back(make_float2(0, 0));
+    int rc;
+    if ((rc = pd->passes.alloc(passes.size())) || (rc = pd->ops.alloc(ops.size())) ||
+        (rc = pd->mats.alloc(mats.size())) || (rc = pd->ids.alloc(ids.size())) ||
+        (rc = pd->gbase.alloc(gbases.size()))) {
+        delete pd;
+        return rc;
+    }
+    CUDA_TRY(cudaMemcpy(pd->passes.p, passes.data(), passes.size() * sizeof(PassDev), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pd->ops.p, ops.data(), ops.size() * sizeof(OpDev), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pd->mats.p, mats.data(), mats.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pd->ids.p, ids.data(), ids.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pd->gbase.p, gbases.data(), gbases.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    pd->upload_bytes = passes.size() * sizeof(PassDev) + ops.size() * sizeof(OpDev) + mats.size() * sizeof(float2) +
+                       ids.size() * sizeof(uint32_t) + gbases.size() * sizeof(uint64_t);
+    pd->ready = true;
+    if (it != g_plan_dev.end()) delete it->second;
+    g_plan_dev[p] = pd;
+    *out = pd;
+    return QSIM_OK;
+}
+
+static void drop_plan_dev(const qsim_plan *p) {
+    std::lock_guard<std::mutex> lk(g_plan_mu);
+    auto it = g_plan_dev.find(p);
+    if (it != g_plan_dev.end()) {
+        delete it->second;
+        g_plan_dev.erase(it);
+    }
+}
+
+}  // namespace qsim
+
+// ---------------------------------------------------------------------------
+// state handle
+// ---------------------------------------------------------------------------
+struct qsim_state {
+    int device = 0;
+    uint32_t n = 0, m = 0, codec = 0;
+    int e = 0;
+    uint8_t *dev_arena = nullptr;
+    uint8_t *host_arena = nullptr;
+    qsim::BlockSlot *table = nullptr;  // device, 2^(n-m) entries
+    std::vector<qsim::StageAccum> stage_acc;
+    std::vector<qsim_kernel_stat> kstats;
+};
+
+namespace qsim {
+
+// small kernels used by the engine and readout
+__global__ void k_init_blocks(float2 *wv, int m, uint64_t local_index) {
+    // wv holds two blocks: [0] with the basis amplitude, [1] all zero
+    const uint64_t N = 2ull << m;
+    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < N; i += uint64_t(gridDim.x) * blockDim.x)
+        wv[i] = make_float2(i == local_index ? 1.f : 0.f, 0.f);
+}
+
+// every block except b0 gets its own copy of the zero stream (Sec. 4.2)
+__global__ void k_replicate_zero(BlockSlot *table, uint32_t nblocks, uint32_t b0, const BlockSlot *zero_slot,
+                                 ArenaDev dev, ArenaDev host, int *status) {
+    __shared__ uint8_t *dst;
+    __shared__ uint32_t tier;
+    const uint64_t bytes = zero_slot->bytes;
+    for (uint32_t b = blockIdx.x; b < nblocks; b += gridDim.x) {
+        if (b == b0) continue;
+        if (threadIdx.x == 0) {
+            const uint64_t sz = (bytes + 255) & ~255ull;
+            uint64_t off = atomicAdd(reinterpret_cast<unsigned long long *>(dev.bump), sz);
+            dst = nullptr;
+            tier = 0;
+            if (off + sz <= dev.cap) {
+                dst = dev.base + off;
+            } else if (host.base) {
+                off = atomicAdd(reinterpret_cast<unsigned long long *>(host.bump), sz);
+                if (off + sz <= host.cap) {
+                    dst = host.base + off;
+                    tier = 1;
+                }
+            }
+            if (!dst) raise_status(status, QSIM_E_NOMEM);
+            table[b].ptr = dst;
+            table[b].bytes = bytes;
+            table[b].tier = tier;
+        }
+        __syncthreads();
+        if (dst) {
+            const uint4 *s = reinterpret_cast<const uint4 *>(zero_slot->ptr);
+            uint4 *d = reinterpret_cast<uint4 *>(dst);
+            for (uint64_t i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = s[i];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_set_slot(BlockSlot *table, uint32_t b, const EncTarget *tgt, const EncResult *res) {
+    table[b].ptr = tgt->ptr;
+    table[b].bytes = res->total;
+    table[b].tier = tgt->tier;
+}
+
+__global__ void k_copy_slot(BlockSlot *dst, const BlockSlot *src) { *dst = *src; }
+
+__global__ void k_sum_table(const BlockSlot *table, uint64_t nblocks, StageAccum *acc) {
+    uint64_t s = 0;
+    for (uint64_t b = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; b < nblocks; b += uint64_t(gridDim.x) * blockDim.x)
+        s += table[b].bytes;
+    atomicAdd(reinterpret_cast<unsigned long long *>(&acc->store_bytes), s);
+}
+
+// FP64 reductions for readout: <ref|sim>, ||ref||^2, ||sim||^2 over count amplitudes
+__global__ void k_reduce_fid(const double2 *__restrict__ ref, const float2 *__restrict__ sim, uint64_t count,
+                             double *acc) {
+    double ip_r = 0, ip_i = 0, nr = 0, ns = 0;
+    for (uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; i < count; i += uint64_t(gridDim.x) * blockDim.x) {
+        const double2 a = ref ? ref[i] : make_double2(0, 0);
+        const float2 b = sim[i];
+        const double br = b.x, bi = b.y;
+        ip_r += a.x * br + a.y * bi;
+        ip_i += a.x * bi - a.y * br;
+        nr += a.x * a.x + a.y * a.y;
+        ns += br * br + bi * bi;
+    }
+    __shared__ double red[4][32];
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        ip_r += __shfl_xor_sync(kFull, ip_r, o);
+        ip_i += __shfl_xor_sync(kFull, ip_i, o);
+        nr += __shfl_xor_sync(kFull, nr, o);
+        ns += __shfl_xor_sync(kFull, ns, o);
+    }
+    if (lane == 0) {
+        red[0][w] = ip_r;
+        red[1][w] = ip_i;
+        red[2][w] = nr;
+        red[3][w] = ns;
+    }
+    __syncthreads();
+    if (threadIdx.x < 4) {
+        double s = 0;
+        for (int i = 0; i < int(blockDim.x / 32); ++i) s += red[threadIdx.x][i];
+        atomicAdd(&acc[threadIdx.x], s);
+    }
+}
+
+__global__ void k_gather_amps(const float2 *__restrict__ blocks, const uint32_t *__restrict__ slot_of,
+                              const uint32_t *__restrict__ local, uint64_t count, int m, float2 *out) {
+    const uint64_t i = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x;
+    if (i < count) out[i] = blocks[(uint64_t(slot_of[i]) << m) + local[i]];
+}
+
+// ---------------------------------------------------------------------------
+// the run
+// ---------------------------------------------------------------------------
+struct StreamWork {
+    cudaStream_t s = nullptr;
+    cudaEvent_t done = nullptr;
+    DevBuf<float2> wv;
+    DevBuf<BlockRef> refs;
+    DevBuf<EncTarget> tgt;
+    DevBuf<EncResult> res;
+    DevBuf<uint64_t> sizes;
+    DevBuf<uint64_t> lb_state;
+    DevBuf<uint32_t> lb_ctr;
+};
+
+static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsim_stats *stats) {
+    const qsim_config &cfg = p->cfg;
+    if (cfg.mode != QSIM_MODE_STREAMS)
+        return set_error(QSIM_E_UNSUPPORTED, "persistent mode is not available in this build");
+    if (cfg.sizing != QSIM_SIZING_EXACT)
+        return set_error(QSIM_E_UNSUPPORTED, "predictor sizing is not available in this build");
+    int dev;
+    CUDA_TRY(cudaGetDevice(&dev));
+    DeviceCtx &dctx = device_ctx(dev);
+    {
+        std::lock_guard<std::mutex> lk(dctx.mu);
+        int rc = ensure_device_ctx(dctx);
+        if (rc) return rc;
+    }
+    PlanDev *pd = nullptr;
+    int rc = upload_plan(p, &pd);
+    if (rc) return rc;
+
+    const uint32_t n = p->n, m = cfg.m, c = n - m;
+    const uint64_t nblocks = 1ull << c;
+    const bool raw = cfg.codec == QSIM_CODEC_NONE;
+    int e = 0;
+    if (!raw && !qsz_step_exponent(cfg.eps * std::pow(2.0, -double(n) / 2.0), &e))
+        return set_error(QSIM_E_INVALID, "error bound out of range");
+    const uint64_t worst = raw ? (8ull << m) : qsz_worst_case(m);
+    const uint64_t slot_worst = (worst + 255) & ~255ull;
+    const uint64_t nframes = raw ? 1 : qsz_nframes(m);
+
+    // ---- pool sizing: device arenas first, pinned host for the rest ----
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    uint32_t maxW = m;
+    for (const StageDev &sd : pd->stages) maxW = std::max(maxW, sd.W);
+    const uint32_t nstreams = cfg.streams;
+    const uint64_t batch_amps = std::max<uint64_t>(1ull << maxW, 1ull << 22);
+    const uint64_t work_bytes = nstreams * batch_amps * 8 * 2;
+    // every block plus the initial zero-stream template
+    const uint64_t need_per_parity = (nblocks + 1) * slot_worst;
+    uint64_t dev_budget = free_b > work_bytes ? uint64_t(0.85 * double(free_b - work_bytes)) : 0;
+    if (cfg.device_tier_cap_bytes) dev_budget = std::min<uint64_t>(dev_budget, cfg.device_tier_cap_bytes);
+    uint64_t dev_cap = std::min<uint64_t>(need_per_parity, dev_budget / 2) & ~uint64_t(255);
+    uint64_t host_cap = need_per_parity > dev_cap ? ((need_per_parity - dev_cap + 4095) & ~uint64_t(4095)) : 0;
+
+    uint8_t *dev_arena[2] = {nullptr, nullptr}, *host_arena[2] = {nullptr, nullptr};
+    uint8_t *host_arena_dev[2] = {nullptr, nullptr};
+    auto cleanup = [&]() {
+        for (int i = 0; i < 2; ++i) {
+            dev_free(dev_arena[i]);
+            host_free(host_arena[i]);
+        }
+    };
+    for (int i = 0; i < 2; ++i) {
+        if (dev_cap && (rc = dev_alloc(reinterpret_cast<void **>(&dev_arena[i]), dev_cap))) { cleanup(); return rc; }
+        if (host_cap) {
+            if ((rc = host_alloc(reinterpret_cast<void **>(&host_arena[i]), host_cap))) { cleanup(); return rc; }
+            cudaError_t ce = cudaHostGetDevicePointer(reinterpret_cast<void **>(&host_arena_dev[i]), host_arena[i], 0);
+            if (ce != cudaSuccess) { cleanup(); return set_error(QSIM_E_CUDA, "cudaHostGetDevicePointer failed"); }
+        }
+    }
+    DevBuf<uint64_t> bumps;
+    DevBuf<BlockSlot> tables;
+    DevBuf<StageAccum> accs;
+    const size_t nst = p->stages.size();
+    if ((rc = bumps.alloc(4)) || (rc = tables.alloc(2 * nblocks)) || (rc = accs.alloc(nst + 1))) { cleanup(); return rc; }
+    CUDA_TRY(cudaMemsetAsync(bumps.p, 0, 4 * sizeof(uint64_t), main));
+    CUDA_TRY(cudaMemsetAsync(accs.p, 0, (nst + 1) * sizeof(StageAccum), main));
+    CUDA_TRY(cudaMemsetAsync(tables.p, 0, 2 * nblocks * sizeof(BlockSlot), main));
+    auto arena_dev = [&](int parity) {
+        ArenaDev a;
+        a.base = dev_arena[parity];
+        a.cap = dev_arena[parity] ? dev_cap : 0;
+        a.bump = bumps.p + 2 * parity;
+        return a;
+    };
+    auto arena_host = [&](int parity) {
+        ArenaDev a;
+        a.base = host_arena_dev[parity];
+        a.cap = host_arena[parity] ? host_cap : 0;
+        a.bump = bumps.p + 2 * parity + 1;
+        return a;
+    };
+
+    // ---- per-stream work buffers ----
+    std::vector<StreamWork> sw(nstreams);
+    uint64_t max_batch_blocks = 0;
+    for (const StageDev &sd : pd->stages) {
+        uint64_t gpb = std::min<uint64_t>(std::max<uint64_t>(1, batch_amps >> sd.W), 32768);
+        gpb = std::min<uint64_t>(gpb, sd.ngroups);
+        max_batch_blocks = std::max<uint64_t>(max_batch_blocks, gpb * sd.G);
+    }
+    max_batch_blocks = std::max<uint64_t>(max_batch_blocks, 2);
+    for (uint32_t i = 0; i < nstreams; ++i) {
+        StreamWork &w = sw[i];
+        CUDA_TRY(cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming));
+        if ((rc = w.wv.alloc(max_batch_blocks << m)) || (rc = w.refs.alloc(max_batch_blocks)) ||
+            (rc = w.tgt.alloc(max_batch_blocks)) || (rc = w.res.alloc(max_batch_blocks)) ||
+            (rc = w.sizes.alloc(max_batch_blocks)) || (rc = w.lb_state.alloc(max_batch_blocks * nframes)) ||
+            (rc = w.lb_ctr.alloc(4))) {
+            cleanup();
+            for (auto &x : sw) { if (x.s) cudaStreamDestroy(x.s); if (x.done) cudaEventDestroy(x.done); }
+            return rc;
+        }
+        CUDA_TRY(cudaMemsetAsync(w.lb_state.p, 0, max_batch_blocks * nframes * sizeof(uint64_t), main));
+        CUDA_TRY(cudaMemsetAsync(w.lb_ctr.p, 0, 4 * sizeof(uint32_t), main));
+    }
+    auto destroy_streams = [&]() {
+        for (auto &x : sw) {
+            if (x.s) cudaStreamDestroy(x.s);
+            if (x.done) cudaEventDestroy(x.done);
+        }
+    };
+    cudaEvent_t ev_start, ev_stop, ev_fork;
+    CUDA_TRY(cudaEventCreate(&ev_start));
+    CUDA_TRY(cudaEventCreate(&ev_stop));
+    CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    int *status = dctx.status;
+    Profiler prof;
+    prof.on = g_profile.load() != 0;
+    CUDA_TRY(cudaEventRecord(ev_start, main));
+
+    // ---- initial store (Sec. 4.2): encode the basis block and one zero block once ----
+    {
+        StreamWork &w = sw[0];
+        CUDA_TRY(cudaEventRecord(ev_fork, main));
+        CUDA_TRY(cudaStreamWaitEvent(w.s, ev_fork, 0));
+        const uint32_t b0 = uint32_t(cfg.init_basis >> m);
+        const uint64_t loc = cfg.init_basis & ((1ull << m) - 1);
+        k_init_blocks<<<256, 256, 0, w.s>>>(w.wv.p, m, loc);
+        count_launch();
+        BlockSlot *tab0 = tables.p;
+        DevBuf<uint32_t> init_ids;
+        DevBuf<BlockSlot> tmpl;
+        if ((rc = init_ids.alloc(2)) || (rc = tmpl.alloc(2))) { cleanup(); destroy_streams(); return rc; }
+        const uint32_t h_ids[2] = {0, 1};
+        CUDA_TRY(cudaMemcpyAsync(init_ids.p, h_ids, sizeof(h_ids), cudaMemcpyHostToDevice, w.s));
+        // encode both blocks into slots of arena 0; tmpl[0] is the basis block, tmpl[1] the zero template
+        if (raw) {
+            launch_reserve(2, nullptr, worst, nullptr, 0, worst, arena_dev(0), arena_host(0), w.tgt.p, w.res.p, 0,
+                           status, w.s);
+            launch_copy_out(w.wv.p, 2, m, w.tgt.p, init_ids.p, tmpl.p, nullptr, status, w.s);
+        } else {
+            CUDA_TRY(cudaMemsetAsync(w.sizes.p, 0, 2 * sizeof(uint64_t), w.s));
+            launch_encode_size(w.wv.p, 2, m, e, w.sizes.p, status, w.s);
+            launch_reserve(2, w.sizes.p, qsz_data_start(m), nullptr, 0, worst, arena_dev(0), arena_host(0), w.tgt.p,
+                           w.res.p, 0, status, w.s);
+            LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p);
+            launch_encode(w.wv.p, 2, m, e, w.tgt.p, w.res.p, 0, init_ids.p, tmpl.p, nullptr, scr, status, w.s);
+        }
+        k_copy_slot<<<1, 1, 0, w.s>>>(tab0 + b0, tmpl.p + 0);
+        count_launch();
+        k_replicate_zero<<<unsigned(std::min<uint64_t>(nblocks, 152 * 8)), 128, 0, w.s>>>(
+            tab0, uint32_t(nblocks), b0, tmpl.p + 1, arena_dev(0), arena_host(0), status);
+        count_launch();
+        k_sum_table<<<64, 256, 0, w.s>>>(tab0, nblocks, accs.p + nst);
+        count_launch();
+        CUDA_TRY(cudaEventRecord(w.done, w.s));
+        CUDA_TRY(cudaStreamWaitEvent(main, w.done, 0));
+        // the zero template slot stays allocated in arena 0 until stage 0 has read its copies
+        CUDA_TRY(cudaStreamSynchronize(w.s));
+    }
+
+    // ---- stage loop ----
+    for (size_t si = 0; si < nst; ++si) {
+        const StageDev &sd = pd->stages[si];
+        const int in_par = si & 1, out_par = (si + 1) & 1;
+        BlockSlot *tab_in = tables.p + in_par * nblocks;
+        BlockSlot *tab_out = tables.p + out_par * nblocks;
+        CUDA_TRY(cudaMemsetAsync(bumps.p + 2 * out_par, 0, 2 * sizeof(uint64_t), main));
+        CUDA_TRY(cudaEventRecord(ev_fork, main));
+        for (auto &w : sw) CUDA_TRY(cudaStreamWaitEvent(w.s, ev_fork, 0));
+        const uint64_t gpb = std::min<uint64_t>(std::min<uint64_t>(std::max<uint64_t>(1, batch_amps >> sd.W), 32768),
+                                                sd.ngroups);
+        const uint64_t nbatches = (sd.ngroups + gpb - 1) / gpb;
+        const uint32_t *ids_stage = pd->ids.p + pd->ids_off[si];
+        const uint64_t *gb_stage = pd->gbase.p + pd->gbase_off[si];
+        StageAccum *acc = accs.p + si;
+        for (uint64_t b = 0; b < nbatches; ++b) {
+            StreamWork &w = sw[b % nstreams];
+            const uint64_t g0 = b * gpb;
+            const uint32_t ng = uint32_t(std::min<uint64_t>(gpb, sd.ngroups - g0));
+            const uint32_t nb = ng * sd.G;
+            const uint32_t *ids = ids_stage + g0 * sd.G;
+            prof.begin(P_GATHER, w.s);
+            launch_gather_refs(tab_in, ids, nb, w.refs.p, w.s);
+            prof.end(w.s);
+            if (raw) {
+                prof.begin(P_COPY_IN, w.s);
+                launch_copy_in(w.refs.p, nb, m, w.wv.p, status, w.s);
+            } else {
+                prof.begin(P_DECODE, w.s);
+                launch_decode(w.refs.p, nb, m, w.wv.p, nullptr, status, w.s);
+            }
+            prof.end(w.s);
+            for (uint32_t pi = 0; pi < sd.npasses; ++pi) {
+                prof.begin(P_PASS, w.s);
+                launch_pass(w.wv.p, sd.W, ng, &sd.passes_host[pi], pd->passes.p + sd.pass_begin + pi, pd->ops.p,
+                            pd->mats.p, gb_stage + g0, cfg.prec, w.s);
+                prof.end(w.s);
+            }
+            if (raw) {
+                prof.begin(P_RESERVE, w.s);
+                launch_reserve(nb, nullptr, worst, nullptr, 0, worst, arena_dev(out_par), arena_host(out_par),
+                               w.tgt.p, w.res.p, 0, status, w.s);
+                prof.end(w.s);
+                prof.begin(P_COPY_OUT, w.s);
+                launch_copy_out(w.wv.p, nb, m, w.tgt.p, ids, tab_out, acc, status, w.s);
+                prof.end(w.s);
+            } else {
+                CUDA_TRY(cudaMemsetAsync(w.sizes.p, 0, nb * sizeof(uint64_t), w.s));
+                prof.begin(P_ENCODE_SIZE, w.s);
+                launch_encode_size(w.wv.p, nb, m, e, w.sizes.p, status, w.s);
+                prof.end(w.s);
+                prof.begin(P_RESERVE, w.s);
+                launch_reserve(nb, w.sizes.p, qsz_data_start(m), nullptr, 0, worst, arena_dev(out_par),
+                               arena_host(out_par), w.tgt.p, w.res.p, 0, status, w.s);
+                prof.end(w.s);
+                LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p);
+                prof.begin(P_ENCODE, w.s);
+                launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
+                prof.end(w.s);
+            }
+        }
+        for (auto &w : sw) {
+            CUDA_TRY(cudaEventRecord(w.done, w.s));
+            CUDA_TRY(cudaStreamWaitEvent(main, w.done, 0));
+        }
+    }
+    CUDA_TRY(cudaEventRecord(ev_stop, main));
+    CUDA_TRY(cudaEventSynchronize(ev_stop));
+    float ms = 0;
+    CUDA_TRY(cudaEventElapsedTime(&ms, ev_start, ev_stop));
+    cudaEventDestroy(ev_start);
+    cudaEventDestroy(ev_stop);
+    cudaEventDestroy(ev_fork);
+    destroy_streams();
+    int st_code = read_status(status, main);
+    if (st_code) {
+        cleanup();
+        return set_error(st_code, "qsim_run: %s", status_text(st_code));
+    }
+
+    qsim_state *S = new qsim_state();
+    S->device = dev;
+    S->n = n;
+    S->m = m;
+    S->codec = cfg.codec;
+    S->e = e;
+    S->stage_acc.resize(nst + 1);
+    CUDA_TRY(cudaMemcpy(S->stage_acc.data(), accs.p, (nst + 1) * sizeof(StageAccum), cudaMemcpyDeviceToHost));
+    const int fin = nst & 1;
+    S->dev_arena = dev_arena[fin];
+    S->host_arena = host_arena[fin];
+    dev_arena[fin] = nullptr;
+    host_arena[fin] = nullptr;
+    cleanup();
+    if ((rc = dev_alloc(reinterpret_cast<void **>(&S->table), nblocks * sizeof(BlockSlot)))) {
+        qsim_state_free(S);
+        return rc;
+    }
+    CUDA_TRY(cudaMemcpy(S->table, tables.p + fin * nblocks, nblocks * sizeof(BlockSlot), cudaMemcpyDeviceToDevice));
+
+    if (prof.on) {
+        double secs[P_NCAT];
+        uint64_t launches[P_NCAT];
+        prof.collect(secs, launches);
+        double bytes[P_NCAT] = {0}, flops[P_NCAT] = {0};
+        const double amps = std::ldexp(1.0, int(n));
+        for (size_t i = 0; i < nst; ++i) {
+            const double in_store = double(i == 0 ? S->stage_acc[nst].store_bytes : S->stage_acc[i - 1].store_bytes);
+            const double out_store = double(S->stage_acc[i].store_bytes);
+            const StageDev &sd = pd->stages[i];
+            bytes[raw ? P_COPY_IN : P_DECODE] += in_store + 8 * amps;
+            bytes[P_PASS] += 16 * amps * sd.npasses;
+            for (const Op &op : p->stages[i].ops)
+                flops[P_PASS] += (op.type == OP_DENSE ? 8.0 * double(1u << op.k) : op.type == OP_DIAG ? 6.0 : 0.0) * amps;
+            if (raw) {
+                bytes[P_COPY_OUT] += 8 * amps + out_store;
+            } else {
+                bytes[P_ENCODE_SIZE] += 8 * amps;
+                bytes[P_ENCODE] += 8 * amps + out_store;
+            }
+        }
+        for (int c = 0; c < P_NCAT; ++c) {
+            if (!launches[c]) continue;
+            qsim_kernel_stat ks;
+            memset(&ks, 0, sizeof(ks));
+            snprintf(ks.name, sizeof(ks.name), "%s", kProfNames[c]);
+            ks.launches = launches[c];
+            ks.seconds = secs[c];
+            ks.alg_bytes = bytes[c];
+            ks.alg_flops = flops[c];
+            S->kstats.push_back(ks);
+        }
+    }
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->seconds = ms * 1e-3;
+        stats->nstages = nst;
+        double E = 0, E2 = 0;
+        for (size_t i = 0; i < nst; ++i) {
+            const StageAccum &a = S->stage_acc[i];
+            E += std::sqrt(a.err_sq);
+            E2 += a.err_sq;
+            stats->peak_store_bytes = std::max<uint64_t>(stats->peak_store_bytes, a.store_bytes);
+            stats->peak_reserved_bytes = std::max<uint64_t>(stats->peak_reserved_bytes, a.reserved_bytes);
+            stats->host_tier_peak_bytes = std::max<uint64_t>(stats->host_tier_peak_bytes, a.host_bytes);
+            stats->overflow_blocks += a.overflow_blocks;
+            stats->blocks_encoded += a.blocks;
+            stats->groups += pd->stages[i].ngroups;
+        }
+        stats->err_norm_sum = E;
+        stats->err_sq_total = E2;
+        if (nst) {
+            stats->final_store_bytes = S->stage_acc[nst - 1].store_bytes;
+            stats->norm_sq = raw ? 0.0 : S->stage_acc[nst - 1].norm_sq;
+        }
+        if (raw) {
+            double ns = 0;
+            qsim_state_norm(S, &ns);
+            stats->norm_sq = ns;
+        }
+        const double b = std::sqrt(stats->norm_sq);
+        stats->fidelity_lower_bound = b > 0 ? std::min(1.0, (1.0 + stats->norm_sq - E * E) / (2.0 * b)) : 0.0;
+        stats->kernel_launches = g_launches.load();
+        stats->h2d_bytes = pd->counted ? 0 : pd->upload_bytes;
+        stats->d2h_bytes = (nst + 1) * sizeof(StageAccum) + sizeof(int);
+    }
+    pd->counted = true;
+    *out = S;
+    return QSIM_OK;
+}
+
+// decode blocks [b0, b0 + count) of a state (block order) into dst
+static int decode_state_blocks(const qsim_state *st, uint64_t b0, uint32_t count, float2 *dst, BlockRef *refs,
+                               uint32_t *ids_dev, int *status, cudaStream_t s) {
+    std::vector<uint32_t> ids(count);
+    for (uint32_t i = 0; i < count; ++i) ids[i] = uint32_t(b0 + i);
+    CUDA_TRY(cudaMemcpyAsync(ids_dev, ids.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    launch_gather_refs(st->table, ids_dev, count, refs, s);
+    if (st->codec == QSIM_CODEC_NONE) launch_copy_in(refs, count, st->m, dst, status, s);
+    else launch_decode(refs, count, st->m, dst, nullptr, status, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return QSIM_OK;
+}
+
+}  // namespace qsim
+
+using namespace qsim;
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+extern "C" {
+
+void qsim_config_default(qsim_config *cfg) {
+    if (!cfg) return;
+    memset(cfg, 0, sizeof(*cfg));
+    cfg->m = 20;
+    cfg->inner = 2;
+    cfg->k = 4;
+    cfg->prec = QSIM_PREC_FP32;
+    cfg->mode = QSIM_MODE_STREAMS;
+    cfg->streams = 2;
+    cfg->sizing = QSIM_SIZING_EXACT;
+    cfg->codec = QSIM_CODEC_QSZ1;
+    cfg->eps = 1e-3;
+    cfg->predictor_margin = 0.05;
+}
+
+const char *qsim_last_error(void) { return g_err; }
+
+uint64_t qsim_kernel_launch_count(void) { return g_launches.load(); }
+
+void qsim_release_cached_memory(void) {
+    Cache &c = cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    for (auto &kv : c.dev_free) cudaFree(kv.second);
+    for (auto &kv : c.host_free) cudaFreeHost(kv.second);
+    c.dev_free.clear();
+    c.host_free.clear();
+}
+
+size_t qsim_worst_case_bytes(uint32_t m) {
+    if (m < uint32_t(kQszMinM) || m > uint32_t(kQszMaxM)) return 0;
+    return size_t(qsz_worst_case(int(m)));
+}
+
+int qsim_plan_stages(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_config *cfg, qsim_plan **out) {
+    try {
+        return build_plan(n, gates, ngates, cfg, out);
+    } catch (const std::bad_alloc &) {
+        return set_error(QSIM_E_NOMEM, "host allocation failed while planning");
+    } catch (...) {
+        return set_error(QSIM_E_INVALID, "planning failed");
+    }
+}
+
+int qsim_plan_info(const qsim_plan *plan, size_t *nstages, uint32_t *stage_inner_masks) {
+    if (!plan || !nstages) return set_error(QSIM_E_INVALID, "null argument");
+    *nstages = plan->stages.size();
+    if (stage_inner_masks)
+        for (size_t i = 0; i < plan->stages.size(); ++i) {
+            uint32_t mk = 0;
+            for (uint32_t q : plan->stages[i].inner) mk |= 1u << (q - plan->cfg.m);
+            stage_inner_masks[i] = mk;
+        }
+    return QSIM_OK;
+}
+
+int qsim_plan_stage_gates(const qsim_plan *plan, size_t stage, size_t *first, size_t *count) {
+    if (!plan || !first || !count) return set_error(QSIM_E_INVALID, "null argument");
+    if (stage >= plan->stages.size()) return set_error(QSIM_E_INVALID, "stage index out of range");
+    *first = plan->stages[stage].first_gate;
+    *count = plan->stages[stage].ngates;
+    return QSIM_OK;
+}
+
+int qsim_plan_get_stats(const qsim_plan *plan, qsim_plan_stats *out) {
+    if (!plan || !out) return set_error(QSIM_E_INVALID, "null argument");
+    *out = plan->stats;
+    return QSIM_OK;
+}
+
+int qsim_plan_stage_ops(const qsim_plan *plan, size_t stage, size_t *count, qsim_op_info *ops) {
+    if (!plan || !count) return set_error(QSIM_E_INVALID, "null argument");
+    if (stage >= plan->stages.size()) return set_error(QSIM_E_INVALID, "stage index out of range");
+    const Stage &st = plan->stages[stage];
+    const size_t cap = *count;
+    *count = st.ops.size();
+    if (!ops) return QSIM_OK;
+    if (cap < st.ops.size()) return set_error(QSIM_E_CAPACITY, "ops capacity %zu < %zu", cap, st.ops.size());
+    const uint32_t m = plan->cfg.m;
+    for (size_t i = 0; i < st.ops.size(); ++i) {
+        const Op &op = st.ops[i];
+        qsim_op_info &o = ops[i];
+        memset(&o, 0, sizeof(o));
+        o.type = op.type;
+        o.ngates = op.ngates;
+        o.basis = op.basis;
+        if (op.type == OP_DENSE) {
+            o.nq = op.k;
+            for (uint32_t j = 0; j < op.k; ++j) o.qubits[j] = op.wq[j] < m ? op.wq[j] : st.inner[op.wq[j] - m];
+        } else if (op.type == OP_DIAG) {
+            o.nq = op.k;
+            for (uint32_t j = 0; j < op.k; ++j) o.qubits[j] = op.fq[j];
+        }
+        o.u = op.u.empty() ? nullptr : reinterpret_cast<const double *>(op.u.data());
+        for (size_t pi = 0; pi < st.passes.size(); ++pi)
+            for (uint32_t oi : st.passes[pi].ops)
+                if (oi == i) o.pass = uint32_t(pi);
+    }
+    return QSIM_OK;
+}
+
+void qsim_plan_free(qsim_plan *plan) {
+    if (!plan) return;
+    drop_plan_dev(plan);
+    delete plan;
+}
+
+int qsim_run(const qsim_plan *plan, void *cuda_stream, qsim_state **out, qsim_stats *stats) {
+    if (!plan || !out) return set_error(QSIM_E_INVALID, "null argument");
+    *out = nullptr;
+    try {
+        return run_plan(plan, static_cast<cudaStream_t>(cuda_stream), out, stats);
+    } catch (const std::bad_alloc &) {
+        return set_error(QSIM_E_NOMEM, "host allocation failed");
+    } catch (...) {
+        return set_error(QSIM_E_CUDA, "run failed");
+    }
+}
+
+int qsim_state_stage_stats(const qsim_state *st, size_t stage, uint64_t *store_bytes, uint64_t *reserved_bytes,
+                           double *err_sq) {
+    if (!st) return set_error(QSIM_E_INVALID, "null state");
+    if (stage + 1 >= st->stage_acc.size()) return set_error(QSIM_E_INVALID, "stage index out of range");
+    const StageAccum &a = st->stage_acc[stage];
+    if (store_bytes) *store_bytes = a.store_bytes;
+    if (reserved_bytes) *reserved_bytes = a.reserved_bytes;
+    if (err_sq) *err_sq = a.err_sq;
+    return QSIM_OK;
+}
+
+void qsim_profile_enable(int on) { g_profile.store(on ? 1 : 0); }
+
+int qsim_state_kernel_stats(const qsim_state *st, qsim_kernel_stat *out, size_t cap, size_t *count) {
+    if (!st || !count) return set_error(QSIM_E_INVALID, "null argument");
+    *count = st->kstats.size();
+    if (!out) return QSIM_OK;
+    if (cap < st->kstats.size()) return set_error(QSIM_E_CAPACITY, "capacity %zu < %zu", cap, st->kstats.size());
+    for (size_t i = 0; i < st->kstats.size(); ++i) out[i] = st->kstats[i];
+    return QSIM_OK;
+}
+
+void qsim_state_free(qsim_state *st) {
+    if (!st) return;
+    dev_free(st->dev_arena);
+    host_free(st->host_arena);
+    dev_free(st->table);
+    delete st;
+}
+
+int qsim_state_decompress(const qsim_state *st, float *d_out, void *cuda_stream) {
+    if (!st || !d_out) return set_error(QSIM_E_INVALID, "null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    const uint64_t nblocks = 1ull << (st->n - st->m);
+    DevBuf<BlockRef> refs;
+    DevBuf<uint32_t> ids;
+    int rc;
+    const uint32_t chunk = uint32_t(std::min<uint64_t>(nblocks, 4096));
+    if ((rc = refs.alloc(chunk)) || (rc = ids.alloc(chunk))) return rc;
+    int *status = device_ctx(st->device).status;
+    for (uint64_t b = 0; b < nblocks; b += chunk) {
+        uint32_t cnt = uint32_t(std::min<uint64_t>(chunk, nblocks - b));
+        rc = decode_state_blocks(st, b, cnt, reinterpret_cast<float2 *>(d_out) + (b << st->m), refs.p, ids.p, status, s);
+        if (rc) return rc;
+    }
+    int code = read_status(status, s);
+    if (code) return set_error(code, "decompress: %s", status_text(code));
+    return QSIM_OK;
+}
+
+int qsim_amplitudes(const qsim_state *st, const uint64_t *idx, size_t count, float *out) {
+    if (!st || (count && (!idx || !out))) return set_error(QSIM_E_INVALID, "null argument");
+    if (!count) return QSIM_OK;
+    const uint32_t m = st->m;
+    const uint64_t N = 1ull << st->n;
+    std::map<uint64_t, uint32_t> slot;
+    for (size_t i = 0; i < count; ++i) {
+        if (idx[i] >= N) return set_error(QSIM_E_INVALID, "amplitude index out of range");
+        slot.emplace(idx[i] >> m, 0);
+    }
+    uint32_t k = 0;
+    std::vector<uint32_t> bids;
+    for (auto &kv : slot) {
+        kv.second = k++;
+        bids.push_back(uint32_t(kv.first));
+    }
+    std::vector<uint32_t> h_slot(count), h_local(count);
+    for (size_t i = 0; i < count; ++i) {
+        h_slot[i] = slot[idx[i] >> m];
+        h_local[i] = uint32_t(idx[i] & ((1ull << m) - 1));
+    }
+    cudaStream_t s = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    DevBuf<BlockRef> refs;
+    DevBuf<uint32_t> ids, d_slot, d_local;
+    DevBuf<float2> blocks, d_out;
+    const uint32_t chunk = uint32_t(std::min<size_t>(bids.size(), std::max<uint64_t>(1, (1ull << 26) >> m)));
+    int rc;
+    if ((rc = refs.alloc(chunk)) || (rc = ids.alloc(chunk)) || (rc = blocks.alloc(uint64_t(chunk) << m)) ||
+        (rc = d_slot.alloc(count)) || (rc = d_local.alloc(count)) || (rc = d_out.alloc(count))) {
+        cudaStreamDestroy(s);
+        return rc;
+    }
+    int *status = device_ctx(st->device).status;
+    std::vector<float2> host(count);
+    // process the touched blocks chunk by chunk
+    for (size_t b0 = 0; b0 < bids.size(); b0 += chunk) {
+        const uint32_t cnt = uint32_t(std::min<size_t>(chunk, bids.size() - b0));
+        CUDA_TRY(cudaMemcpyAsync(ids.p, bids.data() + b0, cnt * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        launch_gather_refs(st->table, ids.p, cnt, refs.p, s);
+        if (st->codec == QSIM_CODEC_NONE) launch_copy_in(refs.p, cnt, m, blocks.p, status, s);
+        else launch_decode(refs.p, cnt, m, blocks.p, nullptr, status, s);
+        std::vector<uint32_t> sel_slot, sel_local;
+        std::vector<size_t> sel_pos;
+        for (size_t i = 0; i < count; ++i)
+            if (h_slot[i] >= b0 && h_slot[i] < b0 + cnt) {
+                sel_slot.push_back(uint32_t(h_slot[i] - b0));
+                sel_local.push_back(h_local[i]);
+                sel_pos.push_back(i);
+            }
+        if (sel_pos.empty()) continue;
+        CUDA_TRY(cudaMemcpyAsync(d_slot.p, sel_slot.data(), sel_slot.size() * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(d_local.p, sel_local.data(), sel_local.size() * 4, cudaMemcpyHostToDevice, s));
+        k_gather_amps<<<unsigned((sel_pos.size() + 255) / 256), 256, 0, s>>>(blocks.p, d_slot.p, d_local.p,
+                                                                            sel_pos.size(), int(m), d_out.p);
+        count_launch();
+        std::vector<float2> tmp(sel_pos.size());
+        CUDA_TRY(cudaMemcpyAsync(tmp.data(), d_out.p, tmp.size() * sizeof(float2), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        for (size_t t = 0; t < sel_pos.size(); ++t) host[sel_pos[t]] = tmp[t];
+    }
+    int code = read_status(status, s);
+    cudaStreamDestroy(s);
+    if (code) return set_error(code, "amplitudes: %s", status_text(code));
+    memcpy(out, host.data(), count * sizeof(float2));
+    return QSIM_OK;
+}
+
+static int reduce_state(const qsim_state *st, const double *ref, double acc_out[4]) {
+    const uint32_t m = st->m;
+    const uint64_t nblocks = 1ull << (st->n - st->m);
+    cudaPointerAttributes attr{};
+    bool ref_dev = false;
+    if (ref) {
+        if (cudaPointerGetAttributes(&attr, ref) == cudaSuccess && attr.type == cudaMemoryTypeDevice) ref_dev = true;
+        cudaGetLastError();
+    }
+    cudaStream_t s = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    const uint32_t chunk = uint32_t(std::min<uint64_t>(nblocks, std::max<uint64_t>(1, (1ull << 24) >> m)));
+    DevBuf<BlockRef> refs;
+    DevBuf<uint32_t> ids;
+    DevBuf<float2> blocks;
+    DevBuf<double2> rbuf;
+    DevBuf<double> acc;
+    int rc;
+    if ((rc = refs.alloc(chunk)) || (rc = ids.alloc(chunk)) || (rc = blocks.alloc(uint64_t(chunk) << m)) ||
+        (rc = acc.alloc(4)) || (ref && !ref_dev && (rc = rbuf.alloc(uint64_t(chunk) << m)))) {
+        cudaStreamDestroy(s);
+        return rc;
+    }
+    CUDA_TRY(cudaMemsetAsync(acc.p, 0, 4 * sizeof(double), s));
+    int *status = device_ctx(st->device).status;
+    for (uint64_t b = 0; b < nblocks; b += chunk) {
+        const uint32_t cnt = uint32_t(std::min<uint64_t>(chunk, nblocks - b));
+        rc = decode_state_blocks(st, b, cnt, blocks.p, refs.p, ids.p, status, s);
+        if (rc) { cudaStreamDestroy(s); return rc; }
+        const uint64_t amps = uint64_t(cnt) << m;
+        const double2 *r = nullptr;
+        if (ref) {
+            if (ref_dev) {
+                r = reinterpret_cast<const double2 *>(ref) + (b << m);
+            } else {
+                CUDA_TRY(cudaMemcpyAsync(rbuf.p, ref + 2 * (b << m), amps * sizeof(double2), cudaMemcpyHostToDevice, s));
+                r = rbuf.p;
+            }
+        }
+        k_reduce_fid<<<unsigned(std::min<uint64_t>(152 * 4, (amps + 255) / 256)), 256, 0, s>>>(r, blocks.p, amps, acc.p);
+        count_launch();
+    }
+    CUDA_TRY(cudaMemcpyAsync(acc_out, acc.p, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    int code = read_status(status, s);
+    cudaStreamDestroy(s);
+    if (code) return set_error(code, "readout: %s", status_text(code));
+    return QSIM_OK;
+}
+
+int qsim_fidelity(const qsim_state *st, const double *ref, double *f) {
+    if (!st || !ref || !f) return set_error(QSIM_E_INVALID, "null argument");
+    double a[4];
+    int rc = reduce_state(st, ref, a);
+    if (rc) return rc;
+    const double den = std::sqrt(a[2] * a[3]);
+    *f = den > 0 ? std::sqrt(a[0] * a[0] + a[1] * a[1]) / den : 0.0;
+    return QSIM_OK;
+}
+
+int qsim_state_norm(const qsim_state *st, double *norm_sq) {
+    if (!st || !norm_sq) return set_error(QSIM_E_INVALID, "null argument");
+    double a[4];
+    int rc = reduce_state(st, nullptr, a);
+    if (rc) return rc;
+    *norm_sq = a[3];
+    return QSIM_OK;
+}
+
+int qsim_state_block_stream(const qsim_state *st, uint64_t block, void *host_out, size_t cap, size_t *bytes) {
+    if (!st || !bytes) return set_error(QSIM_E_INVALID, "null argument");
+    const uint64_t nblocks = 1ull << (st->n - st->m);
+    if (block >= nblocks) return set_error(QSIM_E_INVALID, "block index out of range");
+    BlockSlot slot;
+    CUDA_TRY(cudaMemcpy(&slot, st->table + block, sizeof(slot), cudaMemcpyDeviceToHost));
+    *bytes = slot.bytes;
+    if (cap < slot.bytes) return set_error(QSIM_E_CAPACITY, "buffer of %zu bytes < stream of %llu", cap,
+                                           (unsigned long long)slot.bytes);
+    if (!host_out) return set_error(QSIM_E_INVALID, "null output");
+    CUDA_TRY(cudaMemcpy(host_out, slot.ptr, slot.bytes, cudaMemcpyDefault));
+    return QSIM_OK;
+}
+
+int qsim_compress_block(const float *d_amps, uint32_t m, double eb, void *d_out, size_t cap, size_t *out_bytes,
+                        void *cuda_stream) {
+    if (!d_amps || !d_out || !out_bytes) return set_error(QSIM_E_INVALID, "null argument");
+    if (m < uint32_t(kQszMinM) || m > uint32_t(kQszMaxM)) return set_error(QSIM_E_INVALID, "m=%u not in 5..26", m);
+    if ((reinterpret_cast<uintptr_t>(d_amps) & 15) || (reinterpret_cast<uintptr_t>(d_out) & 15))
+        return set_error(QSIM_E_INVALID, "device buffers must be 16-byte aligned");
+    int e;
+    if (!qsz_step_exponent(eb, &e)) return set_error(QSIM_E_INVALID, "error bound out of range");
+    int dev;
+    CUDA_TRY(cudaGetDevice(&dev));
+    DeviceCtx &c = device_ctx(dev);
+    std::lock_guard<std::mutex> lk(c.mu);
+    int rc = ensure_device_ctx(c);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    EncTarget t{};
+    t.ptr = static_cast<uint8_t *>(d_out);
+    t.cap = cap;
+    EncResult r{};
+    CUDA_TRY(cudaMemcpyAsync(c.tgt, &t, sizeof(t), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c.res, &r, sizeof(r), cudaMemcpyHostToDevice, s));
+    launch_encode(reinterpret_cast<const float2 *>(d_amps), 1, int(m), e, c.tgt, c.res, 0, nullptr, nullptr, nullptr,
+                  make_scratch(c.lb_state, c.lb_ctr), c.status, s);
+    CUDA_TRY(cudaMemcpyAsync(&r, c.res, sizeof(r), cudaMemcpyDeviceToHost, s));
+    int code = read_status(c.status, s);
+    if (code) return set_error(code, "compress: %s", status_text(code));
+    *out_bytes = r.total;
+    if (r.overflow) return set_error(QSIM_E_CAPACITY, "stream needs %llu bytes, cap is %zu",
+                                     (unsigned long long)r.total, cap);
+    return QSIM_OK;
+}
+
+int qsim_decompress_block(const void *d_in, size_t in_bytes, float *d_amps, uint32_t m, void *cuda_stream) {
+    if (!d_in || !d_amps) return set_error(QSIM_E_INVALID, "null argument");
+    if (m < uint32_t(kQszMinM) || m > uint32_t(kQszMaxM)) return set_error(QSIM_E_INVALID, "m=%u not in 5..26", m);
+    if ((reinterpret_cast<uintptr_t>(d_in) & 15) || (reinterpret_cast<uintptr_t>(d_amps) & 15))
+        return set_error(QSIM_E_INVALID, "device buffers must be 16-byte aligned");
+    int dev;
+    CUDA_TRY(cudaGetDevice(&dev));
+    DeviceCtx &c = device_ctx(dev);
+    std::lock_guard<std::mutex> lk(c.mu);
+    int rc = ensure_device_ctx(c);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    BlockRef r{static_cast<const uint8_t *>(d_in), in_bytes};
+    CUDA_TRY(cudaMemcpyAsync(c.ref, &r, sizeof(r), cudaMemcpyHostToDevice, s));
+    launch_decode(c.ref, 1, int(m), reinterpret_cast<float2 *>(d_amps), nullptr, c.status, s);
+    int code = read_status(c.status, s);
+    if (code) return set_error(code, "decompress: %s", status_text(code));
+    return QSIM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,375 @@
+// Host planner: canonicalisation, the circuit partition of Algorithm 1
+// (Sec. 4.1), greedy gate fusion and the layout of each stage's ops into
+// shared-memory tile passes.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <set>
+
+#include "qsim_internal.h"
+
+namespace qsim {
+
+namespace {
+
+bool is_unitary(const std::vector<cd> &u, uint32_t dim) {
+    for (uint32_t i = 0; i < dim; ++i)
+        for (uint32_t j = 0; j < dim; ++j) {
+            cd s = 0;
+            for (uint32_t r = 0; r < dim; ++r) s += std::conj(u[r * dim + i]) * u[r * dim + j];
+            cd want = (i == j) ? cd(1, 0) : cd(0, 0);
+            if (std::abs(s - want) > 1e-8) return false;
+        }
+    return true;
+}
+
+int canonicalize(uint32_t n, const qsim_gate *gates, size_t ngates, std::vector<Gate> *out) {
+    out->clear();
+    out->reserve(ngates);
+    for (size_t i = 0; i < ngates; ++i) {
+        const qsim_gate &g = gates[i];
+        Gate c;
+        if (g.flags & QSIM_GATE_PHASEFLIP) {
+            if (n < 64 && (g.basis >> n) != 0)
+                return set_error(QSIM_E_INVALID, "gate %zu: phase-flip basis out of range", i);
+            c.phaseflip = true;
+            c.diag = true;
+            c.basis = g.basis;
+            c.nq = n;
+            out->push_back(std::move(c));
+            continue;
+        }
+        if (g.nq < 1 || g.nq > 6) return set_error(QSIM_E_INVALID, "gate %zu: nq=%u not in 1..6", i, g.nq);
+        if (!g.u) return set_error(QSIM_E_INVALID, "gate %zu: matrix is NULL", i);
+        c.nq = g.nq;
+        for (uint32_t j = 0; j < g.nq; ++j) {
+            if (g.q[j] >= n) return set_error(QSIM_E_INVALID, "gate %zu: qubit %u >= n", i, g.q[j]);
+            for (uint32_t l = 0; l < j; ++l)
+                if (g.q[l] == g.q[j]) return set_error(QSIM_E_INVALID, "gate %zu: repeated qubit", i);
+            c.q[j] = g.q[j];
+        }
+        uint32_t dim = 1u << g.nq;
+        c.u.resize(size_t(dim) * dim);
+        bool diag = true;
+        for (uint32_t r = 0; r < dim; ++r)
+            for (uint32_t col = 0; col < dim; ++col) {
+                double re = g.u[2 * (r * dim + col)], im = g.u[2 * (r * dim + col) + 1];
+                if (!isfinite(re) || !isfinite(im))
+                    return set_error(QSIM_E_INVALID, "gate %zu: non-finite matrix entry", i);
+                c.u[r * dim + col] = cd(re, im);
+                if (r != col && (re != 0.0 || im != 0.0)) diag = false;
+            }
+        if (!is_unitary(c.u, dim)) return set_error(QSIM_E_INVALID, "gate %zu: matrix is not unitary", i);
+        c.diag = diag;
+        out->push_back(std::move(c));
+    }
+    return QSIM_OK;
+}
+
+// Global qubits a gate counts toward the stage threshold (Algorithm 1). A
+// diagonal gate is block-local whatever its qubits: it counts none when
+// diagonal exemption is on, or when its own globals exceed the threshold.
+int counted_globals(const Gate &g, uint32_t n, uint32_t m, uint32_t thr, bool diag_exempt,
+                    uint64_t *mask) {
+    uint64_t s = 0;
+    uint32_t cnt = 0;
+    if (g.phaseflip) {
+        for (uint32_t q = m; q < n; ++q) { s |= 1ull << q; ++cnt; }
+    } else {
+        for (uint32_t j = 0; j < g.nq; ++j)
+            if (g.q[j] >= m) { s |= 1ull << g.q[j]; ++cnt; }
+    }
+    if (g.diag && (diag_exempt || cnt > thr)) { *mask = 0; return QSIM_OK; }
+    if (cnt > thr)
+        return set_error(QSIM_E_UNSUPPORTED, "a non-diagonal gate touches %u global qubits (threshold %u)",
+                         cnt, thr);
+    *mask = s;
+    return QSIM_OK;
+}
+
+// Embed matrix `u` acting on working bits `bits` (matrix bit j <-> bits[j])
+// into the space of the ascending working-bit set `S`.
+std::vector<cd> embed(const std::vector<cd> &u, const std::vector<uint32_t> &bits,
+                      const std::vector<uint32_t> &S) {
+    const uint32_t k = bits.size(), K = S.size();
+    std::vector<uint32_t> pos(k);
+    uint32_t gate_mask = 0;
+    for (uint32_t j = 0; j < k; ++j) {
+        pos[j] = std::find(S.begin(), S.end(), bits[j]) - S.begin();
+        gate_mask |= 1u << pos[j];
+    }
+    const uint32_t D = 1u << K, d = 1u << k;
+    std::vector<cd> out(size_t(D) * D, cd(0, 0));
+    for (uint32_t r = 0; r < D; ++r)
+        for (uint32_t c = 0; c < D; ++c) {
+            if ((r & ~gate_mask) != (c & ~gate_mask)) continue;
+            uint32_t rs = 0, cs = 0;
+            for (uint32_t j = 0; j < k; ++j) {
+                rs |= ((r >> pos[j]) & 1u) << j;
+                cs |= ((c >> pos[j]) & 1u) << j;
+            }
+            out[size_t(r) * D + c] = u[size_t(rs) * d + cs];
+        }
+    return out;
+}
+
+std::vector<cd> matmul(const std::vector<cd> &a, const std::vector<cd> &b, uint32_t D) {
+    std::vector<cd> c(size_t(D) * D, cd(0, 0));
+    for (uint32_t i = 0; i < D; ++i)
+        for (uint32_t l = 0; l < D; ++l) {
+            cd x = a[size_t(i) * D + l];
+            if (x == cd(0, 0)) continue;
+            for (uint32_t j = 0; j < D; ++j) c[size_t(i) * D + j] += x * b[size_t(l) * D + j];
+        }
+    return c;
+}
+
+bool matrix_is_diagonal(const std::vector<cd> &u, uint32_t D) {
+    for (uint32_t r = 0; r < D; ++r)
+        for (uint32_t c = 0; c < D; ++c)
+            if (r != c && u[size_t(r) * D + c] != cd(0, 0)) return false;
+    return true;
+}
+
+struct Fuser {
+    const std::vector<uint32_t> *inner;
+    uint32_t m, k;
+    std::vector<Op> *ops;
+    bool active = false;
+    std::vector<uint32_t> S;  // ascending working bits
+    std::vector<cd> U;
+    uint32_t ngates = 0;
+
+    int32_t working_bit(uint32_t q) const {
+        if (q < m) return int32_t(q);
+        auto it = std::find(inner->begin(), inner->end(), q);
+        if (it == inner->end()) return -1;
+        return int32_t(m + (it - inner->begin()));
+    }
+    uint32_t qubit_of(uint32_t w) const { return w < m ? w : (*inner)[w - m]; }
+
+    void flush() {
+        if (!active) return;
+        Op op{};
+        const uint32_t D = 1u << S.size();
+        op.k = S.size();
+        op.ngates = ngates;
+        if (matrix_is_diagonal(U, D)) {
+            op.type = OP_DIAG;
+            for (uint32_t j = 0; j < op.k; ++j) op.fq[j] = qubit_of(S[j]);
+            op.u.resize(D);
+            for (uint32_t r = 0; r < D; ++r) op.u[r] = U[size_t(r) * D + r];
+        } else {
+            op.type = OP_DENSE;
+            for (uint32_t j = 0; j < op.k; ++j) op.wq[j] = S[j];
+            op.u = U;
+        }
+        ops->push_back(std::move(op));
+        active = false;
+        S.clear();
+        U.clear();
+        ngates = 0;
+    }
+
+    void add(const Gate &g) {
+        if (g.phaseflip) {
+            flush();
+            Op op{};
+            op.type = OP_PHASEFLIP;
+            op.basis = g.basis;
+            op.ngates = 1;
+            ops->push_back(std::move(op));
+            return;
+        }
+        std::vector<uint32_t> wb(g.nq);
+        bool all_working = true;
+        for (uint32_t j = 0; j < g.nq; ++j) {
+            int32_t w = working_bit(g.q[j]);
+            if (w < 0) all_working = false;
+            wb[j] = uint32_t(w);
+        }
+        if (!all_working || g.nq > k) {
+            // block-local diagonal with outer qubits (or wider than k): a phase op
+            flush();
+            Op op{};
+            op.type = OP_DIAG;
+            op.k = g.nq;
+            op.ngates = 1;
+            const uint32_t d = 1u << g.nq;
+            for (uint32_t j = 0; j < g.nq; ++j) op.fq[j] = g.q[j];
+            op.u.resize(d);
+            for (uint32_t r = 0; r < d; ++r) op.u[r] = g.u[size_t(r) * d + r];
+            ops->push_back(std::move(op));
+            return;
+        }
+        std::set<uint32_t> uni(S.begin(), S.end());
+        uni.insert(wb.begin(), wb.end());
+        if (active && uni.size() <= k) {
+            std::vector<uint32_t> NS(uni.begin(), uni.end());
+            std::vector<cd> cur = embed(U, S, NS);
+            std::vector<cd> gm = embed(g.u, wb, NS);
+            U = matmul(gm, cur, 1u << NS.size());  // later gate on the left
+            S = NS;
+            ++ngates;
+            return;
+        }
+        flush();
+        std::set<uint32_t> own(wb.begin(), wb.end());
+        S.assign(own.begin(), own.end());
+        U = embed(g.u, wb, S);
+        ngates = 1;
+        active = true;
+    }
+};
+
+void layout_passes(Stage &st, uint32_t tile_bits) {
+    const uint32_t W = st.W;
+    uint32_t T = std::min(tile_bits, W);
+    const uint32_t L = std::min<uint32_t>(5, T);
+    st.passes.clear();
+    auto close = [&](std::set<uint32_t> &P, std::vector<uint32_t> &ops) {
+        if (ops.empty()) return;
+        for (uint32_t b = 0; P.size() < T && b < W; ++b) P.insert(b);
+        Pass p{};
+        p.T = T;
+        uint32_t t = 0;
+        for (uint32_t b : P) p.tile_pos[t++] = b;
+        p.ops = ops;
+        st.passes.push_back(std::move(p));
+        ops.clear();
+    };
+    std::set<uint32_t> P;
+    for (uint32_t b = 0; b < L; ++b) P.insert(b);
+    std::vector<uint32_t> cur;
+    for (uint32_t i = 0; i < st.ops.size(); ++i) {
+        const Op &op = st.ops[i];
+        if (op.type == OP_DENSE) {
+            std::set<uint32_t> need(P);
+            for (uint32_t j = 0; j < op.k; ++j) need.insert(op.wq[j]);
+            if (need.size() > T) {
+                close(P, cur);
+                P.clear();
+                for (uint32_t b = 0; b < L; ++b) P.insert(b);
+                for (uint32_t j = 0; j < op.k; ++j) P.insert(op.wq[j]);
+            } else {
+                P = need;
+            }
+        }
+        cur.push_back(i);
+    }
+    close(P, cur);
+}
+
+}  // namespace
+
+bool qsz_step_exponent(double eb, int *e) {
+    if (!(eb > 0.0) || !isfinite(eb)) return false;
+    int x;
+    (void)frexp(2.0 * eb, &x);
+    int v = x - 1;
+    if (v < kQszEMin || v > kQszEMax) return false;
+    *e = v;
+    return true;
+}
+
+int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_config *cfg,
+               qsim_plan **out) {
+    auto t0 = std::chrono::steady_clock::now();
+    if (!out || !cfg) return set_error(QSIM_E_INVALID, "null argument");
+    *out = nullptr;
+    if (n < 5 || n > 40) return set_error(QSIM_E_INVALID, "n=%u not in 5..40", n);
+    if (cfg->m < uint32_t(kQszMinM) || cfg->m > uint32_t(kQszMaxM) || cfg->m > n)
+        return set_error(QSIM_E_INVALID, "m=%u not in 5..min(26, n)", cfg->m);
+    if (cfg->k < 1 || cfg->k > 6) return set_error(QSIM_E_INVALID, "k=%u not in 1..6", cfg->k);
+    if (cfg->prec > QSIM_PREC_BF16X3) return set_error(QSIM_E_INVALID, "bad precision %u", cfg->prec);
+    if (cfg->mode > QSIM_MODE_PERSISTENT) return set_error(QSIM_E_INVALID, "bad mode %u", cfg->mode);
+    if (cfg->codec > QSIM_CODEC_NONE) return set_error(QSIM_E_INVALID, "bad codec %u", cfg->codec);
+    if (cfg->sizing > QSIM_SIZING_PREDICT) return set_error(QSIM_E_INVALID, "bad sizing %u", cfg->sizing);
+    if (cfg->mode == QSIM_MODE_STREAMS && (cfg->streams < 1 || cfg->streams > 16))
+        return set_error(QSIM_E_INVALID, "streams=%u not in 1..16", cfg->streams);
+    if (n < 64 && (cfg->init_basis >> n) != 0) return set_error(QSIM_E_INVALID, "init_basis out of range");
+    if (cfg->codec == QSIM_CODEC_QSZ1) {
+        int e;
+        double eb = cfg->eps * pow(2.0, -double(n) / 2.0);
+        if (!qsz_step_exponent(eb, &e)) return set_error(QSIM_E_INVALID, "eps gives an error bound out of range");
+    }
+    if (ngates && !gates) return set_error(QSIM_E_INVALID, "gates is NULL");
+
+    qsim_plan *p = new (std::nothrow) qsim_plan();
+    if (!p) return set_error(QSIM_E_NOMEM, "plan allocation");
+    p->n = n;
+    p->cfg = *cfg;
+    int rc = canonicalize(n, gates, ngates, &p->gates);
+    if (rc) { delete p; return rc; }
+
+    const uint32_t m = cfg->m;
+    const uint32_t thr = std::max<uint32_t>(cfg->inner, 2);
+    for (size_t i = 0; i < p->gates.size(); ++i) {
+        const Gate &g = p->gates[i];
+        if (!g.phaseflip && !g.diag && g.nq > cfg->k) {
+            delete p;
+            return set_error(QSIM_E_INVALID, "gate %zu is %u-qubit but k=%u", i, g.nq, cfg->k);
+        }
+    }
+
+    // ---- Algorithm 1: greedy in-order partition ----
+    uint64_t cur_mask = 0;
+    size_t cur_first = 0, cur_count = 0;
+    auto emit = [&](uint64_t mask) {
+        Stage st;
+        st.first_gate = cur_first;
+        st.ngates = cur_count;
+        for (uint32_t q = m; q < n; ++q)
+            if ((mask >> q) & 1) st.inner.push_back(q);
+        st.W = m + st.inner.size();
+        p->stages.push_back(std::move(st));
+    };
+    for (size_t i = 0; i < p->gates.size(); ++i) {
+        uint64_t gm;
+        rc = counted_globals(p->gates[i], n, m, thr, cfg->diag_exempt != 0, &gm);
+        if (rc) { delete p; return rc; }
+        if (cur_count && __builtin_popcountll(cur_mask | gm) > int(thr)) {
+            emit(cur_mask);
+            cur_mask = 0;
+            cur_first = i;
+            cur_count = 0;
+        }
+        cur_mask |= gm;
+        ++cur_count;
+    }
+    if (cur_count) emit(cur_mask);
+
+    // ---- fusion and tile passes per stage ----
+    const uint32_t tile_bits = cfg->tile_bits ? cfg->tile_bits : 12;
+    if (tile_bits < 6 || tile_bits > 13) { delete p; return set_error(QSIM_E_INVALID, "tile_bits must be 6..13"); }
+    for (Stage &st : p->stages) {
+        Fuser fz;
+        fz.inner = &st.inner;
+        fz.m = m;
+        fz.k = cfg->k;
+        fz.ops = &st.ops;
+        for (size_t i = st.first_gate; i < st.first_gate + st.ngates; ++i) fz.add(p->gates[i]);
+        fz.flush();
+        layout_passes(st, std::max<uint32_t>(tile_bits, std::min<uint32_t>(st.W, 5 + cfg->k)));
+    }
+
+    qsim_plan_stats &s = p->stats;
+    s.nstages = p->stages.size();
+    s.ngates = p->gates.size();
+    for (const Stage &st : p->stages) {
+        for (const Op &op : st.ops) {
+            if (op.type == OP_DENSE) ++s.dense_ops;
+            else if (op.type == OP_DIAG) ++s.diag_ops;
+            else ++s.phaseflip_ops;
+        }
+        s.passes += st.passes.size();
+        s.max_working_log2 = std::max<uint64_t>(s.max_working_log2, st.W);
+    }
+    s.plan_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = p;
+    return QSIM_OK;
+}
+
+}  // namespace qsim

@@ -1,0 +1,97 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <stdint.h>
+#include <stddef.h>
+
+#include <complex>
+#include <string>
+#include <vector>
+
+#include "../../include/qsim.h"
+
+namespace qsim {
+
+using cd = std::complex<double>;
+
+// ---------------------------------------------------------------------------
+// error reporting (thread-local message, no exceptions across the ABI)
+// ---------------------------------------------------------------------------
+int set_error(int code, const char *fmt, ...);
+void clear_error();
+
+// ---------------------------------------------------------------------------
+// QSZ1 format constants (block codec; the layout is spelled out in codec.cu)
+// ---------------------------------------------------------------------------
+constexpr uint32_t kQszMagic = 0x315A5351u;  // "QSZ1"
+constexpr uint32_t kQszHeader = 32;
+constexpr int kQszMaxFrameLog = 12;
+constexpr int kQszMinM = 5;
+constexpr int kQszMaxM = 26;
+constexpr int kQszEMin = -126;
+constexpr int kQszEMax = 96;
+
+inline uint64_t pad16(uint64_t x) { return (x + 15) & ~uint64_t(15); }
+inline int frame_log_for(int m) { return m < kQszMaxFrameLog ? m : kQszMaxFrameLog; }
+inline uint64_t qsz_nframes(int m) { return uint64_t(1) << (m - frame_log_for(m)); }
+inline uint64_t qsz_data_start(int m) { return kQszHeader + pad16(4 * (qsz_nframes(m) + 1)); }
+inline uint64_t qsz_worst_case(int m) {
+    uint64_t F = uint64_t(1) << frame_log_for(m), C = F / 32;
+    return qsz_data_start(m) + qsz_nframes(m) * (pad16(2 * C) + 8 * F);
+}
+// largest e with 2^e <= 2*eb (frexp, exact); returns false when out of range
+bool qsz_step_exponent(double eb, int *e);
+
+// ---------------------------------------------------------------------------
+// plan
+// ---------------------------------------------------------------------------
+enum OpType : uint32_t { OP_DENSE = 0, OP_DIAG = 1, OP_PHASEFLIP = 2 };
+
+struct Op {
+    OpType type;
+    uint32_t k;             // dense: width; diag: number of qubits
+    uint32_t wq[6];         // dense: working-index bit of matrix bit j
+    uint32_t fq[6];         // diag: full qubit ids (matrix bit j)
+    uint64_t basis;         // phaseflip
+    std::vector<cd> u;      // dense: 2^k x 2^k row-major; diag: 2^k phases
+    uint32_t ngates;        // input gates folded into this op
+};
+
+struct Pass {
+    uint32_t T;                   // tile bits
+    uint32_t tile_pos[16];        // working bit of tile bit t, ascending
+    std::vector<uint32_t> ops;    // indices into Stage::ops
+};
+
+struct Stage {
+    size_t first_gate = 0, ngates = 0;
+    std::vector<uint32_t> inner;  // ascending global qubits that are local in this stage
+    uint32_t W = 0;               // working vector = 2^W amplitudes (m + |inner|)
+    std::vector<Op> ops;
+    std::vector<Pass> passes;
+};
+
+struct Gate {
+    uint32_t nq = 0;
+    uint32_t q[6] = {0, 0, 0, 0, 0, 0};
+    bool diag = false;
+    bool phaseflip = false;
+    uint64_t basis = 0;
+    std::vector<cd> u;  // 2^nq x 2^nq
+};
+
+}  // namespace qsim
+
+struct qsim_plan {
+    uint32_t n = 0;
+    qsim_config cfg{};
+    std::vector<qsim::Gate> gates;
+    std::vector<qsim::Stage> stages;
+    qsim_plan_stats stats{};
+};
+
+namespace qsim {
+// planner.cpp
+int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_config *cfg,
+               qsim_plan **out);
+}  // namespace qsim

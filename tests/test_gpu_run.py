@@ -1,0 +1,151 @@
+"""End-to-end GPU runs through the C ABI vs the oracle: uncompressed runs
+within 1e-5 of FP64, compressed runs on the quantisation grid with fidelity
+>= 0.99, closed forms, determinism across stream counts, the initial store,
+the pinned-host tier and readout calls."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import closed_forms as cf
+from paper_2410_14088_gb300 import inputs, qsim
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def state_c64(st):
+    return st.decompress().cpu().numpy()
+
+
+def test_config0_uncompressed_matches_fp64():
+    c = inputs.random_brick(16, 8, 0)
+    p = qsim.plan_stages(c, m=10, inner=2, k=4, codec=qsim.CODEC_NONE)
+    st = qsim.run(p)
+    got = state_c64(st)
+    want = oracle.simulate(c)
+    assert np.max(np.abs(got - want)) <= 1e-5
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 5, 6])
+def test_fused_widths_uncompressed(k):
+    c = inputs.qft_rz_cx(14, 2, 7) if k > 1 else inputs.qaoa_maxcut(14, 2, 3)
+    kk = max(k, 1)
+    p = qsim.plan_stages(c, m=9, inner=3, k=kk, codec=qsim.CODEC_NONE, tile_bits=10)
+    got = state_c64(qsim.run(p))
+    assert np.max(np.abs(got - oracle.simulate(c))) <= 1e-5
+
+
+def test_config0_compressed():
+    c = inputs.random_brick(16, 8, 0)
+    p = qsim.plan_stages(c, m=10, inner=2, k=4, eps=1e-3)
+    st = qsim.run(p)
+    got = state_c64(st)
+    ideal = oracle.simulate(c)
+    f = oracle.fidelity(ideal, got)
+    assert f >= 0.99
+    # every stored amplitude is on the codec grid q * 2^e
+    eb = 1e-3 * 2.0 ** -8
+    e = oracle.qsz_step_exponent(eb)
+    q = got.view(np.float32).astype(np.float64) / 2.0 ** e
+    assert np.all(q == np.rint(q))
+    # close to the oracle's staged + quantised simulation
+    staged, stages, _ = oracle.simulate_staged(c, 10, 2, 1e-3)
+    assert len(stages) == p.nstages
+    bound = len(stages) * math.sqrt(2 * (1 << 16)) * 2.0 ** e
+    assert np.linalg.norm(got - staged) <= bound
+    # GPU fidelity reduction and the run's rigorous bound
+    assert abs(st.fidelity(ideal) - f) < 1e-9
+    assert st.stats.fidelity_lower_bound <= f + 1e-9
+    assert st.stats.fidelity_lower_bound >= 0.99
+    assert abs(st.norm_sq() - st.stats.norm_sq) < 1e-9
+
+
+def test_streams_are_deterministic():
+    c = inputs.random_brick(16, 6, 4)
+    streams = []
+    for ns in (1, 2, 4):
+        st = qsim.run(qsim.plan_stages(c, m=10, inner=2, k=4, streams=ns))
+        streams.append([st.block_stream(b) for b in range(64)])
+    assert streams[0] == streams[1] == streams[2]
+
+
+def test_initial_store_shortcut():
+    # identity circuit: the store is the basis block plus identical zero streams
+    n, m, basis = 14, 8, 5000
+    c = inputs.Circuit(n, [inputs.RZ(0, 0.0)], basis)
+    st = qsim.run(qsim.plan_stages(c, m=m, inner=2, k=2))
+    blocks = [st.block_stream(b) for b in range(1 << (n - m))]
+    b0 = basis >> m
+    zero = oracle.qsz_encode(np.zeros(2 << m, np.float32), m, 1e-3 * 2 ** (-n / 2))
+    for b, s in enumerate(blocks):
+        if b != b0:
+            assert s == zero
+    one = np.zeros(2 << m, np.float32)
+    one[2 * (basis & ((1 << m) - 1))] = np.float32(np.exp(-0.0j).real)
+    assert blocks[b0] == oracle.qsz_encode(one, m, 1e-3 * 2 ** (-n / 2))
+
+
+@pytest.mark.parametrize("m,inner", [(20, 0), (14, 2), (12, 4)])
+def test_ghz_closed_form(m, inner):
+    n = 20
+    st = qsim.run(qsim.plan_stages(inputs.ghz(n), m=m, inner=inner, k=3, eps=1e-3))
+    got = state_c64(st)
+    assert np.max(np.abs(got - cf.ghz_state(n))) <= 1e-3 * 2 ** (-n / 2) * st.nstages
+
+
+def test_qft_basis_closed_form():
+    n, x = 18, 12345
+    c = inputs.Circuit(n, inputs.qft_gates(n), x)
+    st = qsim.run(qsim.plan_stages(c, m=12, inner=3, k=5, eps=1e-3))
+    want = cf.qft_basis_state(n, x)
+    assert st.fidelity(want) >= 0.99
+    got = state_c64(st)
+    assert np.max(np.abs(got - want)) <= 2 * st.nstages * 1e-3 * 2 ** (-n / 2) + 1e-5
+
+
+def test_grover_closed_form():
+    n, t, marked = 16, 4, 4321
+    st = qsim.run(qsim.plan_stages(inputs.grover(n, t, marked), m=10, inner=2, k=4, eps=1e-3))
+    assert st.fidelity(cf.grover_state(n, t, marked)) >= 0.99
+
+
+def test_amplitudes_and_host_tier():
+    c = inputs.qaoa_maxcut(18, 2, 6)
+    base = qsim.run(qsim.plan_stages(c, m=11, inner=2, k=4))
+    capped = qsim.run(qsim.plan_stages(c, m=11, inner=2, k=4, device_tier_cap_bytes=1 << 16))
+    assert capped.stats.host_tier_peak_bytes > 0
+    for b in range(0, 1 << 7, 9):
+        assert base.block_stream(b) == capped.block_stream(b)
+    full = state_c64(base)
+    idx = np.array([0, 1, 77, 5000, (1 << 18) - 1, 131072], dtype=np.uint64)
+    np.testing.assert_array_equal(capped.amplitudes(idx), full[idx.astype(np.int64)])
+
+
+def test_single_block_and_phaseflip_edges():
+    # m = n: one block, no global qubits; phase flips on several blocks
+    n = 12
+    c = inputs.grover(n, 2, 3001)
+    st = qsim.run(qsim.plan_stages(c, m=12, inner=0, k=3, codec=qsim.CODEC_NONE))
+    assert np.max(np.abs(state_c64(st) - oracle.simulate(c))) <= 1e-5
+    st = qsim.run(qsim.plan_stages(c, m=6, inner=2, k=3, codec=qsim.CODEC_NONE))
+    assert np.max(np.abs(state_c64(st) - oracle.simulate(c))) <= 1e-5
+
+
+def test_config1_full_size_sampled():
+    # 28-qubit QFT of a random basis state + 4 x (RZ layer, CX ladder), m = 22
+    c = inputs.qft_rz_cx(28, 4, 1)
+    p = qsim.plan_stages(c, m=22, inner=2, k=5, eps=1e-3)
+    st = qsim.run(p)
+    assert st.stats.fidelity_lower_bound >= 0.99
+    idx = (inputs.splitmix64_array(77, 4096) >> np.uint64(36)).astype(np.uint64)
+    got = st.amplitudes(idx).astype(np.complex128)
+    want = cf.qft_rz_cx_amplitudes(28, c.meta["x"], c.meta["rz_angles"], idx)
+    eb = 1e-3 * 2.0 ** -14
+    # codec error per stage is <= eb per component; fp32 gate error is far smaller
+    assert np.max(np.abs(got - want)) <= 2 * eb * st.nstages
+    # sampled fidelity estimate
+    fs = abs(np.vdot(want, got)) / (np.linalg.norm(want) * np.linalg.norm(got))
+    assert fs >= 0.99

@@ -1,0 +1,91 @@
+"""Host planner (no GPU): Algorithm 1 parity with the oracle's partition,
+fusion correctness by replaying the fused ops with the oracle, and the
+planner's argument checks."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle.partition import UnsupportedGate, partition
+from paper_2410_14088_gb300 import inputs, qsim
+
+CASES = [
+    (inputs.random_brick(12, 6, 3), 7, 2, 4, 0),
+    (inputs.qft_rz_cx(12, 2, 9), 8, 2, 5, 0),
+    (inputs.qft_rz_cx(14, 3, 1), 9, 3, 3, 0),
+    (inputs.qaoa_maxcut(12, 2, 5), 6, 4, 4, 0),
+    (inputs.qaoa_maxcut(12, 2, 5), 6, 2, 4, 1),
+    (inputs.grover(10, 3, 700), 6, 2, 4, 0),
+    (inputs.ghz(13), 8, 2, 2, 0),
+]
+
+
+@pytest.mark.parametrize("circ,m,inner,k,dx", CASES, ids=lambda x: str(getattr(x, "family", x)))
+def test_partition_matches_oracle(circ, m, inner, k, dx):
+    p = qsim.plan_stages(circ, m=m, inner=inner, k=k, diag_exempt=dx)
+    want = partition(circ.gates, circ.n, m, inner, bool(dx))
+    got = p.stages()
+    assert [(f, c) for f, c, _ in got] == [(s.gate_indices[0], len(s.gate_indices)) for s in want]
+    assert [inn for _, _, inn in got] == [s.inner for s in want]
+
+
+def apply_op(psi, n, op):
+    if op["type"] == 2:
+        oracle.lib().oracle_apply_phaseflip(oracle._ptr(psi, oracle.ctypes.c_double), n, op["basis"])
+        return
+    if op["type"] == 0:
+        u = op["u"]
+    else:
+        u = np.diag(op["u"])
+    g = inputs.Gate("op", op["qubits"], (), u)
+    oracle.apply_gate(psi, n, g)
+
+
+@pytest.mark.parametrize("circ,m,inner,k,dx", CASES, ids=lambda x: str(getattr(x, "family", x)))
+def test_fused_ops_reproduce_the_circuit(circ, m, inner, k, dx):
+    p = qsim.plan_stages(circ, m=m, inner=inner, k=k, diag_exempt=dx)
+    n = circ.n
+    psi = oracle.basis_state(n, circ.init_basis)
+    total_gates = 0
+    for s, (f, c, inner_q) in enumerate(p.stages()):
+        ops = p.stage_ops(s)
+        for op in ops:
+            total_gates += op["ngates"]
+            if op["type"] == 0:
+                assert op["nq"] <= k
+                # dense ops only touch local or inner qubits
+                assert all(q < m or q in inner_q for q in op["qubits"])
+            apply_op(psi, n, op)
+    assert total_gates == len(circ.gates)
+    want = oracle.simulate(circ)
+    assert np.max(np.abs(psi.view(np.complex128) - want)) <= 1e-12
+
+
+def test_fusion_reduces_ops():
+    c = inputs.qft_rz_cx(16, 4, 2)
+    p = qsim.plan_stages(c, m=12, inner=2, k=5)
+    st = p.stats()
+    assert st["dense_ops"] + st["diag_ops"] < len(c.gates) / 2
+    assert st["nstages"] == len(partition(c.gates, 16, 12, 2))
+
+
+def test_errors():
+    c = inputs.random_brick(8, 2, 1)
+    with pytest.raises(qsim.QsimError) as ei:
+        qsim.plan_stages(c, m=4)
+    assert ei.value.code == qsim.E_INVALID
+    with pytest.raises(qsim.QsimError) as ei:
+        qsim.plan_stages(inputs.ghz(8), m=6, k=1)  # CX is a non-diagonal 2-qubit gate
+    assert ei.value.code == qsim.E_INVALID
+    bad = inputs.Gate("bad", (0,), (), np.array([[1, 1], [0, 1]], dtype=np.complex128))
+    with pytest.raises(qsim.QsimError) as ei:
+        qsim.plan_stages(8, [bad], m=6)
+    assert ei.value.code == qsim.E_INVALID
+    three = inputs.Gate("ccx", (5, 6, 7), (), np.kron(np.eye(4), inputs.mat_x()))
+    with pytest.raises(qsim.QsimError) as ei:
+        qsim.plan_stages(8, [three], m=5, inner=2, k=3)
+    assert ei.value.code == qsim.E_UNSUPPORTED
+    with pytest.raises(UnsupportedGate):
+        partition([three], 8, 5, 2)
+    pf = inputs.PHASEFLIP(200, 8)
+    p = qsim.plan_stages(8, [inputs.H(7), pf], m=5, inner=2, k=3)
+    assert p.nstages == 1
