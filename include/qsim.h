@@ -225,6 +225,33 @@ int qsim_compress_block(const float *d_amps, uint32_t m, double eb, void *d_out,
                         size_t *out_bytes, void *cuda_stream);
 
 /*
+ * Allocation-free variant of qsim_compress_block. This is a library
+ * addition with no counterpart in the paper.
+ *
+ * qsim_compress_block allocates device scratch with cudaMalloc on its first
+ * call on a device. Callers that cannot allow an allocation at that point —
+ * an application whose framework already owns the device memory through its
+ * own pool, a service that must keep a fixed footprint once started, or a
+ * latency-critical loop where cudaMalloc/cudaFree would synchronise the
+ * device — use this entry point instead. Its scratch is one fixed device
+ * array inside the library image (look-back words for blocks of up to
+ * 2^QSIM_NOALLOC_MAX_M amplitudes, 32 KiB, plus 256 bytes), held by every GPU
+ * that loads the library until the process exits. It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *
+ * Arguments, output and errors are those of qsim_compress_block; in
+ * addition m > QSIM_NOALLOC_MAX_M is rejected with QSIM_E_INVALID. The first
+ * call on a device looks up the array's device address (once per device,
+ * with that device current); make that first call before any stream capture.
+ * All calls share the one array and each call clears the parts it uses, so
+ * calls must not overlap on the GPU: this call synchronises cuda_stream
+ * before it returns, and calls from several host threads are serialised.
+ */
+#define QSIM_NOALLOC_MAX_M 24
+int qsim_compress_block_noalloc(const float *d_amps, uint32_t m, double eb, void *d_out, size_t cap,
+                                size_t *out_bytes, void *cuda_stream);
+
+/*
  * Decompress a QSZ1 stream (d_in, device, in_bytes) into d_amps (device,
  * 2^m complex64). Synchronises cuda_stream to report the status.
  * Errors: INVALID, CORRUPT (bad magic/header/offsets/widths), CUDA.

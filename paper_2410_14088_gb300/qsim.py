@@ -104,6 +104,7 @@ SIGNATURES = {
     "qsim_state_free": (None, [_VP]),
     "qsim_worst_case_bytes": (_SZ, [_U32]),
     "qsim_compress_block": (ctypes.c_int, [_VP, _U32, ctypes.c_double, _VP, _SZ, ctypes.POINTER(_SZ), _VP]),
+    "qsim_compress_block_noalloc": (ctypes.c_int, [_VP, _U32, ctypes.c_double, _VP, _SZ, ctypes.POINTER(_SZ), _VP]),
     "qsim_decompress_block": (ctypes.c_int, [_VP, _SZ, _VP, _U32, _VP]),
     "qsim_profile_enable": (None, [ctypes.c_int]),
     "qsim_state_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(KernelStat), _SZ, ctypes.POINTER(_SZ)]),
@@ -370,6 +371,20 @@ def compress_block_needed(amps, m, eb, cap, stream=None):
     nb = ctypes.c_size_t()
     rc = lib().qsim_compress_block(ctypes.c_void_p(amps.data_ptr()), m, eb, ctypes.c_void_p(out.data_ptr()), cap,
                                    ctypes.byref(nb), _stream_ptr(stream))
+    return rc, nb.value
+
+
+NOALLOC_MAX_M = 24
+
+
+def compress_block_noalloc(amps, m: int, eb: float, out, cap: Optional[int] = None, stream=None):
+    """qsim_compress_block_noalloc: same stream as compress_block, but the
+    library allocates nothing (its scratch is a fixed device array). `out` is
+    the caller's uint8 CUDA tensor. Returns (rc, nbytes) without raising."""
+    cap = out.numel() if cap is None else cap
+    nb = ctypes.c_size_t()
+    rc = lib().qsim_compress_block_noalloc(ctypes.c_void_p(amps.data_ptr()), m, eb, ctypes.c_void_p(out.data_ptr()),
+                                           cap, ctypes.byref(nb), _stream_ptr(stream))
     return rc, nb.value
 
 
