@@ -23,6 +23,7 @@
 
 #include "codec.cuh"
 #include "device_common.cuh"
+#include "gates.cuh"
 
 namespace qsim {
 
@@ -67,132 +68,202 @@ __device__ __forceinline__ int32_t unzigzag(uint32_t z) {
 // ---------------------------------------------------------------------------
 // Decode: one CTA per frame (grid-stride over all frames of all blocks).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_decode(const BlockRef *__restrict__ in, uint32_t nblocks, int m,
-                                               float2 *__restrict__ wv, uint32_t *__restrict__ hist,
-                                               int *status) {
-    const FrameGeom g = geom(m);
-    __shared__ uint32_t s_w[2 * MAX_C];
-    __shared__ uint32_t s_off[2 * MAX_C];
-    __shared__ uint32_t s_warp[NW];
-    __shared__ uint32_t s_total;
-    __shared__ uint64_t s_hdr[4];  // frame start, frame end, e, ok
-    __shared__ uint32_t s_hist[32];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const uint64_t items = uint64_t(nblocks) * g.nframes;
+// Leading phase ops of a stage, applied to each decoded amplitude: w is the
+// amplitude's working index, gb the full-index bits of its group's outer qubits.
+__device__ __forceinline__ float2 apply_pre_ops(float2 v, uint64_t w, uint64_t gb, const OpDev *ops, uint32_t nops,
+                                                const float2 *__restrict__ mats) {
+    for (uint32_t o = 0; o < nops; ++o) {
+        const OpDev &op = ops[o];
+        if (op.type == OP_DIAG) {
+            uint32_t idx = 0;
+            for (uint32_t j = 0; j < op.k; ++j) {
+                const uint32_t src = op.dsrc[j];
+                const uint64_t bit = src < 64 ? (w >> src) & 1ull : (gb >> (src - 64)) & 1ull;
+                idx |= uint32_t(bit) << j;
+            }
+            const float2 ph = __ldg(mats + op.mat + idx);
+            v = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
+        } else if (op.basis_in_stage && gb == op.basis_outer && w == op.basis_w) {
+            v = make_float2(-v.x, -v.y);
+        }
+    }
+    return v;
+}
 
-    for (uint64_t item = blockIdx.x; item < items; item += gridDim.x) {
+// One warp per frame, no block-wide barriers: the warp reads the header and
+// the frame's offsets with one load per lane, the 2C width bytes with one
+// 8-byte load per lane (lane l holds the widths of chunks 8l..8l+7), builds
+// the chunk offsets with a warp prefix sum, then decodes the chunk pairs
+// (Re chunk c, Im chunk c) eight at a time with all sixteen payload loads in
+// flight: bit-plane transpose, zigzag inverse, inclusive prefix sum (the
+// Lorenzo inverse), x' = q * 2^e, interleaved (re, im) stores.
+__global__ void __launch_bounds__(NT, 3) k_decode(const BlockRef *__restrict__ in, const BlockSlot *__restrict__ table,
+                                               const uint32_t *__restrict__ ids, uint32_t nblocks, int m,
+                                               float2 *__restrict__ wv, uint32_t *__restrict__ hist,
+                                               int *status, PreOps pre) {
+    const FrameGeom g = geom(m);
+    __shared__ OpDev s_pre[kMaxPreOps];
+    __shared__ uint32_t s_hist[NW][32];
+    if (threadIdx.x < pre.count) s_pre[threadIdx.x] = pre.ops[threadIdx.x];
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint64_t items = uint64_t(nblocks) * g.nframes;
+    const uint32_t padw = (2u * g.C + 15u) & ~15u;
+    for (uint64_t item = uint64_t(blockIdx.x) * NW + warp; item < items; item += uint64_t(gridDim.x) * NW) {
         const uint32_t j = uint32_t(item / g.nframes), f = uint32_t(item % g.nframes);
-        const uint8_t *s = in[j].ptr;
-        const uint64_t bytes = in[j].bytes;
+        const uint8_t *sp;
+        uint64_t bytes;
+        if (table) {
+            const BlockSlot sl = table[ids[j]];
+            sp = sl.ptr;
+            bytes = sl.bytes;
+        } else {
+            sp = in[j].ptr;
+            bytes = in[j].bytes;
+        }
         float2 *dst = wv + (uint64_t(j) << m) + uint64_t(f) * g.F;
-        if (tid < 32) s_hist[tid] = 0;
-        if (tid == 0) {
-            uint64_t ok = 1, a = 0, b = 0;
-            int e = 0;
-            if (bytes < 32 || s == nullptr || (reinterpret_cast<uintptr_t>(s) & 15)) {
-                ok = 0;
-            } else {
-                const uint32_t *h32 = reinterpret_cast<const uint32_t *>(s);
-                const uint64_t *h64 = reinterpret_cast<const uint64_t *>(s);
-                uint32_t w1 = h32[1], w2 = h32[2];
-                e = int(int8_t(uint8_t(w2 >> 16)));
-                uint64_t total = h64[2];
-                if (h32[0] != kQszMagic || w1 != 1u || (w2 & 0xff) != uint32_t(m) ||
-                    ((w2 >> 8) & 0xff) != uint32_t(g.fl) || (w2 >> 24) != 0 || h32[3] != g.nframes ||
-                    h64[3] != 0 || e < kQszEMin || e > kQszEMax || total > bytes || total < g.data_start)
-                    ok = 0;
-                if (ok) {
-                    const uint32_t *offs = h32 + 8;
-                    if (offs[0] != g.data_start || offs[g.nframes] != total) ok = 0;
-                    a = offs[f];
-                    b = offs[f + 1];
-                    if (b < a || b > total || a < g.data_start) ok = 0;
-                    if (ok && b > a && (b - a < ((2ull * g.C + 15) & ~15ull) || ((a | b) & 15))) ok = 0;
-                }
-            }
-            s_hdr[0] = a;
-            s_hdr[1] = b;
-            s_hdr[2] = uint64_t(int64_t(e));
-            s_hdr[3] = ok;
+        if (hist) s_hist[warp][lane] = 0;
+        // ---- header and offsets: one load per lane ----
+        const bool can = sp != nullptr && !(reinterpret_cast<uintptr_t>(sp) & 15) && bytes >= g.data_start;
+        uint32_t hv = 0;
+        if (can) {
+            const uint32_t *h32 = reinterpret_cast<const uint32_t *>(sp);
+            if (lane < 8) hv = h32[lane];
+            else if (lane == 8) hv = h32[8];                    // offsets[0]
+            else if (lane == 9) hv = h32[8 + f];                // offsets[f]
+            else if (lane == 10) hv = h32[8 + f + 1];           // offsets[f+1]
+            else if (lane == 11) hv = h32[8 + g.nframes];       // offsets[nframes]
         }
-        __syncthreads();
-        const uint64_t fa = s_hdr[0], fb = s_hdr[1];
-        const int e = int(int64_t(s_hdr[2]));
-        bool ok = s_hdr[3] != 0;
+        const uint32_t magic = __shfl_sync(kFull, hv, 0), w1 = __shfl_sync(kFull, hv, 1);
+        const uint32_t w2 = __shfl_sync(kFull, hv, 2), nfr = __shfl_sync(kFull, hv, 3);
+        const uint64_t total = uint64_t(__shfl_sync(kFull, hv, 4)) | (uint64_t(__shfl_sync(kFull, hv, 5)) << 32);
+        const uint64_t rsv = uint64_t(__shfl_sync(kFull, hv, 6)) | (uint64_t(__shfl_sync(kFull, hv, 7)) << 32);
+        const uint32_t o0 = __shfl_sync(kFull, hv, 8), fa = __shfl_sync(kFull, hv, 9);
+        const uint32_t fb = __shfl_sync(kFull, hv, 10), on = __shfl_sync(kFull, hv, 11);
+        const int e = int(int8_t(uint8_t(w2 >> 16)));
+        bool ok = can && magic == kQszMagic && w1 == 1u && (w2 & 0xff) == uint32_t(m) &&
+                  ((w2 >> 8) & 0xff) == uint32_t(g.fl) && (w2 >> 24) == 0 && nfr == g.nframes && rsv == 0 &&
+                  e >= kQszEMin && e <= kQszEMax && total <= bytes && total >= g.data_start &&
+                  o0 == g.data_start && on == total && fb >= fa && fb <= total && fa >= g.data_start &&
+                  !((fa | fb) & 15u) && (fb == fa || fb - fa >= padw);
+        uint32_t wsum = 0, wmax = 0;
+        uint2 wb = make_uint2(0, 0);
+        uint32_t base_off = 0;
         if (ok && fb > fa) {
-            const uint8_t *fp = s + fa;
-            const uint32_t wv_ = tid < int(2 * g.C) ? fp[tid] : 0;
-            const uint32_t off = block_exclusive_scan<NT>(wv_, s_warp, &s_total);
-            if (tid < int(2 * g.C)) {
-                s_w[tid] = wv_;
-                s_off[tid] = off;
-            }
-            __syncthreads();
-            const uint64_t words = s_total;
-            const uint64_t padw = (2ull * g.C + 15) & ~15ull;
-            // widths > 32 make the stream corrupt (the barrier is reached by every thread)
-            const bool wide = __syncthreads_or(tid < int(2 * g.C) && wv_ > 32) != 0;
-            const bool bad = wide || words == 0 || (fb - fa) != padw + ((4 * words + 15) & ~15ull);
-            if (bad) {
-                ok = false;
-            } else {
-                const uint32_t *payload = reinterpret_cast<const uint32_t *>(fp + padw);
-                const float step = exp2i(e);
-                uint32_t my_max = 0;
-                for (uint32_t c = warp; c < g.C; c += NW) {
-                    const uint32_t wr = s_w[c], wi = s_w[g.C + c];
-                    uint32_t xr = lane < int(wr) ? __ldg(payload + s_off[c] + lane) : 0u;
-                    uint32_t xi = lane < int(wi) ? __ldg(payload + s_off[g.C + c] + lane) : 0u;
-                    uint32_t zr = warp_bit_transpose(xr, lane);
-                    uint32_t zi = warp_bit_transpose(xi, lane);
-                    uint32_t qr = uint32_t(unzigzag(zr)), qi = uint32_t(unzigzag(zi));
+            // ---- widths: lane l holds chunks 8l .. 8l+7 (Re chunks 0..C-1, then Im chunks) ----
+            if (8u * lane < 2u * g.C) wb = *reinterpret_cast<const uint2 *>(sp + fa + 8u * lane);
 #pragma unroll
-                    for (int o = 1; o < 32; o <<= 1) {
-                        uint32_t tr = __shfl_up_sync(kFull, qr, o);
-                        uint32_t ti = __shfl_up_sync(kFull, qi, o);
-                        if (lane >= o) { qr += tr; qi += ti; }
-                    }
-                    const int32_t sr = int32_t(qr), si = int32_t(qi);
-                    dst[c * 32 + lane] = make_float2(float(sr) * step, float(si) * step);
-                    if (hist) {
-                        uint32_t br = 32 - __clz(sr < 0 ? uint32_t(-sr) : uint32_t(sr));
-                        uint32_t bi = 32 - __clz(si < 0 ? uint32_t(-si) : uint32_t(si));
-                        atomicAdd(&s_hist[br & 31], 1u);
-                        atomicAdd(&s_hist[bi & 31], 1u);
-                        my_max = max(my_max, max(br, bi));
-                    }
+            for (int t = 0; t < 4; ++t) {
+                const uint32_t a = (wb.x >> (8 * t)) & 0xff, b = (wb.y >> (8 * t)) & 0xff;
+                wsum += a + b;
+                wmax = max(wmax, max(a, b));
+            }
+            uint32_t incl = wsum;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            base_off = incl - wsum;
+            const uint32_t words = __shfl_sync(kFull, incl, 31);
+            const uint32_t maxw = __reduce_max_sync(kFull, wmax);
+            ok = maxw <= 32 && words > 0 && uint64_t(fb - fa) == padw + ((4ull * words + 15) & ~15ull);
+        }
+        if (!ok) {
+            if (lane == 0) raise_status(status, QSIM_E_CORRUPT);
+        }
+        if (!ok || fb == fa) {
+            for (uint32_t i = lane; i < g.F; i += 32) dst[i] = make_float2(0.f, 0.f);
+            if (hist && lane == 0) atomicAdd(&hist[uint64_t(j) * 32], 2 * g.F);
+            continue;
+        }
+        const uint32_t *payload = reinterpret_cast<const uint32_t *>(sp + fa + padw);
+        const float step = exp2i(e);
+        // ---- chunk pairs, eight at a time ----
+        for (uint32_t c0 = 0; c0 < g.C; c0 += 8) {
+            // widths/offsets of Re chunks c0.. (owner lane c0/8) and Im chunks C+c0.. (owner (C+c0)/8)
+            const uint32_t lr = c0 >> 3, li = (g.C + c0) >> 3;
+            const uint2 wr8 = make_uint2(__shfl_sync(kFull, wb.x, lr), __shfl_sync(kFull, wb.y, lr));
+            const uint2 wi8 = make_uint2(__shfl_sync(kFull, wb.x, li), __shfl_sync(kFull, wb.y, li));
+            uint32_t offr = __shfl_sync(kFull, base_off, lr), offi = __shfl_sync(kFull, base_off, li);
+            // Im chunks of a small frame (C < 8) share the owner lane with the Re chunks: skip those slots
+            const uint32_t si0 = (g.C + c0) & 7u;
+            uint32_t xr[8], xi[8], wr[8], wi[8];
+            {
+                uint32_t sr_ = 0, si_ = 0;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const uint32_t ar = t < 4 ? (wr8.x >> (8 * t)) & 0xff : (wr8.y >> (8 * (t - 4))) & 0xff;
+                    const uint32_t ti = si0 + t;
+                    const uint32_t ai = ti < 8 ? (ti < 4 ? (wi8.x >> (8 * ti)) & 0xff : (wi8.y >> (8 * (ti - 4))) & 0xff) : 0;
+                    wr[t] = ar;
+                    wi[t] = ai;
+                }
+                // offsets of the Im chunks start after the skipped slots of their owner lane
+                for (uint32_t t = 0; t < si0; ++t)
+                    offi += t < 4 ? (wi8.x >> (8 * t)) & 0xff : (wi8.y >> (8 * (t - 4))) & 0xff;
+#pragma unroll
+                for (int t = 0; t < 8; ++t) {
+                    const bool live = c0 + t < g.C;
+                    xr[t] = (live && lane < int(wr[t])) ? __ldg(payload + offr + sr_ + lane) : 0u;
+                    xi[t] = (live && lane < int(wi[t])) ? __ldg(payload + offi + si_ + lane) : 0u;
+                    sr_ += wr[t];
+                    si_ += wi[t];
+                }
+            }
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const uint32_t c = c0 + t;
+                if (c >= g.C) break;
+                const uint32_t zr = warp_bit_transpose(xr[t], lane);
+                const uint32_t zi = warp_bit_transpose(xi[t], lane);
+                uint32_t qr = uint32_t(unzigzag(zr)), qi = uint32_t(unzigzag(zi));
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t tr = __shfl_up_sync(kFull, qr, o);
+                    const uint32_t ti = __shfl_up_sync(kFull, qi, o);
+                    if (lane >= o) { qr += tr; qi += ti; }
+                }
+                const int32_t sr = int32_t(qr), si = int32_t(qi);
+                float2 v = make_float2(float(sr) * step, float(si) * step);
+                if (pre.count) {
+                    const uint64_t w = (uint64_t(j % pre.G) << m) | (uint64_t(f) * g.F + c * 32 + lane);
+                    v = apply_pre_ops(v, w, pre.gbase[j / pre.G], s_pre, pre.count, pre.mats);
+                }
+                dst[c * 32 + lane] = v;
+                if (hist) {
+                    const uint32_t br = 32 - __clz(sr < 0 ? uint32_t(-sr) : uint32_t(sr));
+                    const uint32_t bi = 32 - __clz(si < 0 ? uint32_t(-si) : uint32_t(si));
+                    atomicAdd(&s_hist[warp][br & 31], 1u);
+                    atomicAdd(&s_hist[warp][bi & 31], 1u);
                 }
             }
         }
-        if (!ok) raise_status(status, QSIM_E_CORRUPT);
-        if (!ok || fb == fa) {
-            for (uint32_t i = tid; i < g.F; i += NT) dst[i] = make_float2(0.f, 0.f);
-            if (hist && tid == 0) s_hist[0] += 2 * g.F;
+        if (hist) {
+            __syncwarp();
+            const uint32_t v = s_hist[warp][lane];
+            if (v) atomicAdd(&hist[uint64_t(j) * 32 + lane], v);
+            __syncwarp();
         }
-        __syncthreads();
-        if (hist && tid < 32 && s_hist[tid]) atomicAdd(&hist[uint64_t(j) * 32 + tid], s_hist[tid]);
-        __syncthreads();
     }
 }
 
 // ---------------------------------------------------------------------------
-// Per-frame quantisation + widths. Returns (in registers) the bit-plane words
-// when KEEP is set. Used by both the encoder and the sizing pass.
+// Encode: one CTA per frame, ticket-ordered, decoupled look-back. The frame
+// image (widths, then bit-plane words) is assembled in shared memory while
+// warp 0 finds the frame's byte offset, then copied out with 16-byte stores.
+// The bit planes of a chunk, W_b = ballot(bit b of z_j), are produced for all
+// b at once by a 32x32 bit transpose across the warp (five shuffle stages).
 // ---------------------------------------------------------------------------
-struct QuantOut {
-    double err_sq, norm_sq;
-    int bad;  // QSIM_E_* or 0
-};
+constexpr uint32_t kStageWords = (256 + 8 * 4096) / 4 + 4;  // widths + worst-case payload + pad
 
-// ---------------------------------------------------------------------------
-// Encode: one CTA per frame, ticket-ordered, decoupled look-back.
-// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
                                                const EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
                                                int only_overflowed, const uint32_t *__restrict__ ids,
                                                BlockSlot *__restrict__ table, StageAccum *acc,
                                                LookbackScratch scr, int *status) {
     const FrameGeom g = geom(m);
+    __shared__ __align__(16) uint32_t s_stage[kStageWords];
     __shared__ uint32_t s_w[2 * MAX_C];
     __shared__ uint32_t s_off[2 * MAX_C];
     __shared__ uint32_t s_warp[NW];
@@ -201,6 +272,7 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
     __shared__ uint64_t s_excl;
     __shared__ double s_red[2][NW];
     __shared__ int s_skip;
+    __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     if (tid == 0) {
@@ -214,31 +286,34 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
     __syncthreads();
 
     if (!s_skip) {
-        if (only_overflowed && tid == 0 && f == 0) {
-            // this block is encoded again into a fresh slot
-        }
         const float2 *src = wv + (uint64_t(j) << m) + uint64_t(f) * g.F;
         const float inv_step = exp2i(-e);
         const float step = exp2i(e);
-        uint32_t words_r[MAX_CPW], words_i[MAX_CPW];
-        double err_sq = 0.0, norm_sq = 0.0;
+        // x - x' is exact in FP32 (|x - x'| <= s/2 <= |x'|/2 when q != 0, x' = 0 otherwise), so the
+        // per-thread sums are FP32 and only the per-CTA totals are accumulated in FP64
+        float err_sq = 0.f, norm_sq = 0.f;
         int bad = 0;
+        float2 vin[MAX_CPW];
 #pragma unroll
         for (int i = 0; i < MAX_CPW; ++i) {
-            words_r[i] = 0;
-            words_i[i] = 0;
+            const uint32_t c = warp + i * NW;
+            vin[i] = c < g.C ? __ldcs(src + c * 32 + lane) : make_float2(0.f, 0.f);
+        }
+        uint32_t zr[MAX_CPW], zi[MAX_CPW];
+#pragma unroll
+        for (int i = 0; i < MAX_CPW; ++i) {
+            zr[i] = zi[i] = 0;
             const uint32_t c = warp + i * NW;
             if (c < g.C) {
-                const float2 v = src[c * 32 + lane];
                 int32_t q[2];
-                const float x[2] = {v.x, v.y};
+                const float x[2] = {vin[i].x, vin[i].y};
 #pragma unroll
                 for (int p = 0; p < 2; ++p) {
                     if (!isfinite(x[p])) {
                         bad = QSIM_E_INVALID;
                         q[p] = 0;
                     } else {
-                        float t = x[p] * inv_step;  // exact: power-of-two scaling
+                        const float t = x[p] * inv_step;  // exact: power-of-two scaling
                         if (fabsf(t) >= 1073741824.0f) {
                             bad = bad ? bad : QSIM_E_RANGE;
                             q[p] = 0;
@@ -247,24 +322,16 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
                         }
                     }
                     const float xr = float(q[p]) * step;
-                    const double dx = double(x[p]) - double(xr);
-                    err_sq += dx * dx;
-                    norm_sq += double(xr) * double(xr);
+                    const float dx = x[p] - xr;
+                    err_sq = fmaf(dx, dx, err_sq);
+                    norm_sq = fmaf(xr, xr, norm_sq);
                 }
-                int32_t pr = __shfl_up_sync(kFull, q[0], 1);
-                int32_t pi = __shfl_up_sync(kFull, q[1], 1);
-                const uint32_t zr = zigzag(lane ? int32_t(uint32_t(q[0]) - uint32_t(pr)) : q[0]);
-                const uint32_t zi = zigzag(lane ? int32_t(uint32_t(q[1]) - uint32_t(pi)) : q[1]);
-                const uint32_t wr = 32 - __clz(__reduce_or_sync(kFull, zr));
-                const uint32_t wi = 32 - __clz(__reduce_or_sync(kFull, zi));
-                for (uint32_t b = 0; b < wr; ++b) {
-                    uint32_t bal = __ballot_sync(kFull, (zr >> b) & 1u);
-                    if (lane == int(b)) words_r[i] = bal;
-                }
-                for (uint32_t b = 0; b < wi; ++b) {
-                    uint32_t bal = __ballot_sync(kFull, (zi >> b) & 1u);
-                    if (lane == int(b)) words_i[i] = bal;
-                }
+                const int32_t pr = __shfl_up_sync(kFull, q[0], 1);
+                const int32_t pi = __shfl_up_sync(kFull, q[1], 1);
+                zr[i] = zigzag(lane ? int32_t(uint32_t(q[0]) - uint32_t(pr)) : q[0]);
+                zi[i] = zigzag(lane ? int32_t(uint32_t(q[1]) - uint32_t(pi)) : q[1]);
+                const uint32_t wr = 32 - __clz(__reduce_or_sync(kFull, zr[i]));
+                const uint32_t wi = 32 - __clz(__reduce_or_sync(kFull, zi[i]));
                 if (lane == 0) {
                     s_w[c] = wr;
                     s_w[g.C + c] = wi;
@@ -275,12 +342,23 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
         __syncthreads();
         const uint32_t my_w = tid < int(2 * g.C) ? s_w[tid] : 0;
         const uint32_t my_off = block_exclusive_scan<NT>(my_w, s_warp, &s_total);
+        const uint32_t padw = (2u * g.C + 15u) & ~15u;
         if (tid < int(2 * g.C)) s_off[tid] = my_off;
+        // width bytes (and their zero padding) at the head of the frame image
+        if (tid < int(padw) / 4) {
+            uint32_t wbytes = 0;
+#pragma unroll
+            for (int t = 0; t < 4; ++t) {
+                const uint32_t x = 4 * tid + t;
+                wbytes |= (x < 2 * g.C ? s_w[x] : 0u) << (8 * t);
+            }
+            s_stage[tid] = wbytes;
+        }
         const uint32_t words = s_total;
-        const uint64_t padw = (2ull * g.C + 15) & ~15ull;
         const uint32_t len = words ? uint32_t(padw + ((4ull * words + 15) & ~15ull)) : 0u;
+        __syncthreads();
 
-        // ---- decoupled look-back over the preceding frames of this block ----
+        // ---- warp 0: decoupled look-back over the preceding frames of this block ----
         if (warp == 0) {
             uint64_t *st = scr.state + uint64_t(j) * g.nframes;
             if (f == 0) {
@@ -299,8 +377,8 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
                     if (p >= 0) {
                         long long spins = 0;
                         while (true) {
-                            uint64_t w = ld_relaxed_u64(st + p);
-                            uint32_t fl = uint32_t(w >> 32) & 3u;
+                            const uint64_t w = ld_relaxed_u64(st + p);
+                            const uint32_t fl = uint32_t(w >> 32) & 3u;
                             if (fl != 0 && uint32_t(w >> 34) == epoch) {
                                 flag = fl;
                                 val = uint32_t(w);
@@ -331,25 +409,30 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
                 }
             }
         }
+        // ---- bit-plane words into the frame image: W_b = ballot(bit b of z) ----
+        uint32_t *stage_words = s_stage + padw / 4;
+#pragma unroll
+        for (int i = 0; i < MAX_CPW; ++i) {
+            const uint32_t c = warp + i * NW;
+            if (c < g.C) {
+                const uint32_t wr = s_w[c], wi = s_w[g.C + c];
+                // lane b receives W_b = ballot(bit b of z): the bit-matrix transpose of the chunk's codes
+                const uint32_t word_r = warp_bit_transpose(zr[i], lane);
+                const uint32_t word_i = warp_bit_transpose(zi[i], lane);
+                if (lane < int(wr)) stage_words[s_off[c] + lane] = word_r;
+                if (lane < int(wi)) stage_words[s_off[g.C + c] + lane] = word_i;
+            }
+        }
+        if (words + uint32_t(tid) < (len > padw ? (len - padw) / 4 : 0u)) stage_words[words + tid] = 0;  // pad
         __syncthreads();
         const uint64_t frame_off = g.data_start + s_excl;
         uint8_t *out = tgt[j].ptr;
         const uint64_t cap = tgt[j].cap;
         const bool fits = frame_off + len <= cap;
         if (fits && len) {
-            uint8_t *fp = out + frame_off;
-            if (tid < int(padw)) fp[tid] = tid < int(2 * g.C) ? uint8_t(s_w[tid]) : uint8_t(0);
-            uint32_t *payload = reinterpret_cast<uint32_t *>(fp + padw);
-#pragma unroll
-            for (int i = 0; i < MAX_CPW; ++i) {
-                const uint32_t c = warp + i * NW;
-                if (c < g.C) {
-                    if (lane < int(s_w[c])) payload[s_off[c] + lane] = words_r[i];
-                    if (lane < int(s_w[g.C + c])) payload[s_off[g.C + c] + lane] = words_i[i];
-                }
-            }
-            const uint32_t padded = (len - uint32_t(padw)) / 4;  // words rounded up to 16 bytes
-            if (words + uint32_t(tid) < padded) payload[words + tid] = 0;
+            uint4 *o4 = reinterpret_cast<uint4 *>(out + frame_off);
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(s_stage);
+            for (uint32_t i = tid; i < len / 16; i += NT) o4[i] = s4[i];
         }
         if (!fits && tid == 0) atomicOr(&res[j].overflow, 1u);
         if (tid == 0 && g.data_start <= cap)
@@ -389,53 +472,136 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
             norm_sq += __shfl_xor_sync(kFull, norm_sq, o);
         }
         if (lane == 0) {
-            s_red[0][warp] = err_sq;
-            s_red[1][warp] = norm_sq;
+            s_red[0][warp] = double(err_sq);
+            s_red[1][warp] = double(norm_sq);
         }
         __syncthreads();
         if (tid == 0 && !only_overflowed) {
             double a = 0, b = 0;
             for (int w = 0; w < NW; ++w) { a += s_red[0][w]; b += s_red[1][w]; }
-            atomicAdd(&res[j].err_sq, a);
-            atomicAdd(&res[j].norm_sq, b);
-            if (acc) {
-                atomicAdd(&acc->err_sq, a);
-                atomicAdd(&acc->norm_sq, b);
+            if (scr.part) {
+                scr.part[item] = make_float2(float(a), float(b));  // reduced by the last CTA
+            } else {
+                atomicAdd(&res[j].err_sq, a);
+                atomicAdd(&res[j].norm_sq, b);
+                if (acc) {
+                    atomicAdd(&acc->err_sq, a);
+                    atomicAdd(&acc->norm_sq, b);
+                }
             }
         }
     }
-    // ---- last CTA resets the ticket counter and advances the epoch ----
+    // ---- last CTA: reduce the frame partials, reset the ticket counter, advance the epoch ----
     if (tid == 0) {
         __threadfence();
-        const uint32_t d = atomicAdd(scr.done, 1u);
-        if (d == gridDim.x - 1) {
-            *scr.ticket = 0;
-            *scr.done = 0;
-            __threadfence();
-            atomicExch(scr.epoch, (epoch + 1) & kEpochMask);
+        s_last = atomicAdd(scr.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (scr.part && !only_overflowed) {
+        // warp per block: sum its frames' partials in FP64
+        double ta = 0, tb = 0;
+        for (uint32_t jb = warp; jb < nblocks; jb += NW) {
+            double a = 0, b = 0;
+            for (uint32_t f2 = lane; f2 < g.nframes; f2 += 32) {
+                const float2 p = scr.part[uint64_t(jb) * g.nframes + f2];
+                a += double(p.x);
+                b += double(p.y);
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                a += __shfl_xor_sync(kFull, a, o);
+                b += __shfl_xor_sync(kFull, b, o);
+            }
+            if (lane == 0) {
+                res[jb].err_sq = a;
+                res[jb].norm_sq = b;
+            }
+            ta += a;
+            tb += b;
         }
+        if (lane == 0) {
+            s_red[0][warp] = ta;
+            s_red[1][warp] = tb;
+        }
+        __syncthreads();
+        if (tid == 0 && acc) {
+            double a = 0, b = 0;
+            for (int w = 0; w < NW; ++w) { a += s_red[0][w]; b += s_red[1][w]; }
+            atomicAdd(&acc->err_sq, a);
+            atomicAdd(&acc->norm_sq, b);
+        }
+    }
+    if (tid == 0) {
+        *scr.ticket = 0;
+        *scr.done = 0;
+        __threadfence();
+        atomicExch(scr.epoch, (epoch + 1) & kEpochMask);
     }
 }
 
 // ---------------------------------------------------------------------------
-// Sizing pass: exact stream size of every block (reads the data once more).
+// Reservation of one block's slot from the two-tier pool: device arena
+// first, then the pinned host arena; slots are padded to 256 bytes.
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(NT) k_encode_size(const float2 *__restrict__ wv, uint32_t nblocks, int m,
-                                                    int e, uint64_t *__restrict__ sizes, int *status) {
+__device__ __forceinline__ void reserve_slot(uint64_t want, const ArenaDev &dev, const ArenaDev &host, EncTarget *t,
+                                             int *status) {
+    const uint64_t sz = (want + 255) & ~255ull;
+    uint64_t off = atomicAdd(reinterpret_cast<unsigned long long *>(dev.bump), sz);
+    if (off + sz <= dev.cap) {
+        t->ptr = dev.base + off;
+        t->cap = sz;
+        t->tier = 0;
+        return;
+    }
+    if (host.base) {
+        off = atomicAdd(reinterpret_cast<unsigned long long *>(host.bump), sz);
+        if (off + sz <= host.cap) {
+            t->ptr = host.base + off;
+            t->cap = sz;
+            t->tier = 1;
+            return;
+        }
+    }
+    t->ptr = nullptr;
+    t->cap = 0;
+    t->tier = 0;
+    raise_status(status, QSIM_E_NOMEM);
+}
+
+// ---------------------------------------------------------------------------
+// Sizing pass: exact stream size of every block (reads the data once more),
+// then the last CTA to finish reserves each block's slot and clears the size
+// counters for the next launch.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(NT) k_encode_size(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
+                                                    uint64_t *__restrict__ sizes, uint32_t *done_ctr,
+                                                    ArenaDev dev, ArenaDev host, EncTarget *__restrict__ tgt,
+                                                    EncResult *__restrict__ res, int *status) {
     const FrameGeom g = geom(m);
     __shared__ uint32_t s_words[NW];
+    __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t items = uint64_t(nblocks) * g.nframes;
     const float inv_step = exp2i(-e);
     for (uint64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const uint32_t j = uint32_t(item / g.nframes), f = uint32_t(item % g.nframes);
         const float2 *src = wv + (uint64_t(j) << m) + uint64_t(f) * g.F;
+        float2 vin[MAX_CPW];
+#pragma unroll
+        for (int i = 0; i < MAX_CPW; ++i) {
+            const uint32_t c = warp + i * NW;
+            vin[i] = c < g.C ? src[c * 32 + lane] : make_float2(0.f, 0.f);
+        }
         uint32_t words = 0;
         int bad = 0;
-        for (uint32_t c = warp; c < g.C; c += NW) {
-            const float2 v = src[c * 32 + lane];
+#pragma unroll
+        for (int i = 0; i < MAX_CPW; ++i) {
+            const uint32_t c = warp + i * NW;
+            if (c >= g.C) break;
             int32_t q[2];
-            const float x[2] = {v.x, v.y};
+            const float x[2] = {vin[i].x, vin[i].y};
 #pragma unroll
             for (int p = 0; p < 2; ++p) {
                 float t = x[p] * inv_step;
@@ -461,6 +627,24 @@ __global__ void __launch_bounds__(NT) k_encode_size(const float2 *__restrict__ w
         }
         __syncthreads();
     }
+    if (!done_ctr) return;
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(done_ctr, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (uint32_t j = tid; j < nblocks; j += NT) {
+        const uint64_t want = ld_relaxed_u64(&sizes[j]) + g.data_start;
+        sizes[j] = 0;
+        res[j].total = 0;
+        res[j].overflow = 0;
+        res[j].err_sq = 0;
+        res[j].norm_sq = 0;
+        reserve_slot(want, dev, host, &tgt[j], status);
+    }
+    if (tid == 0) *done_ctr = 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -492,27 +676,7 @@ __global__ void k_reserve(uint32_t nblocks, const uint64_t *__restrict__ need, u
         res[j].err_sq = 0;
         res[j].norm_sq = 0;
     }
-    const uint64_t sz = (want + 255) & ~255ull;
-    uint64_t off = atomicAdd(reinterpret_cast<unsigned long long *>(dev.bump), sz);
-    if (off + sz <= dev.cap) {
-        tgt[j].ptr = dev.base + off;
-        tgt[j].cap = sz;
-        tgt[j].tier = 0;
-        return;
-    }
-    if (host.base) {
-        off = atomicAdd(reinterpret_cast<unsigned long long *>(host.bump), sz);
-        if (off + sz <= host.cap) {
-            tgt[j].ptr = host.base + off;
-            tgt[j].cap = sz;
-            tgt[j].tier = 1;
-            return;
-        }
-    }
-    tgt[j].ptr = nullptr;
-    tgt[j].cap = 0;
-    tgt[j].tier = 0;
-    raise_status(status, QSIM_E_NOMEM);
+    reserve_slot(want, dev, host, &tgt[j], status);
 }
 
 // Raw (uncompressed) store: copy blocks, 16 bytes per thread.
@@ -577,7 +741,16 @@ static unsigned grid_for(uint64_t items, unsigned cap) {
 void launch_decode(const BlockRef *in, uint32_t nblocks, int m, float2 *wv, uint32_t *hist, int *status,
                    cudaStream_t s) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
-    k_decode<<<grid_for(items, 152 * 8), NT, 0, s>>>(in, nblocks, m, wv, hist, status);
+    k_decode<<<grid_for((items + NW - 1) / NW, 152 * 8), NT, 0, s>>>(in, nullptr, nullptr, nblocks, m, wv, hist, status,
+                                                                   PreOps{});
+    count_launch();
+}
+
+void launch_decode_table(const BlockSlot *table, const uint32_t *ids, uint32_t nblocks, int m, float2 *wv,
+                         uint32_t *hist, int *status, const PreOps &pre, cudaStream_t s) {
+    const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
+    k_decode<<<grid_for((items + NW - 1) / NW, 152 * 8), NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist,
+                                                                   status, pre);
     count_launch();
 }
 
@@ -593,7 +766,18 @@ void launch_encode(const float2 *wv, uint32_t nblocks, int m, int e, const EncTa
 void launch_encode_size(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, int *status,
                         cudaStream_t s) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
-    k_encode_size<<<grid_for(items, 152 * 8), NT, 0, s>>>(wv, nblocks, m, e, sizes, status);
+    ArenaDev none{};
+    k_encode_size<<<grid_for(items, 152 * 8), NT, 0, s>>>(wv, nblocks, m, e, sizes, nullptr, none, none, nullptr,
+                                                           nullptr, status);
+    count_launch();
+}
+
+void launch_size_reserve(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, uint32_t *done_ctr,
+                         const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, int *status,
+                         cudaStream_t s) {
+    const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
+    k_encode_size<<<grid_for(items, 152 * 8), NT, 0, s>>>(wv, nblocks, m, e, sizes, done_ctr, dev, host, tgt, res,
+                                                           status);
     count_launch();
 }
 

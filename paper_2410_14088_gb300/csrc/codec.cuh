@@ -63,6 +63,7 @@ struct LookbackScratch {
     uint32_t *ticket;
     uint32_t *done;
     uint32_t *epoch;
+    float2 *part;       // per-frame (err_sq, norm_sq) partials, or null (then per-CTA atomics)
 };
 
 void count_launch();
@@ -74,6 +75,22 @@ void launch_encode(const float2 *wv, uint32_t nblocks, int m, int e, const EncTa
                    const LookbackScratch &scr, int *status, cudaStream_t s);
 void launch_encode_size(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, int *status,
                         cudaStream_t s);
+// sizing pass whose last CTA reserves every block's slot (sizes are left zeroed)
+void launch_size_reserve(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, uint32_t *done_ctr,
+                         const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, int *status,
+                         cudaStream_t s);
+// leading phase ops of a stage for the decoder (count <= kMaxPreOps)
+struct OpDev;
+struct PreOps {
+    const OpDev *ops = nullptr;
+    uint32_t count = 0;
+    uint32_t G = 1;                   // blocks per group
+    const float2 *mats = nullptr;
+    const uint64_t *gbase = nullptr;  // per group of the batch
+};
+// decode with the block references read from table[ids[j]]
+void launch_decode_table(const BlockSlot *table, const uint32_t *ids, uint32_t nblocks, int m, float2 *wv,
+                         uint32_t *hist, int *status, const PreOps &pre, cudaStream_t s);
 void launch_reserve(uint32_t nblocks, const uint64_t *need, uint64_t add_const, const float *pred_log2,
                     double margin, uint64_t worst, const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt,
                     EncResult *res, int retry_overflowed, int *status, cudaStream_t s);

@@ -252,8 +252,9 @@ static int ensure_device_ctx(DeviceCtx &c) {
     return QSIM_OK;
 }
 
-static LookbackScratch make_scratch(uint64_t *state, uint32_t *ctr) {
-    LookbackScratch s;
+static LookbackScratch make_scratch(uint64_t *state, uint32_t *ctr, float2 *part = nullptr) {
+    LookbackScratch s{};
+    s.part = part;
     s.state = state;
     s.ticket = ctr;
     s.done = ctr + 1;
@@ -290,6 +291,7 @@ struct StageDev {
     uint32_t W, G;              // working bits, blocks per group
     uint32_t ngroups;
     uint32_t pass_begin, npasses;
+    uint32_t pre_begin, npre;   // leading phase ops applied by the decoder
     std::vector<PassDev> passes_host;
 };
 
@@ -376,6 +378,34 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                 ids.push_back(uint32_t(full >> m));
             }
         }
+        auto diag_opdev = [&](const Op &op) {
+            OpDev od{};
+            od.type = op.type;
+            od.k = op.k;
+            if (op.type == OP_DIAG) {
+                for (uint32_t j = 0; j < op.k; ++j) {
+                    uint32_t q = op.fq[j];
+                    if (q < m) {
+                        od.dsrc[j] = q;
+                    } else {
+                        auto f = std::find(st.inner.begin(), st.inner.end(), q);
+                        od.dsrc[j] = f != st.inner.end() ? uint32_t(m + (f - st.inner.begin())) : 64 + q;
+                    }
+                }
+                od.mat = mats.size();
+                for (const cd &v : op.u) mats.push_back(make_float2(float(v.real()), float(v.imag())));
+            } else {
+                od.basis_in_stage = 1;
+                od.basis_outer = op.basis & outer_mask;
+                uint64_t w = op.basis & ((1ull << m) - 1);
+                for (size_t t = 0; t < st.inner.size(); ++t) w |= ((op.basis >> st.inner[t]) & 1ull) << (m + t);
+                od.basis_w = w;
+            }
+            return od;
+        };
+        sd.pre_begin = ops.size();
+        sd.npre = st.pre_ops.size();
+        for (uint32_t oi : st.pre_ops) ops.push_back(diag_opdev(st.ops[oi]));
         for (const Pass &ps : st.passes) {
             PassDev P{};
             P.T = ps.T;
@@ -413,26 +443,10 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                     od.mat = mats.size();
                     for (const cd &v : op.u) mats.push_back(make_float2(float(v.real()), float(v.imag())));
                     P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << (2 * op.k));
-                } else if (op.type == OP_DIAG) {
-                    for (uint32_t j = 0; j < op.k; ++j) {
-                        uint32_t q = op.fq[j];
-                        if (q < m) {
-                            od.dsrc[j] = q;
-                        } else {
-                            auto f = std::find(st.inner.begin(), st.inner.end(), q);
-                            od.dsrc[j] = f != st.inner.end() ? uint32_t(m + (f - st.inner.begin())) : 64 + q;
-                        }
-                    }
-                    od.mat = mats.size();
-                    for (const cd &v : op.u) mats.push_back(make_float2(float(v.real()), float(v.imag())));
-                    P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << op.k);
+                    P.kmax = std::max<uint32_t>(P.kmax, op.k);
                 } else {
-                    od.basis_in_stage = 1;
-                    od.basis_outer = op.basis & outer_mask;
-                    uint64_t w = op.basis & ((1ull << m) - 1);
-                    for (size_t t = 0; t < st.inner.size(); ++t)
-                        w |= ((op.basis >> st.inner[t]) & 1ull) << (m + t);
-                    od.basis_w = w;
+                    od = diag_opdev(op);
+                    if (op.type == OP_DIAG) P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << op.k);
                 }
                 ops.push_back(od);
             }
@@ -606,6 +620,7 @@ struct StreamWork {
     DevBuf<uint64_t> sizes;
     DevBuf<uint64_t> lb_state;
     DevBuf<uint32_t> lb_ctr;
+    DevBuf<float2> part;
 };
 
 static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsim_stats *stats) {
@@ -706,6 +721,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
         if ((rc = w.wv.alloc(max_batch_blocks << m)) || (rc = w.refs.alloc(max_batch_blocks)) ||
             (rc = w.tgt.alloc(max_batch_blocks)) || (rc = w.res.alloc(max_batch_blocks)) ||
             (rc = w.sizes.alloc(max_batch_blocks)) || (rc = w.lb_state.alloc(max_batch_blocks * nframes)) ||
+            (rc = w.part.alloc(max_batch_blocks * nframes)) ||
             (rc = w.lb_ctr.alloc(4))) {
             cleanup();
             for (auto &x : sw) { if (x.s) cudaStreamDestroy(x.s); if (x.done) cudaEventDestroy(x.done); }
@@ -713,6 +729,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
         }
         CUDA_TRY(cudaMemsetAsync(w.lb_state.p, 0, max_batch_blocks * nframes * sizeof(uint64_t), main));
         CUDA_TRY(cudaMemsetAsync(w.lb_ctr.p, 0, 4 * sizeof(uint32_t), main));
+        CUDA_TRY(cudaMemsetAsync(w.sizes.p, 0, max_batch_blocks * sizeof(uint64_t), main));
     }
     auto destroy_streams = [&]() {
         for (auto &x : sw) {
@@ -750,10 +767,8 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
                            status, w.s);
             launch_copy_out(w.wv.p, 2, m, w.tgt.p, init_ids.p, tmpl.p, nullptr, status, w.s);
         } else {
-            CUDA_TRY(cudaMemsetAsync(w.sizes.p, 0, 2 * sizeof(uint64_t), w.s));
-            launch_encode_size(w.wv.p, 2, m, e, w.sizes.p, status, w.s);
-            launch_reserve(2, w.sizes.p, qsz_data_start(m), nullptr, 0, worst, arena_dev(0), arena_host(0), w.tgt.p,
-                           w.res.p, 0, status, w.s);
+            launch_size_reserve(w.wv.p, 2, m, e, w.sizes.p, w.lb_ctr.p + 3, arena_dev(0), arena_host(0), w.tgt.p,
+                                w.res.p, status, w.s);
             LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p);
             launch_encode(w.wv.p, 2, m, e, w.tgt.p, w.res.p, 0, init_ids.p, tmpl.p, nullptr, scr, status, w.s);
         }
@@ -791,15 +806,21 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             const uint32_t ng = uint32_t(std::min<uint64_t>(gpb, sd.ngroups - g0));
             const uint32_t nb = ng * sd.G;
             const uint32_t *ids = ids_stage + g0 * sd.G;
-            prof.begin(P_GATHER, w.s);
-            launch_gather_refs(tab_in, ids, nb, w.refs.p, w.s);
-            prof.end(w.s);
             if (raw) {
+                prof.begin(P_GATHER, w.s);
+                launch_gather_refs(tab_in, ids, nb, w.refs.p, w.s);
+                prof.end(w.s);
                 prof.begin(P_COPY_IN, w.s);
                 launch_copy_in(w.refs.p, nb, m, w.wv.p, status, w.s);
             } else {
                 prof.begin(P_DECODE, w.s);
-                launch_decode(w.refs.p, nb, m, w.wv.p, nullptr, status, w.s);
+                PreOps pre;
+                pre.ops = pd->ops.p + sd.pre_begin;
+                pre.count = sd.npre;
+                pre.G = sd.G;
+                pre.mats = pd->mats.p;
+                pre.gbase = gb_stage + g0;
+                launch_decode_table(tab_in, ids, nb, m, w.wv.p, nullptr, status, pre, w.s);
             }
             prof.end(w.s);
             for (uint32_t pi = 0; pi < sd.npasses; ++pi) {
@@ -817,15 +838,11 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
                 launch_copy_out(w.wv.p, nb, m, w.tgt.p, ids, tab_out, acc, status, w.s);
                 prof.end(w.s);
             } else {
-                CUDA_TRY(cudaMemsetAsync(w.sizes.p, 0, nb * sizeof(uint64_t), w.s));
                 prof.begin(P_ENCODE_SIZE, w.s);
-                launch_encode_size(w.wv.p, nb, m, e, w.sizes.p, status, w.s);
+                launch_size_reserve(w.wv.p, nb, m, e, w.sizes.p, w.lb_ctr.p + 3, arena_dev(out_par),
+                                    arena_host(out_par), w.tgt.p, w.res.p, status, w.s);
                 prof.end(w.s);
-                prof.begin(P_RESERVE, w.s);
-                launch_reserve(nb, w.sizes.p, qsz_data_start(m), nullptr, 0, worst, arena_dev(out_par),
-                               arena_host(out_par), w.tgt.p, w.res.p, 0, status, w.s);
-                prof.end(w.s);
-                LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p);
+                LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p, w.part.p);
                 prof.begin(P_ENCODE, w.s);
                 launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
                 prof.end(w.s);
@@ -1056,6 +1073,7 @@ int qsim_plan_stage_ops(const qsim_plan *plan, size_t stage, size_t *count, qsim
             for (uint32_t j = 0; j < op.k; ++j) o.qubits[j] = op.fq[j];
         }
         o.u = op.u.empty() ? nullptr : reinterpret_cast<const double *>(op.u.data());
+        o.pass = 0xFFFFFFFFu;  // applied by the decoder
         for (size_t pi = 0; pi < st.passes.size(); ++pi)
             for (uint32_t oi : st.passes[pi].ops)
                 if (oi == i) o.pass = uint32_t(pi);

@@ -18,6 +18,8 @@ struct PassDev {
     uint32_t nout;           // W - T
     uint32_t op_begin, op_count;
     uint32_t mat_elems;      // largest matrix / phase table of the pass, in float2
+    uint32_t kmax;           // widest dense op of the pass (0 if none)
+    uint32_t pad0;
     uint64_t out_mask;       // working-index mask of the non-tile bits
     uint32_t tile_pos[16];   // working bit of tile bit t (ascending)
     uint32_t out_pos[32];    // working bit of CTA-index bit t

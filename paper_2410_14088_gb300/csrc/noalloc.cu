@@ -108,7 +108,7 @@ extern "C" int qsim_compress_block_noalloc(const float *d_amps, uint32_t m, doub
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(tgt, &t, sizeof(t), cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return set_error(QSIM_E_CUDA, "scratch set-up: %s", cudaGetErrorString(ce));
 
-    LookbackScratch scr;
+    LookbackScratch scr{};
     scr.state = lookback;
     scr.ticket = counters;
     scr.done = counters + 1;

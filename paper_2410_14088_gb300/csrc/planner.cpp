@@ -224,8 +224,15 @@ struct Fuser {
     }
 };
 
-void layout_passes(Stage &st, uint32_t tile_bits) {
+void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
     const uint32_t W = st.W;
+    st.pre_ops.clear();
+    uint32_t first = 0;
+    if (fold_leading_diag) {
+        // leading phase ops need no tile: the decoder applies them per element
+        while (first < st.ops.size() && st.ops[first].type != OP_DENSE && st.pre_ops.size() < kMaxPreOps)
+            st.pre_ops.push_back(first++);
+    }
     uint32_t T = std::min(tile_bits, W);
     const uint32_t L = std::min<uint32_t>(5, T);
     st.passes.clear();
@@ -243,7 +250,7 @@ void layout_passes(Stage &st, uint32_t tile_bits) {
     std::set<uint32_t> P;
     for (uint32_t b = 0; b < L; ++b) P.insert(b);
     std::vector<uint32_t> cur;
-    for (uint32_t i = 0; i < st.ops.size(); ++i) {
+    for (uint32_t i = first; i < st.ops.size(); ++i) {
         const Op &op = st.ops[i];
         if (op.type == OP_DENSE) {
             std::set<uint32_t> need(P);
@@ -352,7 +359,8 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
         fz.ops = &st.ops;
         for (size_t i = st.first_gate; i < st.first_gate + st.ngates; ++i) fz.add(p->gates[i]);
         fz.flush();
-        layout_passes(st, std::max<uint32_t>(tile_bits, std::min<uint32_t>(st.W, 5 + cfg->k)));
+        layout_passes(st, std::max<uint32_t>(tile_bits, std::min<uint32_t>(st.W, 5 + cfg->k)),
+                      cfg->codec == QSIM_CODEC_QSZ1);
     }
 
     qsim_plan_stats &s = p->stats;

@@ -68,8 +68,11 @@ struct Stage {
     std::vector<uint32_t> inner;  // ascending global qubits that are local in this stage
     uint32_t W = 0;               // working vector = 2^W amplitudes (m + |inner|)
     std::vector<Op> ops;
+    std::vector<uint32_t> pre_ops;  // leading diagonal ops applied while decoding (no pass needed)
     std::vector<Pass> passes;
 };
+
+constexpr uint32_t kMaxPreOps = 8;
 
 struct Gate {
     uint32_t nq = 0;
