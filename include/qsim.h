@@ -87,7 +87,7 @@ typedef struct qsim_config {
     uint32_t codec;       /* QSIM_CODEC_* */
     uint32_t graph;       /* 1: capture each run's stage loop in a CUDA graph (persistent mode) */
     uint32_t tile_bits;   /* log2 amplitudes per shared-memory tile, 0 = default */
-    uint32_t reserved0;
+    uint32_t collect;     /* 1: log (features, compressed size) of every encoded block (predictor training) */
     double eps;           /* eb = eps * 2^(-n/2) */
     uint64_t device_tier_cap_bytes; /* bytes of compressed blocks kept on the device; 0 = no cap */
     uint64_t init_basis;  /* initial basis state |init_basis> (Sec. 4.2 initialisation) */
@@ -258,6 +258,53 @@ int qsim_compress_block_noalloc(const float *d_amps, uint32_t m, double eb, void
  */
 int qsim_decompress_block(const void *d_in, size_t in_bytes, float *d_amps, uint32_t m,
                           void *cuda_stream);
+
+/* ---- learned block-size predictor ----------------------------------------- */
+/*
+ * A 41 -> 64 -> 64 -> 1 ReLU MLP predicts log2 of each block's next stream
+ * size from cheap statistics: the 32-bin histogram of code bit lengths as
+ * decoded (fractions), the largest bit length / 32, and 8 stage
+ * features. The histogram is taken over the block's SV group (the blocks a
+ * stage mixes). The output is log2(bytes) - (m + 3). Parameters (6913 floats):
+ * W1[64][41], b1[64], W2[64][64], b2[64], W3[64], b3. This replaces the
+ * paper's reactive fall-back to a second memory level (Sec. 4.4) by a
+ * reservation made before encoding; an under-estimate re-encodes the block
+ * into an exactly sized slot.
+ */
+#define QSIM_MLP_INPUTS 41
+#define QSIM_MLP_PARAMS 6913
+#define QSIM_TRAIN_ROW 42 /* logged row: 41 features then the target */
+
+/* GPU forward pass: y[b] = MLP(x[b]); device pointers; bf16_weights rounds the
+ * weights to BF16 (inference precision). */
+int qsim_mlp_forward(const float *d_params, const float *d_x, size_t batch, float *d_y, int bf16_weights,
+                     void *cuda_stream);
+/* GPU loss 0.5/B sum (y - t)^2 and its gradient (device pointers; *loss is host). */
+int qsim_mlp_loss_grad(const float *d_params, const float *d_x, const float *d_t, size_t batch, float *d_grad,
+                       float *loss, void *cuda_stream);
+/* GPU Adam step (t is 1-based) on n parameters. */
+int qsim_adam_step(float *d_params, const float *d_grad, float *d_m, float *d_v, size_t n, int t, float lr,
+                   float beta1, float beta2, float eps, void *cuda_stream);
+
+typedef struct qsim_train_config {
+    uint32_t epochs;        /* passes over the data */
+    uint32_t batch;         /* samples per Adam step */
+    float lr;               /* Adam learning rate */
+    uint32_t bf16_inference;/* 1: predict with BF16-rounded weights */
+    uint64_t seed;          /* initialisation and shuffling */
+} qsim_train_config;
+
+/* Train the library's predictor on the current device from logged rows (host,
+ * count x QSIM_TRAIN_ROW floats) with the GPU kernels above; *final_loss
+ * (nullable) receives the loss over all rows. Replaces any previous weights. */
+int qsim_predictor_train(const float *rows, size_t count, const qsim_train_config *tc, double *final_loss);
+/* Install / read the predictor's weights (host arrays of QSIM_MLP_PARAMS floats). */
+int qsim_predictor_set(const float *params, size_t n, int bf16_inference);
+int qsim_predictor_get(float *params, size_t n);
+
+/* Rows logged by a run with cfg.collect = 1 (host, cap_rows x QSIM_TRAIN_ROW);
+ * *rows receives the number available. */
+int qsim_state_training_data(const qsim_state *st, float *rows_out, size_t cap_rows, size_t *rows);
 
 /* ---- per-kernel timing ---------------------------------------------------- */
 

@@ -31,6 +31,7 @@
 #include "codec.cuh"
 #include "device_common.cuh"
 #include "gates.cuh"
+#include "mlp.cuh"
 #include "qsim_internal.h"
 
 namespace qsim {
@@ -56,9 +57,9 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 // ---------------------------------------------------------------------------
 static std::atomic<int> g_profile{0};
 enum ProfCat { P_DECODE = 0, P_PASS, P_ENCODE_SIZE, P_RESERVE, P_ENCODE, P_GATHER, P_COPY_IN, P_COPY_OUT, P_INIT,
-               P_NCAT };
+               P_PREDICT, P_REENCODE, P_NCAT };
 static const char *kProfNames[P_NCAT] = {"decode", "gate_pass", "encode_size", "reserve", "encode",
-                                         "gather_refs", "copy_in", "copy_out", "init"};
+                                         "gather_refs", "copy_in", "copy_out", "init", "predict", "reencode"};
 
 struct Profiler {
     bool on = false;
@@ -229,6 +230,10 @@ struct DeviceCtx {
     EncResult *res = nullptr;
     BlockRef *ref = nullptr;
     bool ready = false;
+    // learned size predictor of this device
+    float *pred_params = nullptr;
+    bool pred_ready = false;
+    int pred_bf16 = 0;
 };
 
 static DeviceCtx &device_ctx(int dev) {
@@ -245,6 +250,7 @@ static int ensure_device_ctx(DeviceCtx &c) {
     CUDA_TRY(cudaMalloc(&c.tgt, sizeof(EncTarget)));
     CUDA_TRY(cudaMalloc(&c.res, sizeof(EncResult)));
     CUDA_TRY(cudaMalloc(&c.ref, sizeof(BlockRef)));
+    CUDA_TRY(cudaMalloc(&c.pred_params, kMlpParams * sizeof(float)));
     CUDA_TRY(cudaMemset(c.status, 0, 256));
     CUDA_TRY(cudaMemset(c.lb_state, 0, max_frames * sizeof(uint64_t)));
     CUDA_TRY(cudaMemset(c.lb_ctr, 0, 256));
@@ -501,6 +507,7 @@ struct qsim_state {
     qsim::BlockSlot *table = nullptr;  // device, 2^(n-m) entries
     std::vector<qsim::StageAccum> stage_acc;
     std::vector<qsim_kernel_stat> kstats;
+    std::vector<float> train_rows;  // collect mode: rows of 41 features + target
 };
 
 namespace qsim {
@@ -621,14 +628,14 @@ struct StreamWork {
     DevBuf<uint64_t> lb_state;
     DevBuf<uint32_t> lb_ctr;
     DevBuf<float2> part;
+    DevBuf<uint32_t> hist;   // per block: 32-bin histogram of code bit lengths (decoder)
+    DevBuf<float> pred;      // per block: predicted log2 stream bytes
 };
 
 static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsim_stats *stats) {
     const qsim_config &cfg = p->cfg;
     if (cfg.mode != QSIM_MODE_STREAMS)
         return set_error(QSIM_E_UNSUPPORTED, "persistent mode is not available in this build");
-    if (cfg.sizing != QSIM_SIZING_EXACT)
-        return set_error(QSIM_E_UNSUPPORTED, "predictor sizing is not available in this build");
     int dev;
     CUDA_TRY(cudaGetDevice(&dev));
     DeviceCtx &dctx = device_ctx(dev);
@@ -647,6 +654,10 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
     int e = 0;
     if (!raw && !qsz_step_exponent(cfg.eps * std::pow(2.0, -double(n) / 2.0), &e))
         return set_error(QSIM_E_INVALID, "error bound out of range");
+    const bool predict = cfg.sizing == QSIM_SIZING_PREDICT && !raw;
+    const bool collect = cfg.collect != 0 && !raw;
+    if (predict && !dctx.pred_ready)
+        return set_error(QSIM_E_INVALID, "predictor sizing needs trained weights (qsim_predictor_train/set)");
     const uint64_t worst = raw ? (8ull << m) : qsz_worst_case(m);
     const uint64_t slot_worst = (worst + 255) & ~255ull;
     const uint64_t nframes = raw ? 1 : qsz_nframes(m);
@@ -686,7 +697,13 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
     DevBuf<BlockSlot> tables;
     DevBuf<StageAccum> accs;
     const size_t nst = p->stages.size();
-    if ((rc = bumps.alloc(4)) || (rc = tables.alloc(2 * nblocks)) || (rc = accs.alloc(nst + 1))) { cleanup(); return rc; }
+    DevBuf<float> log_rows;
+    if ((rc = bumps.alloc(4)) || (rc = tables.alloc(2 * nblocks)) || (rc = accs.alloc(nst + 1)) ||
+        (collect && (rc = log_rows.alloc(nst * nblocks * (kMlpIn + 1))))) {
+        cleanup();
+        return rc;
+    }
+    uint64_t log_next = 0;  // next logged row
     CUDA_TRY(cudaMemsetAsync(bumps.p, 0, 4 * sizeof(uint64_t), main));
     CUDA_TRY(cudaMemsetAsync(accs.p, 0, (nst + 1) * sizeof(StageAccum), main));
     CUDA_TRY(cudaMemsetAsync(tables.p, 0, 2 * nblocks * sizeof(BlockSlot), main));
@@ -721,7 +738,8 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
         if ((rc = w.wv.alloc(max_batch_blocks << m)) || (rc = w.refs.alloc(max_batch_blocks)) ||
             (rc = w.tgt.alloc(max_batch_blocks)) || (rc = w.res.alloc(max_batch_blocks)) ||
             (rc = w.sizes.alloc(max_batch_blocks)) || (rc = w.lb_state.alloc(max_batch_blocks * nframes)) ||
-            (rc = w.part.alloc(max_batch_blocks * nframes)) ||
+            (rc = w.part.alloc(max_batch_blocks * nframes)) || (rc = w.hist.alloc(max_batch_blocks * 32)) ||
+            (rc = w.pred.alloc(max_batch_blocks)) ||
             (rc = w.lb_ctr.alloc(4))) {
             cleanup();
             for (auto &x : sw) { if (x.s) cudaStreamDestroy(x.s); if (x.done) cudaEventDestroy(x.done); }
@@ -800,6 +818,24 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
         const uint32_t *ids_stage = pd->ids.p + pd->ids_off[si];
         const uint64_t *gb_stage = pd->gbase.p + pd->gbase_off[si];
         StageAccum *acc = accs.p + si;
+        StageFeatures sf{};
+        {
+            const Stage &st = p->stages[si];
+            uint32_t dense = 0, diag = 0, kmax = 0, nondiag = 0;
+            for (const Op &op : st.ops) {
+                if (op.type == OP_DENSE) { ++dense; kmax = std::max(kmax, op.k); }
+                else ++diag;
+            }
+            for (size_t gi = st.first_gate; gi < st.first_gate + st.ngates; ++gi) nondiag += p->gates[gi].diag ? 0 : 1;
+            sf.v[0] = float(m) / 32.f;
+            sf.v[1] = float(st.inner.size()) / 8.f;
+            sf.v[2] = float(dense) / 16.f;
+            sf.v[3] = float(diag) / 16.f;
+            sf.v[4] = float(kmax) / 6.f;
+            sf.v[5] = float(-e) / 64.f;
+            sf.v[6] = float(st.ngates) / 64.f;
+            sf.v[7] = st.ngates ? float(nondiag) / float(st.ngates) : 0.f;
+        }
         for (uint64_t b = 0; b < nbatches; ++b) {
             StreamWork &w = sw[b % nstreams];
             const uint64_t g0 = b * gpb;
@@ -820,9 +856,18 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
                 pre.G = sd.G;
                 pre.mats = pd->mats.p;
                 pre.gbase = gb_stage + g0;
-                launch_decode_table(tab_in, ids, nb, m, w.wv.p, nullptr, status, pre, w.s);
+                uint32_t *hist = (predict || collect) ? w.hist.p : nullptr;
+                if (hist) CUDA_TRY(cudaMemsetAsync(hist, 0, size_t(nb) * 32 * sizeof(uint32_t), w.s));
+                launch_decode_table(tab_in, ids, nb, m, w.wv.p, hist, status, pre, w.s);
             }
             prof.end(w.s);
+            float *log_ptr = collect ? log_rows.p + log_next * (kMlpIn + 1) : nullptr;
+            if (predict || collect) {
+                prof.begin(P_PREDICT, w.s);
+                launch_predict_sizes(w.hist.p, nb, sd.G, m, sf, predict ? dctx.pred_params : nullptr,
+                                     dctx.pred_bf16, w.pred.p, log_ptr, w.s);
+                prof.end(w.s);
+            }
             for (uint32_t pi = 0; pi < sd.npasses; ++pi) {
                 prof.begin(P_PASS, w.s);
                 launch_pass(w.wv.p, sd.W, ng, &sd.passes_host[pi], pd->passes.p + sd.pass_begin + pi, pd->ops.p,
@@ -838,14 +883,36 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
                 launch_copy_out(w.wv.p, nb, m, w.tgt.p, ids, tab_out, acc, status, w.s);
                 prof.end(w.s);
             } else {
-                prof.begin(P_ENCODE_SIZE, w.s);
-                launch_size_reserve(w.wv.p, nb, m, e, w.sizes.p, w.lb_ctr.p + 3, arena_dev(out_par),
-                                    arena_host(out_par), w.tgt.p, w.res.p, status, w.s);
-                prof.end(w.s);
                 LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p, w.part.p);
-                prof.begin(P_ENCODE, w.s);
-                launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
-                prof.end(w.s);
+                if (predict) {
+                    // reserve 2^pred (1 + margin) bytes, encode once, re-encode under-estimated blocks exactly
+                    prof.begin(P_RESERVE, w.s);
+                    launch_reserve(nb, nullptr, 0, w.pred.p, cfg.predictor_margin, worst, arena_dev(out_par),
+                                   arena_host(out_par), w.tgt.p, w.res.p, 0, status, w.s);
+                    prof.end(w.s);
+                    prof.begin(P_ENCODE, w.s);
+                    launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
+                    prof.end(w.s);
+                    prof.begin(P_RESERVE, w.s);
+                    launch_reserve(nb, nullptr, 0, nullptr, 0, worst, arena_dev(out_par), arena_host(out_par),
+                                   w.tgt.p, w.res.p, 1, status, w.s);
+                    prof.end(w.s);
+                    prof.begin(P_REENCODE, w.s);
+                    launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 1, ids, tab_out, acc, scr, status, w.s);
+                    prof.end(w.s);
+                } else {
+                    prof.begin(P_ENCODE_SIZE, w.s);
+                    launch_size_reserve(w.wv.p, nb, m, e, w.sizes.p, w.lb_ctr.p + 3, arena_dev(out_par),
+                                        arena_host(out_par), w.tgt.p, w.res.p, status, w.s);
+                    prof.end(w.s);
+                    prof.begin(P_ENCODE, w.s);
+                    launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
+                    prof.end(w.s);
+                }
+                if (collect) {
+                    launch_log_targets(w.res.p, nb, m, log_ptr, w.s);
+                    log_next += nb;
+                }
             }
         }
         for (auto &w : sw) {
@@ -875,6 +942,11 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
     S->e = e;
     S->stage_acc.resize(nst + 1);
     CUDA_TRY(cudaMemcpy(S->stage_acc.data(), accs.p, (nst + 1) * sizeof(StageAccum), cudaMemcpyDeviceToHost));
+    if (collect && log_next) {
+        S->train_rows.resize(log_next * (kMlpIn + 1));
+        CUDA_TRY(cudaMemcpy(S->train_rows.data(), log_rows.p, S->train_rows.size() * sizeof(float),
+                            cudaMemcpyDeviceToHost));
+    }
     const int fin = nst & 1;
     S->dev_arena = dev_arena[fin];
     S->host_arena = host_arena[fin];
@@ -1107,6 +1179,147 @@ int qsim_state_stage_stats(const qsim_state *st, size_t stage, uint64_t *store_b
     if (store_bytes) *store_bytes = a.store_bytes;
     if (reserved_bytes) *reserved_bytes = a.reserved_bytes;
     if (err_sq) *err_sq = a.err_sq;
+    return QSIM_OK;
+}
+
+int qsim_mlp_forward(const float *d_params, const float *d_x, size_t batch, float *d_y, int bf16_weights,
+                     void *cuda_stream) {
+    if (!d_params || (batch && (!d_x || !d_y))) return set_error(QSIM_E_INVALID, "null argument");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    launch_mlp_forward(d_params, d_x, uint32_t(batch), d_y, bf16_weights, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return QSIM_OK;
+}
+
+int qsim_mlp_loss_grad(const float *d_params, const float *d_x, const float *d_t, size_t batch, float *d_grad,
+                       float *loss, void *cuda_stream) {
+    if (!d_params || !d_x || !d_t || !d_grad || !batch) return set_error(QSIM_E_INVALID, "bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    DevBuf<float> dl;
+    int rc = dl.alloc(1);
+    if (rc) return rc;
+    rc = launch_mlp_loss_grad(d_params, d_x, kMlpIn, d_t, 1, nullptr, 0, uint32_t(batch), d_grad, dl.p, s);
+    if (rc) return set_error(rc, "loss/grad launch failed");
+    float h = 0;
+    CUDA_TRY(cudaMemcpyAsync(&h, dl.p, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    if (loss) *loss = h;
+    return QSIM_OK;
+}
+
+int qsim_adam_step(float *d_params, const float *d_grad, float *d_m, float *d_v, size_t n, int t, float lr,
+                   float beta1, float beta2, float eps, void *cuda_stream) {
+    if (!d_params || !d_grad || !d_m || !d_v || t < 1) return set_error(QSIM_E_INVALID, "bad argument");
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    launch_adam(d_params, d_grad, d_m, d_v, uint32_t(n), t, lr, beta1, beta2, eps, s);
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return QSIM_OK;
+}
+
+static int predictor_ctx(DeviceCtx **out) {
+    int dev;
+    CUDA_TRY(cudaGetDevice(&dev));
+    DeviceCtx &c = device_ctx(dev);
+    int rc = ensure_device_ctx(c);
+    if (rc) return rc;
+    *out = &c;
+    return QSIM_OK;
+}
+
+int qsim_predictor_set(const float *params, size_t n, int bf16_inference) {
+    if (!params || n != size_t(kMlpParams)) return set_error(QSIM_E_INVALID, "need %d parameters", kMlpParams);
+    DeviceCtx *c;
+    int rc = predictor_ctx(&c);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpy(c->pred_params, params, n * sizeof(float), cudaMemcpyHostToDevice));
+    c->pred_bf16 = bf16_inference;
+    c->pred_ready = true;
+    return QSIM_OK;
+}
+
+int qsim_predictor_get(float *params, size_t n) {
+    if (!params || n != size_t(kMlpParams)) return set_error(QSIM_E_INVALID, "need %d parameters", kMlpParams);
+    DeviceCtx *c;
+    int rc = predictor_ctx(&c);
+    if (rc) return rc;
+    if (!c->pred_ready) return set_error(QSIM_E_INVALID, "predictor has no weights");
+    CUDA_TRY(cudaMemcpy(params, c->pred_params, n * sizeof(float), cudaMemcpyDeviceToHost));
+    return QSIM_OK;
+}
+
+static uint64_t splitmix_next(uint64_t &s) {
+    s += 0x9E3779B97F4A7C15ull;
+    uint64_t z = s;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+int qsim_predictor_train(const float *rows, size_t count, const qsim_train_config *tc, double *final_loss) {
+    if (!rows || !count || !tc || !tc->epochs || !tc->batch) return set_error(QSIM_E_INVALID, "bad argument");
+    DeviceCtx *c;
+    int rc = predictor_ctx(&c);
+    if (rc) return rc;
+    const size_t rowf = kMlpIn + 1;
+    DevBuf<float> d_rows, p, g, m1, m2, loss;
+    DevBuf<uint32_t> perm;
+    if ((rc = d_rows.alloc(count * rowf)) || (rc = p.alloc(kMlpParams)) || (rc = g.alloc(kMlpParams)) ||
+        (rc = m1.alloc(kMlpParams)) || (rc = m2.alloc(kMlpParams)) || (rc = loss.alloc(1)) || (rc = perm.alloc(count)))
+        return rc;
+    cudaStream_t s = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    CUDA_TRY(cudaMemcpyAsync(d_rows.p, rows, count * rowf * sizeof(float), cudaMemcpyHostToDevice, s));
+    // He-uniform initialisation from splitmix64; zero biases
+    uint64_t st = tc->seed;
+    std::vector<float> hp(kMlpParams, 0.f);
+    auto fill = [&](size_t off, int fan_out, int fan_in) {
+        const double lim = std::sqrt(6.0 / fan_in);
+        for (int i = 0; i < fan_out * fan_in; ++i) {
+            const double u = double(splitmix_next(st) >> 11) * (1.0 / 9007199254740992.0);
+            hp[off + i] = float((2 * u - 1) * lim);
+        }
+    };
+    fill(0, kMlpHidden, kMlpIn);
+    fill(kMlpHidden * kMlpIn + kMlpHidden, kMlpHidden, kMlpHidden);
+    fill(kMlpHidden * kMlpIn + kMlpHidden + kMlpHidden * kMlpHidden + kMlpHidden, 1, kMlpHidden);
+    CUDA_TRY(cudaMemcpyAsync(p.p, hp.data(), kMlpParams * sizeof(float), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemsetAsync(m1.p, 0, kMlpParams * sizeof(float), s));
+    CUDA_TRY(cudaMemsetAsync(m2.p, 0, kMlpParams * sizeof(float), s));
+    std::vector<uint32_t> hperm(count);
+    int t = 0;
+    for (uint32_t ep = 0; ep < tc->epochs; ++ep) {
+        for (size_t i = 0; i < count; ++i) hperm[i] = uint32_t(i);
+        for (size_t i = count - 1; i > 0; --i) std::swap(hperm[i], hperm[splitmix_next(st) % (i + 1)]);
+        CUDA_TRY(cudaStreamSynchronize(s));  // hperm is reused: the previous upload must have landed
+        CUDA_TRY(cudaMemcpyAsync(perm.p, hperm.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        for (size_t b0 = 0; b0 < count; b0 += tc->batch) {
+            const uint32_t nb = uint32_t(std::min<size_t>(tc->batch, count - b0));
+            rc = launch_mlp_loss_grad(p.p, d_rows.p, rowf, d_rows.p + kMlpIn, rowf, perm.p, uint32_t(b0), nb, g.p,
+                                      nullptr, s);
+            if (rc) { cudaStreamDestroy(s); return set_error(rc, "loss/grad launch failed"); }
+            launch_adam(p.p, g.p, m1.p, m2.p, kMlpParams, ++t, tc->lr, 0.9f, 0.999f, 1e-8f, s);
+        }
+    }
+    rc = launch_mlp_loss_grad(p.p, d_rows.p, rowf, d_rows.p + kMlpIn, rowf, nullptr, 0, uint32_t(count), g.p, loss.p, s);
+    float hl = 0;
+    CUDA_TRY(cudaMemcpyAsync(&hl, loss.p, sizeof(float), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaMemcpyAsync(c->pred_params, p.p, kMlpParams * sizeof(float), cudaMemcpyDeviceToDevice, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    cudaStreamDestroy(s);
+    c->pred_bf16 = int(tc->bf16_inference);
+    c->pred_ready = true;
+    if (final_loss) *final_loss = hl;
+    return QSIM_OK;
+}
+
+int qsim_state_training_data(const qsim_state *st, float *rows_out, size_t cap_rows, size_t *rows) {
+    if (!st || !rows) return set_error(QSIM_E_INVALID, "null argument");
+    const size_t rowf = kMlpIn + 1;
+    const size_t have = st->train_rows.size() / rowf;
+    *rows = have;
+    if (!rows_out) return QSIM_OK;
+    if (cap_rows < have) return set_error(QSIM_E_CAPACITY, "capacity %zu < %zu rows", cap_rows, have);
+    memcpy(rows_out, st->train_rows.data(), have * rowf * sizeof(float));
     return QSIM_OK;
 }
 

@@ -45,7 +45,7 @@ class Config(ctypes.Structure):
     _fields_ = [("m", ctypes.c_uint32), ("inner", ctypes.c_uint32), ("k", ctypes.c_uint32),
                 ("prec", ctypes.c_uint32), ("mode", ctypes.c_uint32), ("streams", ctypes.c_uint32),
                 ("sizing", ctypes.c_uint32), ("diag_exempt", ctypes.c_uint32), ("codec", ctypes.c_uint32),
-                ("graph", ctypes.c_uint32), ("tile_bits", ctypes.c_uint32), ("reserved0", ctypes.c_uint32),
+                ("graph", ctypes.c_uint32), ("tile_bits", ctypes.c_uint32), ("collect", ctypes.c_uint32),
                 ("eps", ctypes.c_double), ("device_tier_cap_bytes", ctypes.c_uint64),
                 ("init_basis", ctypes.c_uint64), ("predictor_margin", ctypes.c_double),
                 ("reserved", ctypes.c_uint64 * 6)]
@@ -81,6 +81,13 @@ class KernelStat(ctypes.Structure):
                 ("alg_bytes", ctypes.c_double), ("alg_flops", ctypes.c_double)]
 
 
+class TrainConfig(ctypes.Structure):
+    _fields_ = [("epochs", ctypes.c_uint32), ("batch", ctypes.c_uint32), ("lr", ctypes.c_float),
+                ("bf16_inference", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+MLP_INPUTS, MLP_PARAMS, TRAIN_ROW = 41, 6913, 42
+
 # every symbol include/qsim.h declares, with its ctypes signature
 _VP = ctypes.c_void_p
 _SZ = ctypes.c_size_t
@@ -106,6 +113,14 @@ SIGNATURES = {
     "qsim_compress_block": (ctypes.c_int, [_VP, _U32, ctypes.c_double, _VP, _SZ, ctypes.POINTER(_SZ), _VP]),
     "qsim_compress_block_noalloc": (ctypes.c_int, [_VP, _U32, ctypes.c_double, _VP, _SZ, ctypes.POINTER(_SZ), _VP]),
     "qsim_decompress_block": (ctypes.c_int, [_VP, _SZ, _VP, _U32, _VP]),
+    "qsim_mlp_forward": (ctypes.c_int, [_VP, _VP, _SZ, _VP, ctypes.c_int, _VP]),
+    "qsim_mlp_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, ctypes.POINTER(ctypes.c_float), _VP]),
+    "qsim_adam_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _SZ, ctypes.c_int, ctypes.c_float, ctypes.c_float,
+                                      ctypes.c_float, ctypes.c_float, _VP]),
+    "qsim_predictor_train": (ctypes.c_int, [_VP, _SZ, ctypes.POINTER(TrainConfig), ctypes.POINTER(ctypes.c_double)]),
+    "qsim_predictor_set": (ctypes.c_int, [_VP, _SZ, ctypes.c_int]),
+    "qsim_predictor_get": (ctypes.c_int, [_VP, _SZ]),
+    "qsim_state_training_data": (ctypes.c_int, [_VP, _VP, _SZ, ctypes.POINTER(_SZ)]),
     "qsim_profile_enable": (None, [ctypes.c_int]),
     "qsim_state_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(KernelStat), _SZ, ctypes.POINTER(_SZ)]),
     "qsim_last_error": (ctypes.c_char_p, []),
@@ -323,6 +338,15 @@ class State:
                                              ctypes.byref(nb)), "qsim_state_block_stream")
         return buf[: nb.value].tobytes()
 
+    def training_data(self) -> np.ndarray:
+        """Rows (features[41], target) logged by a run with collect=1."""
+        n = ctypes.c_size_t()
+        _check(lib().qsim_state_training_data(self.handle, None, 0, ctypes.byref(n)), "qsim_state_training_data")
+        out = np.empty((max(1, n.value), TRAIN_ROW), dtype=np.float32)
+        _check(lib().qsim_state_training_data(self.handle, ctypes.c_void_p(out.ctypes.data), n.value,
+                                              ctypes.byref(n)), "qsim_state_training_data")
+        return out[: n.value]
+
     def kernel_stats(self):
         cnt = ctypes.c_size_t()
         _check(lib().qsim_state_kernel_stats(self.handle, None, 0, ctypes.byref(cnt)), "qsim_state_kernel_stats")
@@ -404,3 +428,53 @@ def decompress_block_rc(stream_bytes, m: int, nbytes: int, stream=None) -> int:
     out = torch.empty(1 << m, dtype=torch.complex64, device=stream_bytes.device)
     return lib().qsim_decompress_block(ctypes.c_void_p(stream_bytes.data_ptr()), nbytes, ctypes.c_void_p(out.data_ptr()),
                                        m, _stream_ptr(stream))
+
+
+# --------------------------------------------------------------------------
+# learned size predictor
+# --------------------------------------------------------------------------
+
+def mlp_forward(params, x, bf16=False, stream=None):
+    """params: CUDA float32 (6913); x: CUDA float32 (B, 41). Returns y (B)."""
+    import torch
+    y = torch.empty(x.shape[0], dtype=torch.float32, device=x.device)
+    _check(lib().qsim_mlp_forward(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(x.data_ptr()), x.shape[0],
+                                  ctypes.c_void_p(y.data_ptr()), 1 if bf16 else 0, _stream_ptr(stream)),
+           "qsim_mlp_forward")
+    return y
+
+
+def mlp_loss_grad(params, x, t, stream=None):
+    import torch
+    g = torch.empty_like(params)
+    loss = ctypes.c_float()
+    _check(lib().qsim_mlp_loss_grad(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(x.data_ptr()),
+                                    ctypes.c_void_p(t.data_ptr()), x.shape[0], ctypes.c_void_p(g.data_ptr()),
+                                    ctypes.byref(loss), _stream_ptr(stream)), "qsim_mlp_loss_grad")
+    return loss.value, g
+
+
+def adam_step(params, grad, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib().qsim_adam_step(ctypes.c_void_p(params.data_ptr()), ctypes.c_void_p(grad.data_ptr()),
+                                ctypes.c_void_p(m.data_ptr()), ctypes.c_void_p(v.data_ptr()), params.numel(), t, lr,
+                                beta1, beta2, eps, _stream_ptr(stream)), "qsim_adam_step")
+
+
+def predictor_train(rows: np.ndarray, epochs=60, batch=64, lr=3e-3, seed=100, bf16=False) -> float:
+    rows = np.ascontiguousarray(rows, dtype=np.float32).reshape(-1, TRAIN_ROW)
+    tc = TrainConfig(epochs, batch, lr, 1 if bf16 else 0, seed)
+    loss = ctypes.c_double()
+    _check(lib().qsim_predictor_train(ctypes.c_void_p(rows.ctypes.data), rows.shape[0], ctypes.byref(tc),
+                                      ctypes.byref(loss)), "qsim_predictor_train")
+    return loss.value
+
+
+def predictor_set(params: np.ndarray, bf16=False):
+    p = np.ascontiguousarray(params, dtype=np.float32)
+    _check(lib().qsim_predictor_set(ctypes.c_void_p(p.ctypes.data), p.size, 1 if bf16 else 0), "qsim_predictor_set")
+
+
+def predictor_get() -> np.ndarray:
+    p = np.empty(MLP_PARAMS, dtype=np.float32)
+    _check(lib().qsim_predictor_get(ctypes.c_void_p(p.ctypes.data), p.size), "qsim_predictor_get")
+    return p
