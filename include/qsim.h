@@ -306,6 +306,33 @@ int qsim_predictor_get(float *params, size_t n);
  * *rows receives the number available. */
 int qsim_state_training_data(const qsim_state *st, float *rows_out, size_t cap_rows, size_t *rows);
 
+/* ---- autotuner ---------------------------------------------------------------- */
+/*
+ * Picks the SV block size m, the fused width k, the inner size i and the
+ * stream count for a circuit by timing qsim_run on a prefix of it (the paper
+ * tunes inner size and block size by hand, Sec. 5.8). Coordinate search: m,
+ * then k, then i, then streams, each with the others fixed at the best so
+ * far. Results are cached in memory per (n, gate structure, search space,
+ * precision, codec); a second call with the same key returns the cached
+ * choice without running anything.
+ */
+typedef struct qsim_tune_space {
+    uint32_t m_min, m_max;         /* SV block sizes tried */
+    uint32_t k_min, k_max;         /* fused widths tried */
+    uint32_t inner_min, inner_max; /* inner sizes tried */
+    uint32_t streams_mask;         /* bit s set: try s streams (s = 1..16) */
+    uint32_t prefix_gates;         /* gates of the circuit prefix timed (0 = all) */
+    uint32_t reps;                 /* timed runs per candidate (the best is kept) */
+    uint32_t reserved;
+} qsim_tune_space;
+
+/* *best receives base with m, k, inner and streams replaced by the fastest
+ * candidate; *best_seconds (nullable) its prefix time; *candidates (nullable)
+ * the number of configurations timed (0 on a cache hit). */
+int qsim_autotune(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_config *base,
+                  const qsim_tune_space *space, qsim_config *best, double *best_seconds, uint32_t *candidates);
+void qsim_autotune_cache_clear(void);
+
 /* ---- per-kernel timing ---------------------------------------------------- */
 
 /* When enabled, qsim_run brackets every kernel launch with CUDA events on the

@@ -86,6 +86,13 @@ class TrainConfig(ctypes.Structure):
                 ("bf16_inference", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
 
 
+class TuneSpace(ctypes.Structure):
+    _fields_ = [("m_min", ctypes.c_uint32), ("m_max", ctypes.c_uint32), ("k_min", ctypes.c_uint32),
+                ("k_max", ctypes.c_uint32), ("inner_min", ctypes.c_uint32), ("inner_max", ctypes.c_uint32),
+                ("streams_mask", ctypes.c_uint32), ("prefix_gates", ctypes.c_uint32), ("reps", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
 MLP_INPUTS, MLP_PARAMS, TRAIN_ROW = 41, 6913, 42
 
 # every symbol include/qsim.h declares, with its ctypes signature
@@ -121,6 +128,9 @@ SIGNATURES = {
     "qsim_predictor_set": (ctypes.c_int, [_VP, _SZ, ctypes.c_int]),
     "qsim_predictor_get": (ctypes.c_int, [_VP, _SZ]),
     "qsim_state_training_data": (ctypes.c_int, [_VP, _VP, _SZ, ctypes.POINTER(_SZ)]),
+    "qsim_autotune": (ctypes.c_int, [_U32, ctypes.POINTER(Gate), _SZ, ctypes.POINTER(Config), ctypes.POINTER(TuneSpace),
+                                     ctypes.POINTER(Config), ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_U32)]),
+    "qsim_autotune_cache_clear": (None, []),
     "qsim_profile_enable": (None, [ctypes.c_int]),
     "qsim_state_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(KernelStat), _SZ, ctypes.POINTER(_SZ)]),
     "qsim_last_error": (ctypes.c_char_p, []),
@@ -188,29 +198,35 @@ def default_config(**kw) -> Config:
 # planning
 # --------------------------------------------------------------------------
 
+def marshal_gates(gates):
+    """qsim_gate array for a list of inputs.Gate (matrices kept alive in the second return value)."""
+    arr = (Gate * max(1, len(gates)))()
+    mats = []
+    for i, g in enumerate(gates):
+        ga = arr[i]
+        if getattr(g, "phaseflip", False):
+            ga.nq = 0
+            ga.flags = GATE_PHASEFLIP
+            ga.basis = int(g.basis)
+            ga.u = ctypes.POINTER(ctypes.c_double)()
+        else:
+            ga.nq = len(g.qubits)
+            ga.flags = 0
+            for j, q in enumerate(g.qubits):
+                ga.q[j] = q
+            u = np.ascontiguousarray(g.matrix, dtype=np.complex128).view(np.float64).ravel()
+            mats.append(u)
+            ga.u = u.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    return arr, mats
+
+
 class Plan:
     """Owns a qsim_plan handle (plus the gate matrices it was built from)."""
 
     def __init__(self, n: int, gates: Sequence, cfg: Config):
         self.n = n
         self.cfg = cfg
-        arr = (Gate * max(1, len(gates)))()
-        self._mats = []
-        for i, g in enumerate(gates):
-            ga = arr[i]
-            if getattr(g, "phaseflip", False):
-                ga.nq = 0
-                ga.flags = GATE_PHASEFLIP
-                ga.basis = int(g.basis)
-                ga.u = ctypes.POINTER(ctypes.c_double)()
-            else:
-                ga.nq = len(g.qubits)
-                ga.flags = 0
-                for j, q in enumerate(g.qubits):
-                    ga.q[j] = q
-                u = np.ascontiguousarray(g.matrix, dtype=np.complex128).view(np.float64).ravel()
-                self._mats.append(u)
-                ga.u = u.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        arr, self._mats = marshal_gates(gates)
         h = ctypes.c_void_p()
         _check(lib().qsim_plan_stages(n, arr, len(gates), ctypes.byref(cfg), ctypes.byref(h)), "qsim_plan_stages")
         self.handle = h
@@ -478,3 +494,28 @@ def predictor_get() -> np.ndarray:
     p = np.empty(MLP_PARAMS, dtype=np.float32)
     _check(lib().qsim_predictor_get(ctypes.c_void_p(p.ctypes.data), p.size), "qsim_predictor_get")
     return p
+
+
+# --------------------------------------------------------------------------
+# autotuner
+# --------------------------------------------------------------------------
+
+def autotune(circuit, base: Optional[Config] = None, m=(18, 24), k=(3, 6), inner=(2, 4), streams=(1, 2, 4),
+             prefix_gates=0, reps=1):
+    """Returns (best Config, prefix seconds, candidates timed; 0 = cache hit)."""
+    base = base if base is not None else default_config(init_basis=circuit.init_basis)
+    mask = 0
+    for sc in streams:
+        mask |= 1 << sc
+    sp = TuneSpace(m[0], m[1], k[0], k[1], inner[0], inner[1], mask, prefix_gates, reps, 0)
+    arr, mats = marshal_gates(circuit.gates)
+    best = Config()
+    secs = ctypes.c_double()
+    cand = ctypes.c_uint32()
+    _check(lib().qsim_autotune(circuit.n, arr, len(circuit.gates), ctypes.byref(base), ctypes.byref(sp),
+                               ctypes.byref(best), ctypes.byref(secs), ctypes.byref(cand)), "qsim_autotune")
+    return best, secs.value, cand.value
+
+
+def autotune_cache_clear():
+    lib().qsim_autotune_cache_clear()
