@@ -10,8 +10,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libqsim.so")
-SOURCES = ["codec.cu", "gates.cu", "engine.cu", "mlp.cu", "noalloc.cu", "planner.cpp", "autotune.cpp"]
-HEADERS = ["codec.cuh", "gates.cuh", "mlp.cuh", "device_common.cuh", "qsim_internal.h"]
+SOURCES = ["codec.cu", "gates.cu", "engine.cu", "mlp.cu", "persistent.cu", "noalloc.cu", "planner.cpp", "autotune.cpp"]
+HEADERS = ["codec.cuh", "codec_dev.cuh", "gates.cuh", "gates_dev.cuh", "mlp.cuh", "persistent.cuh", "device_common.cuh",
+           "qsim_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

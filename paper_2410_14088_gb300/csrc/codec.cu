@@ -22,6 +22,7 @@
 #include <stdint.h>
 
 #include "codec.cuh"
+#include "codec_dev.cuh"
 #include "device_common.cuh"
 #include "gates.cuh"
 
@@ -29,74 +30,8 @@ namespace qsim {
 
 namespace {
 
-constexpr int NT = 256;          // threads per CTA (8 warps)
-constexpr int NW = NT / 32;
-constexpr int MAX_C = 128;       // chunks per plane per frame (F = 4096)
-constexpr int MAX_CPW = MAX_C / NW;  // chunk pairs per warp
-constexpr uint32_t kFlagA = 1u, kFlagP = 2u;
-constexpr uint32_t kEpochMask = (1u << 30) - 1;
-constexpr long long kSpinLimit = 1ll << 22;
+using namespace cdev;
 
-__device__ __forceinline__ uint64_t lb_word(uint32_t epoch, uint32_t flag, uint32_t value) {
-    return (uint64_t(epoch & kEpochMask) << 34) | (uint64_t(flag) << 32) | value;
-}
-
-struct FrameGeom {
-    int fl;
-    uint32_t F, C, nframes;
-    uint64_t data_start;
-};
-
-__device__ __forceinline__ FrameGeom geom(int m) {
-    FrameGeom g;
-    g.fl = m < 12 ? m : 12;
-    g.F = 1u << g.fl;
-    g.C = g.F / 32;
-    g.nframes = 1u << (m - g.fl);
-    g.data_start = 32 + ((4ull * (g.nframes + 1) + 15) & ~15ull);
-    return g;
-}
-
-__device__ __forceinline__ uint32_t zigzag(int32_t d) {
-    return (uint32_t(d) << 1) ^ uint32_t(d >> 31);
-}
-
-__device__ __forceinline__ int32_t unzigzag(uint32_t z) {
-    return int32_t((z >> 1) ^ (0u - (z & 1u)));
-}
-
-// ---------------------------------------------------------------------------
-// Decode: one CTA per frame (grid-stride over all frames of all blocks).
-// ---------------------------------------------------------------------------
-// Leading phase ops of a stage, applied to each decoded amplitude: w is the
-// amplitude's working index, gb the full-index bits of its group's outer qubits.
-__device__ __forceinline__ float2 apply_pre_ops(float2 v, uint64_t w, uint64_t gb, const OpDev *ops, uint32_t nops,
-                                                const float2 *__restrict__ mats) {
-    for (uint32_t o = 0; o < nops; ++o) {
-        const OpDev &op = ops[o];
-        if (op.type == OP_DIAG) {
-            uint32_t idx = 0;
-            for (uint32_t j = 0; j < op.k; ++j) {
-                const uint32_t src = op.dsrc[j];
-                const uint64_t bit = src < 64 ? (w >> src) & 1ull : (gb >> (src - 64)) & 1ull;
-                idx |= uint32_t(bit) << j;
-            }
-            const float2 ph = __ldg(mats + op.mat + idx);
-            v = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
-        } else if (op.basis_in_stage && gb == op.basis_outer && w == op.basis_w) {
-            v = make_float2(-v.x, -v.y);
-        }
-    }
-    return v;
-}
-
-// One warp per frame, no block-wide barriers: the warp reads the header and
-// the frame's offsets with one load per lane, the 2C width bytes with one
-// 8-byte load per lane (lane l holds the widths of chunks 8l..8l+7), builds
-// the chunk offsets with a warp prefix sum, then decodes the chunk pairs
-// (Re chunk c, Im chunk c) eight at a time with all sixteen payload loads in
-// flight: bit-plane transpose, zigzag inverse, inclusive prefix sum (the
-// Lorenzo inverse), x' = q * 2^e, interleaved (re, im) stores.
 __global__ void __launch_bounds__(NT, 3) k_decode(const BlockRef *__restrict__ in, const BlockSlot *__restrict__ table,
                                                const uint32_t *__restrict__ ids, uint32_t nblocks, int m,
                                                float2 *__restrict__ wv, uint32_t *__restrict__ hist,
@@ -106,9 +41,8 @@ __global__ void __launch_bounds__(NT, 3) k_decode(const BlockRef *__restrict__ i
     __shared__ uint32_t s_hist[NW][32];
     if (threadIdx.x < pre.count) s_pre[threadIdx.x] = pre.ops[threadIdx.x];
     __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int warp = threadIdx.x >> 5;
     const uint64_t items = uint64_t(nblocks) * g.nframes;
-    const uint32_t padw = (2u * g.C + 15u) & ~15u;
     for (uint64_t item = uint64_t(blockIdx.x) * NW + warp; item < items; item += uint64_t(gridDim.x) * NW) {
         const uint32_t j = uint32_t(item / g.nframes), f = uint32_t(item % g.nframes);
         const uint8_t *sp;
@@ -121,141 +55,11 @@ __global__ void __launch_bounds__(NT, 3) k_decode(const BlockRef *__restrict__ i
             sp = in[j].ptr;
             bytes = in[j].bytes;
         }
-        float2 *dst = wv + (uint64_t(j) << m) + uint64_t(f) * g.F;
-        if (hist) s_hist[warp][lane] = 0;
-        // ---- header and offsets: one load per lane ----
-        const bool can = sp != nullptr && !(reinterpret_cast<uintptr_t>(sp) & 15) && bytes >= g.data_start;
-        uint32_t hv = 0;
-        if (can) {
-            const uint32_t *h32 = reinterpret_cast<const uint32_t *>(sp);
-            if (lane < 8) hv = h32[lane];
-            else if (lane == 8) hv = h32[8];                    // offsets[0]
-            else if (lane == 9) hv = h32[8 + f];                // offsets[f]
-            else if (lane == 10) hv = h32[8 + f + 1];           // offsets[f+1]
-            else if (lane == 11) hv = h32[8 + g.nframes];       // offsets[nframes]
-        }
-        const uint32_t magic = __shfl_sync(kFull, hv, 0), w1 = __shfl_sync(kFull, hv, 1);
-        const uint32_t w2 = __shfl_sync(kFull, hv, 2), nfr = __shfl_sync(kFull, hv, 3);
-        const uint64_t total = uint64_t(__shfl_sync(kFull, hv, 4)) | (uint64_t(__shfl_sync(kFull, hv, 5)) << 32);
-        const uint64_t rsv = uint64_t(__shfl_sync(kFull, hv, 6)) | (uint64_t(__shfl_sync(kFull, hv, 7)) << 32);
-        const uint32_t o0 = __shfl_sync(kFull, hv, 8), fa = __shfl_sync(kFull, hv, 9);
-        const uint32_t fb = __shfl_sync(kFull, hv, 10), on = __shfl_sync(kFull, hv, 11);
-        const int e = int(int8_t(uint8_t(w2 >> 16)));
-        bool ok = can && magic == kQszMagic && w1 == 1u && (w2 & 0xff) == uint32_t(m) &&
-                  ((w2 >> 8) & 0xff) == uint32_t(g.fl) && (w2 >> 24) == 0 && nfr == g.nframes && rsv == 0 &&
-                  e >= kQszEMin && e <= kQszEMax && total <= bytes && total >= g.data_start &&
-                  o0 == g.data_start && on == total && fb >= fa && fb <= total && fa >= g.data_start &&
-                  !((fa | fb) & 15u) && (fb == fa || fb - fa >= padw);
-        uint32_t wsum = 0, wmax = 0;
-        uint2 wb = make_uint2(0, 0);
-        uint32_t base_off = 0;
-        if (ok && fb > fa) {
-            // ---- widths: lane l holds chunks 8l .. 8l+7 (Re chunks 0..C-1, then Im chunks) ----
-            if (8u * lane < 2u * g.C) wb = *reinterpret_cast<const uint2 *>(sp + fa + 8u * lane);
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const uint32_t a = (wb.x >> (8 * t)) & 0xff, b = (wb.y >> (8 * t)) & 0xff;
-                wsum += a + b;
-                wmax = max(wmax, max(a, b));
-            }
-            uint32_t incl = wsum;
-#pragma unroll
-            for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, incl, o);
-                if (lane >= o) incl += t;
-            }
-            base_off = incl - wsum;
-            const uint32_t words = __shfl_sync(kFull, incl, 31);
-            const uint32_t maxw = __reduce_max_sync(kFull, wmax);
-            ok = maxw <= 32 && words > 0 && uint64_t(fb - fa) == padw + ((4ull * words + 15) & ~15ull);
-        }
-        if (!ok) {
-            if (lane == 0) raise_status(status, QSIM_E_CORRUPT);
-        }
-        if (!ok || fb == fa) {
-            for (uint32_t i = lane; i < g.F; i += 32) dst[i] = make_float2(0.f, 0.f);
-            if (hist && lane == 0) atomicAdd(&hist[uint64_t(j) * 32], 2 * g.F);
-            continue;
-        }
-        const uint32_t *payload = reinterpret_cast<const uint32_t *>(sp + fa + padw);
-        const float step = exp2i(e);
-        // ---- chunk pairs, eight at a time ----
-        for (uint32_t c0 = 0; c0 < g.C; c0 += 8) {
-            // widths/offsets of Re chunks c0.. (owner lane c0/8) and Im chunks C+c0.. (owner (C+c0)/8)
-            const uint32_t lr = c0 >> 3, li = (g.C + c0) >> 3;
-            const uint2 wr8 = make_uint2(__shfl_sync(kFull, wb.x, lr), __shfl_sync(kFull, wb.y, lr));
-            const uint2 wi8 = make_uint2(__shfl_sync(kFull, wb.x, li), __shfl_sync(kFull, wb.y, li));
-            uint32_t offr = __shfl_sync(kFull, base_off, lr), offi = __shfl_sync(kFull, base_off, li);
-            // Im chunks of a small frame (C < 8) share the owner lane with the Re chunks: skip those slots
-            const uint32_t si0 = (g.C + c0) & 7u;
-            uint32_t xr[8], xi[8], wr[8], wi[8];
-            {
-                uint32_t sr_ = 0, si_ = 0;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const uint32_t ar = t < 4 ? (wr8.x >> (8 * t)) & 0xff : (wr8.y >> (8 * (t - 4))) & 0xff;
-                    const uint32_t ti = si0 + t;
-                    const uint32_t ai = ti < 8 ? (ti < 4 ? (wi8.x >> (8 * ti)) & 0xff : (wi8.y >> (8 * (ti - 4))) & 0xff) : 0;
-                    wr[t] = ar;
-                    wi[t] = ai;
-                }
-                // offsets of the Im chunks start after the skipped slots of their owner lane
-                for (uint32_t t = 0; t < si0; ++t)
-                    offi += t < 4 ? (wi8.x >> (8 * t)) & 0xff : (wi8.y >> (8 * (t - 4))) & 0xff;
-#pragma unroll
-                for (int t = 0; t < 8; ++t) {
-                    const bool live = c0 + t < g.C;
-                    xr[t] = (live && lane < int(wr[t])) ? __ldg(payload + offr + sr_ + lane) : 0u;
-                    xi[t] = (live && lane < int(wi[t])) ? __ldg(payload + offi + si_ + lane) : 0u;
-                    sr_ += wr[t];
-                    si_ += wi[t];
-                }
-            }
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const uint32_t c = c0 + t;
-                if (c >= g.C) break;
-                const uint32_t zr = warp_bit_transpose(xr[t], lane);
-                const uint32_t zi = warp_bit_transpose(xi[t], lane);
-                uint32_t qr = uint32_t(unzigzag(zr)), qi = uint32_t(unzigzag(zi));
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t tr = __shfl_up_sync(kFull, qr, o);
-                    const uint32_t ti = __shfl_up_sync(kFull, qi, o);
-                    if (lane >= o) { qr += tr; qi += ti; }
-                }
-                const int32_t sr = int32_t(qr), si = int32_t(qi);
-                float2 v = make_float2(float(sr) * step, float(si) * step);
-                if (pre.count) {
-                    const uint64_t w = (uint64_t(j % pre.G) << m) | (uint64_t(f) * g.F + c * 32 + lane);
-                    v = apply_pre_ops(v, w, pre.gbase[j / pre.G], s_pre, pre.count, pre.mats);
-                }
-                dst[c * 32 + lane] = v;
-                if (hist) {
-                    const uint32_t br = 32 - __clz(sr < 0 ? uint32_t(-sr) : uint32_t(sr));
-                    const uint32_t bi = 32 - __clz(si < 0 ? uint32_t(-si) : uint32_t(si));
-                    atomicAdd(&s_hist[warp][br & 31], 1u);
-                    atomicAdd(&s_hist[warp][bi & 31], 1u);
-                }
-            }
-        }
-        if (hist) {
-            __syncwarp();
-            const uint32_t v = s_hist[warp][lane];
-            if (v) atomicAdd(&hist[uint64_t(j) * 32 + lane], v);
-            __syncwarp();
-        }
+        decode_frame_warp(sp, bytes, g, m, f, wv + (uint64_t(j) << m) + uint64_t(f) * g.F,
+                          hist ? hist + uint64_t(j) * 32 : nullptr, s_hist[warp], status, s_pre, pre.count, pre.mats,
+                          pre.count ? (uint64_t(j % pre.G) << m) : 0, pre.count ? pre.gbase[j / pre.G] : 0);
     }
 }
-
-// ---------------------------------------------------------------------------
-// Encode: one CTA per frame, ticket-ordered, decoupled look-back. The frame
-// image (widths, then bit-plane words) is assembled in shared memory while
-// warp 0 finds the frame's byte offset, then copied out with 16-byte stores.
-// The bit planes of a chunk, W_b = ballot(bit b of z_j), are produced for all
-// b at once by a 32x32 bit transpose across the warp (five shuffle stages).
-// ---------------------------------------------------------------------------
-constexpr uint32_t kStageWords = (256 + 8 * 4096) / 4 + 4;  // widths + worst-case payload + pad
 
 __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
                                                const EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
@@ -264,13 +68,8 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
                                                LookbackScratch scr, int *status) {
     const FrameGeom g = geom(m);
     __shared__ __align__(16) uint32_t s_stage[kStageWords];
-    __shared__ uint32_t s_w[2 * MAX_C];
-    __shared__ uint32_t s_off[2 * MAX_C];
-    __shared__ uint32_t s_warp[NW];
-    __shared__ uint32_t s_total;
+    __shared__ EncSmem SE;
     __shared__ uint32_t s_item, s_epoch;
-    __shared__ uint64_t s_excl;
-    __shared__ double s_red[2][NW];
     __shared__ int s_skip;
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -284,213 +83,10 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
     const uint32_t j = item / g.nframes, f = item % g.nframes;
     if (tid == 0) s_skip = (j >= nblocks) || (only_overflowed && res[j].overflow == 0);
     __syncthreads();
-
-    if (!s_skip) {
-        const float2 *src = wv + (uint64_t(j) << m) + uint64_t(f) * g.F;
-        const float inv_step = exp2i(-e);
-        const float step = exp2i(e);
-        // x - x' is exact in FP32 (|x - x'| <= s/2 <= |x'|/2 when q != 0, x' = 0 otherwise), so the
-        // per-thread sums are FP32 and only the per-CTA totals are accumulated in FP64
-        float err_sq = 0.f, norm_sq = 0.f;
-        int bad = 0;
-        float2 vin[MAX_CPW];
-#pragma unroll
-        for (int i = 0; i < MAX_CPW; ++i) {
-            const uint32_t c = warp + i * NW;
-            vin[i] = c < g.C ? __ldcs(src + c * 32 + lane) : make_float2(0.f, 0.f);
-        }
-        uint32_t zr[MAX_CPW], zi[MAX_CPW];
-#pragma unroll
-        for (int i = 0; i < MAX_CPW; ++i) {
-            zr[i] = zi[i] = 0;
-            const uint32_t c = warp + i * NW;
-            if (c < g.C) {
-                int32_t q[2];
-                const float x[2] = {vin[i].x, vin[i].y};
-#pragma unroll
-                for (int p = 0; p < 2; ++p) {
-                    if (!isfinite(x[p])) {
-                        bad = QSIM_E_INVALID;
-                        q[p] = 0;
-                    } else {
-                        const float t = x[p] * inv_step;  // exact: power-of-two scaling
-                        if (fabsf(t) >= 1073741824.0f) {
-                            bad = bad ? bad : QSIM_E_RANGE;
-                            q[p] = 0;
-                        } else {
-                            q[p] = __float2int_rn(t);
-                        }
-                    }
-                    const float xr = float(q[p]) * step;
-                    const float dx = x[p] - xr;
-                    err_sq = fmaf(dx, dx, err_sq);
-                    norm_sq = fmaf(xr, xr, norm_sq);
-                }
-                const int32_t pr = __shfl_up_sync(kFull, q[0], 1);
-                const int32_t pi = __shfl_up_sync(kFull, q[1], 1);
-                zr[i] = zigzag(lane ? int32_t(uint32_t(q[0]) - uint32_t(pr)) : q[0]);
-                zi[i] = zigzag(lane ? int32_t(uint32_t(q[1]) - uint32_t(pi)) : q[1]);
-                const uint32_t wr = 32 - __clz(__reduce_or_sync(kFull, zr[i]));
-                const uint32_t wi = 32 - __clz(__reduce_or_sync(kFull, zi[i]));
-                if (lane == 0) {
-                    s_w[c] = wr;
-                    s_w[g.C + c] = wi;
-                }
-            }
-        }
-        if (bad) raise_status(status, bad);
-        __syncthreads();
-        const uint32_t my_w = tid < int(2 * g.C) ? s_w[tid] : 0;
-        const uint32_t my_off = block_exclusive_scan<NT>(my_w, s_warp, &s_total);
-        const uint32_t padw = (2u * g.C + 15u) & ~15u;
-        if (tid < int(2 * g.C)) s_off[tid] = my_off;
-        // width bytes (and their zero padding) at the head of the frame image
-        if (tid < int(padw) / 4) {
-            uint32_t wbytes = 0;
-#pragma unroll
-            for (int t = 0; t < 4; ++t) {
-                const uint32_t x = 4 * tid + t;
-                wbytes |= (x < 2 * g.C ? s_w[x] : 0u) << (8 * t);
-            }
-            s_stage[tid] = wbytes;
-        }
-        const uint32_t words = s_total;
-        const uint32_t len = words ? uint32_t(padw + ((4ull * words + 15) & ~15ull)) : 0u;
-        __syncthreads();
-
-        // ---- warp 0: decoupled look-back over the preceding frames of this block ----
-        if (warp == 0) {
-            uint64_t *st = scr.state + uint64_t(j) * g.nframes;
-            if (f == 0) {
-                if (lane == 0) {
-                    st_relaxed_u64(st, lb_word(epoch, kFlagP, len));
-                    s_excl = 0;
-                }
-            } else {
-                if (lane == 0) st_relaxed_u64(st + f, lb_word(epoch, kFlagA, len));
-                uint64_t excl = 0;
-                int64_t end = int64_t(f) - 1;
-                bool timed_out = false;
-                while (true) {
-                    const int64_t p = end - lane;
-                    uint32_t flag = kFlagP, val = 0;
-                    if (p >= 0) {
-                        long long spins = 0;
-                        while (true) {
-                            const uint64_t w = ld_relaxed_u64(st + p);
-                            const uint32_t fl = uint32_t(w >> 32) & 3u;
-                            if (fl != 0 && uint32_t(w >> 34) == epoch) {
-                                flag = fl;
-                                val = uint32_t(w);
-                                break;
-                            }
-                            if (++spins > kSpinLimit) {
-                                timed_out = true;
-                                flag = kFlagP;
-                                val = 0;
-                                break;
-                            }
-                            __nanosleep(32);
-                        }
-                    }
-                    const uint32_t pmask = __ballot_sync(kFull, flag == kFlagP);
-                    const int first = pmask ? __ffs(pmask) - 1 : 32;
-                    uint64_t contrib = lane <= first ? val : 0;
-#pragma unroll
-                    for (int o = 16; o; o >>= 1) contrib += __shfl_xor_sync(kFull, contrib, o);
-                    excl += contrib;
-                    if (pmask) break;
-                    end -= 32;
-                }
-                if (__any_sync(kFull, timed_out) && lane == 0) raise_status(status, QSIM_E_TIMEOUT);
-                if (lane == 0) {
-                    st_relaxed_u64(st + f, lb_word(epoch, kFlagP, uint32_t(excl + len)));
-                    s_excl = excl;
-                }
-            }
-        }
-        // ---- bit-plane words into the frame image: W_b = ballot(bit b of z) ----
-        uint32_t *stage_words = s_stage + padw / 4;
-#pragma unroll
-        for (int i = 0; i < MAX_CPW; ++i) {
-            const uint32_t c = warp + i * NW;
-            if (c < g.C) {
-                const uint32_t wr = s_w[c], wi = s_w[g.C + c];
-                // lane b receives W_b = ballot(bit b of z): the bit-matrix transpose of the chunk's codes
-                const uint32_t word_r = warp_bit_transpose(zr[i], lane);
-                const uint32_t word_i = warp_bit_transpose(zi[i], lane);
-                if (lane < int(wr)) stage_words[s_off[c] + lane] = word_r;
-                if (lane < int(wi)) stage_words[s_off[g.C + c] + lane] = word_i;
-            }
-        }
-        if (words + uint32_t(tid) < (len > padw ? (len - padw) / 4 : 0u)) stage_words[words + tid] = 0;  // pad
-        __syncthreads();
-        const uint64_t frame_off = g.data_start + s_excl;
-        uint8_t *out = tgt[j].ptr;
-        const uint64_t cap = tgt[j].cap;
-        const bool fits = frame_off + len <= cap;
-        if (fits && len) {
-            uint4 *o4 = reinterpret_cast<uint4 *>(out + frame_off);
-            const uint4 *s4 = reinterpret_cast<const uint4 *>(s_stage);
-            for (uint32_t i = tid; i < len / 16; i += NT) o4[i] = s4[i];
-        }
-        if (!fits && tid == 0) atomicOr(&res[j].overflow, 1u);
-        if (tid == 0 && g.data_start <= cap)
-            reinterpret_cast<uint32_t *>(out + 32)[f] = uint32_t(frame_off);
-        if (f == g.nframes - 1 && tid == 0) {
-            const uint64_t total = frame_off + len;
-            res[j].total = total;
-            if (total <= cap) {
-                uint32_t *h32 = reinterpret_cast<uint32_t *>(out);
-                h32[0] = kQszMagic;
-                h32[1] = 1u;  // version 1, flags 0
-                h32[2] = uint32_t(m) | (uint32_t(g.fl) << 8) | (uint32_t(uint8_t(int8_t(e))) << 16);
-                h32[3] = g.nframes;
-                reinterpret_cast<uint64_t *>(out)[2] = total;
-                reinterpret_cast<uint64_t *>(out)[3] = 0;
-                h32[8 + g.nframes] = uint32_t(total);
-                for (uint64_t b = 32 + 4ull * (g.nframes + 1); b < g.data_start; ++b) out[b] = 0;
-                if (table) {
-                    table[ids[j]].ptr = out;
-                    table[ids[j]].bytes = total;
-                    table[ids[j]].tier = tgt[j].tier;
-                }
-                if (acc) {
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&acc->store_bytes), total);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&acc->reserved_bytes), cap);
-                    if (tgt[j].tier) atomicAdd(reinterpret_cast<unsigned long long *>(&acc->host_bytes), cap);
-                    atomicAdd(reinterpret_cast<unsigned long long *>(&acc->blocks), 1ull);
-                }
-            } else if (acc) {
-                atomicAdd(reinterpret_cast<unsigned long long *>(&acc->overflow_blocks), 1ull);
-            }
-        }
-        // error norms of this frame (only counted once: not on the overflow retry)
-#pragma unroll
-        for (int o = 16; o; o >>= 1) {
-            err_sq += __shfl_xor_sync(kFull, err_sq, o);
-            norm_sq += __shfl_xor_sync(kFull, norm_sq, o);
-        }
-        if (lane == 0) {
-            s_red[0][warp] = double(err_sq);
-            s_red[1][warp] = double(norm_sq);
-        }
-        __syncthreads();
-        if (tid == 0 && !only_overflowed) {
-            double a = 0, b = 0;
-            for (int w = 0; w < NW; ++w) { a += s_red[0][w]; b += s_red[1][w]; }
-            if (scr.part) {
-                scr.part[item] = make_float2(float(a), float(b));  // reduced by the last CTA
-            } else {
-                atomicAdd(&res[j].err_sq, a);
-                atomicAdd(&res[j].norm_sq, b);
-                if (acc) {
-                    atomicAdd(&acc->err_sq, a);
-                    atomicAdd(&acc->norm_sq, b);
-                }
-            }
-        }
-    }
+    if (!s_skip)
+        encode_frame_cta(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, g, m, e, f, scr.state + uint64_t(j) * g.nframes,
+                         epoch, tgt[j], res + j, table ? table + ids[j] : nullptr, acc,
+                         scr.part ? scr.part + item : nullptr, only_overflowed, s_stage, SE, status);
     // ---- last CTA: reduce the frame partials, reset the ticket counter, advance the epoch ----
     if (tid == 0) {
         __threadfence();
@@ -522,13 +118,13 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
             tb += b;
         }
         if (lane == 0) {
-            s_red[0][warp] = ta;
-            s_red[1][warp] = tb;
+            SE.red[0][warp] = ta;
+            SE.red[1][warp] = tb;
         }
         __syncthreads();
         if (tid == 0 && acc) {
             double a = 0, b = 0;
-            for (int w = 0; w < NW; ++w) { a += s_red[0][w]; b += s_red[1][w]; }
+            for (int w = 0; w < NW; ++w) { a += SE.red[0][w]; b += SE.red[1][w]; }
             atomicAdd(&acc->err_sq, a);
             atomicAdd(&acc->norm_sq, b);
         }
@@ -541,40 +137,6 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
     }
 }
 
-// ---------------------------------------------------------------------------
-// Reservation of one block's slot from the two-tier pool: device arena
-// first, then the pinned host arena; slots are padded to 256 bytes.
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void reserve_slot(uint64_t want, const ArenaDev &dev, const ArenaDev &host, EncTarget *t,
-                                             int *status) {
-    const uint64_t sz = (want + 255) & ~255ull;
-    uint64_t off = atomicAdd(reinterpret_cast<unsigned long long *>(dev.bump), sz);
-    if (off + sz <= dev.cap) {
-        t->ptr = dev.base + off;
-        t->cap = sz;
-        t->tier = 0;
-        return;
-    }
-    if (host.base) {
-        off = atomicAdd(reinterpret_cast<unsigned long long *>(host.bump), sz);
-        if (off + sz <= host.cap) {
-            t->ptr = host.base + off;
-            t->cap = sz;
-            t->tier = 1;
-            return;
-        }
-    }
-    t->ptr = nullptr;
-    t->cap = 0;
-    t->tier = 0;
-    raise_status(status, QSIM_E_NOMEM);
-}
-
-// ---------------------------------------------------------------------------
-// Sizing pass: exact stream size of every block (reads the data once more),
-// then the last CTA to finish reserves each block's slot and clears the size
-// counters for the next launch.
-// ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(NT) k_encode_size(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
                                                     uint64_t *__restrict__ sizes, uint32_t *done_ctr,
                                                     ArenaDev dev, ArenaDev host, EncTarget *__restrict__ tgt,
@@ -584,47 +146,10 @@ __global__ void __launch_bounds__(NT) k_encode_size(const float2 *__restrict__ w
     __shared__ bool s_last;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t items = uint64_t(nblocks) * g.nframes;
-    const float inv_step = exp2i(-e);
     for (uint64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const uint32_t j = uint32_t(item / g.nframes), f = uint32_t(item % g.nframes);
-        const float2 *src = wv + (uint64_t(j) << m) + uint64_t(f) * g.F;
-        float2 vin[MAX_CPW];
-#pragma unroll
-        for (int i = 0; i < MAX_CPW; ++i) {
-            const uint32_t c = warp + i * NW;
-            vin[i] = c < g.C ? src[c * 32 + lane] : make_float2(0.f, 0.f);
-        }
-        uint32_t words = 0;
-        int bad = 0;
-#pragma unroll
-        for (int i = 0; i < MAX_CPW; ++i) {
-            const uint32_t c = warp + i * NW;
-            if (c >= g.C) break;
-            int32_t q[2];
-            const float x[2] = {vin[i].x, vin[i].y};
-#pragma unroll
-            for (int p = 0; p < 2; ++p) {
-                float t = x[p] * inv_step;
-                if (!isfinite(x[p])) { bad = QSIM_E_INVALID; q[p] = 0; }
-                else if (fabsf(t) >= 1073741824.0f) { bad = bad ? bad : QSIM_E_RANGE; q[p] = 0; }
-                else q[p] = __float2int_rn(t);
-            }
-            int32_t pr = __shfl_up_sync(kFull, q[0], 1);
-            int32_t pi = __shfl_up_sync(kFull, q[1], 1);
-            const uint32_t zr = zigzag(lane ? int32_t(uint32_t(q[0]) - uint32_t(pr)) : q[0]);
-            const uint32_t zi = zigzag(lane ? int32_t(uint32_t(q[1]) - uint32_t(pi)) : q[1]);
-            words += (32 - __clz(__reduce_or_sync(kFull, zr))) + (32 - __clz(__reduce_or_sync(kFull, zi)));
-        }
-        if (bad) raise_status(status, bad);
-        if (lane == 0) s_words[warp] = words;
-        __syncthreads();
-        if (tid == 0) {
-            uint32_t tot = 0;
-            for (int w = 0; w < NW; ++w) tot += s_words[w];
-            const uint64_t padw = (2ull * g.C + 15) & ~15ull;
-            const uint64_t len = tot ? padw + ((4ull * tot + 15) & ~15ull) : 0;
-            if (len) atomicAdd(reinterpret_cast<unsigned long long *>(&sizes[j]), len);
-        }
+        const uint32_t len = size_frame_cta(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, g, e, s_words, status);
+        if (tid == 0 && len) atomicAdd(reinterpret_cast<unsigned long long *>(&sizes[j]), uint64_t(len));
         __syncthreads();
     }
     if (!done_ctr) return;

@@ -29,6 +29,13 @@ __device__ __forceinline__ void st_relaxed_u64(uint64_t *p, uint64_t v) {
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// nanoseconds of the GPU's global timer (for time-bounded waits)
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+    return t;
+}
+
 // 2^e as a float for e in [-126, 127] (a normal number, exact).
 __device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) << 23); }
 

@@ -32,6 +32,7 @@
 #include "device_common.cuh"
 #include "gates.cuh"
 #include "mlp.cuh"
+#include "persistent.cuh"
 #include "qsim_internal.h"
 
 namespace qsim {
@@ -57,9 +58,10 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 // ---------------------------------------------------------------------------
 static std::atomic<int> g_profile{0};
 enum ProfCat { P_DECODE = 0, P_PASS, P_ENCODE_SIZE, P_RESERVE, P_ENCODE, P_GATHER, P_COPY_IN, P_COPY_OUT, P_INIT,
-               P_PREDICT, P_REENCODE, P_NCAT };
+               P_PREDICT, P_REENCODE, P_STAGE, P_NCAT };
 static const char *kProfNames[P_NCAT] = {"decode", "gate_pass", "encode_size", "reserve", "encode",
-                                         "gather_refs", "copy_in", "copy_out", "init", "predict", "reencode"};
+                                         "gather_refs", "copy_in", "copy_out", "init", "predict", "reencode",
+                                         "stage_persistent"};
 
 struct Profiler {
     bool on = false;
@@ -632,10 +634,201 @@ struct StreamWork {
     DevBuf<float> pred;      // per block: predicted log2 stream bytes
 };
 
+static StageFeatures stage_features(const qsim_plan *p, size_t si, int e) {
+    const Stage &st = p->stages[si];
+    uint32_t dense = 0, diag = 0, kmax = 0, nondiag = 0;
+    for (const Op &op : st.ops) {
+        if (op.type == OP_DENSE) {
+            ++dense;
+            kmax = std::max(kmax, op.k);
+        } else {
+            ++diag;
+        }
+    }
+    for (size_t gi = st.first_gate; gi < st.first_gate + st.ngates; ++gi) nondiag += p->gates[gi].diag ? 0 : 1;
+    StageFeatures sf{};
+    sf.v[0] = float(p->cfg.m) / 32.f;
+    sf.v[1] = float(st.inner.size()) / 8.f;
+    sf.v[2] = float(dense) / 16.f;
+    sf.v[3] = float(diag) / 16.f;
+    sf.v[4] = float(kmax) / 6.f;
+    sf.v[5] = float(-e) / 64.f;
+    sf.v[6] = float(st.ngates) / 64.f;
+    sf.v[7] = st.ngates ? float(nondiag) / float(st.ngates) : 0.f;
+    return sf;
+}
+
+// Mode B: one persistent kernel per stage (optionally the whole stage loop
+// captured into a CUDA graph and launched once).
+template <class DevArenaFn, class HostArenaFn>
+static int run_stages_persistent(const qsim_plan *p, PlanDev *pd, cudaStream_t main, int e, uint64_t worst,
+                                 uint64_t nblocks, BlockSlot *tables, StageAccum *accs, uint64_t *bumps,
+                                 DevArenaFn arena_dev, HostArenaFn arena_host, int *status, Profiler &prof,
+                                 const float *pparams, int pbf16) {
+    const qsim_config &cfg = p->cfg;
+    const uint32_t m = cfg.m;
+    const uint64_t nframes = qsz_nframes(int(m));
+    uint32_t maxW = m, maxG = 1, maxT = 5, max_mat = 0, max_groups = 1;
+    for (const StageDev &sd : pd->stages) {
+        maxW = std::max(maxW, sd.W);
+        maxG = std::max(maxG, sd.G);
+        max_groups = std::max(max_groups, sd.ngroups);
+        for (const PassDev &ps : sd.passes_host) {
+            maxT = std::max(maxT, ps.T);
+            max_mat = std::max(max_mat, ps.mat_elems);
+            if (ps.kmax > 5) return set_error(QSIM_E_INVALID, "persistent mode fuses at most k = 5 qubits");
+        }
+    }
+    // slots: enough working vectors to overlap groups, about 256 MiB of them
+    const uint32_t R = uint32_t(std::max<uint64_t>(2, std::min<uint64_t>(max_groups, (1ull << 25) >> maxW)));
+    DevBuf<float2> wv;
+    DevBuf<uint64_t> lb, sizes;
+    DevBuf<float2> part;
+    DevBuf<EncTarget> tgt;
+    DevBuf<EncResult> res;
+    DevBuf<uint32_t> hist, sync, ctr;
+    int rc;
+    if ((rc = wv.alloc((uint64_t(R) * maxG) << m)) || (rc = lb.alloc(uint64_t(R) * maxG * nframes)) ||
+        (rc = part.alloc(uint64_t(R) * maxG * nframes)) || (rc = tgt.alloc(nblocks)) || (rc = res.alloc(nblocks)) ||
+        (rc = sizes.alloc(nblocks)) || (rc = hist.alloc(pparams ? nblocks * 32 : 1)) ||
+        (rc = sync.alloc(2ull * max_groups * kMaxPhases)) || (rc = ctr.alloc(4)))
+        return rc;
+    CUDA_TRY(cudaMemsetAsync(lb.p, 0, lb.n * sizeof(uint64_t), main));
+    CUDA_TRY(cudaMemsetAsync(ctr.p, 0, 4 * sizeof(uint32_t), main));
+    const size_t smem = persistent_smem_bytes(maxT, max_mat);
+    const size_t nst = p->stages.size();
+    if ((rc = prepare_stage_persistent(int(cfg.prec), smem))) return set_error(rc, "persistent kernel set-up failed");
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // the caller's stream may be the legacy default stream, which cannot be captured: capture on our own
+    cudaStream_t cs = main;
+    cudaEvent_t ev_join = nullptr;
+    if (cfg.graph) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventRecord(ev_join, main));
+        CUDA_TRY(cudaStreamWaitEvent(cs, ev_join, 0));
+        CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    }
+    auto end_capture_on_error = [&]() {
+        if (cfg.graph) {
+            cudaStreamEndCapture(cs, &graph);
+            if (graph) cudaGraphDestroy(graph);
+            cudaEventDestroy(ev_join);
+            cudaStreamDestroy(cs);
+        }
+    };
+    for (size_t si = 0; si < nst; ++si) {
+        const StageDev &sd = pd->stages[si];
+        const int in_par = si & 1, out_par = (si + 1) & 1;
+        PStageArgs a{};
+        a.W = sd.W;
+        a.G = sd.G;
+        a.ngroups = sd.ngroups;
+        a.R = R;
+        a.m = m;
+        a.e = e;
+        a.npre = sd.npre;
+        a.pre_begin = sd.pre_begin;
+        a.pbf16 = uint32_t(pbf16);
+        uint32_t nph = 0;
+        const uint32_t gframes = sd.G * uint32_t(nframes);
+        auto add = [&](uint32_t type, uint32_t count, uint32_t arg) {
+            a.ph[nph].type = type;
+            a.ph[nph].count = count;
+            a.ph[nph].arg = arg;
+            ++nph;
+        };
+        add(PH_DECODE, (gframes + 7) / 8, 0);
+        if (pparams) add(PH_PREDICT, 1, 0);
+        for (uint32_t pi = 0; pi < sd.npasses; ++pi) add(PH_PASS, 1u << sd.passes_host[pi].nout, pi);
+        if (!pparams) add(PH_SIZE, gframes, 0);
+        add(PH_ENCODE, gframes, 0);
+        if (pparams) {
+            add(PH_FIX, 1, 0);
+            add(PH_REENCODE, gframes, 0);
+        }
+        if (nph > uint32_t(kMaxPhases)) {
+            end_capture_on_error();
+            return set_error(QSIM_E_UNSUPPORTED, "stage has too many passes for the persistent kernel");
+        }
+        a.nphases = nph;
+        uint32_t acc_items = 0;
+        for (uint32_t t = 0; t < nph; ++t) {
+            a.ph_start[t] = acc_items;
+            acc_items += a.ph[t].count;
+        }
+        a.per_group = acc_items;
+        a.passes = pd->passes.p + sd.pass_begin;
+        a.ops = pd->ops.p;
+        a.mats = pd->mats.p;
+        a.ids = pd->ids.p + pd->ids_off[si];
+        a.gbase = pd->gbase.p + pd->gbase_off[si];
+        a.tab_in = tables + in_par * nblocks;
+        a.tab_out = tables + out_par * nblocks;
+        a.acc = accs + si;
+        a.dev = arena_dev(out_par);
+        a.host = arena_host(out_par);
+        a.data_start = qsz_data_start(int(m));
+        a.worst = worst;
+        a.wv = wv.p;
+        a.lb = lb.p;
+        a.part = part.p;
+        a.tgt = tgt.p;
+        a.res = res.p;
+        a.sizes = sizes.p;
+        a.hist = pparams ? hist.p : nullptr;
+        a.pparams = pparams;
+        a.sf = stage_features(p, si, e);
+        a.margin = cfg.predictor_margin;
+        a.done = sync.p;
+        a.arrive = sync.p + uint64_t(sd.ngroups) * nph;
+        a.ctr = ctr.p;
+        a.status = status;
+        a.stall_test = (si == 0 && (cfg.reserved[0] & 1)) ? 1u : 0u;
+        a.wait_ns = a.stall_test ? 200000000ull : 2000000000ull;  // 0.2 s in the test, else 2 s
+        cudaError_t ce = cudaMemsetAsync(bumps + 2 * out_par, 0, 2 * sizeof(uint64_t), cs);
+        if (ce == cudaSuccess) ce = cudaMemsetAsync(sync.p, 0, 2ull * sd.ngroups * nph * sizeof(uint32_t), cs);
+        if (ce == cudaSuccess)
+            ce = pparams ? cudaMemsetAsync(hist.p, 0, nblocks * 32 * sizeof(uint32_t), cs)
+                         : cudaMemsetAsync(sizes.p, 0, nblocks * sizeof(uint64_t), cs);
+        if (ce != cudaSuccess) {
+            end_capture_on_error();
+            return set_error(QSIM_E_CUDA, "stage set-up: %s", cudaGetErrorString(ce));
+        }
+        prof.begin(P_STAGE, cs);
+        rc = launch_stage_persistent(a, cfg.prec, smem, cs, nullptr);
+        prof.end(cs);
+        if (rc) {
+            end_capture_on_error();
+            return set_error(rc, "persistent stage launch failed");
+        }
+    }
+    if (cfg.graph) {
+        cudaError_t ge = cudaStreamEndCapture(cs, &graph);
+        if (ge == cudaSuccess) ge = cudaGraphInstantiate(&exec, graph, 0);
+        if (ge == cudaSuccess) ge = cudaGraphLaunch(exec, cs);
+        if (ge == cudaSuccess) ge = cudaEventRecord(ev_join, cs);
+        if (ge == cudaSuccess) ge = cudaStreamWaitEvent(main, ev_join, 0);
+        if (ge == cudaSuccess) ge = cudaStreamSynchronize(cs);
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        cudaEventDestroy(ev_join);
+        cudaStreamDestroy(cs);
+        if (ge != cudaSuccess) return set_error(QSIM_E_CUDA, "graph: %s", cudaGetErrorString(ge));
+    } else {
+        CUDA_TRY(cudaStreamSynchronize(main));  // the local buffers are released on return
+    }
+    return QSIM_OK;
+}
+
 static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsim_stats *stats) {
     const qsim_config &cfg = p->cfg;
-    if (cfg.mode != QSIM_MODE_STREAMS)
-        return set_error(QSIM_E_UNSUPPORTED, "persistent mode is not available in this build");
+    const bool persistent = cfg.mode == QSIM_MODE_PERSISTENT;
+    if (persistent && cfg.codec != QSIM_CODEC_QSZ1)
+        return set_error(QSIM_E_INVALID, "persistent mode runs the compressed store (codec QSZ1)");
+    if (persistent && cfg.collect)
+        return set_error(QSIM_E_INVALID, "training-row collection runs in streams mode");
     int dev;
     CUDA_TRY(cudaGetDevice(&dev));
     DeviceCtx &dctx = device_ctx(dev);
@@ -667,7 +860,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     uint32_t maxW = m;
     for (const StageDev &sd : pd->stages) maxW = std::max(maxW, sd.W);
-    const uint32_t nstreams = cfg.streams;
+    const uint32_t nstreams = persistent ? 1 : cfg.streams;
     const uint64_t batch_amps = std::max<uint64_t>(1ull << maxW, 1ull << 22);
     const uint64_t work_bytes = nstreams * batch_amps * 8 * 2;
     // every block plus the initial zero-stream template
@@ -731,6 +924,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
         max_batch_blocks = std::max<uint64_t>(max_batch_blocks, gpb * sd.G);
     }
     max_batch_blocks = std::max<uint64_t>(max_batch_blocks, 2);
+    if (persistent) max_batch_blocks = 2;  // the stream buffers only serve the initial store
     for (uint32_t i = 0; i < nstreams; ++i) {
         StreamWork &w = sw[i];
         CUDA_TRY(cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking));
@@ -761,7 +955,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
     CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
     int *status = dctx.status;
     Profiler prof;
-    prof.on = g_profile.load() != 0;
+    prof.on = g_profile.load() != 0 && !(persistent && cfg.graph);
     CUDA_TRY(cudaEventRecord(ev_start, main));
 
     // ---- initial store (Sec. 4.2): encode the basis block and one zero block once ----
@@ -804,7 +998,16 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
     }
 
     // ---- stage loop ----
-    for (size_t si = 0; si < nst; ++si) {
+    if (persistent) {
+        rc = run_stages_persistent(p, pd, main, e, worst, nblocks, tables.p, accs.p, bumps.p, arena_dev, arena_host,
+                                   status, prof, predict ? dctx.pred_params : nullptr, dctx.pred_bf16);
+        if (rc) {
+            cleanup();
+            destroy_streams();
+            return rc;
+        }
+    }
+    for (size_t si = 0; si < (persistent ? 0 : nst); ++si) {
         const StageDev &sd = pd->stages[si];
         const int in_par = si & 1, out_par = (si + 1) & 1;
         BlockSlot *tab_in = tables.p + in_par * nblocks;
@@ -971,8 +1174,12 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             const StageDev &sd = pd->stages[i];
             bytes[raw ? P_COPY_IN : P_DECODE] += in_store + 8 * amps;
             bytes[P_PASS] += 16 * amps * sd.npasses;
-            for (const Op &op : p->stages[i].ops)
-                flops[P_PASS] += (op.type == OP_DENSE ? 8.0 * double(1u << op.k) : op.type == OP_DIAG ? 6.0 : 0.0) * amps;
+            bytes[P_STAGE] += in_store + out_store + 8 * amps * (2 + (predict ? 0 : 1)) + 16 * amps * sd.npasses;
+            for (const Op &op : p->stages[i].ops) {
+                const double fl = (op.type == OP_DENSE ? 8.0 * double(1u << op.k) : op.type == OP_DIAG ? 6.0 : 0.0) * amps;
+                flops[P_PASS] += fl;
+                flops[P_STAGE] += fl;
+            }
             if (raw) {
                 bytes[P_COPY_OUT] += 8 * amps + out_store;
             } else {

@@ -1,0 +1,386 @@
+// Device functions of the gate passes (shared by the per-pass kernels and the
+// persistent stage kernel). See gates.cu for the method.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "codec.cuh"
+#include "device_common.cuh"
+#include "gates.cuh"
+
+namespace qsim {
+namespace gdev {
+
+
+__device__ __forceinline__ uint32_t swz(uint32_t i) {
+    return i ^ (((i >> 4) ^ (i >> 8) ^ (i >> 12)) & 15u);
+}
+
+struct PassSmem {
+    PassDev p;
+    OpDev op;
+    uint32_t hi[256];
+    uint32_t offs[64];
+};
+
+template <int NT, int K>
+__device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const PassSmem &S, uint32_t T) {
+    constexpr int D = 1 << K;
+    const uint32_t ngroups = 1u << (T - K);
+    const uint32_t nc = T - K;
+    for (uint32_t g = threadIdx.x; g < ngroups; g += NT) {
+        uint32_t b = 0;
+        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.op.comp[t];
+        float2 x[D];
+#pragma unroll
+        for (int c = 0; c < D; ++c) x[c] = tile[swz(b | S.offs[c])];
+#pragma unroll 1
+        for (int r = 0; r < D; ++r) {
+            const float4 *row = reinterpret_cast<const float4 *>(U + r * D);
+            float ar = 0.f, ai = 0.f;
+            if constexpr (D == 2) {
+                float4 u = row[0];
+                ar = fmaf(u.x, x[0].x, ar); ar = fmaf(-u.y, x[0].y, ar);
+                ai = fmaf(u.x, x[0].y, ai); ai = fmaf(u.y, x[0].x, ai);
+                ar = fmaf(u.z, x[1].x, ar); ar = fmaf(-u.w, x[1].y, ar);
+                ai = fmaf(u.z, x[1].y, ai); ai = fmaf(u.w, x[1].x, ai);
+            } else {
+#pragma unroll
+                for (int c = 0; c < D; c += 2) {
+                    float4 u = row[c / 2];
+                    ar = fmaf(u.x, x[c].x, ar); ar = fmaf(-u.y, x[c].y, ar);
+                    ai = fmaf(u.x, x[c].y, ai); ai = fmaf(u.y, x[c].x, ai);
+                    ar = fmaf(u.z, x[c + 1].x, ar); ar = fmaf(-u.w, x[c + 1].y, ar);
+                    ai = fmaf(u.z, x[c + 1].y, ai); ai = fmaf(u.w, x[c + 1].x, ai);
+                }
+            }
+            tile[swz(b | S.offs[r])] = make_float2(ar, ai);
+        }
+    }
+}
+
+template <int NT>
+__device__ __forceinline__ void apply_dense_k1(float2 *tile, const float2 *U, const PassSmem &S, uint32_t T) {
+    const uint32_t ngroups = 1u << (T - 1);
+    const uint32_t nc = T - 1;
+    const float2 u00 = U[0], u01 = U[1], u10 = U[2], u11 = U[3];
+    for (uint32_t g = threadIdx.x; g < ngroups; g += NT) {
+        uint32_t b = 0;
+        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.op.comp[t];
+        const uint32_t i0 = swz(b), i1 = swz(b | S.offs[1]);
+        const float2 x0 = tile[i0], x1 = tile[i1];
+        tile[i0] = make_float2(u00.x * x0.x - u00.y * x0.y + u01.x * x1.x - u01.y * x1.y,
+                               u00.x * x0.y + u00.y * x0.x + u01.x * x1.y + u01.y * x1.x);
+        tile[i1] = make_float2(u10.x * x0.x - u10.y * x0.y + u11.x * x1.x - u11.y * x1.y,
+                               u10.x * x0.y + u10.y * x0.x + u11.x * x1.y + u11.y * x1.x);
+    }
+}
+
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+    asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+
+
+// ---------------------------------------------------------------------------
+// Tensor-core dense ops (warp-level MMA). A dense k-qubit op on the tile is the
+// real GEMM  Y^T (G x 2D) = X^T (G x 2D) * U_r^T (2D x 2D), D = 2^k, G = 2^(T-k)
+// index groups, with U_r = [[Re U, -Im U], [Im U, Re U]] acting on
+// (re_0..re_{D-1}, im_0..im_{D-1}). Each warp owns G/4 rows (groups): it reads
+// its rows' inputs from the tile into A fragments, accumulates in FP32 and
+// writes its rows' outputs back in place (no other warp touches those rows).
+// TF32: one m16n8k8 MMA per fragment. BF16x3: x = hi + mid + lo (BF16 each),
+// the six products of order <= 2 (hi*hi, hi*mid, mid*hi, hi*lo, lo*hi,
+// mid*mid) with m16n8k16, all into the same FP32 accumulators.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t f32_to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+__device__ __forceinline__ void mma_tf32(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4], const uint32_t (&b)[2]) {
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+        : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+}
+
+// three BF16 parts of x: hi = bf16(x), mid = bf16(x - hi), lo = bf16(x - hi - mid)
+__device__ __forceinline__ void split3(float x, __nv_bfloat16 &h, __nv_bfloat16 &m, __nv_bfloat16 &l) {
+    h = __float2bfloat16_rn(x);
+    const float r1 = x - __bfloat162float(h);
+    m = __float2bfloat16_rn(r1);
+    l = __float2bfloat16_rn(r1 - __bfloat162float(m));
+}
+
+__device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo_half, __nv_bfloat16 hi_half) {
+    return uint32_t(__bfloat16_as_ushort(lo_half)) | (uint32_t(__bfloat16_as_ushort(hi_half)) << 16);
+}
+
+// real input kk of the op for the group whose tile base index is b
+__device__ __forceinline__ float xin(const float2 *tile, uint32_t b, const uint32_t *offs, uint32_t kk, uint32_t D) {
+    const float2 v = tile[swz(b | offs[kk < D ? kk : kk - D])];
+    return kk < D ? v.x : v.y;
+}
+
+// U_r^T[kk][n] = U_r[n][kk]
+__device__ __forceinline__ float uin(const float2 *U, uint32_t n, uint32_t kk, uint32_t D) {
+    const float2 u = U[(n < D ? n : n - D) * D + (kk < D ? kk : kk - D)];
+    if (n < D) return kk < D ? u.x : -u.y;
+    return kk < D ? u.y : u.x;
+}
+
+template <int NT, int K, int PREC>
+__device__ __forceinline__ void apply_dense_mma(float2 *tile, const float2 *U, const PassSmem &S, uint32_t T) {
+    constexpr uint32_t D = 1u << K, N2 = 2 * D;
+    const uint32_t G = 1u << (T - K);              // rows
+    const uint32_t rows_per_warp = G / (NT / 32);
+    const uint32_t MT = rows_per_warp / 16;        // m16 tiles per warp
+    constexpr uint32_t NTILES = N2 / 8;             // n8 tiles
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t gq = lane >> 2, tq = lane & 3;
+    const uint32_t nc = T - K;
+    // this warp's rows: row0 + mt*16 + {gq, gq+8}
+    const uint32_t row0 = warp * rows_per_warp;
+    constexpr uint32_t MT_MAX = 8;
+    uint32_t base[MT_MAX][2];
+#pragma unroll
+    for (uint32_t mt = 0; mt < MT_MAX; ++mt) {
+        if (mt >= MT) break;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const uint32_t g = row0 + mt * 16 + gq + 8 * h;
+            uint32_t b = 0;
+            for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.op.comp[t];
+            base[mt][h] = b;
+        }
+    }
+    // accumulators: MT x NTILES x 4, MT * NTILES == 16 for T = 12
+    float acc[16][4];
+#pragma unroll
+    for (int i = 0; i < 16; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    const uint32_t *offs = S.offs;
+    if constexpr (PREC == QSIM_PREC_TF32) {
+        for (uint32_t k0 = 0; k0 < N2; k0 += 8) {
+            uint32_t bfr[NTILES][2];
+#pragma unroll
+            for (uint32_t nt = 0; nt < NTILES; ++nt) {
+                bfr[nt][0] = f32_to_tf32(uin(U, nt * 8 + gq, k0 + tq, D));
+                bfr[nt][1] = f32_to_tf32(uin(U, nt * 8 + gq, k0 + tq + 4, D));
+            }
+#pragma unroll
+            for (uint32_t mt = 0; mt < MT_MAX; ++mt) {
+                if (mt >= MT) break;
+                uint32_t a[4];
+                a[0] = f32_to_tf32(xin(tile, base[mt][0], offs, k0 + tq, D));
+                a[1] = f32_to_tf32(xin(tile, base[mt][1], offs, k0 + tq, D));
+                a[2] = f32_to_tf32(xin(tile, base[mt][0], offs, k0 + tq + 4, D));
+                a[3] = f32_to_tf32(xin(tile, base[mt][1], offs, k0 + tq + 4, D));
+#pragma unroll
+                for (uint32_t nt = 0; nt < NTILES; ++nt) mma_tf32(acc[(mt * NTILES + nt) & 15], a, bfr[nt]);
+            }
+        }
+    } else {
+        for (uint32_t k0 = 0; k0 < N2; k0 += 16) {
+            uint32_t bh[NTILES][2], bm[NTILES][2], bl[NTILES][2];
+#pragma unroll
+            for (uint32_t nt = 0; nt < NTILES; ++nt) {
+#pragma unroll
+                for (int r = 0; r < 2; ++r) {
+                    __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+                    split3(uin(U, nt * 8 + gq, k0 + 2 * tq + 8 * r, D), h0, m0, l0);
+                    split3(uin(U, nt * 8 + gq, k0 + 2 * tq + 1 + 8 * r, D), h1, m1, l1);
+                    bh[nt][r] = pack_bf16(h0, h1);
+                    bm[nt][r] = pack_bf16(m0, m1);
+                    bl[nt][r] = pack_bf16(l0, l1);
+                }
+            }
+#pragma unroll
+            for (uint32_t mt = 0; mt < MT_MAX; ++mt) {
+                if (mt >= MT) break;
+                uint32_t ah[4], am[4], al[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const uint32_t b = base[mt][q & 1];
+                    const uint32_t col = k0 + 2 * tq + 8 * (q >> 1);
+                    __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+                    split3(xin(tile, b, offs, col, D), h0, m0, l0);
+                    split3(xin(tile, b, offs, col + 1, D), h1, m1, l1);
+                    ah[q] = pack_bf16(h0, h1);
+                    am[q] = pack_bf16(m0, m1);
+                    al[q] = pack_bf16(l0, l1);
+                }
+#pragma unroll
+                for (uint32_t nt = 0; nt < NTILES; ++nt) {
+                    float (&c)[4] = acc[(mt * NTILES + nt) & 15];
+                    mma_bf16(c, al, bh[nt]);
+                    mma_bf16(c, ah, bl[nt]);
+                    mma_bf16(c, am, bm[nt]);
+                    mma_bf16(c, am, bh[nt]);
+                    mma_bf16(c, ah, bm[nt]);
+                    mma_bf16(c, ah, bh[nt]);
+                }
+            }
+        }
+    }
+    __syncwarp();
+    // outputs: tile j < NTILES/2 holds re of outputs 8j + 2tq (+1), tile j + NTILES/2 the im parts
+#pragma unroll
+    for (uint32_t mt = 0; mt < MT_MAX; ++mt) {
+        if (mt >= MT) break;
+#pragma unroll
+        for (uint32_t j = 0; j < NTILES / 2; ++j) {
+            const float (&re)[4] = acc[(mt * NTILES + j) & 15];
+            const float (&im)[4] = acc[(mt * NTILES + j + NTILES / 2) & 15];
+            const uint32_t r0 = 8 * j + 2 * tq;
+            tile[swz(base[mt][0] | offs[r0])] = make_float2(re[0], im[0]);
+            tile[swz(base[mt][0] | offs[r0 + 1])] = make_float2(re[1], im[1]);
+            tile[swz(base[mt][1] | offs[r0])] = make_float2(re[2], im[2]);
+            tile[swz(base[mt][1] | offs[r0 + 1])] = make_float2(re[3], im[3]);
+        }
+    }
+}
+
+// Dense op of width k (<= KMAX) on the shared-memory tile; the tensor-core
+// form needs 4096-amplitude tiles and at least 16 index groups per warp.
+template <int NT, int KMAX, int PREC>
+__device__ __forceinline__ void apply_dense_dispatch(uint32_t k, float2 *tile, const float2 *mat, const PassSmem &S,
+                                                     uint32_t T) {
+    constexpr bool TC = PREC != QSIM_PREC_FP32;
+    const bool tc_ok = TC && T == 12 && ((1u << (T - k)) / (NT / 32)) >= 16;
+    switch (k) {
+        case 1: apply_dense_k1<NT>(tile, mat, S, T); break;
+        case 2: if constexpr (KMAX >= 2) apply_dense<NT, 2>(tile, mat, S, T); break;
+        case 3:
+            if constexpr (KMAX >= 3) {
+                if (tc_ok) apply_dense_mma<NT, 3, PREC>(tile, mat, S, T);
+                else apply_dense<NT, 3>(tile, mat, S, T);
+            }
+            break;
+        case 4:
+            if constexpr (KMAX >= 4) {
+                if (tc_ok) apply_dense_mma<NT, 4, PREC>(tile, mat, S, T);
+                else apply_dense<NT, 4>(tile, mat, S, T);
+            }
+            break;
+        case 5:
+            if constexpr (KMAX >= 5) {
+                if (tc_ok) apply_dense_mma<NT, 5, PREC>(tile, mat, S, T);
+                else apply_dense<NT, 5>(tile, mat, S, T);
+            }
+            break;
+        default:
+            if constexpr (KMAX >= 6) {
+                if (tc_ok) apply_dense_mma<NT, 6, PREC>(tile, mat, S, T);
+                else apply_dense<NT, 6>(tile, mat, S, T);
+            }
+            break;
+    }
+}
+
+// One tile of one pass: stage the 2^T amplitudes of tile `cta` of the group's
+// working vector g in shared memory, apply the pass's ops, store them back.
+// CG selects L2-only loads, needed when the working vector was written by
+// other CTAs of the same launch (the persistent stage kernel).
+template <int NT, int KMAX, int PREC, bool CG>
+__device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev *__restrict__ pd,
+                                          const OpDev *__restrict__ ops, const float2 *__restrict__ mats,
+                                          uint64_t cta, uint64_t gb, PassSmem &S, float2 *tile) {
+    const int tid = threadIdx.x;
+    if (tid == 0) S.p = *pd;
+    __syncthreads();
+    const uint32_t T = S.p.T, L = S.p.L, nout = S.p.nout;
+    float2 *mat = tile + (1u << T);
+    const uint32_t nhi = 1u << (T - L);
+    for (uint32_t h = tid; h < nhi; h += NT) {
+        uint32_t o = 0;
+        for (uint32_t t = 0; t < T - L; ++t) o |= ((h >> t) & 1u) << S.p.tile_pos[L + t];
+        S.hi[h] = o;
+    }
+    uint64_t base = 0;
+    for (uint32_t t = 0; t < nout; ++t) base |= ((cta >> t) & 1ull) << S.p.out_pos[t];
+    const uint32_t lmask = (1u << L) - 1;
+    __syncthreads();
+    if constexpr (CG) {
+        // batches of eight L2 loads in flight per thread, then the shared-memory stores
+        for (uint32_t i0 = tid; i0 < (1u << T); i0 += 8 * NT) {
+            float2 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t i = i0 + u * NT;
+                if (i < (1u << T)) v[u] = __ldcg(&g[base | (i & lmask) | S.hi[i >> L]]);
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const uint32_t i = i0 + u * NT;
+                if (i < (1u << T)) tile[swz(i)] = v[u];
+            }
+        }
+    } else {
+        for (uint32_t i = tid; i < (1u << T); i += NT) cp_async8(&tile[swz(i)], &g[base | (i & lmask) | S.hi[i >> L]]);
+        cp_async_wait_all();
+    }
+    for (uint32_t oi = 0; oi < S.p.op_count; ++oi) {
+        __syncthreads();
+        if (tid == 0) S.op = ops[S.p.op_begin + oi];
+        __syncthreads();
+        const uint32_t type = S.op.type, k = S.op.k;
+        if (type == OP_DENSE) {
+            const uint32_t D = 1u << k;
+            for (uint32_t i = tid; i < D * D; i += NT) mat[i] = mats[S.op.mat + i];
+            if (tid < int(D)) {
+                uint32_t o = 0;
+                for (uint32_t j = 0; j < k; ++j) o |= ((uint32_t(tid) >> j) & 1u) << S.op.tq[j];
+                S.offs[tid] = o;
+            }
+            __syncthreads();
+            if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, mat, S, T);
+        } else if (type == OP_DIAG) {
+            const uint32_t D = 1u << k;
+            for (uint32_t i = tid; i < D; i += NT) mat[i] = mats[S.op.mat + i];
+            __syncthreads();
+            for (uint32_t i = tid; i < (1u << T); i += NT) {
+                const uint64_t w = base | (i & lmask) | S.hi[i >> L];
+                uint32_t idx = 0;
+                for (uint32_t j = 0; j < k; ++j) {
+                    const uint32_t src = S.op.dsrc[j];
+                    const uint64_t bit = src < 64 ? (w >> src) & 1ull : (gb >> (src - 64)) & 1ull;
+                    idx |= uint32_t(bit) << j;
+                }
+                const float2 ph = mat[idx];
+                float2 &a = tile[swz(i)];
+                const float2 v = a;
+                a = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
+            }
+        } else {
+            if (tid == 0 && S.op.basis_in_stage && gb == S.op.basis_outer &&
+                (S.op.basis_w & S.p.out_mask) == base) {
+                uint32_t ti = 0;
+                for (uint32_t t = 0; t < T; ++t) ti |= uint32_t((S.op.basis_w >> S.p.tile_pos[t]) & 1ull) << t;
+                float2 &a = tile[swz(ti)];
+                a = make_float2(-a.x, -a.y);
+            }
+        }
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < (1u << T); i += NT) g[base | (i & lmask) | S.hi[i >> L]] = tile[swz(i)];
+}
+
+}  // namespace gdev
+}  // namespace qsim

@@ -32,25 +32,6 @@ constexpr int OW1 = 0, OB1 = OW1 + HID * IN, OW2 = OB1 + HID, OB2 = OW2 + HID * 
 
 __device__ __forceinline__ float round_bf16(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
 
-// forward of one sample with weights in shared memory
-__device__ __forceinline__ float mlp_forward_one(const float *w, const float *x) {
-    float h1[HID];
-#pragma unroll 4
-    for (int i = 0; i < HID; ++i) {
-        float a = w[OB1 + i];
-        for (int j = 0; j < IN; ++j) a = fmaf(w[OW1 + i * IN + j], x[j], a);
-        h1[i] = fmaxf(a, 0.f);
-    }
-    float y = w[OB3];
-    for (int i = 0; i < HID; ++i) {
-        float a = w[OB2 + i];
-#pragma unroll
-        for (int j = 0; j < HID; ++j) a = fmaf(w[OW2 + i * HID + j], h1[j], a);
-        y = fmaf(w[OW3 + i], fmaxf(a, 0.f), y);
-    }
-    return y;
-}
-
 __device__ __forceinline__ void load_weights(float *w, const float *params, bool bf16) {
     for (int i = threadIdx.x; i < NP; i += blockDim.x) w[i] = bf16 ? round_bf16(params[i]) : params[i];
 }
@@ -77,19 +58,9 @@ __global__ void k_predict_sizes(const uint32_t *__restrict__ hist, uint32_t nblo
     if (params) load_weights(w, params, bf16 != 0);
     __syncthreads();
     // a stage mixes the G blocks of an SV group, so the histogram is the group's
-    const float inv = 1.0f / (float(G) * float(2ull << m));
     for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nblocks; j += gridDim.x * blockDim.x) {
         float x[IN];
-        int maxb = 0;
-        const uint64_t g0 = uint64_t(j / G) * G;
-        for (int b = 0; b < 32; ++b) {
-            uint32_t c = 0;
-            for (uint32_t jj = 0; jj < G; ++jj) c += hist[(g0 + jj) * 32 + b];
-            x[b] = float(c) * inv;
-            if (c) maxb = b;
-        }
-        x[32] = float(maxb) / 32.f;
-        for (int t = 0; t < 8; ++t) x[33 + t] = sf.v[t];
+        mlp_features(hist, j, G, m, sf, x);
         if (feat_out)
             for (int t = 0; t < IN; ++t) feat_out[uint64_t(j) * (IN + 1) + t] = x[t];
         if (params && pred) pred[j] = mlp_forward_one(w, x) + float(m + 3);

@@ -1,0 +1,305 @@
+// Persistent stage kernel (sm_103a): one launch runs a whole stage.
+//
+// The paper overlaps the SV groups of a stage by dealing them round-robin to
+// CUDA streams (Sec. 4.2). Here the same overlap happens inside one launch:
+// every CTA repeatedly takes the next work item from a global queue, whose
+// order is, group after group, the group's phases
+//     decode frames -> [predict + reserve] -> gate-pass tiles (pass by pass)
+//     -> [sizing frames] -> encode frames -> [exact re-reserve -> re-encode]
+// and waits (bounded spin) until the group's previous phase is complete
+// before running its item. Groups are independent (Sec. 4.1), so different
+// CTAs work on different phases of different groups at the same time, and a
+// group's work item only waits on items that come earlier in the queue, which
+// were taken by CTAs that are already running: the schedule cannot deadlock
+// even when not every CTA is resident. Working vectors rotate over R slots;
+// the first item of group g also waits for group g - R to finish.
+//
+// Data produced by other CTAs of the same launch is read through L2 (ld.cg),
+// since the per-SM L1 caches are not coherent within a launch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "codec.cuh"
+#include "codec_dev.cuh"
+#include "device_common.cuh"
+#include "gates.cuh"
+#include "gates_dev.cuh"
+#include "mlp.cuh"
+#include "persistent.cuh"
+
+namespace qsim {
+
+namespace {
+
+using cdev::FrameGeom;
+using cdev::geom;
+
+constexpr int PT = 256;  // threads per CTA
+
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__device__ __forceinline__ EncTarget load_target(const EncTarget *t) {
+    EncTarget r;
+    r.ptr = reinterpret_cast<uint8_t *>(__ldcg(reinterpret_cast<const unsigned long long *>(&t->ptr)));
+    r.cap = __ldcg(reinterpret_cast<const unsigned long long *>(&t->cap));
+    r.tier = __ldcg(&t->tier);
+    r.pad = 0;
+    return r;
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(PT, 2) k_stage_persistent(PStageArgs A) {
+    extern __shared__ float4 dsm[];
+    __shared__ gdev::PassSmem PS;
+    __shared__ cdev::EncSmem SE;
+    __shared__ OpDev s_pre[kMaxPreOps];
+    __shared__ uint32_t s_hist[PT / 32][32];
+    __shared__ uint32_t s_words[PT / 32];
+    __shared__ uint32_t s_item, s_epoch;
+    __shared__ int s_flag;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid < int(A.npre)) s_pre[tid] = A.ops[A.pre_begin + tid];
+    if (tid == 0) s_epoch = ld_relaxed_u32(A.ctr + 2) & cdev::kEpochMask;
+    __syncthreads();
+    const FrameGeom g = geom(int(A.m));
+    const uint32_t nph = A.nphases;
+    const uint64_t total = uint64_t(A.ngroups) * A.per_group;
+    const uint32_t gframes = A.G * g.nframes;
+
+    while (true) {
+        if (tid == 0) s_item = atomicAdd(A.ctr, 1u);
+        __syncthreads();
+        const uint32_t item = s_item;
+        if (item >= total) break;
+        const uint32_t grp = item / A.per_group, r = item % A.per_group;
+        uint32_t p = 0;
+        while (p + 1 < nph && r >= A.ph_start[p + 1]) ++p;
+        const uint32_t i = r - A.ph_start[p];
+        const uint32_t type = A.ph[p].type;
+        // ---- dependency: the group's previous phase, or the slot's previous group ----
+        if (tid == 0) {
+            const uint32_t *flag = nullptr;
+            uint32_t need = 0;
+            if (p > 0) {
+                flag = A.done + uint64_t(grp) * nph + p - 1;
+                need = A.ph[p - 1].count;
+            } else if (grp >= A.R) {
+                flag = A.done + uint64_t(grp - A.R) * nph + nph - 1;
+                need = A.ph[nph - 1].count;
+            }
+            if (A.stall_test && grp == 0 && p == 1) ++need;  // never reached: exercises the time limit
+            if (flag) {
+                const uint64_t t0 = global_ns();
+                while (ld_acquire_u32(flag) < need) {
+                    if (global_ns() - t0 > A.wait_ns) {
+                        raise_status(A.status, QSIM_E_TIMEOUT);
+                        break;
+                    }
+                    __nanosleep(256);
+                }
+            }
+            // after any device error the remaining items only keep the schedule going
+            s_flag = ld_relaxed_u32(reinterpret_cast<const uint32_t *>(A.status)) != 0;
+        }
+        __syncthreads();
+        const bool abort_item = s_flag != 0;
+        __syncthreads();
+        const uint32_t slot = grp % A.R;
+        float2 *wv = A.wv + ((uint64_t(slot) * A.G) << A.m);
+        const uint32_t *ids = A.ids + uint64_t(grp) * A.G;
+        const uint64_t gb = A.gbase[grp];
+        const uint64_t bbase = uint64_t(grp) * A.G;  // per-group block arrays
+        bool by_arrival = type == PH_SIZE || type == PH_ENCODE;
+        if (abort_item) {
+            // skip the work, keep the counts
+        } else if (type == PH_DECODE) {
+            const uint32_t fi = i * (PT / 32) + warp;
+            if (fi < gframes) {
+                const uint32_t jj = fi / g.nframes, f = fi % g.nframes;
+                const BlockSlot sl = A.tab_in[ids[jj]];
+                cdev::decode_frame_warp(sl.ptr, sl.bytes, g, int(A.m), f, wv + (uint64_t(jj) << A.m) + uint64_t(f) * g.F,
+                                        A.hist ? A.hist + (bbase + jj) * 32 : nullptr, s_hist[warp], A.status, s_pre,
+                                        A.npre, A.mats, uint64_t(jj) << A.m, gb);
+            }
+        } else if (type == PH_PASS) {
+            gdev::pass_tile<PT, 5, PREC, true>(wv, A.passes + A.ph[p].arg, A.ops, A.mats, i, gb, PS,
+                                               reinterpret_cast<float2 *>(dsm));
+        } else if (type == PH_SIZE) {
+            const uint32_t jj = i / g.nframes, f = i % g.nframes;
+            const uint32_t len = cdev::size_frame_cta<true>(wv + (uint64_t(jj) << A.m) + uint64_t(f) * g.F, g, A.e,
+                                                            s_words, A.status);
+            if (tid == 0 && len) atomicAdd(reinterpret_cast<unsigned long long *>(&A.sizes[bbase + jj]), uint64_t(len));
+        } else if (type == PH_PREDICT) {
+            float *w = reinterpret_cast<float *>(dsm);
+            for (int t = tid; t < kMlpParams; t += PT) {
+                const float v = A.pparams[t];
+                w[t] = A.pbf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
+            }
+            __syncthreads();
+            for (uint32_t jj = tid; jj < A.G; jj += PT) {
+                float x[kMlpIn];
+                mlp_features(A.hist + bbase * 32, jj, A.G, int(A.m), A.sf, x);
+                double pr = double(mlp_forward_one(w, x)) + double(A.m + 3);
+                pr = pr < 0 ? 0 : (pr > 40 ? 40 : pr);
+                const double want = exp2(pr) * (1.0 + A.margin);
+                EncResult &rs = A.res[bbase + jj];
+                rs.total = 0;
+                rs.overflow = 0;
+                rs.err_sq = 0;
+                rs.norm_sq = 0;
+                cdev::reserve_slot(want >= double(A.worst) ? A.worst : uint64_t(want), A.dev, A.host,
+                                   &A.tgt[bbase + jj], A.status);
+            }
+        } else if (type == PH_ENCODE || type == PH_REENCODE) {
+            const uint32_t jj = i / g.nframes, f = i % g.nframes;
+            const bool retry = type == PH_REENCODE;
+            if (tid == 0) s_flag = retry ? int(__ldcg(&A.res[bbase + jj].overflow) != 0) : 1;
+            __syncthreads();
+            if (s_flag) {
+                const uint32_t epoch = (s_epoch + 2 * grp + (retry ? 1 : 0)) & cdev::kEpochMask;
+                cdev::encode_frame_cta<true>(wv + (uint64_t(jj) << A.m) + uint64_t(f) * g.F, g, int(A.m), A.e, f,
+                                             A.lb + (uint64_t(slot) * A.G + jj) * g.nframes, epoch,
+                                             load_target(&A.tgt[bbase + jj]), &A.res[bbase + jj], A.tab_out + ids[jj],
+                                             A.acc, retry ? nullptr : A.part + (uint64_t(slot) * A.G + jj) * g.nframes + f,
+                                             retry ? 1 : 0, reinterpret_cast<uint32_t *>(dsm), SE, A.status);
+            }
+        } else if (type == PH_FIX) {
+            for (uint32_t jj = tid; jj < A.G; jj += PT) {
+                EncResult &rs = A.res[bbase + jj];
+                if (__ldcg(&rs.overflow))
+                    cdev::reserve_slot(__ldcg(reinterpret_cast<const unsigned long long *>(&rs.total)), A.dev, A.host,
+                                       &A.tgt[bbase + jj], A.status);
+            }
+        }
+        // ---- completion ----
+        __syncthreads();
+        uint32_t *done = A.done + uint64_t(grp) * nph + p;
+        if (!by_arrival) {
+            if (tid == 0) {
+                __threadfence();
+                atomicAdd(done, 1u);
+            }
+            continue;
+        }
+        if (tid == 0) {
+            __threadfence();
+            s_flag = atomicAdd(A.arrive + uint64_t(grp) * nph + p, 1u) == A.ph[p].count - 1;
+        }
+        __syncthreads();
+        if (!s_flag) continue;
+        __threadfence();
+        if (abort_item) {
+            // no reservation or statistics after an error
+        } else if (type == PH_SIZE) {
+            // the group's exact sizes are complete: reserve its slots
+            for (uint32_t jj = tid; jj < A.G; jj += PT) {
+                const uint64_t want = atomicAdd(reinterpret_cast<unsigned long long *>(&A.sizes[bbase + jj]), 0ull) +
+                                      A.data_start;
+                EncResult &rs = A.res[bbase + jj];
+                rs.total = 0;
+                rs.overflow = 0;
+                rs.err_sq = 0;
+                rs.norm_sq = 0;
+                cdev::reserve_slot(want, A.dev, A.host, &A.tgt[bbase + jj], A.status);
+            }
+        } else {
+            // the group's frames are encoded: fold their error partials into the stage totals
+            double a = 0, b = 0;
+            for (uint32_t t = tid; t < gframes; t += PT) {
+                const float2 v = __ldcg(A.part + uint64_t(slot) * gframes + t);
+                a += double(v.x);
+                b += double(v.y);
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                a += __shfl_xor_sync(kFull, a, o);
+                b += __shfl_xor_sync(kFull, b, o);
+            }
+            if ((tid & 31) == 0) {
+                atomicAdd(&A.acc->err_sq, a);
+                atomicAdd(&A.acc->norm_sq, b);
+            }
+        }
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicExch(done, A.ph[p].count);
+        }
+    }
+    // the last CTA out resets the queue and advances the look-back epoch
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(A.ctr + 1, 1u) == gridDim.x - 1) {
+            A.ctr[0] = 0;
+            A.ctr[1] = 0;
+            __threadfence();
+            atomicExch(A.ctr + 2, (s_epoch + 2 * A.ngroups) & cdev::kEpochMask);
+        }
+    }
+}
+
+template <int PREC>
+struct LaunchShape {
+    static int grid;
+    static size_t attr_smem;
+};
+template <int PREC> int LaunchShape<PREC>::grid = 0;
+template <int PREC> size_t LaunchShape<PREC>::attr_smem = 0;
+
+// kernel attributes and the grid (one wave of resident CTAs); done outside any stream capture
+template <int PREC>
+int prepare_prec(size_t smem) {
+    if (LaunchShape<PREC>::attr_smem < smem) {
+        if (cudaFuncSetAttribute(k_stage_persistent<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
+            cudaSuccess)
+            return QSIM_E_CUDA;
+        LaunchShape<PREC>::attr_smem = smem;
+        LaunchShape<PREC>::grid = 0;
+    }
+    if (!LaunchShape<PREC>::grid) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_persistent<PREC>, PT, smem);
+        LaunchShape<PREC>::grid = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    return QSIM_OK;
+}
+
+template <int PREC>
+int launch_stage_prec(const PStageArgs &a, size_t smem, cudaStream_t s, int *grid_out) {
+    if (LaunchShape<PREC>::attr_smem < smem || !LaunchShape<PREC>::grid) return QSIM_E_INVALID;
+    const int grid = LaunchShape<PREC>::grid;
+    k_stage_persistent<PREC><<<grid, PT, smem, s>>>(a);
+    if (grid_out) *grid_out = grid;
+    count_launch();
+    return QSIM_OK;
+}
+
+}  // namespace
+
+size_t persistent_smem_bytes(uint32_t T, uint32_t mat_elems) {
+    size_t pass = (size_t(1) << T) * sizeof(float2) + size_t(mat_elems) * sizeof(float2);
+    size_t enc = size_t(cdev::kStageWords) * sizeof(uint32_t);
+    size_t mlp = size_t(kMlpParams) * sizeof(float);
+    size_t m = pass > enc ? pass : enc;
+    return m > mlp ? m : mlp;
+}
+
+int prepare_stage_persistent(int prec, size_t smem) {
+    if (prec == QSIM_PREC_TF32) return prepare_prec<QSIM_PREC_TF32>(smem);
+    if (prec == QSIM_PREC_BF16X3) return prepare_prec<QSIM_PREC_BF16X3>(smem);
+    return prepare_prec<QSIM_PREC_FP32>(smem);
+}
+
+int launch_stage_persistent(const PStageArgs &a, int prec, size_t smem, cudaStream_t s, int *grid) {
+    if (prec == QSIM_PREC_TF32) return launch_stage_prec<QSIM_PREC_TF32>(a, smem, s, grid);
+    if (prec == QSIM_PREC_BF16X3) return launch_stage_prec<QSIM_PREC_BF16X3>(a, smem, s, grid);
+    return launch_stage_prec<QSIM_PREC_FP32>(a, smem, s, grid);
+}
+
+}  // namespace qsim
