@@ -61,12 +61,26 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0, help="budget of the CPU oracle sample")
     ap.add_argument("--no-profile", action="store_true")
+    ap.add_argument("--mode", default="streams", choices=["streams", "persistent"])
+    ap.add_argument("--graph", action="store_true", help="persistent mode: capture the stage loop in a CUDA graph")
+    ap.add_argument("--sizing", default="exact", choices=["exact", "predict"])
+    ap.add_argument("--margin", type=float, default=0.25, help="predictor reservation margin")
+    ap.add_argument("--workload", default="qft", choices=["qft", "qaoa", "random"],
+                    help="qft: QFT + 4 x (RZ, CX ladder) on n qubits; qaoa: MaxCut p=3 on a random 3-regular "
+                         "graph of n vertices; random: U3 + CZ brick of depth --depth")
+    ap.add_argument("--depth", type=int, default=14)
+    ap.add_argument("--cap-gib", type=float, default=0.0, help="device tier cap (pinned host holds the rest)")
     return ap.parse_args()
 
 
-def workload(args):
+def workload(args, seed=None):
     from paper_2410_14088_gb300 import inputs
-    return inputs.qft_rz_cx(args.n, 4, args.seed)
+    seed = args.seed if seed is None else seed
+    if args.workload == "qaoa":
+        return inputs.qaoa_maxcut(args.n, 3, seed)
+    if args.workload == "random":
+        return inputs.random_brick(args.n, args.depth, seed)
+    return inputs.qft_rz_cx(args.n, 4, seed)
 
 
 def load_peaks():
@@ -219,11 +233,16 @@ def run_reference(args, rank, world):
 
 
 def config_dict(args):
-    return {"workload": f"qft{args.n}+4x(rz,cx-ladder), m={args.m}, inner={args.inner}, k={args.k}, "
-                        f"eps={args.eps:g}, prec={args.prec}",
-            "n_qubits": args.n, "gates": 626 if args.n == 28 else None, "block_log2": args.m, "inner": args.inner,
-            "k": args.k, "eps": args.eps, "prec": args.prec, "streams": args.streams,
-            "l2_policy": "working set (2 GiB state, ~1 GB compressed) > L2 (129 MB); no flush"}
+    name = {"qft": f"qft{args.n}+4x(rz,cx-ladder)", "qaoa": f"qaoa-maxcut p=3, 3-regular n={args.n}",
+            "random": f"random u3+cz brick n={args.n} depth={args.depth}"}[args.workload]
+    raw = 8 << args.n
+    return {"workload": f"{name}, m={args.m}, inner={args.inner}, k={args.k}, eps={args.eps:g}, prec={args.prec}, "
+                        f"mode={args.mode}{'+graph' if args.graph else ''}, sizing={args.sizing}",
+            "n_qubits": args.n, "gates": len(workload(args).gates), "block_log2": args.m, "inner": args.inner,
+            "k": args.k, "eps": args.eps, "prec": args.prec, "streams": args.streams, "mode": args.mode,
+            "graph": bool(args.graph), "sizing": args.sizing, "device_tier_cap_gib": args.cap_gib,
+            "l2_policy": f"working set ({raw / 2**30:.3g} GiB state, compressed ~{raw / 2.8 / 2**30:.2g} GiB) "
+                         f"> L2 (129 MB); no flush"}
 
 
 # --------------------------------------------------------------------------
@@ -241,7 +260,26 @@ def run_ours(args, rank, world, dist):
     circ = workload(args)
     G = len(circ.gates)
     n = circ.n
-    kw = dict(m=args.m, inner=args.inner, k=args.k, eps=args.eps, prec=prec, streams=args.streams)
+    kw = dict(m=args.m, inner=args.inner, k=args.k, eps=args.eps, prec=prec, streams=args.streams,
+              mode=qsim.MODE_PERSISTENT if args.mode == "persistent" else qsim.MODE_STREAMS,
+              graph=1 if args.graph else 0,
+              sizing=qsim.SIZING_PREDICT if args.sizing == "predict" else qsim.SIZING_EXACT,
+              predictor_margin=args.margin,
+              device_tier_cap_bytes=int(args.cap_gib * (1 << 30)))
+    train_info = None
+    if args.sizing == "predict":
+        # training rows from exact-sizing runs of training seeds (100+) of the same family, not timed
+        import numpy as np
+        t0 = time.perf_counter()
+        rows = []
+        tkw = dict(kw, mode=qsim.MODE_STREAMS, sizing=qsim.SIZING_EXACT, graph=0)
+        for sd in (100, 101):
+            st = qsim.run(qsim.plan_stages(workload(args, sd), collect=1, **tkw))
+            rows.append(st.training_data())
+            del st
+        rows = np.concatenate(rows)
+        loss = qsim.predictor_train(rows, epochs=40, batch=64, lr=3e-3, seed=100)
+        train_info = {"rows": int(rows.shape[0]), "loss": loss, "seconds": time.perf_counter() - t0}
     plan = qsim.plan_stages(circ, **kw)
     stream = torch.cuda.current_stream()
 
@@ -332,7 +370,7 @@ def run_ours(args, rank, world, dist):
         gbps = d["alg_bytes"] / max(1e-12, d["seconds"]) / 1e9
         tflops = d["alg_flops"] / max(1e-12, d["seconds"]) / 1e12
         hbm_frac = gbps / peaks["hbm_gbs"]
-        if dom == "gate_pass" and args.prec == "fp32" and tflops / fp32_peak_tflops > hbm_frac:
+        if dom in ("gate_pass", "stage_persistent") and args.prec == "fp32" and tflops / fp32_peak_tflops > hbm_frac:
             roofline = {"kernel": dom, "bound": "alu", "achieved": tflops, "peak": fp32_peak_tflops,
                         "unit": "TFLOP/s", "frac": tflops / fp32_peak_tflops,
                         "peak_source": f"derived: {NUM_SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {sm_max:.0f} MHz",
@@ -352,6 +390,8 @@ def run_ours(args, rank, world, dist):
         "compression_ratio": cr, "compression_ratio_vs_complex128": 2 * cr,
         "fidelity_lower_bound": last["fidelity_lower_bound"], "norm_sq": last["norm_sq"],
         "stages": last["nstages"], "plan_seconds": plan.stats()["plan_seconds"],
+        "overflow_blocks": last["overflow_blocks"], "peak_reserved_bytes": last["peak_reserved_bytes"],
+        "host_tier_peak_bytes": last["host_tier_peak_bytes"], "predictor_training": train_info,
         "e2e": {"value": e2e, "unit": "updates/s", "h2d_bytes_per_step": h2d // args.steps,
                 "d2h_bytes_per_step": d2h // args.steps},
         "gpu_launches": launches,

@@ -53,6 +53,31 @@ __device__ __forceinline__ int32_t unzigzag(uint32_t z) {
 // ---------------------------------------------------------------------------
 // Decode: one CTA per frame (grid-stride over all frames of all blocks).
 // ---------------------------------------------------------------------------
+// The same for lane `lane` of a 32-amplitude chunk starting at working index
+// w0: the phase index splits into bits of w0 / the group (same for the chunk)
+// and bits 0..4 of the lane.
+__device__ __forceinline__ float2 apply_pre_ops_chunk(float2 v, uint64_t w0, uint32_t lane, uint64_t gb,
+                                                      const OpDev *ops, uint32_t nops, const float2 *__restrict__ mats) {
+    for (uint32_t o = 0; o < nops; ++o) {
+        const OpDev &op = ops[o];
+        if (op.type == OP_DIAG) {
+            uint32_t idx = 0;
+            for (uint32_t j = 0; j < op.k; ++j) {
+                const uint32_t src = op.dsrc[j];
+                uint32_t bit;
+                if (src < 5) bit = (lane >> src) & 1u;
+                else bit = uint32_t(src < 64 ? (w0 >> src) & 1ull : (gb >> (src - 64)) & 1ull);
+                idx |= bit << j;
+            }
+            const float2 ph = __ldg(mats + op.mat + idx);
+            v = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
+        } else if (op.basis_in_stage && gb == op.basis_outer && (w0 | lane) == op.basis_w) {
+            v = make_float2(-v.x, -v.y);
+        }
+    }
+    return v;
+}
+
 // Leading phase ops of a stage, applied to each decoded amplitude: w is the
 // amplitude's working index, gb the full-index bits of its group's outer qubits.
 __device__ __forceinline__ float2 apply_pre_ops(float2 v, uint64_t w, uint64_t gb, const OpDev *ops, uint32_t nops,
@@ -194,10 +219,7 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
             }
             const int32_t sr = int32_t(qr), si = int32_t(qi);
             float2 v = make_float2(float(sr) * step, float(si) * step);
-            if (npre) {
-                const uint64_t w = wbase | (uint64_t(f) * g.F + c * 32 + lane);
-                v = apply_pre_ops(v, w, gb, pre_ops, npre, mats);
-            }
+            if (npre) v = apply_pre_ops_chunk(v, wbase | (uint64_t(f) * g.F + c * 32), lane, gb, pre_ops, npre, mats);
             dst[c * 32 + lane] = v;
             if (hist_j) {
                 const uint32_t br = 32 - __clz(sr < 0 ? uint32_t(-sr) : uint32_t(sr));

@@ -309,6 +309,7 @@ struct PlanDev {
     DevBuf<PassDev> passes;
     DevBuf<OpDev> ops;
     DevBuf<float2> mats;
+    DevBuf<uint32_t> bfr;     // B-fragment tables of the dense ops (tensor-core precisions)
     DevBuf<uint32_t> ids;     // per stage: 2^c block ids, group-major
     DevBuf<uint64_t> gbase;   // per stage: per group outer bits
     std::vector<StageDev> stages;
@@ -358,6 +359,7 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
     std::vector<PassDev> passes;
     std::vector<OpDev> ops;
     std::vector<float2> mats;
+    std::vector<uint32_t> bfr;
     std::vector<uint32_t> ids;
     std::vector<uint64_t> gbases;
     for (const Stage &st : p->stages) {
@@ -390,6 +392,7 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
             OpDev od{};
             od.type = op.type;
             od.k = op.k;
+            for (int j = 0; j < 6; ++j) od.dtile[j] = 255;
             if (op.type == OP_DIAG) {
                 for (uint32_t j = 0; j < op.k; ++j) {
                     uint32_t q = op.fq[j];
@@ -451,10 +454,24 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                     od.mat = mats.size();
                     for (const cd &v : op.u) mats.push_back(make_float2(float(v.real()), float(v.imag())));
                     P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << (2 * op.k));
+                    if (p->cfg.prec != QSIM_PREC_FP32 && op.k >= 3 && op.k <= 5) {
+                        od.bfrag = bfr.size();
+                        bfr.resize(bfr.size() + bfrag_words(op.k, int(p->cfg.prec)));
+                        build_bfrag_table(reinterpret_cast<const double *>(op.u.data()), op.k, int(p->cfg.prec),
+                                          bfr.data() + od.bfrag);
+                    }
                     P.kmax = std::max<uint32_t>(P.kmax, op.k);
                 } else {
                     od = diag_opdev(op);
-                    if (op.type == OP_DIAG) P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << op.k);
+                    if (op.type == OP_DIAG) {
+                        P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << op.k);
+                        for (uint32_t j = 0; j < op.k; ++j) {
+                            od.dtile[j] = 255;
+                            if (od.dsrc[j] < 64)
+                                for (uint32_t t = 0; t < ps.T; ++t)
+                                    if (ps.tile_pos[t] == od.dsrc[j]) od.dtile[j] = t;
+                        }
+                    }
                 }
                 ops.push_back(od);
             }
@@ -465,9 +482,10 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
         pd->stages.push_back(std::move(sd));
     }
     if (mats.empty()) mats.push_back(make_float2(0, 0));
+    if (bfr.empty()) bfr.push_back(0);
     int rc;
     if ((rc = pd->passes.alloc(passes.size())) || (rc = pd->ops.alloc(ops.size())) ||
-        (rc = pd->mats.alloc(mats.size())) || (rc = pd->ids.alloc(ids.size())) ||
+        (rc = pd->mats.alloc(mats.size())) || (rc = pd->ids.alloc(ids.size())) || (rc = pd->bfr.alloc(bfr.size())) ||
         (rc = pd->gbase.alloc(gbases.size()))) {
         delete pd;
         return rc;
@@ -475,9 +493,11 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
     CUDA_TRY(cudaMemcpy(pd->passes.p, passes.data(), passes.size() * sizeof(PassDev), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pd->ops.p, ops.data(), ops.size() * sizeof(OpDev), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pd->mats.p, mats.data(), mats.size() * sizeof(float2), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pd->bfr.p, bfr.data(), bfr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pd->ids.p, ids.data(), ids.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pd->gbase.p, gbases.data(), gbases.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
     pd->upload_bytes = passes.size() * sizeof(PassDev) + ops.size() * sizeof(OpDev) + mats.size() * sizeof(float2) +
+                       bfr.size() * sizeof(uint32_t) +
                        ids.size() * sizeof(uint32_t) + gbases.size() * sizeof(uint64_t);
     pd->ready = true;
     if (it != g_plan_dev.end()) delete it->second;
@@ -762,6 +782,7 @@ static int run_stages_persistent(const qsim_plan *p, PlanDev *pd, cudaStream_t m
         a.passes = pd->passes.p + sd.pass_begin;
         a.ops = pd->ops.p;
         a.mats = pd->mats.p;
+        a.bfr = pd->bfr.p;
         a.ids = pd->ids.p + pd->ids_off[si];
         a.gbase = pd->gbase.p + pd->gbase_off[si];
         a.tab_in = tables + in_par * nblocks;
@@ -1074,7 +1095,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             for (uint32_t pi = 0; pi < sd.npasses; ++pi) {
                 prof.begin(P_PASS, w.s);
                 launch_pass(w.wv.p, sd.W, ng, &sd.passes_host[pi], pd->passes.p + sd.pass_begin + pi, pd->ops.p,
-                            pd->mats.p, gb_stage + g0, cfg.prec, w.s);
+                            pd->mats.p, pd->bfr.p, gb_stage + g0, cfg.prec, w.s);
                 prof.end(w.s);
             }
             if (raw) {

@@ -15,6 +15,7 @@
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "codec.cuh"
 #include "device_common.cuh"
@@ -29,56 +30,128 @@ using namespace gdev;
 constexpr int NT = 128;
 
 template <int KMAX, int PREC>
-__global__ void __launch_bounds__(NT, ((KMAX >= 6 || PREC != QSIM_PREC_FP32) ? 2 : 4))
+__global__ void __launch_bounds__(NT, (KMAX >= 6 ? 2 : 4))
     k_pass(float2 *__restrict__ wv, uint32_t W, const PassDev *__restrict__ pd, const OpDev *__restrict__ ops,
-           const float2 *__restrict__ mats, const uint64_t *__restrict__ gbase) {
+           const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr, const uint64_t *__restrict__ gbase) {
     extern __shared__ float4 dyn_smem[];
     __shared__ PassSmem S;
     float2 *g = wv + (uint64_t(blockIdx.y) << W);
     const uint64_t gb = gbase ? gbase[blockIdx.y] : 0ull;
-    pass_tile<NT, KMAX, PREC, false>(g, pd, ops, mats, blockIdx.x, gb, S, reinterpret_cast<float2 *>(dyn_smem));
+    pass_tile<NT, KMAX, PREC, false>(g, pd, ops, mats, bfr, blockIdx.x, gb, S, reinterpret_cast<float2 *>(dyn_smem));
 }
 
 template <int KMAX, int PREC>
 void launch_pass_k(dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W, const PassDev *pd,
-                   const OpDev *ops, const float2 *mats, const uint64_t *gbase) {
+                   const OpDev *ops, const float2 *mats, const uint32_t *bfr, const uint64_t *gbase) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_pass<KMAX, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    k_pass<KMAX, PREC><<<grid, NT, smem, s>>>(wv, W, pd, ops, mats, gbase);
+    k_pass<KMAX, PREC><<<grid, NT, smem, s>>>(wv, W, pd, ops, mats, bfr, gbase);
 }
 
 template <int PREC>
 void launch_pass_prec(uint32_t kmax, dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W,
-                      const PassDev *pd, const OpDev *ops, const float2 *mats, const uint64_t *gbase) {
+                      const PassDev *pd, const OpDev *ops, const float2 *mats, const uint32_t *bfr,
+                      const uint64_t *gbase) {
     switch (kmax) {
-        case 0: launch_pass_k<0, PREC>(grid, smem, s, wv, W, pd, ops, mats, gbase); break;
-        case 1: launch_pass_k<1, PREC>(grid, smem, s, wv, W, pd, ops, mats, gbase); break;
-        case 2: launch_pass_k<2, PREC>(grid, smem, s, wv, W, pd, ops, mats, gbase); break;
-        case 3: launch_pass_k<3, PREC>(grid, smem, s, wv, W, pd, ops, mats, gbase); break;
-        case 4: launch_pass_k<4, PREC>(grid, smem, s, wv, W, pd, ops, mats, gbase); break;
-        case 5: launch_pass_k<5, PREC>(grid, smem, s, wv, W, pd, ops, mats, gbase); break;
-        default: launch_pass_k<6, PREC>(grid, smem, s, wv, W, pd, ops, mats, gbase); break;
+        case 0: launch_pass_k<0, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
+        case 1: launch_pass_k<1, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
+        case 2: launch_pass_k<2, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
+        case 3: launch_pass_k<3, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
+        case 4: launch_pass_k<4, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
+        case 5: launch_pass_k<5, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
+        default: launch_pass_k<6, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
     }
 }
 
 }  // namespace
 
+// ---------------------------------------------------------------------------
+// host: B-fragment tables
+// ---------------------------------------------------------------------------
+static uint32_t f32_bits(float f) {
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+static float bits_f32(uint32_t u) {
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+// round to TF32 (10 explicit mantissa bits), nearest with ties away from zero
+static uint32_t to_tf32(float x) { return (f32_bits(x) + 0x1000u) & ~0x1FFFu; }
+// round to BF16, nearest even
+static uint16_t to_bf16(float x) {
+    const uint32_t u = f32_bits(x);
+    return uint16_t((u + 0x7FFFu + ((u >> 16) & 1u)) >> 16);
+}
+static float from_bf16(uint16_t h) { return bits_f32(uint32_t(h) << 16); }
+
+size_t bfrag_words(uint32_t k, int prec) {
+    const size_t n2 = size_t(2) << k;
+    return prec == QSIM_PREC_TF32 ? n2 * n2 : 3 * n2 * n2 / 2;
+}
+
+void build_bfrag_table(const double *u, uint32_t k, int prec, uint32_t *out) {
+    const uint32_t D = 1u << k, N2 = 2 * D, NTILES = N2 / 8;
+    // U_r^T[kk][n] = U_r[n][kk] as float
+    auto ur = [&](uint32_t n, uint32_t kk) -> float {
+        const uint32_t r = n % D, c = kk % D;
+        const double re = u[2 * (size_t(r) * D + c)], im = u[2 * (size_t(r) * D + c) + 1];
+        if (n < D) return float(kk < D ? re : -im);
+        return float(kk < D ? im : re);
+    };
+    if (prec == QSIM_PREC_TF32) {
+        const uint32_t KS = N2 / 8;
+        for (uint32_t ks = 0; ks < KS; ++ks)
+            for (uint32_t nt = 0; nt < NTILES; ++nt)
+                for (uint32_t lane = 0; lane < 32; ++lane) {
+                    const uint32_t g = lane / 4, t = lane % 4;
+                    uint32_t *o = out + ((size_t(ks) * NTILES + nt) * 32 + lane) * 2;
+                    o[0] = to_tf32(ur(nt * 8 + g, ks * 8 + t));
+                    o[1] = to_tf32(ur(nt * 8 + g, ks * 8 + t + 4));
+                }
+        return;
+    }
+    const uint32_t KS = N2 / 16;
+    const size_t part = size_t(KS) * NTILES * 32 * 2;
+    for (uint32_t ks = 0; ks < KS; ++ks)
+        for (uint32_t nt = 0; nt < NTILES; ++nt)
+            for (uint32_t lane = 0; lane < 32; ++lane) {
+                const uint32_t g = lane / 4, t = lane % 4;
+                for (int r = 0; r < 2; ++r) {
+                    uint16_t h[2], m[2], l[2];
+                    for (int q = 0; q < 2; ++q) {
+                        const float x = ur(nt * 8 + g, ks * 16 + 2 * t + q + 8 * r);
+                        h[q] = to_bf16(x);
+                        const float r1 = x - from_bf16(h[q]);
+                        m[q] = to_bf16(r1);
+                        l[q] = to_bf16(r1 - from_bf16(m[q]));
+                    }
+                    const size_t e = ((size_t(ks) * NTILES + nt) * 32 + lane) * 2 + r;
+                    out[e] = uint32_t(h[0]) | (uint32_t(h[1]) << 16);
+                    out[part + e] = uint32_t(m[0]) | (uint32_t(m[1]) << 16);
+                    out[2 * part + e] = uint32_t(l[0]) | (uint32_t(l[1]) << 16);
+                }
+            }
+}
+
 void launch_pass(float2 *wv, uint32_t W, uint32_t ngroups, const PassDev *pass_host, const PassDev *pass_dev,
-                 const OpDev *ops_dev, const float2 *mats_dev, const uint64_t *gbase_dev, int prec,
-                 cudaStream_t s) {
+                 const OpDev *ops_dev, const float2 *mats_dev, const uint32_t *bfr_dev, const uint64_t *gbase_dev,
+                 int prec, cudaStream_t s) {
     const uint32_t T = pass_host->T;
     const size_t smem = (size_t(1) << T) * sizeof(float2) + size_t(pass_host->mat_elems) * sizeof(float2);
     dim3 grid(1u << pass_host->nout, ngroups);
     const uint32_t kmax = pass_host->kmax;
     if (prec == QSIM_PREC_TF32 && kmax >= 3)
-        launch_pass_prec<QSIM_PREC_TF32>(kmax, grid, smem, s, wv, W, pass_dev, ops_dev, mats_dev, gbase_dev);
+        launch_pass_prec<QSIM_PREC_TF32>(kmax, grid, smem, s, wv, W, pass_dev, ops_dev, mats_dev, bfr_dev, gbase_dev);
     else if (prec == QSIM_PREC_BF16X3 && kmax >= 3)
-        launch_pass_prec<QSIM_PREC_BF16X3>(kmax, grid, smem, s, wv, W, pass_dev, ops_dev, mats_dev, gbase_dev);
+        launch_pass_prec<QSIM_PREC_BF16X3>(kmax, grid, smem, s, wv, W, pass_dev, ops_dev, mats_dev, bfr_dev, gbase_dev);
     else
-        launch_pass_prec<QSIM_PREC_FP32>(kmax, grid, smem, s, wv, W, pass_dev, ops_dev, mats_dev, gbase_dev);
+        launch_pass_prec<QSIM_PREC_FP32>(kmax, grid, smem, s, wv, W, pass_dev, ops_dev, mats_dev, bfr_dev, gbase_dev);
     count_launch();
 }
 

@@ -32,17 +32,28 @@ struct OpDev {
     uint32_t pad0;
     uint32_t tq[6];          // dense: tile bit of matrix bit j
     uint32_t dsrc[6];        // diag: working bit (< 64) or 64 + full qubit (outer, from group base)
+    uint32_t dtile[6];       // diag in a pass: tile bit of qubit j, or 255 when the bit is constant over a tile
     uint32_t comp[16];       // dense: complement tile bits; comp[0..3] feed the lane bits
     uint64_t basis_outer;    // phase flip: basis & outer mask (full index bits)
     uint64_t basis_w;        // phase flip: working index of the basis state
     uint32_t basis_in_stage; // phase flip: 1 if the basis' outer bits can match a group
-    uint32_t pad1;
+    uint32_t bfrag;          // dense, tensor-core precisions: word offset of the op's B-fragment table
 };
 
 // wv: ngroups consecutive working vectors of 2^W amplitudes; gbase[g] is the
 // full-index value of group g's outer bits.
+// B-fragment tables (tensor-core precisions): the real matrix U_r^T of every
+// dense op, rounded to TF32 or split into BF16 hi/mid/lo, laid out in the
+// register order of the warp MMA's B operand so a lane loads its fragment
+// with one 8-byte load:
+//   TF32 (m16n8k8):  [kstep][ntile][lane][2]      = U_r^T[8 ks + t (+4)][8 nt + g]
+//   BF16 (m16n8k16): [part][kstep][ntile][lane][2] = pairs U_r^T[16 ks + 2t (+1) (+8)][8 nt + g]
+// with g = lane / 4, t = lane % 4, U_r = [[Re U, -Im U], [Im U, Re U]].
+void build_bfrag_table(const double *u_interleaved, uint32_t k, int prec, uint32_t *out);
+size_t bfrag_words(uint32_t k, int prec);
+
 void launch_pass(float2 *wv, uint32_t W, uint32_t ngroups, const PassDev *pass_host, const PassDev *pass_dev,
-                 const OpDev *ops_dev, const float2 *mats_dev, const uint64_t *gbase_dev, int prec,
-                 cudaStream_t s);
+                 const OpDev *ops_dev, const float2 *mats_dev, const uint32_t *bfr_dev, const uint64_t *gbase_dev,
+                 int prec, cudaStream_t s);
 
 }  // namespace qsim

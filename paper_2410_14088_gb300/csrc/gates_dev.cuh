@@ -23,6 +23,9 @@ struct PassSmem {
     OpDev op;
     uint32_t hi[256];
     uint32_t offs[64];
+    uint8_t dlut_lo[128];  // diagonal op: phase-index bits contributed by tile bits 0..6
+    uint8_t dlut_hi[64];   // and by tile bits 7..12
+    uint32_t dconst;       // and by the bits that are constant over the tile
 };
 
 template <int NT, int K>
@@ -133,36 +136,24 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo_half, __nv_bfloat
     return uint32_t(__bfloat16_as_ushort(lo_half)) | (uint32_t(__bfloat16_as_ushort(hi_half)) << 16);
 }
 
-// real input kk of the op for the group whose tile base index is b
-__device__ __forceinline__ float xin(const float2 *tile, uint32_t b, const uint32_t *offs, uint32_t kk, uint32_t D) {
-    const float2 v = tile[swz(b | offs[kk < D ? kk : kk - D])];
-    return kk < D ? v.x : v.y;
-}
-
-// U_r^T[kk][n] = U_r[n][kk]
-__device__ __forceinline__ float uin(const float2 *U, uint32_t n, uint32_t kk, uint32_t D) {
-    const float2 u = U[(n < D ? n : n - D) * D + (kk < D ? kk : kk - D)];
-    if (n < D) return kk < D ? u.x : -u.y;
-    return kk < D ? u.y : u.x;
-}
-
 template <int NT, int K, int PREC>
-__device__ __forceinline__ void apply_dense_mma(float2 *tile, const float2 *U, const PassSmem &S, uint32_t T) {
+__device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__restrict__ bfr, const PassSmem &S,
+                                                uint32_t T) {
+    // tensor-core shape: T = 12 (4096-amplitude tiles), checked by the caller
     constexpr uint32_t D = 1u << K, N2 = 2 * D;
-    const uint32_t G = 1u << (T - K);              // rows
-    const uint32_t rows_per_warp = G / (NT / 32);
-    const uint32_t MT = rows_per_warp / 16;        // m16 tiles per warp
-    constexpr uint32_t NTILES = N2 / 8;             // n8 tiles
+    constexpr uint32_t KW = PREC == QSIM_PREC_TF32 ? 8 : 16;  // MMA k width
+    constexpr uint32_t KS = N2 / KW;                           // k-steps; the first half reads Re, the second Im
+    constexpr uint32_t NTILES = N2 / 8;                        // n8 tiles
+    constexpr uint32_t ROWS = (1u << (12 - K)) / (NT / 32);    // index groups per warp
+    constexpr uint32_t MT = ROWS / 16;                         // m16 tiles per warp
+    static_assert(MT >= 1, "tensor-core tile needs 16 rows per warp");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t gq = lane >> 2, tq = lane & 3;
     const uint32_t nc = T - K;
-    // this warp's rows: row0 + mt*16 + {gq, gq+8}
-    const uint32_t row0 = warp * rows_per_warp;
-    constexpr uint32_t MT_MAX = 8;
-    uint32_t base[MT_MAX][2];
+    const uint32_t row0 = warp * ROWS;
+    uint32_t base[MT][2];
 #pragma unroll
-    for (uint32_t mt = 0; mt < MT_MAX; ++mt) {
-        if (mt >= MT) break;
+    for (uint32_t mt = 0; mt < MT; ++mt)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint32_t g = row0 + mt * 16 + gq + 8 * h;
@@ -170,84 +161,83 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const float2 *U, c
             for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.op.comp[t];
             base[mt][h] = b;
         }
-    }
-    // accumulators: MT x NTILES x 4, MT * NTILES == 16 for T = 12
-    float acc[16][4];
+    float acc[MT * NTILES][4];
 #pragma unroll
-    for (int i = 0; i < 16; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
-    const uint32_t *offs = S.offs;
-    if constexpr (PREC == QSIM_PREC_TF32) {
-        for (uint32_t k0 = 0; k0 < N2; k0 += 8) {
-            uint32_t bfr[NTILES][2];
+    for (uint32_t i = 0; i < MT * NTILES; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
+    const uint2 *bf2 = reinterpret_cast<const uint2 *>(bfr);
+    // k-step pairs (ks, ks + KS/2) read the same complex inputs: Re parts for ks, Im parts for ks + KS/2
+#pragma unroll 1
+    for (uint32_t ks = 0; ks < KS / 2; ++ks) {
+        if constexpr (PREC == QSIM_PREC_TF32) {
+            const uint32_t c0 = S.offs[ks * 8 + tq], c1 = S.offs[ks * 8 + tq + 4];
+            uint32_t are[MT][4], aim[MT][4];
+#pragma unroll
+            for (uint32_t mt = 0; mt < MT; ++mt) {
+                const float2 v00 = tile[swz(base[mt][0] | c0)], v10 = tile[swz(base[mt][1] | c0)];
+                const float2 v01 = tile[swz(base[mt][0] | c1)], v11 = tile[swz(base[mt][1] | c1)];
+                are[mt][0] = f32_to_tf32(v00.x); are[mt][1] = f32_to_tf32(v10.x);
+                are[mt][2] = f32_to_tf32(v01.x); are[mt][3] = f32_to_tf32(v11.x);
+                aim[mt][0] = f32_to_tf32(v00.y); aim[mt][1] = f32_to_tf32(v10.y);
+                aim[mt][2] = f32_to_tf32(v01.y); aim[mt][3] = f32_to_tf32(v11.y);
+            }
 #pragma unroll
             for (uint32_t nt = 0; nt < NTILES; ++nt) {
-                bfr[nt][0] = f32_to_tf32(uin(U, nt * 8 + gq, k0 + tq, D));
-                bfr[nt][1] = f32_to_tf32(uin(U, nt * 8 + gq, k0 + tq + 4, D));
-            }
+                const uint2 bre = __ldg(bf2 + (ks * NTILES + nt) * 32 + lane);
+                const uint2 bim = __ldg(bf2 + ((ks + KS / 2) * NTILES + nt) * 32 + lane);
+                const uint32_t b0[2] = {bre.x, bre.y}, b1[2] = {bim.x, bim.y};
 #pragma unroll
-            for (uint32_t mt = 0; mt < MT_MAX; ++mt) {
-                if (mt >= MT) break;
-                uint32_t a[4];
-                a[0] = f32_to_tf32(xin(tile, base[mt][0], offs, k0 + tq, D));
-                a[1] = f32_to_tf32(xin(tile, base[mt][1], offs, k0 + tq, D));
-                a[2] = f32_to_tf32(xin(tile, base[mt][0], offs, k0 + tq + 4, D));
-                a[3] = f32_to_tf32(xin(tile, base[mt][1], offs, k0 + tq + 4, D));
-#pragma unroll
-                for (uint32_t nt = 0; nt < NTILES; ++nt) mma_tf32(acc[(mt * NTILES + nt) & 15], a, bfr[nt]);
-            }
-        }
-    } else {
-        for (uint32_t k0 = 0; k0 < N2; k0 += 16) {
-            uint32_t bh[NTILES][2], bm[NTILES][2], bl[NTILES][2];
-#pragma unroll
-            for (uint32_t nt = 0; nt < NTILES; ++nt) {
-#pragma unroll
-                for (int r = 0; r < 2; ++r) {
-                    __nv_bfloat16 h0, m0, l0, h1, m1, l1;
-                    split3(uin(U, nt * 8 + gq, k0 + 2 * tq + 8 * r, D), h0, m0, l0);
-                    split3(uin(U, nt * 8 + gq, k0 + 2 * tq + 1 + 8 * r, D), h1, m1, l1);
-                    bh[nt][r] = pack_bf16(h0, h1);
-                    bm[nt][r] = pack_bf16(m0, m1);
-                    bl[nt][r] = pack_bf16(l0, l1);
+                for (uint32_t mt = 0; mt < MT; ++mt) {
+                    mma_tf32(acc[mt * NTILES + nt], are[mt], b0);
+                    mma_tf32(acc[mt * NTILES + nt], aim[mt], b1);
                 }
             }
+        } else {
+            // columns 2t, 2t+1, 2t+8, 2t+9 of the k-step
+            const uint32_t cc[4] = {S.offs[ks * 16 + 2 * tq], S.offs[ks * 16 + 2 * tq + 1], S.offs[ks * 16 + 2 * tq + 8],
+                                    S.offs[ks * 16 + 2 * tq + 9]};
+            constexpr uint32_t PART = KS * NTILES * 32;  // uint2 entries per part
 #pragma unroll
-            for (uint32_t mt = 0; mt < MT_MAX; ++mt) {
-                if (mt >= MT) break;
-                uint32_t ah[4], am[4], al[4];
+            for (int ri = 0; ri < 2; ++ri) {  // Re inputs with k-step ks, then Im inputs with ks + KS/2
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const uint32_t b = base[mt][q & 1];
-                    const uint32_t col = k0 + 2 * tq + 8 * (q >> 1);
-                    __nv_bfloat16 h0, m0, l0, h1, m1, l1;
-                    split3(xin(tile, b, offs, col, D), h0, m0, l0);
-                    split3(xin(tile, b, offs, col + 1, D), h1, m1, l1);
-                    ah[q] = pack_bf16(h0, h1);
-                    am[q] = pack_bf16(m0, m1);
-                    al[q] = pack_bf16(l0, l1);
-                }
+                for (uint32_t mt = 0; mt < MT; ++mt) {
+                    uint32_t ah[4], am[4], al[4];
 #pragma unroll
-                for (uint32_t nt = 0; nt < NTILES; ++nt) {
-                    float (&c)[4] = acc[(mt * NTILES + nt) & 15];
-                    mma_bf16(c, al, bh[nt]);
-                    mma_bf16(c, ah, bl[nt]);
-                    mma_bf16(c, am, bm[nt]);
-                    mma_bf16(c, am, bh[nt]);
-                    mma_bf16(c, ah, bm[nt]);
-                    mma_bf16(c, ah, bh[nt]);
+                    for (int q = 0; q < 4; ++q) {
+                        const uint32_t b = base[mt][q & 1];
+                        const float2 x0 = tile[swz(b | cc[(q >> 1) * 2])], x1 = tile[swz(b | cc[(q >> 1) * 2 + 1])];
+                        __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+                        split3(ri ? x0.y : x0.x, h0, m0, l0);
+                        split3(ri ? x1.y : x1.x, h1, m1, l1);
+                        ah[q] = pack_bf16(h0, h1);
+                        am[q] = pack_bf16(m0, m1);
+                        al[q] = pack_bf16(l0, l1);
+                    }
+#pragma unroll
+                    for (uint32_t nt = 0; nt < NTILES; ++nt) {
+                        const uint32_t e = ((ks + ri * (KS / 2)) * NTILES + nt) * 32 + lane;
+                        const uint2 bh = __ldg(bf2 + e), bm = __ldg(bf2 + PART + e), bl = __ldg(bf2 + 2 * PART + e);
+                        const uint32_t vh[2] = {bh.x, bh.y}, vm[2] = {bm.x, bm.y}, vl[2] = {bl.x, bl.y};
+                        float (&c)[4] = acc[mt * NTILES + nt];
+                        mma_bf16(c, al, vh);
+                        mma_bf16(c, ah, vl);
+                        mma_bf16(c, am, vm);
+                        mma_bf16(c, am, vh);
+                        mma_bf16(c, ah, vm);
+                        mma_bf16(c, ah, vh);
+                    }
                 }
             }
         }
     }
     __syncwarp();
-    // outputs: tile j < NTILES/2 holds re of outputs 8j + 2tq (+1), tile j + NTILES/2 the im parts
+    const uint32_t *offs = S.offs;
+    // outputs: n-tile j < NTILES/2 holds Re of outputs 8j + 2tq (+1), tile j + NTILES/2 the Im parts
 #pragma unroll
-    for (uint32_t mt = 0; mt < MT_MAX; ++mt) {
-        if (mt >= MT) break;
+    for (uint32_t mt = 0; mt < MT; ++mt) {
 #pragma unroll
         for (uint32_t j = 0; j < NTILES / 2; ++j) {
-            const float (&re)[4] = acc[(mt * NTILES + j) & 15];
-            const float (&im)[4] = acc[(mt * NTILES + j + NTILES / 2) & 15];
+            const float (&re)[4] = acc[mt * NTILES + j];
+            const float (&im)[4] = acc[mt * NTILES + j + NTILES / 2];
             const uint32_t r0 = 8 * j + 2 * tq;
             tile[swz(base[mt][0] | offs[r0])] = make_float2(re[0], im[0]);
             tile[swz(base[mt][0] | offs[r0 + 1])] = make_float2(re[1], im[1]);
@@ -260,36 +250,36 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const float2 *U, c
 // Dense op of width k (<= KMAX) on the shared-memory tile; the tensor-core
 // form needs 4096-amplitude tiles and at least 16 index groups per warp.
 template <int NT, int KMAX, int PREC>
-__device__ __forceinline__ void apply_dense_dispatch(uint32_t k, float2 *tile, const float2 *mat, const PassSmem &S,
-                                                     uint32_t T) {
+__device__ __forceinline__ void apply_dense_dispatch(uint32_t k, float2 *tile, const float2 *mat, const uint32_t *bfr,
+                                                     const PassSmem &S, uint32_t T) {
     constexpr bool TC = PREC != QSIM_PREC_FP32;
-    const bool tc_ok = TC && T == 12 && ((1u << (T - k)) / (NT / 32)) >= 16;
+    const uint32_t min_k = PREC == QSIM_PREC_TF32 ? 3u : 4u;  // an MMA k-step must not straddle Re and Im
+    const bool tc_ok = TC && k >= min_k && k <= 5 && T == 12;  // 16+ index groups per warp for NT <= 256
     switch (k) {
         case 1: apply_dense_k1<NT>(tile, mat, S, T); break;
         case 2: if constexpr (KMAX >= 2) apply_dense<NT, 2>(tile, mat, S, T); break;
         case 3:
             if constexpr (KMAX >= 3) {
-                if (tc_ok) apply_dense_mma<NT, 3, PREC>(tile, mat, S, T);
-                else apply_dense<NT, 3>(tile, mat, S, T);
+                if constexpr (PREC == QSIM_PREC_TF32) {
+                    if (tc_ok) { apply_dense_mma<NT, 3, PREC>(tile, bfr, S, T); break; }
+                }
+                apply_dense<NT, 3>(tile, mat, S, T);
             }
             break;
         case 4:
             if constexpr (KMAX >= 4) {
-                if (tc_ok) apply_dense_mma<NT, 4, PREC>(tile, mat, S, T);
+                if (tc_ok) apply_dense_mma<NT, 4, PREC>(tile, bfr, S, T);
                 else apply_dense<NT, 4>(tile, mat, S, T);
             }
             break;
         case 5:
             if constexpr (KMAX >= 5) {
-                if (tc_ok) apply_dense_mma<NT, 5, PREC>(tile, mat, S, T);
+                if (tc_ok) apply_dense_mma<NT, 5, PREC>(tile, bfr, S, T);
                 else apply_dense<NT, 5>(tile, mat, S, T);
             }
             break;
         default:
-            if constexpr (KMAX >= 6) {
-                if (tc_ok) apply_dense_mma<NT, 6, PREC>(tile, mat, S, T);
-                else apply_dense<NT, 6>(tile, mat, S, T);
-            }
+            if constexpr (KMAX >= 6) apply_dense<NT, 6>(tile, mat, S, T);
             break;
     }
 }
@@ -301,7 +291,8 @@ __device__ __forceinline__ void apply_dense_dispatch(uint32_t k, float2 *tile, c
 template <int NT, int KMAX, int PREC, bool CG>
 __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev *__restrict__ pd,
                                           const OpDev *__restrict__ ops, const float2 *__restrict__ mats,
-                                          uint64_t cta, uint64_t gb, PassSmem &S, float2 *tile) {
+                                          const uint32_t *__restrict__ bfr, uint64_t cta, uint64_t gb, PassSmem &S,
+                                          float2 *tile) {
     const int tid = threadIdx.x;
     if (tid == 0) S.p = *pd;
     __syncthreads();
@@ -350,20 +341,38 @@ __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev 
                 S.offs[tid] = o;
             }
             __syncthreads();
-            if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, mat, S, T);
+            if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, mat, bfr + S.op.bfrag, S, T);
         } else if (type == OP_DIAG) {
+            // phase index = bits constant over the tile | lookups over the tile bits
             const uint32_t D = 1u << k;
             for (uint32_t i = tid; i < D; i += NT) mat[i] = mats[S.op.mat + i];
-            __syncthreads();
-            for (uint32_t i = tid; i < (1u << T); i += NT) {
-                const uint64_t w = base | (i & lmask) | S.hi[i >> L];
+            for (uint32_t v = tid; v < 192; v += NT) {
+                const bool lo = v < 128;
+                const uint32_t x = lo ? v : v - 128;
                 uint32_t idx = 0;
                 for (uint32_t j = 0; j < k; ++j) {
+                    const uint32_t t = S.op.dtile[j];
+                    if (t == 255) continue;
+                    if (lo && t < 7) idx |= ((x >> t) & 1u) << j;
+                    if (!lo && t >= 7) idx |= ((x >> (t - 7)) & 1u) << j;
+                }
+                if (lo) S.dlut_lo[x] = uint8_t(idx);
+                else S.dlut_hi[x] = uint8_t(idx);
+            }
+            if (tid == 0) {
+                uint32_t idx = 0;
+                for (uint32_t j = 0; j < k; ++j) {
+                    if (S.op.dtile[j] != 255) continue;
                     const uint32_t src = S.op.dsrc[j];
-                    const uint64_t bit = src < 64 ? (w >> src) & 1ull : (gb >> (src - 64)) & 1ull;
+                    const uint64_t bit = src < 64 ? (base >> src) & 1ull : (gb >> (src - 64)) & 1ull;
                     idx |= uint32_t(bit) << j;
                 }
-                const float2 ph = mat[idx];
+                S.dconst = idx;
+            }
+            __syncthreads();
+            const uint32_t dc = S.dconst;
+            for (uint32_t i = tid; i < (1u << T); i += NT) {
+                const float2 ph = mat[dc | S.dlut_lo[i & 127u] | S.dlut_hi[i >> 7]];
                 float2 &a = tile[swz(i)];
                 const float2 v = a;
                 a = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PStageArgs A) {
                                         A.npre, A.mats, uint64_t(jj) << A.m, gb);
             }
         } else if (type == PH_PASS) {
-            gdev::pass_tile<PT, 5, PREC, true>(wv, A.passes + A.ph[p].arg, A.ops, A.mats, i, gb, PS,
+            gdev::pass_tile<PT, 5, PREC, true>(wv, A.passes + A.ph[p].arg, A.ops, A.mats, A.bfr, i, gb, PS,
                                                reinterpret_cast<float2 *>(dsm));
         } else if (type == PH_SIZE) {
             const uint32_t jj = i / g.nframes, f = i % g.nframes;

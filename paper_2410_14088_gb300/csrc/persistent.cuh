@@ -34,6 +34,7 @@ struct PStageArgs {
     const PassDev *passes;
     const OpDev *ops;
     const float2 *mats;
+    const uint32_t *bfr;     // B-fragment tables of the tensor-core precisions
     const uint32_t *ids;     // group-major block ids of the stage
     const uint64_t *gbase;   // per group: full-index bits of its outer qubits
     BlockSlot *tab_in, *tab_out;
