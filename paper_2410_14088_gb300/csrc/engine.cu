@@ -19,6 +19,7 @@
 #include <stdarg.h>
 #include <stdio.h>
 #include <string.h>
+#include <unistd.h>
 
 #include <algorithm>
 #include <atomic>
@@ -321,17 +322,30 @@ struct PlanDev {
 static std::mutex g_plan_mu;
 static std::map<const qsim_plan *, PlanDev *> g_plan_dev;
 
-static void order_complement(OpDev &od, uint32_t T) {
+// Order the op's complement tile bits (the bits that enumerate its index
+// groups). Tile bit t lands on bank-pair bit t % 4 of the swizzled layout; a
+// half-warp's 16 accesses are conflict-free when the 4 tile bits that vary
+// across them fall on 4 different residues. SIMT ops: lanes are consecutive
+// groups, so the first 4 complement bits take distinct residues. Tensor-core
+// ops: a half-warp spans 2 row bits (complement bits 0, 1) and 2 column bits
+// (the op's matrix bits 0, 1), so the first 2 complement bits avoid the
+// residues of those columns.
+static void order_complement(OpDev &od, uint32_t T, bool mma) {
     bool is_t[16] = {false};
     for (uint32_t j = 0; j < od.k; ++j) is_t[od.tq[j]] = true;
     std::vector<uint32_t> comp;
     for (uint32_t t = 0; t < T; ++t)
         if (!is_t[t]) comp.push_back(t);
-    // lane bits: one complement bit per bank residue (tile bit t lands on bank bit t % 4)
     std::vector<uint32_t> first, rest;
     bool have[4] = {false, false, false, false};
+    uint32_t want = 4;
+    if (mma && od.k >= 2) {
+        have[od.tq[0] % 4] = true;
+        have[od.tq[1] % 4] = true;
+        want = 2;
+    }
     for (uint32_t t : comp) {
-        if (!have[t % 4] && first.size() < 4) {
+        if (!have[t % 4] && first.size() < want) {
             have[t % 4] = true;
             first.push_back(t);
         } else {
@@ -450,7 +464,9 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                         while (ps.tile_pos[t] != op.wq[j]) ++t;
                         od.tq[j] = t;
                     }
-                    order_complement(od, ps.T);
+                    const uint32_t min_k = p->cfg.prec == QSIM_PREC_TF32 ? 3u : 4u;
+                    order_complement(od, ps.T,
+                                     p->cfg.prec != QSIM_PREC_FP32 && op.k >= min_k && op.k <= 5 && ps.T == 12);
                     od.mat = mats.size();
                     for (const cd &v : op.u) mats.push_back(make_float2(float(v.real()), float(v.imag())));
                     P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << (2 * op.k));
@@ -889,7 +905,16 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
     uint64_t dev_budget = free_b > work_bytes ? uint64_t(0.85 * double(free_b - work_bytes)) : 0;
     if (cfg.device_tier_cap_bytes) dev_budget = std::min<uint64_t>(dev_budget, cfg.device_tier_cap_bytes);
     uint64_t dev_cap = std::min<uint64_t>(need_per_parity, dev_budget / 2) & ~uint64_t(255);
-    uint64_t host_cap = need_per_parity > dev_cap ? ((need_per_parity - dev_cap + 4095) & ~uint64_t(4095)) : 0;
+    // the pinned-host level is sized by the host's memory (at most 40 % of it per stage parity); it is only
+    // set up when the device level is capped or cannot hold a raw-sized store
+    const uint64_t raw_need = (nblocks + 1) * (((8ull << m) + qsz_data_start(int(m)) + 255) & ~255ull);
+    uint64_t host_cap = 0;
+    if (need_per_parity > dev_cap && (cfg.device_tier_cap_bytes || raw_need > dev_cap)) {
+        const long pages = sysconf(_SC_PHYS_PAGES), page = sysconf(_SC_PAGE_SIZE);
+        const uint64_t host_phys = (pages > 0 && page > 0) ? uint64_t(pages) * uint64_t(page) : (64ull << 30);
+        host_cap = std::min<uint64_t>(need_per_parity - dev_cap, uint64_t(0.4 * double(host_phys)));
+        host_cap = (host_cap + 4095) & ~uint64_t(4095);
+    }
 
     uint8_t *dev_arena[2] = {nullptr, nullptr}, *host_arena[2] = {nullptr, nullptr};
     uint8_t *host_arena_dev[2] = {nullptr, nullptr};

@@ -171,3 +171,19 @@ def test_tensor_core_compressed_run():
     for prec in (qsim.PREC_TF32, qsim.PREC_BF16X3):
         st = qsim.run(qsim.plan_stages(c, m=10, inner=2, k=5, eps=1e-3, prec=prec))
         assert st.fidelity(ideal) >= 0.99
+
+
+@pytest.mark.parametrize("prec,rel_tol", [(qsim.PREC_FP32, 1e-4), (qsim.PREC_TF32, 2e-2), (qsim.PREC_BF16X3, 1e-4)],
+                         ids=["fp32", "tf32", "bf16x3"])
+def test_config1_gate_error_vs_fp64(prec, rel_tol):
+    # the 28-qubit QFT + RZ/CX workload, codec off: only the gate arithmetic differs from the exact state
+    c = inputs.qft_rz_cx(28, 4, 1)
+    st = qsim.run(qsim.plan_stages(c, m=22, inner=4, k=5, codec=qsim.CODEC_NONE, prec=prec))
+    idx = (inputs.splitmix64_array(91, 4096) >> np.uint64(36)).astype(np.uint64)
+    got = st.amplitudes(idx).astype(np.complex128)
+    want = cf.qft_rz_cx_amplitudes(28, c.meta["x"], c.meta["rz_angles"], idx)
+    err = float(np.max(np.abs(got - want)))
+    rel = err / 2.0 ** -14
+    print(f"\ngate error vs FP64, 28-qubit QFT+RZ/CX, prec={prec}: max-abs {err:.3e}, relative to 2^-14: {rel:.3e}")
+    assert err <= 1e-5 or prec == qsim.PREC_TF32
+    assert rel <= rel_tol
