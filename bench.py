@@ -65,22 +65,42 @@ def parse_args():
     ap.add_argument("--graph", action="store_true", help="persistent mode: capture the stage loop in a CUDA graph")
     ap.add_argument("--sizing", default="exact", choices=["exact", "predict"])
     ap.add_argument("--margin", type=float, default=0.25, help="predictor reservation margin")
-    ap.add_argument("--workload", default="qft", choices=["qft", "qaoa", "random"],
+    ap.add_argument("--diag-exempt", action="store_true", help="diagonal gates never count as global (Algorithm 1)")
+    ap.add_argument("--train-n", type=int, default=0, help="qubits of the predictor's training circuits (0 = n)")
+    ap.add_argument("--workload", default="qft", choices=["qft", "qaoa", "random", "mirror", "batch"],
                     help="qft: QFT + 4 x (RZ, CX ladder) on n qubits; qaoa: MaxCut p=3 on a random 3-regular "
-                         "graph of n vertices; random: U3 + CZ brick of depth --depth")
+                         "graph of n vertices; random: U3 + CZ brick of depth --depth; mirror: depth/2 random "
+                         "layers then their inverse (ideal final state |0...0>); batch: --batch independent "
+                         "circuits (GHZ, QFT, random depth 8, Grover 3-6 iterations; n ~ U{20..30}) in one "
+                         "persistent launch")
+    ap.add_argument("--batch", type=int, default=64, help="batch workload: number of circuits")
+    ap.add_argument("--no-tune", action="store_true", help="batch workload: fixed m, k instead of the autotuner")
     ap.add_argument("--depth", type=int, default=14)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement (long workloads)")
     ap.add_argument("--cap-gib", type=float, default=0.0, help="device tier cap (pinned host holds the rest)")
     return ap.parse_args()
 
 
-def workload(args, seed=None):
+def batch_workload(args, seed=None):
+    from paper_2410_14088_gb300 import inputs
+    return inputs.batch_circuits(args.seed if seed is None else seed, count=args.batch, nmin=20, nmax=30)
+
+
+def workload(args, seed=None, n=None):
     from paper_2410_14088_gb300 import inputs
     seed = args.seed if seed is None else seed
+    n = args.n if n is None else n
+    if args.workload == "batch":
+        # the oracle sample of the batch: its first random circuit (per-amplitude cost does not depend on n)
+        cs = batch_workload(args, seed)
+        return next((c for c in cs if c.family == "random"), cs[0])
     if args.workload == "qaoa":
-        return inputs.qaoa_maxcut(args.n, 3, seed)
+        return inputs.qaoa_maxcut(n, 3, seed)
     if args.workload == "random":
-        return inputs.random_brick(args.n, args.depth, seed)
-    return inputs.qft_rz_cx(args.n, 4, seed)
+        return inputs.random_brick(n, args.depth, seed)
+    if args.workload == "mirror":
+        return inputs.mirror_brick(n, args.depth // 2, seed)
+    return inputs.qft_rz_cx(n, 4, seed)
 
 
 def load_peaks():
@@ -164,7 +184,7 @@ class OracleSampler:
 
         self.np, self.oracle = np, oracle
         self.circ = workload(args)
-        self.n, self.m = self.circ.n, args.m
+        self.n, self.m = self.circ.n, min(args.m, self.circ.n - 4)
         self.eb = args.eps * 2.0 ** (-self.n / 2)
         self.stages = partition(self.circ.gates, self.n, self.m, args.inner)
         self.psi = oracle.basis_state(self.n, self.circ.init_basis)
@@ -233,8 +253,20 @@ def run_reference(args, rank, world):
 
 
 def config_dict(args):
+    if args.workload == "batch":
+        cs = batch_workload(args)
+        return {"workload": f"batch of {args.batch} circuits (ghz, qft, random u3+cz depth 8, grover 3-6 "
+                            f"iterations; n~U{{20..30}}, seed {args.seed}), one persistent launch, eps={args.eps:g}, "
+                            f"prec={args.prec}, sizing={args.sizing}, m/k/inner "
+                            f"{'fixed' if args.no_tune else 'autotuned per circuit'}",
+                "circuits": len(cs), "n_qubits": [min(c.n for c in cs), max(c.n for c in cs)],
+                "gates": sum(len(c.gates) for c in cs), "eps": args.eps, "prec": args.prec,
+                "mode": "persistent (one launch for the batch)", "sizing": args.sizing,
+                "raw_state_gib": sum(8 << c.n for c in cs) / 2**30,
+                "l2_policy": "working set (all circuits' compressed stores) > L2 (129 MB); no flush"}
     name = {"qft": f"qft{args.n}+4x(rz,cx-ladder)", "qaoa": f"qaoa-maxcut p=3, 3-regular n={args.n}",
-            "random": f"random u3+cz brick n={args.n} depth={args.depth}"}[args.workload]
+            "random": f"random u3+cz brick n={args.n} depth={args.depth}",
+            "mirror": f"mirror u3+cz brick n={args.n} depth={args.depth}"}[args.workload]
     raw = 8 << args.n
     return {"workload": f"{name}, m={args.m}, inner={args.inner}, k={args.k}, eps={args.eps:g}, prec={args.prec}, "
                         f"mode={args.mode}{'+graph' if args.graph else ''}, sizing={args.sizing}",
@@ -264,7 +296,7 @@ def run_ours(args, rank, world, dist):
               mode=qsim.MODE_PERSISTENT if args.mode == "persistent" else qsim.MODE_STREAMS,
               graph=1 if args.graph else 0,
               sizing=qsim.SIZING_PREDICT if args.sizing == "predict" else qsim.SIZING_EXACT,
-              predictor_margin=args.margin,
+              predictor_margin=args.margin, diag_exempt=1 if args.diag_exempt else 0,
               device_tier_cap_bytes=int(args.cap_gib * (1 << 30)))
     train_info = None
     if args.sizing == "predict":
@@ -274,7 +306,7 @@ def run_ours(args, rank, world, dist):
         rows = []
         tkw = dict(kw, mode=qsim.MODE_STREAMS, sizing=qsim.SIZING_EXACT, graph=0)
         for sd in (100, 101):
-            st = qsim.run(qsim.plan_stages(workload(args, sd), collect=1, **tkw))
+            st = qsim.run(qsim.plan_stages(workload(args, sd, args.train_n or None), collect=1, **tkw))
             rows.append(st.training_data())
             del st
         rows = np.concatenate(rows)
@@ -333,7 +365,7 @@ def run_ours(args, rank, world, dist):
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     h2d = d2h = 0
-    for _ in range(args.steps):
+    for _ in range(0 if args.no_e2e else args.steps):
         p2 = qsim.plan_stages(circ, **kw)
         st = qsim.run(p2)
         amps = st.amplitudes(idx)
@@ -347,7 +379,7 @@ def run_ours(args, rank, world, dist):
         t = torch.tensor([te_ms], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         te_ms = float(t.item())
-    e2e = world * args.steps * (1 << n) * G / (te_ms * 1e-3)
+    e2e = world * args.steps * (1 << n) * G / (te_ms * 1e-3) if not args.no_e2e else None
 
     if rank != 0:
         return
@@ -391,6 +423,12 @@ def run_ours(args, rank, world, dist):
         roofline["traffic"] = traffic_for(dom, d["alg_bytes"] / max(1, d["launches"]))
         roofline["ms_per_launch"] = per_launch_s * 1e3
     cr = 8.0 * (1 << n) / max(1, last["peak_store_bytes"])
+    mirror_fidelity = None
+    if args.workload == "mirror":
+        st = qsim.run(plan)
+        a0 = st.amplitudes(np.array([0], dtype=np.uint64))[0]
+        mirror_fidelity = float(abs(a0) / math.sqrt(st.norm_sq()))
+        del st
     line = {
         "metric": "amplitude-gate updates/s incl. codec & compression ratio at fidelity>=0.99",
         "value": ups, "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -403,8 +441,9 @@ def run_ours(args, rank, world, dist):
         "stages": last["nstages"], "plan_seconds": plan.stats()["plan_seconds"],
         "overflow_blocks": last["overflow_blocks"], "peak_reserved_bytes": last["peak_reserved_bytes"],
         "host_tier_peak_bytes": last["host_tier_peak_bytes"], "predictor_training": train_info,
+        "mirror_fidelity": mirror_fidelity,
         "e2e": {"value": e2e, "unit": "updates/s", "h2d_bytes_per_step": h2d // args.steps,
-                "d2h_bytes_per_step": d2h // args.steps},
+                "d2h_bytes_per_step": d2h // args.steps} if e2e is not None else None,
         "gpu_launches": launches,
         "roofline": roofline,
         "kernels": kernels,
@@ -419,6 +458,153 @@ def run_ours(args, rank, world, dist):
         cups, sample, threads, _ = smp.result()
         line["cpu_baseline"] = {"value": cups, "unit": "updates/s", "cores": threads, "kind": "oracle",
                                 "sample": sample}
+    print(json.dumps(line), flush=True)
+
+
+def run_batch_bench(args, rank, world, dist):
+    """Config of a batch of independent circuits: one qsim_run_batch per step."""
+    import numpy as np
+    import torch
+
+    from paper_2410_14088_gb300 import inputs, qsim
+
+    dev = int(os.environ.get("LOCAL_RANK", 0))
+    torch.cuda.set_device(dev)
+    prec = {"fp32": qsim.PREC_FP32, "tf32": qsim.PREC_TF32, "bf16x3": qsim.PREC_BF16X3}[args.prec]
+    circuits = batch_workload(args)
+    base = dict(eps=args.eps, prec=prec, mode=qsim.MODE_PERSISTENT,
+                sizing=qsim.SIZING_PREDICT if args.sizing == "predict" else qsim.SIZING_EXACT,
+                predictor_margin=args.margin)
+    train_info = None
+    if args.sizing == "predict":
+        # training rows from exact-sizing runs of a training batch (seed 100+), not timed
+        t0 = time.perf_counter()
+        rows = []
+        for c in inputs.batch_circuits(100, count=8, nmin=20, nmax=24):
+            st = qsim.run(qsim.plan_stages(c, m=min(20, c.n - 4), inner=2, k=5, eps=args.eps, prec=prec, collect=1))
+            rows.append(st.training_data())
+            del st
+        rows = np.concatenate(rows)
+        loss = qsim.predictor_train(rows, epochs=40, batch=64, lr=3e-3, seed=100)
+        train_info = {"rows": int(rows.shape[0]), "loss": loss, "seconds": time.perf_counter() - t0}
+    t0 = time.perf_counter()
+    cfgs, timed_candidates = [], 0
+    for c in circuits:
+        if args.no_tune:
+            cfgs.append(dict(m=min(args.m, c.n - 4), inner=2, k=min(args.k, 5)))
+            continue
+        bc = qsim.default_config(init_basis=c.init_basis, **base)
+        best, _, cand = qsim.autotune(c, bc, m=(max(12, c.n - 12), min(24, c.n - 4)), k=(3, 5), inner=(2, 4),
+                                      streams=(1,), prefix_gates=min(len(c.gates), 96), reps=1)
+        timed_candidates += cand
+        cfgs.append(dict(m=best.m, inner=best.inner, k=best.k))
+    tune_info = None if args.no_tune else {"seconds": time.perf_counter() - t0, "candidates_timed": timed_candidates,
+                                           "m": sorted(set(c["m"] for c in cfgs)),
+                                           "k": sorted(set(c["k"] for c in cfgs)),
+                                           "inner": sorted(set(c["inner"] for c in cfgs))}
+    plans = [qsim.plan_stages(c, **cfg, **base) for c, cfg in zip(circuits, cfgs)]
+    updates = sum((1 << c.n) * len(c.gates) for c in circuits)
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        states, _ = qsim.run_batch(plans)
+        del states
+    barrier()
+    qsim.profile_enable(not args.no_profile)
+    sampler = ClockSampler(dev)
+    sampler.start()
+    launches0 = qsim.launch_count()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    ev0.record(stream)
+    launch_acc = {"launches": 0, "seconds": 0.0, "alg_bytes": 0.0, "alg_flops": 0.0}
+    for _ in range(args.steps):
+        states, launch = qsim.run_batch(plans)
+        for f in launch_acc:
+            launch_acc[f] += launch[f]
+        stats = [st.stats.as_dict() for st in states]
+        del states
+    ev1.record(stream)
+    barrier()
+    clocks = sampler.stop()
+    qsim.profile_enable(False)
+    launches = qsim.launch_count() - launches0
+    t_max = ev0.elapsed_time(ev1)
+    if dist is not None:
+        t = torch.tensor([t_max], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_max = float(t.item())
+    ups = world * args.steps * updates / (t_max * 1e-3)
+
+    # e2e: plans from the host gate lists, the batch, 64 sampled amplitudes of every circuit read back
+    barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    h2d = d2h = 0
+    for _ in range(args.steps):
+        ps = [qsim.plan_stages(c, **cfg, **base) for c, cfg in zip(circuits, cfgs)]
+        sts, _ = qsim.run_batch(ps)
+        for c, st in zip(circuits, sts):
+            idx = np.arange(0, 1 << c.n, (1 << c.n) // 64, dtype=np.uint64)[:64]
+            a = st.amplitudes(idx)
+            h2d += st.stats.h2d_bytes + idx.nbytes
+            d2h += st.stats.d2h_bytes + a.nbytes
+        del sts, ps
+    e1.record(stream)
+    barrier()
+    te_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([te_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te_ms = float(t.item())
+    e2e = world * args.steps * updates / (te_ms * 1e-3)
+    if rank != 0:
+        return
+    peaks, peaks_kind = load_peaks()
+    roofline = None
+    if launch_acc["launches"]:
+        gbps = launch_acc["alg_bytes"] / max(1e-12, launch_acc["seconds"]) / 1e9
+        roofline = {"bound": "hbm", "achieved": gbps, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                    "peak_source": f"{peaks_kind} hbm_gbs (copy)", "frac": gbps / peaks["hbm_gbs"],
+                    "kernel": "stage_persistent (whole batch)", "traffic": None,
+                    "ms_per_launch": 1e3 * launch_acc["seconds"] / launch_acc["launches"],
+                    "tflops": launch_acc["alg_flops"] / max(1e-12, launch_acc["seconds"]) / 1e12}
+    raw = sum(8.0 * (1 << c.n) for c in circuits)
+    line = {
+        "metric": "amplitude-gate updates/s incl. codec & compression ratio at fidelity>=0.99",
+        "value": ups, "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec], "data": "synthetic",
+        "config": config_dict(args),
+        "compression_ratio": raw / max(1, sum(s["peak_store_bytes"] for s in stats)),
+        "fidelity_lower_bound_min": min(s["fidelity_lower_bound"] for s in stats),
+        "fidelity_lower_bound_per_circuit": [round(s["fidelity_lower_bound"], 6) for s in stats],
+        "stages_total": sum(s["nstages"] for s in stats),
+        "overflow_blocks": sum(s["overflow_blocks"] for s in stats),
+        "host_tier_peak_bytes": sum(s["host_tier_peak_bytes"] for s in stats),
+        "predictor_training": train_info, "autotune": tune_info,
+        "e2e": {"value": e2e, "unit": "updates/s", "h2d_bytes_per_step": h2d // args.steps,
+                "d2h_bytes_per_step": d2h // args.steps},
+        "gpu_launches": launches,
+        "roofline": roofline,
+        "clocks": clocks,
+        "peaks": peaks_kind,
+    }
+    if not args.no_cpu_baseline:
+        smp = OracleSampler(args)
+        smp.step(0.5, record=False)
+        for _ in range(3):
+            smp.step(args.cpu_seconds / 3)
+        cups, sample, threads, _ = smp.result()
+        line["cpu_baseline"] = {"value": cups, "unit": "updates/s", "cores": threads, "kind": "oracle",
+                                "sample": "per-amplitude-gate rate of the batch's first random circuit: " + sample}
     print(json.dumps(line), flush=True)
 
 
@@ -460,7 +646,10 @@ def main():
         torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", 0)))
         tdist.init_process_group("nccl")
         dist = tdist
-    run_ours(args, rank, world, dist)
+    if args.workload == "batch":
+        run_batch_bench(args, rank, world, dist)
+    else:
+        run_ours(args, rank, world, dist)
     if dist is not None:
         dist.destroy_process_group()
 

@@ -137,7 +137,7 @@ int qsim_plan_get_stats(const qsim_plan *plan, qsim_plan_stats *out);
 typedef struct qsim_op_info {
     uint32_t type;      /* 0 dense matrix, 1 diagonal phases, 2 phase flip */
     uint32_t nq;        /* qubits of the op (0 for a phase flip) */
-    uint32_t qubits[6]; /* full qubit ids; matrix bit j <-> qubits[j] */
+    uint32_t qubits[8]; /* full qubit ids; matrix bit j <-> qubits[j] (dense ops <= 6, diagonal ops <= 8) */
     uint32_t ngates;    /* input gates folded into the op */
     uint32_t pass;      /* index of the shared-memory tile pass within the stage */
     uint64_t basis;     /* phase flip: the flipped basis state */
@@ -355,6 +355,33 @@ typedef struct qsim_kernel_stat {
 } qsim_kernel_stat;
 
 int qsim_state_kernel_stats(const qsim_state *st, qsim_kernel_stat *out, size_t cap, size_t *count);
+
+/* ---- a batch of independent circuits ----------------------------------------
+ * Runs `count` planned circuits together: their initial stores, then ONE launch
+ * of the persistent stage kernel whose work queue holds every stage of every
+ * circuit. Stages are dealt round-robin over the circuits (stage 0 of each,
+ * then stage 1 of each, ...); a circuit's stage waits on the device for all
+ * groups of its previous stage (a bounded wait, QSIM_E_TIMEOUT), so one
+ * circuit's stage boundary overlaps the other circuits' work. The paper runs
+ * one circuit at a time; this extends its group pipeline (Sec. 4.2) to many
+ * independent state vectors, each with its own block size, fused width and
+ * error bound.
+ *   plans   host array of `count` plans. Each must use codec QSZ1, k <= 5 and
+ *           no row collection; all must use the same precision. Their mode and
+ *           streams fields are ignored; sizing is exact or predict per plan
+ *           (predict needs trained weights); the first plan's `graph` flag
+ *           decides whether the launch is captured in a CUDA graph.
+ *   states  out: host array of `count` handles, each freed by qsim_state_free.
+ *   stats   nullable: `count` entries; `seconds` is the whole batch's time.
+ *   launch  nullable: event time, algorithmic bytes and flops of the batch's
+ *           persistent launch.
+ * Memory: each circuit gets a share of the device and pinned-host levels in
+ * proportion to its worst-case store size.
+ * Errors: INVALID (empty batch, mixed precision, a plan the persistent kernel
+ * cannot run), UNSUPPORTED, NOMEM, RANGE, TIMEOUT, CUDA. On error every
+ * states[i] is NULL. */
+int qsim_run_batch(const qsim_plan *const *plans, size_t count, void *cuda_stream, qsim_state **states,
+                   qsim_stats *stats, qsim_kernel_stat *launch);
 
 /* ---- misc ------------------------------------------------------------------ */
 const char *qsim_last_error(void);

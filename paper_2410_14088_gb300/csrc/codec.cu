@@ -140,7 +140,8 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
 __global__ void __launch_bounds__(NT) k_encode_size(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
                                                     uint64_t *__restrict__ sizes, uint32_t *done_ctr,
                                                     ArenaDev dev, ArenaDev host, EncTarget *__restrict__ tgt,
-                                                    EncResult *__restrict__ res, int *status) {
+                                                    EncResult *__restrict__ res, int *status, uint8_t *__restrict__ wrec,
+                                                    uint32_t *__restrict__ flen, uint32_t *__restrict__ foff) {
     const FrameGeom g = geom(m);
     __shared__ uint32_t s_words[NW];
     __shared__ bool s_last;
@@ -148,9 +149,12 @@ __global__ void __launch_bounds__(NT) k_encode_size(const float2 *__restrict__ w
     const uint64_t items = uint64_t(nblocks) * g.nframes;
     for (uint64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const uint32_t j = uint32_t(item / g.nframes), f = uint32_t(item % g.nframes);
-        const uint32_t len = size_frame_cta(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, g, e, s_words, status);
-        if (tid == 0 && len) atomicAdd(reinterpret_cast<unsigned long long *>(&sizes[j]), uint64_t(len));
-        __syncthreads();
+        const uint32_t len = size_frame_cta(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, g, e, s_words, status,
+                                            wrec ? wrec + item * 256 : nullptr);
+        if (tid == 0) {
+            if (len) atomicAdd(reinterpret_cast<unsigned long long *>(&sizes[j]), uint64_t(len));
+            if (flen) flen[item] = len;
+        }
     }
     if (!done_ctr) return;
     if (tid == 0) {
@@ -160,16 +164,107 @@ __global__ void __launch_bounds__(NT) k_encode_size(const float2 *__restrict__ w
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    for (uint32_t j = tid; j < nblocks; j += NT) {
-        const uint64_t want = ld_relaxed_u64(&sizes[j]) + g.data_start;
-        sizes[j] = 0;
-        res[j].total = 0;
-        res[j].overflow = 0;
-        res[j].err_sq = 0;
-        res[j].norm_sq = 0;
-        reserve_slot(want, dev, host, &tgt[j], status);
+    if (foff) {
+        // warp per block: frame offsets = data_start + exclusive prefix of the frame lengths
+        for (uint32_t jb = warp; jb < nblocks; jb += NW) {
+            uint32_t run = uint32_t(g.data_start);
+            for (uint32_t f0 = 0; f0 < g.nframes; f0 += 32) {
+                const uint64_t it = uint64_t(jb) * g.nframes + f0 + lane;
+                const uint32_t v = f0 + lane < g.nframes ? __ldcg(flen + it) : 0u;
+                uint32_t incl = v;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                    if (lane >= o) incl += t;
+                }
+                if (f0 + lane < g.nframes) foff[it] = run + incl - v;
+                run += __shfl_sync(kFull, incl, 31);
+            }
+            if (lane == 0) {
+                sizes[jb] = 0;
+                res[jb].total = 0;
+                res[jb].overflow = 0;
+                res[jb].err_sq = 0;
+                res[jb].norm_sq = 0;
+                reserve_slot(run, dev, host, &tgt[jb], status);
+            }
+        }
+    } else {
+        for (uint32_t j = tid; j < nblocks; j += NT) {
+            const uint64_t want = ld_relaxed_u64(&sizes[j]) + g.data_start;
+            sizes[j] = 0;
+            res[j].total = 0;
+            res[j].overflow = 0;
+            res[j].err_sq = 0;
+            res[j].norm_sq = 0;
+            reserve_slot(want, dev, host, &tgt[j], status);
+        }
     }
     if (tid == 0) *done_ctr = 0;
+}
+
+// Exact-sizing encoder: one warp per frame, widths and frame offsets from the
+// sizing pass; the last CTA folds the frames' error partials into the blocks'
+// and the stage's totals.
+__global__ void __launch_bounds__(NT) k_encode_known(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
+                                                     const EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
+                                                     const uint32_t *__restrict__ ids, BlockSlot *__restrict__ table,
+                                                     StageAccum *acc, const uint8_t *__restrict__ wrec,
+                                                     const uint32_t *__restrict__ flen,
+                                                     const uint32_t *__restrict__ foff, float2 *__restrict__ part,
+                                                     uint32_t *done_ctr, int *status) {
+    const FrameGeom g = geom(m);
+    __shared__ bool s_last;
+    __shared__ double s_red[2][NW];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint64_t items = uint64_t(nblocks) * g.nframes;
+    for (uint64_t item = uint64_t(blockIdx.x) * NW + warp; item < items; item += uint64_t(gridDim.x) * NW) {
+        const uint32_t j = uint32_t(item / g.nframes), f = uint32_t(item % g.nframes);
+        encode_frame_warp_known(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, g, m, e, f, wrec + item * 256, foff[item],
+                                flen[item], tgt[j], res + j, table ? table + ids[j] : nullptr, acc, part + item,
+                                status);
+    }
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(done_ctr, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    double ta = 0, tb = 0;
+    for (uint32_t jb = warp; jb < nblocks; jb += NW) {
+        double a = 0, b = 0;
+        for (uint32_t f2 = lane; f2 < g.nframes; f2 += 32) {
+            const float2 p = __ldcg(part + uint64_t(jb) * g.nframes + f2);
+            a += double(p.x);
+            b += double(p.y);
+        }
+#pragma unroll
+        for (int o = 16; o; o >>= 1) {
+            a += __shfl_xor_sync(kFull, a, o);
+            b += __shfl_xor_sync(kFull, b, o);
+        }
+        if (lane == 0) {
+            res[jb].err_sq = a;
+            res[jb].norm_sq = b;
+        }
+        ta += a;
+        tb += b;
+    }
+    if (lane == 0) {
+        s_red[0][warp] = ta;
+        s_red[1][warp] = tb;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        if (acc) {
+            double a = 0, b = 0;
+            for (int w = 0; w < NW; ++w) { a += s_red[0][w]; b += s_red[1][w]; }
+            atomicAdd(&acc->err_sq, a);
+            atomicAdd(&acc->norm_sq, b);
+        }
+        *done_ctr = 0;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -293,16 +388,26 @@ void launch_encode_size(const float2 *wv, uint32_t nblocks, int m, int e, uint64
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
     ArenaDev none{};
     k_encode_size<<<grid_for(items, 152 * 8), NT, 0, s>>>(wv, nblocks, m, e, sizes, nullptr, none, none, nullptr,
-                                                           nullptr, status);
+                                                           nullptr, status, nullptr, nullptr, nullptr);
     count_launch();
 }
 
 void launch_size_reserve(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, uint32_t *done_ctr,
                          const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, int *status,
-                         cudaStream_t s) {
+                         cudaStream_t s, uint8_t *wrec, uint32_t *flen, uint32_t *foff) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
     k_encode_size<<<grid_for(items, 152 * 8), NT, 0, s>>>(wv, nblocks, m, e, sizes, done_ctr, dev, host, tgt, res,
-                                                           status);
+                                                           status, wrec, flen, foff);
+    count_launch();
+}
+
+void launch_encode_known(const float2 *wv, uint32_t nblocks, int m, int e, const EncTarget *tgt, EncResult *res,
+                         const uint32_t *ids, BlockSlot *table, StageAccum *acc, const uint8_t *wrec,
+                         const uint32_t *flen, const uint32_t *foff, float2 *part, uint32_t *done_ctr, int *status,
+                         cudaStream_t s) {
+    const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
+    k_encode_known<<<grid_for((items + NW - 1) / NW, 152 * 8), NT, 0, s>>>(wv, nblocks, m, e, tgt, res, ids, table, acc,
+                                                                         wrec, flen, foff, part, done_ctr, status);
     count_launch();
 }
 

@@ -76,8 +76,14 @@ void launch_encode(const float2 *wv, uint32_t nblocks, int m, int e, const EncTa
 void launch_encode_size(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, int *status,
                         cudaStream_t s);
 // sizing pass whose last CTA reserves every block's slot (sizes are left zeroed)
+// with wrec/flen/foff it also records every frame's chunk widths (256 bytes per frame), length and offset
 void launch_size_reserve(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, uint32_t *done_ctr,
                          const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, int *status,
+                         cudaStream_t s, uint8_t *wrec = nullptr, uint32_t *flen = nullptr, uint32_t *foff = nullptr);
+// exact-sizing encoder (warp per frame) using the records of launch_size_reserve
+void launch_encode_known(const float2 *wv, uint32_t nblocks, int m, int e, const EncTarget *tgt, EncResult *res,
+                         const uint32_t *ids, BlockSlot *table, StageAccum *acc, const uint8_t *wrec,
+                         const uint32_t *flen, const uint32_t *foff, float2 *part, uint32_t *done_ctr, int *status,
                          cudaStream_t s);
 // leading phase ops of a stage for the decoder (count <= kMaxPreOps)
 struct OpDev;

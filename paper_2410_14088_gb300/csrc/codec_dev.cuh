@@ -514,7 +514,7 @@ __device__ __forceinline__ void reserve_slot(uint64_t want, const ArenaDev &dev,
 // CTA; the result is returned to every thread. s_words holds NW words.
 template <bool CG = false>
 __device__ __forceinline__ uint32_t size_frame_cta(const float2 *__restrict__ src, const FrameGeom &g, int e,
-                                                   uint32_t *s_words, int *status) {
+                                                   uint32_t *s_words, int *status, uint8_t *wrec = nullptr) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float inv_step = exp2i(-e);
     float2 vin[MAX_CPW];
@@ -542,7 +542,12 @@ __device__ __forceinline__ uint32_t size_frame_cta(const float2 *__restrict__ sr
         int32_t pi = __shfl_up_sync(kFull, q[1], 1);
         const uint32_t zr = zigzag(lane ? int32_t(uint32_t(q[0]) - uint32_t(pr)) : q[0]);
         const uint32_t zi = zigzag(lane ? int32_t(uint32_t(q[1]) - uint32_t(pi)) : q[1]);
-        words += (32 - __clz(__reduce_or_sync(kFull, zr))) + (32 - __clz(__reduce_or_sync(kFull, zi)));
+        const uint32_t wr = 32 - __clz(__reduce_or_sync(kFull, zr)), wi = 32 - __clz(__reduce_or_sync(kFull, zi));
+        words += wr + wi;
+        if (wrec && lane == 0) {
+            wrec[c] = uint8_t(wr);
+            wrec[g.C + c] = uint8_t(wi);
+        }
     }
     if (bad) raise_status(status, bad);
     if (lane == 0) s_words[warp] = words;
@@ -553,6 +558,143 @@ __device__ __forceinline__ uint32_t size_frame_cta(const float2 *__restrict__ sr
     __syncthreads();
     const uint64_t padw = (2ull * g.C + 15) & ~15ull;
     return tot ? uint32_t(padw + ((4ull * tot + 15) & ~15ull)) : 0u;
+}
+
+
+// Encode frame f of one block with one warp when the frame's chunk widths
+// (wrec: 2C bytes, Re then Im, written by the sizing pass) and its byte offset
+// in the block's stream are known: no look-back and no block-wide barrier.
+// The words go straight to their place in the slot; lane 0 also writes the
+// frame's offset-table entry and, for the block's last frame, the header.
+template <bool CG = false>
+__device__ __forceinline__ void encode_frame_warp_known(const float2 *__restrict__ src, const FrameGeom &g, int m,
+                                                        int e, uint32_t f, const uint8_t *__restrict__ wrec,
+                                                        uint32_t frame_off, uint32_t len, EncTarget tgt,
+                                                        EncResult *res_j, BlockSlot *table_slot, StageAccum *acc,
+                                                        float2 *part_item, int *status) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t padw = (2u * g.C + 15u) & ~15u;
+    const float inv_step = exp2i(-e), step = exp2i(e);
+    uint8_t *out = tgt.ptr;
+    const uint64_t cap = tgt.cap;
+    const bool fits = out != nullptr && uint64_t(frame_off) + len <= cap;
+    // widths: lane l holds those of chunks 8l .. 8l+7 (bytes past 2C are masked to zero)
+    uint2 wb = make_uint2(0, 0);
+    if (8u * lane < 2u * g.C) {
+        wb = *reinterpret_cast<const uint2 *>(wrec + 8u * lane);
+        const uint32_t valid = 2u * g.C - 8u * lane;  // bytes of this lane that are widths
+        if (valid < 8) {
+            const uint64_t keep = (1ull << (8 * valid)) - 1;
+            const uint64_t v = (uint64_t(wb.y) << 32 | wb.x) & keep;
+            wb = make_uint2(uint32_t(v), uint32_t(v >> 32));
+        }
+    }
+    uint32_t wsum = 0;
+#pragma unroll
+    for (int t = 0; t < 4; ++t) wsum += ((wb.x >> (8 * t)) & 0xff) + ((wb.y >> (8 * t)) & 0xff);
+    uint32_t incl = wsum;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += t;
+    }
+    const uint32_t base_off = incl - wsum;
+    const uint32_t words = __shfl_sync(kFull, incl, 31);
+    uint32_t *payload = fits ? reinterpret_cast<uint32_t *>(out + frame_off + padw) : nullptr;
+    if (fits && len && 8u * lane < padw) *reinterpret_cast<uint2 *>(out + frame_off + 8u * lane) = wb;
+    float err_sq = 0.f, norm_sq = 0.f;
+    int bad = 0;
+    for (uint32_t c0 = 0; c0 < g.C; c0 += 8) {
+        const uint32_t lr = c0 >> 3, li = (g.C + c0) >> 3;
+        const uint2 wr8 = make_uint2(__shfl_sync(kFull, wb.x, lr), __shfl_sync(kFull, wb.y, lr));
+        const uint2 wi8 = make_uint2(__shfl_sync(kFull, wb.x, li), __shfl_sync(kFull, wb.y, li));
+        uint32_t offr = __shfl_sync(kFull, base_off, lr), offi = __shfl_sync(kFull, base_off, li);
+        const uint32_t si0 = (g.C + c0) & 7u;
+        for (uint32_t t = 0; t < si0; ++t) offi += t < 4 ? (wi8.x >> (8 * t)) & 0xff : (wi8.y >> (8 * (t - 4))) & 0xff;
+        float2 vin[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t c = c0 + t;
+            vin[t] = c < g.C ? (CG ? __ldcg(src + c * 32 + lane) : __ldcs(src + c * 32 + lane)) : make_float2(0.f, 0.f);
+        }
+        uint32_t sr_ = 0, si_ = 0;
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t c = c0 + t;
+            if (c >= g.C) break;
+            const uint32_t ti = si0 + t;
+            const uint32_t wr = t < 4 ? (wr8.x >> (8 * t)) & 0xff : (wr8.y >> (8 * (t - 4))) & 0xff;
+            const uint32_t wi = ti < 8 ? (ti < 4 ? (wi8.x >> (8 * ti)) & 0xff : (wi8.y >> (8 * (ti - 4))) & 0xff) : 0;
+            int32_t q[2];
+            const float x[2] = {vin[t].x, vin[t].y};
+#pragma unroll
+            for (int pl = 0; pl < 2; ++pl) {
+                const float tq = x[pl] * inv_step;  // exact: power-of-two scaling
+                if (!(fabsf(tq) < 1073741824.0f)) {  // NaN, Inf or out of range
+                    bad = isfinite(x[pl]) ? (bad ? bad : QSIM_E_RANGE) : QSIM_E_INVALID;
+                    q[pl] = 0;
+                } else {
+                    q[pl] = __float2int_rn(tq);
+                }
+                const float xr = float(q[pl]) * step;
+                const float dx = x[pl] - xr;
+                err_sq = fmaf(dx, dx, err_sq);
+                norm_sq = fmaf(xr, xr, norm_sq);
+            }
+            const int32_t pr = __shfl_up_sync(kFull, q[0], 1);
+            const int32_t pi = __shfl_up_sync(kFull, q[1], 1);
+            const uint32_t zr = zigzag(lane ? int32_t(uint32_t(q[0]) - uint32_t(pr)) : q[0]);
+            const uint32_t zi = zigzag(lane ? int32_t(uint32_t(q[1]) - uint32_t(pi)) : q[1]);
+            const uint32_t word_r = warp_bit_transpose(zr, lane);
+            const uint32_t word_i = warp_bit_transpose(zi, lane);
+            if (payload) {
+                if (lane < int(wr)) payload[offr + sr_ + lane] = word_r;
+                if (lane < int(wi)) payload[offi + si_ + lane] = word_i;
+            }
+            sr_ += wr;
+            si_ += wi;
+        }
+    }
+    if (payload && len && words + uint32_t(lane) < (len - padw) / 4) payload[words + lane] = 0;  // pad to 16 B
+    if (bad) raise_status(status, bad);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        err_sq += __shfl_xor_sync(kFull, err_sq, o);
+        norm_sq += __shfl_xor_sync(kFull, norm_sq, o);
+    }
+    if (lane == 0) {
+        if (part_item) *part_item = make_float2(err_sq, norm_sq);
+        if (!fits && res_j) atomicOr(&res_j->overflow, 1u);
+        if (out && g.data_start <= cap) reinterpret_cast<uint32_t *>(out + 32)[f] = frame_off;
+        if (f == g.nframes - 1) {
+            const uint64_t total = uint64_t(frame_off) + len;
+            if (res_j) res_j->total = total;
+            if (out && total <= cap) {
+                uint32_t *h32 = reinterpret_cast<uint32_t *>(out);
+                h32[0] = kQszMagic;
+                h32[1] = 1u;  // version 1, flags 0
+                h32[2] = uint32_t(m) | (uint32_t(g.fl) << 8) | (uint32_t(uint8_t(int8_t(e))) << 16);
+                h32[3] = g.nframes;
+                reinterpret_cast<uint64_t *>(out)[2] = total;
+                reinterpret_cast<uint64_t *>(out)[3] = 0;
+                h32[8 + g.nframes] = uint32_t(total);
+                for (uint64_t b = 32 + 4ull * (g.nframes + 1); b < g.data_start; ++b) out[b] = 0;
+                if (table_slot) {
+                    table_slot->ptr = out;
+                    table_slot->bytes = total;
+                    table_slot->tier = tgt.tier;
+                }
+                if (acc) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&acc->store_bytes), total);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&acc->reserved_bytes), cap);
+                    if (tgt.tier) atomicAdd(reinterpret_cast<unsigned long long *>(&acc->host_bytes), cap);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&acc->blocks), 1ull);
+                }
+            } else if (acc) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&acc->overflow_blocks), 1ull);
+            }
+        }
+    }
 }
 
 }  // namespace cdev

@@ -26,6 +26,7 @@
 #include <chrono>
 #include <cmath>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <vector>
 
@@ -158,6 +159,15 @@ static int dev_alloc(void **p, size_t bytes) {
     std::lock_guard<std::mutex> lk(c.mu);
     c.dev_live[*p] = bytes;
     return QSIM_OK;
+}
+
+// bytes of device memory held by the cache for reuse (free for a new run's sizing)
+static uint64_t cached_dev_bytes() {
+    Cache &c = cache();
+    std::lock_guard<std::mutex> lk(c.mu);
+    uint64_t b = 0;
+    for (const auto &kv : c.dev_free) b += kv.first;
+    return b;
 }
 
 static void dev_free(void *p) {
@@ -406,7 +416,7 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
             OpDev od{};
             od.type = op.type;
             od.k = op.k;
-            for (int j = 0; j < 6; ++j) od.dtile[j] = 255;
+            for (int j = 0; j < 8; ++j) od.dtile[j] = 255;
             if (op.type == OP_DIAG) {
                 for (uint32_t j = 0; j < op.k; ++j) {
                     uint32_t q = op.fq[j];
@@ -486,6 +496,27 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                             if (od.dsrc[j] < 64)
                                 for (uint32_t t = 0; t < ps.T; ++t)
                                     if (ps.tile_pos[t] == od.dsrc[j]) od.dtile[j] = t;
+                        }
+                        // phase-index bits contributed by tile bits 0..6 (128 bytes) and 7..12 (64 bytes)
+                        uint8_t lut[192];
+                        for (uint32_t v = 0; v < 192; ++v) {
+                            const bool lo = v < 128;
+                            const uint32_t x = lo ? v : v - 128;
+                            uint32_t idx = 0;
+                            for (uint32_t j = 0; j < op.k; ++j) {
+                                const uint32_t t = od.dtile[j];
+                                if (t == 255) continue;
+                                if (lo && t < 7) idx |= ((x >> t) & 1u) << j;
+                                if (!lo && t >= 7) idx |= ((x >> (t - 7)) & 1u) << j;
+                            }
+                            lut[v] = uint8_t(idx);
+                        }
+                        while (mats.size() & 1) mats.push_back(make_float2(0, 0));  // 16-byte aligned
+                        od.dlut = mats.size();
+                        for (uint32_t w = 0; w < 24; ++w) {
+                            float2 f;
+                            memcpy(&f, lut + 8 * w, 8);
+                            mats.push_back(f);
                         }
                     }
                 }
@@ -668,6 +699,8 @@ struct StreamWork {
     DevBuf<float2> part;
     DevBuf<uint32_t> hist;   // per block: 32-bin histogram of code bit lengths (decoder)
     DevBuf<float> pred;      // per block: predicted log2 stream bytes
+    DevBuf<uint8_t> wrec;    // per frame: chunk widths recorded by the sizing pass
+    DevBuf<uint32_t> flen, foff;  // per frame: stream bytes and offset
 };
 
 static StageFeatures stage_features(const qsim_plan *p, size_t si, int e) {
@@ -694,100 +727,278 @@ static StageFeatures stage_features(const qsim_plan *p, size_t si, int e) {
     return sf;
 }
 
-// Mode B: one persistent kernel per stage (optionally the whole stage loop
-// captured into a CUDA graph and launched once).
-template <class DevArenaFn, class HostArenaFn>
-static int run_stages_persistent(const qsim_plan *p, PlanDev *pd, cudaStream_t main, int e, uint64_t worst,
-                                 uint64_t nblocks, BlockSlot *tables, StageAccum *accs, uint64_t *bumps,
-                                 DevArenaFn arena_dev, HostArenaFn arena_host, int *status, Profiler &prof,
-                                 const float *pparams, int pbf16) {
+// ---------------------------------------------------------------------------
+// one circuit's run: validation, compressed store, tables and statistics
+// ---------------------------------------------------------------------------
+struct RunCtx {
+    const qsim_plan *p = nullptr;
+    PlanDev *pd = nullptr;
+    uint32_t n = 0, m = 0;
+    uint64_t nblocks = 0, nframes = 1;
+    size_t nst = 0;
+    bool raw = false, predict = false, collect = false, persistent = false;
+    int e = 0;
+    uint64_t worst = 0, slot_worst = 0;
+    uint64_t need_per_parity = 0;  // every block at its worst-case size, plus the zero template
+    uint64_t raw_need = 0;         // the same for uncompressed blocks
+    uint64_t dev_cap = 0, host_cap = 0;
+    uint8_t *dev_arena[2] = {nullptr, nullptr}, *host_arena[2] = {nullptr, nullptr};
+    uint8_t *host_arena_dev[2] = {nullptr, nullptr};
+    DevBuf<uint64_t> bumps;      // per parity: device and host bump offsets
+    DevBuf<BlockSlot> tables;    // per parity: block table
+    DevBuf<StageAccum> accs;     // per stage, then the initial store
+    DevBuf<float> log_rows;      // collect mode: predictor training rows
+    DevBuf<uint32_t> init_ids;   // initial store: the two encoded blocks
+    DevBuf<BlockSlot> tmpl;
+    uint64_t log_next = 0;
+    ArenaDev arena_dev(int parity) const {
+        ArenaDev a;
+        a.base = dev_arena[parity];
+        a.cap = dev_arena[parity] ? dev_cap : 0;
+        a.bump = bumps.p + 2 * parity;
+        return a;
+    }
+    ArenaDev arena_host(int parity) const {
+        ArenaDev a;
+        a.base = host_arena_dev[parity];
+        a.cap = host_arena[parity] ? host_cap : 0;
+        a.bump = bumps.p + 2 * parity + 1;
+        return a;
+    }
+    void free_arenas() {
+        for (int i = 0; i < 2; ++i) {
+            dev_free(dev_arena[i]);
+            host_free(host_arena[i]);
+            dev_arena[i] = host_arena[i] = host_arena_dev[i] = nullptr;
+        }
+    }
+    ~RunCtx() { free_arenas(); }
+};
+
+static uint64_t host_phys_bytes() {
+    const long pages = sysconf(_SC_PHYS_PAGES), page = sysconf(_SC_PAGE_SIZE);
+    return (pages > 0 && page > 0) ? uint64_t(pages) * uint64_t(page) : (64ull << 30);
+}
+
+static int prepare_run(RunCtx &R, const qsim_plan *p, const DeviceCtx &dctx) {
     const qsim_config &cfg = p->cfg;
-    const uint32_t m = cfg.m;
-    const uint64_t nframes = qsz_nframes(int(m));
-    uint32_t maxW = m, maxG = 1, maxT = 5, max_mat = 0, max_groups = 1;
-    for (const StageDev &sd : pd->stages) {
-        maxW = std::max(maxW, sd.W);
-        maxG = std::max(maxG, sd.G);
-        max_groups = std::max(max_groups, sd.ngroups);
+    R.p = p;
+    R.persistent = cfg.mode == QSIM_MODE_PERSISTENT;
+    if (R.persistent && cfg.codec != QSIM_CODEC_QSZ1)
+        return set_error(QSIM_E_INVALID, "persistent mode runs the compressed store (codec QSZ1)");
+    if (R.persistent && cfg.collect)
+        return set_error(QSIM_E_INVALID, "training-row collection runs in streams mode");
+    int rc = upload_plan(p, &R.pd);
+    if (rc) return rc;
+    R.n = p->n;
+    R.m = cfg.m;
+    R.nblocks = 1ull << (R.n - R.m);
+    R.nst = p->stages.size();
+    R.raw = cfg.codec == QSIM_CODEC_NONE;
+    if (!R.raw && !qsz_step_exponent(cfg.eps * std::pow(2.0, -double(R.n) / 2.0), &R.e))
+        return set_error(QSIM_E_INVALID, "error bound out of range");
+    R.predict = cfg.sizing == QSIM_SIZING_PREDICT && !R.raw;
+    R.collect = cfg.collect != 0 && !R.raw;
+    if (R.predict && !dctx.pred_ready)
+        return set_error(QSIM_E_INVALID, "predictor sizing needs trained weights (qsim_predictor_train/set)");
+    R.worst = R.raw ? (8ull << R.m) : qsz_worst_case(R.m);
+    R.slot_worst = (R.worst + 255) & ~255ull;
+    R.nframes = R.raw ? 1 : qsz_nframes(R.m);
+    R.need_per_parity = (R.nblocks + 1) * R.slot_worst;
+    R.raw_need = (R.nblocks + 1) * (((8ull << R.m) + qsz_data_start(int(R.m)) + 255) & ~255ull);
+    return QSIM_OK;
+}
+
+// Pool sizing: device arenas first (both parities within dev_budget), pinned
+// host for the rest (at most host_limit per parity). The host level is only set
+// up when the device level is capped or cannot hold a raw-sized store.
+static int alloc_run(RunCtx &R, uint64_t dev_budget, uint64_t host_limit, cudaStream_t main) {
+    const qsim_config &cfg = R.p->cfg;
+    if (cfg.device_tier_cap_bytes) dev_budget = std::min<uint64_t>(dev_budget, cfg.device_tier_cap_bytes);
+    R.dev_cap = std::min<uint64_t>(R.need_per_parity, dev_budget / 2) & ~uint64_t(255);
+    R.host_cap = 0;
+    if (R.need_per_parity > R.dev_cap && (cfg.device_tier_cap_bytes || R.raw_need > R.dev_cap)) {
+        R.host_cap = std::min<uint64_t>(R.need_per_parity - R.dev_cap, host_limit);
+        R.host_cap = (R.host_cap + 4095) & ~uint64_t(4095);
+    }
+    int rc;
+    for (int i = 0; i < 2; ++i) {
+        if (R.dev_cap && (rc = dev_alloc(reinterpret_cast<void **>(&R.dev_arena[i]), R.dev_cap))) return rc;
+        if (R.host_cap) {
+            if ((rc = host_alloc(reinterpret_cast<void **>(&R.host_arena[i]), R.host_cap))) return rc;
+            cudaError_t ce = cudaHostGetDevicePointer(reinterpret_cast<void **>(&R.host_arena_dev[i]), R.host_arena[i], 0);
+            if (ce != cudaSuccess) return set_error(QSIM_E_CUDA, "cudaHostGetDevicePointer failed");
+        }
+    }
+    if ((rc = R.bumps.alloc(4)) || (rc = R.tables.alloc(2 * R.nblocks)) || (rc = R.accs.alloc(R.nst + 1)) ||
+        (rc = R.init_ids.alloc(2)) || (rc = R.tmpl.alloc(2)) ||
+        (R.collect && (rc = R.log_rows.alloc(R.nst * R.nblocks * (kMlpIn + 1)))))
+        return rc;
+    CUDA_TRY(cudaMemsetAsync(R.bumps.p, 0, 4 * sizeof(uint64_t), main));
+    CUDA_TRY(cudaMemsetAsync(R.accs.p, 0, (R.nst + 1) * sizeof(StageAccum), main));
+    CUDA_TRY(cudaMemsetAsync(R.tables.p, 0, 2 * R.nblocks * sizeof(BlockSlot), main));
+    return QSIM_OK;
+}
+
+// Initial store (Sec. 4.2): encode the basis block and one zero block once, every
+// other block gets a copy of the zero stream. Runs on w.s; w.wv holds two blocks.
+static int init_store(RunCtx &R, StreamWork &w, int *status) {
+    const qsim_config &cfg = R.p->cfg;
+    const uint32_t m = R.m;
+    const uint32_t b0 = uint32_t(cfg.init_basis >> m);
+    const uint64_t loc = cfg.init_basis & ((1ull << m) - 1);
+    k_init_blocks<<<256, 256, 0, w.s>>>(w.wv.p, m, loc);
+    count_launch();
+    static const uint32_t h_ids[2] = {0, 1};
+    CUDA_TRY(cudaMemcpyAsync(R.init_ids.p, h_ids, sizeof(h_ids), cudaMemcpyHostToDevice, w.s));
+    // encode both blocks into slots of arena 0; tmpl[0] is the basis block, tmpl[1] the zero template
+    if (R.raw) {
+        launch_reserve(2, nullptr, R.worst, nullptr, 0, R.worst, R.arena_dev(0), R.arena_host(0), w.tgt.p, w.res.p, 0,
+                       status, w.s);
+        launch_copy_out(w.wv.p, 2, m, w.tgt.p, R.init_ids.p, R.tmpl.p, nullptr, status, w.s);
+    } else {
+        launch_size_reserve(w.wv.p, 2, m, R.e, w.sizes.p, w.lb_ctr.p + 3, R.arena_dev(0), R.arena_host(0), w.tgt.p,
+                            w.res.p, status, w.s);
+        LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p);
+        launch_encode(w.wv.p, 2, m, R.e, w.tgt.p, w.res.p, 0, R.init_ids.p, R.tmpl.p, nullptr, scr, status, w.s);
+    }
+    BlockSlot *tab0 = R.tables.p;
+    k_copy_slot<<<1, 1, 0, w.s>>>(tab0 + b0, R.tmpl.p + 0);
+    count_launch();
+    // the zero template slot stays allocated in arena 0 until stage 0 has read its copies
+    k_replicate_zero<<<unsigned(std::min<uint64_t>(R.nblocks, 152 * 8)), 128, 0, w.s>>>(
+        tab0, uint32_t(R.nblocks), b0, R.tmpl.p + 1, R.arena_dev(0), R.arena_host(0), status);
+    count_launch();
+    k_sum_table<<<64, 256, 0, w.s>>>(tab0, R.nblocks, R.accs.p + R.nst);
+    count_launch();
+    return QSIM_OK;
+}
+
+// Mode B: the persistent stage kernel over a queue of segments (one stage of
+// one circuit each). One circuit: one launch per stage (optionally the stage
+// loop captured in one CUDA graph). Several circuits: one launch for all of
+// them, stages dealt round-robin over the circuits so that one circuit's stage
+// boundary overlaps the other circuits' work.
+struct PBlockBufs {
+    DevBuf<EncTarget> tgt;
+    DevBuf<EncResult> res;
+    DevBuf<uint64_t> sizes;
+    DevBuf<uint32_t> hist;
+};
+
+static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cudaStream_t main, int *status,
+                          Profiler &prof, const DeviceCtx &dctx, uint64_t slot_budget_amps) {
+    const qsim_config &cfg0 = rs[0]->p->cfg;
+    const int prec = int(cfg0.prec);
+    // ---- segments in queue order ----
+    struct SegRef {
+        uint32_t c, si;
+    };
+    std::vector<SegRef> order;
+    size_t max_nst = 0;
+    for (const RunCtx *R : rs) max_nst = std::max(max_nst, R->nst);
+    for (size_t r = 0; r < max_nst; ++r)
+        for (uint32_t c = 0; c < rs.size(); ++c)
+            if (r < rs[c]->nst) order.push_back({c, uint32_t(r)});
+    const size_t nseg = order.size();
+    if (!nseg) return QSIM_OK;
+    std::vector<std::vector<uint32_t>> seg_of(rs.size());
+    for (uint32_t c = 0; c < rs.size(); ++c) seg_of[c].assign(rs[c]->nst, 0);
+    for (size_t k = 0; k < nseg; ++k) seg_of[order[k].c][order[k].si] = uint32_t(k);
+
+    uint64_t slot_amps = 0, slot_frames = 0, total_groups = 0;
+    uint32_t maxT = 5, max_mat = 0;
+    for (const SegRef &sr : order) {
+        const RunCtx &R = *rs[sr.c];
+        const StageDev &sd = R.pd->stages[sr.si];
+        slot_amps = std::max<uint64_t>(slot_amps, 1ull << sd.W);
+        slot_frames = std::max<uint64_t>(slot_frames, uint64_t(sd.G) * R.nframes);
+        total_groups += sd.ngroups;
         for (const PassDev &ps : sd.passes_host) {
             maxT = std::max(maxT, ps.T);
             max_mat = std::max(max_mat, ps.mat_elems);
             if (ps.kmax > 5) return set_error(QSIM_E_INVALID, "persistent mode fuses at most k = 5 qubits");
         }
     }
-    // slots: enough working vectors to overlap groups, about 256 MiB of them
-    const uint32_t R = uint32_t(std::max<uint64_t>(2, std::min<uint64_t>(max_groups, (1ull << 25) >> maxW)));
-    DevBuf<float2> wv;
-    DevBuf<uint64_t> lb, sizes;
-    DevBuf<float2> part;
-    DevBuf<EncTarget> tgt;
-    DevBuf<EncResult> res;
-    DevBuf<uint32_t> hist, sync, ctr;
+    // working-vector slots: enough to overlap groups within about slot_budget_amps amplitudes
+    uint64_t launch_groups_max = 0;
+    if (one_launch) {
+        launch_groups_max = total_groups;
+    } else {
+        for (const SegRef &sr : order)
+            launch_groups_max = std::max<uint64_t>(launch_groups_max, rs[sr.c]->pd->stages[sr.si].ngroups);
+    }
+    const uint32_t R_slots =
+        uint32_t(std::max<uint64_t>(2, std::min<uint64_t>(launch_groups_max, slot_budget_amps / slot_amps)));
+
+    std::vector<std::unique_ptr<PBlockBufs>> bb(rs.size());
     int rc;
-    if ((rc = wv.alloc((uint64_t(R) * maxG) << m)) || (rc = lb.alloc(uint64_t(R) * maxG * nframes)) ||
-        (rc = part.alloc(uint64_t(R) * maxG * nframes)) || (rc = tgt.alloc(nblocks)) || (rc = res.alloc(nblocks)) ||
-        (rc = sizes.alloc(nblocks)) || (rc = hist.alloc(pparams ? nblocks * 32 : 1)) ||
-        (rc = sync.alloc(2ull * max_groups * kMaxPhases)) || (rc = ctr.alloc(4)))
+    for (size_t c = 0; c < rs.size(); ++c) {
+        const RunCtx &R = *rs[c];
+        bb[c].reset(new PBlockBufs());
+        PBlockBufs &b = *bb[c];
+        if ((rc = b.tgt.alloc(R.nblocks)) || (rc = b.res.alloc(R.nblocks)) || (rc = b.sizes.alloc(R.nblocks)) ||
+            (R.predict && (rc = b.hist.alloc(R.nblocks * 32))))
+            return rc;
+        CUDA_TRY(cudaMemsetAsync(b.sizes.p, 0, R.nblocks * sizeof(uint64_t), main));
+        if (R.predict) CUDA_TRY(cudaMemsetAsync(b.hist.p, 0, R.nblocks * 32 * sizeof(uint32_t), main));
+    }
+    DevBuf<float2> wv, part;
+    DevBuf<uint64_t> lb;
+    DevBuf<uint32_t> sync, fin, ctr;
+    DevBuf<PSeg> dsegs;
+    if ((rc = wv.alloc(uint64_t(R_slots) * slot_amps)) || (rc = lb.alloc(uint64_t(R_slots) * slot_frames)) ||
+        (rc = part.alloc(uint64_t(R_slots) * slot_frames)) || (rc = sync.alloc(2 * total_groups * kMaxPhases)) ||
+        (rc = fin.alloc(2 * nseg)) || (rc = ctr.alloc(4)) || (rc = dsegs.alloc(nseg)))
         return rc;
     CUDA_TRY(cudaMemsetAsync(lb.p, 0, lb.n * sizeof(uint64_t), main));
+    CUDA_TRY(cudaMemsetAsync(sync.p, 0, sync.n * sizeof(uint32_t), main));
+    CUDA_TRY(cudaMemsetAsync(fin.p, 0, fin.n * sizeof(uint32_t), main));
     CUDA_TRY(cudaMemsetAsync(ctr.p, 0, 4 * sizeof(uint32_t), main));
-    const size_t smem = persistent_smem_bytes(maxT, max_mat);
-    const size_t nst = p->stages.size();
-    if ((rc = prepare_stage_persistent(int(cfg.prec), smem))) return set_error(rc, "persistent kernel set-up failed");
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
-    // the caller's stream may be the legacy default stream, which cannot be captured: capture on our own
-    cudaStream_t cs = main;
-    cudaEvent_t ev_join = nullptr;
-    if (cfg.graph) {
-        CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
-        CUDA_TRY(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
-        CUDA_TRY(cudaEventRecord(ev_join, main));
-        CUDA_TRY(cudaStreamWaitEvent(cs, ev_join, 0));
-        CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
-    }
-    auto end_capture_on_error = [&]() {
-        if (cfg.graph) {
-            cudaStreamEndCapture(cs, &graph);
-            if (graph) cudaGraphDestroy(graph);
-            cudaEventDestroy(ev_join);
-            cudaStreamDestroy(cs);
-        }
-    };
-    for (size_t si = 0; si < nst; ++si) {
-        const StageDev &sd = pd->stages[si];
+
+    // ---- segment descriptors ----
+    std::vector<PSeg> segs(nseg);
+    std::vector<uint64_t> seg_items(nseg), seg_group_off(nseg);  // group offset into the done/arrive arrays
+    uint64_t group_off = 0;
+    bool stall = false;
+    for (size_t k = 0; k < nseg; ++k) {
+        const RunCtx &R = *rs[order[k].c];
+        const size_t si = order[k].si;
+        const qsim_config &cfg = R.p->cfg;
+        const StageDev &sd = R.pd->stages[si];
         const int in_par = si & 1, out_par = (si + 1) & 1;
-        PStageArgs a{};
+        PSeg &a = segs[k];
+        memset(&a, 0, sizeof(a));
         a.W = sd.W;
         a.G = sd.G;
         a.ngroups = sd.ngroups;
-        a.R = R;
-        a.m = m;
-        a.e = e;
+        a.m = R.m;
+        a.e = R.e;
         a.npre = sd.npre;
         a.pre_begin = sd.pre_begin;
-        a.pbf16 = uint32_t(pbf16);
+        a.pbf16 = uint32_t(dctx.pred_bf16);
         uint32_t nph = 0;
-        const uint32_t gframes = sd.G * uint32_t(nframes);
+        const uint32_t gframes = sd.G * uint32_t(R.nframes);
         auto add = [&](uint32_t type, uint32_t count, uint32_t arg) {
-            a.ph[nph].type = type;
-            a.ph[nph].count = count;
-            a.ph[nph].arg = arg;
+            if (nph < uint32_t(kMaxPhases)) {
+                a.ph[nph].type = type;
+                a.ph[nph].count = count;
+                a.ph[nph].arg = arg;
+            }
             ++nph;
         };
         add(PH_DECODE, (gframes + 7) / 8, 0);
-        if (pparams) add(PH_PREDICT, 1, 0);
+        if (R.predict) add(PH_PREDICT, 1, 0);
         for (uint32_t pi = 0; pi < sd.npasses; ++pi) add(PH_PASS, 1u << sd.passes_host[pi].nout, pi);
-        if (!pparams) add(PH_SIZE, gframes, 0);
+        if (!R.predict) add(PH_SIZE, gframes, 0);
         add(PH_ENCODE, gframes, 0);
-        if (pparams) {
+        if (R.predict) {
             add(PH_FIX, 1, 0);
             add(PH_REENCODE, gframes, 0);
         }
-        if (nph > uint32_t(kMaxPhases)) {
-            end_capture_on_error();
+        // the last phase index is the group's finished flag
+        if (nph > uint32_t(kMaxPhases) - 1)
             return set_error(QSIM_E_UNSUPPORTED, "stage has too many passes for the persistent kernel");
-        }
         a.nphases = nph;
         uint32_t acc_items = 0;
         for (uint32_t t = 0; t < nph; ++t) {
@@ -795,61 +1006,112 @@ static int run_stages_persistent(const qsim_plan *p, PlanDev *pd, cudaStream_t m
             acc_items += a.ph[t].count;
         }
         a.per_group = acc_items;
-        a.passes = pd->passes.p + sd.pass_begin;
-        a.ops = pd->ops.p;
-        a.mats = pd->mats.p;
-        a.bfr = pd->bfr.p;
-        a.ids = pd->ids.p + pd->ids_off[si];
-        a.gbase = pd->gbase.p + pd->gbase_off[si];
-        a.tab_in = tables + in_par * nblocks;
-        a.tab_out = tables + out_par * nblocks;
-        a.acc = accs + si;
-        a.dev = arena_dev(out_par);
-        a.host = arena_host(out_par);
-        a.data_start = qsz_data_start(int(m));
-        a.worst = worst;
-        a.wv = wv.p;
-        a.lb = lb.p;
-        a.part = part.p;
-        a.tgt = tgt.p;
-        a.res = res.p;
-        a.sizes = sizes.p;
-        a.hist = pparams ? hist.p : nullptr;
-        a.pparams = pparams;
-        a.sf = stage_features(p, si, e);
+        seg_items[k] = uint64_t(sd.ngroups) * acc_items;
+        a.passes = R.pd->passes.p + sd.pass_begin;
+        a.ops = R.pd->ops.p;
+        a.mats = R.pd->mats.p;
+        a.bfr = R.pd->bfr.p;
+        a.ids = R.pd->ids.p + R.pd->ids_off[si];
+        a.gbase = R.pd->gbase.p + R.pd->gbase_off[si];
+        a.tab_in = R.tables.p + in_par * R.nblocks;
+        a.tab_out = R.tables.p + out_par * R.nblocks;
+        a.acc = R.accs.p + si;
+        a.dev = R.arena_dev(out_par);
+        a.host = R.arena_host(out_par);
+        a.data_start = qsz_data_start(int(R.m));
+        a.worst = R.worst;
+        PBlockBufs &b = *bb[order[k].c];
+        a.tgt = b.tgt.p;
+        a.res = b.res.p;
+        a.sizes = b.sizes.p;
+        a.hist = R.predict ? b.hist.p : nullptr;
+        a.pparams = R.predict ? dctx.pred_params : nullptr;
+        a.sf = stage_features(R.p, si, R.e);
         a.margin = cfg.predictor_margin;
-        a.done = sync.p;
-        a.arrive = sync.p + uint64_t(sd.ngroups) * nph;
-        a.ctr = ctr.p;
-        a.status = status;
         a.stall_test = (si == 0 && (cfg.reserved[0] & 1)) ? 1u : 0u;
-        a.wait_ns = a.stall_test ? 200000000ull : 2000000000ull;  // 0.2 s in the test, else 2 s
-        cudaError_t ce = cudaMemsetAsync(bumps + 2 * out_par, 0, 2 * sizeof(uint64_t), cs);
-        if (ce == cudaSuccess) ce = cudaMemsetAsync(sync.p, 0, 2ull * sd.ngroups * nph * sizeof(uint32_t), cs);
-        if (ce == cudaSuccess)
-            ce = pparams ? cudaMemsetAsync(hist.p, 0, nblocks * 32 * sizeof(uint32_t), cs)
-                         : cudaMemsetAsync(sizes.p, 0, nblocks * sizeof(uint64_t), cs);
-        if (ce != cudaSuccess) {
-            end_capture_on_error();
-            return set_error(QSIM_E_CUDA, "stage set-up: %s", cudaGetErrorString(ce));
+        stall = stall || a.stall_test;
+        a.prev_flag = (one_launch && si > 0) ? fin.p + 2 * seg_of[order[k].c][si - 1] + 1 : nullptr;
+        a.fin_count = fin.p + 2 * k;
+        a.fin_flag = fin.p + 2 * k + 1;
+        a.reset_bumps = R.bumps.p + 2 * in_par;  // the next stage writes where this one read
+        seg_group_off[k] = group_off;
+        group_off += sd.ngroups;
+    }
+    // queue positions: one launch for everything, or one launch per segment
+    {
+        uint64_t item = 0;
+        uint32_t group = 0;
+        for (size_t k = 0; k < nseg; ++k) {
+            if (!one_launch) item = 0, group = 0;
+            segs[k].item_begin = item;
+            segs[k].group_begin = group;
+            item += seg_items[k];
+            group += segs[k].ngroups;
+            if (item >= (1ull << 32)) return set_error(QSIM_E_UNSUPPORTED, "work queue longer than 2^32 items");
         }
+    }
+    CUDA_TRY(cudaMemcpyAsync(dsegs.p, segs.data(), nseg * sizeof(PSeg), cudaMemcpyHostToDevice, main));
+    const size_t smem = persistent_smem_bytes(maxT, max_mat);
+    if ((rc = prepare_stage_persistent(prec, smem))) return set_error(rc, "persistent kernel set-up failed");
+
+    PLaunch L{};
+    L.R = R_slots;
+    L.slot_amps = slot_amps;
+    L.slot_frames = slot_frames;
+    L.wv = wv.p;
+    L.lb = lb.p;
+    L.part = part.p;
+    L.ctr = ctr.p;
+    L.status = status;
+    L.wait_ns = stall ? 200000000ull : 2000000000ull;  // 0.2 s in the bounded-wait test, else 2 s
+
+    const bool graph = cfg0.graph != 0;
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    // the caller's stream may be the legacy default stream, which cannot be captured: capture on our own
+    cudaStream_t cs = main;
+    cudaEvent_t ev_join = nullptr;
+    if (graph) {
+        CUDA_TRY(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&ev_join, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventRecord(ev_join, main));
+        CUDA_TRY(cudaStreamWaitEvent(cs, ev_join, 0));
+        CUDA_TRY(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+    }
+    auto end_capture_on_error = [&]() {
+        if (graph) {
+            cudaStreamEndCapture(cs, &g);
+            if (g) cudaGraphDestroy(g);
+            cudaEventDestroy(ev_join);
+            cudaStreamDestroy(cs);
+        }
+    };
+    const size_t nlaunch = one_launch ? 1 : nseg;
+    for (size_t l = 0; l < nlaunch; ++l) {
+        const size_t k0 = one_launch ? 0 : l, k1 = one_launch ? nseg : l + 1;
+        L.segs = dsegs.p + k0;
+        L.nseg = uint32_t(k1 - k0);
+        L.total_items = segs[k1 - 1].item_begin + seg_items[k1 - 1];
+        L.total_groups = segs[k1 - 1].group_begin + segs[k1 - 1].ngroups;
+        L.done = sync.p + seg_group_off[k0] * kMaxPhases;
+        L.arrive = sync.p + (total_groups + seg_group_off[k0]) * kMaxPhases;
         prof.begin(P_STAGE, cs);
-        rc = launch_stage_persistent(a, cfg.prec, smem, cs, nullptr);
+        rc = launch_stage_persistent(L, prec, smem, cs, nullptr);
         prof.end(cs);
         if (rc) {
             end_capture_on_error();
             return set_error(rc, "persistent stage launch failed");
         }
     }
-    if (cfg.graph) {
-        cudaError_t ge = cudaStreamEndCapture(cs, &graph);
-        if (ge == cudaSuccess) ge = cudaGraphInstantiate(&exec, graph, 0);
+    if (graph) {
+        cudaError_t ge = cudaStreamEndCapture(cs, &g);
+        if (ge == cudaSuccess) ge = cudaGraphInstantiate(&exec, g, 0);
         if (ge == cudaSuccess) ge = cudaGraphLaunch(exec, cs);
         if (ge == cudaSuccess) ge = cudaEventRecord(ev_join, cs);
         if (ge == cudaSuccess) ge = cudaStreamWaitEvent(main, ev_join, 0);
         if (ge == cudaSuccess) ge = cudaStreamSynchronize(cs);
         if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
+        if (g) cudaGraphDestroy(g);
         cudaEventDestroy(ev_join);
         cudaStreamDestroy(cs);
         if (ge != cudaSuccess) return set_error(QSIM_E_CUDA, "graph: %s", cudaGetErrorString(ge));
@@ -859,361 +1121,45 @@ static int run_stages_persistent(const qsim_plan *p, PlanDev *pd, cudaStream_t m
     return QSIM_OK;
 }
 
-static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsim_stats *stats) {
-    const qsim_config &cfg = p->cfg;
-    const bool persistent = cfg.mode == QSIM_MODE_PERSISTENT;
-    if (persistent && cfg.codec != QSIM_CODEC_QSZ1)
-        return set_error(QSIM_E_INVALID, "persistent mode runs the compressed store (codec QSZ1)");
-    if (persistent && cfg.collect)
-        return set_error(QSIM_E_INVALID, "training-row collection runs in streams mode");
-    int dev;
-    CUDA_TRY(cudaGetDevice(&dev));
-    DeviceCtx &dctx = device_ctx(dev);
-    {
-        std::lock_guard<std::mutex> lk(dctx.mu);
-        int rc = ensure_device_ctx(dctx);
-        if (rc) return rc;
-    }
-    PlanDev *pd = nullptr;
-    int rc = upload_plan(p, &pd);
-    if (rc) return rc;
-
-    const uint32_t n = p->n, m = cfg.m, c = n - m;
-    const uint64_t nblocks = 1ull << c;
-    const bool raw = cfg.codec == QSIM_CODEC_NONE;
-    int e = 0;
-    if (!raw && !qsz_step_exponent(cfg.eps * std::pow(2.0, -double(n) / 2.0), &e))
-        return set_error(QSIM_E_INVALID, "error bound out of range");
-    const bool predict = cfg.sizing == QSIM_SIZING_PREDICT && !raw;
-    const bool collect = cfg.collect != 0 && !raw;
-    if (predict && !dctx.pred_ready)
-        return set_error(QSIM_E_INVALID, "predictor sizing needs trained weights (qsim_predictor_train/set)");
-    const uint64_t worst = raw ? (8ull << m) : qsz_worst_case(m);
-    const uint64_t slot_worst = (worst + 255) & ~255ull;
-    const uint64_t nframes = raw ? 1 : qsz_nframes(m);
-
-    // ---- pool sizing: device arenas first, pinned host for the rest ----
-    size_t free_b = 0, total_b = 0;
-    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
-    uint32_t maxW = m;
-    for (const StageDev &sd : pd->stages) maxW = std::max(maxW, sd.W);
-    const uint32_t nstreams = persistent ? 1 : cfg.streams;
-    const uint64_t batch_amps = std::max<uint64_t>(1ull << maxW, 1ull << 22);
-    const uint64_t work_bytes = nstreams * batch_amps * 8 * 2;
-    // every block plus the initial zero-stream template
-    const uint64_t need_per_parity = (nblocks + 1) * slot_worst;
-    uint64_t dev_budget = free_b > work_bytes ? uint64_t(0.85 * double(free_b - work_bytes)) : 0;
-    if (cfg.device_tier_cap_bytes) dev_budget = std::min<uint64_t>(dev_budget, cfg.device_tier_cap_bytes);
-    uint64_t dev_cap = std::min<uint64_t>(need_per_parity, dev_budget / 2) & ~uint64_t(255);
-    // the pinned-host level is sized by the host's memory (at most 40 % of it per stage parity); it is only
-    // set up when the device level is capped or cannot hold a raw-sized store
-    const uint64_t raw_need = (nblocks + 1) * (((8ull << m) + qsz_data_start(int(m)) + 255) & ~255ull);
-    uint64_t host_cap = 0;
-    if (need_per_parity > dev_cap && (cfg.device_tier_cap_bytes || raw_need > dev_cap)) {
-        const long pages = sysconf(_SC_PHYS_PAGES), page = sysconf(_SC_PAGE_SIZE);
-        const uint64_t host_phys = (pages > 0 && page > 0) ? uint64_t(pages) * uint64_t(page) : (64ull << 30);
-        host_cap = std::min<uint64_t>(need_per_parity - dev_cap, uint64_t(0.4 * double(host_phys)));
-        host_cap = (host_cap + 4095) & ~uint64_t(4095);
-    }
-
-    uint8_t *dev_arena[2] = {nullptr, nullptr}, *host_arena[2] = {nullptr, nullptr};
-    uint8_t *host_arena_dev[2] = {nullptr, nullptr};
-    auto cleanup = [&]() {
-        for (int i = 0; i < 2; ++i) {
-            dev_free(dev_arena[i]);
-            host_free(host_arena[i]);
-        }
-    };
-    for (int i = 0; i < 2; ++i) {
-        if (dev_cap && (rc = dev_alloc(reinterpret_cast<void **>(&dev_arena[i]), dev_cap))) { cleanup(); return rc; }
-        if (host_cap) {
-            if ((rc = host_alloc(reinterpret_cast<void **>(&host_arena[i]), host_cap))) { cleanup(); return rc; }
-            cudaError_t ce = cudaHostGetDevicePointer(reinterpret_cast<void **>(&host_arena_dev[i]), host_arena[i], 0);
-            if (ce != cudaSuccess) { cleanup(); return set_error(QSIM_E_CUDA, "cudaHostGetDevicePointer failed"); }
-        }
-    }
-    DevBuf<uint64_t> bumps;
-    DevBuf<BlockSlot> tables;
-    DevBuf<StageAccum> accs;
-    const size_t nst = p->stages.size();
-    DevBuf<float> log_rows;
-    if ((rc = bumps.alloc(4)) || (rc = tables.alloc(2 * nblocks)) || (rc = accs.alloc(nst + 1)) ||
-        (collect && (rc = log_rows.alloc(nst * nblocks * (kMlpIn + 1))))) {
-        cleanup();
-        return rc;
-    }
-    uint64_t log_next = 0;  // next logged row
-    CUDA_TRY(cudaMemsetAsync(bumps.p, 0, 4 * sizeof(uint64_t), main));
-    CUDA_TRY(cudaMemsetAsync(accs.p, 0, (nst + 1) * sizeof(StageAccum), main));
-    CUDA_TRY(cudaMemsetAsync(tables.p, 0, 2 * nblocks * sizeof(BlockSlot), main));
-    auto arena_dev = [&](int parity) {
-        ArenaDev a;
-        a.base = dev_arena[parity];
-        a.cap = dev_arena[parity] ? dev_cap : 0;
-        a.bump = bumps.p + 2 * parity;
-        return a;
-    };
-    auto arena_host = [&](int parity) {
-        ArenaDev a;
-        a.base = host_arena_dev[parity];
-        a.cap = host_arena[parity] ? host_cap : 0;
-        a.bump = bumps.p + 2 * parity + 1;
-        return a;
-    };
-
-    // ---- per-stream work buffers ----
-    std::vector<StreamWork> sw(nstreams);
-    uint64_t max_batch_blocks = 0;
-    for (const StageDev &sd : pd->stages) {
-        uint64_t gpb = std::min<uint64_t>(std::max<uint64_t>(1, batch_amps >> sd.W), 32768);
-        gpb = std::min<uint64_t>(gpb, sd.ngroups);
-        max_batch_blocks = std::max<uint64_t>(max_batch_blocks, gpb * sd.G);
-    }
-    max_batch_blocks = std::max<uint64_t>(max_batch_blocks, 2);
-    if (persistent) max_batch_blocks = 2;  // the stream buffers only serve the initial store
-    for (uint32_t i = 0; i < nstreams; ++i) {
-        StreamWork &w = sw[i];
-        CUDA_TRY(cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking));
-        CUDA_TRY(cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming));
-        if ((rc = w.wv.alloc(max_batch_blocks << m)) || (rc = w.refs.alloc(max_batch_blocks)) ||
-            (rc = w.tgt.alloc(max_batch_blocks)) || (rc = w.res.alloc(max_batch_blocks)) ||
-            (rc = w.sizes.alloc(max_batch_blocks)) || (rc = w.lb_state.alloc(max_batch_blocks * nframes)) ||
-            (rc = w.part.alloc(max_batch_blocks * nframes)) || (rc = w.hist.alloc(max_batch_blocks * 32)) ||
-            (rc = w.pred.alloc(max_batch_blocks)) ||
-            (rc = w.lb_ctr.alloc(4))) {
-            cleanup();
-            for (auto &x : sw) { if (x.s) cudaStreamDestroy(x.s); if (x.done) cudaEventDestroy(x.done); }
-            return rc;
-        }
-        CUDA_TRY(cudaMemsetAsync(w.lb_state.p, 0, max_batch_blocks * nframes * sizeof(uint64_t), main));
-        CUDA_TRY(cudaMemsetAsync(w.lb_ctr.p, 0, 4 * sizeof(uint32_t), main));
-        CUDA_TRY(cudaMemsetAsync(w.sizes.p, 0, max_batch_blocks * sizeof(uint64_t), main));
-    }
-    auto destroy_streams = [&]() {
-        for (auto &x : sw) {
-            if (x.s) cudaStreamDestroy(x.s);
-            if (x.done) cudaEventDestroy(x.done);
-        }
-    };
-    cudaEvent_t ev_start, ev_stop, ev_fork;
-    CUDA_TRY(cudaEventCreate(&ev_start));
-    CUDA_TRY(cudaEventCreate(&ev_stop));
-    CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
-    int *status = dctx.status;
-    Profiler prof;
-    prof.on = g_profile.load() != 0 && !(persistent && cfg.graph);
-    CUDA_TRY(cudaEventRecord(ev_start, main));
-
-    // ---- initial store (Sec. 4.2): encode the basis block and one zero block once ----
-    {
-        StreamWork &w = sw[0];
-        CUDA_TRY(cudaEventRecord(ev_fork, main));
-        CUDA_TRY(cudaStreamWaitEvent(w.s, ev_fork, 0));
-        const uint32_t b0 = uint32_t(cfg.init_basis >> m);
-        const uint64_t loc = cfg.init_basis & ((1ull << m) - 1);
-        k_init_blocks<<<256, 256, 0, w.s>>>(w.wv.p, m, loc);
-        count_launch();
-        BlockSlot *tab0 = tables.p;
-        DevBuf<uint32_t> init_ids;
-        DevBuf<BlockSlot> tmpl;
-        if ((rc = init_ids.alloc(2)) || (rc = tmpl.alloc(2))) { cleanup(); destroy_streams(); return rc; }
-        const uint32_t h_ids[2] = {0, 1};
-        CUDA_TRY(cudaMemcpyAsync(init_ids.p, h_ids, sizeof(h_ids), cudaMemcpyHostToDevice, w.s));
-        // encode both blocks into slots of arena 0; tmpl[0] is the basis block, tmpl[1] the zero template
-        if (raw) {
-            launch_reserve(2, nullptr, worst, nullptr, 0, worst, arena_dev(0), arena_host(0), w.tgt.p, w.res.p, 0,
-                           status, w.s);
-            launch_copy_out(w.wv.p, 2, m, w.tgt.p, init_ids.p, tmpl.p, nullptr, status, w.s);
-        } else {
-            launch_size_reserve(w.wv.p, 2, m, e, w.sizes.p, w.lb_ctr.p + 3, arena_dev(0), arena_host(0), w.tgt.p,
-                                w.res.p, status, w.s);
-            LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p);
-            launch_encode(w.wv.p, 2, m, e, w.tgt.p, w.res.p, 0, init_ids.p, tmpl.p, nullptr, scr, status, w.s);
-        }
-        k_copy_slot<<<1, 1, 0, w.s>>>(tab0 + b0, tmpl.p + 0);
-        count_launch();
-        k_replicate_zero<<<unsigned(std::min<uint64_t>(nblocks, 152 * 8)), 128, 0, w.s>>>(
-            tab0, uint32_t(nblocks), b0, tmpl.p + 1, arena_dev(0), arena_host(0), status);
-        count_launch();
-        k_sum_table<<<64, 256, 0, w.s>>>(tab0, nblocks, accs.p + nst);
-        count_launch();
-        CUDA_TRY(cudaEventRecord(w.done, w.s));
-        CUDA_TRY(cudaStreamWaitEvent(main, w.done, 0));
-        // the zero template slot stays allocated in arena 0 until stage 0 has read its copies
-        CUDA_TRY(cudaStreamSynchronize(w.s));
-    }
-
-    // ---- stage loop ----
-    if (persistent) {
-        rc = run_stages_persistent(p, pd, main, e, worst, nblocks, tables.p, accs.p, bumps.p, arena_dev, arena_host,
-                                   status, prof, predict ? dctx.pred_params : nullptr, dctx.pred_bf16);
-        if (rc) {
-            cleanup();
-            destroy_streams();
-            return rc;
-        }
-    }
-    for (size_t si = 0; si < (persistent ? 0 : nst); ++si) {
-        const StageDev &sd = pd->stages[si];
-        const int in_par = si & 1, out_par = (si + 1) & 1;
-        BlockSlot *tab_in = tables.p + in_par * nblocks;
-        BlockSlot *tab_out = tables.p + out_par * nblocks;
-        CUDA_TRY(cudaMemsetAsync(bumps.p + 2 * out_par, 0, 2 * sizeof(uint64_t), main));
-        CUDA_TRY(cudaEventRecord(ev_fork, main));
-        for (auto &w : sw) CUDA_TRY(cudaStreamWaitEvent(w.s, ev_fork, 0));
-        const uint64_t gpb = std::min<uint64_t>(std::min<uint64_t>(std::max<uint64_t>(1, batch_amps >> sd.W), 32768),
-                                                sd.ngroups);
-        const uint64_t nbatches = (sd.ngroups + gpb - 1) / gpb;
-        const uint32_t *ids_stage = pd->ids.p + pd->ids_off[si];
-        const uint64_t *gb_stage = pd->gbase.p + pd->gbase_off[si];
-        StageAccum *acc = accs.p + si;
-        StageFeatures sf{};
-        {
-            const Stage &st = p->stages[si];
-            uint32_t dense = 0, diag = 0, kmax = 0, nondiag = 0;
-            for (const Op &op : st.ops) {
-                if (op.type == OP_DENSE) { ++dense; kmax = std::max(kmax, op.k); }
-                else ++diag;
-            }
-            for (size_t gi = st.first_gate; gi < st.first_gate + st.ngates; ++gi) nondiag += p->gates[gi].diag ? 0 : 1;
-            sf.v[0] = float(m) / 32.f;
-            sf.v[1] = float(st.inner.size()) / 8.f;
-            sf.v[2] = float(dense) / 16.f;
-            sf.v[3] = float(diag) / 16.f;
-            sf.v[4] = float(kmax) / 6.f;
-            sf.v[5] = float(-e) / 64.f;
-            sf.v[6] = float(st.ngates) / 64.f;
-            sf.v[7] = st.ngates ? float(nondiag) / float(st.ngates) : 0.f;
-        }
-        for (uint64_t b = 0; b < nbatches; ++b) {
-            StreamWork &w = sw[b % nstreams];
-            const uint64_t g0 = b * gpb;
-            const uint32_t ng = uint32_t(std::min<uint64_t>(gpb, sd.ngroups - g0));
-            const uint32_t nb = ng * sd.G;
-            const uint32_t *ids = ids_stage + g0 * sd.G;
-            if (raw) {
-                prof.begin(P_GATHER, w.s);
-                launch_gather_refs(tab_in, ids, nb, w.refs.p, w.s);
-                prof.end(w.s);
-                prof.begin(P_COPY_IN, w.s);
-                launch_copy_in(w.refs.p, nb, m, w.wv.p, status, w.s);
-            } else {
-                prof.begin(P_DECODE, w.s);
-                PreOps pre;
-                pre.ops = pd->ops.p + sd.pre_begin;
-                pre.count = sd.npre;
-                pre.G = sd.G;
-                pre.mats = pd->mats.p;
-                pre.gbase = gb_stage + g0;
-                uint32_t *hist = (predict || collect) ? w.hist.p : nullptr;
-                if (hist) CUDA_TRY(cudaMemsetAsync(hist, 0, size_t(nb) * 32 * sizeof(uint32_t), w.s));
-                launch_decode_table(tab_in, ids, nb, m, w.wv.p, hist, status, pre, w.s);
-            }
-            prof.end(w.s);
-            float *log_ptr = collect ? log_rows.p + log_next * (kMlpIn + 1) : nullptr;
-            if (predict || collect) {
-                prof.begin(P_PREDICT, w.s);
-                launch_predict_sizes(w.hist.p, nb, sd.G, m, sf, predict ? dctx.pred_params : nullptr,
-                                     dctx.pred_bf16, w.pred.p, log_ptr, w.s);
-                prof.end(w.s);
-            }
-            for (uint32_t pi = 0; pi < sd.npasses; ++pi) {
-                prof.begin(P_PASS, w.s);
-                launch_pass(w.wv.p, sd.W, ng, &sd.passes_host[pi], pd->passes.p + sd.pass_begin + pi, pd->ops.p,
-                            pd->mats.p, pd->bfr.p, gb_stage + g0, cfg.prec, w.s);
-                prof.end(w.s);
-            }
-            if (raw) {
-                prof.begin(P_RESERVE, w.s);
-                launch_reserve(nb, nullptr, worst, nullptr, 0, worst, arena_dev(out_par), arena_host(out_par),
-                               w.tgt.p, w.res.p, 0, status, w.s);
-                prof.end(w.s);
-                prof.begin(P_COPY_OUT, w.s);
-                launch_copy_out(w.wv.p, nb, m, w.tgt.p, ids, tab_out, acc, status, w.s);
-                prof.end(w.s);
-            } else {
-                LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p, w.part.p);
-                if (predict) {
-                    // reserve 2^pred (1 + margin) bytes, encode once, re-encode under-estimated blocks exactly
-                    prof.begin(P_RESERVE, w.s);
-                    launch_reserve(nb, nullptr, 0, w.pred.p, cfg.predictor_margin, worst, arena_dev(out_par),
-                                   arena_host(out_par), w.tgt.p, w.res.p, 0, status, w.s);
-                    prof.end(w.s);
-                    prof.begin(P_ENCODE, w.s);
-                    launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
-                    prof.end(w.s);
-                    prof.begin(P_RESERVE, w.s);
-                    launch_reserve(nb, nullptr, 0, nullptr, 0, worst, arena_dev(out_par), arena_host(out_par),
-                                   w.tgt.p, w.res.p, 1, status, w.s);
-                    prof.end(w.s);
-                    prof.begin(P_REENCODE, w.s);
-                    launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 1, ids, tab_out, acc, scr, status, w.s);
-                    prof.end(w.s);
-                } else {
-                    prof.begin(P_ENCODE_SIZE, w.s);
-                    launch_size_reserve(w.wv.p, nb, m, e, w.sizes.p, w.lb_ctr.p + 3, arena_dev(out_par),
-                                        arena_host(out_par), w.tgt.p, w.res.p, status, w.s);
-                    prof.end(w.s);
-                    prof.begin(P_ENCODE, w.s);
-                    launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
-                    prof.end(w.s);
-                }
-                if (collect) {
-                    launch_log_targets(w.res.p, nb, m, log_ptr, w.s);
-                    log_next += nb;
-                }
-            }
-        }
-        for (auto &w : sw) {
-            CUDA_TRY(cudaEventRecord(w.done, w.s));
-            CUDA_TRY(cudaStreamWaitEvent(main, w.done, 0));
-        }
-    }
-    CUDA_TRY(cudaEventRecord(ev_stop, main));
-    CUDA_TRY(cudaEventSynchronize(ev_stop));
-    float ms = 0;
-    CUDA_TRY(cudaEventElapsedTime(&ms, ev_start, ev_stop));
-    cudaEventDestroy(ev_start);
-    cudaEventDestroy(ev_stop);
-    cudaEventDestroy(ev_fork);
-    destroy_streams();
-    int st_code = read_status(status, main);
-    if (st_code) {
-        cleanup();
-        return set_error(st_code, "qsim_run: %s", status_text(st_code));
-    }
-
+// The run's state handle and statistics (after the stream has been synchronised).
+static int finish_run(RunCtx &R, int dev, double ms, Profiler *prof, qsim_stats *stats, qsim_state **out) {
+    const qsim_plan *p = R.p;
+    PlanDev *pd = R.pd;
+    const size_t nst = R.nst;
+    const bool raw = R.raw, predict = R.predict;
+    const uint64_t nblocks = R.nblocks;
+    int rc;
     qsim_state *S = new qsim_state();
     S->device = dev;
-    S->n = n;
-    S->m = m;
-    S->codec = cfg.codec;
-    S->e = e;
+    S->n = R.n;
+    S->m = R.m;
+    S->codec = p->cfg.codec;
+    S->e = R.e;
     S->stage_acc.resize(nst + 1);
-    CUDA_TRY(cudaMemcpy(S->stage_acc.data(), accs.p, (nst + 1) * sizeof(StageAccum), cudaMemcpyDeviceToHost));
-    if (collect && log_next) {
-        S->train_rows.resize(log_next * (kMlpIn + 1));
-        CUDA_TRY(cudaMemcpy(S->train_rows.data(), log_rows.p, S->train_rows.size() * sizeof(float),
+    CUDA_TRY(cudaMemcpy(S->stage_acc.data(), R.accs.p, (nst + 1) * sizeof(StageAccum), cudaMemcpyDeviceToHost));
+    if (R.collect && R.log_next) {
+        S->train_rows.resize(R.log_next * (kMlpIn + 1));
+        CUDA_TRY(cudaMemcpy(S->train_rows.data(), R.log_rows.p, S->train_rows.size() * sizeof(float),
                             cudaMemcpyDeviceToHost));
     }
     const int fin = nst & 1;
-    S->dev_arena = dev_arena[fin];
-    S->host_arena = host_arena[fin];
-    dev_arena[fin] = nullptr;
-    host_arena[fin] = nullptr;
-    cleanup();
+    S->dev_arena = R.dev_arena[fin];
+    S->host_arena = R.host_arena[fin];
+    R.dev_arena[fin] = nullptr;
+    R.host_arena[fin] = nullptr;
+    R.free_arenas();
     if ((rc = dev_alloc(reinterpret_cast<void **>(&S->table), nblocks * sizeof(BlockSlot)))) {
         qsim_state_free(S);
         return rc;
     }
-    CUDA_TRY(cudaMemcpy(S->table, tables.p + fin * nblocks, nblocks * sizeof(BlockSlot), cudaMemcpyDeviceToDevice));
+    CUDA_TRY(cudaMemcpy(S->table, R.tables.p + fin * nblocks, nblocks * sizeof(BlockSlot), cudaMemcpyDeviceToDevice));
 
-    if (prof.on) {
+    if (prof && prof->on) {
         double secs[P_NCAT];
         uint64_t launches[P_NCAT];
-        prof.collect(secs, launches);
+        prof->collect(secs, launches);
         double bytes[P_NCAT] = {0}, flops[P_NCAT] = {0};
-        const double amps = std::ldexp(1.0, int(n));
+        const double amps = std::ldexp(1.0, int(R.n));
         for (size_t i = 0; i < nst; ++i) {
             const double in_store = double(i == 0 ? S->stage_acc[nst].store_bytes : S->stage_acc[i - 1].store_bytes);
             const double out_store = double(S->stage_acc[i].store_bytes);
@@ -1280,6 +1226,351 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
     }
     pd->counted = true;
     *out = S;
+    return QSIM_OK;
+}
+
+static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsim_stats *stats) {
+    const qsim_config &cfg = p->cfg;
+    int dev;
+    CUDA_TRY(cudaGetDevice(&dev));
+    DeviceCtx &dctx = device_ctx(dev);
+    {
+        std::lock_guard<std::mutex> lk(dctx.mu);
+        int rc = ensure_device_ctx(dctx);
+        if (rc) return rc;
+    }
+    RunCtx RC;
+    int rc = prepare_run(RC, p, dctx);
+    if (rc) return rc;
+    PlanDev *pd = RC.pd;
+    const bool persistent = RC.persistent, raw = RC.raw, predict = RC.predict, collect = RC.collect;
+    const uint32_t m = RC.m;
+    const uint64_t nblocks = RC.nblocks, nframes = RC.nframes, worst = RC.worst;
+    const int e = RC.e;
+    const size_t nst = RC.nst;
+
+    // ---- pool sizing: device arenas first, pinned host for the rest ----
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    free_b += cached_dev_bytes();  // an earlier run's cached arenas are reused or released
+    uint32_t maxW = m;
+    for (const StageDev &sd : pd->stages) maxW = std::max(maxW, sd.W);
+    const uint32_t nstreams = persistent ? 1 : cfg.streams;
+    const uint64_t batch_amps = std::max<uint64_t>(1ull << maxW, 1ull << 22);
+    const uint64_t work_bytes = nstreams * batch_amps * 8 * 2;
+    const uint64_t dev_budget = free_b > work_bytes ? uint64_t(0.85 * double(free_b - work_bytes)) : 0;
+    // the pinned-host level holds at most 30 % of the host's memory per stage parity
+    if ((rc = alloc_run(RC, dev_budget, uint64_t(0.3 * double(host_phys_bytes())), main))) return rc;
+    auto arena_dev = [&](int parity) { return RC.arena_dev(parity); };
+    auto arena_host = [&](int parity) { return RC.arena_host(parity); };
+    BlockSlot *const tables_p = RC.tables.p;
+    StageAccum *const accs_p = RC.accs.p;
+    uint64_t *const bumps_p = RC.bumps.p;
+
+    // ---- per-stream work buffers ----
+    std::vector<StreamWork> sw(nstreams);
+    uint64_t max_batch_blocks = 0;
+    for (const StageDev &sd : pd->stages) {
+        uint64_t gpb = std::min<uint64_t>(std::max<uint64_t>(1, batch_amps >> sd.W), 32768);
+        gpb = std::min<uint64_t>(gpb, sd.ngroups);
+        max_batch_blocks = std::max<uint64_t>(max_batch_blocks, gpb * sd.G);
+    }
+    max_batch_blocks = std::max<uint64_t>(max_batch_blocks, 2);
+    if (persistent) max_batch_blocks = 2;  // the stream buffers only serve the initial store
+    auto destroy_streams = [&]() {
+        for (auto &x : sw) {
+            if (x.s) cudaStreamDestroy(x.s);
+            if (x.done) cudaEventDestroy(x.done);
+            x.s = nullptr;
+            x.done = nullptr;
+        }
+    };
+    for (uint32_t i = 0; i < nstreams; ++i) {
+        StreamWork &w = sw[i];
+        CUDA_TRY(cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking));
+        CUDA_TRY(cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming));
+        if ((rc = w.wv.alloc(max_batch_blocks << m)) || (rc = w.refs.alloc(max_batch_blocks)) ||
+            (rc = w.tgt.alloc(max_batch_blocks)) || (rc = w.res.alloc(max_batch_blocks)) ||
+            (rc = w.sizes.alloc(max_batch_blocks)) || (rc = w.lb_state.alloc(max_batch_blocks * nframes)) ||
+            (rc = w.part.alloc(max_batch_blocks * nframes)) || (rc = w.hist.alloc(max_batch_blocks * 32)) ||
+            (rc = w.pred.alloc(max_batch_blocks)) ||
+            (!persistent && (rc = w.wrec.alloc(max_batch_blocks * nframes * 256))) ||
+            (rc = w.flen.alloc(max_batch_blocks * nframes)) || (rc = w.foff.alloc(max_batch_blocks * nframes)) ||
+            (rc = w.lb_ctr.alloc(4))) {
+            destroy_streams();
+            return rc;
+        }
+        CUDA_TRY(cudaMemsetAsync(w.lb_state.p, 0, max_batch_blocks * nframes * sizeof(uint64_t), main));
+        CUDA_TRY(cudaMemsetAsync(w.lb_ctr.p, 0, 4 * sizeof(uint32_t), main));
+        CUDA_TRY(cudaMemsetAsync(w.sizes.p, 0, max_batch_blocks * sizeof(uint64_t), main));
+    }
+    cudaEvent_t ev_start, ev_stop, ev_fork;
+    CUDA_TRY(cudaEventCreate(&ev_start));
+    CUDA_TRY(cudaEventCreate(&ev_stop));
+    CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
+    int *status = dctx.status;
+    Profiler prof;
+    prof.on = g_profile.load() != 0 && !(persistent && cfg.graph);
+    CUDA_TRY(cudaEventRecord(ev_start, main));
+
+    // ---- initial store ----
+    {
+        StreamWork &w = sw[0];
+        CUDA_TRY(cudaEventRecord(ev_fork, main));
+        CUDA_TRY(cudaStreamWaitEvent(w.s, ev_fork, 0));
+        if ((rc = init_store(RC, w, status))) {
+            destroy_streams();
+            return rc;
+        }
+        CUDA_TRY(cudaEventRecord(w.done, w.s));
+        CUDA_TRY(cudaStreamWaitEvent(main, w.done, 0));
+    }
+
+    // ---- stage loop ----
+    if (persistent) {
+        std::vector<RunCtx *> one{&RC};
+        rc = run_persistent(one, false, main, status, prof, dctx, 1ull << 25);
+        if (rc) {
+            destroy_streams();
+            return rc;
+        }
+    }
+    for (size_t si = 0; si < (persistent ? 0 : nst); ++si) {
+        const StageDev &sd = pd->stages[si];
+        const int in_par = si & 1, out_par = (si + 1) & 1;
+        BlockSlot *tab_in = tables_p + in_par * nblocks;
+        BlockSlot *tab_out = tables_p + out_par * nblocks;
+        CUDA_TRY(cudaMemsetAsync(bumps_p + 2 * out_par, 0, 2 * sizeof(uint64_t), main));
+        CUDA_TRY(cudaEventRecord(ev_fork, main));
+        for (auto &w : sw) CUDA_TRY(cudaStreamWaitEvent(w.s, ev_fork, 0));
+        const uint64_t gpb = std::min<uint64_t>(std::min<uint64_t>(std::max<uint64_t>(1, batch_amps >> sd.W), 32768),
+                                                sd.ngroups);
+        const uint64_t nbatches = (sd.ngroups + gpb - 1) / gpb;
+        const uint32_t *ids_stage = pd->ids.p + pd->ids_off[si];
+        const uint64_t *gb_stage = pd->gbase.p + pd->gbase_off[si];
+        StageAccum *acc = accs_p + si;
+        StageFeatures sf{};
+        {
+            const Stage &st = p->stages[si];
+            uint32_t dense = 0, diag = 0, kmax = 0, nondiag = 0;
+            for (const Op &op : st.ops) {
+                if (op.type == OP_DENSE) { ++dense; kmax = std::max(kmax, op.k); }
+                else ++diag;
+            }
+            for (size_t gi = st.first_gate; gi < st.first_gate + st.ngates; ++gi) nondiag += p->gates[gi].diag ? 0 : 1;
+            sf.v[0] = float(m) / 32.f;
+            sf.v[1] = float(st.inner.size()) / 8.f;
+            sf.v[2] = float(dense) / 16.f;
+            sf.v[3] = float(diag) / 16.f;
+            sf.v[4] = float(kmax) / 6.f;
+            sf.v[5] = float(-e) / 64.f;
+            sf.v[6] = float(st.ngates) / 64.f;
+            sf.v[7] = st.ngates ? float(nondiag) / float(st.ngates) : 0.f;
+        }
+        for (uint64_t b = 0; b < nbatches; ++b) {
+            StreamWork &w = sw[b % nstreams];
+            const uint64_t g0 = b * gpb;
+            const uint32_t ng = uint32_t(std::min<uint64_t>(gpb, sd.ngroups - g0));
+            const uint32_t nb = ng * sd.G;
+            const uint32_t *ids = ids_stage + g0 * sd.G;
+            if (raw) {
+                prof.begin(P_GATHER, w.s);
+                launch_gather_refs(tab_in, ids, nb, w.refs.p, w.s);
+                prof.end(w.s);
+                prof.begin(P_COPY_IN, w.s);
+                launch_copy_in(w.refs.p, nb, m, w.wv.p, status, w.s);
+            } else {
+                prof.begin(P_DECODE, w.s);
+                PreOps pre;
+                pre.ops = pd->ops.p + sd.pre_begin;
+                pre.count = sd.npre;
+                pre.G = sd.G;
+                pre.mats = pd->mats.p;
+                pre.gbase = gb_stage + g0;
+                uint32_t *hist = (predict || collect) ? w.hist.p : nullptr;
+                if (hist) CUDA_TRY(cudaMemsetAsync(hist, 0, size_t(nb) * 32 * sizeof(uint32_t), w.s));
+                launch_decode_table(tab_in, ids, nb, m, w.wv.p, hist, status, pre, w.s);
+            }
+            prof.end(w.s);
+            float *log_ptr = collect ? RC.log_rows.p + RC.log_next * (kMlpIn + 1) : nullptr;
+            if (predict || collect) {
+                prof.begin(P_PREDICT, w.s);
+                launch_predict_sizes(w.hist.p, nb, sd.G, m, sf, predict ? dctx.pred_params : nullptr,
+                                     dctx.pred_bf16, w.pred.p, log_ptr, w.s);
+                prof.end(w.s);
+            }
+            for (uint32_t pi = 0; pi < sd.npasses; ++pi) {
+                prof.begin(P_PASS, w.s);
+                launch_pass(w.wv.p, sd.W, ng, &sd.passes_host[pi], pd->passes.p + sd.pass_begin + pi, pd->ops.p,
+                            pd->mats.p, pd->bfr.p, gb_stage + g0, cfg.prec, w.s);
+                prof.end(w.s);
+            }
+            if (raw) {
+                prof.begin(P_RESERVE, w.s);
+                launch_reserve(nb, nullptr, worst, nullptr, 0, worst, arena_dev(out_par), arena_host(out_par),
+                               w.tgt.p, w.res.p, 0, status, w.s);
+                prof.end(w.s);
+                prof.begin(P_COPY_OUT, w.s);
+                launch_copy_out(w.wv.p, nb, m, w.tgt.p, ids, tab_out, acc, status, w.s);
+                prof.end(w.s);
+            } else {
+                LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p, w.part.p);
+                if (predict) {
+                    // reserve 2^pred (1 + margin) bytes, encode once, re-encode under-estimated blocks exactly
+                    prof.begin(P_RESERVE, w.s);
+                    launch_reserve(nb, nullptr, 0, w.pred.p, cfg.predictor_margin, worst, arena_dev(out_par),
+                                   arena_host(out_par), w.tgt.p, w.res.p, 0, status, w.s);
+                    prof.end(w.s);
+                    prof.begin(P_ENCODE, w.s);
+                    launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
+                    prof.end(w.s);
+                    prof.begin(P_RESERVE, w.s);
+                    launch_reserve(nb, nullptr, 0, nullptr, 0, worst, arena_dev(out_par), arena_host(out_par),
+                                   w.tgt.p, w.res.p, 1, status, w.s);
+                    prof.end(w.s);
+                    prof.begin(P_REENCODE, w.s);
+                    launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 1, ids, tab_out, acc, scr, status, w.s);
+                    prof.end(w.s);
+                } else {
+                    prof.begin(P_ENCODE_SIZE, w.s);
+                    launch_size_reserve(w.wv.p, nb, m, e, w.sizes.p, w.lb_ctr.p + 3, arena_dev(out_par),
+                                        arena_host(out_par), w.tgt.p, w.res.p, status, w.s, w.wrec.p, w.flen.p,
+                                        w.foff.p);
+                    prof.end(w.s);
+                    prof.begin(P_ENCODE, w.s);
+                    launch_encode_known(w.wv.p, nb, m, e, w.tgt.p, w.res.p, ids, tab_out, acc, w.wrec.p, w.flen.p,
+                                        w.foff.p, w.part.p, w.lb_ctr.p + 1, status, w.s);
+                    prof.end(w.s);
+                }
+                if (collect) {
+                    launch_log_targets(w.res.p, nb, m, log_ptr, w.s);
+                    RC.log_next += nb;
+                }
+            }
+        }
+        for (auto &w : sw) {
+            CUDA_TRY(cudaEventRecord(w.done, w.s));
+            CUDA_TRY(cudaStreamWaitEvent(main, w.done, 0));
+        }
+    }
+    CUDA_TRY(cudaEventRecord(ev_stop, main));
+    CUDA_TRY(cudaEventSynchronize(ev_stop));
+    float ms = 0;
+    CUDA_TRY(cudaEventElapsedTime(&ms, ev_start, ev_stop));
+    cudaEventDestroy(ev_start);
+    cudaEventDestroy(ev_stop);
+    cudaEventDestroy(ev_fork);
+    destroy_streams();
+    int st_code = read_status(status, main);
+    if (st_code) return set_error(st_code, "qsim_run: %s", status_text(st_code));
+    return finish_run(RC, dev, ms, &prof, stats, out);
+}
+
+// A batch of circuits: initial stores, then one persistent launch over every
+// stage of every circuit.
+static int run_batch(const qsim_plan *const *plans, size_t count, cudaStream_t main, qsim_state **out,
+                     qsim_stats *stats, qsim_kernel_stat *launch_stat) {
+    int dev;
+    CUDA_TRY(cudaGetDevice(&dev));
+    DeviceCtx &dctx = device_ctx(dev);
+    {
+        std::lock_guard<std::mutex> lk(dctx.mu);
+        int rc = ensure_device_ctx(dctx);
+        if (rc) return rc;
+    }
+    std::vector<std::unique_ptr<RunCtx>> rs(count);
+    std::vector<RunCtx *> rp(count);
+    int rc;
+    uint64_t slot_amps = 0, sum_need = 0;
+    uint32_t mmax = 0;
+    for (size_t c = 0; c < count; ++c) {
+        const qsim_plan *p = plans[c];
+        if (!p) return set_error(QSIM_E_INVALID, "batch entry %zu is null", c);
+        const qsim_config &cfg = p->cfg;
+        if (cfg.codec != QSIM_CODEC_QSZ1 || cfg.collect)
+            return set_error(QSIM_E_INVALID, "batch entry %zu: a batch runs the compressed store without row collection",
+                             c);
+        if (cfg.prec != plans[0]->cfg.prec)
+            return set_error(QSIM_E_INVALID, "batch entry %zu: every circuit of a batch uses the same precision", c);
+        rs[c].reset(new RunCtx());
+        rp[c] = rs[c].get();
+        if ((rc = prepare_run(*rs[c], p, dctx))) return rc;
+        for (const StageDev &sd : rs[c]->pd->stages) slot_amps = std::max<uint64_t>(slot_amps, 1ull << sd.W);
+        sum_need += rs[c]->need_per_parity;
+        mmax = std::max(mmax, rs[c]->m);
+    }
+    const uint64_t slot_budget = 1ull << 27;  // working-vector slots of the launch: about 1 GiB
+    size_t free_b = 0, total_b = 0;
+    CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
+    free_b += cached_dev_bytes();
+    const uint64_t work_bytes = std::max<uint64_t>(2 * slot_amps, slot_budget) * 8 * 2 + (16ull << (mmax + 1));
+    const double dev_budget = free_b > work_bytes ? 0.85 * double(free_b - work_bytes) : 0.0;
+    const double host_budget = 0.3 * double(host_phys_bytes());
+    // each circuit's share of both levels follows its worst-case need
+    for (size_t c = 0; c < count; ++c) {
+        const double f = double(rs[c]->need_per_parity) / double(sum_need);
+        if ((rc = alloc_run(*rs[c], uint64_t(dev_budget * f), uint64_t(host_budget * f), main))) return rc;
+    }
+    StreamWork w;
+    const uint64_t nframes_max = qsz_nframes(int(mmax));
+    if ((rc = w.wv.alloc(2ull << mmax)) || (rc = w.tgt.alloc(2)) || (rc = w.res.alloc(2)) || (rc = w.sizes.alloc(2)) ||
+        (rc = w.lb_state.alloc(2 * nframes_max)) || (rc = w.lb_ctr.alloc(4)))
+        return rc;
+    CUDA_TRY(cudaMemsetAsync(w.lb_state.p, 0, 2 * nframes_max * sizeof(uint64_t), main));
+    CUDA_TRY(cudaMemsetAsync(w.lb_ctr.p, 0, 4 * sizeof(uint32_t), main));
+    CUDA_TRY(cudaMemsetAsync(w.sizes.p, 0, 2 * sizeof(uint64_t), main));
+    w.s = main;  // the initial stores run on the caller's stream, one after another
+    cudaEvent_t ev_start, ev_stop;
+    CUDA_TRY(cudaEventCreate(&ev_start));
+    CUDA_TRY(cudaEventCreate(&ev_stop));
+    int *status = dctx.status;
+    Profiler prof;
+    prof.on = (g_profile.load() != 0 || launch_stat) && !plans[0]->cfg.graph;
+    CUDA_TRY(cudaEventRecord(ev_start, main));
+    for (size_t c = 0; c < count && !rc; ++c) rc = init_store(*rs[c], w, status);
+    w.s = nullptr;  // not ours to destroy
+    if (rc) return rc;
+    if ((rc = run_persistent(rp, true, main, status, prof, dctx, slot_budget))) return rc;
+    CUDA_TRY(cudaEventRecord(ev_stop, main));
+    CUDA_TRY(cudaEventSynchronize(ev_stop));
+    float ms = 0;
+    CUDA_TRY(cudaEventElapsedTime(&ms, ev_start, ev_stop));
+    cudaEventDestroy(ev_start);
+    cudaEventDestroy(ev_stop);
+    int st_code = read_status(status, main);
+    if (st_code) return set_error(st_code, "qsim_run_batch: %s", status_text(st_code));
+    double alg_bytes = 0, alg_flops = 0;
+    for (size_t c = 0; c < count; ++c) {
+        if ((rc = finish_run(*rs[c], dev, ms, nullptr, stats ? stats + c : nullptr, out + c))) {
+            for (size_t d = 0; d < c; ++d) {
+                qsim_state_free(out[d]);
+                out[d] = nullptr;
+            }
+            return rc;
+        }
+        const RunCtx &R = *rs[c];
+        const qsim_state *S = out[c];
+        const double amps = std::ldexp(1.0, int(R.n));
+        for (size_t i = 0; i < R.nst; ++i) {
+            const double in_store = double(i == 0 ? S->stage_acc[R.nst].store_bytes : S->stage_acc[i - 1].store_bytes);
+            const double out_store = double(S->stage_acc[i].store_bytes);
+            alg_bytes += in_store + out_store + 8 * amps * (2 + (R.predict ? 0 : 1)) +
+                         16 * amps * R.pd->stages[i].npasses;
+            for (const Op &op : R.p->stages[i].ops)
+                alg_flops += (op.type == OP_DENSE ? 8.0 * double(1u << op.k) : op.type == OP_DIAG ? 6.0 : 0.0) * amps;
+        }
+    }
+    if (launch_stat) {
+        memset(launch_stat, 0, sizeof(*launch_stat));
+        snprintf(launch_stat->name, sizeof(launch_stat->name), "%s", kProfNames[P_STAGE]);
+        double secs[P_NCAT];
+        uint64_t launches[P_NCAT];
+        prof.collect(secs, launches);
+        launch_stat->launches = launches[P_STAGE];
+        launch_stat->seconds = secs[P_STAGE];
+        launch_stat->alg_bytes = alg_bytes;
+        launch_stat->alg_flops = alg_flops;
+    }
     return QSIM_OK;
 }
 
@@ -1421,6 +1712,19 @@ int qsim_run(const qsim_plan *plan, void *cuda_stream, qsim_state **out, qsim_st
         return set_error(QSIM_E_NOMEM, "host allocation failed");
     } catch (...) {
         return set_error(QSIM_E_CUDA, "run failed");
+    }
+}
+
+int qsim_run_batch(const qsim_plan *const *plans, size_t count, void *cuda_stream, qsim_state **states,
+                   qsim_stats *stats, qsim_kernel_stat *launch) {
+    if (!plans || !states || count == 0) return set_error(QSIM_E_INVALID, "empty batch or null argument");
+    for (size_t c = 0; c < count; ++c) states[c] = nullptr;
+    try {
+        return run_batch(plans, count, static_cast<cudaStream_t>(cuda_stream), states, stats, launch);
+    } catch (const std::bad_alloc &) {
+        return set_error(QSIM_E_NOMEM, "host allocation failed");
+    } catch (...) {
+        return set_error(QSIM_E_CUDA, "batch run failed");
     }
 }
 

@@ -25,14 +25,14 @@ struct PassDev {
     uint32_t out_pos[32];    // working bit of CTA-index bit t
 };
 
-struct OpDev {
+struct __align__(16) OpDev {
     uint32_t type;           // 0 dense, 1 diagonal, 2 phase flip
     uint32_t k;
     uint32_t mat;            // float2 offset of the matrix (dense) or phases (diag)
-    uint32_t pad0;
+    uint32_t dlut;           // diag in a pass: float2 offset of its 192 phase-index bytes (see PassSmem)
     uint32_t tq[6];          // dense: tile bit of matrix bit j
-    uint32_t dsrc[6];        // diag: working bit (< 64) or 64 + full qubit (outer, from group base)
-    uint32_t dtile[6];       // diag in a pass: tile bit of qubit j, or 255 when the bit is constant over a tile
+    uint32_t dsrc[8];        // diag: working bit (< 64) or 64 + full qubit (outer, from group base)
+    uint32_t dtile[8];       // diag in a pass: tile bit of qubit j, or 255 when the bit is constant over a tile
     uint32_t comp[16];       // dense: complement tile bits; comp[0..3] feed the lane bits
     uint64_t basis_outer;    // phase flip: basis & outer mask (full index bits)
     uint64_t basis_w;        // phase flip: working index of the basis state

@@ -4,6 +4,7 @@
 
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include "codec.cuh"
@@ -18,15 +19,26 @@ __device__ __forceinline__ uint32_t swz(uint32_t i) {
     return i ^ (((i >> 4) ^ (i >> 8) ^ (i >> 12)) & 15u);
 }
 
+// CTA-cooperative copy of a descriptor (4-byte words)
+template <int NT, class T>
+__device__ __forceinline__ void coop_copy(T &dst, const T *__restrict__ src) {
+    static_assert(sizeof(T) % 4 == 0, "descriptor size");
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    uint32_t *d = reinterpret_cast<uint32_t *>(&dst);
+    for (int t = threadIdx.x; t < int(sizeof(T) / 4); t += NT) d[t] = __ldg(s + t);
+}
+
 struct PassSmem {
     PassDev p;
     OpDev op;
     uint32_t hi[256];
     uint32_t offs[64];
     uint8_t dlut_lo[128];  // diagonal op: phase-index bits contributed by tile bits 0..6
-    uint8_t dlut_hi[64];   // and by tile bits 7..12
+    uint8_t dlut_hi[64];   // and by tile bits 7..12 (directly after dlut_lo)
     uint32_t dconst;       // and by the bits that are constant over the tile
 };
+static_assert(offsetof(PassSmem, dlut_hi) == offsetof(PassSmem, dlut_lo) + 128 && offsetof(PassSmem, dlut_lo) % 4 == 0,
+              "the phase-index tables are copied as one 192-byte run of words");
 
 template <int NT, int K>
 __device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const PassSmem &S, uint32_t T) {
@@ -294,7 +306,7 @@ __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev 
                                           const uint32_t *__restrict__ bfr, uint64_t cta, uint64_t gb, PassSmem &S,
                                           float2 *tile) {
     const int tid = threadIdx.x;
-    if (tid == 0) S.p = *pd;
+    coop_copy<NT>(S.p, pd);
     __syncthreads();
     const uint32_t T = S.p.T, L = S.p.L, nout = S.p.nout;
     float2 *mat = tile + (1u << T);
@@ -329,12 +341,15 @@ __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev 
     }
     for (uint32_t oi = 0; oi < S.p.op_count; ++oi) {
         __syncthreads();
-        if (tid == 0) S.op = ops[S.p.op_begin + oi];
+        coop_copy<NT>(S.op, ops + S.p.op_begin + oi);
         __syncthreads();
         const uint32_t type = S.op.type, k = S.op.k;
         if (type == OP_DENSE) {
             const uint32_t D = 1u << k;
-            for (uint32_t i = tid; i < D * D; i += NT) mat[i] = mats[S.op.mat + i];
+            // the tensor-core form reads the op's B-fragment table instead of the matrix
+            const bool tc = PREC != QSIM_PREC_FP32 && k >= (PREC == QSIM_PREC_TF32 ? 3u : 4u) && k <= 5 && T == 12;
+            if (!tc)
+                for (uint32_t i = tid; i < D * D; i += NT) mat[i] = mats[S.op.mat + i];
             if (tid < int(D)) {
                 uint32_t o = 0;
                 for (uint32_t j = 0; j < k; ++j) o |= ((uint32_t(tid) >> j) & 1u) << S.op.tq[j];
@@ -346,19 +361,9 @@ __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev 
             // phase index = bits constant over the tile | lookups over the tile bits
             const uint32_t D = 1u << k;
             for (uint32_t i = tid; i < D; i += NT) mat[i] = mats[S.op.mat + i];
-            for (uint32_t v = tid; v < 192; v += NT) {
-                const bool lo = v < 128;
-                const uint32_t x = lo ? v : v - 128;
-                uint32_t idx = 0;
-                for (uint32_t j = 0; j < k; ++j) {
-                    const uint32_t t = S.op.dtile[j];
-                    if (t == 255) continue;
-                    if (lo && t < 7) idx |= ((x >> t) & 1u) << j;
-                    if (!lo && t >= 7) idx |= ((x >> (t - 7)) & 1u) << j;
-                }
-                if (lo) S.dlut_lo[x] = uint8_t(idx);
-                else S.dlut_hi[x] = uint8_t(idx);
-            }
+            if (tid < 48)  // the host-built phase-index tables, 192 bytes
+                reinterpret_cast<uint32_t *>(S.dlut_lo)[tid] =
+                    __ldg(reinterpret_cast<const uint32_t *>(mats + S.op.dlut) + tid);
             if (tid == 0) {
                 uint32_t idx = 0;
                 for (uint32_t j = 0; j < k; ++j) {

@@ -52,132 +52,169 @@ __device__ __forceinline__ EncTarget load_target(const EncTarget *t) {
 }
 
 template <int PREC>
-__global__ void __launch_bounds__(PT, 2) k_stage_persistent(PStageArgs A) {
+__global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
     extern __shared__ float4 dsm[];
     __shared__ gdev::PassSmem PS;
     __shared__ cdev::EncSmem SE;
     __shared__ OpDev s_pre[kMaxPreOps];
+    __shared__ __align__(16) PSeg S;
     __shared__ uint32_t s_hist[PT / 32][32];
     __shared__ uint32_t s_words[PT / 32];
-    __shared__ uint32_t s_item, s_epoch;
+    __shared__ uint32_t s_item, s_epoch, s_seg, s_next;
     __shared__ int s_flag;
     const int tid = threadIdx.x, warp = tid >> 5;
-    if (tid < int(A.npre)) s_pre[tid] = A.ops[A.pre_begin + tid];
-    if (tid == 0) s_epoch = ld_relaxed_u32(A.ctr + 2) & cdev::kEpochMask;
+    if (tid == 0) {
+        s_epoch = ld_relaxed_u32(L.ctr + 2) & cdev::kEpochMask;
+        s_seg = ~0u;
+    }
     __syncthreads();
-    const FrameGeom g = geom(int(A.m));
-    const uint32_t nph = A.nphases;
-    const uint64_t total = uint64_t(A.ngroups) * A.per_group;
-    const uint32_t gframes = A.G * g.nframes;
 
     while (true) {
-        if (tid == 0) s_item = atomicAdd(A.ctr, 1u);
+        if (tid == 0) {
+            s_item = atomicAdd(L.ctr, 1u);
+            // the segment holding the item: last one with item_begin <= item
+            uint32_t lo = 0, hi = L.nseg - 1;
+            if (s_item < L.total_items) {
+                while (lo < hi) {
+                    const uint32_t mid = (lo + hi + 1) >> 1;
+                    if (__ldg(reinterpret_cast<const unsigned long long *>(&L.segs[mid].item_begin)) <= s_item)
+                        lo = mid;
+                    else
+                        hi = mid - 1;
+                }
+            }
+            s_next = lo;
+        }
         __syncthreads();
         const uint32_t item = s_item;
-        if (item >= total) break;
-        const uint32_t grp = item / A.per_group, r = item % A.per_group;
+        if (item >= L.total_items) break;
+        const uint32_t want = s_next;
+        if (want != s_seg) {  // uniform: a new segment, load its descriptor and leading phase ops
+            __syncthreads();
+            const unsigned long long *src = reinterpret_cast<const unsigned long long *>(L.segs + want);
+            unsigned long long *dst = reinterpret_cast<unsigned long long *>(&S);
+            for (int t = tid; t < int(sizeof(PSeg) / 8); t += PT) dst[t] = __ldg(src + t);
+            __syncthreads();
+            if (tid < int(S.npre)) s_pre[tid] = S.ops[S.pre_begin + tid];
+            if (tid == 0) s_seg = want;
+            __syncthreads();
+        }
+        const FrameGeom g = geom(int(S.m));
+        const uint32_t nph = S.nphases;
+        const uint32_t gframes = S.G * g.nframes;
+        const uint32_t rel = uint32_t(item - S.item_begin);
+        const uint32_t grp = rel / S.per_group, r = rel % S.per_group;
+        const uint32_t q = S.group_begin + grp;  // the group's number in this launch
         uint32_t p = 0;
-        while (p + 1 < nph && r >= A.ph_start[p + 1]) ++p;
-        const uint32_t i = r - A.ph_start[p];
-        const uint32_t type = A.ph[p].type;
-        // ---- dependency: the group's previous phase, or the slot's previous group ----
+        while (p + 1 < nph && r >= S.ph_start[p + 1]) ++p;
+        const uint32_t i = r - S.ph_start[p];
+        const uint32_t type = S.ph[p].type;
+        // ---- dependencies: the group's previous phase; for its first phase the
+        // slot's previous group and the circuit's previous stage ----
         if (tid == 0) {
-            const uint32_t *flag = nullptr;
+            const uint32_t *flag = nullptr, *flag2 = nullptr;
             uint32_t need = 0;
             if (p > 0) {
-                flag = A.done + uint64_t(grp) * nph + p - 1;
-                need = A.ph[p - 1].count;
-            } else if (grp >= A.R) {
-                flag = A.done + uint64_t(grp - A.R) * nph + nph - 1;
-                need = A.ph[nph - 1].count;
+                flag = L.done + uint64_t(q) * kMaxPhases + p - 1;
+                need = S.ph[p - 1].count;
+            } else {
+                if (q >= L.R) {
+                    flag = L.done + uint64_t(q - L.R) * kMaxPhases + kMaxPhases - 1;
+                    need = 1;
+                }
+                flag2 = S.prev_flag;
             }
-            if (A.stall_test && grp == 0 && p == 1) ++need;  // never reached: exercises the time limit
-            if (flag) {
+            if (S.stall_test && grp == 0 && p == 1) ++need;  // never reached: exercises the time limit
+            if (flag || flag2) {
                 const uint64_t t0 = global_ns();
-                while (ld_acquire_u32(flag) < need) {
-                    if (global_ns() - t0 > A.wait_ns) {
-                        raise_status(A.status, QSIM_E_TIMEOUT);
+                while ((flag && ld_acquire_u32(flag) < need) || (flag2 && ld_acquire_u32(flag2) == 0)) {
+                    if (global_ns() - t0 > L.wait_ns) {
+                        raise_status(L.status, QSIM_E_TIMEOUT);
                         break;
                     }
                     __nanosleep(256);
                 }
             }
             // after any device error the remaining items only keep the schedule going
-            s_flag = ld_relaxed_u32(reinterpret_cast<const uint32_t *>(A.status)) != 0;
+            s_flag = ld_relaxed_u32(reinterpret_cast<const uint32_t *>(L.status)) != 0;
         }
         __syncthreads();
         const bool abort_item = s_flag != 0;
         __syncthreads();
-        const uint32_t slot = grp % A.R;
-        float2 *wv = A.wv + ((uint64_t(slot) * A.G) << A.m);
-        const uint32_t *ids = A.ids + uint64_t(grp) * A.G;
-        const uint64_t gb = A.gbase[grp];
-        const uint64_t bbase = uint64_t(grp) * A.G;  // per-group block arrays
-        bool by_arrival = type == PH_SIZE || type == PH_ENCODE;
+        const uint32_t slot = q % L.R;
+        float2 *wv = L.wv + uint64_t(slot) * L.slot_amps;
+        float2 *part = L.part + uint64_t(slot) * L.slot_frames;
+        const uint32_t *ids = S.ids + uint64_t(grp) * S.G;
+        const uint64_t gb = S.gbase[grp];
+        const uint64_t bbase = uint64_t(grp) * S.G;  // per-group block arrays
+        bool by_arrival = type == PH_SIZE || type == PH_ENCODE || type == PH_REENCODE;
         if (abort_item) {
             // skip the work, keep the counts
         } else if (type == PH_DECODE) {
             const uint32_t fi = i * (PT / 32) + warp;
             if (fi < gframes) {
                 const uint32_t jj = fi / g.nframes, f = fi % g.nframes;
-                const BlockSlot sl = A.tab_in[ids[jj]];
-                cdev::decode_frame_warp(sl.ptr, sl.bytes, g, int(A.m), f, wv + (uint64_t(jj) << A.m) + uint64_t(f) * g.F,
-                                        A.hist ? A.hist + (bbase + jj) * 32 : nullptr, s_hist[warp], A.status, s_pre,
-                                        A.npre, A.mats, uint64_t(jj) << A.m, gb);
+                const BlockSlot sl = S.tab_in[ids[jj]];
+                cdev::decode_frame_warp(sl.ptr, sl.bytes, g, int(S.m), f, wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F,
+                                        S.hist ? S.hist + (bbase + jj) * 32 : nullptr, s_hist[warp], L.status, s_pre,
+                                        S.npre, S.mats, uint64_t(jj) << S.m, gb);
             }
         } else if (type == PH_PASS) {
-            gdev::pass_tile<PT, 5, PREC, true>(wv, A.passes + A.ph[p].arg, A.ops, A.mats, A.bfr, i, gb, PS,
+            gdev::pass_tile<PT, 5, PREC, true>(wv, S.passes + S.ph[p].arg, S.ops, S.mats, S.bfr, i, gb, PS,
                                                reinterpret_cast<float2 *>(dsm));
         } else if (type == PH_SIZE) {
             const uint32_t jj = i / g.nframes, f = i % g.nframes;
-            const uint32_t len = cdev::size_frame_cta<true>(wv + (uint64_t(jj) << A.m) + uint64_t(f) * g.F, g, A.e,
-                                                            s_words, A.status);
-            if (tid == 0 && len) atomicAdd(reinterpret_cast<unsigned long long *>(&A.sizes[bbase + jj]), uint64_t(len));
+            const uint32_t len = cdev::size_frame_cta<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g, S.e,
+                                                            s_words, L.status);
+            if (tid == 0 && len) atomicAdd(reinterpret_cast<unsigned long long *>(&S.sizes[bbase + jj]), uint64_t(len));
         } else if (type == PH_PREDICT) {
             float *w = reinterpret_cast<float *>(dsm);
             for (int t = tid; t < kMlpParams; t += PT) {
-                const float v = A.pparams[t];
-                w[t] = A.pbf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
+                const float v = S.pparams[t];
+                w[t] = S.pbf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
             }
             __syncthreads();
-            for (uint32_t jj = tid; jj < A.G; jj += PT) {
+            for (uint32_t jj = tid; jj < S.G; jj += PT) {
                 float x[kMlpIn];
-                mlp_features(A.hist + bbase * 32, jj, A.G, int(A.m), A.sf, x);
-                double pr = double(mlp_forward_one(w, x)) + double(A.m + 3);
+                mlp_features(S.hist + bbase * 32, jj, S.G, int(S.m), S.sf, x);
+                double pr = double(mlp_forward_one(w, x)) + double(S.m + 3);
                 pr = pr < 0 ? 0 : (pr > 40 ? 40 : pr);
-                const double want = exp2(pr) * (1.0 + A.margin);
-                EncResult &rs = A.res[bbase + jj];
+                const double want_b = exp2(pr) * (1.0 + S.margin);
+                EncResult &rs = S.res[bbase + jj];
                 rs.total = 0;
                 rs.overflow = 0;
                 rs.err_sq = 0;
                 rs.norm_sq = 0;
-                cdev::reserve_slot(want >= double(A.worst) ? A.worst : uint64_t(want), A.dev, A.host,
-                                   &A.tgt[bbase + jj], A.status);
+                cdev::reserve_slot(want_b >= double(S.worst) ? S.worst : uint64_t(want_b), S.dev, S.host,
+                                   &S.tgt[bbase + jj], L.status);
             }
+            __syncthreads();
+            // the group's histograms are consumed: leave them zero for the next stage
+            for (uint32_t t = tid; t < S.G * 32; t += PT) S.hist[bbase * 32 + t] = 0;
         } else if (type == PH_ENCODE || type == PH_REENCODE) {
             const uint32_t jj = i / g.nframes, f = i % g.nframes;
             const bool retry = type == PH_REENCODE;
-            if (tid == 0) s_flag = retry ? int(__ldcg(&A.res[bbase + jj].overflow) != 0) : 1;
+            if (tid == 0) s_flag = retry ? int(__ldcg(&S.res[bbase + jj].overflow) != 0) : 1;
             __syncthreads();
             if (s_flag) {
-                const uint32_t epoch = (s_epoch + 2 * grp + (retry ? 1 : 0)) & cdev::kEpochMask;
-                cdev::encode_frame_cta<true>(wv + (uint64_t(jj) << A.m) + uint64_t(f) * g.F, g, int(A.m), A.e, f,
-                                             A.lb + (uint64_t(slot) * A.G + jj) * g.nframes, epoch,
-                                             load_target(&A.tgt[bbase + jj]), &A.res[bbase + jj], A.tab_out + ids[jj],
-                                             A.acc, retry ? nullptr : A.part + (uint64_t(slot) * A.G + jj) * g.nframes + f,
-                                             retry ? 1 : 0, reinterpret_cast<uint32_t *>(dsm), SE, A.status);
+                const uint32_t epoch = (s_epoch + 2 * q + (retry ? 1 : 0)) & cdev::kEpochMask;
+                cdev::encode_frame_cta<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g, int(S.m), S.e, f,
+                                             L.lb + uint64_t(slot) * L.slot_frames + uint64_t(jj) * g.nframes, epoch,
+                                             load_target(&S.tgt[bbase + jj]), &S.res[bbase + jj], S.tab_out + ids[jj],
+                                             S.acc, retry ? nullptr : part + uint64_t(jj) * g.nframes + f,
+                                             retry ? 1 : 0, reinterpret_cast<uint32_t *>(dsm), SE, L.status);
             }
         } else if (type == PH_FIX) {
-            for (uint32_t jj = tid; jj < A.G; jj += PT) {
-                EncResult &rs = A.res[bbase + jj];
+            for (uint32_t jj = tid; jj < S.G; jj += PT) {
+                EncResult &rs = S.res[bbase + jj];
                 if (__ldcg(&rs.overflow))
-                    cdev::reserve_slot(__ldcg(reinterpret_cast<const unsigned long long *>(&rs.total)), A.dev, A.host,
-                                       &A.tgt[bbase + jj], A.status);
+                    cdev::reserve_slot(__ldcg(reinterpret_cast<const unsigned long long *>(&rs.total)), S.dev, S.host,
+                                       &S.tgt[bbase + jj], L.status);
             }
         }
         // ---- completion ----
         __syncthreads();
-        uint32_t *done = A.done + uint64_t(grp) * nph + p;
+        uint32_t *done = L.done + uint64_t(q) * kMaxPhases + p;
         if (!by_arrival) {
             if (tid == 0) {
                 __threadfence();
@@ -187,7 +224,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PStageArgs A) {
         }
         if (tid == 0) {
             __threadfence();
-            s_flag = atomicAdd(A.arrive + uint64_t(grp) * nph + p, 1u) == A.ph[p].count - 1;
+            s_flag = atomicAdd(L.arrive + uint64_t(q) * kMaxPhases + p, 1u) == S.ph[p].count - 1;
         }
         __syncthreads();
         if (!s_flag) continue;
@@ -195,22 +232,22 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PStageArgs A) {
         if (abort_item) {
             // no reservation or statistics after an error
         } else if (type == PH_SIZE) {
-            // the group's exact sizes are complete: reserve its slots
-            for (uint32_t jj = tid; jj < A.G; jj += PT) {
-                const uint64_t want = atomicAdd(reinterpret_cast<unsigned long long *>(&A.sizes[bbase + jj]), 0ull) +
-                                      A.data_start;
-                EncResult &rs = A.res[bbase + jj];
+            // the group's exact sizes are complete: reserve its slots (and clear the sums for the next stage)
+            for (uint32_t jj = tid; jj < S.G; jj += PT) {
+                const uint64_t want_b =
+                    atomicExch(reinterpret_cast<unsigned long long *>(&S.sizes[bbase + jj]), 0ull) + S.data_start;
+                EncResult &rs = S.res[bbase + jj];
                 rs.total = 0;
                 rs.overflow = 0;
                 rs.err_sq = 0;
                 rs.norm_sq = 0;
-                cdev::reserve_slot(want, A.dev, A.host, &A.tgt[bbase + jj], A.status);
+                cdev::reserve_slot(want_b, S.dev, S.host, &S.tgt[bbase + jj], L.status);
             }
-        } else {
+        } else if (type == PH_ENCODE) {
             // the group's frames are encoded: fold their error partials into the stage totals
             double a = 0, b = 0;
             for (uint32_t t = tid; t < gframes; t += PT) {
-                const float2 v = __ldcg(A.part + uint64_t(slot) * gframes + t);
+                const float2 v = __ldcg(part + t);
                 a += double(v.x);
                 b += double(v.y);
             }
@@ -220,24 +257,37 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PStageArgs A) {
                 b += __shfl_xor_sync(kFull, b, o);
             }
             if ((tid & 31) == 0) {
-                atomicAdd(&A.acc->err_sq, a);
-                atomicAdd(&A.acc->norm_sq, b);
+                atomicAdd(&S.acc->err_sq, a);
+                atomicAdd(&S.acc->norm_sq, b);
             }
         }
         __syncthreads();
         if (tid == 0) {
             __threadfence();
-            atomicExch(done, A.ph[p].count);
+            atomicExch(done, S.ph[p].count);
+            if (p == nph - 1) {
+                // the group is finished: its slot may be reused; the stage may be complete
+                atomicExch(L.done + uint64_t(q) * kMaxPhases + kMaxPhases - 1, 1u);
+                if (atomicAdd(S.fin_count, 1u) == S.ngroups - 1) {
+                    if (S.reset_bumps) {
+                        // every group of the stage has read its input arena: the next stage writes there
+                        S.reset_bumps[0] = 0;
+                        S.reset_bumps[1] = 0;
+                    }
+                    __threadfence();
+                    atomicExch(S.fin_flag, 1u);
+                }
+            }
         }
     }
     // the last CTA out resets the queue and advances the look-back epoch
     if (tid == 0) {
         __threadfence();
-        if (atomicAdd(A.ctr + 1, 1u) == gridDim.x - 1) {
-            A.ctr[0] = 0;
-            A.ctr[1] = 0;
+        if (atomicAdd(L.ctr + 1, 1u) == gridDim.x - 1) {
+            L.ctr[0] = 0;
+            L.ctr[1] = 0;
             __threadfence();
-            atomicExch(A.ctr + 2, (s_epoch + 2 * A.ngroups) & cdev::kEpochMask);
+            atomicExch(L.ctr + 2, (s_epoch + 2 * L.total_groups) & cdev::kEpochMask);
         }
     }
 }
@@ -271,7 +321,7 @@ int prepare_prec(size_t smem) {
 }
 
 template <int PREC>
-int launch_stage_prec(const PStageArgs &a, size_t smem, cudaStream_t s, int *grid_out) {
+int launch_stage_prec(const PLaunch &a, size_t smem, cudaStream_t s, int *grid_out) {
     if (LaunchShape<PREC>::attr_smem < smem || !LaunchShape<PREC>::grid) return QSIM_E_INVALID;
     const int grid = LaunchShape<PREC>::grid;
     k_stage_persistent<PREC><<<grid, PT, smem, s>>>(a);
@@ -296,7 +346,7 @@ int prepare_stage_persistent(int prec, size_t smem) {
     return prepare_prec<QSIM_PREC_FP32>(smem);
 }
 
-int launch_stage_persistent(const PStageArgs &a, int prec, size_t smem, cudaStream_t s, int *grid) {
+int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid) {
     if (prec == QSIM_PREC_TF32) return launch_stage_prec<QSIM_PREC_TF32>(a, smem, s, grid);
     if (prec == QSIM_PREC_BF16X3) return launch_stage_prec<QSIM_PREC_BF16X3>(a, smem, s, grid);
     return launch_stage_prec<QSIM_PREC_FP32>(a, smem, s, grid);

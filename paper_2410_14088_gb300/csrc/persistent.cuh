@@ -26,9 +26,16 @@ struct PPhase {
 
 constexpr int kMaxPhases = 40;
 
-struct PStageArgs {
-    uint32_t W, G, ngroups, R, m, nphases, per_group, npre, pre_begin, pbf16;
+// One segment of the work queue: one stage of one circuit. The queue holds
+// ngroups x per_group items starting at item_begin; its groups take the launch's
+// group numbers group_begin .. group_begin + ngroups - 1 (working-vector slot,
+// look-back epoch and the done/arrive counters follow that number).
+struct PSeg {
+    uint64_t item_begin;
+    uint32_t group_begin;
+    uint32_t W, G, ngroups, m, nphases, per_group, npre, pre_begin, pbf16;
     int e;
+    uint32_t stall_test;  // 1: group 0's second phase waits for a count never reached (bounded-wait test)
     PPhase ph[kMaxPhases];
     uint32_t ph_start[kMaxPhases];
     const PassDev *passes;
@@ -41,11 +48,7 @@ struct PStageArgs {
     StageAccum *acc;
     ArenaDev dev, host;
     uint64_t data_start, worst;
-    // per slot (R working vectors)
-    float2 *wv;
-    uint64_t *lb;
-    float2 *part;
-    // per block of the stage (group-major)
+    // per block of the stage (group-major); the kernel leaves sizes and hist zeroed for the next stage
     EncTarget *tgt;
     EncResult *res;
     uint64_t *sizes;
@@ -54,16 +57,33 @@ struct PStageArgs {
     const float *pparams;
     StageFeatures sf;
     double margin;
-    // schedule
-    uint32_t *done, *arrive;  // ngroups x nphases each
+    // stage barrier within one launch: the previous stage of the same circuit
+    // (null when it ran in an earlier launch) and this stage's own counters
+    const uint32_t *prev_flag;  // becomes 1 once every group of the previous stage has finished
+    uint32_t *fin_count;        // groups of this stage finished
+    uint32_t *fin_flag;         // set to 1 after the last group (and the arena reset below)
+    uint64_t *reset_bumps;      // two bump words zeroed when the stage is complete (null: none)
+};
+
+struct PLaunch {
+    const PSeg *segs;        // device array, ordered by item_begin
+    uint32_t nseg;
+    uint64_t total_items;    // below 2^32
+    uint32_t total_groups;
+    uint32_t R;              // working-vector slots
+    uint64_t slot_amps;      // amplitudes per slot (>= 2^W of every segment)
+    uint64_t slot_frames;    // frames per slot (>= G x frames per block of every segment)
+    float2 *wv;
+    uint64_t *lb;
+    float2 *part;
+    uint32_t *done, *arrive;  // per launch group x kMaxPhases each, zero at launch
     uint32_t *ctr;            // queue head, CTAs finished, look-back epoch
     int *status;
-    uint32_t stall_test;      // 1: group 0's second phase waits for a count never reached (bounded-wait test)
     uint64_t wait_ns;         // limit of every dependency wait
 };
 
 size_t persistent_smem_bytes(uint32_t T, uint32_t mat_elems);
 int prepare_stage_persistent(int prec, size_t smem);
-int launch_stage_persistent(const PStageArgs &a, int prec, size_t smem, cudaStream_t s, int *grid);
+int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid);
 
 }  // namespace qsim

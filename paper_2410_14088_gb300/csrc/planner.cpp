@@ -133,6 +133,12 @@ bool matrix_is_diagonal(const std::vector<cd> &u, uint32_t D) {
     return true;
 }
 
+// Greedy fusion in circuit order. Non-diagonal gates grow the active dense op
+// while the union of its qubits stays <= k. Diagonal gates are first folded
+// back into the pending diagonal op when they commute with every op placed
+// after it (their qubits are disjoint from those ops' qubits; diagonal ops and
+// phase flips commute with them anyway), up to kMaxDiagQubits qubits; else they
+// join the active op; else they open a new pending diagonal op.
 struct Fuser {
     const std::vector<uint32_t> *inner;
     uint32_t m, k;
@@ -141,6 +147,8 @@ struct Fuser {
     std::vector<uint32_t> S;  // ascending working bits
     std::vector<cd> U;
     uint32_t ngates = 0;
+    int64_t diag_op = -1;          // index of the pending diagonal op in *ops
+    std::set<uint32_t> blockers;   // full qubits of the ops placed after it
 
     int32_t working_bit(uint32_t q) const {
         if (q < m) return int32_t(q);
@@ -166,6 +174,7 @@ struct Fuser {
             for (uint32_t j = 0; j < op.k; ++j) op.wq[j] = S[j];
             op.u = U;
         }
+        for (uint32_t w : S) blockers.insert(qubit_of(w));
         ops->push_back(std::move(op));
         active = false;
         S.clear();
@@ -173,8 +182,48 @@ struct Fuser {
         ngates = 0;
     }
 
+    // ops[diag_op] *= the diagonal gate g (phases multiply; qubit sets unite)
+    void fold_diag(const Gate &g) {
+        Op &d = (*ops)[size_t(diag_op)];
+        std::set<uint32_t> uni(d.fq, d.fq + d.k);
+        uni.insert(g.q, g.q + g.nq);
+        const std::vector<uint32_t> NQ(uni.begin(), uni.end());
+        const uint32_t K = NQ.size(), dg = 1u << g.nq;
+        std::vector<cd> nu(size_t(1) << K);
+        for (uint32_t x = 0; x < (1u << K); ++x) {
+            uint32_t a = 0, b = 0;
+            for (uint32_t j = 0; j < K; ++j) {
+                const uint32_t bit = (x >> j) & 1u;
+                for (uint32_t i = 0; i < d.k; ++i)
+                    if (d.fq[i] == NQ[j]) a |= bit << i;
+                for (uint32_t i = 0; i < g.nq; ++i)
+                    if (g.q[i] == NQ[j]) b |= bit << i;
+            }
+            nu[x] = d.u[a] * g.u[size_t(b) * dg + b];
+        }
+        d.k = K;
+        for (uint32_t j = 0; j < K; ++j) d.fq[j] = NQ[j];
+        d.u = std::move(nu);
+        d.ngates += 1;
+    }
+
+    // the gate joins the active op if the union of qubits stays <= k
+    bool try_join(const Gate &g, const std::vector<uint32_t> &wb) {
+        std::set<uint32_t> uni(S.begin(), S.end());
+        uni.insert(wb.begin(), wb.end());
+        if (!active || uni.size() > k) return false;
+        std::vector<uint32_t> NS(uni.begin(), uni.end());
+        std::vector<cd> cur = embed(U, S, NS);
+        std::vector<cd> gm = embed(g.u, wb, NS);
+        U = matmul(gm, cur, 1u << NS.size());  // later gate on the left
+        S = NS;
+        ++ngates;
+        return true;
+    }
+
     void add(const Gate &g) {
         if (g.phaseflip) {
+            // diagonal: the pending diagonal op may still move across it
             flush();
             Op op{};
             op.type = OP_PHASEFLIP;
@@ -190,8 +239,26 @@ struct Fuser {
             if (w < 0) all_working = false;
             wb[j] = uint32_t(w);
         }
-        if (!all_working || g.nq > k) {
-            // block-local diagonal with outer qubits (or wider than k): a phase op
+        if (g.diag) {
+            bool touches_active = false, commutes = diag_op >= 0;
+            for (uint32_t j = 0; j < g.nq; ++j) {
+                if (all_working && std::find(S.begin(), S.end(), wb[j]) != S.end()) touches_active = true;
+                if (blockers.count(g.q[j])) commutes = false;
+                if (active && working_bit(g.q[j]) >= 0 &&
+                    std::find(S.begin(), S.end(), uint32_t(working_bit(g.q[j]))) != S.end())
+                    commutes = false;
+            }
+            if (all_working && g.nq <= k && touches_active && try_join(g, wb)) return;
+            if (commutes) {
+                const Op &d = (*ops)[size_t(diag_op)];
+                std::set<uint32_t> uni(d.fq, d.fq + d.k);
+                uni.insert(g.q, g.q + g.nq);
+                if (uni.size() <= kMaxDiagQubits) {
+                    fold_diag(g);
+                    return;
+                }
+            }
+            if (all_working && g.nq <= k && try_join(g, wb)) return;
             flush();
             Op op{};
             op.type = OP_DIAG;
@@ -202,19 +269,11 @@ struct Fuser {
             op.u.resize(d);
             for (uint32_t r = 0; r < d; ++r) op.u[r] = g.u[size_t(r) * d + r];
             ops->push_back(std::move(op));
+            diag_op = int64_t(ops->size()) - 1;
+            blockers.clear();
             return;
         }
-        std::set<uint32_t> uni(S.begin(), S.end());
-        uni.insert(wb.begin(), wb.end());
-        if (active && uni.size() <= k) {
-            std::vector<uint32_t> NS(uni.begin(), uni.end());
-            std::vector<cd> cur = embed(U, S, NS);
-            std::vector<cd> gm = embed(g.u, wb, NS);
-            U = matmul(gm, cur, 1u << NS.size());  // later gate on the left
-            S = NS;
-            ++ngates;
-            return;
-        }
+        if (try_join(g, wb)) return;
         flush();
         std::set<uint32_t> own(wb.begin(), wb.end());
         S.assign(own.begin(), own.end());

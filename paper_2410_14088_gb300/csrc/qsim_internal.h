@@ -51,7 +51,7 @@ struct Op {
     OpType type;
     uint32_t k;             // dense: width; diag: number of qubits
     uint32_t wq[6];         // dense: working-index bit of matrix bit j
-    uint32_t fq[6];         // diag: full qubit ids (matrix bit j)
+    uint32_t fq[8];         // diag: full qubit ids (matrix bit j)
     uint64_t basis;         // phaseflip
     std::vector<cd> u;      // dense: 2^k x 2^k row-major; diag: 2^k phases
     uint32_t ngates;        // input gates folded into this op
@@ -73,6 +73,7 @@ struct Stage {
 };
 
 constexpr uint32_t kMaxPreOps = 8;
+constexpr uint32_t kMaxDiagQubits = 8;  // widest fused diagonal op (phase index fits a byte)
 
 struct Gate {
     uint32_t nq = 0;

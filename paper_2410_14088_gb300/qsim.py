@@ -58,7 +58,7 @@ class PlanStats(ctypes.Structure):
 
 
 class OpInfo(ctypes.Structure):
-    _fields_ = [("type", ctypes.c_uint32), ("nq", ctypes.c_uint32), ("qubits", ctypes.c_uint32 * 6),
+    _fields_ = [("type", ctypes.c_uint32), ("nq", ctypes.c_uint32), ("qubits", ctypes.c_uint32 * 8),
                 ("ngates", ctypes.c_uint32), ("pass_", ctypes.c_uint32), ("basis", ctypes.c_uint64),
                 ("u", ctypes.POINTER(ctypes.c_double))]
 
@@ -133,6 +133,8 @@ SIGNATURES = {
     "qsim_autotune_cache_clear": (None, []),
     "qsim_profile_enable": (None, [ctypes.c_int]),
     "qsim_state_kernel_stats": (ctypes.c_int, [_VP, ctypes.POINTER(KernelStat), _SZ, ctypes.POINTER(_SZ)]),
+    "qsim_run_batch": (ctypes.c_int, [ctypes.POINTER(_VP), _SZ, _VP, ctypes.POINTER(_VP), ctypes.POINTER(Stats),
+                                      ctypes.POINTER(KernelStat)]),
     "qsim_last_error": (ctypes.c_char_p, []),
     "qsim_kernel_launch_count": (_U64, []),
     "qsim_release_cached_memory": (None, []),
@@ -384,6 +386,21 @@ def run(plan: Plan, stream=None) -> State:
     st = Stats()
     _check(lib().qsim_run(plan.handle, _stream_ptr(stream), ctypes.byref(h), ctypes.byref(st)), "qsim_run")
     return State(h, plan.n, plan.cfg.m, st, plan.nstages)
+
+
+def run_batch(plans, stream=None):
+    """Run several plans in one persistent launch (qsim_run_batch). Returns
+    (states, launch) where launch is the persistent launch's kernel statistic."""
+    n = len(plans)
+    handles = (_VP * n)(*[p.handle for p in plans])
+    outs = (_VP * n)()
+    stats = (Stats * n)()
+    ks = KernelStat()
+    _check(lib().qsim_run_batch(handles, n, _stream_ptr(stream), outs, stats, ctypes.byref(ks)), "qsim_run_batch")
+    states = [State(_VP(outs[i]), plans[i].n, plans[i].cfg.m, stats[i], plans[i].nstages) for i in range(n)]
+    launch = {"name": ks.name.decode(), "launches": ks.launches, "seconds": ks.seconds, "alg_bytes": ks.alg_bytes,
+              "alg_flops": ks.alg_flops}
+    return states, launch
 
 
 # --------------------------------------------------------------------------
