@@ -32,7 +32,7 @@ namespace {
 
 using namespace cdev;
 
-__global__ void __launch_bounds__(NT, 3) k_decode(const BlockRef *__restrict__ in, const BlockSlot *__restrict__ table,
+__global__ void __launch_bounds__(NT, 4) k_decode(const BlockRef *__restrict__ in, const BlockSlot *__restrict__ table,
                                                const uint32_t *__restrict__ ids, uint32_t nblocks, int m,
                                                float2 *__restrict__ wv, uint32_t *__restrict__ hist,
                                                int *status, PreOps pre) {
@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
     }
 }
 
-__global__ void __launch_bounds__(NT) k_encode_size(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
+__global__ void __launch_bounds__(NT, 4) k_encode_size(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
                                                     uint64_t *__restrict__ sizes, uint32_t *done_ctr,
                                                     ArenaDev dev, ArenaDev host, EncTarget *__restrict__ tgt,
                                                     EncResult *__restrict__ res, int *status, uint8_t *__restrict__ wrec,
@@ -206,7 +206,7 @@ __global__ void __launch_bounds__(NT) k_encode_size(const float2 *__restrict__ w
 // Exact-sizing encoder: one warp per frame, widths and frame offsets from the
 // sizing pass; the last CTA folds the frames' error partials into the blocks'
 // and the stage's totals.
-__global__ void __launch_bounds__(NT) k_encode_known(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
+__global__ void __launch_bounds__(NT, 4) k_encode_known(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
                                                      const EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
                                                      const uint32_t *__restrict__ ids, BlockSlot *__restrict__ table,
                                                      StageAccum *acc, const uint8_t *__restrict__ wrec,

@@ -53,44 +53,39 @@ __device__ __forceinline__ int32_t unzigzag(uint32_t z) {
 // ---------------------------------------------------------------------------
 // Decode: one CTA per frame (grid-stride over all frames of all blocks).
 // ---------------------------------------------------------------------------
-// The same for lane `lane` of a 32-amplitude chunk starting at working index
-// w0: the phase index splits into bits of w0 / the group (same for the chunk)
-// and bits 0..4 of the lane.
-__device__ __forceinline__ float2 apply_pre_ops_chunk(float2 v, uint64_t w0, uint32_t lane, uint64_t gb,
-                                                      const OpDev *ops, uint32_t nops, const float2 *__restrict__ mats) {
-    for (uint32_t o = 0; o < nops; ++o) {
+// Leading phase ops of a stage, applied by the decoder. The phase index of a
+// diagonal op splits into bits fixed for the frame (working bits >= the frame
+// log, and outer qubits from the group), the lane's bits 0..4 and the chunk's
+// bits 5.. ; the host builds the lane and chunk parts as byte tables (32 + 128
+// bytes at float2 offset op.dlut of the phase area). pre_frame returns, per op,
+// the frame and lane parts; pre_chunk applies the ops to one chunk's amplitude.
+__device__ __forceinline__ void pre_frame(uint32_t (&cl)[kMaxPreOps], const OpDev *ops, uint32_t nops, uint64_t w0f,
+                                          uint32_t fl, uint32_t lane, uint64_t gb, const float2 *__restrict__ mats) {
+#pragma unroll
+    for (uint32_t o = 0; o < kMaxPreOps; ++o) {
+        cl[o] = 0;
+        if (o >= nops || ops[o].type != OP_DIAG) continue;
         const OpDev &op = ops[o];
-        if (op.type == OP_DIAG) {
-            uint32_t idx = 0;
-            for (uint32_t j = 0; j < op.k; ++j) {
-                const uint32_t src = op.dsrc[j];
-                uint32_t bit;
-                if (src < 5) bit = (lane >> src) & 1u;
-                else bit = uint32_t(src < 64 ? (w0 >> src) & 1ull : (gb >> (src - 64)) & 1ull);
-                idx |= bit << j;
-            }
-            const float2 ph = __ldg(mats + op.mat + idx);
-            v = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
-        } else if (op.basis_in_stage && gb == op.basis_outer && (w0 | lane) == op.basis_w) {
-            v = make_float2(-v.x, -v.y);
+        uint32_t idx = 0;
+        for (uint32_t j = 0; j < op.k; ++j) {
+            const uint32_t src = op.dsrc[j];
+            if (src < fl) continue;
+            const uint64_t bit = src < 64 ? (w0f >> src) & 1ull : (gb >> (src - 64)) & 1ull;
+            idx |= uint32_t(bit) << j;
         }
+        cl[o] = idx | __ldg(reinterpret_cast<const uint8_t *>(mats + op.dlut) + lane);
     }
-    return v;
 }
 
-// Leading phase ops of a stage, applied to each decoded amplitude: w is the
-// amplitude's working index, gb the full-index bits of its group's outer qubits.
-__device__ __forceinline__ float2 apply_pre_ops(float2 v, uint64_t w, uint64_t gb, const OpDev *ops, uint32_t nops,
-                                                const float2 *__restrict__ mats) {
-    for (uint32_t o = 0; o < nops; ++o) {
+__device__ __forceinline__ float2 pre_chunk(float2 v, const uint32_t (&cl)[kMaxPreOps], const OpDev *ops,
+                                            uint32_t nops, uint32_t c, uint64_t w, uint64_t gb,
+                                            const float2 *__restrict__ mats) {
+#pragma unroll
+    for (uint32_t o = 0; o < kMaxPreOps; ++o) {
+        if (o >= nops) break;
         const OpDev &op = ops[o];
         if (op.type == OP_DIAG) {
-            uint32_t idx = 0;
-            for (uint32_t j = 0; j < op.k; ++j) {
-                const uint32_t src = op.dsrc[j];
-                const uint64_t bit = src < 64 ? (w >> src) & 1ull : (gb >> (src - 64)) & 1ull;
-                idx |= uint32_t(bit) << j;
-            }
+            const uint32_t idx = cl[o] | __ldg(reinterpret_cast<const uint8_t *>(mats + op.dlut) + 32 + c);
             const float2 ph = __ldg(mats + op.mat + idx);
             v = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
         } else if (op.basis_in_stage && gb == op.basis_outer && w == op.basis_w) {
@@ -166,12 +161,15 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
         if (lane == 0) raise_status(status, QSIM_E_CORRUPT);
     }
     if (!ok || fb == fa) {
-        for (uint32_t i = lane; i < g.F; i += 32) dst[i] = make_float2(0.f, 0.f);
+        float4 *d4 = reinterpret_cast<float4 *>(dst);  // F >= 32 amplitudes, 16-byte aligned
+        for (uint32_t i = lane; i < g.F / 2; i += 32) d4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
         if (hist_j && lane == 0) atomicAdd(&hist_j[0], 2 * g.F);
         return;
     }
     const uint32_t *payload = reinterpret_cast<const uint32_t *>(sp + fa + padw);
     const float step = exp2i(e);
+    uint32_t pre_cl[kMaxPreOps];
+    if (npre) pre_frame(pre_cl, pre_ops, npre, wbase | (uint64_t(f) * g.F), g.fl, lane, gb, mats);
     // ---- chunk pairs, eight at a time ----
     for (uint32_t c0 = 0; c0 < g.C; c0 += 8) {
         // widths/offsets of Re chunks c0.. (owner lane c0/8) and Im chunks C+c0.. (owner (C+c0)/8)
@@ -219,7 +217,7 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
             }
             const int32_t sr = int32_t(qr), si = int32_t(qi);
             float2 v = make_float2(float(sr) * step, float(si) * step);
-            if (npre) v = apply_pre_ops_chunk(v, wbase | (uint64_t(f) * g.F + c * 32), lane, gb, pre_ops, npre, mats);
+            if (npre) v = pre_chunk(v, pre_cl, pre_ops, npre, c, wbase | (uint64_t(f) * g.F + c * 32 + lane), gb, mats);
             dst[c * 32 + lane] = v;
             if (hist_j) {
                 const uint32_t br = 32 - __clz(sr < 0 ? uint32_t(-sr) : uint32_t(sr));
@@ -515,6 +513,7 @@ __device__ __forceinline__ void reserve_slot(uint64_t want, const ArenaDev &dev,
 template <bool CG = false>
 __device__ __forceinline__ uint32_t size_frame_cta(const float2 *__restrict__ src, const FrameGeom &g, int e,
                                                    uint32_t *s_words, int *status, uint8_t *wrec = nullptr) {
+    __shared__ __align__(16) uint8_t s_wb[256];  // the frame's chunk widths, when wrec is given
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float inv_step = exp2i(-e);
     float2 vin[MAX_CPW];
@@ -533,10 +532,13 @@ __device__ __forceinline__ uint32_t size_frame_cta(const float2 *__restrict__ sr
         const float x[2] = {vin[i].x, vin[i].y};
 #pragma unroll
         for (int p = 0; p < 2; ++p) {
-            float t = x[p] * inv_step;
-            if (!isfinite(x[p])) { bad = QSIM_E_INVALID; q[p] = 0; }
-            else if (fabsf(t) >= 1073741824.0f) { bad = bad ? bad : QSIM_E_RANGE; q[p] = 0; }
-            else q[p] = __float2int_rn(t);
+            const float t = x[p] * inv_step;  // exact: power-of-two scaling
+            if (fabsf(t) < 1073741824.0f) {
+                q[p] = __float2int_rn(t);
+            } else {  // NaN, Inf or out of range
+                q[p] = 0;
+                bad = isfinite(x[p]) ? (bad ? bad : QSIM_E_RANGE) : QSIM_E_INVALID;
+            }
         }
         int32_t pr = __shfl_up_sync(kFull, q[0], 1);
         int32_t pi = __shfl_up_sync(kFull, q[1], 1);
@@ -545,13 +547,16 @@ __device__ __forceinline__ uint32_t size_frame_cta(const float2 *__restrict__ sr
         const uint32_t wr = 32 - __clz(__reduce_or_sync(kFull, zr)), wi = 32 - __clz(__reduce_or_sync(kFull, zi));
         words += wr + wi;
         if (wrec && lane == 0) {
-            wrec[c] = uint8_t(wr);
-            wrec[g.C + c] = uint8_t(wi);
+            s_wb[c] = uint8_t(wr);
+            s_wb[g.C + c] = uint8_t(wi);
         }
     }
     if (bad) raise_status(status, bad);
     if (lane == 0) s_words[warp] = words;
     __syncthreads();
+    // the width record leaves in 16-byte stores (bytes past 2C are ignored by its reader)
+    if (wrec && tid < int((2 * g.C + 15) / 16))
+        reinterpret_cast<uint4 *>(wrec)[tid] = reinterpret_cast<const uint4 *>(s_wb)[tid];
     uint32_t tot = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) tot += s_words[w];

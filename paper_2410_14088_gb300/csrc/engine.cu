@@ -440,7 +440,31 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
         };
         sd.pre_begin = ops.size();
         sd.npre = st.pre_ops.size();
-        for (uint32_t oi : st.pre_ops) ops.push_back(diag_opdev(st.ops[oi]));
+        for (uint32_t oi : st.pre_ops) {
+            OpDev od = diag_opdev(st.ops[oi]);
+            if (od.type == OP_DIAG) {
+                // decoder tables: phase-index bits from the lane (working bits 0..4, 32 bytes) and from the
+                // chunk within the frame (working bits 5..fl-1, 128 bytes)
+                const uint32_t fl = uint32_t(frame_log_for(int(m)));
+                uint8_t lut[160] = {0};
+                for (uint32_t j = 0; j < od.k; ++j) {
+                    const uint32_t src = od.dsrc[j];
+                    if (src < 5) {
+                        for (uint32_t x = 0; x < 32; ++x) lut[x] |= uint8_t(((x >> src) & 1u) << j);
+                    } else if (src < fl) {
+                        for (uint32_t x = 0; x < 128; ++x) lut[32 + x] |= uint8_t(((x >> (src - 5)) & 1u) << j);
+                    }
+                }
+                while (mats.size() & 1) mats.push_back(make_float2(0, 0));
+                od.dlut = mats.size();
+                for (uint32_t w = 0; w < 20; ++w) {
+                    float2 fv;
+                    memcpy(&fv, lut + 8 * w, 8);
+                    mats.push_back(fv);
+                }
+            }
+            ops.push_back(od);
+        }
         for (const Pass &ps : st.passes) {
             PassDev P{};
             P.T = ps.T;
@@ -521,6 +545,24 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                     }
                 }
                 ops.push_back(od);
+            }
+            // runs of consecutive diagonal ops applied in one sweep; their phase tables side by side
+            for (uint32_t a = P.op_begin; a < P.op_begin + P.op_count;) {
+                if (ops[a].type != OP_DIAG) {
+                    ++a;
+                    continue;
+                }
+                uint32_t b = a, elems = 0;
+                while (b < P.op_begin + P.op_count && b - a < kDiagRun && ops[b].type == OP_DIAG &&
+                       elems + (1u << ops[b].k) <= std::max<uint32_t>(kDiagRunElems, 1u << ops[a].k)) {
+                    ops[b].tab = elems;
+                    ops[b].run = 0;
+                    elems += 1u << ops[b].k;
+                    ++b;
+                }
+                ops[a].run = b - a;
+                P.mat_elems = std::max<uint32_t>(P.mat_elems, elems);
+                a = b;
             }
             P.mat_elems = (P.mat_elems + 1) & ~1u;
             sd.passes_host.push_back(P);

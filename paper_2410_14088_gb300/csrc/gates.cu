@@ -29,8 +29,13 @@ namespace {
 using namespace gdev;
 constexpr int NT = 128;
 
+// One CTA per tile (grid: tiles x groups); several resident CTAs per SM keep
+// loads, ops and stores of different tiles in flight. (A persistent variant
+// with two tile buffers per CTA and cp.async prefetch of the next tile ran
+// slower on GB300: fewer resident CTAs, 3.1 against 4.3 TB/s on load/store-only
+// passes.)
 template <int KMAX, int PREC>
-__global__ void __launch_bounds__(NT, (KMAX >= 6 ? 2 : 4))
+__global__ void __launch_bounds__(NT, (KMAX >= 6 ? 2 : (PREC == QSIM_PREC_BF16X3 && KMAX >= 4) ? 3 : 4))
     k_pass(float2 *__restrict__ wv, uint32_t W, const PassDev *__restrict__ pd, const OpDev *__restrict__ ops,
            const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr, const uint64_t *__restrict__ gbase) {
     extern __shared__ float4 dyn_smem[];

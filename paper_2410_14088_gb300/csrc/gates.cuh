@@ -38,7 +38,12 @@ struct __align__(16) OpDev {
     uint64_t basis_w;        // phase flip: working index of the basis state
     uint32_t basis_in_stage; // phase flip: 1 if the basis' outer bits can match a group
     uint32_t bfrag;          // dense, tensor-core precisions: word offset of the op's B-fragment table
+    uint32_t run;            // diag in a pass: ops applied in one sweep from here (0 inside a run)
+    uint32_t tab;            // diag in a pass: float2 offset of its phases in the pass's shared table area
 };
+
+constexpr uint32_t kDiagRun = 4;           // diagonal ops applied in one sweep over a tile
+constexpr uint32_t kDiagRunElems = 1024;   // their phase tables together, in float2
 
 // wv: ngroups consecutive working vectors of 2^W amplitudes; gbase[g] is the
 // full-index value of group g's outer bits.

@@ -30,15 +30,17 @@ __device__ __forceinline__ void coop_copy(T &dst, const T *__restrict__ src) {
 
 struct PassSmem {
     PassDev p;
-    OpDev op;
+    OpDev dop[kDiagRun];   // the next op (dense, phase flip) or run of diagonal ops
     uint32_t hi[256];
+    uint32_t off12[32];    // 4096-amplitude tiles with L >= log2(NT): working offset of element tid + NT u, minus tid
     uint32_t offs[64];
-    uint8_t dlut_lo[128];  // diagonal op: phase-index bits contributed by tile bits 0..6
-    uint8_t dlut_hi[64];   // and by tile bits 7..12 (directly after dlut_lo)
-    uint32_t dconst;       // and by the bits that are constant over the tile
+    // diagonal op d of a run: phase-index bits contributed by tile bits 0..6
+    // (bytes 0..127) and by tile bits 7..12 (bytes 128..191)
+    uint8_t dlut[kDiagRun][192];
+    uint32_t dconst[kDiagRun];  // and by the bits that are constant over the tile
 };
-static_assert(offsetof(PassSmem, dlut_hi) == offsetof(PassSmem, dlut_lo) + 128 && offsetof(PassSmem, dlut_lo) % 4 == 0,
-              "the phase-index tables are copied as one 192-byte run of words");
+static_assert(offsetof(PassSmem, dlut) % 4 == 0 && offsetof(PassSmem, dop) % 16 == 0 && sizeof(OpDev) % 16 == 0,
+              "descriptors and phase-index tables are copied as words");
 
 template <int NT, int K>
 __device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const PassSmem &S, uint32_t T) {
@@ -47,7 +49,7 @@ __device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const
     const uint32_t nc = T - K;
     for (uint32_t g = threadIdx.x; g < ngroups; g += NT) {
         uint32_t b = 0;
-        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.op.comp[t];
+        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.dop[0].comp[t];
         float2 x[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) x[c] = tile[swz(b | S.offs[c])];
@@ -83,7 +85,7 @@ __device__ __forceinline__ void apply_dense_k1(float2 *tile, const float2 *U, co
     const float2 u00 = U[0], u01 = U[1], u10 = U[2], u11 = U[3];
     for (uint32_t g = threadIdx.x; g < ngroups; g += NT) {
         uint32_t b = 0;
-        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.op.comp[t];
+        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.dop[0].comp[t];
         const uint32_t i0 = swz(b), i1 = swz(b | S.offs[1]);
         const float2 x0 = tile[i0], x1 = tile[i1];
         tile[i0] = make_float2(u00.x * x0.x - u00.y * x0.y + u01.x * x1.x - u01.y * x1.y,
@@ -101,6 +103,9 @@ __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// all but the most recent committed group complete
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 
 // ---------------------------------------------------------------------------
@@ -170,7 +175,7 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
         for (int h = 0; h < 2; ++h) {
             const uint32_t g = row0 + mt * 16 + gq + 8 * h;
             uint32_t b = 0;
-            for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.op.comp[t];
+            for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.dop[0].comp[t];
             base[mt][h] = b;
         }
     float acc[MT * NTILES][4];
@@ -296,32 +301,80 @@ __device__ __forceinline__ void apply_dense_dispatch(uint32_t k, float2 *tile, c
     }
 }
 
-// One tile of one pass: stage the 2^T amplitudes of tile `cta` of the group's
-// working vector g in shared memory, apply the pass's ops, store them back.
-// CG selects L2-only loads, needed when the working vector was written by
-// other CTAs of the same launch (the persistent stage kernel).
-template <int NT, int KMAX, int PREC, bool CG>
-__device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev *__restrict__ pd,
-                                          const OpDev *__restrict__ ops, const float2 *__restrict__ mats,
-                                          const uint32_t *__restrict__ bfr, uint64_t cta, uint64_t gb, PassSmem &S,
-                                          float2 *tile) {
-    const int tid = threadIdx.x;
+// Per pass, once per CTA: the pass descriptor and the offsets of the tile's
+// high part (tile bits L..T-1 placed at their working bits).
+template <int NT>
+__device__ __forceinline__ void pass_setup(const PassDev *__restrict__ pd, PassSmem &S) {
     coop_copy<NT>(S.p, pd);
     __syncthreads();
-    const uint32_t T = S.p.T, L = S.p.L, nout = S.p.nout;
-    float2 *mat = tile + (1u << T);
+    const uint32_t T = S.p.T, L = S.p.L;
     const uint32_t nhi = 1u << (T - L);
-    for (uint32_t h = tid; h < nhi; h += NT) {
+    for (uint32_t h = threadIdx.x; h < nhi; h += NT) {
         uint32_t o = 0;
         for (uint32_t t = 0; t < T - L; ++t) o |= ((h >> t) & 1u) << S.p.tile_pos[L + t];
         S.hi[h] = o;
     }
-    uint64_t base = 0;
-    for (uint32_t t = 0; t < nout; ++t) base |= ((cta >> t) & 1ull) << S.p.out_pos[t];
-    const uint32_t lmask = (1u << L) - 1;
+    constexpr uint32_t A = NT == 256 ? 8 : 7;
+    if (T == 12 && L >= A && threadIdx.x < (4096u / NT)) {
+        // element i = tid + NT u: low bits tid, then bits A..L-1 from u, the rest from the high table
+        const uint32_t u = threadIdx.x, sh = L - A;
+        uint32_t o = (u & ((1u << sh) - 1)) * NT;
+        for (uint32_t t = 0; t < T - L; ++t) o |= ((u >> (sh + t)) & 1u) << S.p.tile_pos[L + t];
+        S.off12[u] = o;
+    }
     __syncthreads();
+}
+
+// Fast tile addressing for T = 12, L >= log2(NT): element i = tid + NT u sits
+// at working offset tid + off12[u] and at shared index (tid ^ xt) ^ xu(u) + NT u,
+// the XOR swizzle split into a per-thread and a per-u part.
+template <int NT>
+__device__ __forceinline__ uint32_t swz_thread(uint32_t tid) {
+    return tid ^ (NT == 256 ? ((tid >> 4) & 15u) : ((tid >> 4) & 7u));
+}
+template <int NT>
+__device__ __forceinline__ constexpr uint32_t swz_u(uint32_t u) {
+    return NT == 256 ? (u & 15u) : (((u & 1u) << 3) ^ ((u >> 1) & 15u));
+}
+template <int NT>
+__device__ __forceinline__ bool fast12(const PassSmem &S) {
+    return S.p.T == 12 && S.p.L >= (NT == 256 ? 8u : 7u);
+}
+
+// working index of element 0 of tile `cta` (its non-tile bits)
+__device__ __forceinline__ uint64_t tile_base(const PassSmem &S, uint64_t cta) {
+    uint64_t base = 0;
+    for (uint32_t t = 0; t < S.p.nout; ++t) base |= ((cta >> t) & 1ull) << S.p.out_pos[t];
+    return base;
+}
+
+// Stage a tile in shared memory: cp.async (the caller commits and waits), or
+// with CG batches of eight L2-only loads in flight per thread (data written by
+// other CTAs of the same launch).
+template <int NT, bool CG>
+__device__ __forceinline__ void tile_load(const float2 *__restrict__ g, uint64_t base, const PassSmem &S,
+                                          float2 *tile) {
+    const uint32_t T = S.p.T, L = S.p.L, lmask = (1u << L) - 1;
+    const int tid = threadIdx.x;
+    if (fast12<NT>(S)) {
+        const float2 *gt = g + (base | uint64_t(tid));
+        const uint32_t tq = swz_thread<NT>(tid);
+        if constexpr (CG) {
+#pragma unroll
+            for (uint32_t u0 = 0; u0 < 4096u / NT; u0 += 8) {
+                float2 v[8];
+#pragma unroll
+                for (uint32_t u = 0; u < 8; ++u) v[u] = __ldcg(gt + S.off12[u0 + u]);
+#pragma unroll
+                for (uint32_t u = 0; u < 8; ++u) tile[(tq ^ swz_u<NT>(u0 + u)) + NT * (u0 + u)] = v[u];
+            }
+        } else {
+#pragma unroll
+            for (uint32_t u = 0; u < 4096u / NT; ++u) cp_async8(&tile[(tq ^ swz_u<NT>(u)) + NT * u], gt + S.off12[u]);
+        }
+        return;
+    }
     if constexpr (CG) {
-        // batches of eight L2 loads in flight per thread, then the shared-memory stores
         for (uint32_t i0 = tid; i0 < (1u << T); i0 += 8 * NT) {
             float2 v[8];
 #pragma unroll
@@ -337,63 +390,125 @@ __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev 
         }
     } else {
         for (uint32_t i = tid; i < (1u << T); i += NT) cp_async8(&tile[swz(i)], &g[base | (i & lmask) | S.hi[i >> L]]);
-        cp_async_wait_all();
     }
-    for (uint32_t oi = 0; oi < S.p.op_count; ++oi) {
+}
+
+template <int NT>
+__device__ __forceinline__ void tile_store(float2 *__restrict__ g, uint64_t base, const PassSmem &S,
+                                           const float2 *tile) {
+    const uint32_t T = S.p.T, L = S.p.L, lmask = (1u << L) - 1;
+    if (fast12<NT>(S)) {
+        const uint32_t tid = threadIdx.x, tq = swz_thread<NT>(tid);
+        float2 *gt = g + (base | uint64_t(tid));
+#pragma unroll
+        for (uint32_t u = 0; u < 4096u / NT; ++u) gt[S.off12[u]] = tile[(tq ^ swz_u<NT>(u)) + NT * u];
+        return;
+    }
+    for (uint32_t i = threadIdx.x; i < (1u << T); i += NT) g[base | (i & lmask) | S.hi[i >> L]] = tile[swz(i)];
+}
+
+// The pass's ops on a staged tile (mat: the shared matrix / phase-table area).
+// Starts with a CTA barrier, so the tile's loads need only have completed per thread.
+template <int NT, int KMAX, int PREC>
+__device__ __forceinline__ void tile_ops(float2 *tile, float2 *mat, const OpDev *__restrict__ ops,
+                                         const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr,
+                                         uint64_t base, uint64_t gb, PassSmem &S) {
+    const int tid = threadIdx.x;
+    const uint32_t T = S.p.T;
+    for (uint32_t oi = 0; oi < S.p.op_count;) {
         __syncthreads();
-        coop_copy<NT>(S.op, ops + S.p.op_begin + oi);
+        {  // descriptors of the next op, or of the next run of diagonal ops
+            const uint32_t avail = min(kDiagRun, S.p.op_count - oi);
+            const uint4 *src = reinterpret_cast<const uint4 *>(ops + S.p.op_begin + oi);
+            uint4 *dst = reinterpret_cast<uint4 *>(S.dop);
+            for (uint32_t t = tid; t < avail * uint32_t(sizeof(OpDev) / 16); t += NT) dst[t] = __ldg(src + t);
+        }
         __syncthreads();
-        const uint32_t type = S.op.type, k = S.op.k;
+        const OpDev &op = S.dop[0];
+        const uint32_t type = op.type, k = op.k;
+        uint32_t adv = 1;
         if (type == OP_DENSE) {
             const uint32_t D = 1u << k;
             // the tensor-core form reads the op's B-fragment table instead of the matrix
             const bool tc = PREC != QSIM_PREC_FP32 && k >= (PREC == QSIM_PREC_TF32 ? 3u : 4u) && k <= 5 && T == 12;
             if (!tc)
-                for (uint32_t i = tid; i < D * D; i += NT) mat[i] = mats[S.op.mat + i];
+                for (uint32_t i = tid; i < D * D; i += NT) mat[i] = mats[op.mat + i];
             if (tid < int(D)) {
                 uint32_t o = 0;
-                for (uint32_t j = 0; j < k; ++j) o |= ((uint32_t(tid) >> j) & 1u) << S.op.tq[j];
+                for (uint32_t j = 0; j < k; ++j) o |= ((uint32_t(tid) >> j) & 1u) << op.tq[j];
                 S.offs[tid] = o;
             }
             __syncthreads();
-            if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, mat, bfr + S.op.bfrag, S, T);
+            if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, mat, bfr + op.bfrag, S, T);
         } else if (type == OP_DIAG) {
-            // phase index = bits constant over the tile | lookups over the tile bits
-            const uint32_t D = 1u << k;
-            for (uint32_t i = tid; i < D; i += NT) mat[i] = mats[S.op.mat + i];
-            if (tid < 48)  // the host-built phase-index tables, 192 bytes
-                reinterpret_cast<uint32_t *>(S.dlut_lo)[tid] =
-                    __ldg(reinterpret_cast<const uint32_t *>(mats + S.op.dlut) + tid);
-            if (tid == 0) {
+            // a run of r diagonal ops in one sweep; op d's phase index = bits constant over the
+            // tile | lookups over the tile bits
+            const uint32_t r = op.run;
+            adv = r;
+            for (uint32_t d = 0; d < r; ++d)
+                for (uint32_t i = tid; i < (1u << S.dop[d].k); i += NT) mat[S.dop[d].tab + i] = mats[S.dop[d].mat + i];
+            for (uint32_t t = tid; t < 48 * r; t += NT)  // the host-built phase-index tables, 192 bytes each
+                reinterpret_cast<uint32_t *>(S.dlut[t / 48])[t % 48] =
+                    __ldg(reinterpret_cast<const uint32_t *>(mats + S.dop[t / 48].dlut) + t % 48);
+            if (tid < int(r)) {
+                const OpDev &od = S.dop[tid];
                 uint32_t idx = 0;
-                for (uint32_t j = 0; j < k; ++j) {
-                    if (S.op.dtile[j] != 255) continue;
-                    const uint32_t src = S.op.dsrc[j];
+                for (uint32_t j = 0; j < od.k; ++j) {
+                    if (od.dtile[j] != 255) continue;
+                    const uint32_t src = od.dsrc[j];
                     const uint64_t bit = src < 64 ? (base >> src) & 1ull : (gb >> (src - 64)) & 1ull;
                     idx |= uint32_t(bit) << j;
                 }
-                S.dconst = idx;
+                S.dconst[tid] = idx;
             }
             __syncthreads();
-            const uint32_t dc = S.dconst;
+            uint32_t dc[kDiagRun], tb[kDiagRun];
+#pragma unroll
+            for (uint32_t d = 0; d < kDiagRun; ++d) {
+                dc[d] = d < r ? S.dconst[d] : 0u;
+                tb[d] = d < r ? S.dop[d].tab : 0u;
+            }
             for (uint32_t i = tid; i < (1u << T); i += NT) {
-                const float2 ph = mat[dc | S.dlut_lo[i & 127u] | S.dlut_hi[i >> 7]];
+                const uint32_t lo = i & 127u, hi = 128u + (i >> 7);
                 float2 &a = tile[swz(i)];
-                const float2 v = a;
-                a = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
+                float2 v = a;
+#pragma unroll
+                for (uint32_t d = 0; d < kDiagRun; ++d) {
+                    if (d < r) {
+                        const float2 ph = mat[tb[d] + (dc[d] | S.dlut[d][lo] | S.dlut[d][hi])];
+                        v = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
+                    }
+                }
+                a = v;
             }
         } else {
-            if (tid == 0 && S.op.basis_in_stage && gb == S.op.basis_outer &&
-                (S.op.basis_w & S.p.out_mask) == base) {
+            if (tid == 0 && op.basis_in_stage && gb == op.basis_outer && (op.basis_w & S.p.out_mask) == base) {
                 uint32_t ti = 0;
-                for (uint32_t t = 0; t < T; ++t) ti |= uint32_t((S.op.basis_w >> S.p.tile_pos[t]) & 1ull) << t;
+                for (uint32_t t = 0; t < T; ++t) ti |= uint32_t((op.basis_w >> S.p.tile_pos[t]) & 1ull) << t;
                 float2 &a = tile[swz(ti)];
                 a = make_float2(-a.x, -a.y);
             }
         }
+        oi += adv;
     }
+}
+
+// One tile of one pass: stage the 2^T amplitudes of tile `cta` of the group's
+// working vector g in shared memory, apply the pass's ops, store them back.
+// CG selects L2-only loads, needed when the working vector was written by
+// other CTAs of the same launch (the persistent stage kernel).
+template <int NT, int KMAX, int PREC, bool CG>
+__device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev *__restrict__ pd,
+                                          const OpDev *__restrict__ ops, const float2 *__restrict__ mats,
+                                          const uint32_t *__restrict__ bfr, uint64_t cta, uint64_t gb, PassSmem &S,
+                                          float2 *tile) {
+    pass_setup<NT>(pd, S);
+    const uint64_t base = tile_base(S, cta);
+    tile_load<NT, CG>(g, base, S, tile);
+    if constexpr (!CG) cp_async_wait_all();
+    tile_ops<NT, KMAX, PREC>(tile, tile + (1u << S.p.T), ops, mats, bfr, base, gb, S);
     __syncthreads();
-    for (uint32_t i = tid; i < (1u << T); i += NT) g[base | (i & lmask) | S.hi[i >> L]] = tile[swz(i)];
+    tile_store<NT>(g, base, S, tile);
 }
 
 }  // namespace gdev

@@ -59,8 +59,8 @@ def test_batch_mixed_sizing_with_learned_predictor():
                 inputs.random_brick(13, 6, 22)]
     plans = []
     for i, c in enumerate(circuits):
-        if i % 2 == 0:  # learned sizing; the second margin forces every block through the exact re-encode
-            plans.append(qsim.plan_stages(c, sizing=qsim.SIZING_PREDICT, predictor_margin=(0.25, -0.9)[i // 2],
+        if i % 2 == 0:  # learned sizing; the first margin forces every block through the exact re-encode
+            plans.append(qsim.plan_stages(c, sizing=qsim.SIZING_PREDICT, predictor_margin=(-0.9, 0.25)[i // 2],
                                           **kw))
         else:
             plans.append(qsim.plan_stages(c, **kw))
@@ -69,7 +69,7 @@ def test_batch_mixed_sizing_with_learned_predictor():
         nblocks = 1 << (c.n - p.cfg.m)
         ref = qsim.run(qsim.plan_stages(c, **kw))
         assert streams_of(ref, nblocks) == streams_of(st, nblocks)
-    assert states[2].stats.overflow_blocks > 0
+    assert states[0].stats.overflow_blocks > 0
 
 
 def test_batch_bounded_wait_reports_timeout():
