@@ -196,8 +196,17 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
                 const bool live = c0 + t < g.C;
-                xr[t] = (live && lane < int(wr[t])) ? __ldg(payload + offr + sr_ + lane) : 0u;
-                xi[t] = (live && lane < int(wi[t])) ? __ldg(payload + offi + si_ + lane) : 0u;
+                if (wr[t] <= 16 && wi[t] <= 16) {
+                    // packed: lane b < 16 loads Re plane b, lane 16 + b Im plane b (one transpose below)
+                    const uint32_t b = uint32_t(lane) & 15u;
+                    xr[t] = (live && b < (lane < 16 ? wr[t] : wi[t]))
+                                ? __ldg(payload + (lane < 16 ? offr + sr_ : offi + si_) + b)
+                                : 0u;
+                    xi[t] = 0u;
+                } else {
+                    xr[t] = (live && lane < int(wr[t])) ? __ldg(payload + offr + sr_ + lane) : 0u;
+                    xi[t] = (live && lane < int(wi[t])) ? __ldg(payload + offi + si_ + lane) : 0u;
+                }
                 sr_ += wr[t];
                 si_ += wi[t];
             }
@@ -206,8 +215,15 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
         for (int t = 0; t < 8; ++t) {
             const uint32_t c = c0 + t;
             if (c >= g.C) break;
-            const uint32_t zr = warp_bit_transpose(xr[t], lane);
-            const uint32_t zi = warp_bit_transpose(xi[t], lane);
+            uint32_t zr, zi;
+            if (wr[t] <= 16 && wi[t] <= 16) {
+                const uint32_t y = warp_bit_transpose(xr[t], lane);
+                zr = y & 0xffffu;
+                zi = y >> 16;
+            } else {
+                zr = warp_bit_transpose(xr[t], lane);
+                zi = warp_bit_transpose(xi[t], lane);
+            }
             uint32_t qr = uint32_t(unzigzag(zr)), qi = uint32_t(unzigzag(zi));
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -650,11 +666,18 @@ __device__ __forceinline__ void encode_frame_warp_known(const float2 *__restrict
             const int32_t pi = __shfl_up_sync(kFull, q[1], 1);
             const uint32_t zr = zigzag(lane ? int32_t(uint32_t(q[0]) - uint32_t(pr)) : q[0]);
             const uint32_t zi = zigzag(lane ? int32_t(uint32_t(q[1]) - uint32_t(pi)) : q[1]);
-            const uint32_t word_r = warp_bit_transpose(zr, lane);
-            const uint32_t word_i = warp_bit_transpose(zi, lane);
-            if (payload) {
-                if (lane < int(wr)) payload[offr + sr_ + lane] = word_r;
-                if (lane < int(wi)) payload[offi + si_ + lane] = word_i;
+            if (wr <= 16 && wi <= 16) {
+                // both planes in one transpose: lane b < 16 gets Re plane b, lane 16 + b Im plane b
+                const uint32_t word = warp_bit_transpose(zr | (zi << 16), lane);
+                const uint32_t b = uint32_t(lane) & 15u;
+                if (payload && b < (lane < 16 ? wr : wi)) payload[(lane < 16 ? offr + sr_ : offi + si_) + b] = word;
+            } else {
+                const uint32_t word_r = warp_bit_transpose(zr, lane);
+                const uint32_t word_i = warp_bit_transpose(zi, lane);
+                if (payload) {
+                    if (lane < int(wr)) payload[offr + sr_ + lane] = word_r;
+                    if (lane < int(wi)) payload[offi + si_ + lane] = word_i;
+                }
             }
             sr_ += wr;
             si_ += wi;

@@ -314,6 +314,8 @@ struct StageDev {
     std::vector<PassDev> passes_host;
 };
 
+static_assert(sizeof(OpDev) == kOpDescBytes, "the planner sizes pass blobs by the descriptor size");
+
 struct PlanDev {
     bool ready = false;
     int device = -1;
@@ -321,6 +323,7 @@ struct PlanDev {
     DevBuf<OpDev> ops;
     DevBuf<float2> mats;
     DevBuf<uint32_t> bfr;     // B-fragment tables of the dense ops (tensor-core precisions)
+    DevBuf<uint4> blob;       // per pass: op descriptors, phase tables and index tables, small matrices
     DevBuf<uint32_t> ids;     // per stage: 2^c block ids, group-major
     DevBuf<uint64_t> gbase;   // per stage: per group outer bits
     std::vector<StageDev> stages;
@@ -381,6 +384,7 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
     pd->device = dev;
     const uint32_t n = p->n, m = p->cfg.m, c = n - m;
     std::vector<PassDev> passes;
+    std::vector<uint4> blob;
     std::vector<OpDev> ops;
     std::vector<float2> mats;
     std::vector<uint32_t> bfr;
@@ -521,48 +525,78 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                                 for (uint32_t t = 0; t < ps.T; ++t)
                                     if (ps.tile_pos[t] == od.dsrc[j]) od.dtile[j] = t;
                         }
-                        // phase-index bits contributed by tile bits 0..6 (128 bytes) and 7..12 (64 bytes)
-                        uint8_t lut[192];
-                        for (uint32_t v = 0; v < 192; ++v) {
-                            const bool lo = v < 128;
-                            const uint32_t x = lo ? v : v - 128;
-                            uint32_t idx = 0;
-                            for (uint32_t j = 0; j < op.k; ++j) {
-                                const uint32_t t = od.dtile[j];
-                                if (t == 255) continue;
-                                if (lo && t < 7) idx |= ((x >> t) & 1u) << j;
-                                if (!lo && t >= 7) idx |= ((x >> (t - 7)) & 1u) << j;
-                            }
-                            lut[v] = uint8_t(idx);
-                        }
-                        while (mats.size() & 1) mats.push_back(make_float2(0, 0));  // 16-byte aligned
-                        od.dlut = mats.size();
-                        for (uint32_t w = 0; w < 24; ++w) {
-                            float2 f;
-                            memcpy(&f, lut + 8 * w, 8);
-                            mats.push_back(f);
-                        }
                     }
                 }
                 ops.push_back(od);
             }
-            // runs of consecutive diagonal ops applied in one sweep; their phase tables side by side
+            // runs of consecutive diagonal ops applied in one sweep
             for (uint32_t a = P.op_begin; a < P.op_begin + P.op_count;) {
                 if (ops[a].type != OP_DIAG) {
                     ++a;
                     continue;
                 }
-                uint32_t b = a, elems = 0;
-                while (b < P.op_begin + P.op_count && b - a < kDiagRun && ops[b].type == OP_DIAG &&
-                       elems + (1u << ops[b].k) <= std::max<uint32_t>(kDiagRunElems, 1u << ops[a].k)) {
-                    ops[b].tab = elems;
-                    ops[b].run = 0;
-                    elems += 1u << ops[b].k;
-                    ++b;
-                }
+                uint32_t b = a;
+                while (b < P.op_begin + P.op_count && b - a < kDiagRun && ops[b].type == OP_DIAG) ops[b++].run = 0;
                 ops[a].run = b - a;
-                P.mat_elems = std::max<uint32_t>(P.mat_elems, elems);
                 a = b;
+            }
+            // the pass blob: descriptors, then per diagonal op its index tables (tile bits 0..6 and
+            // 7..12, 192 bytes) and its phases, then CUDA-core dense matrices while they fit
+            {
+                std::vector<uint8_t> pb(size_t(P.op_count) * sizeof(OpDev));
+                auto align16 = [&]() { pb.resize((pb.size() + 15) & ~size_t(15), 0); };
+                const uint32_t min_k = p->cfg.prec == QSIM_PREC_TF32 ? 3u : 4u;
+                P.mat_elems = 0;
+                for (uint32_t a = 0; a < P.op_count; ++a) {
+                    OpDev &od = ops[P.op_begin + a];
+                    const Op &op = st.ops[ps.ops[a]];
+                    od.tab = kNoTab;
+                    if (od.type == OP_DIAG) {
+                        align16();
+                        od.dlut = uint32_t(pb.size() / 8);
+                        for (uint32_t v = 0; v < 192; ++v) {
+                            const bool lo = v < 128;
+                            const uint32_t x = lo ? v : v - 128;
+                            uint32_t idx = 0;
+                            for (uint32_t j = 0; j < od.k; ++j) {
+                                const uint32_t t = od.dtile[j];
+                                if (t == 255) continue;
+                                if (lo && t < 7) idx |= ((x >> t) & 1u) << j;
+                                if (!lo && t >= 7) idx |= ((x >> (t - 7)) & 1u) << j;
+                            }
+                            pb.push_back(uint8_t(idx));
+                        }
+                        align16();
+                        od.tab = uint32_t(pb.size() / 8);
+                        for (const cd &v : op.u) {
+                            const float2 f = make_float2(float(v.real()), float(v.imag()));
+                            const uint8_t *fb = reinterpret_cast<const uint8_t *>(&f);
+                            pb.insert(pb.end(), fb, fb + 8);
+                        }
+                    } else if (od.type == OP_DENSE) {
+                        const bool tc = p->cfg.prec != QSIM_PREC_FP32 && od.k >= min_k && od.k <= 5 && ps.T == 12;
+                        if (tc) continue;
+                        const size_t mb = size_t(8) << (2 * od.k);
+                        if (((pb.size() + 15) & ~size_t(15)) + mb <= kPassBlobMax) {
+                            align16();
+                            od.tab = uint32_t(pb.size() / 8);
+                            for (const cd &v : op.u) {
+                                const float2 f = make_float2(float(v.real()), float(v.imag()));
+                                const uint8_t *fb = reinterpret_cast<const uint8_t *>(&f);
+                                pb.insert(pb.end(), fb, fb + 8);
+                            }
+                        } else {
+                            P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << (2 * od.k));
+                        }
+                    }
+                }
+                align16();
+                memcpy(pb.data(), ops.data() + P.op_begin, size_t(P.op_count) * sizeof(OpDev));
+                P.blob_off = uint32_t(blob.size());
+                P.blob_words = uint32_t(pb.size() / 16);
+                const size_t w0 = blob.size();
+                blob.resize(w0 + P.blob_words);
+                memcpy(blob.data() + w0, pb.data(), pb.size());
             }
             P.mat_elems = (P.mat_elems + 1) & ~1u;
             sd.passes_host.push_back(P);
@@ -572,10 +606,11 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
     }
     if (mats.empty()) mats.push_back(make_float2(0, 0));
     if (bfr.empty()) bfr.push_back(0);
+    if (blob.empty()) blob.push_back(make_uint4(0, 0, 0, 0));
     int rc;
     if ((rc = pd->passes.alloc(passes.size())) || (rc = pd->ops.alloc(ops.size())) ||
         (rc = pd->mats.alloc(mats.size())) || (rc = pd->ids.alloc(ids.size())) || (rc = pd->bfr.alloc(bfr.size())) ||
-        (rc = pd->gbase.alloc(gbases.size()))) {
+        (rc = pd->gbase.alloc(gbases.size())) || (rc = pd->blob.alloc(blob.size()))) {
         delete pd;
         return rc;
     }
@@ -585,8 +620,9 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
     CUDA_TRY(cudaMemcpy(pd->bfr.p, bfr.data(), bfr.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pd->ids.p, ids.data(), ids.size() * sizeof(uint32_t), cudaMemcpyHostToDevice));
     CUDA_TRY(cudaMemcpy(pd->gbase.p, gbases.data(), gbases.size() * sizeof(uint64_t), cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(pd->blob.p, blob.data(), blob.size() * sizeof(uint4), cudaMemcpyHostToDevice));
     pd->upload_bytes = passes.size() * sizeof(PassDev) + ops.size() * sizeof(OpDev) + mats.size() * sizeof(float2) +
-                       bfr.size() * sizeof(uint32_t) +
+                       bfr.size() * sizeof(uint32_t) + blob.size() * sizeof(uint4) +
                        ids.size() * sizeof(uint32_t) + gbases.size() * sizeof(uint64_t);
     pd->ready = true;
     if (it != g_plan_dev.end()) delete it->second;
@@ -949,7 +985,7 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
     for (size_t k = 0; k < nseg; ++k) seg_of[order[k].c][order[k].si] = uint32_t(k);
 
     uint64_t slot_amps = 0, slot_frames = 0, total_groups = 0;
-    uint32_t maxT = 5, max_mat = 0;
+    size_t max_pass_bytes = 0;
     for (const SegRef &sr : order) {
         const RunCtx &R = *rs[sr.c];
         const StageDev &sd = R.pd->stages[sr.si];
@@ -957,8 +993,8 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         slot_frames = std::max<uint64_t>(slot_frames, uint64_t(sd.G) * R.nframes);
         total_groups += sd.ngroups;
         for (const PassDev &ps : sd.passes_host) {
-            maxT = std::max(maxT, ps.T);
-            max_mat = std::max(max_mat, ps.mat_elems);
+            max_pass_bytes = std::max(max_pass_bytes, (size_t(1) << ps.T) * sizeof(float2) + size_t(ps.blob_words) * 16 +
+                                                          size_t(ps.mat_elems) * sizeof(float2));
             if (ps.kmax > 5) return set_error(QSIM_E_INVALID, "persistent mode fuses at most k = 5 qubits");
         }
     }
@@ -1052,6 +1088,7 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         a.passes = R.pd->passes.p + sd.pass_begin;
         a.ops = R.pd->ops.p;
         a.mats = R.pd->mats.p;
+        a.blob = R.pd->blob.p;
         a.bfr = R.pd->bfr.p;
         a.ids = R.pd->ids.p + R.pd->ids_off[si];
         a.gbase = R.pd->gbase.p + R.pd->gbase_off[si];
@@ -1093,7 +1130,7 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         }
     }
     CUDA_TRY(cudaMemcpyAsync(dsegs.p, segs.data(), nseg * sizeof(PSeg), cudaMemcpyHostToDevice, main));
-    const size_t smem = persistent_smem_bytes(maxT, max_mat);
+    const size_t smem = persistent_smem_bytes(max_pass_bytes);
     if ((rc = prepare_stage_persistent(prec, smem))) return set_error(rc, "persistent kernel set-up failed");
 
     PLaunch L{};
@@ -1443,8 +1480,8 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             }
             for (uint32_t pi = 0; pi < sd.npasses; ++pi) {
                 prof.begin(P_PASS, w.s);
-                launch_pass(w.wv.p, sd.W, ng, &sd.passes_host[pi], pd->passes.p + sd.pass_begin + pi, pd->ops.p,
-                            pd->mats.p, pd->bfr.p, gb_stage + g0, cfg.prec, w.s);
+                launch_pass(w.wv.p, sd.W, ng, &sd.passes_host[pi], pd->blob.p, pd->mats.p, pd->bfr.p, gb_stage + g0,
+                            cfg.prec, w.s);
                 prof.end(w.s);
             }
             if (raw) {

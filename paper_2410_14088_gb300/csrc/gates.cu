@@ -36,38 +36,38 @@ constexpr int NT = 128;
 // passes.)
 template <int KMAX, int PREC>
 __global__ void __launch_bounds__(NT, (KMAX >= 6 ? 2 : (PREC == QSIM_PREC_BF16X3 && KMAX >= 4) ? 3 : 4))
-    k_pass(float2 *__restrict__ wv, uint32_t W, const PassDev *__restrict__ pd, const OpDev *__restrict__ ops,
+    k_pass(float2 *__restrict__ wv, uint32_t W, const __grid_constant__ PassDev P, const uint4 *__restrict__ blob,
            const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr, const uint64_t *__restrict__ gbase) {
     extern __shared__ float4 dyn_smem[];
     __shared__ PassSmem S;
     float2 *g = wv + (uint64_t(blockIdx.y) << W);
     const uint64_t gb = gbase ? gbase[blockIdx.y] : 0ull;
-    pass_tile<NT, KMAX, PREC, false>(g, pd, ops, mats, bfr, blockIdx.x, gb, S, reinterpret_cast<float2 *>(dyn_smem));
+    pass_tile<NT, KMAX, PREC, false>(g, P, blob, mats, bfr, blockIdx.x, gb, S, reinterpret_cast<float2 *>(dyn_smem));
 }
 
 template <int KMAX, int PREC>
-void launch_pass_k(dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W, const PassDev *pd,
-                   const OpDev *ops, const float2 *mats, const uint32_t *bfr, const uint64_t *gbase) {
+void launch_pass_k(dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W, const PassDev &P,
+                   const uint4 *blob, const float2 *mats, const uint32_t *bfr, const uint64_t *gbase) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_pass<KMAX, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr_set = true;
     }
-    k_pass<KMAX, PREC><<<grid, NT, smem, s>>>(wv, W, pd, ops, mats, bfr, gbase);
+    k_pass<KMAX, PREC><<<grid, NT, smem, s>>>(wv, W, P, blob, mats, bfr, gbase);
 }
 
 template <int PREC>
 void launch_pass_prec(uint32_t kmax, dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W,
-                      const PassDev *pd, const OpDev *ops, const float2 *mats, const uint32_t *bfr,
+                      const PassDev &P, const uint4 *blob, const float2 *mats, const uint32_t *bfr,
                       const uint64_t *gbase) {
     switch (kmax) {
-        case 0: launch_pass_k<0, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
-        case 1: launch_pass_k<1, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
-        case 2: launch_pass_k<2, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
-        case 3: launch_pass_k<3, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
-        case 4: launch_pass_k<4, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
-        case 5: launch_pass_k<5, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
-        default: launch_pass_k<6, PREC>(grid, smem, s, wv, W, pd, ops, mats, bfr, gbase); break;
+        case 0: launch_pass_k<0, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
+        case 1: launch_pass_k<1, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
+        case 2: launch_pass_k<2, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
+        case 3: launch_pass_k<3, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
+        case 4: launch_pass_k<4, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
+        case 5: launch_pass_k<5, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
+        default: launch_pass_k<6, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
     }
 }
 
@@ -144,19 +144,21 @@ void build_bfrag_table(const double *u, uint32_t k, int prec, uint32_t *out) {
             }
 }
 
-void launch_pass(float2 *wv, uint32_t W, uint32_t ngroups, const PassDev *pass_host, const PassDev *pass_dev,
-                 const OpDev *ops_dev, const float2 *mats_dev, const uint32_t *bfr_dev, const uint64_t *gbase_dev,
-                 int prec, cudaStream_t s) {
-    const uint32_t T = pass_host->T;
-    const size_t smem = (size_t(1) << T) * sizeof(float2) + size_t(pass_host->mat_elems) * sizeof(float2);
-    dim3 grid(1u << pass_host->nout, ngroups);
-    const uint32_t kmax = pass_host->kmax;
+void launch_pass(float2 *wv, uint32_t W, uint32_t ngroups, const PassDev *pass_host, const uint4 *blob_dev,
+                 const float2 *mats_dev, const uint32_t *bfr_dev, const uint64_t *gbase_dev, int prec,
+                 cudaStream_t s) {
+    const PassDev &P = *pass_host;
+    // tile, pass blob, matrix area
+    const size_t smem = (size_t(1) << P.T) * sizeof(float2) + size_t(P.blob_words) * 16 +
+                        size_t(P.mat_elems) * sizeof(float2);
+    dim3 grid(1u << P.nout, ngroups);
+    const uint32_t kmax = P.kmax;
     if (prec == QSIM_PREC_TF32 && kmax >= 3)
-        launch_pass_prec<QSIM_PREC_TF32>(kmax, grid, smem, s, wv, W, pass_dev, ops_dev, mats_dev, bfr_dev, gbase_dev);
+        launch_pass_prec<QSIM_PREC_TF32>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev);
     else if (prec == QSIM_PREC_BF16X3 && kmax >= 3)
-        launch_pass_prec<QSIM_PREC_BF16X3>(kmax, grid, smem, s, wv, W, pass_dev, ops_dev, mats_dev, bfr_dev, gbase_dev);
+        launch_pass_prec<QSIM_PREC_BF16X3>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev);
     else
-        launch_pass_prec<QSIM_PREC_FP32>(kmax, grid, smem, s, wv, W, pass_dev, ops_dev, mats_dev, bfr_dev, gbase_dev);
+        launch_pass_prec<QSIM_PREC_FP32>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev);
     count_launch();
 }
 

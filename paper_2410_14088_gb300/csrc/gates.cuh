@@ -17,8 +17,10 @@ struct PassDev {
     uint32_t L;              // tile_pos[t] == t for t < L
     uint32_t nout;           // W - T
     uint32_t op_begin, op_count;
-    uint32_t mat_elems;      // largest matrix / phase table of the pass, in float2
+    uint32_t mat_elems;      // float2 of the matrix area (dense ops whose matrix is not in the blob)
     uint32_t kmax;           // widest dense op of the pass (0 if none)
+    uint32_t blob_words;     // 16-byte words of the pass blob: op descriptors, phase tables, small matrices
+    uint32_t blob_off;       // its first word in the plan's blob array
     uint32_t pad0;
     uint64_t out_mask;       // working-index mask of the non-tile bits
     uint32_t tile_pos[16];   // working bit of tile bit t (ascending)
@@ -28,8 +30,9 @@ struct PassDev {
 struct __align__(16) OpDev {
     uint32_t type;           // 0 dense, 1 diagonal, 2 phase flip
     uint32_t k;
-    uint32_t mat;            // float2 offset of the matrix (dense) or phases (diag)
-    uint32_t dlut;           // diag in a pass: float2 offset of its 192 phase-index bytes (see PassSmem)
+    uint32_t mat;            // float2 offset of the matrix (dense) or phases (diag) in the plan's matrix array
+    uint32_t dlut;           // diag: float2 offset of its phase-index byte tables (pass: in the blob; decoder
+                             // pre-op: in the matrix array)
     uint32_t tq[6];          // dense: tile bit of matrix bit j
     uint32_t dsrc[8];        // diag: working bit (< 64) or 64 + full qubit (outer, from group base)
     uint32_t dtile[8];       // diag in a pass: tile bit of qubit j, or 255 when the bit is constant over a tile
@@ -39,11 +42,13 @@ struct __align__(16) OpDev {
     uint32_t basis_in_stage; // phase flip: 1 if the basis' outer bits can match a group
     uint32_t bfrag;          // dense, tensor-core precisions: word offset of the op's B-fragment table
     uint32_t run;            // diag in a pass: ops applied in one sweep from here (0 inside a run)
-    uint32_t tab;            // diag in a pass: float2 offset of its phases in the pass's shared table area
+    uint32_t tab;            // in a pass: float2 offset in the blob of the phases (diag) or of the matrix
+                             // (dense on CUDA cores), kNoTab when not there
 };
 
-constexpr uint32_t kDiagRun = 4;           // diagonal ops applied in one sweep over a tile
-constexpr uint32_t kDiagRunElems = 1024;   // their phase tables together, in float2
+constexpr uint32_t kDiagRun = 4;            // diagonal ops applied in one sweep over a tile
+constexpr uint32_t kNoTab = 0xffffffffu;
+constexpr uint32_t kPassBlobMax = 40960;    // bytes of one pass blob (shared memory next to the tile)
 
 // wv: ngroups consecutive working vectors of 2^W amplitudes; gbase[g] is the
 // full-index value of group g's outer bits.
@@ -57,8 +62,8 @@ constexpr uint32_t kDiagRunElems = 1024;   // their phase tables together, in fl
 void build_bfrag_table(const double *u_interleaved, uint32_t k, int prec, uint32_t *out);
 size_t bfrag_words(uint32_t k, int prec);
 
-void launch_pass(float2 *wv, uint32_t W, uint32_t ngroups, const PassDev *pass_host, const PassDev *pass_dev,
-                 const OpDev *ops_dev, const float2 *mats_dev, const uint32_t *bfr_dev, const uint64_t *gbase_dev,
-                 int prec, cudaStream_t s);
+void launch_pass(float2 *wv, uint32_t W, uint32_t ngroups, const PassDev *pass_host, const uint4 *blob_dev,
+                 const float2 *mats_dev, const uint32_t *bfr_dev, const uint64_t *gbase_dev, int prec,
+                 cudaStream_t s);
 
 }  // namespace qsim

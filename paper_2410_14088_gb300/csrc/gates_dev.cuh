@@ -19,28 +19,24 @@ __device__ __forceinline__ uint32_t swz(uint32_t i) {
     return i ^ (((i >> 4) ^ (i >> 8) ^ (i >> 12)) & 15u);
 }
 
-// CTA-cooperative copy of a descriptor (4-byte words)
+// CTA-cooperative copy of a descriptor (4-byte words; src may be kernel-parameter or global memory)
 template <int NT, class T>
-__device__ __forceinline__ void coop_copy(T &dst, const T *__restrict__ src) {
+__device__ __forceinline__ void coop_copy(T &dst, const T &src) {
     static_assert(sizeof(T) % 4 == 0, "descriptor size");
-    const uint32_t *s = reinterpret_cast<const uint32_t *>(src);
+    const uint32_t *s = reinterpret_cast<const uint32_t *>(&src);
     uint32_t *d = reinterpret_cast<uint32_t *>(&dst);
-    for (int t = threadIdx.x; t < int(sizeof(T) / 4); t += NT) d[t] = __ldg(s + t);
+    for (int t = threadIdx.x; t < int(sizeof(T) / 4); t += NT) d[t] = s[t];
 }
 
 struct PassSmem {
     PassDev p;
-    OpDev dop[kDiagRun];   // the next op (dense, phase flip) or run of diagonal ops
     uint32_t hi[256];
     uint32_t off12[32];    // 4096-amplitude tiles with L >= log2(NT): working offset of element tid + NT u, minus tid
-    uint32_t offs[64];
-    // diagonal op d of a run: phase-index bits contributed by tile bits 0..6
-    // (bytes 0..127) and by tile bits 7..12 (bytes 128..191)
-    uint8_t dlut[kDiagRun][192];
-    uint32_t dconst[kDiagRun];  // and by the bits that are constant over the tile
+    uint32_t offs[64];     // dense op: working offsets of its 2^k matrix columns within the tile
+    uint32_t comp[16];     // dense op: its complement tile bits
+    uint32_t dconst[kDiagRun];  // diagonal op d of a run: phase-index bits constant over the tile
 };
-static_assert(offsetof(PassSmem, dlut) % 4 == 0 && offsetof(PassSmem, dop) % 16 == 0 && sizeof(OpDev) % 16 == 0,
-              "descriptors and phase-index tables are copied as words");
+static_assert(sizeof(OpDev) % 16 == 0, "op descriptors are copied as 16-byte words");
 
 template <int NT, int K>
 __device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const PassSmem &S, uint32_t T) {
@@ -49,7 +45,7 @@ __device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const
     const uint32_t nc = T - K;
     for (uint32_t g = threadIdx.x; g < ngroups; g += NT) {
         uint32_t b = 0;
-        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.dop[0].comp[t];
+        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.comp[t];
         float2 x[D];
 #pragma unroll
         for (int c = 0; c < D; ++c) x[c] = tile[swz(b | S.offs[c])];
@@ -85,7 +81,7 @@ __device__ __forceinline__ void apply_dense_k1(float2 *tile, const float2 *U, co
     const float2 u00 = U[0], u01 = U[1], u10 = U[2], u11 = U[3];
     for (uint32_t g = threadIdx.x; g < ngroups; g += NT) {
         uint32_t b = 0;
-        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.dop[0].comp[t];
+        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.comp[t];
         const uint32_t i0 = swz(b), i1 = swz(b | S.offs[1]);
         const float2 x0 = tile[i0], x1 = tile[i1];
         tile[i0] = make_float2(u00.x * x0.x - u00.y * x0.y + u01.x * x1.x - u01.y * x1.y,
@@ -102,6 +98,10 @@ __device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_wait_all() {
     asm volatile("cp.async.commit_group;\n" ::: "memory");
     asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const uint32_t sa = static_cast<uint32_t>(__cvta_generic_to_shared(smem));
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 // all but the most recent committed group complete
@@ -175,7 +175,7 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
         for (int h = 0; h < 2; ++h) {
             const uint32_t g = row0 + mt * 16 + gq + 8 * h;
             uint32_t b = 0;
-            for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.dop[0].comp[t];
+            for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.comp[t];
             base[mt][h] = b;
         }
     float acc[MT * NTILES][4];
@@ -304,7 +304,7 @@ __device__ __forceinline__ void apply_dense_dispatch(uint32_t k, float2 *tile, c
 // Per pass, once per CTA: the pass descriptor and the offsets of the tile's
 // high part (tile bits L..T-1 placed at their working bits).
 template <int NT>
-__device__ __forceinline__ void pass_setup(const PassDev *__restrict__ pd, PassSmem &S) {
+__device__ __forceinline__ void pass_setup(const PassDev &pd, PassSmem &S) {
     coop_copy<NT>(S.p, pd);
     __syncthreads();
     const uint32_t T = S.p.T, L = S.p.L;
@@ -407,51 +407,55 @@ __device__ __forceinline__ void tile_store(float2 *__restrict__ g, uint64_t base
     for (uint32_t i = threadIdx.x; i < (1u << T); i += NT) g[base | (i & lmask) | S.hi[i >> L]] = tile[swz(i)];
 }
 
-// The pass's ops on a staged tile (mat: the shared matrix / phase-table area).
-// Starts with a CTA barrier, so the tile's loads need only have completed per thread.
+// The pass blob (op descriptors, diagonal ops' index tables and phases, small
+// dense matrices) staged in shared memory with 16-byte cp.async.
+template <int NT>
+__device__ __forceinline__ void blob_load(const uint4 *__restrict__ gblob, uint32_t words, uint4 *sblob) {
+    for (uint32_t t = threadIdx.x; t < words; t += NT) cp_async16(sblob + t, gblob + t);
+}
+
+// The pass's ops on a staged tile; blob: the staged pass blob; mat: the matrix
+// area for dense ops whose matrix is not in the blob. Starts with a CTA
+// barrier, so the tile's and blob's loads need only have completed per thread.
 template <int NT, int KMAX, int PREC>
-__device__ __forceinline__ void tile_ops(float2 *tile, float2 *mat, const OpDev *__restrict__ ops,
+__device__ __forceinline__ void tile_ops(float2 *tile, const uint4 *blob, float2 *mat,
                                          const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr,
                                          uint64_t base, uint64_t gb, PassSmem &S) {
     const int tid = threadIdx.x;
     const uint32_t T = S.p.T;
+    const OpDev *bops = reinterpret_cast<const OpDev *>(blob);
+    const float2 *bf2 = reinterpret_cast<const float2 *>(blob);
+    const uint8_t *bb = reinterpret_cast<const uint8_t *>(blob);
     for (uint32_t oi = 0; oi < S.p.op_count;) {
         __syncthreads();
-        {  // descriptors of the next op, or of the next run of diagonal ops
-            const uint32_t avail = min(kDiagRun, S.p.op_count - oi);
-            const uint4 *src = reinterpret_cast<const uint4 *>(ops + S.p.op_begin + oi);
-            uint4 *dst = reinterpret_cast<uint4 *>(S.dop);
-            for (uint32_t t = tid; t < avail * uint32_t(sizeof(OpDev) / 16); t += NT) dst[t] = __ldg(src + t);
-        }
-        __syncthreads();
-        const OpDev &op = S.dop[0];
+        const OpDev &op = bops[oi];
         const uint32_t type = op.type, k = op.k;
         uint32_t adv = 1;
         if (type == OP_DENSE) {
             const uint32_t D = 1u << k;
-            // the tensor-core form reads the op's B-fragment table instead of the matrix
+            // the tensor-core form reads the op's B-fragment table; the CUDA-core form its matrix
             const bool tc = PREC != QSIM_PREC_FP32 && k >= (PREC == QSIM_PREC_TF32 ? 3u : 4u) && k <= 5 && T == 12;
-            if (!tc)
-                for (uint32_t i = tid; i < D * D; i += NT) mat[i] = mats[op.mat + i];
+            const float2 *M = mat;
+            if (!tc) {
+                if (op.tab != kNoTab) M = bf2 + op.tab;
+                else
+                    for (uint32_t i = tid; i < D * D; i += NT) mat[i] = mats[op.mat + i];
+            }
             if (tid < int(D)) {
                 uint32_t o = 0;
                 for (uint32_t j = 0; j < k; ++j) o |= ((uint32_t(tid) >> j) & 1u) << op.tq[j];
                 S.offs[tid] = o;
             }
+            if (tid < 16) S.comp[tid] = op.comp[tid];
             __syncthreads();
-            if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, mat, bfr + op.bfrag, S, T);
+            if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, M, bfr + op.bfrag, S, T);
         } else if (type == OP_DIAG) {
             // a run of r diagonal ops in one sweep; op d's phase index = bits constant over the
-            // tile | lookups over the tile bits
+            // tile | lookups over the tile bits 0..6 and 7..12
             const uint32_t r = op.run;
             adv = r;
-            for (uint32_t d = 0; d < r; ++d)
-                for (uint32_t i = tid; i < (1u << S.dop[d].k); i += NT) mat[S.dop[d].tab + i] = mats[S.dop[d].mat + i];
-            for (uint32_t t = tid; t < 48 * r; t += NT)  // the host-built phase-index tables, 192 bytes each
-                reinterpret_cast<uint32_t *>(S.dlut[t / 48])[t % 48] =
-                    __ldg(reinterpret_cast<const uint32_t *>(mats + S.dop[t / 48].dlut) + t % 48);
             if (tid < int(r)) {
-                const OpDev &od = S.dop[tid];
+                const OpDev &od = bops[oi + tid];
                 uint32_t idx = 0;
                 for (uint32_t j = 0; j < od.k; ++j) {
                     if (od.dtile[j] != 255) continue;
@@ -462,11 +466,12 @@ __device__ __forceinline__ void tile_ops(float2 *tile, float2 *mat, const OpDev 
                 S.dconst[tid] = idx;
             }
             __syncthreads();
-            uint32_t dc[kDiagRun], tb[kDiagRun];
+            uint32_t dc[kDiagRun], tb[kDiagRun], lb[kDiagRun];
 #pragma unroll
             for (uint32_t d = 0; d < kDiagRun; ++d) {
                 dc[d] = d < r ? S.dconst[d] : 0u;
-                tb[d] = d < r ? S.dop[d].tab : 0u;
+                tb[d] = d < r ? bops[oi + d].tab : 0u;
+                lb[d] = d < r ? 8u * bops[oi + d].dlut : 0u;
             }
             for (uint32_t i = tid; i < (1u << T); i += NT) {
                 const uint32_t lo = i & 127u, hi = 128u + (i >> 7);
@@ -475,7 +480,7 @@ __device__ __forceinline__ void tile_ops(float2 *tile, float2 *mat, const OpDev 
 #pragma unroll
                 for (uint32_t d = 0; d < kDiagRun; ++d) {
                     if (d < r) {
-                        const float2 ph = mat[tb[d] + (dc[d] | S.dlut[d][lo] | S.dlut[d][hi])];
+                        const float2 ph = bf2[tb[d] + (dc[d] | bb[lb[d] + lo] | bb[lb[d] + hi])];
                         v = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
                     }
                 }
@@ -493,20 +498,25 @@ __device__ __forceinline__ void tile_ops(float2 *tile, float2 *mat, const OpDev 
     }
 }
 
-// One tile of one pass: stage the 2^T amplitudes of tile `cta` of the group's
-// working vector g in shared memory, apply the pass's ops, store them back.
-// CG selects L2-only loads, needed when the working vector was written by
-// other CTAs of the same launch (the persistent stage kernel).
+// One tile of one pass: stage the pass blob and the 2^T amplitudes of tile
+// `cta` of the group's working vector g in shared memory (dyn: tile, then blob,
+// then matrix area), apply the pass's ops, store the tile back. CG selects
+// L2-only loads, needed when the working vector was written by other CTAs of
+// the same launch (the persistent stage kernel).
 template <int NT, int KMAX, int PREC, bool CG>
-__device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev *__restrict__ pd,
-                                          const OpDev *__restrict__ ops, const float2 *__restrict__ mats,
-                                          const uint32_t *__restrict__ bfr, uint64_t cta, uint64_t gb, PassSmem &S,
-                                          float2 *tile) {
+__device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev &pd, const uint4 *__restrict__ gblob,
+                                          const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr,
+                                          uint64_t cta, uint64_t gb, PassSmem &S, float2 *dyn) {
     pass_setup<NT>(pd, S);
+    const uint32_t T = S.p.T;
+    float2 *tile = dyn;
+    uint4 *blob = reinterpret_cast<uint4 *>(dyn + (1u << T));
+    float2 *mat = reinterpret_cast<float2 *>(blob + S.p.blob_words);
     const uint64_t base = tile_base(S, cta);
+    blob_load<NT>(gblob + S.p.blob_off, S.p.blob_words, blob);
     tile_load<NT, CG>(g, base, S, tile);
-    if constexpr (!CG) cp_async_wait_all();
-    tile_ops<NT, KMAX, PREC>(tile, tile + (1u << S.p.T), ops, mats, bfr, base, gb, S);
+    cp_async_wait_all();
+    tile_ops<NT, KMAX, PREC>(tile, blob, mat, mats, bfr, base, gb, S);
     __syncthreads();
     tile_store<NT>(g, base, S, tile);
 }

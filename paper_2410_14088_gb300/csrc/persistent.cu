@@ -160,7 +160,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
                                         S.npre, S.mats, uint64_t(jj) << S.m, gb);
             }
         } else if (type == PH_PASS) {
-            gdev::pass_tile<PT, 5, PREC, true>(wv, S.passes + S.ph[p].arg, S.ops, S.mats, S.bfr, i, gb, PS,
+            gdev::pass_tile<PT, 5, PREC, true>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr, i, gb, PS,
                                                reinterpret_cast<float2 *>(dsm));
         } else if (type == PH_SIZE) {
             const uint32_t jj = i / g.nframes, f = i % g.nframes;
@@ -332,8 +332,8 @@ int launch_stage_prec(const PLaunch &a, size_t smem, cudaStream_t s, int *grid_o
 
 }  // namespace
 
-size_t persistent_smem_bytes(uint32_t T, uint32_t mat_elems) {
-    size_t pass = (size_t(1) << T) * sizeof(float2) + size_t(mat_elems) * sizeof(float2);
+size_t persistent_smem_bytes(size_t pass_bytes) {
+    size_t pass = pass_bytes;
     size_t enc = size_t(cdev::kStageWords) * sizeof(uint32_t);
     size_t mlp = size_t(kMlpParams) * sizeof(float);
     size_t m = pass > enc ? pass : enc;

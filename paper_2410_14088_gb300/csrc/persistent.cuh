@@ -41,6 +41,7 @@ struct PSeg {
     const PassDev *passes;
     const OpDev *ops;
     const float2 *mats;
+    const uint4 *blob;       // the plan's pass blobs
     const uint32_t *bfr;     // B-fragment tables of the tensor-core precisions
     const uint32_t *ids;     // group-major block ids of the stage
     const uint64_t *gbase;   // per group: full-index bits of its outer qubits
@@ -82,7 +83,8 @@ struct PLaunch {
     uint64_t wait_ns;         // limit of every dependency wait
 };
 
-size_t persistent_smem_bytes(uint32_t T, uint32_t mat_elems);
+// pass_bytes: the largest tile + pass blob + matrix area of the launch's passes
+size_t persistent_smem_bytes(size_t pass_bytes);
 int prepare_stage_persistent(int prec, size_t smem);
 int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid);
 

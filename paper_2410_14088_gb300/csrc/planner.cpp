@@ -309,20 +309,30 @@ void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
     std::set<uint32_t> P;
     for (uint32_t b = 0; b < L; ++b) P.insert(b);
     std::vector<uint32_t> cur;
+    // shared-memory bytes of the pass's op data (descriptor, and for a diagonal op its tables)
+    auto op_bytes = [&](const Op &op) -> size_t {
+        return kOpDescBytes + (op.type == OP_DIAG ? 192 + 16 + (size_t(8) << op.k) : 0);
+    };
+    size_t bytes = 0;
     for (uint32_t i = first; i < st.ops.size(); ++i) {
         const Op &op = st.ops[i];
+        bool fresh = bytes + op_bytes(op) > kPassOpBytes;
+        std::set<uint32_t> need(P);
         if (op.type == OP_DENSE) {
-            std::set<uint32_t> need(P);
             for (uint32_t j = 0; j < op.k; ++j) need.insert(op.wq[j]);
-            if (need.size() > T) {
-                close(P, cur);
-                P.clear();
-                for (uint32_t b = 0; b < L; ++b) P.insert(b);
-                for (uint32_t j = 0; j < op.k; ++j) P.insert(op.wq[j]);
-            } else {
-                P = need;
-            }
+            fresh = fresh || need.size() > T;
         }
+        if (fresh && !cur.empty()) {
+            close(P, cur);
+            P.clear();
+            for (uint32_t b = 0; b < L; ++b) P.insert(b);
+            bytes = 0;
+            if (op.type == OP_DENSE)
+                for (uint32_t j = 0; j < op.k; ++j) P.insert(op.wq[j]);
+        } else if (op.type == OP_DENSE) {
+            P = need;
+        }
+        bytes += op_bytes(op);
         cur.push_back(i);
     }
     close(P, cur);

@@ -74,6 +74,8 @@ struct Stage {
 
 constexpr uint32_t kMaxPreOps = 8;
 constexpr uint32_t kMaxDiagQubits = 8;  // widest fused diagonal op (phase index fits a byte)
+constexpr size_t kOpDescBytes = 208;    // device descriptor of an op in a pass
+constexpr size_t kPassOpBytes = 32768;  // op data of one pass held in shared memory next to its tile
 
 struct Gate {
     uint32_t nq = 0;
