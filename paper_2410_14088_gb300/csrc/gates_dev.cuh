@@ -33,7 +33,11 @@ struct PassSmem {
     uint32_t hi[256];
     uint32_t off12[32];    // 4096-amplitude tiles with L >= log2(NT): working offset of element tid + NT u, minus tid
     uint32_t offs[64];     // dense op: working offsets of its 2^k matrix columns within the tile
+    uint32_t offs_sw[64];  // the same through the swizzle
     uint32_t comp[16];     // dense op: its complement tile bits
+    // dense op: swizzled base of index group g = cb[0][g & 63] ^ cb[1][g >> 6] (the swizzle is
+    // linear over GF(2), so swz(b | c) = swz(b) ^ swz(c) for disjoint bit sets b, c)
+    uint32_t cb[2][64];
     uint32_t dconst[kDiagRun];  // diagonal op d of a run: phase-index bits constant over the tile
 };
 static_assert(sizeof(OpDev) % 16 == 0, "op descriptors are copied as 16-byte words");
@@ -42,13 +46,11 @@ template <int NT, int K>
 __device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const PassSmem &S, uint32_t T) {
     constexpr int D = 1 << K;
     const uint32_t ngroups = 1u << (T - K);
-    const uint32_t nc = T - K;
     for (uint32_t g = threadIdx.x; g < ngroups; g += NT) {
-        uint32_t b = 0;
-        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.comp[t];
+        const uint32_t sb = S.cb[0][g & 63u] ^ S.cb[1][g >> 6];
         float2 x[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) x[c] = tile[swz(b | S.offs[c])];
+        for (int c = 0; c < D; ++c) x[c] = tile[sb ^ S.offs_sw[c]];
 #pragma unroll 1
         for (int r = 0; r < D; ++r) {
             const float4 *row = reinterpret_cast<const float4 *>(U + r * D);
@@ -69,7 +71,7 @@ __device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const
                     ai = fmaf(u.z, x[c + 1].y, ai); ai = fmaf(u.w, x[c + 1].x, ai);
                 }
             }
-            tile[swz(b | S.offs[r])] = make_float2(ar, ai);
+            tile[sb ^ S.offs_sw[r]] = make_float2(ar, ai);
         }
     }
 }
@@ -77,12 +79,9 @@ __device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const
 template <int NT>
 __device__ __forceinline__ void apply_dense_k1(float2 *tile, const float2 *U, const PassSmem &S, uint32_t T) {
     const uint32_t ngroups = 1u << (T - 1);
-    const uint32_t nc = T - 1;
     const float2 u00 = U[0], u01 = U[1], u10 = U[2], u11 = U[3];
     for (uint32_t g = threadIdx.x; g < ngroups; g += NT) {
-        uint32_t b = 0;
-        for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.comp[t];
-        const uint32_t i0 = swz(b), i1 = swz(b | S.offs[1]);
+        const uint32_t i0 = S.cb[0][g & 63u] ^ S.cb[1][g >> 6], i1 = i0 ^ S.offs_sw[1];
         const float2 x0 = tile[i0], x1 = tile[i1];
         tile[i0] = make_float2(u00.x * x0.x - u00.y * x0.y + u01.x * x1.x - u01.y * x1.y,
                                u00.x * x0.y + u00.y * x0.x + u01.x * x1.y + u01.y * x1.x);
@@ -166,17 +165,14 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
     static_assert(MT >= 1, "tensor-core tile needs 16 rows per warp");
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint32_t gq = lane >> 2, tq = lane & 3;
-    const uint32_t nc = T - K;
     const uint32_t row0 = warp * ROWS;
-    uint32_t base[MT][2];
+    uint32_t base[MT][2];  // swizzled bases of the lane's index groups
 #pragma unroll
     for (uint32_t mt = 0; mt < MT; ++mt)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint32_t g = row0 + mt * 16 + gq + 8 * h;
-            uint32_t b = 0;
-            for (uint32_t t = 0; t < nc; ++t) b |= ((g >> t) & 1u) << S.comp[t];
-            base[mt][h] = b;
+            base[mt][h] = S.cb[0][g & 63u] ^ S.cb[1][g >> 6];
         }
     float acc[MT * NTILES][4];
 #pragma unroll
@@ -186,12 +182,12 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
 #pragma unroll 1
     for (uint32_t ks = 0; ks < KS / 2; ++ks) {
         if constexpr (PREC == QSIM_PREC_TF32) {
-            const uint32_t c0 = S.offs[ks * 8 + tq], c1 = S.offs[ks * 8 + tq + 4];
+            const uint32_t c0 = S.offs_sw[ks * 8 + tq], c1 = S.offs_sw[ks * 8 + tq + 4];
             uint32_t are[MT][4], aim[MT][4];
 #pragma unroll
             for (uint32_t mt = 0; mt < MT; ++mt) {
-                const float2 v00 = tile[swz(base[mt][0] | c0)], v10 = tile[swz(base[mt][1] | c0)];
-                const float2 v01 = tile[swz(base[mt][0] | c1)], v11 = tile[swz(base[mt][1] | c1)];
+                const float2 v00 = tile[base[mt][0] ^ c0], v10 = tile[base[mt][1] ^ c0];
+                const float2 v01 = tile[base[mt][0] ^ c1], v11 = tile[base[mt][1] ^ c1];
                 are[mt][0] = f32_to_tf32(v00.x); are[mt][1] = f32_to_tf32(v10.x);
                 are[mt][2] = f32_to_tf32(v01.x); are[mt][3] = f32_to_tf32(v11.x);
                 aim[mt][0] = f32_to_tf32(v00.y); aim[mt][1] = f32_to_tf32(v10.y);
@@ -210,8 +206,8 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
             }
         } else {
             // columns 2t, 2t+1, 2t+8, 2t+9 of the k-step
-            const uint32_t cc[4] = {S.offs[ks * 16 + 2 * tq], S.offs[ks * 16 + 2 * tq + 1], S.offs[ks * 16 + 2 * tq + 8],
-                                    S.offs[ks * 16 + 2 * tq + 9]};
+            const uint32_t cc[4] = {S.offs_sw[ks * 16 + 2 * tq], S.offs_sw[ks * 16 + 2 * tq + 1],
+                                    S.offs_sw[ks * 16 + 2 * tq + 8], S.offs_sw[ks * 16 + 2 * tq + 9]};
             constexpr uint32_t PART = KS * NTILES * 32;  // uint2 entries per part
 #pragma unroll
             for (int ri = 0; ri < 2; ++ri) {  // Re inputs with k-step ks, then Im inputs with ks + KS/2
@@ -221,7 +217,7 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
                         const uint32_t b = base[mt][q & 1];
-                        const float2 x0 = tile[swz(b | cc[(q >> 1) * 2])], x1 = tile[swz(b | cc[(q >> 1) * 2 + 1])];
+                        const float2 x0 = tile[b ^ cc[(q >> 1) * 2]], x1 = tile[b ^ cc[(q >> 1) * 2 + 1]];
                         __nv_bfloat16 h0, m0, l0, h1, m1, l1;
                         split3(ri ? x0.y : x0.x, h0, m0, l0);
                         split3(ri ? x1.y : x1.x, h1, m1, l1);
@@ -247,7 +243,7 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
         }
     }
     __syncwarp();
-    const uint32_t *offs = S.offs;
+    const uint32_t *offs = S.offs_sw;
     // outputs: n-tile j < NTILES/2 holds Re of outputs 8j + 2tq (+1), tile j + NTILES/2 the Im parts
 #pragma unroll
     for (uint32_t mt = 0; mt < MT; ++mt) {
@@ -256,10 +252,10 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
             const float (&re)[4] = acc[mt * NTILES + j];
             const float (&im)[4] = acc[mt * NTILES + j + NTILES / 2];
             const uint32_t r0 = 8 * j + 2 * tq;
-            tile[swz(base[mt][0] | offs[r0])] = make_float2(re[0], im[0]);
-            tile[swz(base[mt][0] | offs[r0 + 1])] = make_float2(re[1], im[1]);
-            tile[swz(base[mt][1] | offs[r0])] = make_float2(re[2], im[2]);
-            tile[swz(base[mt][1] | offs[r0 + 1])] = make_float2(re[3], im[3]);
+            tile[base[mt][0] ^ offs[r0]] = make_float2(re[0], im[0]);
+            tile[base[mt][0] ^ offs[r0 + 1]] = make_float2(re[1], im[1]);
+            tile[base[mt][1] ^ offs[r0]] = make_float2(re[2], im[2]);
+            tile[base[mt][1] ^ offs[r0 + 1]] = make_float2(re[3], im[3]);
         }
     }
 }
@@ -445,8 +441,19 @@ __device__ __forceinline__ void tile_ops(float2 *tile, const uint4 *blob, float2
                 uint32_t o = 0;
                 for (uint32_t j = 0; j < k; ++j) o |= ((uint32_t(tid) >> j) & 1u) << op.tq[j];
                 S.offs[tid] = o;
+                S.offs_sw[tid] = swz(o);
             }
             if (tid < 16) S.comp[tid] = op.comp[tid];
+            {
+                const uint32_t nc = T - k;
+                for (uint32_t x = tid; x < 128; x += NT) {
+                    const uint32_t half = x >> 6, v = x & 63u;
+                    uint32_t b = 0;
+                    for (uint32_t t = 0; t < 6; ++t)
+                        if (6 * half + t < nc) b |= ((v >> t) & 1u) << op.comp[6 * half + t];
+                    S.cb[half][v] = swz(b);
+                }
+            }
             __syncthreads();
             if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, M, bfr + op.bfrag, S, T);
         } else if (type == OP_DIAG) {
@@ -473,18 +480,39 @@ __device__ __forceinline__ void tile_ops(float2 *tile, const uint4 *blob, float2
                 tb[d] = d < r ? bops[oi + d].tab : 0u;
                 lb[d] = d < r ? 8u * bops[oi + d].dlut : 0u;
             }
-            for (uint32_t i = tid; i < (1u << T); i += NT) {
-                const uint32_t lo = i & 127u, hi = 128u + (i >> 7);
-                float2 &a = tile[swz(i)];
-                float2 v = a;
+            if (T == 12) {
+                // element i = tid + NT u: tile bits 0..6 fixed per thread, bits 7..11 from u
+                const uint32_t tq = swz_thread<NT>(tid), lo = uint32_t(tid) & 127u, hib = 128u + (uint32_t(tid) >> 7);
+                uint32_t fix[kDiagRun];
 #pragma unroll
-                for (uint32_t d = 0; d < kDiagRun; ++d) {
-                    if (d < r) {
-                        const float2 ph = bf2[tb[d] + (dc[d] | bb[lb[d] + lo] | bb[lb[d] + hi])];
-                        v = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
+                for (uint32_t d = 0; d < kDiagRun; ++d) fix[d] = d < r ? (dc[d] | bb[lb[d] + lo]) + tb[d] : 0u;
+#pragma unroll
+                for (uint32_t u = 0; u < 4096u / NT; ++u) {
+                    float2 &a = tile[(tq ^ swz_u<NT>(u)) + NT * u];
+                    float2 v = a;
+#pragma unroll
+                    for (uint32_t d = 0; d < kDiagRun; ++d) {
+                        if (d < r) {
+                            const float2 ph = bf2[fix[d] + bb[lb[d] + hib + (NT / 128) * u]];
+                            v = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
+                        }
                     }
+                    a = v;
                 }
-                a = v;
+            } else {
+                for (uint32_t i = tid; i < (1u << T); i += NT) {
+                    const uint32_t lo = i & 127u, hi = 128u + (i >> 7);
+                    float2 &a = tile[swz(i)];
+                    float2 v = a;
+#pragma unroll
+                    for (uint32_t d = 0; d < kDiagRun; ++d) {
+                        if (d < r) {
+                            const float2 ph = bf2[tb[d] + (dc[d] | bb[lb[d] + lo] | bb[lb[d] + hi])];
+                            v = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
+                        }
+                    }
+                    a = v;
+                }
             }
         } else {
             if (tid == 0 && op.basis_in_stage && gb == op.basis_outer && (op.basis_w & S.p.out_mask) == base) {
