@@ -582,6 +582,67 @@ __device__ __forceinline__ uint32_t size_frame_cta(const float2 *__restrict__ sr
 }
 
 
+// Exact stream bytes of one frame with one warp (no block-wide barrier); the
+// chunk widths go to wrec (2C bytes, Re then Im) for encode_frame_warp_known.
+template <bool CG = false>
+__device__ __forceinline__ uint32_t size_frame_warp(const float2 *__restrict__ src, const FrameGeom &g, int e,
+                                                    uint8_t *__restrict__ wrec, int *status) {
+    const int lane = threadIdx.x & 31;
+    const float inv_step = exp2i(-e);
+    uint32_t words = 0, wre = 0, wim = 0;  // lane l packs the widths of chunks 4l .. 4l+3
+    int bad = 0;
+    for (uint32_t c0 = 0; c0 < g.C; c0 += 8) {
+        float2 vin[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t c = c0 + t;
+            vin[t] = c < g.C ? (CG ? __ldcg(src + c * 32 + lane) : __ldcs(src + c * 32 + lane)) : make_float2(0.f, 0.f);
+        }
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t c = c0 + t;
+            if (c >= g.C) break;
+            int32_t q[2];
+            const float x[2] = {vin[t].x, vin[t].y};
+#pragma unroll
+            for (int pl = 0; pl < 2; ++pl) {
+                const float tq = x[pl] * inv_step;  // exact: power-of-two scaling
+                if (fabsf(tq) < 1073741824.0f) {
+                    q[pl] = __float2int_rn(tq);
+                } else {  // NaN, Inf or out of range
+                    q[pl] = 0;
+                    bad = isfinite(x[pl]) ? (bad ? bad : QSIM_E_RANGE) : QSIM_E_INVALID;
+                }
+            }
+            const int32_t pr = __shfl_up_sync(kFull, q[0], 1);
+            const int32_t pi = __shfl_up_sync(kFull, q[1], 1);
+            const uint32_t zr = zigzag(lane ? int32_t(uint32_t(q[0]) - uint32_t(pr)) : q[0]);
+            const uint32_t zi = zigzag(lane ? int32_t(uint32_t(q[1]) - uint32_t(pi)) : q[1]);
+            const uint32_t wr = 32 - __clz(__reduce_or_sync(kFull, zr)), wi = 32 - __clz(__reduce_or_sync(kFull, zi));
+            words += wr + wi;
+            if (uint32_t(lane) == (c >> 2)) {
+                wre |= wr << (8 * (c & 3));
+                wim |= wi << (8 * (c & 3));
+            }
+        }
+    }
+    if (bad) raise_status(status, bad);
+    if (g.C >= 4) {  // word stores: Re widths at bytes [0, C), Im widths at [C, 2C)
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(wrec);
+        if (4u * lane < g.C) {
+            w32[lane] = wre;
+            w32[g.C / 4 + lane] = wim;
+        }
+    } else if (lane == 0) {
+        for (uint32_t c = 0; c < g.C; ++c) {
+            wrec[c] = uint8_t(wre >> (8 * c));
+            wrec[g.C + c] = uint8_t(wim >> (8 * c));
+        }
+    }
+    const uint32_t padw = (2u * g.C + 15u) & ~15u;
+    return words ? padw + ((4u * words + 15u) & ~15u) : 0u;
+}
+
 // Encode frame f of one block with one warp when the frame's chunk widths
 // (wrec: 2C bytes, Re then Im, written by the sizing pass) and its byte offset
 // in the block's stream are known: no look-back and no block-wide barrier.
@@ -602,7 +663,8 @@ __device__ __forceinline__ void encode_frame_warp_known(const float2 *__restrict
     // widths: lane l holds those of chunks 8l .. 8l+7 (bytes past 2C are masked to zero)
     uint2 wb = make_uint2(0, 0);
     if (8u * lane < 2u * g.C) {
-        wb = *reinterpret_cast<const uint2 *>(wrec + 8u * lane);
+        wb = CG ? __ldcg(reinterpret_cast<const uint2 *>(wrec + 8u * lane))
+                : *reinterpret_cast<const uint2 *>(wrec + 8u * lane);
         const uint32_t valid = 2u * g.C - 8u * lane;  // bytes of this lane that are widths
         if (valid < 8) {
             const uint64_t keep = (1ull << (8 * valid)) - 1;

@@ -984,13 +984,11 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
     for (uint32_t c = 0; c < rs.size(); ++c) seg_of[c].assign(rs[c]->nst, 0);
     for (size_t k = 0; k < nseg; ++k) seg_of[order[k].c][order[k].si] = uint32_t(k);
 
-    uint64_t slot_amps = 0, slot_frames = 0, total_groups = 0;
+    uint64_t total_groups = 0;
     size_t max_pass_bytes = 0;
     for (const SegRef &sr : order) {
         const RunCtx &R = *rs[sr.c];
         const StageDev &sd = R.pd->stages[sr.si];
-        slot_amps = std::max<uint64_t>(slot_amps, 1ull << sd.W);
-        slot_frames = std::max<uint64_t>(slot_frames, uint64_t(sd.G) * R.nframes);
         total_groups += sd.ngroups;
         for (const PassDev &ps : sd.passes_host) {
             max_pass_bytes = std::max(max_pass_bytes, (size_t(1) << ps.T) * sizeof(float2) + size_t(ps.blob_words) * 16 +
@@ -998,17 +996,6 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
             if (ps.kmax > 5) return set_error(QSIM_E_INVALID, "persistent mode fuses at most k = 5 qubits");
         }
     }
-    // working-vector slots: enough to overlap groups within about slot_budget_amps amplitudes
-    uint64_t launch_groups_max = 0;
-    if (one_launch) {
-        launch_groups_max = total_groups;
-    } else {
-        for (const SegRef &sr : order)
-            launch_groups_max = std::max<uint64_t>(launch_groups_max, rs[sr.c]->pd->stages[sr.si].ngroups);
-    }
-    const uint32_t R_slots =
-        uint32_t(std::max<uint64_t>(2, std::min<uint64_t>(launch_groups_max, slot_budget_amps / slot_amps)));
-
     std::vector<std::unique_ptr<PBlockBufs>> bb(rs.size());
     int rc;
     for (size_t c = 0; c < rs.size(); ++c) {
@@ -1021,14 +1008,74 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         CUDA_TRY(cudaMemsetAsync(b.sizes.p, 0, R.nblocks * sizeof(uint64_t), main));
         if (R.predict) CUDA_TRY(cudaMemsetAsync(b.hist.p, 0, R.nblocks * 32 * sizeof(uint32_t), main));
     }
+    // Working-vector slots, planned per launch: one ring of slots per working-vector size (2^W amplitudes),
+    // each ring about slot_budget_amps large (at least 2 slots, at most the launch's groups of that size);
+    // a group takes the next slot of its ring and waits for the slot's previous group.
+    std::vector<uint64_t> g_wv(total_groups);
+    std::vector<uint32_t> g_frame(total_groups), g_prev(total_groups, kNoGroup);
+    uint64_t wv_total = 0, frames_total = 0;
+    {
+        const size_t nlaunch_plan = one_launch ? 1 : nseg;
+        uint64_t q_global = 0;
+        for (size_t l = 0; l < nlaunch_plan; ++l) {
+            const size_t k0 = one_launch ? 0 : l, k1 = one_launch ? nseg : l + 1;
+            struct Ring {
+                uint64_t amps = 0, frames = 0, groups = 0, slots = 0, used = 0, wv_base = 0, fr_base = 0;
+                std::vector<uint32_t> last;  // per slot: launch group that used it last
+            };
+            std::map<uint32_t, Ring> rings;  // by W
+            for (size_t k = k0; k < k1; ++k) {
+                const RunCtx &R = *rs[order[k].c];
+                const StageDev &sd = R.pd->stages[order[k].si];
+                Ring &rg = rings[sd.W];
+                rg.amps = 1ull << sd.W;
+                rg.frames = std::max<uint64_t>(rg.frames, uint64_t(sd.G) * R.nframes);
+                rg.groups += sd.ngroups;
+            }
+            uint64_t wv_l = 0, fr_l = 0;
+            for (auto &kv : rings) {
+                Ring &rg = kv.second;
+                rg.slots = std::max<uint64_t>(2, std::min<uint64_t>(rg.groups, slot_budget_amps / rg.amps));
+                rg.slots = std::min<uint64_t>(rg.slots, rg.groups);
+                rg.last.assign(rg.slots, kNoGroup);
+                rg.wv_base = wv_l;
+                rg.fr_base = fr_l;
+                wv_l += rg.slots * rg.amps;
+                fr_l += rg.slots * rg.frames;
+            }
+            wv_total = std::max(wv_total, wv_l);
+            frames_total = std::max(frames_total, fr_l);
+            uint32_t q_local = 0;
+            for (size_t k = k0; k < k1; ++k) {
+                const StageDev &sd = rs[order[k].c]->pd->stages[order[k].si];
+                Ring &rg = rings[sd.W];
+                for (uint32_t gi = 0; gi < sd.ngroups; ++gi, ++q_local, ++q_global) {
+                    const uint64_t slot = rg.used++ % rg.slots;
+                    g_wv[q_global] = rg.wv_base + slot * rg.amps;
+                    g_frame[q_global] = uint32_t(rg.fr_base + slot * rg.frames);
+                    g_prev[q_global] = rg.last[slot];
+                    rg.last[slot] = q_local;
+                }
+            }
+        }
+        if (frames_total >= (1ull << 32)) return set_error(QSIM_E_UNSUPPORTED, "working-vector slot plan too large");
+    }
     DevBuf<float2> wv, part;
-    DevBuf<uint64_t> lb;
-    DevBuf<uint32_t> sync, fin, ctr;
+    DevBuf<uint8_t> wrec;
+    DevBuf<uint32_t> flen, foff;
+    DevBuf<uint64_t> lb, dg_wv;
+    DevBuf<uint32_t> sync, fin, ctr, dg_frame, dg_prev;
     DevBuf<PSeg> dsegs;
-    if ((rc = wv.alloc(uint64_t(R_slots) * slot_amps)) || (rc = lb.alloc(uint64_t(R_slots) * slot_frames)) ||
-        (rc = part.alloc(uint64_t(R_slots) * slot_frames)) || (rc = sync.alloc(2 * total_groups * kMaxPhases)) ||
-        (rc = fin.alloc(2 * nseg)) || (rc = ctr.alloc(4)) || (rc = dsegs.alloc(nseg)))
+    if ((rc = wv.alloc(wv_total)) || (rc = lb.alloc(frames_total)) || (rc = part.alloc(frames_total)) ||
+        (rc = sync.alloc(2 * total_groups * kMaxPhases)) || (rc = fin.alloc(2 * nseg)) || (rc = ctr.alloc(4)) ||
+        (rc = dsegs.alloc(nseg)) || (rc = dg_wv.alloc(total_groups)) || (rc = dg_frame.alloc(total_groups)) ||
+        (rc = dg_prev.alloc(total_groups)) || (rc = wrec.alloc(frames_total * 256)) ||
+        (rc = flen.alloc(frames_total)) || (rc = foff.alloc(frames_total)))
         return rc;
+    CUDA_TRY(cudaMemcpyAsync(dg_wv.p, g_wv.data(), total_groups * sizeof(uint64_t), cudaMemcpyHostToDevice, main));
+    CUDA_TRY(cudaMemcpyAsync(dg_frame.p, g_frame.data(), total_groups * sizeof(uint32_t), cudaMemcpyHostToDevice,
+                             main));
+    CUDA_TRY(cudaMemcpyAsync(dg_prev.p, g_prev.data(), total_groups * sizeof(uint32_t), cudaMemcpyHostToDevice, main));
     CUDA_TRY(cudaMemsetAsync(lb.p, 0, lb.n * sizeof(uint64_t), main));
     CUDA_TRY(cudaMemsetAsync(sync.p, 0, sync.n * sizeof(uint32_t), main));
     CUDA_TRY(cudaMemsetAsync(fin.p, 0, fin.n * sizeof(uint32_t), main));
@@ -1068,8 +1115,12 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         add(PH_DECODE, (gframes + 7) / 8, 0);
         if (R.predict) add(PH_PREDICT, 1, 0);
         for (uint32_t pi = 0; pi < sd.npasses; ++pi) add(PH_PASS, 1u << sd.passes_host[pi].nout, pi);
-        if (!R.predict) add(PH_SIZE, gframes, 0);
-        add(PH_ENCODE, gframes, 0);
+        if (R.predict) {
+            add(PH_ENCODE, gframes, 0);
+        } else {
+            add(PH_SIZE_W, (gframes + 7) / 8, 0);
+            add(PH_ENCODE_W, (gframes + 7) / 8, 0);
+        }
         if (R.predict) {
             add(PH_FIX, 1, 0);
             add(PH_REENCODE, gframes, 0);
@@ -1134,10 +1185,10 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
     if ((rc = prepare_stage_persistent(prec, smem))) return set_error(rc, "persistent kernel set-up failed");
 
     PLaunch L{};
-    L.R = R_slots;
-    L.slot_amps = slot_amps;
-    L.slot_frames = slot_frames;
     L.wv = wv.p;
+    L.wrec = wrec.p;
+    L.flen = flen.p;
+    L.foff = foff.p;
     L.lb = lb.p;
     L.part = part.p;
     L.ctr = ctr.p;
@@ -1172,6 +1223,9 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         L.nseg = uint32_t(k1 - k0);
         L.total_items = segs[k1 - 1].item_begin + seg_items[k1 - 1];
         L.total_groups = segs[k1 - 1].group_begin + segs[k1 - 1].ngroups;
+        L.g_wv = dg_wv.p + seg_group_off[k0];
+        L.g_frame = dg_frame.p + seg_group_off[k0];
+        L.g_prev = dg_prev.p + seg_group_off[k0];
         L.done = sync.p + seg_group_off[k0] * kMaxPhases;
         L.arrive = sync.p + (total_groups + seg_group_off[k0]) * kMaxPhases;
         prof.begin(P_STAGE, cs);
@@ -1560,7 +1614,8 @@ static int run_batch(const qsim_plan *const *plans, size_t count, cudaStream_t m
     std::vector<std::unique_ptr<RunCtx>> rs(count);
     std::vector<RunCtx *> rp(count);
     int rc;
-    uint64_t slot_amps = 0, sum_need = 0;
+    uint64_t sum_need = 0;
+    std::map<uint32_t, uint64_t> w_groups;  // working-vector sizes of the batch and their group counts
     uint32_t mmax = 0;
     for (size_t c = 0; c < count; ++c) {
         const qsim_plan *p = plans[c];
@@ -1574,7 +1629,7 @@ static int run_batch(const qsim_plan *const *plans, size_t count, cudaStream_t m
         rs[c].reset(new RunCtx());
         rp[c] = rs[c].get();
         if ((rc = prepare_run(*rs[c], p, dctx))) return rc;
-        for (const StageDev &sd : rs[c]->pd->stages) slot_amps = std::max<uint64_t>(slot_amps, 1ull << sd.W);
+        for (const StageDev &sd : rs[c]->pd->stages) w_groups[sd.W] += sd.ngroups;
         sum_need += rs[c]->need_per_parity;
         mmax = std::max(mmax, rs[c]->m);
     }
@@ -1582,7 +1637,11 @@ static int run_batch(const qsim_plan *const *plans, size_t count, cudaStream_t m
     size_t free_b = 0, total_b = 0;
     CUDA_TRY(cudaMemGetInfo(&free_b, &total_b));
     free_b += cached_dev_bytes();
-    const uint64_t work_bytes = std::max<uint64_t>(2 * slot_amps, slot_budget) * 8 * 2 + (16ull << (mmax + 1));
+    // working-vector slot rings (one per size) with their frame scratch, and the initial-store buffers
+    uint64_t ring_amps = 0;
+    for (const auto &kv : w_groups)
+        ring_amps += std::min<uint64_t>(kv.second, std::max<uint64_t>(2, slot_budget >> kv.first)) << kv.first;
+    const uint64_t work_bytes = ring_amps * 8 * 5 / 4 + (16ull << (mmax + 1));
     const double dev_budget = free_b > work_bytes ? 0.85 * double(free_b - work_bytes) : 0.0;
     const double host_budget = 0.3 * double(host_phys_bytes());
     // each circuit's share of both levels follows its worst-case need

@@ -11,8 +11,10 @@
 // CTAs work on different phases of different groups at the same time, and a
 // group's work item only waits on items that come earlier in the queue, which
 // were taken by CTAs that are already running: the schedule cannot deadlock
-// even when not every CTA is resident. Working vectors rotate over R slots;
-// the first item of group g also waits for group g - R to finish.
+// even when not every CTA is resident. Working vectors live in slots planned
+// on the host: one ring of slots per working-vector size, so that many small
+// groups can be in flight next to a few large ones; the first item of a group
+// also waits for the slot's previous group (earlier in the queue) to finish.
 //
 // Data produced by other CTAs of the same launch is read through L2 (ld.cg),
 // since the per-SM L1 caches are not coherent within a launch.
@@ -118,8 +120,9 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
                 flag = L.done + uint64_t(q) * kMaxPhases + p - 1;
                 need = S.ph[p - 1].count;
             } else {
-                if (q >= L.R) {
-                    flag = L.done + uint64_t(q - L.R) * kMaxPhases + kMaxPhases - 1;
+                const uint32_t prev = L.g_prev[q];
+                if (prev != kNoGroup) {  // the slot's previous group must have finished
+                    flag = L.done + uint64_t(prev) * kMaxPhases + kMaxPhases - 1;
                     need = 1;
                 }
                 flag2 = S.prev_flag;
@@ -141,13 +144,14 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
         __syncthreads();
         const bool abort_item = s_flag != 0;
         __syncthreads();
-        const uint32_t slot = q % L.R;
-        float2 *wv = L.wv + uint64_t(slot) * L.slot_amps;
-        float2 *part = L.part + uint64_t(slot) * L.slot_frames;
+        float2 *wv = L.wv + L.g_wv[q];
+        float2 *part = L.part + L.g_frame[q];
         const uint32_t *ids = S.ids + uint64_t(grp) * S.G;
         const uint64_t gb = S.gbase[grp];
         const uint64_t bbase = uint64_t(grp) * S.G;  // per-group block arrays
-        bool by_arrival = type == PH_SIZE || type == PH_ENCODE || type == PH_REENCODE;
+        const uint32_t sf0 = L.g_frame[q];  // the slot's first frame in wrec / flen / foff / part / lb
+        bool by_arrival = type == PH_SIZE || type == PH_ENCODE || type == PH_REENCODE || type == PH_SIZE_W ||
+                          type == PH_ENCODE_W;
         if (abort_item) {
             // skip the work, keep the counts
         } else if (type == PH_DECODE) {
@@ -167,6 +171,24 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             const uint32_t len = cdev::size_frame_cta<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g, S.e,
                                                             s_words, L.status);
             if (tid == 0 && len) atomicAdd(reinterpret_cast<unsigned long long *>(&S.sizes[bbase + jj]), uint64_t(len));
+        } else if (type == PH_SIZE_W) {
+            const uint32_t fi = i * (PT / 32) + warp;
+            if (fi < gframes) {
+                const uint32_t jj = fi / g.nframes, f = fi % g.nframes;
+                const uint32_t len = cdev::size_frame_warp<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g,
+                                                                 S.e, L.wrec + uint64_t(sf0 + fi) * 256, L.status);
+                if ((tid & 31) == 0) L.flen[sf0 + fi] = len;
+            }
+        } else if (type == PH_ENCODE_W) {
+            const uint32_t fi = i * (PT / 32) + warp;
+            if (fi < gframes) {
+                const uint32_t jj = fi / g.nframes, f = fi % g.nframes;
+                cdev::encode_frame_warp_known<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g, int(S.m), S.e,
+                                                    f, L.wrec + uint64_t(sf0 + fi) * 256, __ldcg(L.foff + sf0 + fi),
+                                                    __ldcg(L.flen + sf0 + fi), load_target(&S.tgt[bbase + jj]),
+                                                    &S.res[bbase + jj], S.tab_out + ids[jj], S.acc, part + fi,
+                                                    L.status);
+            }
         } else if (type == PH_PREDICT) {
             float *w = reinterpret_cast<float *>(dsm);
             for (int t = tid; t < kMlpParams; t += PT) {
@@ -199,7 +221,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             if (s_flag) {
                 const uint32_t epoch = (s_epoch + 2 * q + (retry ? 1 : 0)) & cdev::kEpochMask;
                 cdev::encode_frame_cta<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g, int(S.m), S.e, f,
-                                             L.lb + uint64_t(slot) * L.slot_frames + uint64_t(jj) * g.nframes, epoch,
+                                             L.lb + L.g_frame[q] + uint64_t(jj) * g.nframes, epoch,
                                              load_target(&S.tgt[bbase + jj]), &S.res[bbase + jj], S.tab_out + ids[jj],
                                              S.acc, retry ? nullptr : part + uint64_t(jj) * g.nframes + f,
                                              retry ? 1 : 0, reinterpret_cast<uint32_t *>(dsm), SE, L.status);
@@ -243,7 +265,33 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
                 rs.norm_sq = 0;
                 cdev::reserve_slot(want_b, S.dev, S.host, &S.tgt[bbase + jj], L.status);
             }
-        } else if (type == PH_ENCODE) {
+        } else if (type == PH_SIZE_W) {
+            // the group's frame lengths are complete: frame offsets (warp per block) and the group's slots
+            const int lane = tid & 31;
+            for (uint32_t jj = warp; jj < S.G; jj += PT / 32) {
+                uint32_t run = uint32_t(S.data_start);
+                for (uint32_t f0 = 0; f0 < g.nframes; f0 += 32) {
+                    const uint32_t fi = sf0 + jj * g.nframes + f0 + lane;
+                    const uint32_t v = f0 + lane < g.nframes ? __ldcg(L.flen + fi) : 0u;
+                    uint32_t incl = v;
+#pragma unroll
+                    for (int o = 1; o < 32; o <<= 1) {
+                        const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                        if (lane >= o) incl += t;
+                    }
+                    if (f0 + lane < g.nframes) L.foff[fi] = run + incl - v;
+                    run += __shfl_sync(kFull, incl, 31);
+                }
+                if (lane == 0) {
+                    EncResult &rs = S.res[bbase + jj];
+                    rs.total = 0;
+                    rs.overflow = 0;
+                    rs.err_sq = 0;
+                    rs.norm_sq = 0;
+                    cdev::reserve_slot(run, S.dev, S.host, &S.tgt[bbase + jj], L.status);
+                }
+            }
+        } else if (type == PH_ENCODE || type == PH_ENCODE_W) {
             // the group's frames are encoded: fold their error partials into the stage totals
             double a = 0, b = 0;
             for (uint32_t t = tid; t < gframes; t += PT) {

@@ -17,14 +17,19 @@ enum PhaseType : uint32_t {
     PH_PREDICT = 3,  // one item: predicted sizes and slot reservation for the group
     PH_ENCODE = 4,   // one frame; the last item folds the group's error partials into the stage totals
     PH_FIX = 5,      // one item: exact slots for blocks whose prediction was too small
-    PH_REENCODE = 6  // one frame of an overflowed block (others skip)
+    PH_REENCODE = 6, // one frame of an overflowed block (others skip)
+    PH_SIZE_W = 7,   // exact sizing, eight frames per item (one warp each): widths and frame length;
+                     // the last item turns the lengths into frame offsets and reserves the group's slots
+    PH_ENCODE_W = 8  // exact sizing, eight frames per item (one warp each) at the known offsets; the last
+                     // item folds the group's error partials into the stage totals
 };
 
 struct PPhase {
     uint32_t type, count, arg, pad;
 };
 
-constexpr int kMaxPhases = 40;
+constexpr int kMaxPhases = 128;
+constexpr uint32_t kNoGroup = 0xffffffffu;
 
 // One segment of the work queue: one stage of one circuit. The queue holds
 // ngroups x per_group items starting at item_begin; its groups take the launch's
@@ -71,12 +76,17 @@ struct PLaunch {
     uint32_t nseg;
     uint64_t total_items;    // below 2^32
     uint32_t total_groups;
-    uint32_t R;              // working-vector slots
-    uint64_t slot_amps;      // amplitudes per slot (>= 2^W of every segment)
-    uint64_t slot_frames;    // frames per slot (>= G x frames per block of every segment)
+    // per launch group (host-planned working-vector slots): amplitude offset of its slot in wv,
+    // frame offset of its slot in lb and part, and the group that used the slot before (kNoGroup: none)
+    const uint64_t *g_wv;
+    const uint32_t *g_frame;
+    const uint32_t *g_prev;
     float2 *wv;
     uint64_t *lb;
     float2 *part;
+    uint8_t *wrec;    // per slot frame: chunk widths (256 bytes)
+    uint32_t *flen;   // per slot frame: stream bytes
+    uint32_t *foff;   // per slot frame: byte offset in the block's stream
     uint32_t *done, *arrive;  // per launch group x kMaxPhases each, zero at launch
     uint32_t *ctr;            // queue head, CTAs finished, look-back epoch
     int *status;
