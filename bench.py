@@ -75,6 +75,9 @@ def parse_args():
                          "persistent launch")
     ap.add_argument("--batch", type=int, default=64, help="batch workload: number of circuits")
     ap.add_argument("--no-tune", action="store_true", help="batch workload: fixed m, k instead of the autotuner")
+    ap.add_argument("--tune", action="store_true",
+                    help="single-circuit workloads: pick m, k, inner (and streams) with the autotuner first "
+                         "(not timed; m in 18..24, k in 3..5 in persistent mode, 3..6 otherwise)")
     ap.add_argument("--depth", type=int, default=14)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement (long workloads)")
     ap.add_argument("--cap-gib", type=float, default=0.0, help="device tier cap (pinned host holds the rest)")
@@ -312,6 +315,19 @@ def run_ours(args, rank, world, dist):
         rows = np.concatenate(rows)
         loss = qsim.predictor_train(rows, epochs=40, batch=64, lr=3e-3, seed=100)
         train_info = {"rows": int(rows.shape[0]), "loss": loss, "seconds": time.perf_counter() - t0}
+    tune_info = None
+    if args.tune:
+        t0 = time.perf_counter()
+        base = qsim.default_config(init_basis=circ.init_basis, **kw)
+        kmax = 5 if args.mode == "persistent" else 6
+        best, secs, cand = qsim.autotune(circ, base, m=(18, min(24, n - 2)), k=(3, kmax), inner=(2, 5),
+                                         streams=(1, 2) if args.mode == "streams" else (1,),
+                                         prefix_gates=min(len(circ.gates), 160), reps=1, max_working_log2=n - 2)
+        for f in ("m", "k", "inner", "streams"):
+            kw[f] = getattr(best, f)
+        args.m, args.k, args.inner, args.streams = best.m, best.k, best.inner, best.streams
+        tune_info = {"seconds": time.perf_counter() - t0, "candidates_timed": cand, "prefix_seconds": secs,
+                     "m": best.m, "k": best.k, "inner": best.inner, "streams": best.streams}
     plan = qsim.plan_stages(circ, **kw)
     stream = torch.cuda.current_stream()
 
@@ -441,6 +457,7 @@ def run_ours(args, rank, world, dist):
         "stages": last["nstages"], "plan_seconds": plan.stats()["plan_seconds"],
         "overflow_blocks": last["overflow_blocks"], "peak_reserved_bytes": last["peak_reserved_bytes"],
         "host_tier_peak_bytes": last["host_tier_peak_bytes"], "predictor_training": train_info,
+        "autotune": tune_info,
         "mirror_fidelity": mirror_fidelity,
         "e2e": {"value": e2e, "unit": "updates/s", "h2d_bytes_per_step": h2d // args.steps,
                 "d2h_bytes_per_step": d2h // args.steps} if e2e is not None else None,
@@ -495,7 +512,8 @@ def run_batch_bench(args, rank, world, dist):
             continue
         bc = qsim.default_config(init_basis=c.init_basis, **base)
         best, _, cand = qsim.autotune(c, bc, m=(max(12, c.n - 12), min(24, c.n - 4)), k=(3, 5), inner=(2, 4),
-                                      streams=(1,), prefix_gates=min(len(c.gates), 96), reps=1)
+                                      streams=(1,), prefix_gates=min(len(c.gates), 96), reps=1,
+                                      max_working_log2=c.n - 2)
         timed_candidates += cand
         cfgs.append(dict(m=best.m, inner=best.inner, k=best.k))
     tune_info = None if args.no_tune else {"seconds": time.perf_counter() - t0, "candidates_timed": timed_candidates,

@@ -326,7 +326,8 @@ typedef struct qsim_tune_space {
     uint32_t streams_mask;         /* bit s set: try s streams (s = 1..16) */
     uint32_t prefix_gates;         /* gates of the circuit prefix timed (0 = all) */
     uint32_t reps;                 /* timed runs per candidate (the best is kept) */
-    uint32_t reserved;
+    uint32_t max_working_log2;     /* skip candidates with m + inner above this (0: no limit), e.g. n - 2 to
+                                      keep at least four SV groups per stage */
 } qsim_tune_space;
 
 /* *best receives base with m, k, inner and streams replaced by the fastest

@@ -88,6 +88,11 @@ extern "C" int qsim_autotune(uint32_t n, const qsim_gate *gates, size_t ngates, 
     cur.m = clampu(cur.m ? cur.m : 22, space->m_min, std::min<uint32_t>(space->m_max, n));
     cur.k = clampu(cur.k ? cur.k : 5, space->k_min, space->k_max);
     cur.inner = clampu(cur.inner, space->inner_min, space->inner_max);
+    const uint32_t wmax = space->max_working_log2;
+    auto fits = [&](const qsim_config &c) { return !wmax || c.m + c.inner <= wmax; };
+    while (!fits(cur) && cur.inner > space->inner_min) --cur.inner;
+    while (!fits(cur) && cur.m > space->m_min) --cur.m;
+    if (!fits(cur)) return set_error(QSIM_E_INVALID, "no candidate within the working-vector limit");
     uint32_t s0 = cur.streams;
     if (!(space->streams_mask & (1u << s0))) {
         s0 = 1;
@@ -103,6 +108,7 @@ extern "C" int qsim_autotune(uint32_t n, const qsim_gate *gates, size_t ngates, 
             if (v == cur.*field) continue;
             qsim_config c = cur;
             c.*field = v;
+            if (!fits(c)) continue;
             const double t = time_candidate(n, gates, ng, c, space->reps);
             ++timed;
             if (t < cur_t) {

@@ -137,6 +137,84 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
     }
 }
 
+// Learned-sizing encoder: one warp per frame, frames taken by ticket in
+// block-major order so a frame's predecessors are always already being encoded;
+// the frame offset comes from a warp look-back (epoch-tagged status words). The
+// last CTA folds the frame partials, resets the ticket and advances the epoch.
+__global__ void __launch_bounds__(NT, 4) k_encode_lbw(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
+                                                   const EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
+                                                   int only_overflowed, const uint32_t *__restrict__ ids,
+                                                   BlockSlot *__restrict__ table, StageAccum *acc,
+                                                   LookbackScratch scr, int *status) {
+    const FrameGeom g = geom(m);
+    __shared__ uint32_t s_wb[NW][64];
+    __shared__ double s_red[2][NW];
+    __shared__ bool s_last;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    uint32_t item = 0, epoch = 0;
+    if (lane == 0) {
+        item = atomicAdd(scr.ticket, 1u);
+        epoch = ld_relaxed_u32(scr.epoch) & kEpochMask;
+    }
+    item = __shfl_sync(kFull, item, 0);
+    epoch = __shfl_sync(kFull, epoch, 0);
+    const uint32_t j = item / g.nframes, f = item % g.nframes;
+    bool skip = j >= nblocks;
+    if (!skip && only_overflowed) skip = __ldcg(&res[j].overflow) == 0;
+    if (!skip)
+        encode_frame_warp_lb(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, g, m, e, f,
+                             scr.state + uint64_t(j) * g.nframes, epoch, tgt[j], res + j,
+                             table ? table + ids[j] : nullptr, acc,
+                             (scr.part && !only_overflowed) ? scr.part + item : nullptr, s_wb[warp], status);
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(scr.done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    if (scr.part && !only_overflowed) {
+        double ta = 0, tb = 0;
+        for (uint32_t jb = warp; jb < nblocks; jb += NW) {
+            double a = 0, b = 0;
+            for (uint32_t f2 = lane; f2 < g.nframes; f2 += 32) {
+                const float2 p = __ldcg(scr.part + uint64_t(jb) * g.nframes + f2);
+                a += double(p.x);
+                b += double(p.y);
+            }
+#pragma unroll
+            for (int o = 16; o; o >>= 1) {
+                a += __shfl_xor_sync(kFull, a, o);
+                b += __shfl_xor_sync(kFull, b, o);
+            }
+            if (lane == 0) {
+                res[jb].err_sq = a;
+                res[jb].norm_sq = b;
+            }
+            ta += a;
+            tb += b;
+        }
+        if (lane == 0) {
+            s_red[0][warp] = ta;
+            s_red[1][warp] = tb;
+        }
+        __syncthreads();
+        if (tid == 0 && acc) {
+            double a = 0, b = 0;
+            for (int w = 0; w < NW; ++w) { a += s_red[0][w]; b += s_red[1][w]; }
+            atomicAdd(&acc->err_sq, a);
+            atomicAdd(&acc->norm_sq, b);
+        }
+    }
+    if (tid == 0) {
+        *scr.ticket = 0;
+        *scr.done = 0;
+        __threadfence();
+        atomicExch(scr.epoch, (epoch + 1) & kEpochMask);
+    }
+}
+
 __global__ void __launch_bounds__(NT, 4) k_encode_size(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
                                                     uint64_t *__restrict__ sizes, uint32_t *done_ctr,
                                                     ArenaDev dev, ArenaDev host, EncTarget *__restrict__ tgt,
@@ -398,6 +476,15 @@ void launch_size_reserve(const float2 *wv, uint32_t nblocks, int m, int e, uint6
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
     k_encode_size<<<grid_for(items, 152 * 8), NT, 0, s>>>(wv, nblocks, m, e, sizes, done_ctr, dev, host, tgt, res,
                                                            status, wrec, flen, foff);
+    count_launch();
+}
+
+void launch_encode_lbw(const float2 *wv, uint32_t nblocks, int m, int e, const EncTarget *tgt, EncResult *res,
+                       int only_overflowed, const uint32_t *ids, BlockSlot *table, StageAccum *acc,
+                       const LookbackScratch &scr, int *status, cudaStream_t s) {
+    const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
+    k_encode_lbw<<<unsigned((items + NW - 1) / NW), NT, 0, s>>>(wv, nblocks, m, e, tgt, res, only_overflowed, ids,
+                                                                table, acc, scr, status);
     count_launch();
 }
 

@@ -582,21 +582,23 @@ __device__ __forceinline__ uint32_t size_frame_cta(const float2 *__restrict__ sr
 }
 
 
-// Exact stream bytes of one frame with one warp (no block-wide barrier); the
-// chunk widths go to wrec (2C bytes, Re then Im) for encode_frame_warp_known.
+// Chunk widths of one frame with one warp (no block-wide barrier): lane l
+// receives the Re widths of chunks 4l .. 4l+3 packed in wre and the Im widths
+// in wim; returns the frame's bit-plane words.
 template <bool CG = false>
-__device__ __forceinline__ uint32_t size_frame_warp(const float2 *__restrict__ src, const FrameGeom &g, int e,
-                                                    uint8_t *__restrict__ wrec, int *status) {
+__device__ __forceinline__ uint32_t frame_widths_warp(const float2 *__restrict__ src, const FrameGeom &g, int e,
+                                                      uint32_t &wre, uint32_t &wim, int *status) {
     const int lane = threadIdx.x & 31;
     const float inv_step = exp2i(-e);
-    uint32_t words = 0, wre = 0, wim = 0;  // lane l packs the widths of chunks 4l .. 4l+3
+    uint32_t words = 0;
     int bad = 0;
+    wre = wim = 0;
     for (uint32_t c0 = 0; c0 < g.C; c0 += 8) {
         float2 vin[8];
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             const uint32_t c = c0 + t;
-            vin[t] = c < g.C ? (CG ? __ldcg(src + c * 32 + lane) : __ldcs(src + c * 32 + lane)) : make_float2(0.f, 0.f);
+            vin[t] = c < g.C ? (CG ? __ldcg(src + c * 32 + lane) : src[c * 32 + lane]) : make_float2(0.f, 0.f);
         }
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
@@ -627,20 +629,41 @@ __device__ __forceinline__ uint32_t size_frame_warp(const float2 *__restrict__ s
         }
     }
     if (bad) raise_status(status, bad);
-    if (g.C >= 4) {  // word stores: Re widths at bytes [0, C), Im widths at [C, 2C)
-        uint32_t *w32 = reinterpret_cast<uint32_t *>(wrec);
+    return words;
+}
+
+// The width record (2C bytes, Re then Im) from the packed widths, as words:
+// Re widths at bytes [0, C), Im widths at [C, 2C). dst may be global or shared.
+__device__ __forceinline__ void store_widths_warp(uint8_t *dst, const FrameGeom &g, uint32_t wre, uint32_t wim) {
+    const int lane = threadIdx.x & 31;
+    if (g.C >= 4) {
+        uint32_t *w32 = reinterpret_cast<uint32_t *>(dst);
         if (4u * lane < g.C) {
             w32[lane] = wre;
             w32[g.C / 4 + lane] = wim;
         }
     } else if (lane == 0) {
         for (uint32_t c = 0; c < g.C; ++c) {
-            wrec[c] = uint8_t(wre >> (8 * c));
-            wrec[g.C + c] = uint8_t(wim >> (8 * c));
+            dst[c] = uint8_t(wre >> (8 * c));
+            dst[g.C + c] = uint8_t(wim >> (8 * c));
         }
     }
+}
+
+__device__ __forceinline__ uint32_t frame_len(const FrameGeom &g, uint32_t words) {
     const uint32_t padw = (2u * g.C + 15u) & ~15u;
     return words ? padw + ((4u * words + 15u) & ~15u) : 0u;
+}
+
+// Exact stream bytes of one frame with one warp; the chunk widths go to wrec
+// (2C bytes) for encode_frame_warp_known.
+template <bool CG = false>
+__device__ __forceinline__ uint32_t size_frame_warp(const float2 *__restrict__ src, const FrameGeom &g, int e,
+                                                    uint8_t *__restrict__ wrec, int *status) {
+    uint32_t wre, wim;
+    const uint32_t words = frame_widths_warp<CG>(src, g, e, wre, wim, status);
+    store_widths_warp(wrec, g, wre, wim);
+    return frame_len(g, words);
 }
 
 // Encode frame f of one block with one warp when the frame's chunk widths
@@ -648,19 +671,11 @@ __device__ __forceinline__ uint32_t size_frame_warp(const float2 *__restrict__ s
 // in the block's stream are known: no look-back and no block-wide barrier.
 // The words go straight to their place in the slot; lane 0 also writes the
 // frame's offset-table entry and, for the block's last frame, the header.
-template <bool CG = false>
-__device__ __forceinline__ void encode_frame_warp_known(const float2 *__restrict__ src, const FrameGeom &g, int m,
-                                                        int e, uint32_t f, const uint8_t *__restrict__ wrec,
-                                                        uint32_t frame_off, uint32_t len, EncTarget tgt,
-                                                        EncResult *res_j, BlockSlot *table_slot, StageAccum *acc,
-                                                        float2 *part_item, int *status) {
-    const int lane = threadIdx.x & 31;
-    const uint32_t padw = (2u * g.C + 15u) & ~15u;
-    const float inv_step = exp2i(-e), step = exp2i(e);
-    uint8_t *out = tgt.ptr;
-    const uint64_t cap = tgt.cap;
-    const bool fits = out != nullptr && uint64_t(frame_off) + len <= cap;
-    // widths: lane l holds those of chunks 8l .. 8l+7 (bytes past 2C are masked to zero)
+// Width record bytes 8 lane .. 8 lane + 7 (bytes past 2C masked to zero);
+// with CG the record is read through L2 (written by other CTAs of the launch).
+template <bool CG>
+__device__ __forceinline__ uint2 load_widths_warp(const uint8_t *wrec, const FrameGeom &g) {
+    const uint32_t lane = threadIdx.x & 31;
     uint2 wb = make_uint2(0, 0);
     if (8u * lane < 2u * g.C) {
         wb = CG ? __ldcg(reinterpret_cast<const uint2 *>(wrec + 8u * lane))
@@ -672,6 +687,22 @@ __device__ __forceinline__ void encode_frame_warp_known(const float2 *__restrict
             wb = make_uint2(uint32_t(v), uint32_t(v >> 32));
         }
     }
+    return wb;
+}
+
+// Encode frame f with one warp at byte offset frame_off of the block's stream,
+// given its widths (wb, as load_widths_warp) and length.
+template <bool CG = false>
+__device__ __forceinline__ void encode_frame_warp_core(const float2 *__restrict__ src, const FrameGeom &g, int m,
+                                                       int e, uint32_t f, uint2 wb, uint32_t frame_off, uint32_t len,
+                                                       EncTarget tgt, EncResult *res_j, BlockSlot *table_slot,
+                                                       StageAccum *acc, float2 *part_item, int *status) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t padw = (2u * g.C + 15u) & ~15u;
+    const float inv_step = exp2i(-e), step = exp2i(e);
+    uint8_t *out = tgt.ptr;
+    const uint64_t cap = tgt.cap;
+    const bool fits = out != nullptr && uint64_t(frame_off) + len <= cap;
     uint32_t wsum = 0;
 #pragma unroll
     for (int t = 0; t < 4; ++t) wsum += ((wb.x >> (8 * t)) & 0xff) + ((wb.y >> (8 * t)) & 0xff);
@@ -785,6 +816,91 @@ __device__ __forceinline__ void encode_frame_warp_known(const float2 *__restrict
             }
         }
     }
+}
+
+// Exact-sizing encoder: widths (wrec) and frame offset from the sizing pass.
+template <bool CG = false>
+__device__ __forceinline__ void encode_frame_warp_known(const float2 *__restrict__ src, const FrameGeom &g, int m,
+                                                        int e, uint32_t f, const uint8_t *__restrict__ wrec,
+                                                        uint32_t frame_off, uint32_t len, EncTarget tgt,
+                                                        EncResult *res_j, BlockSlot *table_slot, StageAccum *acc,
+                                                        float2 *part_item, int *status) {
+    encode_frame_warp_core<CG>(src, g, m, e, f, load_widths_warp<CG>(wrec, g), frame_off, len, tgt, res_j,
+                               table_slot, acc, part_item, status);
+}
+
+// Warp look-back over the preceding frames of the block (status words of lb_block,
+// tagged with epoch): publishes frame f's length, returns the bytes of frames 0..f-1.
+// Every wait is time-bounded (QSIM_E_TIMEOUT).
+__device__ __forceinline__ uint32_t lookback_warp(uint64_t *lb_block, uint32_t f, uint32_t epoch, uint32_t len,
+                                                  int *status) {
+    const int lane = threadIdx.x & 31;
+    uint64_t *st = lb_block;
+    if (f == 0) {
+        if (lane == 0) st_relaxed_u64(st, lb_word(epoch, kFlagP, len));
+        return 0;
+    }
+    if (lane == 0) st_relaxed_u64(st + f, lb_word(epoch, kFlagA, len));
+    uint64_t excl = 0;
+    int64_t end = int64_t(f) - 1;
+    bool timed_out = false;
+    while (true) {
+        const int64_t p = end - lane;
+        uint32_t flag = kFlagP, val = 0;
+        if (p >= 0) {
+            long long spins = 0;
+            const uint64_t t0 = global_ns();
+            while (true) {
+                const uint64_t w = ld_relaxed_u64(st + p);
+                const uint32_t fl = uint32_t(w >> 32) & 3u;
+                if (fl != 0 && uint32_t(w >> 34) == epoch) {
+                    flag = fl;
+                    val = uint32_t(w);
+                    break;
+                }
+                if (++spins > kSpinLimit || global_ns() - t0 > kLookbackWaitNs) {
+                    timed_out = true;
+                    flag = kFlagP;
+                    val = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        const uint32_t pmask = __ballot_sync(kFull, flag == kFlagP);
+        const int first = pmask ? __ffs(pmask) - 1 : 32;
+        uint64_t contrib = lane <= first ? val : 0;
+#pragma unroll
+        for (int o = 16; o; o >>= 1) contrib += __shfl_xor_sync(kFull, contrib, o);
+        excl += contrib;
+        if (pmask) break;
+        end -= 32;
+    }
+    if (__any_sync(kFull, timed_out) && lane == 0) raise_status(status, QSIM_E_TIMEOUT);
+    if (lane == 0) st_relaxed_u64(st + f, lb_word(epoch, kFlagP, uint32_t(excl + len)));
+    return uint32_t(excl);
+}
+
+// Learned-sizing encoder, one warp per frame: widths pass, look-back for the
+// frame's offset, then the frame is read again (from L2) and written into the
+// reserved slot if it fits (else the block's overflow flag is set and
+// res.total still receives the exact size). s_wb: 64 words of shared memory
+// for this warp. Frames of a block must be taken in order (ticket or queue).
+template <bool CG = false>
+__device__ __forceinline__ void encode_frame_warp_lb(const float2 *__restrict__ src, const FrameGeom &g, int m, int e,
+                                                     uint32_t f, uint64_t *lb_block, uint32_t epoch, EncTarget tgt,
+                                                     EncResult *res_j, BlockSlot *table_slot, StageAccum *acc,
+                                                     float2 *part_item, uint32_t *s_wb, int *status) {
+    uint32_t wre, wim;
+    const uint32_t words = frame_widths_warp<CG>(src, g, e, wre, wim, status);
+    const uint32_t len = frame_len(g, words);
+    store_widths_warp(reinterpret_cast<uint8_t *>(s_wb), g, wre, wim);
+    __syncwarp();
+    const uint2 wb = load_widths_warp<false>(reinterpret_cast<const uint8_t *>(s_wb), g);
+    __syncwarp();
+    const uint32_t excl = lookback_warp(lb_block, f, epoch, len, status);
+    encode_frame_warp_core<CG>(src, g, m, e, f, wb, uint32_t(g.data_start) + excl, len, tgt, res_j, table_slot, acc,
+                               part_item, status);
 }
 
 }  // namespace cdev

@@ -488,6 +488,10 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                 }
             }
             P.out_mask = om;
+            if (ps.T > kMaxTileBits || o != P.nout)
+                return set_error(QSIM_E_INVALID, "internal: pass tile layout out of range");
+            for (uint32_t t = 0; t < ps.T; ++t)
+                if (ps.tile_pos[t] >= st.W) return set_error(QSIM_E_INVALID, "internal: tile bit outside the working vector");
             P.op_begin = ops.size();
             P.op_count = ps.ops.size();
             P.mat_elems = 0;
@@ -1116,14 +1120,14 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         if (R.predict) add(PH_PREDICT, 1, 0);
         for (uint32_t pi = 0; pi < sd.npasses; ++pi) add(PH_PASS, 1u << sd.passes_host[pi].nout, pi);
         if (R.predict) {
-            add(PH_ENCODE, gframes, 0);
+            add(PH_ENCODE, (gframes + 7) / 8, 0);
         } else {
             add(PH_SIZE_W, (gframes + 7) / 8, 0);
             add(PH_ENCODE_W, (gframes + 7) / 8, 0);
         }
         if (R.predict) {
             add(PH_FIX, 1, 0);
-            add(PH_REENCODE, gframes, 0);
+            add(PH_REENCODE, (gframes + 7) / 8, 0);
         }
         // the last phase index is the group's finished flag
         if (nph > uint32_t(kMaxPhases) - 1)
@@ -1555,14 +1559,14 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
                                    arena_host(out_par), w.tgt.p, w.res.p, 0, status, w.s);
                     prof.end(w.s);
                     prof.begin(P_ENCODE, w.s);
-                    launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
+                    launch_encode_lbw(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
                     prof.end(w.s);
                     prof.begin(P_RESERVE, w.s);
                     launch_reserve(nb, nullptr, 0, nullptr, 0, worst, arena_dev(out_par), arena_host(out_par),
                                    w.tgt.p, w.res.p, 1, status, w.s);
                     prof.end(w.s);
                     prof.begin(P_REENCODE, w.s);
-                    launch_encode(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 1, ids, tab_out, acc, scr, status, w.s);
+                    launch_encode_lbw(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 1, ids, tab_out, acc, scr, status, w.s);
                     prof.end(w.s);
                 } else {
                     prof.begin(P_ENCODE_SIZE, w.s);

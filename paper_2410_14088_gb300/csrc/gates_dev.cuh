@@ -30,8 +30,9 @@ __device__ __forceinline__ void coop_copy(T &dst, const T &src) {
 
 struct PassSmem {
     PassDev p;
-    uint32_t hi[256];
-    uint32_t off12[32];    // 4096-amplitude tiles with L >= log2(NT): working offset of element tid + NT u, minus tid
+    // 4096-amplitude tiles: element tid + NT u sits at working offset tpart[tid] + off12[u]
+    uint32_t off12[32];
+    uint32_t tpart[256];
     uint32_t offs[64];     // dense op: working offsets of its 2^k matrix columns within the tile
     uint32_t offs_sw[64];  // the same through the swizzle
     uint32_t comp[16];     // dense op: its complement tile bits
@@ -303,26 +304,25 @@ template <int NT>
 __device__ __forceinline__ void pass_setup(const PassDev &pd, PassSmem &S) {
     coop_copy<NT>(S.p, pd);
     __syncthreads();
-    const uint32_t T = S.p.T, L = S.p.L;
-    const uint32_t nhi = 1u << (T - L);
-    for (uint32_t h = threadIdx.x; h < nhi; h += NT) {
-        uint32_t o = 0;
-        for (uint32_t t = 0; t < T - L; ++t) o |= ((h >> t) & 1u) << S.p.tile_pos[L + t];
-        S.hi[h] = o;
-    }
+    const uint32_t T = S.p.T;
     constexpr uint32_t A = NT == 256 ? 8 : 7;
-    if (T == 12 && L >= A && threadIdx.x < (4096u / NT)) {
-        // element i = tid + NT u: low bits tid, then bits A..L-1 from u, the rest from the high table
-        const uint32_t u = threadIdx.x, sh = L - A;
-        uint32_t o = (u & ((1u << sh) - 1)) * NT;
-        for (uint32_t t = 0; t < T - L; ++t) o |= ((u >> (sh + t)) & 1u) << S.p.tile_pos[L + t];
-        S.off12[u] = o;
+    if (T == 12) {
+        // element i = tid + NT u: tile bits 0..A-1 from tid, A..11 from u (disjoint working bits)
+        const uint32_t x = threadIdx.x;
+        uint32_t o = 0;
+        for (uint32_t t = 0; t < A; ++t) o |= ((x >> t) & 1u) << S.p.tile_pos[t];
+        S.tpart[x] = o;
+        if (x < (4096u / NT)) {
+            uint32_t h = 0;
+            for (uint32_t t = A; t < 12; ++t) h |= ((x >> (t - A)) & 1u) << S.p.tile_pos[t];
+            S.off12[x] = h;
+        }
     }
     __syncthreads();
 }
 
-// Fast tile addressing for T = 12, L >= log2(NT): element i = tid + NT u sits
-// at working offset tid + off12[u] and at shared index (tid ^ xt) ^ xu(u) + NT u,
+// Fast tile addressing for T = 12: element i = tid + NT u sits at working
+// offset tpart[tid] + off12[u] and at shared index (tid ^ xt) ^ xu(u) + NT u,
 // the XOR swizzle split into a per-thread and a per-u part.
 template <int NT>
 __device__ __forceinline__ uint32_t swz_thread(uint32_t tid) {
@@ -334,7 +334,14 @@ __device__ __forceinline__ constexpr uint32_t swz_u(uint32_t u) {
 }
 template <int NT>
 __device__ __forceinline__ bool fast12(const PassSmem &S) {
-    return S.p.T == 12 && S.p.L >= (NT == 256 ? 8u : 7u);
+    return S.p.T == 12;
+}
+
+// working offset of the tile bits L..T-1 of tile element h << L (tiles other than 4096 amplitudes)
+__device__ __forceinline__ uint32_t hi_off(const PassSmem &S, uint32_t h) {
+    uint32_t o = 0;
+    for (uint32_t t = 0; t < S.p.T - S.p.L; ++t) o |= ((h >> t) & 1u) << S.p.tile_pos[S.p.L + t];
+    return o;
 }
 
 // working index of element 0 of tile `cta` (its non-tile bits)
@@ -353,7 +360,7 @@ __device__ __forceinline__ void tile_load(const float2 *__restrict__ g, uint64_t
     const uint32_t T = S.p.T, L = S.p.L, lmask = (1u << L) - 1;
     const int tid = threadIdx.x;
     if (fast12<NT>(S)) {
-        const float2 *gt = g + (base | uint64_t(tid));
+        const float2 *gt = g + (base | uint64_t(S.tpart[tid]));
         const uint32_t tq = swz_thread<NT>(tid);
         if constexpr (CG) {
 #pragma unroll
@@ -376,7 +383,7 @@ __device__ __forceinline__ void tile_load(const float2 *__restrict__ g, uint64_t
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
                 const uint32_t i = i0 + u * NT;
-                if (i < (1u << T)) v[u] = __ldcg(&g[base | (i & lmask) | S.hi[i >> L]]);
+                if (i < (1u << T)) v[u] = __ldcg(&g[base | (i & lmask) | hi_off(S, i >> L)]);
             }
 #pragma unroll
             for (int u = 0; u < 8; ++u) {
@@ -385,7 +392,7 @@ __device__ __forceinline__ void tile_load(const float2 *__restrict__ g, uint64_t
             }
         }
     } else {
-        for (uint32_t i = tid; i < (1u << T); i += NT) cp_async8(&tile[swz(i)], &g[base | (i & lmask) | S.hi[i >> L]]);
+        for (uint32_t i = tid; i < (1u << T); i += NT) cp_async8(&tile[swz(i)], &g[base | (i & lmask) | hi_off(S, i >> L)]);
     }
 }
 
@@ -395,12 +402,12 @@ __device__ __forceinline__ void tile_store(float2 *__restrict__ g, uint64_t base
     const uint32_t T = S.p.T, L = S.p.L, lmask = (1u << L) - 1;
     if (fast12<NT>(S)) {
         const uint32_t tid = threadIdx.x, tq = swz_thread<NT>(tid);
-        float2 *gt = g + (base | uint64_t(tid));
+        float2 *gt = g + (base | uint64_t(S.tpart[tid]));
 #pragma unroll
         for (uint32_t u = 0; u < 4096u / NT; ++u) gt[S.off12[u]] = tile[(tq ^ swz_u<NT>(u)) + NT * u];
         return;
     }
-    for (uint32_t i = threadIdx.x; i < (1u << T); i += NT) g[base | (i & lmask) | S.hi[i >> L]] = tile[swz(i)];
+    for (uint32_t i = threadIdx.x; i < (1u << T); i += NT) g[base | (i & lmask) | hi_off(S, i >> L)] = tile[swz(i)];
 }
 
 // The pass blob (op descriptors, diagonal ops' index tables and phases, small

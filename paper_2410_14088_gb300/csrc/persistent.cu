@@ -57,7 +57,7 @@ template <int PREC>
 __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
     extern __shared__ float4 dsm[];
     __shared__ gdev::PassSmem PS;
-    __shared__ cdev::EncSmem SE;
+    __shared__ uint32_t s_wb[PT / 32][64];
     __shared__ OpDev s_pre[kMaxPreOps];
     __shared__ __align__(16) PSeg S;
     __shared__ uint32_t s_hist[PT / 32][32];
@@ -214,17 +214,19 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             // the group's histograms are consumed: leave them zero for the next stage
             for (uint32_t t = tid; t < S.G * 32; t += PT) S.hist[bbase * 32 + t] = 0;
         } else if (type == PH_ENCODE || type == PH_REENCODE) {
-            const uint32_t jj = i / g.nframes, f = i % g.nframes;
+            // learned sizing: eight frames per item, one warp each, offsets by warp look-back
+            const uint32_t fi = i * (PT / 32) + warp;
             const bool retry = type == PH_REENCODE;
-            if (tid == 0) s_flag = retry ? int(__ldcg(&S.res[bbase + jj].overflow) != 0) : 1;
-            __syncthreads();
-            if (s_flag) {
-                const uint32_t epoch = (s_epoch + 2 * q + (retry ? 1 : 0)) & cdev::kEpochMask;
-                cdev::encode_frame_cta<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g, int(S.m), S.e, f,
-                                             L.lb + L.g_frame[q] + uint64_t(jj) * g.nframes, epoch,
-                                             load_target(&S.tgt[bbase + jj]), &S.res[bbase + jj], S.tab_out + ids[jj],
-                                             S.acc, retry ? nullptr : part + uint64_t(jj) * g.nframes + f,
-                                             retry ? 1 : 0, reinterpret_cast<uint32_t *>(dsm), SE, L.status);
+            if (fi < gframes) {
+                const uint32_t jj = fi / g.nframes, f = fi % g.nframes;
+                if (!retry || __ldcg(&S.res[bbase + jj].overflow) != 0) {
+                    const uint32_t epoch = (s_epoch + 2 * q + (retry ? 1 : 0)) & cdev::kEpochMask;
+                    cdev::encode_frame_warp_lb<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g, int(S.m), S.e,
+                                                     f, L.lb + L.g_frame[q] + uint64_t(jj) * g.nframes, epoch,
+                                                     load_target(&S.tgt[bbase + jj]), &S.res[bbase + jj],
+                                                     S.tab_out + ids[jj], S.acc, retry ? nullptr : part + fi,
+                                                     s_wb[warp], L.status);
+                }
             }
         } else if (type == PH_FIX) {
             for (uint32_t jj = tid; jj < S.G; jj += PT) {
@@ -381,11 +383,8 @@ int launch_stage_prec(const PLaunch &a, size_t smem, cudaStream_t s, int *grid_o
 }  // namespace
 
 size_t persistent_smem_bytes(size_t pass_bytes) {
-    size_t pass = pass_bytes;
-    size_t enc = size_t(cdev::kStageWords) * sizeof(uint32_t);
-    size_t mlp = size_t(kMlpParams) * sizeof(float);
-    size_t m = pass > enc ? pass : enc;
-    return m > mlp ? m : mlp;
+    const size_t mlp = size_t(kMlpParams) * sizeof(float);
+    return pass_bytes > mlp ? pass_bytes : mlp;
 }
 
 int prepare_stage_persistent(int prec, size_t smem) {

@@ -283,6 +283,8 @@ struct Fuser {
     }
 };
 
+constexpr uint32_t kCoalesceBits = 3;
+
 void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
     const uint32_t W = st.W;
     st.pre_ops.clear();
@@ -293,7 +295,9 @@ void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
             st.pre_ops.push_back(first++);
     }
     uint32_t T = std::min(tile_bits, W);
-    const uint32_t L = std::min<uint32_t>(5, T);
+    // the low kCoalesceBits working bits are always tile bits: rows of 2^kCoalesceBits amplitudes
+    // (64 bytes, two DRAM sectors) are read and written whole
+    const uint32_t L = std::min<uint32_t>(kCoalesceBits, T);
     st.passes.clear();
     auto close = [&](std::set<uint32_t> &P, std::vector<uint32_t> &ops) {
         if (ops.empty()) return;

@@ -90,7 +90,7 @@ class TuneSpace(ctypes.Structure):
     _fields_ = [("m_min", ctypes.c_uint32), ("m_max", ctypes.c_uint32), ("k_min", ctypes.c_uint32),
                 ("k_max", ctypes.c_uint32), ("inner_min", ctypes.c_uint32), ("inner_max", ctypes.c_uint32),
                 ("streams_mask", ctypes.c_uint32), ("prefix_gates", ctypes.c_uint32), ("reps", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("max_working_log2", ctypes.c_uint32)]
 
 
 MLP_INPUTS, MLP_PARAMS, TRAIN_ROW = 41, 6913, 42
@@ -518,13 +518,13 @@ def predictor_get() -> np.ndarray:
 # --------------------------------------------------------------------------
 
 def autotune(circuit, base: Optional[Config] = None, m=(18, 24), k=(3, 6), inner=(2, 4), streams=(1, 2, 4),
-             prefix_gates=0, reps=1):
+             prefix_gates=0, reps=1, max_working_log2=0):
     """Returns (best Config, prefix seconds, candidates timed; 0 = cache hit)."""
     base = base if base is not None else default_config(init_basis=circuit.init_basis)
     mask = 0
     for sc in streams:
         mask |= 1 << sc
-    sp = TuneSpace(m[0], m[1], k[0], k[1], inner[0], inner[1], mask, prefix_gates, reps, 0)
+    sp = TuneSpace(m[0], m[1], k[0], k[1], inner[0], inner[1], mask, prefix_gates, reps, max_working_log2)
     arr, mats = marshal_gates(circuit.gates)
     best = Config()
     secs = ctypes.c_double()

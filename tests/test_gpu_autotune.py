@@ -27,3 +27,14 @@ def test_autotune_rejects_empty_space():
     c = inputs.ghz(12)
     with pytest.raises(qsim.QsimError):
         qsim.autotune(c, m=(9, 8))
+
+
+def test_autotune_working_vector_limit():
+    # candidates whose working vector (m + inner bits) exceeds the limit are not timed
+    c = inputs.qft_rz_cx(18, 1, 4)
+    qsim.autotune_cache_clear()
+    best, _, cand = qsim.autotune(c, m=(10, 16), k=(3, 5), inner=(2, 4), streams=(1,), prefix_gates=120, reps=1,
+                                  max_working_log2=c.n - 2)
+    assert best.m + best.inner <= c.n - 2 and cand >= 1
+    with pytest.raises(qsim.QsimError):
+        qsim.autotune(c, m=(12, 14), inner=(3, 4), max_working_log2=10)
