@@ -146,6 +146,8 @@ __global__ void __launch_bounds__(NT, 4) k_encode_lbw(const float2 *__restrict__
                                                    int only_overflowed, const uint32_t *__restrict__ ids,
                                                    BlockSlot *__restrict__ table, StageAccum *acc,
                                                    LookbackScratch scr, int *status) {
+    // a re-encode with nothing to redo leaves the ticket, the counters and the epoch alone
+    if (only_overflowed && scr.pending && ld_relaxed_u32(scr.pending) == 0) return;
     const FrameGeom g = geom(m);
     __shared__ uint32_t s_wb[NW][64];
     __shared__ double s_red[2][NW];
@@ -353,12 +355,14 @@ __global__ void __launch_bounds__(NT, 4) k_encode_known(const float2 *__restrict
 __global__ void k_reserve(uint32_t nblocks, const uint64_t *__restrict__ need, uint64_t add_const,
                           const float *__restrict__ pred_log2, double margin, uint64_t worst,
                           ArenaDev dev, ArenaDev host, EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
-                          int retry_overflowed, int *status) {
+                          int retry_overflowed, int *status, uint32_t *pending) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pending && !retry_overflowed && j == 0) *pending = 0;
     if (j >= nblocks) return;
     uint64_t want;
     if (retry_overflowed) {
         if (res[j].overflow == 0) return;
+        if (pending) atomicAdd(pending, 1u);
         want = res[j].total;
     } else if (pred_log2) {
         double p = double(pred_log2[j]);
@@ -500,9 +504,9 @@ void launch_encode_known(const float2 *wv, uint32_t nblocks, int m, int e, const
 
 void launch_reserve(uint32_t nblocks, const uint64_t *need, uint64_t add_const, const float *pred_log2,
                     double margin, uint64_t worst, const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt,
-                    EncResult *res, int retry_overflowed, int *status, cudaStream_t s) {
+                    EncResult *res, int retry_overflowed, int *status, cudaStream_t s, uint32_t *pending) {
     k_reserve<<<(nblocks + 127) / 128, 128, 0, s>>>(nblocks, need, add_const, pred_log2, margin, worst, dev, host,
-                                                    tgt, res, retry_overflowed, status);
+                                                    tgt, res, retry_overflowed, status, pending);
     count_launch();
 }
 

@@ -64,6 +64,7 @@ struct LookbackScratch {
     uint32_t *done;
     uint32_t *epoch;
     float2 *part;       // per-frame (err_sq, norm_sq) partials, or null (then per-CTA atomics)
+    uint32_t *pending;  // learned sizing: blocks to re-encode (counted by the exact re-reservation), or null
 };
 
 void count_launch();
@@ -102,9 +103,10 @@ struct PreOps {
 // decode with the block references read from table[ids[j]]
 void launch_decode_table(const BlockSlot *table, const uint32_t *ids, uint32_t nblocks, int m, float2 *wv,
                          uint32_t *hist, int *status, const PreOps &pre, cudaStream_t s);
+// pending (nullable): zeroed by a first reservation, counts the blocks re-reserved by retry_overflowed
 void launch_reserve(uint32_t nblocks, const uint64_t *need, uint64_t add_const, const float *pred_log2,
                     double margin, uint64_t worst, const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt,
-                    EncResult *res, int retry_overflowed, int *status, cudaStream_t s);
+                    EncResult *res, int retry_overflowed, int *status, cudaStream_t s, uint32_t *pending = nullptr);
 void launch_copy_out(const float2 *wv, uint32_t nblocks, int m, const EncTarget *tgt, const uint32_t *ids,
                      BlockSlot *table, StageAccum *acc, int *status, cudaStream_t s);
 void launch_copy_in(const BlockRef *in, uint32_t nblocks, int m, float2 *wv, int *status, cudaStream_t s);

@@ -274,6 +274,7 @@ static int ensure_device_ctx(DeviceCtx &c) {
 static LookbackScratch make_scratch(uint64_t *state, uint32_t *ctr, float2 *part = nullptr) {
     LookbackScratch s{};
     s.part = part;
+    s.pending = nullptr;
     s.state = state;
     s.ticket = ctr;
     s.done = ctr + 1;
@@ -1433,12 +1434,12 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             (rc = w.pred.alloc(max_batch_blocks)) ||
             (!persistent && (rc = w.wrec.alloc(max_batch_blocks * nframes * 256))) ||
             (rc = w.flen.alloc(max_batch_blocks * nframes)) || (rc = w.foff.alloc(max_batch_blocks * nframes)) ||
-            (rc = w.lb_ctr.alloc(4))) {
+            (rc = w.lb_ctr.alloc(8))) {
             destroy_streams();
             return rc;
         }
         CUDA_TRY(cudaMemsetAsync(w.lb_state.p, 0, max_batch_blocks * nframes * sizeof(uint64_t), main));
-        CUDA_TRY(cudaMemsetAsync(w.lb_ctr.p, 0, 4 * sizeof(uint32_t), main));
+        CUDA_TRY(cudaMemsetAsync(w.lb_ctr.p, 0, 8 * sizeof(uint32_t), main));
         CUDA_TRY(cudaMemsetAsync(w.sizes.p, 0, max_batch_blocks * sizeof(uint64_t), main));
     }
     cudaEvent_t ev_start, ev_stop, ev_fork;
@@ -1552,18 +1553,19 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
                 prof.end(w.s);
             } else {
                 LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p, w.part.p);
+                scr.pending = w.lb_ctr.p + 4;
                 if (predict) {
                     // reserve 2^pred (1 + margin) bytes, encode once, re-encode under-estimated blocks exactly
                     prof.begin(P_RESERVE, w.s);
                     launch_reserve(nb, nullptr, 0, w.pred.p, cfg.predictor_margin, worst, arena_dev(out_par),
-                                   arena_host(out_par), w.tgt.p, w.res.p, 0, status, w.s);
+                                   arena_host(out_par), w.tgt.p, w.res.p, 0, status, w.s, scr.pending);
                     prof.end(w.s);
                     prof.begin(P_ENCODE, w.s);
                     launch_encode_lbw(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
                     prof.end(w.s);
                     prof.begin(P_RESERVE, w.s);
                     launch_reserve(nb, nullptr, 0, nullptr, 0, worst, arena_dev(out_par), arena_host(out_par),
-                                   w.tgt.p, w.res.p, 1, status, w.s);
+                                   w.tgt.p, w.res.p, 1, status, w.s, scr.pending);
                     prof.end(w.s);
                     prof.begin(P_REENCODE, w.s);
                     launch_encode_lbw(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 1, ids, tab_out, acc, scr, status, w.s);
