@@ -135,14 +135,18 @@ int qsim_plan_get_stats(const qsim_plan *plan, qsim_plan_stats *out);
 
 /* Introspection of a stage's fused ops (what the gate passes apply). */
 typedef struct qsim_op_info {
-    uint32_t type;      /* 0 dense matrix, 1 diagonal phases, 2 phase flip */
+    uint32_t type;      /* 0 dense matrix, 1 diagonal phases, 2 phase flip, 3 controlled-separable diagonal */
     uint32_t nq;        /* qubits of the op (0 for a phase flip) */
-    uint32_t qubits[8]; /* full qubit ids; matrix bit j <-> qubits[j] (dense ops <= 6, diagonal ops <= 8) */
+    uint32_t qubits[8]; /* full qubit ids; matrix bit j <-> qubits[j] (dense ops <= 6, diagonal ops <= 8;
+                           type 3: the first 8 of qlist) */
     uint32_t ngates;    /* input gates folded into the op */
     uint32_t pass;      /* index of the shared-memory tile pass within the stage */
     uint64_t basis;     /* phase flip: the flipped basis state */
     const double *u;    /* dense: 2^nq x 2^nq complex128 row-major; diagonal: 2^nq complex128;
+                           type 3: K[0], K[1], then per target D[0][0], D[0][1], D[1][0], D[1][1]
+                           (complex128), phase(x) = K[b] prod_t D_t[b][x_t] with b the control bit;
                            owned by the plan */
+    const uint32_t *qlist; /* type 3: nq qubits, the control then the targets; owned by the plan */
 } qsim_op_info;
 
 /* *count receives the number of ops of `stage`; if ops is not NULL it must

@@ -520,6 +520,23 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                                           bfr.data() + od.bfrag);
                     }
                     P.kmax = std::max<uint32_t>(P.kmax, op.k);
+                } else if (op.type == OP_CSEP) {
+                    // control and targets: tile bits, or bits constant over a tile (working bit or outer qubit)
+                    auto source = [&](uint32_t q) -> uint32_t {
+                        if (q < m) return q;
+                        auto f = std::find(st.inner.begin(), st.inner.end(), q);
+                        return f != st.inner.end() ? uint32_t(m + (f - st.inner.begin())) : 64 + q;
+                    };
+                    auto tile_bit = [&](uint32_t src) -> int32_t {
+                        if (src >= 64) return -1;
+                        for (uint32_t t = 0; t < ps.T; ++t)
+                            if (ps.tile_pos[t] == src) return int32_t(t);
+                        return -1;
+                    };
+                    od.k = uint32_t(op.csep_q.size());
+                    const uint32_t cs = source(op.csep_q[0]);
+                    const int32_t ctb = tile_bit(cs);
+                    od.cctl = ctb >= 0 ? uint32_t(ctb) : (kCtlConst | cs);
                 } else {
                     od = diag_opdev(op);
                     if (op.type == OP_DIAG) {
@@ -578,6 +595,55 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                             const uint8_t *fb = reinterpret_cast<const uint8_t *>(&f);
                             pb.insert(pb.end(), fb, fb + 8);
                         }
+                    } else if (od.type == OP_CSEP) {
+                        // P_lo[b][x] over tile bits 0..6, P_hi[b][y] over tile bits 7.. (with K[b]), and the
+                        // records {source, D[0][0], D[0][1], D[1][0], D[1][1]} of the targets outside the tile
+                        auto source = [&](uint32_t q) -> uint32_t {
+                            if (q < m) return q;
+                            auto f = std::find(st.inner.begin(), st.inner.end(), q);
+                            return f != st.inner.end() ? uint32_t(m + (f - st.inner.begin())) : 64 + q;
+                        };
+                        std::vector<cd> plo(256, cd(1, 0)), phi(128, cd(1, 0));
+                        for (uint32_t b = 0; b < 2; ++b)
+                            for (uint32_t y = 0; y < 64; ++y) phi[64 * b + y] = op.u[b];
+                        std::vector<float2> recs;
+                        for (size_t t = 1; t < op.csep_q.size(); ++t) {
+                            const cd *D = op.u.data() + 2 + 4 * (t - 1);
+                            const uint32_t src = source(op.csep_q[t]);
+                            int32_t tb = -1;
+                            if (src < 64)
+                                for (uint32_t x = 0; x < ps.T; ++x)
+                                    if (ps.tile_pos[x] == src) tb = int32_t(x);
+                            if (tb >= 0 && tb < 7) {
+                                for (uint32_t b = 0; b < 2; ++b)
+                                    for (uint32_t x = 0; x < 128; ++x) plo[128 * b + x] *= D[2 * b + ((x >> tb) & 1u)];
+                            } else if (tb >= 7) {
+                                for (uint32_t b = 0; b < 2; ++b)
+                                    for (uint32_t y = 0; y < 64; ++y) phi[64 * b + y] *= D[2 * b + ((y >> (tb - 7)) & 1u)];
+                            } else {
+                                float2 r0;
+                                const uint32_t srcw = src;
+                                memcpy(&r0.x, &srcw, 4);
+                                r0.y = 0.f;
+                                recs.push_back(r0);
+                                for (int v = 0; v < 4; ++v)
+                                    recs.push_back(make_float2(float(D[v].real()), float(D[v].imag())));
+                            }
+                        }
+                        auto put = [&](const float2 &f) {
+                            const uint8_t *fb = reinterpret_cast<const uint8_t *>(&f);
+                            pb.insert(pb.end(), fb, fb + 8);
+                        };
+                        align16();
+                        od.tab = uint32_t(pb.size() / 8);
+                        for (const cd &v : plo) put(make_float2(float(v.real()), float(v.imag())));
+                        align16();
+                        od.dlut = uint32_t(pb.size() / 8);
+                        for (const cd &v : phi) put(make_float2(float(v.real()), float(v.imag())));
+                        align16();
+                        od.mat = uint32_t(pb.size() / 8);
+                        od.ncst = uint32_t(recs.size() / 5);
+                        for (const float2 &f : recs) put(f);
                     } else if (od.type == OP_DENSE) {
                         const bool tc = p->cfg.prec != QSIM_PREC_FP32 && od.k >= min_k && od.k <= 5 && ps.T == 12;
                         if (tc) continue;
@@ -1306,7 +1372,8 @@ static int finish_run(RunCtx &R, int dev, double ms, Profiler *prof, qsim_stats 
             bytes[P_PASS] += 16 * amps * sd.npasses;
             bytes[P_STAGE] += in_store + out_store + 8 * amps * (2 + (predict ? 0 : 1)) + 16 * amps * sd.npasses;
             for (const Op &op : p->stages[i].ops) {
-                const double fl = (op.type == OP_DENSE ? 8.0 * double(1u << op.k) : op.type == OP_DIAG ? 6.0 : 0.0) * amps;
+                const double fl = (op.type == OP_DENSE ? 8.0 * double(1u << op.k)
+                                   : op.type == OP_DIAG ? 6.0 : op.type == OP_CSEP ? 12.0 : 0.0) * amps;
                 flops[P_PASS] += fl;
                 flops[P_STAGE] += fl;
             }
@@ -1701,7 +1768,8 @@ static int run_batch(const qsim_plan *const *plans, size_t count, cudaStream_t m
             alg_bytes += in_store + out_store + 8 * amps * (2 + (R.predict ? 0 : 1)) +
                          16 * amps * R.pd->stages[i].npasses;
             for (const Op &op : R.p->stages[i].ops)
-                alg_flops += (op.type == OP_DENSE ? 8.0 * double(1u << op.k) : op.type == OP_DIAG ? 6.0 : 0.0) * amps;
+                alg_flops += (op.type == OP_DENSE ? 8.0 * double(1u << op.k)
+                              : op.type == OP_DIAG ? 6.0 : op.type == OP_CSEP ? 12.0 : 0.0) * amps;
         }
     }
     if (launch_stat) {
@@ -1831,6 +1899,10 @@ int qsim_plan_stage_ops(const qsim_plan *plan, size_t stage, size_t *count, qsim
         } else if (op.type == OP_DIAG) {
             o.nq = op.k;
             for (uint32_t j = 0; j < op.k; ++j) o.qubits[j] = op.fq[j];
+        } else if (op.type == OP_CSEP) {
+            o.nq = uint32_t(op.csep_q.size());
+            for (uint32_t j = 0; j < o.nq && j < 8; ++j) o.qubits[j] = op.csep_q[j];
+            o.qlist = op.csep_q.data();
         }
         o.u = op.u.empty() ? nullptr : reinterpret_cast<const double *>(op.u.data());
         o.pass = 0xFFFFFFFFu;  // applied by the decoder

@@ -40,6 +40,10 @@ struct PassSmem {
     // linear over GF(2), so swz(b | c) = swz(b) ^ swz(c) for disjoint bit sets b, c)
     uint32_t cb[2][64];
     uint32_t dconst[kDiagRun];  // diagonal op d of a run: phase-index bits constant over the tile
+    // controlled-separable op: per branch b, csq[b][h] = P_hi[b][h] * (factors of the targets outside the tile)
+    float2 csq[2][64];
+    float2 ck[2];
+    uint32_t cbconst;           // the branch when the control is outside the tile
 };
 static_assert(sizeof(OpDev) % 16 == 0, "op descriptors are copied as 16-byte words");
 
@@ -519,6 +523,59 @@ __device__ __forceinline__ void tile_ops(float2 *tile, const uint4 *blob, float2
                         }
                     }
                     a = v;
+                }
+            }
+        } else if (type == OP_CSEP) {
+            // phase(x) = P_lo[b][tile bits 0..6] * P_hi[b][tile bits 7..] * K_b, b = the control bit,
+            // K_b from the targets outside the tile
+            const float2 *plo = bf2 + op.tab, *phi = bf2 + op.dlut;
+            if (tid < 2) {
+                float2 kb = make_float2(1.f, 0.f);
+                const float2 *rec = bf2 + op.mat;
+                for (uint32_t c = 0; c < op.ncst; ++c) {
+                    const uint32_t src = __float_as_uint(rec[5 * c].x);
+                    const uint32_t bit = uint32_t(src < 64 ? (base >> src) & 1ull : (gb >> (src - 64)) & 1ull);
+                    const float2 d = rec[5 * c + 1 + 2 * tid + bit];
+                    kb = make_float2(kb.x * d.x - kb.y * d.y, kb.x * d.y + kb.y * d.x);
+                }
+                S.ck[tid] = kb;
+                if (tid == 0) {
+                    const uint32_t src = op.cctl & ~kCtlConst;
+                    S.cbconst = (op.cctl & kCtlConst)
+                                    ? uint32_t(src < 64 ? (base >> src) & 1ull : (gb >> (src - 64)) & 1ull)
+                                    : 0u;
+                }
+            }
+            __syncthreads();
+            for (uint32_t x = tid; x < 128; x += NT) {
+                const uint32_t b = x >> 6;
+                const float2 h = phi[x], kb = S.ck[b];
+                S.csq[b][x & 63u] = make_float2(h.x * kb.x - h.y * kb.y, h.x * kb.y + h.y * kb.x);
+            }
+            __syncthreads();
+            const bool ctile = !(op.cctl & kCtlConst);
+            const uint32_t ct = op.cctl & 31u, bconst = S.cbconst;
+            if (T == 12) {
+                const uint32_t tq = swz_thread<NT>(tid), lo = uint32_t(tid) & 127u, hib = uint32_t(tid) >> 7;
+                const float2 pl0 = plo[lo], pl1 = plo[128 + lo];
+#pragma unroll
+                for (uint32_t u = 0; u < 4096u / NT; ++u) {
+                    const uint32_t i = uint32_t(tid) + NT * u, hi = hib + (NT / 128) * u;
+                    const uint32_t b = ctile ? (i >> ct) & 1u : bconst;
+                    const float2 q = S.csq[b][hi], pl = b ? pl1 : pl0;
+                    const float2 ph = make_float2(pl.x * q.x - pl.y * q.y, pl.x * q.y + pl.y * q.x);
+                    float2 &a = tile[(tq ^ swz_u<NT>(u)) + NT * u];
+                    const float2 v = a;
+                    a = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
+                }
+            } else {
+                for (uint32_t i = tid; i < (1u << T); i += NT) {
+                    const uint32_t b = ctile ? (i >> ct) & 1u : bconst;
+                    const float2 q = S.csq[b][i >> 7], pl = plo[128 * b + (i & 127u)];
+                    const float2 ph = make_float2(pl.x * q.x - pl.y * q.y, pl.x * q.y + pl.y * q.x);
+                    float2 &a = tile[swz(i)];
+                    const float2 v = a;
+                    a = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
                 }
             }
         } else {

@@ -149,6 +149,10 @@ struct Fuser {
     uint32_t ngates = 0;
     int64_t diag_op = -1;          // index of the pending diagonal op in *ops
     std::set<uint32_t> blockers;   // full qubits of the ops placed after it
+    int64_t csep_op = -1;          // index of the pending controlled-separable diagonal op
+    std::set<uint32_t> csep_blockers;
+    uint32_t last2[2] = {0, 0};    // qubits of the last two-qubit diagonal gate seen
+    bool have_last2 = false;
 
     int32_t working_bit(uint32_t q) const {
         if (q < m) return int32_t(q);
@@ -174,7 +178,10 @@ struct Fuser {
             for (uint32_t j = 0; j < op.k; ++j) op.wq[j] = S[j];
             op.u = U;
         }
-        for (uint32_t w : S) blockers.insert(qubit_of(w));
+        for (uint32_t w : S) {
+            blockers.insert(qubit_of(w));
+            csep_blockers.insert(qubit_of(w));
+        }
         ops->push_back(std::move(op));
         active = false;
         S.clear();
@@ -205,6 +212,68 @@ struct Fuser {
         for (uint32_t j = 0; j < K; ++j) d.fq[j] = NQ[j];
         d.u = std::move(nu);
         d.ngates += 1;
+    }
+
+    // a one- or two-qubit diagonal gate g folded into the pending controlled-separable op
+    bool fold_csep(const Gate &g) {
+        Op &c = (*ops)[size_t(csep_op)];
+        const uint32_t ctl = c.csep_q[0];
+        const uint32_t d = 1u << g.nq;
+        auto target_index = [&](uint32_t q) -> int64_t {
+            for (size_t t = 1; t < c.csep_q.size(); ++t)
+                if (c.csep_q[t] == q) return int64_t(t - 1);
+            return -1;
+        };
+        auto add_target = [&](uint32_t q) -> size_t {
+            c.csep_q.push_back(q);
+            for (int v = 0; v < 4; ++v) c.u.push_back(cd(1, 0));
+            return c.csep_q.size() - 2;
+        };
+        const cd *gd = nullptr;
+        std::vector<cd> diag(d);
+        for (uint32_t r = 0; r < d; ++r) diag[r] = g.u[size_t(r) * d + r];
+        gd = diag.data();
+        if (g.nq == 1) {
+            if (g.q[0] == ctl) {
+                c.u[0] *= gd[0];
+                c.u[1] *= gd[1];
+            } else {
+                int64_t t = target_index(g.q[0]);
+                if (t < 0) t = int64_t(add_target(g.q[0]));
+                for (int b = 0; b < 2; ++b)
+                    for (int x = 0; x < 2; ++x) c.u[2 + 4 * size_t(t) + 2 * b + x] *= gd[x];
+            }
+        } else {
+            // matrix bit 0 <-> g.q[0], bit 1 <-> g.q[1]
+            const bool c0 = g.q[0] == ctl;
+            const uint32_t tq = c0 ? g.q[1] : g.q[0];
+            int64_t t = target_index(tq);
+            if (t < 0) t = int64_t(add_target(tq));
+            for (int b = 0; b < 2; ++b)
+                for (int x = 0; x < 2; ++x) {
+                    const uint32_t idx = c0 ? uint32_t(b | (x << 1)) : uint32_t(x | (b << 1));
+                    c.u[2 + 4 * size_t(t) + 2 * b + x] *= gd[idx];
+                }
+        }
+        c.k = uint32_t(c.csep_q.size());
+        c.ngates += 1;
+        return true;
+    }
+
+    bool csep_accepts(const Gate &g) const {
+        if (csep_op < 0 || g.nq > 2) return false;
+        const Op &c = (*ops)[size_t(csep_op)];
+        const uint32_t ctl = c.csep_q[0];
+        for (uint32_t j = 0; j < g.nq; ++j) {
+            if (csep_blockers.count(g.q[j])) return false;
+            const int32_t w = working_bit(g.q[j]);
+            if (active && w >= 0 && std::find(S.begin(), S.end(), uint32_t(w)) != S.end()) return false;
+        }
+        if (g.nq == 2) return g.q[0] == ctl || g.q[1] == ctl;
+        if (g.q[0] == ctl) return true;
+        for (size_t t = 1; t < c.csep_q.size(); ++t)
+            if (c.csep_q[t] == g.q[0]) return true;
+        return false;
     }
 
     // the gate joins the active op if the union of qubits stays <= k
@@ -240,6 +309,22 @@ struct Fuser {
             wb[j] = uint32_t(w);
         }
         if (g.diag) {
+            // two-qubit diagonal gates sharing a qubit with the previous one form a star: fold it into a
+            // controlled-separable op on the shared qubit
+            uint32_t star = 0;
+            bool is_star = false;
+            if (g.nq == 2) {
+                if (have_last2)
+                    for (uint32_t a = 0; a < 2; ++a)
+                        for (uint32_t b = 0; b < 2; ++b)
+                            if (!is_star && g.q[a] == last2[b]) {
+                                star = g.q[a];
+                                is_star = true;
+                            }
+                last2[0] = g.q[0];
+                last2[1] = g.q[1];
+                have_last2 = true;
+            }
             bool touches_active = false, commutes = diag_op >= 0;
             for (uint32_t j = 0; j < g.nq; ++j) {
                 if (all_working && std::find(S.begin(), S.end(), wb[j]) != S.end()) touches_active = true;
@@ -249,6 +334,10 @@ struct Fuser {
                     commutes = false;
             }
             if (all_working && g.nq <= k && touches_active && try_join(g, wb)) return;
+            if (csep_accepts(g)) {
+                fold_csep(g);
+                return;
+            }
             if (commutes) {
                 const Op &d = (*ops)[size_t(diag_op)];
                 std::set<uint32_t> uni(d.fq, d.fq + d.k);
@@ -260,6 +349,19 @@ struct Fuser {
             }
             if (all_working && g.nq <= k && try_join(g, wb)) return;
             flush();
+            if (is_star) {
+                Op op{};
+                op.type = OP_CSEP;
+                op.csep_q.push_back(star);
+                op.u = {cd(1, 0), cd(1, 0)};
+                op.k = 1;
+                op.ngates = 0;
+                ops->push_back(std::move(op));
+                csep_op = int64_t(ops->size()) - 1;
+                csep_blockers.clear();
+                fold_csep(g);
+                return;
+            }
             Op op{};
             op.type = OP_DIAG;
             op.k = g.nq;
@@ -285,13 +387,35 @@ struct Fuser {
 
 constexpr uint32_t kCoalesceBits = 3;
 
+// A controlled-separable op on at most kMaxDiagQubits qubits becomes an ordinary
+// diagonal op (its phase table written out), which the decoder can also apply.
+void narrow_csep_ops(std::vector<Op> &ops) {
+    for (Op &op : ops) {
+        if (op.type != OP_CSEP || op.csep_q.size() > kMaxDiagQubits) continue;
+        const uint32_t K = uint32_t(op.csep_q.size());
+        std::vector<cd> tab(size_t(1) << K);
+        for (uint32_t x = 0; x < (1u << K); ++x) {
+            const uint32_t b = x & 1u;  // matrix bit 0 <-> the control
+            cd ph = op.u[b];
+            for (uint32_t t = 1; t < K; ++t) ph *= op.u[2 + 4 * size_t(t - 1) + 2 * b + ((x >> t) & 1u)];
+            tab[x] = ph;
+        }
+        op.type = OP_DIAG;
+        op.k = K;
+        for (uint32_t j = 0; j < K; ++j) op.fq[j] = op.csep_q[j];
+        op.u = std::move(tab);
+        op.csep_q.clear();
+    }
+}
+
 void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
     const uint32_t W = st.W;
     st.pre_ops.clear();
     uint32_t first = 0;
     if (fold_leading_diag) {
         // leading phase ops need no tile: the decoder applies them per element
-        while (first < st.ops.size() && st.ops[first].type != OP_DENSE && st.pre_ops.size() < kMaxPreOps)
+        while (first < st.ops.size() && (st.ops[first].type == OP_DIAG || st.ops[first].type == OP_PHASEFLIP) &&
+               st.pre_ops.size() < kMaxPreOps)
             st.pre_ops.push_back(first++);
     }
     uint32_t T = std::min(tile_bits, W);
@@ -315,6 +439,7 @@ void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
     std::vector<uint32_t> cur;
     // shared-memory bytes of the pass's op data (descriptor, and for a diagonal op its tables)
     auto op_bytes = [&](const Op &op) -> size_t {
+        if (op.type == OP_CSEP) return kOpDescBytes + kCsepTableBytes + 48 * size_t(op.k);
         return kOpDescBytes + (op.type == OP_DIAG ? 192 + 16 + (size_t(8) << op.k) : 0);
     };
     size_t bytes = 0;
@@ -434,6 +559,7 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
         fz.ops = &st.ops;
         for (size_t i = st.first_gate; i < st.first_gate + st.ngates; ++i) fz.add(p->gates[i]);
         fz.flush();
+        narrow_csep_ops(st.ops);
         layout_passes(st, std::max<uint32_t>(tile_bits, std::min<uint32_t>(st.W, 5 + cfg->k)),
                       cfg->codec == QSIM_CODEC_QSZ1);
     }
@@ -444,7 +570,7 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
     for (const Stage &st : p->stages) {
         for (const Op &op : st.ops) {
             if (op.type == OP_DENSE) ++s.dense_ops;
-            else if (op.type == OP_DIAG) ++s.diag_ops;
+            else if (op.type == OP_DIAG || op.type == OP_CSEP) ++s.diag_ops;
             else ++s.phaseflip_ops;
         }
         s.passes += st.passes.size();

@@ -45,7 +45,7 @@ bool qsz_step_exponent(double eb, int *e);
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------
-enum OpType : uint32_t { OP_DENSE = 0, OP_DIAG = 1, OP_PHASEFLIP = 2 };
+enum OpType : uint32_t { OP_DENSE = 0, OP_DIAG = 1, OP_PHASEFLIP = 2, OP_CSEP = 3 };
 
 struct Op {
     OpType type;
@@ -53,8 +53,11 @@ struct Op {
     uint32_t wq[6];         // dense: working-index bit of matrix bit j
     uint32_t fq[8];         // diag: full qubit ids (matrix bit j)
     uint64_t basis;         // phaseflip
-    std::vector<cd> u;      // dense: 2^k x 2^k row-major; diag: 2^k phases
+    std::vector<cd> u;      // dense: 2^k x 2^k row-major; diag: 2^k phases; csep: see below
     uint32_t ngates;        // input gates folded into this op
+    // csep (controlled-separable diagonal): phase(x) = K[b] * prod_t D_t[b][x_t] with b = x_c;
+    // csep_q = {c, t_1, t_2, ...} (full qubits), u = {K[0], K[1], then per target D[0][0], D[0][1], D[1][0], D[1][1]}
+    std::vector<uint32_t> csep_q;
 };
 
 struct Pass {
@@ -76,6 +79,7 @@ constexpr uint32_t kMaxPreOps = 8;
 constexpr uint32_t kMaxDiagQubits = 8;  // widest fused diagonal op (phase index fits a byte)
 constexpr size_t kOpDescBytes = 208;    // device descriptor of an op in a pass
 constexpr size_t kPassOpBytes = 32768;  // op data of one pass held in shared memory next to its tile
+constexpr size_t kCsepTableBytes = 3072; // controlled-separable op: tile-bit tables P_lo[2][128], P_hi[2][64]
 
 struct Gate {
     uint32_t nq = 0;

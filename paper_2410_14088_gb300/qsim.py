@@ -60,7 +60,7 @@ class PlanStats(ctypes.Structure):
 class OpInfo(ctypes.Structure):
     _fields_ = [("type", ctypes.c_uint32), ("nq", ctypes.c_uint32), ("qubits", ctypes.c_uint32 * 8),
                 ("ngates", ctypes.c_uint32), ("pass_", ctypes.c_uint32), ("basis", ctypes.c_uint64),
-                ("u", ctypes.POINTER(ctypes.c_double))]
+                ("u", ctypes.POINTER(ctypes.c_double)), ("qlist", ctypes.POINTER(ctypes.c_uint32))]
 
 
 class Stats(ctypes.Structure):
@@ -274,6 +274,9 @@ class Plan:
             elif o.type == 1:
                 D = 1 << o.nq
                 d["u"] = np.ctypeslib.as_array(o.u, shape=(2 * D,)).copy().view(np.complex128)
+            elif o.type == 3:
+                d["qubits"] = tuple(int(x) for x in np.ctypeslib.as_array(o.qlist, shape=(o.nq,)))
+                d["u"] = np.ctypeslib.as_array(o.u, shape=(2 * (2 + 4 * (o.nq - 1)),)).copy().view(np.complex128)
             ops.append(d)
         return ops
 

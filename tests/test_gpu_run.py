@@ -107,6 +107,24 @@ def test_qft_basis_closed_form():
     assert np.max(np.abs(got - want)) <= 2 * st.nstages * 1e-3 * 2 ** (-n / 2) + 1e-5
 
 
+@pytest.mark.parametrize("prec", [qsim.PREC_FP32, qsim.PREC_TF32], ids=["fp32", "tf32"])
+@pytest.mark.parametrize("mode", [qsim.MODE_STREAMS, qsim.MODE_PERSISTENT], ids=["streams", "persistent"])
+def test_qft_separable_phase_ops(prec, mode):
+    # a 20-qubit QFT folds its far controlled phases into controlled-separable ops (targets inside and
+    # outside the tiles, control inside and outside); uncompressed result against the FP64 closed form
+    n, x = 20, 0x5A5A5
+    c = inputs.Circuit(n, inputs.qft_gates(n), x)
+    p = qsim.plan_stages(c, m=14, inner=4, k=5, codec=qsim.CODEC_NONE, prec=prec, mode=qsim.MODE_STREAMS)
+    assert any(o["type"] == 3 for s in range(p.nstages) for o in p.stage_ops(s))
+    if mode == qsim.MODE_PERSISTENT:  # the compressed store (persistent mode runs QSZ1)
+        st = qsim.run(qsim.plan_stages(c, m=14, inner=4, k=5, eps=1e-4, prec=prec, mode=mode))
+        assert st.fidelity(cf.qft_basis_state(n, x)) >= 0.999
+        return
+    got = state_c64(qsim.run(p))
+    tol = 1e-5 if prec == qsim.PREC_FP32 else 1e-2 * 2 ** (-n / 2)  # TF32: 1 % of the amplitude scale
+    assert np.max(np.abs(got - cf.qft_basis_state(n, x))) <= tol
+
+
 def test_grover_closed_form():
     n, t, marked = 16, 4, 4321
     st = qsim.run(qsim.plan_stages(inputs.grover(n, t, marked), m=10, inner=2, k=4, eps=1e-3))

@@ -29,6 +29,19 @@ def test_partition_matches_oracle(circ, m, inner, k, dx):
 
 
 def apply_op(psi, n, op):
+    if op["type"] == 3:
+        # controlled-separable diagonal: phase(x) = K[b] prod_t D_t[b][x_t], b = bit of the control qubit
+        q = op["qubits"]
+        u = op["u"]
+        x = np.arange(1 << n, dtype=np.int64)
+        b = (x >> q[0]) & 1
+        ph = np.where(b == 1, u[1], u[0])
+        for t, qt in enumerate(q[1:]):
+            xt = (x >> qt) & 1
+            ph = ph * u[2 + 4 * t + 2 * b + xt]
+        v = psi.view(np.complex128)
+        v *= ph
+        return
     if op["type"] == 2:
         oracle.lib().oracle_apply_phaseflip(oracle._ptr(psi, oracle.ctypes.c_double), n, op["basis"])
         return
