@@ -325,6 +325,8 @@ __device__ __forceinline__ void pass_setup(const PassDev &pd, PassSmem &S) {
     __syncthreads();
 }
 
+constexpr uint32_t kCgBatch = 16;
+
 // Fast tile addressing for T = 12: element i = tid + NT u sits at working
 // offset tpart[tid] + off12[u] and at shared index (tid ^ xt) ^ xu(u) + NT u,
 // the XOR swizzle split into a per-thread and a per-u part.
@@ -367,13 +369,14 @@ __device__ __forceinline__ void tile_load(const float2 *__restrict__ g, uint64_t
         const float2 *gt = g + (base | uint64_t(S.tpart[tid]));
         const uint32_t tq = swz_thread<NT>(tid);
         if constexpr (CG) {
+            constexpr uint32_t B = kCgBatch;  // L2 loads in flight per thread
 #pragma unroll
-            for (uint32_t u0 = 0; u0 < 4096u / NT; u0 += 8) {
-                float2 v[8];
+            for (uint32_t u0 = 0; u0 < 4096u / NT; u0 += B) {
+                float2 v[B];
 #pragma unroll
-                for (uint32_t u = 0; u < 8; ++u) v[u] = __ldcg(gt + S.off12[u0 + u]);
+                for (uint32_t u = 0; u < B; ++u) v[u] = __ldcg(gt + S.off12[u0 + u]);
 #pragma unroll
-                for (uint32_t u = 0; u < 8; ++u) tile[(tq ^ swz_u<NT>(u0 + u)) + NT * (u0 + u)] = v[u];
+                for (uint32_t u = 0; u < B; ++u) tile[(tq ^ swz_u<NT>(u0 + u)) + NT * (u0 + u)] = v[u];
             }
         } else {
 #pragma unroll
