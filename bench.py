@@ -106,6 +106,22 @@ def workload(args, seed=None, n=None):
     return inputs.qft_rz_cx(n, 4, seed)
 
 
+def max_over_ranks(x, dist, device="cuda"):
+    """The largest of the ranks' values (every rank gets it); x itself without a process group."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world, steps, units_per_step, max_ms):
+    """Whole-job throughput: every rank runs `steps` steps of `units_per_step` units (weak scaling), timed by the
+    slowest rank."""
+    return world * steps * units_per_step / (max_ms * 1e-3)
+
+
 def load_peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -367,12 +383,8 @@ def run_ours(args, rank, world, dist):
     qsim.profile_enable(False)
     launches = qsim.launch_count() - launches0
     t_ms = ev0.elapsed_time(ev1)
-    t_max = t_ms
-    if dist is not None:
-        t = torch.tensor([t_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    ups = world * args.steps * (1 << n) * G / (t_max * 1e-3)
+    t_max = max_over_ranks(t_ms, dist)
+    ups = job_rate(world, args.steps, (1 << n) * G, t_max)
 
     # ---- timed: e2e through the public API from host data ----
     idx = np.arange(0, 1 << n, (1 << n) // 4096, dtype=np.uint64)[:4096]
@@ -390,12 +402,8 @@ def run_ours(args, rank, world, dist):
         del st, p2
     e1.record(stream)
     barrier()
-    te_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([te_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te_ms = float(t.item())
-    e2e = world * args.steps * (1 << n) * G / (te_ms * 1e-3) if not args.no_e2e else None
+    te_ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    e2e = job_rate(world, args.steps, (1 << n) * G, te_ms) if not args.no_e2e else None
 
     if rank != 0:
         return
@@ -553,12 +561,8 @@ def run_batch_bench(args, rank, world, dist):
     clocks = sampler.stop()
     qsim.profile_enable(False)
     launches = qsim.launch_count() - launches0
-    t_max = ev0.elapsed_time(ev1)
-    if dist is not None:
-        t = torch.tensor([t_max], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    ups = world * args.steps * updates / (t_max * 1e-3)
+    t_max = max_over_ranks(ev0.elapsed_time(ev1), dist)
+    ups = job_rate(world, args.steps, updates, t_max)
 
     # e2e: plans from the host gate lists, the batch, 64 sampled amplitudes of every circuit read back
     barrier()
@@ -577,12 +581,8 @@ def run_batch_bench(args, rank, world, dist):
         del sts, ps
     e1.record(stream)
     barrier()
-    te_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([te_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        te_ms = float(t.item())
-    e2e = world * args.steps * updates / (te_ms * 1e-3)
+    te_ms = max_over_ranks(e0.elapsed_time(e1), dist)
+    e2e = job_rate(world, args.steps, updates, te_ms)
     if rank != 0:
         return
     peaks, peaks_kind = load_peaks()
