@@ -30,6 +30,8 @@
 #include <mutex>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "codec.cuh"
 #include "device_common.cuh"
 #include "gates.cuh"
@@ -118,6 +120,19 @@ struct Profiler {
             return set_error(_e == cudaErrorMemoryAllocation ? QSIM_E_NOMEM : QSIM_E_CUDA,  \
                              "%s: %s (%s:%d)", #expr, cudaGetErrorString(_e), __FILE__, __LINE__); \
     } while (0)
+
+// NVTX range for timeline tools (a no-op when none is attached)
+struct NvtxRange {
+    explicit NvtxRange(const char *fmt, ...) {
+        char buf[96];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        nvtxRangePushA(buf);
+    }
+    ~NvtxRange() { nvtxRangePop(); }
+};
 
 // ---------------------------------------------------------------------------
 // caching allocator (device and pinned host), exact-size reuse
@@ -1289,6 +1304,8 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
     };
     const size_t nlaunch = one_launch ? 1 : nseg;
     for (size_t l = 0; l < nlaunch; ++l) {
+        NvtxRange launch_range(one_launch ? "persistent launch: %zu segments" : "persistent stage %zu",
+                               one_launch ? nseg : l);
         const size_t k0 = one_launch ? 0 : l, k1 = one_launch ? nseg : l + 1;
         L.segs = dsegs.p + k0;
         L.nseg = uint32_t(k1 - k0);
@@ -1435,6 +1452,7 @@ static int finish_run(RunCtx &R, int dev, double ms, Profiler *prof, qsim_stats 
 }
 
 static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsim_stats *stats) {
+    NvtxRange run_range("qsim_run n=%u", p->n);
     const qsim_config &cfg = p->cfg;
     int dev;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -1541,6 +1559,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
         }
     }
     for (size_t si = 0; si < (persistent ? 0 : nst); ++si) {
+        NvtxRange stage_range("stage %zu", si);
         const StageDev &sd = pd->stages[si];
         const int in_par = si & 1, out_par = (si + 1) & 1;
         BlockSlot *tab_in = tables_p + in_par * nblocks;
@@ -1573,6 +1592,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             sf.v[7] = st.ngates ? float(nondiag) / float(st.ngates) : 0.f;
         }
         for (uint64_t b = 0; b < nbatches; ++b) {
+            NvtxRange group_range("groups %llu..", (unsigned long long)(b * gpb));
             StreamWork &w = sw[b % nstreams];
             const uint64_t g0 = b * gpb;
             const uint32_t ng = uint32_t(std::min<uint64_t>(gpb, sd.ngroups - g0));
@@ -1676,6 +1696,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
 // stage of every circuit.
 static int run_batch(const qsim_plan *const *plans, size_t count, cudaStream_t main, qsim_state **out,
                      qsim_stats *stats, qsim_kernel_stat *launch_stat) {
+    NvtxRange batch_range("qsim_run_batch %zu circuits", count);
     int dev;
     CUDA_TRY(cudaGetDevice(&dev));
     DeviceCtx &dctx = device_ctx(dev);
