@@ -142,10 +142,10 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
 // the frame offset comes from a warp look-back (epoch-tagged status words). The
 // last CTA folds the frame partials, resets the ticket and advances the epoch.
 __global__ void __launch_bounds__(NT, 4) k_encode_lbw(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
-                                                   const EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
+                                                   EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
                                                    int only_overflowed, const uint32_t *__restrict__ ids,
                                                    BlockSlot *__restrict__ table, StageAccum *acc,
-                                                   LookbackScratch scr, int *status) {
+                                                   LookbackScratch scr, ArenaDev dev, ArenaDev host, int *status) {
     // a re-encode with nothing to redo leaves the ticket, the counters and the epoch alone
     if (only_overflowed && scr.pending && ld_relaxed_u32(scr.pending) == 0) return;
     const FrameGeom g = geom(m);
@@ -208,6 +208,16 @@ __global__ void __launch_bounds__(NT, 4) k_encode_lbw(const float2 *__restrict__
             atomicAdd(&acc->err_sq, a);
             atomicAdd(&acc->norm_sq, b);
         }
+    }
+    if (!only_overflowed && dev.bump) {
+        // blocks whose predicted slot was too small get an exact one now (res.total holds their exact size)
+        for (uint32_t jb = tid; jb < nblocks; jb += NT)
+            if (__ldcg(&res[jb].overflow)) {
+                if (scr.pending) atomicAdd(scr.pending, 1u);
+                reserve_slot(__ldcg(reinterpret_cast<const unsigned long long *>(&res[jb].total)), dev, host,
+                             &tgt[jb], status);
+            }
+        __syncthreads();
     }
     if (tid == 0) {
         *scr.ticket = 0;
@@ -483,12 +493,15 @@ void launch_size_reserve(const float2 *wv, uint32_t nblocks, int m, int e, uint6
     count_launch();
 }
 
-void launch_encode_lbw(const float2 *wv, uint32_t nblocks, int m, int e, const EncTarget *tgt, EncResult *res,
+void launch_encode_lbw(const float2 *wv, uint32_t nblocks, int m, int e, EncTarget *tgt, EncResult *res,
                        int only_overflowed, const uint32_t *ids, BlockSlot *table, StageAccum *acc,
-                       const LookbackScratch &scr, int *status, cudaStream_t s) {
+                       const LookbackScratch &scr, const ArenaDev *fix_dev, const ArenaDev *fix_host, int *status,
+                       cudaStream_t s) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
+    ArenaDev none{};
     k_encode_lbw<<<unsigned((items + NW - 1) / NW), NT, 0, s>>>(wv, nblocks, m, e, tgt, res, only_overflowed, ids,
-                                                                table, acc, scr, status);
+                                                                table, acc, scr, fix_dev ? *fix_dev : none,
+                                                                fix_host ? *fix_host : none, status);
     count_launch();
 }
 

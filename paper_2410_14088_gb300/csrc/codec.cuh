@@ -82,10 +82,12 @@ void launch_size_reserve(const float2 *wv, uint32_t nblocks, int m, int e, uint6
                          const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, int *status,
                          cudaStream_t s, uint8_t *wrec = nullptr, uint32_t *flen = nullptr, uint32_t *foff = nullptr);
 // learned-sizing encoder (warp per frame, ticket order, warp look-back); only_overflowed: re-encode the blocks
-// whose first pass overflowed its reserved slot
-void launch_encode_lbw(const float2 *wv, uint32_t nblocks, int m, int e, const EncTarget *tgt, EncResult *res,
+// whose first pass overflowed its reserved slot. With fix_dev/fix_host the first pass's last CTA reserves exact
+// slots for those blocks (counted in scr.pending).
+void launch_encode_lbw(const float2 *wv, uint32_t nblocks, int m, int e, EncTarget *tgt, EncResult *res,
                        int only_overflowed, const uint32_t *ids, BlockSlot *table, StageAccum *acc,
-                       const LookbackScratch &scr, int *status, cudaStream_t s);
+                       const LookbackScratch &scr, const ArenaDev *fix_dev, const ArenaDev *fix_host, int *status,
+                       cudaStream_t s);
 // exact-sizing encoder (warp per frame) using the records of launch_size_reserve
 void launch_encode_known(const float2 *wv, uint32_t nblocks, int m, int e, const EncTarget *tgt, EncResult *res,
                          const uint32_t *ids, BlockSlot *table, StageAccum *acc, const uint8_t *wrec,

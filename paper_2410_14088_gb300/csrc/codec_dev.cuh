@@ -235,11 +235,9 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
             float2 v = make_float2(float(sr) * step, float(si) * step);
             if (npre) v = pre_chunk(v, pre_cl, pre_ops, npre, c, wbase | (uint64_t(f) * g.F + c * 32 + lane), gb, mats);
             dst[c * 32 + lane] = v;
-            if (hist_j) {
-                const uint32_t br = 32 - __clz(sr < 0 ? uint32_t(-sr) : uint32_t(sr));
-                const uint32_t bi = 32 - __clz(si < 0 ? uint32_t(-si) : uint32_t(si));
-                atomicAdd(&s_hist_w[br & 31], 1u);
-                atomicAdd(&s_hist_w[bi & 31], 1u);
+            if (hist_j && lane == 0) {  // the chunk's code widths, 32 values each
+                atomicAdd(&s_hist_w[min(wr[t], 31u)], 32u);
+                atomicAdd(&s_hist_w[min(wi[t], 31u)], 32u);
             }
         }
     }

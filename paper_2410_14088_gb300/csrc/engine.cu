@@ -1648,14 +1648,13 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
                                    arena_host(out_par), w.tgt.p, w.res.p, 0, status, w.s, scr.pending);
                     prof.end(w.s);
                     prof.begin(P_ENCODE, w.s);
-                    launch_encode_lbw(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, status, w.s);
-                    prof.end(w.s);
-                    prof.begin(P_RESERVE, w.s);
-                    launch_reserve(nb, nullptr, 0, nullptr, 0, worst, arena_dev(out_par), arena_host(out_par),
-                                   w.tgt.p, w.res.p, 1, status, w.s, scr.pending);
+                    const ArenaDev fd = arena_dev(out_par), fh = arena_host(out_par);
+                    launch_encode_lbw(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, &fd, &fh, status,
+                                      w.s);
                     prof.end(w.s);
                     prof.begin(P_REENCODE, w.s);
-                    launch_encode_lbw(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 1, ids, tab_out, acc, scr, status, w.s);
+                    launch_encode_lbw(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 1, ids, tab_out, acc, scr, nullptr, nullptr,
+                                      status, w.s);
                     prof.end(w.s);
                 } else {
                     prof.begin(P_ENCODE_SIZE, w.s);

@@ -51,19 +51,54 @@ __global__ void k_mlp_forward(const float *__restrict__ params, const float *__r
 // Features of each block of a batch from the decoder's bit-length histogram,
 // then the prediction; optionally the features are also written out (for
 // the training log, completed by the target once the exact size is known).
-__global__ void k_predict_sizes(const uint32_t *__restrict__ hist, uint32_t nblocks, uint32_t G, int m,
-                                StageFeatures sf, const float *__restrict__ params, int bf16,
-                                float *__restrict__ pred, float *__restrict__ feat_out) {
+// One warp per block: the features (the SV group's width histogram, the largest
+// populated bin, the stage features), then the forward pass with the hidden
+// units spread over the lanes (two per lane per layer).
+__global__ void __launch_bounds__(128) k_predict_sizes(const uint32_t *__restrict__ hist, uint32_t nblocks,
+                                                       uint32_t G, int m, StageFeatures sf,
+                                                       const float *__restrict__ params, int bf16,
+                                                       float *__restrict__ pred, float *__restrict__ feat_out) {
     __shared__ float w[NP];
+    __shared__ float xs[4][IN + 1];
+    __shared__ float hs[4][HID];
     if (params) load_weights(w, params, bf16 != 0);
     __syncthreads();
-    // a stage mixes the G blocks of an SV group, so the histogram is the group's
-    for (uint32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < nblocks; j += gridDim.x * blockDim.x) {
-        float x[IN];
-        mlp_features(hist, j, G, m, sf, x);
+    const int lane = threadIdx.x & 31, wi = threadIdx.x >> 5;
+    const float inv = 1.0f / (float(G) * float(2ull << m));
+    for (uint32_t j = blockIdx.x * 4 + wi; j < nblocks; j += gridDim.x * 4) {
+        // a stage mixes the G blocks of an SV group, so the histogram is the group's
+        const uint64_t g0 = uint64_t(j / G) * G;
+        uint32_t c = 0;
+        for (uint32_t jj = 0; jj < G; ++jj) c += __ldcg(hist + (g0 + jj) * 32 + lane);
+        const uint32_t nz = __ballot_sync(0xffffffffu, c != 0);
+        xs[wi][lane] = float(c) * inv;
+        if (lane == 0) xs[wi][32] = float(nz ? 31 - __clz(nz) : 0) / 32.f;
+        if (lane < 8) xs[wi][33 + lane] = sf.v[lane];
+        __syncwarp();
         if (feat_out)
-            for (int t = 0; t < IN; ++t) feat_out[uint64_t(j) * (IN + 1) + t] = x[t];
-        if (params && pred) pred[j] = mlp_forward_one(w, x) + float(m + 3);
+            for (int t = lane; t < IN; t += 32) feat_out[uint64_t(j) * (IN + 1) + t] = xs[wi][t];
+        if (params && pred) {
+            float a0 = w[OB1 + lane], a1 = w[OB1 + lane + 32];
+            for (int t = 0; t < IN; ++t) {
+                const float x = xs[wi][t];
+                a0 = fmaf(w[OW1 + lane * IN + t], x, a0);
+                a1 = fmaf(w[OW1 + (lane + 32) * IN + t], x, a1);
+            }
+            hs[wi][lane] = fmaxf(a0, 0.f);
+            hs[wi][lane + 32] = fmaxf(a1, 0.f);
+            __syncwarp();
+            float b0 = w[OB2 + lane], b1 = w[OB2 + lane + 32];
+            for (int t = 0; t < HID; ++t) {
+                const float h = hs[wi][t];
+                b0 = fmaf(w[OW2 + lane * HID + t], h, b0);
+                b1 = fmaf(w[OW2 + (lane + 32) * HID + t], h, b1);
+            }
+            float y = w[OW3 + lane] * fmaxf(b0, 0.f) + w[OW3 + lane + 32] * fmaxf(b1, 0.f);
+#pragma unroll
+            for (int o = 16; o; o >>= 1) y += __shfl_xor_sync(0xffffffffu, y, o);
+            if (lane == 0) pred[j] = y + w[OB3] + float(m + 3);
+        }
+        __syncwarp();
     }
 }
 
@@ -210,7 +245,7 @@ void launch_mlp_forward(const float *params, const float *x, uint32_t batch, flo
 
 void launch_predict_sizes(const uint32_t *hist, uint32_t nblocks, uint32_t G, int m, const StageFeatures &sf,
                           const float *params, int bf16, float *pred, float *feat_out, cudaStream_t s) {
-    const unsigned grid = (nblocks + 127) / 128;
+    const unsigned grid = (nblocks + 3) / 4;
     k_predict_sizes<<<grid ? grid : 1, 128, 0, s>>>(hist, nblocks, G, m, sf, params, bf16, pred, feat_out);
     count_launch();
 }

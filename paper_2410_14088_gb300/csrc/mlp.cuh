@@ -38,8 +38,9 @@ __device__ __forceinline__ float mlp_forward_one(const float *w, const float *x)
     return y;
 }
 
-// the 41 inputs of block j of a batch: its SV group's bit-length histogram (G blocks of 2^(m+1) values each,
-// hist read through L2), the largest populated bin / 32 and the stage features
+// the 41 inputs of block j of a batch: its SV group's code-width histogram (each 32-value chunk of the decoded
+// input counts 32 in the bin of its width; G blocks of 2^(m+1) values each, hist read through L2), the largest
+// populated bin / 32 and the stage features
 __device__ __forceinline__ void mlp_features(const uint32_t *hist, uint32_t j, uint32_t G, int m,
                                              const StageFeatures &sf, float *x) {
     const float inv = 1.0f / (float(G) * float(2ull << m));
