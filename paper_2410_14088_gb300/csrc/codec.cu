@@ -32,14 +32,20 @@ namespace {
 
 using namespace cdev;
 
-__global__ void __launch_bounds__(NT, 4) k_decode(const BlockRef *__restrict__ in, const BlockSlot *__restrict__ table,
+// NP: the most leading phase ops the kernel applies (pre.count <= NP).
+template <int NP>
+__global__ void __launch_bounds__(NT, 3) k_decode(const BlockRef *__restrict__ in, const BlockSlot *__restrict__ table,
                                                const uint32_t *__restrict__ ids, uint32_t nblocks, int m,
                                                float2 *__restrict__ wv, uint32_t *__restrict__ hist,
                                                int *status, PreOps pre) {
     const FrameGeom g = geom(m);
-    __shared__ OpDev s_pre[kMaxPreOps];
+    __shared__ OpDev s_pre[NP > 0 ? NP : 1];
+    __shared__ uint2 s_pre_ab[NP > 0 ? NP : 1];
     __shared__ uint32_t s_hist[NW][32];
-    if (threadIdx.x < pre.count) s_pre[threadIdx.x] = pre.ops[threadIdx.x];
+    if (NP > 0 && threadIdx.x < pre.count) {
+        s_pre[threadIdx.x] = pre.ops[threadIdx.x];
+        s_pre_ab[threadIdx.x] = pre_setup(pre.ops[threadIdx.x]);
+    }
     __syncthreads();
     const int warp = threadIdx.x >> 5;
     const uint64_t items = uint64_t(nblocks) * g.nframes;
@@ -55,9 +61,10 @@ __global__ void __launch_bounds__(NT, 4) k_decode(const BlockRef *__restrict__ i
             sp = in[j].ptr;
             bytes = in[j].bytes;
         }
-        decode_frame_warp(sp, bytes, g, m, f, wv + (uint64_t(j) << m) + uint64_t(f) * g.F,
-                          hist ? hist + uint64_t(j) * 32 : nullptr, s_hist[warp], status, s_pre, pre.count, pre.mats,
-                          pre.count ? (uint64_t(j % pre.G) << m) : 0, pre.count ? pre.gbase[j / pre.G] : 0);
+        decode_frame_warp<NP>(sp, bytes, g, m, f, wv + (uint64_t(j) << m) + uint64_t(f) * g.F,
+                              hist ? hist + uint64_t(j) * 32 : nullptr, s_hist[warp], status, s_pre, s_pre_ab,
+                              pre.count, pre.mats, pre.count ? (uint64_t(j % pre.G) << m) : 0,
+                              pre.count ? pre.gbase[j / pre.G] : 0);
     }
 }
 
@@ -227,7 +234,7 @@ __global__ void __launch_bounds__(NT, 4) k_encode_lbw(const float2 *__restrict__
     }
 }
 
-__global__ void __launch_bounds__(NT, 4) k_encode_size(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
+__global__ void __launch_bounds__(NT, 3) k_encode_size(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
                                                     uint64_t *__restrict__ sizes, uint32_t *done_ctr,
                                                     ArenaDev dev, ArenaDev host, EncTarget *__restrict__ tgt,
                                                     EncResult *__restrict__ res, int *status, uint8_t *__restrict__ wrec,
@@ -296,7 +303,7 @@ __global__ void __launch_bounds__(NT, 4) k_encode_size(const float2 *__restrict_
 // Exact-sizing encoder: one warp per frame, widths and frame offsets from the
 // sizing pass; the last CTA folds the frames' error partials into the blocks'
 // and the stage's totals.
-__global__ void __launch_bounds__(NT, 4) k_encode_known(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
+__global__ void __launch_bounds__(NT, 3) k_encode_known(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
                                                      const EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
                                                      const uint32_t *__restrict__ ids, BlockSlot *__restrict__ table,
                                                      StageAccum *acc, const uint8_t *__restrict__ wrec,
@@ -453,16 +460,21 @@ static unsigned grid_for(uint64_t items, unsigned cap) {
 void launch_decode(const BlockRef *in, uint32_t nblocks, int m, float2 *wv, uint32_t *hist, int *status,
                    cudaStream_t s) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
-    k_decode<<<grid_for((items + NW - 1) / NW, 152 * 8), NT, 0, s>>>(in, nullptr, nullptr, nblocks, m, wv, hist, status,
-                                                                   PreOps{});
+    k_decode<0><<<grid_for((items + NW - 1) / NW, 152 * 8), NT, 0, s>>>(in, nullptr, nullptr, nblocks, m, wv, hist,
+                                                                      status, PreOps{});
     count_launch();
 }
 
 void launch_decode_table(const BlockSlot *table, const uint32_t *ids, uint32_t nblocks, int m, float2 *wv,
                          uint32_t *hist, int *status, const PreOps &pre, cudaStream_t s) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
-    k_decode<<<grid_for((items + NW - 1) / NW, 152 * 8), NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist,
-                                                                   status, pre);
+    const unsigned grid = grid_for((items + NW - 1) / NW, 152 * 8);
+    if (pre.count == 0)
+        k_decode<0><<<grid, NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist, status, pre);
+    else if (pre.count <= 2)
+        k_decode<2><<<grid, NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist, status, pre);
+    else
+        k_decode<kMaxPreOps><<<grid, NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist, status, pre);
     count_launch();
 }
 

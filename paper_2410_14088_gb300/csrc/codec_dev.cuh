@@ -57,38 +57,60 @@ __device__ __forceinline__ int32_t unzigzag(uint32_t z) {
 // diagonal op splits into bits fixed for the frame (working bits >= the frame
 // log, and outer qubits from the group), the lane's bits 0..4 and the chunk's
 // bits 5.. ; the host builds the lane and chunk parts as byte tables (32 + 128
-// bytes at float2 offset op.dlut of the phase area). pre_frame returns, per op,
-// the frame and lane parts; pre_chunk applies the ops to one chunk's amplitude.
-__device__ __forceinline__ void pre_frame(uint32_t (&cl)[kMaxPreOps], const OpDev *ops, uint32_t nops, uint64_t w0f,
-                                          uint32_t fl, uint32_t lane, uint64_t gb, const float2 *__restrict__ mats) {
+// bytes at float2 offset op.dlut of the phase area). pre_setup gives each op
+// its launch-wide table offsets (shared memory), pre_frame its per-lane
+// register for the frame, and pre_chunk applies the ops to one chunk's
+// amplitude.
+constexpr uint32_t kPreFlip = 0xFFFFFFFFu;  // pre_ab[o].y of a phase flip
+constexpr uint32_t kPreNone = 0xFFFFFFFFu;  // register of a flip whose amplitude is not in this lane
+
+// ab.x: byte offset of a diagonal op's chunk table in the phase area; ab.y: float2 offset of its phase
+// table, or kPreFlip for a phase flip.
+__device__ __forceinline__ uint2 pre_setup(const OpDev &op) {
+    return op.type == OP_DIAG ? make_uint2(uint32_t(op.dlut) * 8u + 32u, uint32_t(op.mat)) : make_uint2(0u, kPreFlip);
+}
+
+// Per-lane register of each op for the frame whose first working index is w0f: a diagonal op's frame
+// and lane bits of the phase index; for a phase flip, the chunk of the marked amplitude in the lane that
+// holds it (kPreNone elsewhere).
+template <int NP>
+__device__ __forceinline__ void pre_frame(uint32_t (&cl)[NP > 0 ? NP : 1], const OpDev *ops, uint32_t nops,
+                                          uint64_t w0f, uint32_t fl, uint32_t lane, uint64_t gb,
+                                          const float2 *__restrict__ mats) {
 #pragma unroll
-    for (uint32_t o = 0; o < kMaxPreOps; ++o) {
-        cl[o] = 0;
-        if (o >= nops || ops[o].type != OP_DIAG) continue;
+    for (int o = 0; o < NP; ++o) {
+        cl[o] = kPreNone;
+        if (uint32_t(o) >= nops) continue;
         const OpDev &op = ops[o];
-        uint32_t idx = 0;
-        for (uint32_t j = 0; j < op.k; ++j) {
-            const uint32_t src = op.dsrc[j];
-            if (src < fl) continue;
-            const uint64_t bit = src < 64 ? (w0f >> src) & 1ull : (gb >> (src - 64)) & 1ull;
-            idx |= uint32_t(bit) << j;
+        if (op.type == OP_DIAG) {
+            uint32_t idx = 0;
+            for (uint32_t j = 0; j < op.k; ++j) {
+                const uint32_t src = op.dsrc[j];
+                if (src < fl) continue;
+                const uint64_t bit = src < 64 ? (w0f >> src) & 1ull : (gb >> (src - 64)) & 1ull;
+                idx |= uint32_t(bit) << j;
+            }
+            cl[o] = idx | __ldg(reinterpret_cast<const uint8_t *>(mats + op.dlut) + lane);
+        } else if (op.basis_in_stage && gb == op.basis_outer && op.basis_w >= w0f &&
+                   op.basis_w - w0f < (uint64_t(1) << fl)) {
+            const uint32_t off = uint32_t(op.basis_w - w0f);
+            if ((off & 31u) == lane) cl[o] = off >> 5;
         }
-        cl[o] = idx | __ldg(reinterpret_cast<const uint8_t *>(mats + op.dlut) + lane);
     }
 }
 
-__device__ __forceinline__ float2 pre_chunk(float2 v, const uint32_t (&cl)[kMaxPreOps], const OpDev *ops,
-                                            uint32_t nops, uint32_t c, uint64_t w, uint64_t gb,
-                                            const float2 *__restrict__ mats) {
+template <int NP>
+__device__ __forceinline__ float2 pre_chunk(float2 v, const uint32_t (&cl)[NP > 0 ? NP : 1], const uint2 *pre_ab,
+                                            uint32_t nops, uint32_t c, const float2 *__restrict__ mats) {
 #pragma unroll
-    for (uint32_t o = 0; o < kMaxPreOps; ++o) {
-        if (o >= nops) break;
-        const OpDev &op = ops[o];
-        if (op.type == OP_DIAG) {
-            const uint32_t idx = cl[o] | __ldg(reinterpret_cast<const uint8_t *>(mats + op.dlut) + 32 + c);
-            const float2 ph = __ldg(mats + op.mat + idx);
+    for (int o = 0; o < NP; ++o) {
+        if (uint32_t(o) >= nops) break;
+        const uint2 ab = pre_ab[o];
+        if (ab.y != kPreFlip) {
+            const uint32_t idx = cl[o] | __ldg(reinterpret_cast<const uint8_t *>(mats) + ab.x + c);
+            const float2 ph = __ldg(mats + ab.y + idx);
             v = make_float2(ph.x * v.x - ph.y * v.y, ph.x * v.y + ph.y * v.x);
-        } else if (op.basis_in_stage && gb == op.basis_outer && w == op.basis_w) {
+        } else if (c == cl[o]) {
             v = make_float2(-v.x, -v.y);
         }
     }
@@ -102,11 +124,12 @@ __device__ __forceinline__ float2 pre_chunk(float2 v, const uint32_t (&cl)[kMaxP
 // (Re chunk c, Im chunk c) eight at a time with all sixteen payload loads in
 // flight: bit-plane transpose, zigzag inverse, inclusive prefix sum (the
 // Lorenzo inverse), x' = q * 2^e, interleaved (re, im) stores.
-template <bool CG = false>
+template <int NP, bool CG = false>
 __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t bytes, const FrameGeom &g, int m,
                                                   uint32_t f, float2 *__restrict__ dst, uint32_t *hist_j,
                                                   uint32_t *s_hist_w, int *status, const OpDev *pre_ops,
-                                                  uint32_t npre, const float2 *__restrict__ mats, uint64_t wbase,
+                                                  const uint2 *pre_ab, uint32_t npre,
+                                                  const float2 *__restrict__ mats, uint64_t wbase,
                                                   uint64_t gb) {
     const int lane = threadIdx.x & 31;
     const uint32_t padw = (2u * g.C + 15u) & ~15u;
@@ -168,8 +191,8 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
     }
     const uint32_t *payload = reinterpret_cast<const uint32_t *>(sp + fa + padw);
     const float step = exp2i(e);
-    uint32_t pre_cl[kMaxPreOps];
-    if (npre) pre_frame(pre_cl, pre_ops, npre, wbase | (uint64_t(f) * g.F), g.fl, lane, gb, mats);
+    uint32_t pre[NP > 0 ? NP : 1];
+    if (NP > 0 && npre) pre_frame<NP>(pre, pre_ops, npre, wbase | (uint64_t(f) * g.F), g.fl, lane, gb, mats);
     // ---- chunk pairs, eight at a time ----
     for (uint32_t c0 = 0; c0 < g.C; c0 += 8) {
         // widths/offsets of Re chunks c0.. (owner lane c0/8) and Im chunks C+c0.. (owner (C+c0)/8)
@@ -233,7 +256,7 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
             }
             const int32_t sr = int32_t(qr), si = int32_t(qi);
             float2 v = make_float2(float(sr) * step, float(si) * step);
-            if (npre) v = pre_chunk(v, pre_cl, pre_ops, npre, c, wbase | (uint64_t(f) * g.F + c * 32 + lane), gb, mats);
+            if (NP > 0 && npre) v = pre_chunk<NP>(v, pre, pre_ab, npre, c, mats);
             dst[c * 32 + lane] = v;
             if (hist_j && lane == 0) {  // the chunk's code widths, 32 values each
                 atomicAdd(&s_hist_w[min(wr[t], 31u)], 32u);

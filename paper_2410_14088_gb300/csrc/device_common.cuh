@@ -41,6 +41,14 @@ __device__ __forceinline__ float exp2i(int e) { return __int_as_float((e + 127) 
 
 // Transpose the 32x32 bit matrix held one row per lane (row = lane, column =
 // bit): afterwards lane j holds the word whose bit i was bit j of lane i.
+// Stage s exchanges s x s sub-blocks between lanes l and l ^ s: the lower
+// lane keeps the bits under mask `left` and takes the partner's bits under
+// `left` moved up by s; the upper lane keeps ~left and takes the partner's
+// ~left bits moved down by s. Each lane sends its word rotated (right by s
+// from the lower lane, left by s from the upper one), so that the received
+// word already has the needed bits in place: one rotate, one shuffle and one
+// bitwise select per stage. The masks repeat with period 2s, so the upper
+// lane's mask ~left is `left` rotated by s.
 __device__ __forceinline__ uint32_t warp_bit_transpose(uint32_t x, int lane) {
 #pragma unroll
     for (int s = 16; s >= 1; s >>= 1) {
@@ -49,11 +57,11 @@ __device__ __forceinline__ uint32_t warp_bit_transpose(uint32_t x, int lane) {
                             : (s == 4)  ? 0x0F0F0F0Fu
                             : (s == 2)  ? 0x33333333u
                                         : 0x55555555u;
-        uint32_t partner = __shfl_xor_sync(kFull, x, s);
-        if ((lane & s) == 0)
-            x = (x & left) | ((partner & left) << s);
-        else
-            x = (x & ~left) | ((partner & ~left) >> s);
+        const uint32_t t = uint32_t(lane) & uint32_t(s);                    // 0 (lower) or s (upper)
+        const uint32_t keep = __funnelshift_r(left, left, t);                // ~left = left rotated by s
+        const uint32_t sent = __funnelshift_r(x, x, uint32_t(s) - 2u * t);  // rotate right by s or 32 - s
+        const uint32_t got = __shfl_xor_sync(kFull, sent, s);
+        x = (x & keep) | (got & ~keep);
     }
     return x;
 }

@@ -59,6 +59,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
     __shared__ gdev::PassSmem PS;
     __shared__ uint32_t s_wb[PT / 32][64];
     __shared__ OpDev s_pre[kMaxPreOps];
+    __shared__ uint2 s_pre_ab[kMaxPreOps];
     __shared__ __align__(16) PSeg S;
     __shared__ uint32_t s_hist[PT / 32][32];
     __shared__ uint32_t s_words[PT / 32];
@@ -97,7 +98,10 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             unsigned long long *dst = reinterpret_cast<unsigned long long *>(&S);
             for (int t = tid; t < int(sizeof(PSeg) / 8); t += PT) dst[t] = __ldg(src + t);
             __syncthreads();
-            if (tid < int(S.npre)) s_pre[tid] = S.ops[S.pre_begin + tid];
+            if (tid < int(S.npre)) {
+                s_pre[tid] = S.ops[S.pre_begin + tid];
+                s_pre_ab[tid] = cdev::pre_setup(S.ops[S.pre_begin + tid]);
+            }
             if (tid == 0) s_seg = want;
             __syncthreads();
         }
@@ -159,9 +163,11 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             if (fi < gframes) {
                 const uint32_t jj = fi / g.nframes, f = fi % g.nframes;
                 const BlockSlot sl = S.tab_in[ids[jj]];
-                cdev::decode_frame_warp(sl.ptr, sl.bytes, g, int(S.m), f, wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F,
-                                        S.hist ? S.hist + (bbase + jj) * 32 : nullptr, s_hist[warp], L.status, s_pre,
-                                        S.npre, S.mats, uint64_t(jj) << S.m, gb);
+                cdev::decode_frame_warp<kMaxPreOps>(sl.ptr, sl.bytes, g, int(S.m), f,
+                                                    wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F,
+                                                    S.hist ? S.hist + (bbase + jj) * 32 : nullptr, s_hist[warp],
+                                                    L.status, s_pre, s_pre_ab, S.npre, S.mats,
+                                                    uint64_t(jj) << S.m, gb);
             }
         } else if (type == PH_PASS) {
             gdev::pass_tile<PT, 5, PREC, true>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr, i, gb, PS,
