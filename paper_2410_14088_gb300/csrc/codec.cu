@@ -234,26 +234,22 @@ __global__ void __launch_bounds__(NT, 4) k_encode_lbw(const float2 *__restrict__
     }
 }
 
+// Sizing pass (one CTA per frame) whose last CTA reserves every block's slot
+// from the summed frame lengths; sizes are left zeroed for the next use.
 __global__ void __launch_bounds__(NT, 3) k_encode_size(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
                                                     uint64_t *__restrict__ sizes, uint32_t *done_ctr,
                                                     ArenaDev dev, ArenaDev host, EncTarget *__restrict__ tgt,
-                                                    EncResult *__restrict__ res, int *status, uint8_t *__restrict__ wrec,
-                                                    uint32_t *__restrict__ flen, uint32_t *__restrict__ foff) {
+                                                    EncResult *__restrict__ res, int *status) {
     const FrameGeom g = geom(m);
     __shared__ uint32_t s_words[NW];
     __shared__ bool s_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     const uint64_t items = uint64_t(nblocks) * g.nframes;
     for (uint64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const uint32_t j = uint32_t(item / g.nframes), f = uint32_t(item % g.nframes);
-        const uint32_t len = size_frame_cta(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, g, e, s_words, status,
-                                            wrec ? wrec + item * 256 : nullptr);
-        if (tid == 0) {
-            if (len) atomicAdd(reinterpret_cast<unsigned long long *>(&sizes[j]), uint64_t(len));
-            if (flen) flen[item] = len;
-        }
+        const uint32_t len = size_frame_cta(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, g, e, s_words, status);
+        if (tid == 0 && len) atomicAdd(reinterpret_cast<unsigned long long *>(&sizes[j]), uint64_t(len));
     }
-    if (!done_ctr) return;
     if (tid == 0) {
         __threadfence();
         s_last = atomicAdd(done_ctr, 1u) == gridDim.x - 1;
@@ -261,55 +257,30 @@ __global__ void __launch_bounds__(NT, 3) k_encode_size(const float2 *__restrict_
     __syncthreads();
     if (!s_last) return;
     __threadfence();
-    if (foff) {
-        // warp per block: frame offsets = data_start + exclusive prefix of the frame lengths
-        for (uint32_t jb = warp; jb < nblocks; jb += NW) {
-            uint32_t run = uint32_t(g.data_start);
-            for (uint32_t f0 = 0; f0 < g.nframes; f0 += 32) {
-                const uint64_t it = uint64_t(jb) * g.nframes + f0 + lane;
-                const uint32_t v = f0 + lane < g.nframes ? __ldcg(flen + it) : 0u;
-                uint32_t incl = v;
-#pragma unroll
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t t = __shfl_up_sync(kFull, incl, o);
-                    if (lane >= o) incl += t;
-                }
-                if (f0 + lane < g.nframes) foff[it] = run + incl - v;
-                run += __shfl_sync(kFull, incl, 31);
-            }
-            if (lane == 0) {
-                sizes[jb] = 0;
-                res[jb].total = 0;
-                res[jb].overflow = 0;
-                res[jb].err_sq = 0;
-                res[jb].norm_sq = 0;
-                reserve_slot(run, dev, host, &tgt[jb], status);
-            }
-        }
-    } else {
-        for (uint32_t j = tid; j < nblocks; j += NT) {
-            const uint64_t want = ld_relaxed_u64(&sizes[j]) + g.data_start;
-            sizes[j] = 0;
-            res[j].total = 0;
-            res[j].overflow = 0;
-            res[j].err_sq = 0;
-            res[j].norm_sq = 0;
-            reserve_slot(want, dev, host, &tgt[j], status);
-        }
+    for (uint32_t j = tid; j < nblocks; j += NT) {
+        const uint64_t want = ld_relaxed_u64(&sizes[j]) + g.data_start;
+        sizes[j] = 0;
+        res[j].total = 0;
+        res[j].overflow = 0;
+        res[j].err_sq = 0;
+        res[j].norm_sq = 0;
+        reserve_slot(want, dev, host, &tgt[j], status);
     }
     if (tid == 0) *done_ctr = 0;
 }
 
-// Exact-sizing encoder: one warp per frame, widths and frame offsets from the
-// sizing pass; the last CTA folds the frames' error partials into the blocks'
-// and the stage's totals.
-__global__ void __launch_bounds__(NT, 3) k_encode_known(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
-                                                     const EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
-                                                     const uint32_t *__restrict__ ids, BlockSlot *__restrict__ table,
-                                                     StageAccum *acc, const uint8_t *__restrict__ wrec,
-                                                     const uint32_t *__restrict__ flen,
-                                                     const uint32_t *__restrict__ foff, float2 *__restrict__ part,
-                                                     uint32_t *done_ctr, int *status) {
+// In-place exact encoder, pass 1: one warp per frame encodes the frame over
+// its own amplitudes (Im-plane words to im, F words per frame) and records
+// its length and word counts; the last CTA turns the frame lengths into frame
+// offsets, reserves each block's exact slot and folds the frames' error
+// partials into the blocks' and the stage's totals.
+__global__ void __launch_bounds__(NT, 3) k_encode_ip(float2 *wv, uint32_t *__restrict__ im, uint32_t nblocks, int m,
+                                                  int e, uint32_t *done_ctr, ArenaDev dev, ArenaDev host,
+                                                  EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
+                                                  StageAccum *acc, uint8_t *__restrict__ wrec,
+                                                  uint32_t *__restrict__ flen, uint32_t *__restrict__ fwords,
+                                                  uint32_t *__restrict__ foff, float2 *__restrict__ part,
+                                                  int *status) {
     const FrameGeom g = geom(m);
     __shared__ bool s_last;
     __shared__ double s_red[2][NW];
@@ -317,9 +288,13 @@ __global__ void __launch_bounds__(NT, 3) k_encode_known(const float2 *__restrict
     const uint64_t items = uint64_t(nblocks) * g.nframes;
     for (uint64_t item = uint64_t(blockIdx.x) * NW + warp; item < items; item += uint64_t(gridDim.x) * NW) {
         const uint32_t j = uint32_t(item / g.nframes), f = uint32_t(item % g.nframes);
-        encode_frame_warp_known(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, g, m, e, f, wrec + item * 256, foff[item],
-                                flen[item], tgt[j], res + j, table ? table + ids[j] : nullptr, acc, part + item,
-                                status);
+        uint32_t words;
+        const uint32_t len = encode_frame_warp_ip(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, im + item * g.F, g, e,
+                                                  wrec + item * 256, words, part + item, status);
+        if (lane == 0) {
+            flen[item] = len;
+            fwords[item] = words;
+        }
     }
     if (tid == 0) {
         __threadfence();
@@ -328,13 +303,29 @@ __global__ void __launch_bounds__(NT, 3) k_encode_known(const float2 *__restrict
     __syncthreads();
     if (!s_last) return;
     __threadfence();
+    // warp per block: frame offsets = data_start + exclusive prefix of the frame lengths; exact slot;
+    // the block's error sums in FP64
     double ta = 0, tb = 0;
     for (uint32_t jb = warp; jb < nblocks; jb += NW) {
+        uint32_t run = uint32_t(g.data_start);
         double a = 0, b = 0;
-        for (uint32_t f2 = lane; f2 < g.nframes; f2 += 32) {
-            const float2 p = __ldcg(part + uint64_t(jb) * g.nframes + f2);
-            a += double(p.x);
-            b += double(p.y);
+        for (uint32_t f0 = 0; f0 < g.nframes; f0 += 32) {
+            const uint64_t it = uint64_t(jb) * g.nframes + f0 + lane;
+            const bool live = f0 + lane < g.nframes;
+            const uint32_t v = live ? __ldcg(flen + it) : 0u;
+            if (live) {
+                const float2 pp = __ldcg(part + it);
+                a += double(pp.x);
+                b += double(pp.y);
+            }
+            uint32_t incl = v;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (live) foff[it] = run + incl - v;
+            run += __shfl_sync(kFull, incl, 31);
         }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
@@ -342,8 +333,11 @@ __global__ void __launch_bounds__(NT, 3) k_encode_known(const float2 *__restrict
             b += __shfl_xor_sync(kFull, b, o);
         }
         if (lane == 0) {
+            res[jb].total = 0;
+            res[jb].overflow = 0;
             res[jb].err_sq = a;
             res[jb].norm_sq = b;
+            reserve_slot(run, dev, host, &tgt[jb], status);
         }
         ta += a;
         tb += b;
@@ -361,6 +355,26 @@ __global__ void __launch_bounds__(NT, 3) k_encode_known(const float2 *__restrict
             atomicAdd(&acc->norm_sq, b);
         }
         *done_ctr = 0;
+    }
+}
+
+// In-place exact encoder, pass 2: one warp per frame copies the frame's
+// pieces to its offset in the block's slot.
+__global__ void __launch_bounds__(NT) k_frame_copy(const float2 *__restrict__ wv, const uint32_t *__restrict__ im,
+                                                   uint32_t nblocks, int m, int e, const EncTarget *__restrict__ tgt,
+                                                   EncResult *__restrict__ res, const uint32_t *__restrict__ ids,
+                                                   BlockSlot *__restrict__ table, StageAccum *acc,
+                                                   const uint8_t *__restrict__ wrec, const uint32_t *__restrict__ flen,
+                                                   const uint32_t *__restrict__ fwords,
+                                                   const uint32_t *__restrict__ foff) {
+    const FrameGeom g = geom(m);
+    const int warp = threadIdx.x >> 5;
+    const uint64_t items = uint64_t(nblocks) * g.nframes;
+    for (uint64_t item = uint64_t(blockIdx.x) * NW + warp; item < items; item += uint64_t(gridDim.x) * NW) {
+        const uint32_t j = uint32_t(item / g.nframes), f = uint32_t(item % g.nframes);
+        copy_frame_warp(reinterpret_cast<const uint32_t *>(wv + (uint64_t(j) << m) + uint64_t(f) * g.F),
+                        im + item * g.F, wrec + item * 256, fwords[item], flen[item], foff[item], g, m, e, f, tgt[j],
+                        res + j, table ? table + ids[j] : nullptr, acc);
     }
 }
 
@@ -487,21 +501,13 @@ void launch_encode(const float2 *wv, uint32_t nblocks, int m, int e, const EncTa
     count_launch();
 }
 
-void launch_encode_size(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, int *status,
-                        cudaStream_t s) {
-    const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
-    ArenaDev none{};
-    k_encode_size<<<grid_for(items, 152 * 8), NT, 0, s>>>(wv, nblocks, m, e, sizes, nullptr, none, none, nullptr,
-                                                           nullptr, status, nullptr, nullptr, nullptr);
-    count_launch();
-}
 
 void launch_size_reserve(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, uint32_t *done_ctr,
                          const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, int *status,
-                         cudaStream_t s, uint8_t *wrec, uint32_t *flen, uint32_t *foff) {
+                         cudaStream_t s) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
     k_encode_size<<<grid_for(items, 152 * 8), NT, 0, s>>>(wv, nblocks, m, e, sizes, done_ctr, dev, host, tgt, res,
-                                                           status, wrec, flen, foff);
+                                                           status);
     count_launch();
 }
 
@@ -517,13 +523,22 @@ void launch_encode_lbw(const float2 *wv, uint32_t nblocks, int m, int e, EncTarg
     count_launch();
 }
 
-void launch_encode_known(const float2 *wv, uint32_t nblocks, int m, int e, const EncTarget *tgt, EncResult *res,
-                         const uint32_t *ids, BlockSlot *table, StageAccum *acc, const uint8_t *wrec,
-                         const uint32_t *flen, const uint32_t *foff, float2 *part, uint32_t *done_ctr, int *status,
-                         cudaStream_t s) {
+void launch_encode_ip(float2 *wv, uint32_t *im, uint32_t nblocks, int m, int e, uint32_t *done_ctr,
+                      const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, StageAccum *acc,
+                      uint8_t *wrec, uint32_t *flen, uint32_t *fwords, uint32_t *foff, float2 *part, int *status,
+                      cudaStream_t s) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
-    k_encode_known<<<grid_for((items + NW - 1) / NW, 152 * 8), NT, 0, s>>>(wv, nblocks, m, e, tgt, res, ids, table, acc,
-                                                                         wrec, flen, foff, part, done_ctr, status);
+    k_encode_ip<<<grid_for((items + NW - 1) / NW, 152 * 8), NT, 0, s>>>(wv, im, nblocks, m, e, done_ctr, dev, host,
+                                                                      tgt, res, acc, wrec, flen, fwords, foff, part,
+                                                                      status);
+    count_launch();
+}
+void launch_frame_copy(const float2 *wv, const uint32_t *im, uint32_t nblocks, int m, int e, const EncTarget *tgt,
+                       EncResult *res, const uint32_t *ids, BlockSlot *table, StageAccum *acc, const uint8_t *wrec,
+                       const uint32_t *flen, const uint32_t *fwords, const uint32_t *foff, cudaStream_t s) {
+    const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
+    k_frame_copy<<<grid_for((items + NW - 1) / NW, 152 * 16), NT, 0, s>>>(wv, im, nblocks, m, e, tgt, res, ids,
+                                                                        table, acc, wrec, flen, fwords, foff);
     count_launch();
 }
 

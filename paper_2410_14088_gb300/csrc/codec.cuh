@@ -74,13 +74,10 @@ void launch_decode(const BlockRef *in, uint32_t nblocks, int m, float2 *wv, uint
 void launch_encode(const float2 *wv, uint32_t nblocks, int m, int e, const EncTarget *tgt, EncResult *res,
                    int only_overflowed, const uint32_t *ids, BlockSlot *table, StageAccum *acc,
                    const LookbackScratch &scr, int *status, cudaStream_t s);
-void launch_encode_size(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, int *status,
-                        cudaStream_t s);
 // sizing pass whose last CTA reserves every block's slot (sizes are left zeroed)
-// with wrec/flen/foff it also records every frame's chunk widths (256 bytes per frame), length and offset
 void launch_size_reserve(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, uint32_t *done_ctr,
                          const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, int *status,
-                         cudaStream_t s, uint8_t *wrec = nullptr, uint32_t *flen = nullptr, uint32_t *foff = nullptr);
+                         cudaStream_t s);
 // learned-sizing encoder (warp per frame, ticket order, warp look-back); only_overflowed: re-encode the blocks
 // whose first pass overflowed its reserved slot. With fix_dev/fix_host the first pass's last CTA reserves exact
 // slots for those blocks (counted in scr.pending).
@@ -88,11 +85,16 @@ void launch_encode_lbw(const float2 *wv, uint32_t nblocks, int m, int e, EncTarg
                        int only_overflowed, const uint32_t *ids, BlockSlot *table, StageAccum *acc,
                        const LookbackScratch &scr, const ArenaDev *fix_dev, const ArenaDev *fix_host, int *status,
                        cudaStream_t s);
-// exact-sizing encoder (warp per frame) using the records of launch_size_reserve
-void launch_encode_known(const float2 *wv, uint32_t nblocks, int m, int e, const EncTarget *tgt, EncResult *res,
-                         const uint32_t *ids, BlockSlot *table, StageAccum *acc, const uint8_t *wrec,
-                         const uint32_t *flen, const uint32_t *foff, float2 *part, uint32_t *done_ctr, int *status,
-                         cudaStream_t s);
+// In-place exact encoder: pass 1 encodes every frame over its own amplitudes (Im-plane words to im, 4 bytes
+// per amplitude), records the frames' lengths, word counts (fwords) and offsets and reserves each block's
+// exact slot; pass 2 (launch_frame_copy) copies the frames into the slots. wv is overwritten.
+void launch_encode_ip(float2 *wv, uint32_t *im, uint32_t nblocks, int m, int e, uint32_t *done_ctr,
+                      const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, StageAccum *acc,
+                      uint8_t *wrec, uint32_t *flen, uint32_t *fwords, uint32_t *foff, float2 *part, int *status,
+                      cudaStream_t s);
+void launch_frame_copy(const float2 *wv, const uint32_t *im, uint32_t nblocks, int m, int e, const EncTarget *tgt,
+                       EncResult *res, const uint32_t *ids, BlockSlot *table, StageAccum *acc, const uint8_t *wrec,
+                       const uint32_t *flen, const uint32_t *fwords, const uint32_t *foff, cudaStream_t s);
 // leading phase ops of a stage for the decoder (count <= kMaxPreOps)
 struct OpDev;
 struct PreOps {

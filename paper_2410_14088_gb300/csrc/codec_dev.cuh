@@ -549,9 +549,8 @@ __device__ __forceinline__ void reserve_slot(uint64_t want, const ArenaDev &dev,
 // CTA; the result is returned to every thread. s_words holds NW words.
 template <bool CG = false>
 __device__ __forceinline__ uint32_t size_frame_cta(const float2 *__restrict__ src, const FrameGeom &g, int e,
-                                                   uint32_t *s_words, int *status, uint8_t *wrec = nullptr) {
-    __shared__ __align__(16) uint8_t s_wb[256];  // the frame's chunk widths, when wrec is given
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+                                                   uint32_t *s_words, int *status) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float inv_step = exp2i(-e);
     float2 vin[MAX_CPW];
 #pragma unroll
@@ -583,17 +582,10 @@ __device__ __forceinline__ uint32_t size_frame_cta(const float2 *__restrict__ sr
         const uint32_t zi = zigzag(lane ? int32_t(uint32_t(q[1]) - uint32_t(pi)) : q[1]);
         const uint32_t wr = 32 - __clz(__reduce_or_sync(kFull, zr)), wi = 32 - __clz(__reduce_or_sync(kFull, zi));
         words += wr + wi;
-        if (wrec && lane == 0) {
-            s_wb[c] = uint8_t(wr);
-            s_wb[g.C + c] = uint8_t(wi);
-        }
     }
     if (bad) raise_status(status, bad);
     if (lane == 0) s_words[warp] = words;
     __syncthreads();
-    // the width record leaves in 16-byte stores (bytes past 2C are ignored by its reader)
-    if (wrec && tid < int((2 * g.C + 15) / 16))
-        reinterpret_cast<uint4 *>(wrec)[tid] = reinterpret_cast<const uint4 *>(s_wb)[tid];
     uint32_t tot = 0;
 #pragma unroll
     for (int w = 0; w < NW; ++w) tot += s_words[w];
@@ -848,6 +840,185 @@ __device__ __forceinline__ void encode_frame_warp_known(const float2 *__restrict
                                                         float2 *part_item, int *status) {
     encode_frame_warp_core<CG>(src, g, m, e, f, load_widths_warp<CG>(wrec, g), frame_off, len, tgt, res_j,
                                table_slot, acc, part_item, status);
+}
+
+// In-place exact encoder, first of two passes: one warp reads frame f once
+// and writes its bit-plane words without knowing the frame's place in the
+// stream. The Re-plane words go over the frame's own amplitudes (the words of
+// chunk c end at or before byte 128 (c + 1) of the frame, and every chunk up
+// to c has been read by then), the Im-plane words to im (one word per
+// amplitude of scratch), the chunk widths to wrec (2C bytes). Returns the
+// frame's stream bytes; words receives its Re-plane words | Im-plane words << 16
+// (each at most 4096). The second pass (copy_frame_warp) moves the pieces to
+// the frame's offset in the block's slot.
+__device__ __forceinline__ uint32_t encode_frame_warp_ip(float2 *frame, uint32_t *__restrict__ im,
+                                                         const FrameGeom &g, int e, uint8_t *__restrict__ wrec,
+                                                         uint32_t &words, float2 *part_item, int *status) {
+    const int lane = threadIdx.x & 31;
+    const float inv_step = exp2i(-e), step = exp2i(e);
+    uint32_t *re = reinterpret_cast<uint32_t *>(frame);  // aliases frame: no __restrict__
+    uint32_t ro = 0, io = 0, wre = 0, wim = 0;
+    float err_sq = 0.f, norm_sq = 0.f;
+    int bad = 0;
+    for (uint32_t c0 = 0; c0 < g.C; c0 += 8) {
+        float2 vin[8];
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t c = c0 + t;
+            vin[t] = c < g.C ? frame[c * 32 + lane] : make_float2(0.f, 0.f);
+        }
+        __syncwarp();  // every lane's reads of this batch come before the batch's in-place writes
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t c = c0 + t;
+            if (c >= g.C) break;
+            int32_t q[2];
+            const float x[2] = {vin[t].x, vin[t].y};
+#pragma unroll
+            for (int pl = 0; pl < 2; ++pl) {
+                const float tq = x[pl] * inv_step;  // exact: power-of-two scaling
+                if (!(fabsf(tq) < 1073741824.0f)) {  // NaN, Inf or out of range
+                    bad = isfinite(x[pl]) ? (bad ? bad : QSIM_E_RANGE) : QSIM_E_INVALID;
+                    q[pl] = 0;
+                } else {
+                    q[pl] = __float2int_rn(tq);
+                }
+                const float xr = float(q[pl]) * step;
+                const float dx = x[pl] - xr;
+                err_sq = fmaf(dx, dx, err_sq);
+                norm_sq = fmaf(xr, xr, norm_sq);
+            }
+            const int32_t pr = __shfl_up_sync(kFull, q[0], 1);
+            const int32_t pi = __shfl_up_sync(kFull, q[1], 1);
+            const uint32_t zr = zigzag(lane ? int32_t(uint32_t(q[0]) - uint32_t(pr)) : q[0]);
+            const uint32_t zi = zigzag(lane ? int32_t(uint32_t(q[1]) - uint32_t(pi)) : q[1]);
+            // a plane's width is one more than its highest nonzero bit plane: taken from the transposed words
+            uint32_t wr, wi;
+            if (!__any_sync(kFull, (zr | zi) >> 16)) {
+                // both planes in one transpose: lane b < 16 gets Re plane b, lane 16 + b Im plane b
+                const uint32_t word = warp_bit_transpose(zr | (zi << 16), lane);
+                const uint32_t nz = __ballot_sync(kFull, word != 0);
+                wr = 32 - __clz(nz & 0xffffu);
+                wi = 32 - __clz(nz >> 16);
+                const uint32_t b = uint32_t(lane) & 15u;
+                if (lane < 16) {
+                    if (b < wr) re[ro + b] = word;
+                } else if (b < wi) {
+                    im[io + b] = word;
+                }
+            } else {
+                const uint32_t word_r = warp_bit_transpose(zr, lane);
+                const uint32_t word_i = warp_bit_transpose(zi, lane);
+                wr = 32 - __clz(__ballot_sync(kFull, word_r != 0));
+                wi = 32 - __clz(__ballot_sync(kFull, word_i != 0));
+                if (lane < int(wr)) re[ro + lane] = word_r;
+                if (lane < int(wi)) im[io + lane] = word_i;
+            }
+            if (uint32_t(lane) == (c >> 2)) {
+                wre |= wr << (8 * (c & 3));
+                wim |= wi << (8 * (c & 3));
+            }
+            ro += wr;
+            io += wi;
+        }
+    }
+    if (bad) raise_status(status, bad);
+    store_widths_warp(wrec, g, wre, wim);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+        err_sq += __shfl_xor_sync(kFull, err_sq, o);
+        norm_sq += __shfl_xor_sync(kFull, norm_sq, o);
+    }
+    if (lane == 0 && part_item) *part_item = make_float2(err_sq, norm_sq);
+    words = ro | (io << 16);
+    return frame_len(g, ro + io);
+}
+
+// Second pass of the in-place encoder: frame f's widths (wrec), Re-plane
+// words (re, 16-byte aligned) and Im-plane words (im) are copied to byte
+// offset frame_off of the block's slot and padded to 16 bytes; lane 0 writes
+// the frame's offset-table entry and, for the block's last frame, the header,
+// the block's table slot and the stage totals. words = Re words | Im words << 16.
+// A slot too small (only after a failed reservation) sets the block's
+// overflow flag instead.
+__device__ __forceinline__ void copy_frame_warp(const uint32_t *__restrict__ re, const uint32_t *__restrict__ im,
+                                                const uint8_t *__restrict__ wrec, uint32_t words, uint32_t len,
+                                                uint32_t frame_off, const FrameGeom &g, int m, int e, uint32_t f,
+                                                EncTarget tgt, EncResult *res_j, BlockSlot *table_slot,
+                                                StageAccum *acc) {
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t padw = (2u * g.C + 15u) & ~15u;
+    const uint32_t nre = words & 0xffffu, nim = words >> 16;
+    uint8_t *out = tgt.ptr;
+    const uint64_t cap = tgt.cap;
+    const bool fits = out != nullptr && uint64_t(frame_off) + len <= cap;
+    if (fits && len) {
+        uint8_t *dst = out + frame_off;
+        const uint2 wb = load_widths_warp<true>(wrec, g);
+        if (8u * lane < padw) *reinterpret_cast<uint2 *>(dst + 8u * lane) = wb;
+        // payload word i: Re word i (i < nre), Im word i - nre (i - nre < nim), else zero padding; written
+        // as 16-byte vectors, four per lane in flight
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + padw);  // 16-byte aligned
+        const uint32_t n4 = (len - padw) / 16;
+        for (uint32_t k0 = lane; k0 < n4; k0 += 128) {
+            uint4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t k = k0 + 32u * u, i = 4u * k;
+                if (k >= n4) break;
+                if (i + 4 <= nre) {
+                    v[u] = __ldcg(reinterpret_cast<const uint4 *>(re) + k);
+                } else if (i >= nre && !((i - nre) & 3u) && i - nre + 4 <= nim) {
+                    v[u] = __ldcg(reinterpret_cast<const uint4 *>(im + (i - nre)));
+                } else {
+                    uint32_t w[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        const uint32_t ii = i + t;
+                        w[t] = ii < nre ? __ldcg(re + ii) : (ii - nre < nim ? __ldcg(im + (ii - nre)) : 0u);
+                    }
+                    v[u] = make_uint4(w[0], w[1], w[2], w[3]);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const uint32_t k = k0 + 32u * u;
+                if (k < n4) d4[k] = v[u];
+            }
+        }
+    }
+    if (lane == 0) {
+        if (!fits && res_j) atomicOr(&res_j->overflow, 1u);
+        if (out && g.data_start <= cap) reinterpret_cast<uint32_t *>(out + 32)[f] = frame_off;
+        if (f == g.nframes - 1) {
+            const uint64_t total = uint64_t(frame_off) + len;
+            if (res_j) res_j->total = total;
+            if (out && total <= cap) {
+                uint32_t *h32 = reinterpret_cast<uint32_t *>(out);
+                h32[0] = kQszMagic;
+                h32[1] = 1u;  // version 1, flags 0
+                h32[2] = uint32_t(m) | (uint32_t(g.fl) << 8) | (uint32_t(uint8_t(int8_t(e))) << 16);
+                h32[3] = g.nframes;
+                reinterpret_cast<uint64_t *>(out)[2] = total;
+                reinterpret_cast<uint64_t *>(out)[3] = 0;
+                h32[8 + g.nframes] = uint32_t(total);
+                for (uint64_t b = 32 + 4ull * (g.nframes + 1); b < g.data_start; ++b) out[b] = 0;
+                if (table_slot) {
+                    table_slot->ptr = out;
+                    table_slot->bytes = total;
+                    table_slot->tier = tgt.tier;
+                }
+                if (acc) {
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&acc->store_bytes), total);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&acc->reserved_bytes), cap);
+                    if (tgt.tier) atomicAdd(reinterpret_cast<unsigned long long *>(&acc->host_bytes), cap);
+                    atomicAdd(reinterpret_cast<unsigned long long *>(&acc->blocks), 1ull);
+                }
+            } else if (acc) {
+                atomicAdd(reinterpret_cast<unsigned long long *>(&acc->overflow_blocks), 1ull);
+            }
+        }
+    }
 }
 
 // Warp look-back over the preceding frames of the block (status words of lb_block,

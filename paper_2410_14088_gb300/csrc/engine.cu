@@ -62,10 +62,10 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 // ---------------------------------------------------------------------------
 static std::atomic<int> g_profile{0};
 enum ProfCat { P_DECODE = 0, P_PASS, P_ENCODE_SIZE, P_RESERVE, P_ENCODE, P_GATHER, P_COPY_IN, P_COPY_OUT, P_INIT,
-               P_PREDICT, P_REENCODE, P_STAGE, P_NCAT };
+               P_PREDICT, P_REENCODE, P_STAGE, P_FRAME_COPY, P_NCAT };
 static const char *kProfNames[P_NCAT] = {"decode", "gate_pass", "encode_size", "reserve", "encode",
                                          "gather_refs", "copy_in", "copy_out", "init", "predict", "reencode",
-                                         "stage_persistent"};
+                                         "stage_persistent", "frame_copy"};
 
 struct Profiler {
     bool on = false;
@@ -865,6 +865,8 @@ struct StreamWork {
     DevBuf<float> pred;      // per block: predicted log2 stream bytes
     DevBuf<uint8_t> wrec;    // per frame: chunk widths recorded by the sizing pass
     DevBuf<uint32_t> flen, foff;  // per frame: stream bytes and offset
+    DevBuf<uint32_t> fwords;      // per frame: Re words | Im words << 16 (in-place encoder)
+    DevBuf<uint32_t> imsc;        // Im-plane words of the in-place encoder, one word per amplitude
 };
 
 static StageFeatures stage_features(const qsim_plan *p, size_t si, int e) {
@@ -1396,9 +1398,11 @@ static int finish_run(RunCtx &R, int dev, double ms, Profiler *prof, qsim_stats 
             }
             if (raw) {
                 bytes[P_COPY_OUT] += 8 * amps + out_store;
-            } else {
-                bytes[P_ENCODE_SIZE] += 8 * amps;
+            } else if (predict) {
                 bytes[P_ENCODE] += 8 * amps + out_store;
+            } else {
+                bytes[P_ENCODE] += 8 * amps + out_store;  // frames written in place
+                bytes[P_FRAME_COPY] += 2 * out_store;
             }
         }
         for (int c = 0; c < P_NCAT; ++c) {
@@ -1518,6 +1522,8 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             (rc = w.part.alloc(max_batch_blocks * nframes)) || (rc = w.hist.alloc(max_batch_blocks * 32)) ||
             (rc = w.pred.alloc(max_batch_blocks)) ||
             (!persistent && (rc = w.wrec.alloc(max_batch_blocks * nframes * 256))) ||
+            (!persistent && !predict && !raw && (rc = w.imsc.alloc(max_batch_blocks << m))) ||
+            (!persistent && (rc = w.fwords.alloc(max_batch_blocks * nframes))) ||
             (rc = w.flen.alloc(max_batch_blocks * nframes)) || (rc = w.foff.alloc(max_batch_blocks * nframes)) ||
             (rc = w.lb_ctr.alloc(8))) {
             destroy_streams();
@@ -1657,14 +1663,15 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
                                       status, w.s);
                     prof.end(w.s);
                 } else {
-                    prof.begin(P_ENCODE_SIZE, w.s);
-                    launch_size_reserve(w.wv.p, nb, m, e, w.sizes.p, w.lb_ctr.p + 3, arena_dev(out_par),
-                                        arena_host(out_par), w.tgt.p, w.res.p, status, w.s, w.wrec.p, w.flen.p,
-                                        w.foff.p);
-                    prof.end(w.s);
+                    // exact sizing: encode every frame in place, reserve exact slots, copy the frames over
                     prof.begin(P_ENCODE, w.s);
-                    launch_encode_known(w.wv.p, nb, m, e, w.tgt.p, w.res.p, ids, tab_out, acc, w.wrec.p, w.flen.p,
-                                        w.foff.p, w.part.p, w.lb_ctr.p + 1, status, w.s);
+                    launch_encode_ip(w.wv.p, w.imsc.p, nb, m, e, w.lb_ctr.p + 3, arena_dev(out_par),
+                                     arena_host(out_par), w.tgt.p, w.res.p, acc, w.wrec.p, w.flen.p, w.fwords.p,
+                                     w.foff.p, w.part.p, status, w.s);
+                    prof.end(w.s);
+                    prof.begin(P_FRAME_COPY, w.s);
+                    launch_frame_copy(w.wv.p, w.imsc.p, nb, m, e, w.tgt.p, w.res.p, ids, tab_out, acc, w.wrec.p,
+                                      w.flen.p, w.fwords.p, w.foff.p, w.s);
                     prof.end(w.s);
                 }
                 if (collect) {
