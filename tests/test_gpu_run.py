@@ -64,6 +64,24 @@ def test_config0_compressed():
     assert abs(st.norm_sq() - st.stats.norm_sq) < 1e-6
 
 
+@pytest.mark.parametrize("m,eps,mode", [(6, 1e-3, qsim.MODE_STREAMS), (9, 1e-6, qsim.MODE_STREAMS),
+                                         (13, 1e-3, qsim.MODE_STREAMS), (13, 1e-6, qsim.MODE_STREAMS),
+                                         (13, 1e-6, qsim.MODE_PERSISTENT)])
+def test_stored_streams_reencode_exactly(m, eps, mode):
+    # every block stream the stage loop stored equals the oracle's encoding of the block's decoded amplitudes
+    # (decoded values lie on the grid, so re-quantising them is exact); eps 1e-6 gives chunk widths above 16
+    # bits (two bit-plane transposes per chunk pair; the step 2^-27 still keeps |x| = 1 of the initial basis
+    # state below 2^30 steps), m 6 and 9 frames shorter than 4096 amplitudes
+    n = 15
+    c = inputs.random_brick(n, 4, 7)
+    st = qsim.run(qsim.plan_stages(c, m=m, inner=2, k=4, eps=eps, mode=mode))
+    amps = state_c64(st).view(np.float32)
+    eb = eps * 2.0 ** (-n / 2)
+    for b in range(1 << (n - m)):
+        blk = amps[(b << (m + 1)):((b + 1) << (m + 1))]
+        assert st.block_stream(b) == oracle.qsz_encode(blk, m, eb), b
+
+
 def test_streams_are_deterministic():
     c = inputs.random_brick(16, 6, 4)
     streams = []
