@@ -183,8 +183,9 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
 #pragma unroll
     for (uint32_t i = 0; i < MT * NTILES; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.f;
     const uint2 *bf2 = reinterpret_cast<const uint2 *>(bfr);
-    // k-step pairs (ks, ks + KS/2) read the same complex inputs: Re parts for ks, Im parts for ks + KS/2
-#pragma unroll 1
+    // k-step pairs (ks, ks + KS/2) read the same complex inputs: Re parts for ks, Im parts for ks + KS/2;
+    // unrolled so that the next pair's operand loads overlap the current pair's MMAs
+#pragma unroll
     for (uint32_t ks = 0; ks < KS / 2; ++ks) {
         if constexpr (PREC == QSIM_PREC_TF32) {
             const uint32_t c0 = S.offs_sw[ks * 8 + tq], c1 = S.offs_sw[ks * 8 + tq + 4];
