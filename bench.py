@@ -405,6 +405,18 @@ def run_ours(args, rank, world, dist):
     te_ms = max_over_ranks(e0.elapsed_time(e1), dist)
     e2e = job_rate(world, args.steps, (1 << n) * G, te_ms) if not args.no_e2e else None
 
+    # ---- per-kernel times without the other stream's kernels beside them (roofline context) ----
+    kstats_serial = None
+    if not args.no_profile and args.mode == "streams" and args.streams > 1:
+        plan1 = qsim.plan_stages(circ, **dict(kw, streams=1))
+        st = qsim.run(plan1)
+        del st
+        qsim.profile_enable(True)
+        st = qsim.run(plan1)
+        kstats_serial = st.kernel_stats()
+        qsim.profile_enable(False)
+        del st, plan1
+
     if rank != 0:
         return
     last = stats[-1]
@@ -446,6 +458,17 @@ def run_ours(args, rank, world, dist):
         roofline["other_bounds"] = [{k: c[k] for k in ("bound", "frac")} for c in cands if c["bound"] != roofline["bound"]]
         roofline["traffic"] = traffic_for(dom, d["alg_bytes"] / max(1, d["launches"]))
         roofline["ms_per_launch"] = per_launch_s * 1e3
+        if kstats_serial and dom in kstats_serial:
+            # the same kernel in one more run on a single stream: its launches then share the GPU with nothing
+            ds = kstats_serial[dom]
+            secs = max(1e-12, ds["seconds"])
+            ach = (ds["alg_bytes"] if roofline["unit"] == "GB/s" else ds["alg_flops"]) / secs / (
+                1e9 if roofline["unit"] == "GB/s" else 1e12)
+            roofline["one_stream"] = {"achieved": ach, "frac": ach / roofline["peak"],
+                                      "ms_per_launch": 1e3 * ds["seconds"] / max(1, ds["launches"]),
+                                      "note": "one extra run of the plan on 1 stream after the timed region; "
+                                              "with 2 streams each launch shares the GPU with the other "
+                                              "stream's kernels, which lengthens its event-timed duration"}
     cr = 8.0 * (1 << n) / max(1, last["peak_store_bytes"])
     mirror_fidelity = None
     if args.workload == "mirror":

@@ -274,7 +274,7 @@ __global__ void __launch_bounds__(NT, 3) k_encode_size(const float2 *__restrict_
 // its length and word counts; the last CTA turns the frame lengths into frame
 // offsets, reserves each block's exact slot and folds the frames' error
 // partials into the blocks' and the stage's totals.
-__global__ void __launch_bounds__(NT, 3) k_encode_ip(float2 *wv, uint32_t *__restrict__ im, uint32_t nblocks, int m,
+__global__ void __launch_bounds__(NT, 4) k_encode_ip(float2 *wv, uint32_t *__restrict__ im, uint32_t nblocks, int m,
                                                   int e, uint32_t *done_ctr, ArenaDev dev, ArenaDev host,
                                                   EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
                                                   StageAccum *acc, uint8_t *__restrict__ wrec,
