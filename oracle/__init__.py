@@ -7,8 +7,8 @@ the CUDA path; the two meet only in the seeded input generators
 (`paper_2410_14088_gb300.inputs`), which hold none of the method's arithmetic.
 
 Modules:
-  * this file    — ctypes front end of qsim_oracle.c (state update, QSZ1 codec,
-                   MLP) and the circuit-level drivers built on it;
+  * this file    — ctypes front end of qsim_oracle.c (state update, QSZ1 and
+                   QSZR codecs, MLP) and the circuit-level drivers built on it;
   * partition.py — the paper's circuit partition (Algorithm 1, Sec. 4.1);
   * closed_forms.py — closed-form final states used as pins.
 
@@ -18,6 +18,10 @@ Parity status per function (what pins it is in tests/test_oracle_*.py):
   qsz_encode/decode   pinned: point-wise bound on every value, round trip equals
                       the quantised input, hand-assembled streams of the format
                       (tests/golden/), worst-case size formula, corruption checks.
+  qszr_encode/decode  pinned: point-wise relative bound on every normal value
+                      (Eq. 1-2), exact zeros and signs, the shift against its
+                      defining inequality, a stream assembled by hand in the
+                      test, sign-chunk elision lengths, idempotence, corruption.
   partition           pinned: invariants of Algorithm 1 plus hand-worked cases.
   mlp_*               pinned: central finite differences, closed-form linear case,
                       Adam against its published recurrence on a scalar.
@@ -68,6 +72,16 @@ def lib():
         L.oracle_qsz_encode.restype = ctypes.c_int
         L.oracle_qsz_decode.argtypes = [u8p, ctypes.c_uint64, ctypes.c_int, fp]
         L.oracle_qsz_decode.restype = ctypes.c_int
+        L.oracle_qszr_shift.argtypes = [ctypes.c_double, ip]
+        L.oracle_qszr_shift.restype = ctypes.c_int
+        L.oracle_qszr_worst_case_bytes.argtypes = [ctypes.c_int]
+        L.oracle_qszr_worst_case_bytes.restype = ctypes.c_uint64
+        L.oracle_qszr_quantize.argtypes = [fp, ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), u8p]
+        L.oracle_qszr_quantize.restype = ctypes.c_int
+        L.oracle_qszr_encode.argtypes = [fp, ctypes.c_int, ctypes.c_double, u8p, ctypes.c_uint64, u64p]
+        L.oracle_qszr_encode.restype = ctypes.c_int
+        L.oracle_qszr_decode.argtypes = [u8p, ctypes.c_uint64, ctypes.c_int, fp]
+        L.oracle_qszr_decode.restype = ctypes.c_int
         L.oracle_mlp_nparams.argtypes = []
         L.oracle_mlp_nparams.restype = ctypes.c_int
         L.oracle_mlp_forward.argtypes = [dp, dp, ctypes.c_int, dp]
@@ -212,6 +226,59 @@ def qsz_reconstruct(amps: np.ndarray, e: int) -> np.ndarray:
     """x' = q * 2^e for every component (what decode(encode(x)) returns)."""
     q = qsz_quantize(amps, e)
     return (q.astype(np.float64) * 2.0 ** e).astype(np.float32)
+
+
+def qszr_shift(rel: float) -> int:
+    """Quantisation shift k of the relative-bound codec (largest k with 2^(k-24) <= b_r / (1 + b_r))."""
+    k = ctypes.c_int()
+    rc = lib().oracle_qszr_shift(rel, ctypes.byref(k))
+    if rc:
+        raise OracleError(rc, "qszr_shift")
+    return k.value
+
+
+def qszr_worst_case_bytes(m: int) -> int:
+    return int(lib().oracle_qszr_worst_case_bytes(m))
+
+
+def qszr_quantize(x: np.ndarray, k: int):
+    """(codes, signs) of every component under shift k."""
+    x = np.ascontiguousarray(x, dtype=np.float32)
+    q = np.empty(x.size, dtype=np.int32)
+    s = np.empty(x.size, dtype=np.uint8)
+    rc = lib().oracle_qszr_quantize(_ptr(x, ctypes.c_float), x.size, k, _ptr(q, ctypes.c_int32),
+                                    _ptr(s, ctypes.c_uint8))
+    if rc:
+        raise OracleError(rc, "qszr_quantize")
+    return q, s
+
+
+def qszr_encode(amps: np.ndarray, m: int, rel: float, cap: Optional[int] = None) -> bytes:
+    """Encode 2^m interleaved complex64 amplitudes under the point-wise relative bound rel."""
+    a = np.ascontiguousarray(amps, dtype=np.float32)
+    if a.size != 2 << m:
+        raise ValueError("block size mismatch")
+    cap = qszr_worst_case_bytes(m) if cap is None else cap
+    out = np.zeros(max(cap, 1), dtype=np.uint8)
+    nb = ctypes.c_uint64()
+    rc = lib().oracle_qszr_encode(_ptr(a, ctypes.c_float), m, rel, _ptr(out, ctypes.c_uint8), cap,
+                                  ctypes.byref(nb))
+    if rc:
+        err = OracleError(rc, "qszr_encode")
+        err.needed = nb.value
+        raise err
+    return out[: nb.value].tobytes()
+
+
+def qszr_decode(stream: bytes, m: int) -> np.ndarray:
+    buf = np.frombuffer(stream, dtype=np.uint8).copy()
+    if buf.size == 0:
+        buf = np.zeros(1, dtype=np.uint8)
+    out = np.empty(2 << m, dtype=np.float32)
+    rc = lib().oracle_qszr_decode(_ptr(buf, ctypes.c_uint8), len(stream), m, _ptr(out, ctypes.c_float))
+    if rc:
+        raise OracleError(rc, "qszr_decode")
+    return out
 
 
 # --------------------------------------------------------------------------

@@ -12,6 +12,9 @@
  *   2. QSZ1 block codec, scalar (the project's own absolute-error-bounded
  *      format, standing in for the closed compressor the paper used in
  *      Sec. 4.3 / Sec. 5.1; the bound eb replaces the paper's relative bound).
+ *   2b. QSZR block codec, scalar (point-wise relative error bound, Sec. 4.3
+ *      Eq. 1-2 and Algorithm 2: sign bitmap with all-0 / all-1 chunk
+ *      elision, log-domain quantisation of |x|).
  *   3. Size-predictor MLP, float64 forward / backward / Adam step.
  *
  * Build: gcc -O2 -fopenmp -shared -fPIC (see oracle/build.py).
@@ -456,6 +459,294 @@ int oracle_qsz_decode(const uint8_t *in, uint64_t in_bytes, int m, float *amps)
                 for (int j = 0; j < 32; ++j) {
                     acc += (uint32_t)unzigzag(zc[j]);
                     dst[2 * (c * 32 + j) + plane] = (float)(int32_t)acc * step;
+                }
+            }
+    }
+    return OR_OK;
+}
+
+/* ====================================================================== */
+/* 2b. QSZR codec (scalar): point-wise RELATIVE error bound (Sec. 4.3,      */
+/*     Eq. 1-2, Algorithm 2).                                                */
+/*                                                                           */
+/* Algorithm 2 records each value's sign in a bitmap, takes |x|, applies     */
+/* log2 and compresses the logs under an absolute bound b_a. Here the log2   */
+/* of |x| is read off its FP32 bit pattern U = bits(|x|): for a normal       */
+/* x = 2^E (1 + M 2^-23), U = (E + 127) 2^23 + M, i.e. 2^23 (E + M 2^-23)    */
+/* plus a constant, where E + M 2^-23 is log2|x| with the fraction taken     */
+/* linearly (Mitchell's approximation). Its slope d|x| / dL = 2^E <= |x|,    */
+/* so an absolute error delta on L moves |x| by at most delta |x| (and by at */
+/* most delta / (1 - delta/2) across a binade edge). Quantising U with step  */
+/* 2^k, k the largest integer with 2^(k-24) <= b_r / (1 + b_r), therefore    */
+/* bounds every normal value's relative error by b_r; Eq. 2's              */
+/* b_a = log2(1 + b_r) is the same statement for the exact log2. Integer     */
+/* codes keep encoder and decoder exact without a transcendental function.   */
+/* Subnormal values (|x| < 2^-126) get an absolute error <= 2^(k-150).       */
+/*                                                                           */
+/* Per component x: U = bits(|x|); q = (U + 2^(k-1)) >> k; sign s = 1 iff    */
+/* x < 0 and q != 0 (Algorithm 2's bitmap: 1 marks a negative value; a value */
+/* that reconstructs to zero keeps sign 0); reconstruction |x'| = float with */
+/* bits q << k, x' = s ? -|x'| : |x'|. Non-finite x: invalid; |x| >= 2^64:   */
+/* out of range.                                                             */
+/*                                                                           */
+/* Stream: header 32 B as QSZ1 but magic 0x525A5351 ("QSZR") and byte 10 =  */
+/* k; offsets[nframes + 1] padded to 16 B; frames of F = min(4096, 2^m)     */
+/* amplitudes, C = F/32 chunks per plane, chunk index t = plane*C + chunk.   */
+/* Codes q run through the QSZ1 chunk pipeline (Lorenzo delta, zigzag, width,*/
+/* bit planes). A frame whose codes are all zero has length 0. Otherwise:    */
+/*   u8 widths[2C], padded to 16 B;                                          */
+/*   sign chunk types, 2 bits per chunk t (byte t/4, bits 2(t%4)): 0 = all   */
+/*     32 signs 0, 1 = all 32 signs 1, 2 = mixed (the pre-scan of the sign   */
+/*     bitmap that drops all-0 and all-1 chunks), padded to 16 B;            */
+/*   the sign word (bit j = sign of value j) of every mixed chunk, in t      */
+/*     order, u32 each, padded to 16 B;                                      */
+/*   the code bit planes as in QSZ1, padded to 16 B.                         */
+/* ====================================================================== */
+
+#define QSZR_MAGIC 0x525A5351u
+#define QSZR_K_MIN 1
+#define QSZR_K_MAX 22
+
+/* Largest k with 2^(k-24) <= b_r / (1 + b_r), in [QSZR_K_MIN, QSZR_K_MAX]. */
+int oracle_qszr_shift(double rel, int *k_out)
+{
+    if (!(rel > 0.0) || !(rel < 1.0))
+        return OR_E_INVALID;
+    const double t = ldexp(rel / (1.0 + rel), 24);
+    int x;
+    (void)frexp(t, &x); /* t = f 2^x, f in [0.5, 1): floor(log2 t) = x - 1 */
+    int k = x - 1;
+    while (k > QSZR_K_MIN - 1 && ldexp(1.0, k - 24) > rel / (1.0 + rel)) --k; /* guard the rounding of t */
+    if (k < QSZR_K_MIN || k > QSZR_K_MAX)
+        return OR_E_INVALID;
+    *k_out = k;
+    return OR_OK;
+}
+
+uint64_t oracle_qszr_worst_case_bytes(int m)
+{
+    int fl = frame_log_for(m);
+    uint64_t F = 1ULL << fl, nframes = 1ULL << (m - fl), C = F / 32;
+    return QSZ_HEADER + pad16(4 * (nframes + 1)) +
+           nframes * (pad16(2 * C) + pad16((2 * C + 3) / 4) + pad16(8 * C) + 8 * F);
+}
+
+static uint32_t f32_bits_or(float f)
+{
+    uint32_t u;
+    memcpy(&u, &f, 4);
+    return u;
+}
+static float bits_f32_or(uint32_t u)
+{
+    float f;
+    memcpy(&f, &u, 4);
+    return f;
+}
+
+/* Codes and signs of `count` components with shift k. */
+int oracle_qszr_quantize(const float *x, int64_t count, int k, int32_t *q, uint8_t *sign)
+{
+    for (int64_t i = 0; i < count; ++i) {
+        if (!isfinite(x[i]))
+            return OR_E_INVALID;
+        const uint32_t U = f32_bits_or(x[i]) & 0x7FFFFFFFu;
+        if (U >= 0x5F800000u) /* |x| >= 2^64 */
+            return OR_E_RANGE;
+        const uint32_t c = (U + (1u << (k - 1))) >> k;
+        q[i] = (int32_t)c;
+        sign[i] = (uint8_t)(x[i] < 0.0f && c != 0);
+    }
+    return OR_OK;
+}
+
+int oracle_qszr_encode(const float *amps, int m, double rel, uint8_t *out, uint64_t cap, uint64_t *out_bytes)
+{
+    if (m < QSZ_MIN_M || m > QSZ_MAX_M)
+        return OR_E_INVALID;
+    int k;
+    int rc = oracle_qszr_shift(rel, &k);
+    if (rc)
+        return rc;
+    const int fl = frame_log_for(m);
+    const int64_t N = 1LL << m, F = 1LL << fl, C = F / 32, nframes = N / F, NC = N / 32;
+    int32_t *q = (int32_t *)malloc(sizeof(int32_t) * 2 * N);  /* plane-major */
+    uint8_t *sg = (uint8_t *)malloc((size_t)(2 * N));
+    float *tmp = (float *)malloc(sizeof(float) * N);
+    uint32_t *z = (uint32_t *)malloc(sizeof(uint32_t) * 2 * N);
+    uint8_t *w = (uint8_t *)malloc((size_t)(2 * NC));
+    uint32_t *sw = (uint32_t *)malloc(sizeof(uint32_t) * 2 * NC); /* sign word per chunk */
+    uint64_t *offs = (uint64_t *)malloc(sizeof(uint64_t) * (nframes + 1));
+    if (!q || !sg || !tmp || !z || !w || !sw || !offs) {
+        free(q); free(sg); free(tmp); free(z); free(w); free(sw); free(offs);
+        return OR_E_INVALID;
+    }
+    for (int plane = 0; plane < 2 && !rc; ++plane) {
+        for (int64_t i = 0; i < N; ++i) tmp[i] = amps[2 * i + plane];
+        rc = oracle_qszr_quantize(tmp, N, k, q + plane * N, sg + plane * N);
+    }
+    free(tmp);
+    if (rc) {
+        free(q); free(sg); free(z); free(w); free(sw); free(offs);
+        return rc;
+    }
+    for (int plane = 0; plane < 2; ++plane)
+        for (int64_t ch = 0; ch < NC; ++ch) {
+            uint32_t acc = 0, s = 0;
+            for (int j = 0; j < 32; ++j) {
+                const int64_t i = plane * N + ch * 32 + j;
+                const int32_t d = j == 0 ? q[i] : (int32_t)((uint32_t)q[i] - (uint32_t)q[i - 1]);
+                z[i] = zigzag(d);
+                acc |= z[i];
+                s |= (uint32_t)sg[i] << j;
+            }
+            w[plane * NC + ch] = (uint8_t)bit_length(acc);
+            sw[plane * NC + ch] = s;
+        }
+    free(q); free(sg);
+    const uint64_t data_start = QSZ_HEADER + pad16(4 * (uint64_t)(nframes + 1));
+    const uint64_t tbytes = (uint64_t)(2 * C + 3) / 4;
+    uint64_t pos = data_start;
+    for (int64_t f = 0; f < nframes; ++f) {
+        offs[f] = pos;
+        uint64_t words = 0, mixed = 0;
+        for (int plane = 0; plane < 2; ++plane)
+            for (int64_t c = 0; c < C; ++c) {
+                const int64_t t = plane * NC + f * C + c;
+                words += w[t];
+                mixed += sw[t] != 0 && sw[t] != 0xFFFFFFFFu;
+            }
+        if (words)
+            pos += pad16(2 * C) + pad16(tbytes) + pad16(4 * mixed) + pad16(4 * words);
+    }
+    offs[nframes] = pos;
+    *out_bytes = pos;
+    if (pos > cap) {
+        free(z); free(w); free(sw); free(offs);
+        return OR_E_CAPACITY;
+    }
+    memset(out, 0, pos);
+    put_u32(out + 0, QSZR_MAGIC);
+    put_u16(out + 4, 1);
+    put_u16(out + 6, 0);
+    out[8] = (uint8_t)m;
+    out[9] = (uint8_t)fl;
+    out[10] = (uint8_t)k;
+    out[11] = 0;
+    put_u32(out + 12, (uint32_t)nframes);
+    put_u64(out + 16, pos);
+    put_u64(out + 24, 0);
+    for (int64_t f = 0; f <= nframes; ++f)
+        put_u32(out + QSZ_HEADER + 4 * f, (uint32_t)offs[f]);
+    for (int64_t f = 0; f < nframes; ++f) {
+        if (offs[f + 1] == offs[f])
+            continue;
+        uint8_t *fp = out + offs[f];
+        for (int plane = 0; plane < 2; ++plane)
+            for (int64_t c = 0; c < C; ++c)
+                fp[plane * C + c] = w[plane * NC + f * C + c];
+        uint8_t *tp = fp + pad16(2 * C);
+        uint8_t *mp = tp + pad16(tbytes);
+        uint64_t mixed = 0;
+        for (int plane = 0; plane < 2; ++plane)
+            for (int64_t c = 0; c < C; ++c) {
+                const int64_t t = plane * C + c;
+                const uint32_t s = sw[plane * NC + f * C + c];
+                const uint32_t type = s == 0 ? 0u : s == 0xFFFFFFFFu ? 1u : 2u;
+                tp[t / 4] |= (uint8_t)(type << (2 * (t % 4)));
+                if (type == 2)
+                    put_u32(mp + 4 * mixed++, s);
+            }
+        uint8_t *wp = mp + pad16(4 * mixed);
+        for (int plane = 0; plane < 2; ++plane)
+            for (int64_t c = 0; c < C; ++c) {
+                const int64_t ch = f * C + c;
+                const int wc = w[plane * NC + ch];
+                for (int b = 0; b < wc; ++b) {
+                    uint32_t word = 0;
+                    for (int j = 0; j < 32; ++j)
+                        word |= ((z[plane * N + ch * 32 + j] >> b) & 1u) << j;
+                    put_u32(wp, word);
+                    wp += 4;
+                }
+            }
+    }
+    free(z); free(w); free(sw); free(offs);
+    return OR_OK;
+}
+
+int oracle_qszr_decode(const uint8_t *in, uint64_t in_bytes, int m, float *amps)
+{
+    if (m < QSZ_MIN_M || m > QSZ_MAX_M)
+        return OR_E_INVALID;
+    if (in_bytes < QSZ_HEADER || get_u32(in) != QSZR_MAGIC || get_u16(in + 4) != 1 || get_u16(in + 6) != 0)
+        return OR_E_CORRUPT;
+    const int fl = frame_log_for(m);
+    const int64_t N = 1LL << m, F = 1LL << fl, C = F / 32, nframes = N / F;
+    const int k = in[10];
+    const uint64_t total = get_u64(in + 16);
+    if (in[8] != m || in[9] != fl || in[11] != 0 || get_u32(in + 12) != (uint32_t)nframes ||
+        get_u64(in + 24) != 0 || k < QSZR_K_MIN || k > QSZR_K_MAX)
+        return OR_E_CORRUPT;
+    const uint64_t data_start = QSZ_HEADER + pad16(4 * (uint64_t)(nframes + 1));
+    if (total > in_bytes || total < data_start)
+        return OR_E_CORRUPT;
+    if (get_u32(in + QSZ_HEADER) != data_start || get_u32(in + QSZ_HEADER + 4 * nframes) != total)
+        return OR_E_CORRUPT;
+    const uint64_t tbytes = (uint64_t)(2 * C + 3) / 4;
+    for (int64_t f = 0; f < nframes; ++f) {
+        const uint64_t a = get_u32(in + QSZ_HEADER + 4 * f), b = get_u32(in + QSZ_HEADER + 4 * (f + 1));
+        if (b < a || b > total)
+            return OR_E_CORRUPT;
+        float *dst = amps + 2 * f * F;
+        if (a == b) {
+            for (int64_t i = 0; i < 2 * F; ++i) dst[i] = 0.0f;
+            continue;
+        }
+        const uint8_t *fp = in + a;
+        if (b - a < pad16(2 * C) + pad16(tbytes))
+            return OR_E_CORRUPT;
+        uint64_t words = 0, mixed = 0;
+        for (int64_t t = 0; t < 2 * C; ++t) {
+            if (fp[t] > 32)
+                return OR_E_CORRUPT;
+            words += fp[t];
+        }
+        const uint8_t *tp = fp + pad16(2 * C);
+        for (int64_t t = 0; t < 2 * C; ++t) {
+            const uint32_t type = (tp[t / 4] >> (2 * (t % 4))) & 3u;
+            if (type == 3)
+                return OR_E_CORRUPT;
+            mixed += type == 2;
+        }
+        if (words == 0 || b - a != pad16(2 * C) + pad16(tbytes) + pad16(4 * mixed) + pad16(4 * words))
+            return OR_E_CORRUPT;
+        const uint8_t *mp = tp + pad16(tbytes);
+        const uint8_t *wp = mp + pad16(4 * mixed);
+        for (int plane = 0; plane < 2; ++plane)
+            for (int64_t c = 0; c < C; ++c) {
+                const int64_t t = plane * C + c;
+                const uint32_t type = (tp[t / 4] >> (2 * (t % 4))) & 3u;
+                uint32_t s = type == 0 ? 0u : 0xFFFFFFFFu;
+                if (type == 2) {
+                    s = get_u32(mp);
+                    mp += 4;
+                }
+                const int wc = fp[t];
+                uint32_t zc[32];
+                for (int j = 0; j < 32; ++j) zc[j] = 0;
+                for (int bb = 0; bb < wc; ++bb) {
+                    const uint32_t word = get_u32(wp);
+                    wp += 4;
+                    for (int j = 0; j < 32; ++j) zc[j] |= ((word >> j) & 1u) << bb;
+                }
+                uint32_t acc = 0;
+                for (int j = 0; j < 32; ++j) {
+                    acc += (uint32_t)unzigzag(zc[j]);
+                    if (acc > (0x5F800000u >> k)) /* no encoder writes a code above 2^64 / 2^k */
+                        return OR_E_CORRUPT;
+                    const float mag = bits_f32_or(acc << k);
+                    dst[2 * (c * 32 + j) + plane] = ((s >> j) & 1u) ? -mag : mag;
                 }
             }
     }
