@@ -69,8 +69,10 @@ typedef struct qsim_gate {
 #define QSIM_MODE_STREAMS 0u    /* SV groups round-robin over CUDA streams (Sec. 4.2) */
 #define QSIM_MODE_PERSISTENT 1u /* one persistent kernel per stage over a group queue */
 
-#define QSIM_CODEC_QSZ1 0u /* compressed blocks (the method) */
+#define QSIM_CODEC_QSZ1 0u /* compressed blocks under a point-wise absolute bound (the method) */
 #define QSIM_CODEC_NONE 1u /* raw complex64 blocks: the no-compression comparison run */
+#define QSIM_CODEC_QSZR 2u /* compressed blocks under a point-wise relative bound eps (Sec. 4.3,
+                              Eq. 1-2, Algorithm 2): streams mode with exact sizing only */
 
 #define QSIM_SIZING_EXACT 0u   /* a sizing pass computes each block's exact size first */
 #define QSIM_SIZING_PREDICT 1u /* learned size predictor reserves space; overflow re-encodes */
@@ -88,7 +90,7 @@ typedef struct qsim_config {
     uint32_t graph;       /* 1: capture each run's stage loop in a CUDA graph (persistent mode) */
     uint32_t tile_bits;   /* log2 amplitudes per shared-memory tile, 0 = default */
     uint32_t collect;     /* 1: log (features, compressed size) of every encoded block (predictor training) */
-    double eps;           /* eb = eps * 2^(-n/2) */
+    double eps;           /* QSZ1: eb = eps * 2^(-n/2); QSZR: the relative bound b_r, in (2^-23, 1) */
     uint64_t device_tier_cap_bytes; /* bytes of compressed blocks kept on the device; 0 = no cap */
     uint64_t init_basis;  /* initial basis state |init_basis> (Sec. 4.2 initialisation) */
     double predictor_margin; /* predictor reservation = 2^pred * (1 + margin) */
@@ -217,7 +219,10 @@ void qsim_state_free(qsim_state *st);
 
 /* Worst-case QSZ1 stream size for a block of 2^m amplitudes:
  * 32 + pad16(4 (nframes+1)) + nframes (pad16(2C) + 8F), F = min(4096, 2^m). */
+/* Largest stream of a 2^m-amplitude block: QSZ1 (absolute bound), and QSZR (relative bound). 0 if m is
+ * outside 5..26. */
 size_t qsim_worst_case_bytes(uint32_t m);
+size_t qsim_worst_case_bytes_rel(uint32_t m);
 
 /*
  * Compress one block of 2^m complex64 amplitudes (d_amps, device) under the
@@ -259,9 +264,27 @@ int qsim_compress_block_noalloc(const float *d_amps, uint32_t m, double eb, void
                                 size_t *out_bytes, void *cuda_stream);
 
 /*
- * Decompress a QSZ1 stream (d_in, device, in_bytes) into d_amps (device,
- * 2^m complex64). Synchronises cuda_stream to report the status.
- * Errors: INVALID, CORRUPT (bad magic/header/offsets/widths), CUDA.
+ * Compress one block of 2^m complex64 amplitudes (d_amps, device) under the
+ * point-wise RELATIVE bound rel (Sec. 4.3, Eq. 1-2; Algorithm 2's sign bitmap
+ * with all-0 / all-1 chunks stored as 2-bit types) into a QSZR stream in
+ * d_out (device, cap bytes). Every reconstructed component x' of a normal
+ * input x satisfies |x' - x| <= rel |x| with the sign of x kept; zeros stay
+ * zero; subnormal inputs get an absolute error below 2^(k-150) (k the code
+ * shift, the largest integer with 2^(k-24) <= rel / (1 + rel)).
+ * d_amps is not modified (the block is copied to library scratch, grown by
+ * cudaMalloc when a larger m is first used). Synchronises cuda_stream and
+ * writes the stream size to *out_bytes (host).
+ * Errors: INVALID (m outside 5..26, rel outside (2^-23, 1), NaN/Inf input),
+ * RANGE (|x| >= 2^64), CAPACITY (*out_bytes = the size needed), NOMEM, CUDA.
+ */
+int qsim_compress_block_rel(const float *d_amps, uint32_t m, double rel, void *d_out, size_t cap,
+                            size_t *out_bytes, void *cuda_stream);
+
+/*
+ * Decompress a QSZ1 or QSZR stream (d_in, device, in_bytes; the format is
+ * read from its magic number) into d_amps (device, 2^m complex64).
+ * Synchronises cuda_stream to report the status.
+ * Errors: INVALID, CORRUPT (bad magic/header/offsets/widths/sign types), CUDA.
  */
 int qsim_decompress_block(const void *d_in, size_t in_bytes, float *d_amps, uint32_t m,
                           void *cuda_stream);

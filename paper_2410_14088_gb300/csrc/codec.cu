@@ -33,7 +33,7 @@ namespace {
 using namespace cdev;
 
 // NP: the most leading phase ops the kernel applies (pre.count <= NP).
-template <int NP>
+template <int NP, bool REL>
 __global__ void __launch_bounds__(NT, 3) k_decode(const BlockRef *__restrict__ in, const BlockSlot *__restrict__ table,
                                                const uint32_t *__restrict__ ids, uint32_t nblocks, int m,
                                                float2 *__restrict__ wv, uint32_t *__restrict__ hist,
@@ -61,10 +61,10 @@ __global__ void __launch_bounds__(NT, 3) k_decode(const BlockRef *__restrict__ i
             sp = in[j].ptr;
             bytes = in[j].bytes;
         }
-        decode_frame_warp<NP>(sp, bytes, g, m, f, wv + (uint64_t(j) << m) + uint64_t(f) * g.F,
-                              hist ? hist + uint64_t(j) * 32 : nullptr, s_hist[warp], status, s_pre, s_pre_ab,
-                              pre.count, pre.mats, pre.count ? (uint64_t(j % pre.G) << m) : 0,
-                              pre.count ? pre.gbase[j / pre.G] : 0);
+        decode_frame_warp<NP, false, REL>(sp, bytes, g, m, f, wv + (uint64_t(j) << m) + uint64_t(f) * g.F,
+                                         hist ? hist + uint64_t(j) * 32 : nullptr, s_hist[warp], status, s_pre,
+                                         s_pre_ab, pre.count, pre.mats, pre.count ? (uint64_t(j % pre.G) << m) : 0,
+                                         pre.count ? pre.gbase[j / pre.G] : 0);
     }
 }
 
@@ -274,26 +274,31 @@ __global__ void __launch_bounds__(NT, 3) k_encode_size(const float2 *__restrict_
 // its length and word counts; the last CTA turns the frame lengths into frame
 // offsets, reserves each block's exact slot and folds the frames' error
 // partials into the blocks' and the stage's totals.
+// REL: the relative-bound format (e is the shift k, side records of kQszrSideBytes, mixed sign words counted
+// in fmixed). Without a device arena (dev.bump null) the targets are the caller's and nothing is reserved.
+template <bool REL>
 __global__ void __launch_bounds__(NT, 4) k_encode_ip(float2 *wv, uint32_t *__restrict__ im, uint32_t nblocks, int m,
                                                   int e, uint32_t *done_ctr, ArenaDev dev, ArenaDev host,
                                                   EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
                                                   StageAccum *acc, uint8_t *__restrict__ wrec,
                                                   uint32_t *__restrict__ flen, uint32_t *__restrict__ fwords,
-                                                  uint32_t *__restrict__ foff, float2 *__restrict__ part,
-                                                  int *status) {
+                                                  uint32_t *__restrict__ fmixed, uint32_t *__restrict__ foff,
+                                                  float2 *__restrict__ part, int *status) {
     const FrameGeom g = geom(m);
+    constexpr uint32_t kSide = REL ? kQszrSideBytes : 256u;
     __shared__ bool s_last;
     __shared__ double s_red[2][NW];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint64_t items = uint64_t(nblocks) * g.nframes;
     for (uint64_t item = uint64_t(blockIdx.x) * NW + warp; item < items; item += uint64_t(gridDim.x) * NW) {
         const uint32_t j = uint32_t(item / g.nframes), f = uint32_t(item % g.nframes);
-        uint32_t words;
-        const uint32_t len = encode_frame_warp_ip(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, im + item * g.F, g, e,
-                                                  wrec + item * 256, words, part + item, status);
+        uint32_t words, mixed;
+        const uint32_t len = encode_frame_warp_ip<REL>(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, im + item * g.F,
+                                                       g, e, wrec + item * kSide, words, mixed, part + item, status);
         if (lane == 0) {
             flen[item] = len;
             fwords[item] = words;
+            if (REL) fmixed[item] = mixed;
         }
     }
     if (tid == 0) {
@@ -337,7 +342,7 @@ __global__ void __launch_bounds__(NT, 4) k_encode_ip(float2 *wv, uint32_t *__res
             res[jb].overflow = 0;
             res[jb].err_sq = a;
             res[jb].norm_sq = b;
-            reserve_slot(run, dev, host, &tgt[jb], status);
+            if (dev.bump) reserve_slot(run, dev, host, &tgt[jb], status);
         }
         ta += a;
         tb += b;
@@ -360,21 +365,24 @@ __global__ void __launch_bounds__(NT, 4) k_encode_ip(float2 *wv, uint32_t *__res
 
 // In-place exact encoder, pass 2: one warp per frame copies the frame's
 // pieces to its offset in the block's slot.
+template <bool REL>
 __global__ void __launch_bounds__(NT) k_frame_copy(const float2 *__restrict__ wv, const uint32_t *__restrict__ im,
                                                    uint32_t nblocks, int m, int e, const EncTarget *__restrict__ tgt,
                                                    EncResult *__restrict__ res, const uint32_t *__restrict__ ids,
                                                    BlockSlot *__restrict__ table, StageAccum *acc,
                                                    const uint8_t *__restrict__ wrec, const uint32_t *__restrict__ flen,
                                                    const uint32_t *__restrict__ fwords,
+                                                   const uint32_t *__restrict__ fmixed,
                                                    const uint32_t *__restrict__ foff) {
     const FrameGeom g = geom(m);
+    constexpr uint32_t kSide = REL ? kQszrSideBytes : 256u;
     const int warp = threadIdx.x >> 5;
     const uint64_t items = uint64_t(nblocks) * g.nframes;
     for (uint64_t item = uint64_t(blockIdx.x) * NW + warp; item < items; item += uint64_t(gridDim.x) * NW) {
         const uint32_t j = uint32_t(item / g.nframes), f = uint32_t(item % g.nframes);
-        copy_frame_warp(reinterpret_cast<const uint32_t *>(wv + (uint64_t(j) << m) + uint64_t(f) * g.F),
-                        im + item * g.F, wrec + item * 256, fwords[item], flen[item], foff[item], g, m, e, f, tgt[j],
-                        res + j, table ? table + ids[j] : nullptr, acc);
+        copy_frame_warp<REL>(reinterpret_cast<const uint32_t *>(wv + (uint64_t(j) << m) + uint64_t(f) * g.F),
+                             im + item * g.F, wrec + item * kSide, fwords[item], REL ? fmixed[item] : 0u, flen[item],
+                             foff[item], g, m, e, f, tgt[j], res + j, table ? table + ids[j] : nullptr, acc);
     }
 }
 
@@ -472,23 +480,35 @@ static unsigned grid_for(uint64_t items, unsigned cap) {
 }
 
 void launch_decode(const BlockRef *in, uint32_t nblocks, int m, float2 *wv, uint32_t *hist, int *status,
-                   cudaStream_t s) {
+                   cudaStream_t s, bool rel) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
-    k_decode<0><<<grid_for((items + NW - 1) / NW, 152 * 8), NT, 0, s>>>(in, nullptr, nullptr, nblocks, m, wv, hist,
-                                                                      status, PreOps{});
+    const unsigned grid = grid_for((items + NW - 1) / NW, 152 * 8);
+    if (rel)
+        k_decode<0, true><<<grid, NT, 0, s>>>(in, nullptr, nullptr, nblocks, m, wv, hist, status, PreOps{});
+    else
+        k_decode<0, false><<<grid, NT, 0, s>>>(in, nullptr, nullptr, nblocks, m, wv, hist, status, PreOps{});
     count_launch();
 }
 
-void launch_decode_table(const BlockSlot *table, const uint32_t *ids, uint32_t nblocks, int m, float2 *wv,
+template <bool REL>
+static void decode_table(const BlockSlot *table, const uint32_t *ids, uint32_t nblocks, int m, float2 *wv,
                          uint32_t *hist, int *status, const PreOps &pre, cudaStream_t s) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
     const unsigned grid = grid_for((items + NW - 1) / NW, 152 * 8);
     if (pre.count == 0)
-        k_decode<0><<<grid, NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist, status, pre);
+        k_decode<0, REL><<<grid, NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist, status, pre);
     else if (pre.count <= 2)
-        k_decode<2><<<grid, NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist, status, pre);
+        k_decode<2, REL><<<grid, NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist, status, pre);
     else
-        k_decode<kMaxPreOps><<<grid, NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist, status, pre);
+        k_decode<kMaxPreOps, REL><<<grid, NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist, status, pre);
+}
+
+void launch_decode_table(const BlockSlot *table, const uint32_t *ids, uint32_t nblocks, int m, float2 *wv,
+                         uint32_t *hist, int *status, const PreOps &pre, cudaStream_t s, bool rel) {
+    if (rel)
+        decode_table<true>(table, ids, nblocks, m, wv, hist, status, pre, s);
+    else
+        decode_table<false>(table, ids, nblocks, m, wv, hist, status, pre, s);
     count_launch();
 }
 
@@ -526,19 +546,29 @@ void launch_encode_lbw(const float2 *wv, uint32_t nblocks, int m, int e, EncTarg
 void launch_encode_ip(float2 *wv, uint32_t *im, uint32_t nblocks, int m, int e, uint32_t *done_ctr,
                       const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, StageAccum *acc,
                       uint8_t *wrec, uint32_t *flen, uint32_t *fwords, uint32_t *foff, float2 *part, int *status,
-                      cudaStream_t s) {
+                      cudaStream_t s, bool rel, uint32_t *fmixed) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
-    k_encode_ip<<<grid_for((items + NW - 1) / NW, 152 * 8), NT, 0, s>>>(wv, im, nblocks, m, e, done_ctr, dev, host,
-                                                                      tgt, res, acc, wrec, flen, fwords, foff, part,
-                                                                      status);
+    const unsigned grid = grid_for((items + NW - 1) / NW, 152 * 8);
+    if (rel)
+        k_encode_ip<true><<<grid, NT, 0, s>>>(wv, im, nblocks, m, e, done_ctr, dev, host, tgt, res, acc, wrec, flen,
+                                              fwords, fmixed, foff, part, status);
+    else
+        k_encode_ip<false><<<grid, NT, 0, s>>>(wv, im, nblocks, m, e, done_ctr, dev, host, tgt, res, acc, wrec, flen,
+                                               fwords, fmixed, foff, part, status);
     count_launch();
 }
 void launch_frame_copy(const float2 *wv, const uint32_t *im, uint32_t nblocks, int m, int e, const EncTarget *tgt,
                        EncResult *res, const uint32_t *ids, BlockSlot *table, StageAccum *acc, const uint8_t *wrec,
-                       const uint32_t *flen, const uint32_t *fwords, const uint32_t *foff, cudaStream_t s) {
+                       const uint32_t *flen, const uint32_t *fwords, const uint32_t *foff, cudaStream_t s, bool rel,
+                       const uint32_t *fmixed) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
-    k_frame_copy<<<grid_for((items + NW - 1) / NW, 152 * 16), NT, 0, s>>>(wv, im, nblocks, m, e, tgt, res, ids,
-                                                                        table, acc, wrec, flen, fwords, foff);
+    const unsigned grid = grid_for((items + NW - 1) / NW, 152 * 16);
+    if (rel)
+        k_frame_copy<true><<<grid, NT, 0, s>>>(wv, im, nblocks, m, e, tgt, res, ids, table, acc, wrec, flen, fwords,
+                                               fmixed, foff);
+    else
+        k_frame_copy<false><<<grid, NT, 0, s>>>(wv, im, nblocks, m, e, tgt, res, ids, table, acc, wrec, flen, fwords,
+                                                fmixed, foff);
     count_launch();
 }
 

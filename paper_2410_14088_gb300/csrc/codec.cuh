@@ -69,8 +69,9 @@ struct LookbackScratch {
 
 void count_launch();
 
+// rel: the stream is QSZR (relative bound) rather than QSZ1
 void launch_decode(const BlockRef *in, uint32_t nblocks, int m, float2 *wv, uint32_t *hist, int *status,
-                   cudaStream_t s);
+                   cudaStream_t s, bool rel = false);
 void launch_encode(const float2 *wv, uint32_t nblocks, int m, int e, const EncTarget *tgt, EncResult *res,
                    int only_overflowed, const uint32_t *ids, BlockSlot *table, StageAccum *acc,
                    const LookbackScratch &scr, int *status, cudaStream_t s);
@@ -88,13 +89,16 @@ void launch_encode_lbw(const float2 *wv, uint32_t nblocks, int m, int e, EncTarg
 // In-place exact encoder: pass 1 encodes every frame over its own amplitudes (Im-plane words to im, 4 bytes
 // per amplitude), records the frames' lengths, word counts (fwords) and offsets and reserves each block's
 // exact slot; pass 2 (launch_frame_copy) copies the frames into the slots. wv is overwritten.
+// rel: QSZR (e is the shift k, wrec holds kQszrSideBytes per frame, fmixed one word per frame); without a
+// device arena (dev.bump null) tgt is the caller's and nothing is reserved.
 void launch_encode_ip(float2 *wv, uint32_t *im, uint32_t nblocks, int m, int e, uint32_t *done_ctr,
                       const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, StageAccum *acc,
                       uint8_t *wrec, uint32_t *flen, uint32_t *fwords, uint32_t *foff, float2 *part, int *status,
-                      cudaStream_t s);
+                      cudaStream_t s, bool rel = false, uint32_t *fmixed = nullptr);
 void launch_frame_copy(const float2 *wv, const uint32_t *im, uint32_t nblocks, int m, int e, const EncTarget *tgt,
                        EncResult *res, const uint32_t *ids, BlockSlot *table, StageAccum *acc, const uint8_t *wrec,
-                       const uint32_t *flen, const uint32_t *fwords, const uint32_t *foff, cudaStream_t s);
+                       const uint32_t *flen, const uint32_t *fwords, const uint32_t *foff, cudaStream_t s,
+                       bool rel = false, const uint32_t *fmixed = nullptr);
 // leading phase ops of a stage for the decoder (count <= kMaxPreOps)
 struct OpDev;
 struct PreOps {
@@ -106,7 +110,7 @@ struct PreOps {
 };
 // decode with the block references read from table[ids[j]]
 void launch_decode_table(const BlockSlot *table, const uint32_t *ids, uint32_t nblocks, int m, float2 *wv,
-                         uint32_t *hist, int *status, const PreOps &pre, cudaStream_t s);
+                         uint32_t *hist, int *status, const PreOps &pre, cudaStream_t s, bool rel = false);
 // pending (nullable): zeroed by a first reservation, counts the blocks re-reserved by retry_overflowed
 void launch_reserve(uint32_t nblocks, const uint64_t *need, uint64_t add_const, const float *pred_log2,
                     double margin, uint64_t worst, const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt,

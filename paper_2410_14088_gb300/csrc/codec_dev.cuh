@@ -42,6 +42,14 @@ __device__ __forceinline__ FrameGeom geom(int m) {
     return g;
 }
 
+// QSZR (relative bound): per-frame side record of the in-place encoder (widths at 0, sign chunk types at
+// kSideTypes, Re and Im mixed sign words at kSideMixRe / kSideMixIm) and the code range (|x| < 2^64)
+constexpr uint32_t kSideTypes = 256, kSideMixRe = 320, kSideMixIm = 832;
+constexpr uint32_t kQszrMaxU = 0x5F800000u;
+
+// sign chunk type: 0 all clear, 1 all set, 2 mixed
+__device__ __forceinline__ uint32_t sign_type(uint32_t w) { return w == 0u ? 0u : (w == 0xFFFFFFFFu ? 1u : 2u); }
+
 __device__ __forceinline__ uint32_t zigzag(int32_t d) {
     return (uint32_t(d) << 1) ^ uint32_t(d >> 31);
 }
@@ -123,8 +131,12 @@ __device__ __forceinline__ float2 pre_chunk(float2 v, const uint32_t (&cl)[NP > 
 // the chunk offsets with a warp prefix sum, then decodes the chunk pairs
 // (Re chunk c, Im chunk c) eight at a time with all sixteen payload loads in
 // flight: bit-plane transpose, zigzag inverse, inclusive prefix sum (the
-// Lorenzo inverse), x' = q * 2^e, interleaved (re, im) stores.
-template <int NP, bool CG = false>
+// Lorenzo inverse), x' = q * 2^e, interleaved (re, im) stores. With REL the
+// stream is QSZR: the header's exponent byte is the shift k, the frame adds
+// the sign chunk types (lanes 0.. hold the types of chunks 16l..16l+15, the
+// mixed chunks ranked by a warp prefix sum) and the mixed sign words, and
+// x' = +-float(bits q << k).
+template <int NP, bool CG = false, bool REL = false>
 __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t bytes, const FrameGeom &g, int m,
                                                   uint32_t f, float2 *__restrict__ dst, uint32_t *hist_j,
                                                   uint32_t *s_hist_w, int *status, const OpDev *pre_ops,
@@ -151,15 +163,17 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
     const uint64_t rsv = uint64_t(__shfl_sync(kFull, hv, 6)) | (uint64_t(__shfl_sync(kFull, hv, 7)) << 32);
     const uint32_t o0 = __shfl_sync(kFull, hv, 8), fa = __shfl_sync(kFull, hv, 9);
     const uint32_t fb = __shfl_sync(kFull, hv, 10), on = __shfl_sync(kFull, hv, 11);
-    const int e = int(int8_t(uint8_t(w2 >> 16)));
-    bool ok = can && magic == kQszMagic && w1 == 1u && (w2 & 0xff) == uint32_t(m) &&
+    const int e = REL ? int(uint8_t(w2 >> 16)) : int(int8_t(uint8_t(w2 >> 16)));
+    const uint32_t tbp = REL ? ((((2u * g.C + 3u) / 4u) + 15u) & ~15u) : 0u;  // sign chunk types, padded
+    bool ok = can && magic == (REL ? kQszrMagic : kQszMagic) && w1 == 1u && (w2 & 0xff) == uint32_t(m) &&
               ((w2 >> 8) & 0xff) == uint32_t(g.fl) && (w2 >> 24) == 0 && nfr == g.nframes && rsv == 0 &&
-              e >= kQszEMin && e <= kQszEMax && total <= bytes && total >= g.data_start &&
-              o0 == g.data_start && on == total && fb >= fa && fb <= total && fa >= g.data_start &&
-              !((fa | fb) & 15u) && (fb == fa || fb - fa >= padw);
+              (REL ? (e >= kQszrKMin && e <= kQszrKMax) : (e >= kQszEMin && e <= kQszEMax)) && total <= bytes &&
+              total >= g.data_start && o0 == g.data_start && on == total && fb >= fa && fb <= total &&
+              fa >= g.data_start && !((fa | fb) & 15u) && (fb == fa || fb - fa >= padw + tbp);
     uint32_t wsum = 0, wmax = 0;
     uint2 wb = make_uint2(0, 0);
     uint32_t base_off = 0;
+    uint32_t tw = 0, mbase = 0, nmix = 0;  // REL: sign chunk types of chunks 16 lane.., mixed ranks
     if (ok && fb > fa) {
         // ---- widths: lane l holds chunks 8l .. 8l+7 (Re chunks 0..C-1, then Im chunks) ----
         if (8u * lane < 2u * g.C) wb = *reinterpret_cast<const uint2 *>(sp + fa + 8u * lane);
@@ -178,7 +192,23 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
         base_off = incl - wsum;
         const uint32_t words = __shfl_sync(kFull, incl, 31);
         const uint32_t maxw = __reduce_max_sync(kFull, wmax);
-        ok = maxw <= 32 && words > 0 && uint64_t(fb - fa) == padw + ((4ull * words + 15) & ~15ull);
+        bool tok = true;
+        if constexpr (REL) {
+            if (16u * uint32_t(lane) < 2u * g.C) tw = *reinterpret_cast<const uint32_t *>(sp + fa + padw + 4u * lane);
+            const uint32_t hi = tw & 0xAAAAAAAAu;  // type 2 (mixed) sets the odd bit alone; type 3 is invalid
+            tok = __all_sync(kFull, (hi & (tw << 1)) == 0u);
+            const uint32_t cnt = __popc(hi);
+            uint32_t mi = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(kFull, mi, o);
+                if (lane >= o) mi += t;
+            }
+            mbase = mi - cnt;
+            nmix = __shfl_sync(kFull, mi, 31);
+        }
+        ok = tok && maxw <= 32 && words > 0 &&
+             uint64_t(fb - fa) == padw + tbp + ((4ull * nmix + 15) & ~15ull) + ((4ull * words + 15) & ~15ull);
     }
     if (!ok) {
         if (lane == 0) raise_status(status, QSIM_E_CORRUPT);
@@ -189,8 +219,11 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
         if (hist_j && lane == 0) atomicAdd(&hist_j[0], 2 * g.F);
         return;
     }
-    const uint32_t *payload = reinterpret_cast<const uint32_t *>(sp + fa + padw);
-    const float step = exp2i(e);
+    const uint32_t *mixw = reinterpret_cast<const uint32_t *>(sp + fa + padw + tbp);
+    const uint32_t *payload =
+        reinterpret_cast<const uint32_t *>(sp + fa + padw + tbp + (REL ? ((4u * nmix + 15u) & ~15u) : 0u));
+    const float step = REL ? 0.f : exp2i(e);
+    bool qbad = false;
     uint32_t pre[NP > 0 ? NP : 1];
     if (NP > 0 && npre) pre_frame<NP>(pre, pre_ops, npre, wbase | (uint64_t(f) * g.F), g.fl, lane, gb, mats);
     // ---- chunk pairs, eight at a time ----
@@ -203,6 +236,14 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
         // Im chunks of a small frame (C < 8) share the owner lane with the Re chunks: skip those slots
         const uint32_t si0 = (g.C + c0) & 7u;
         uint32_t xr[8], xi[8], wr[8], wi[8];
+        // REL: sign chunk types of this batch (owners c0/16 and (C+c0)/16) and the mixed ranks before them
+        uint32_t twr = 0, twi = 0, mbr = 0, mbi = 0;
+        if constexpr (REL) {
+            twr = __shfl_sync(kFull, tw, c0 >> 4);
+            mbr = __shfl_sync(kFull, mbase, c0 >> 4);
+            twi = __shfl_sync(kFull, tw, (g.C + c0) >> 4);
+            mbi = __shfl_sync(kFull, mbase, (g.C + c0) >> 4);
+        }
         {
             uint32_t sr_ = 0, si_ = 0;
 #pragma unroll
@@ -254,8 +295,21 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
                 const uint32_t ti = __shfl_up_sync(kFull, qi, o);
                 if (lane >= o) { qr += tr; qi += ti; }
             }
-            const int32_t sr = int32_t(qr), si = int32_t(qi);
-            float2 v = make_float2(float(sr) * step, float(si) * step);
+            float2 v;
+            if constexpr (REL) {
+                // sign words: all clear, all set, or the chunk's stored word (its rank among the mixed chunks)
+                const uint32_t pr = 2u * (c & 15u), pi = 2u * ((g.C + c) & 15u);
+                const uint32_t tr = (twr >> pr) & 3u, ti = (twi >> pi) & 3u;
+                uint32_t swr = tr ? 0xFFFFFFFFu : 0u, swi = ti ? 0xFFFFFFFFu : 0u;
+                if (tr == 2u) swr = __ldg(mixw + mbr + __popc(twr & 0xAAAAAAAAu & ((1u << pr) - 1u)));
+                if (ti == 2u) swi = __ldg(mixw + mbi + __popc(twi & 0xAAAAAAAAu & ((1u << pi) - 1u)));
+                qbad |= qr > (kQszrMaxU >> e) || qi > (kQszrMaxU >> e);
+                const float mr = __uint_as_float(qr << e), mi = __uint_as_float(qi << e);
+                v = make_float2(((swr >> lane) & 1u) ? -mr : mr, ((swi >> lane) & 1u) ? -mi : mi);
+            } else {
+                const int32_t sr = int32_t(qr), si = int32_t(qi);
+                v = make_float2(float(sr) * step, float(si) * step);
+            }
             if (NP > 0 && npre) v = pre_chunk<NP>(v, pre, pre_ab, npre, c, mats);
             dst[c * 32 + lane] = v;
             if (hist_j && lane == 0) {  // the chunk's code widths, 32 values each
@@ -264,6 +318,7 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
             }
         }
     }
+    if (REL && __any_sync(kFull, qbad) && lane == 0) raise_status(status, QSIM_E_CORRUPT);
     if (hist_j) {
         __syncwarp();
         const uint32_t v = s_hist_w[lane];
@@ -663,6 +718,8 @@ __device__ __forceinline__ void store_widths_warp(uint8_t *dst, const FrameGeom 
     }
 }
 
+__device__ __forceinline__ uint64_t pad16d(uint64_t x) { return (x + 15u) & ~uint64_t(15); }
+
 __device__ __forceinline__ uint32_t frame_len(const FrameGeom &g, uint32_t words) {
     const uint32_t padw = (2u * g.C + 15u) & ~15u;
     return words ? padw + ((4u * words + 15u) & ~15u) : 0u;
@@ -842,22 +899,57 @@ __device__ __forceinline__ void encode_frame_warp_known(const float2 *__restrict
                                table_slot, acc, part_item, status);
 }
 
+// ---------------------------------------------------------------------------
+// Relative-bound variant (QSZR, Sec. 4.3 Eq. 1-2 and Algorithm 2). The code of
+// a component x is its FP32 magnitude bit pattern U = bits(|x|) (exponent plus
+// linear mantissa: log2|x| up to a scale and offset) rounded to a multiple of
+// 2^k: q = (U + 2^(k-1)) >> k; the sign (1 for x < 0 with q != 0) goes to a
+// per-chunk sign word W = ballot(sign), stored only for chunks whose signs are
+// mixed (2-bit chunk types: 0 all clear, 1 all set, 2 mixed). Reconstruction
+// |x'| = float(bits q << k).
+// ---------------------------------------------------------------------------
+
+// code of one component; bad collects QSIM_E_INVALID (non-finite, wins) or QSIM_E_RANGE
+template <bool REL>
+__device__ __forceinline__ int32_t quantize_one(float x, float inv_step, uint32_t k, int &bad) {
+    if constexpr (REL) {
+        const uint32_t U = __float_as_uint(x) & 0x7FFFFFFFu;
+        if (U >= kQszrMaxU) {
+            bad = U >= 0x7F800000u ? QSIM_E_INVALID : (bad ? bad : QSIM_E_RANGE);
+            return 0;
+        }
+        return int32_t((U + (1u << (k - 1))) >> k);
+    } else {
+        const float tq = x * inv_step;  // exact: power-of-two scaling
+        if (!(fabsf(tq) < 1073741824.0f)) {  // NaN, Inf or out of range
+            bad = isfinite(x) ? (bad ? bad : QSIM_E_RANGE) : QSIM_E_INVALID;
+            return 0;
+        }
+        return __float2int_rn(tq);
+    }
+}
+
 // In-place exact encoder, first of two passes: one warp reads frame f once
 // and writes its bit-plane words without knowing the frame's place in the
 // stream. The Re-plane words go over the frame's own amplitudes (the words of
 // chunk c end at or before byte 128 (c + 1) of the frame, and every chunk up
 // to c has been read by then), the Im-plane words to im (one word per
-// amplitude of scratch), the chunk widths to wrec (2C bytes). Returns the
-// frame's stream bytes; words receives its Re-plane words | Im-plane words << 16
-// (each at most 4096). The second pass (copy_frame_warp) moves the pieces to
-// the frame's offset in the block's slot.
+// amplitude of scratch), the chunk widths to side (2C bytes; for REL also the
+// sign chunk types and mixed sign words). Returns the frame's stream bytes;
+// words receives its Re-plane words | Im-plane words << 16 (each at most
+// 4096), mixed (REL) its Re | Im mixed sign chunks << 16. The second pass
+// (copy_frame_warp) moves the pieces to the frame's offset in the block's slot.
+// e is the step exponent (QSZ1) or the shift k (REL).
+template <bool REL = false>
 __device__ __forceinline__ uint32_t encode_frame_warp_ip(float2 *frame, uint32_t *__restrict__ im,
-                                                         const FrameGeom &g, int e, uint8_t *__restrict__ wrec,
-                                                         uint32_t &words, float2 *part_item, int *status) {
+                                                         const FrameGeom &g, int e, uint8_t *__restrict__ side,
+                                                         uint32_t &words, uint32_t &mixed, float2 *part_item,
+                                                         int *status) {
     const int lane = threadIdx.x & 31;
-    const float inv_step = exp2i(-e), step = exp2i(e);
+    const float inv_step = REL ? 0.f : exp2i(-e), step = REL ? 0.f : exp2i(e);
+    const uint32_t k = uint32_t(e);
     uint32_t *re = reinterpret_cast<uint32_t *>(frame);  // aliases frame: no __restrict__
-    uint32_t ro = 0, io = 0, wre = 0, wim = 0;
+    uint32_t ro = 0, io = 0, wre = 0, wim = 0, tw = 0, mr = 0, mi = 0;
     float err_sq = 0.f, norm_sq = 0.f;
     int bad = 0;
     for (uint32_t c0 = 0; c0 < g.C; c0 += 8) {
@@ -873,20 +965,36 @@ __device__ __forceinline__ uint32_t encode_frame_warp_ip(float2 *frame, uint32_t
             const uint32_t c = c0 + t;
             if (c >= g.C) break;
             int32_t q[2];
+            bool neg[2];
             const float x[2] = {vin[t].x, vin[t].y};
 #pragma unroll
             for (int pl = 0; pl < 2; ++pl) {
-                const float tq = x[pl] * inv_step;  // exact: power-of-two scaling
-                if (!(fabsf(tq) < 1073741824.0f)) {  // NaN, Inf or out of range
-                    bad = isfinite(x[pl]) ? (bad ? bad : QSIM_E_RANGE) : QSIM_E_INVALID;
-                    q[pl] = 0;
+                q[pl] = quantize_one<REL>(x[pl], inv_step, k, bad);
+                float xr;
+                if constexpr (REL) {
+                    neg[pl] = x[pl] < 0.f && q[pl] != 0;
+                    const float mag = __uint_as_float(uint32_t(q[pl]) << k);
+                    xr = neg[pl] ? -mag : mag;
                 } else {
-                    q[pl] = __float2int_rn(tq);
+                    xr = float(q[pl]) * step;
                 }
-                const float xr = float(q[pl]) * step;
                 const float dx = x[pl] - xr;
                 err_sq = fmaf(dx, dx, err_sq);
                 norm_sq = fmaf(xr, xr, norm_sq);
+            }
+            if constexpr (REL) {
+                // sign pre-scan: chunk types (owner lane t >> 4 of chunk index t = plane C + c), mixed words
+                const uint32_t sr = __ballot_sync(kFull, neg[0]), si = __ballot_sync(kFull, neg[1]);
+                const uint32_t tr = sign_type(sr), ti = sign_type(si);
+                const uint32_t ir = c, ii = g.C + c;
+                if (uint32_t(lane) == (ir >> 4)) tw |= tr << (2 * (ir & 15));
+                if (uint32_t(lane) == (ii >> 4)) tw |= ti << (2 * (ii & 15));
+                if (lane == 0) {
+                    if (tr == 2) reinterpret_cast<uint32_t *>(side + kSideMixRe)[mr] = sr;
+                    if (ti == 2) reinterpret_cast<uint32_t *>(side + kSideMixIm)[mi] = si;
+                }
+                mr += tr == 2;
+                mi += ti == 2;
             }
             const int32_t pr = __shfl_up_sync(kFull, q[0], 1);
             const int32_t pi = __shfl_up_sync(kFull, q[1], 1);
@@ -923,7 +1031,10 @@ __device__ __forceinline__ uint32_t encode_frame_warp_ip(float2 *frame, uint32_t
         }
     }
     if (bad) raise_status(status, bad);
-    store_widths_warp(wrec, g, wre, wim);
+    store_widths_warp(side, g, wre, wim);
+    if constexpr (REL) {
+        if (16u * uint32_t(lane) < 2u * g.C) reinterpret_cast<uint32_t *>(side + kSideTypes)[lane] = tw;
+    }
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
         err_sq += __shfl_xor_sync(kFull, err_sq, o);
@@ -931,20 +1042,26 @@ __device__ __forceinline__ uint32_t encode_frame_warp_ip(float2 *frame, uint32_t
     }
     if (lane == 0 && part_item) *part_item = make_float2(err_sq, norm_sq);
     words = ro | (io << 16);
-    return frame_len(g, ro + io);
+    mixed = mr | (mi << 16);
+    if (ro + io == 0) return 0u;
+    uint32_t len = frame_len(g, ro + io);
+    if constexpr (REL) len += uint32_t(pad16d((2u * g.C + 3u) / 4u) + pad16d(4u * (mr + mi)));
+    return len;
 }
 
-// Second pass of the in-place encoder: frame f's widths (wrec), Re-plane
-// words (re, 16-byte aligned) and Im-plane words (im) are copied to byte
-// offset frame_off of the block's slot and padded to 16 bytes; lane 0 writes
-// the frame's offset-table entry and, for the block's last frame, the header,
-// the block's table slot and the stage totals. words = Re words | Im words << 16.
-// A slot too small (only after a failed reservation) sets the block's
-// overflow flag instead.
+// Second pass of the in-place encoder: frame f's widths (and for REL its sign
+// chunk types and mixed sign words) from side, its Re-plane words (re, 16-byte
+// aligned) and Im-plane words (im) are copied to byte offset frame_off of the
+// block's slot and padded to 16 bytes; lane 0 writes the frame's offset-table
+// entry and, for the block's last frame, the header, the block's table slot
+// and the stage totals. words = Re words | Im words << 16, mixed = Re | Im
+// mixed sign chunks << 16. A slot too small (only after a failed reservation
+// or a caller's short buffer) sets the block's overflow flag instead.
+template <bool REL = false>
 __device__ __forceinline__ void copy_frame_warp(const uint32_t *__restrict__ re, const uint32_t *__restrict__ im,
-                                                const uint8_t *__restrict__ wrec, uint32_t words, uint32_t len,
-                                                uint32_t frame_off, const FrameGeom &g, int m, int e, uint32_t f,
-                                                EncTarget tgt, EncResult *res_j, BlockSlot *table_slot,
+                                                const uint8_t *__restrict__ side, uint32_t words, uint32_t mixed,
+                                                uint32_t len, uint32_t frame_off, const FrameGeom &g, int m, int e,
+                                                uint32_t f, EncTarget tgt, EncResult *res_j, BlockSlot *table_slot,
                                                 StageAccum *acc) {
     const uint32_t lane = threadIdx.x & 31;
     const uint32_t padw = (2u * g.C + 15u) & ~15u;
@@ -954,12 +1071,25 @@ __device__ __forceinline__ void copy_frame_warp(const uint32_t *__restrict__ re,
     const bool fits = out != nullptr && uint64_t(frame_off) + len <= cap;
     if (fits && len) {
         uint8_t *dst = out + frame_off;
-        const uint2 wb = load_widths_warp<true>(wrec, g);
+        const uint2 wb = load_widths_warp<true>(side, g);
         if (8u * lane < padw) *reinterpret_cast<uint2 *>(dst + 8u * lane) = wb;
+        uint32_t head = padw;
+        if constexpr (REL) {
+            // sign chunk types, then the mixed sign words (Re chunks first), each part padded to 16 bytes
+            const uint32_t tb = uint32_t(pad16d((2u * g.C + 3u) / 4u)), mre = mixed & 0xffffu, mim = mixed >> 16;
+            const uint32_t nmw = uint32_t(pad16d(4u * (mre + mim))) / 4u;
+            uint32_t *tdst = reinterpret_cast<uint32_t *>(dst + padw);
+            if (4u * lane < tb) tdst[lane] = 16u * lane < 2u * g.C ? __ldcg(reinterpret_cast<const uint32_t *>(side + kSideTypes) + lane) : 0u;
+            uint32_t *mdst = reinterpret_cast<uint32_t *>(dst + padw + tb);
+            for (uint32_t i = lane; i < nmw; i += 32)
+                mdst[i] = i < mre ? __ldcg(reinterpret_cast<const uint32_t *>(side + kSideMixRe) + i)
+                                  : (i < mre + mim ? __ldcg(reinterpret_cast<const uint32_t *>(side + kSideMixIm) + (i - mre)) : 0u);
+            head = padw + tb + 4u * nmw;
+        }
         // payload word i: Re word i (i < nre), Im word i - nre (i - nre < nim), else zero padding; written
         // as 16-byte vectors, four per lane in flight
-        uint4 *d4 = reinterpret_cast<uint4 *>(dst + padw);  // 16-byte aligned
-        const uint32_t n4 = (len - padw) / 16;
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst + head);  // 16-byte aligned
+        const uint32_t n4 = (len - head) / 16;
         for (uint32_t k0 = lane; k0 < n4; k0 += 128) {
             uint4 v[4];
 #pragma unroll
@@ -995,7 +1125,7 @@ __device__ __forceinline__ void copy_frame_warp(const uint32_t *__restrict__ re,
             if (res_j) res_j->total = total;
             if (out && total <= cap) {
                 uint32_t *h32 = reinterpret_cast<uint32_t *>(out);
-                h32[0] = kQszMagic;
+                h32[0] = REL ? kQszrMagic : kQszMagic;
                 h32[1] = 1u;  // version 1, flags 0
                 h32[2] = uint32_t(m) | (uint32_t(g.fl) << 8) | (uint32_t(uint8_t(int8_t(e))) << 16);
                 h32[3] = g.nframes;

@@ -251,6 +251,9 @@ struct DevBuf {
 // ---------------------------------------------------------------------------
 struct DeviceCtx {
     std::mutex mu;  // serialises the single-block entry points
+    // relative-bound block compression: a copy of the block, the Im-plane scratch and the per-frame records
+    uint8_t *rel_buf = nullptr;
+    size_t rel_cap = 0;
     int *status = nullptr;
     uint64_t *lb_state = nullptr;
     uint32_t *lb_ctr = nullptr;  // ticket, done, epoch
@@ -866,6 +869,7 @@ struct StreamWork {
     DevBuf<uint8_t> wrec;    // per frame: chunk widths recorded by the sizing pass
     DevBuf<uint32_t> flen, foff;  // per frame: stream bytes and offset
     DevBuf<uint32_t> fwords;      // per frame: Re words | Im words << 16 (in-place encoder)
+    DevBuf<uint32_t> fmixed;      // per frame: Re | Im mixed sign chunks << 16 (relative-bound codec)
     DevBuf<uint32_t> imsc;        // Im-plane words of the in-place encoder, one word per amplitude
 };
 
@@ -903,6 +907,7 @@ struct RunCtx {
     uint64_t nblocks = 0, nframes = 1;
     size_t nst = 0;
     bool raw = false, predict = false, collect = false, persistent = false;
+    bool rel = false;  // QSZR: point-wise relative bound; e is then the code shift k
     int e = 0;
     uint64_t worst = 0, slot_worst = 0;
     uint64_t need_per_parity = 0;  // every block at its worst-case size, plus the zero template
@@ -961,13 +966,17 @@ static int prepare_run(RunCtx &R, const qsim_plan *p, const DeviceCtx &dctx) {
     R.nblocks = 1ull << (R.n - R.m);
     R.nst = p->stages.size();
     R.raw = cfg.codec == QSIM_CODEC_NONE;
-    if (!R.raw && !qsz_step_exponent(cfg.eps * std::pow(2.0, -double(R.n) / 2.0), &R.e))
+    R.rel = cfg.codec == QSIM_CODEC_QSZR;
+    if (R.rel && (R.persistent || cfg.sizing != QSIM_SIZING_EXACT || cfg.collect))
+        return set_error(QSIM_E_UNSUPPORTED, "the relative-bound codec runs in streams mode with exact sizing");
+    if (R.rel ? !qszr_shift(cfg.eps, &R.e)
+              : (!R.raw && !qsz_step_exponent(cfg.eps * std::pow(2.0, -double(R.n) / 2.0), &R.e)))
         return set_error(QSIM_E_INVALID, "error bound out of range");
     R.predict = cfg.sizing == QSIM_SIZING_PREDICT && !R.raw;
     R.collect = cfg.collect != 0 && !R.raw;
     if (R.predict && !dctx.pred_ready)
         return set_error(QSIM_E_INVALID, "predictor sizing needs trained weights (qsim_predictor_train/set)");
-    R.worst = R.raw ? (8ull << R.m) : qsz_worst_case(R.m);
+    R.worst = R.raw ? (8ull << R.m) : (R.rel ? qszr_worst_case(R.m) : qsz_worst_case(R.m));
     R.slot_worst = (R.worst + 255) & ~255ull;
     R.nframes = R.raw ? 1 : qsz_nframes(R.m);
     R.need_per_parity = (R.nblocks + 1) * R.slot_worst;
@@ -1022,6 +1031,13 @@ static int init_store(RunCtx &R, StreamWork &w, int *status) {
         launch_reserve(2, nullptr, R.worst, nullptr, 0, R.worst, R.arena_dev(0), R.arena_host(0), w.tgt.p, w.res.p, 0,
                        status, w.s);
         launch_copy_out(w.wv.p, 2, m, w.tgt.p, R.init_ids.p, R.tmpl.p, nullptr, status, w.s);
+    } else if (R.rel) {
+        // the in-place encoder and its frame copy (relative-bound streams)
+        launch_encode_ip(w.wv.p, w.imsc.p, 2, int(m), R.e, w.lb_ctr.p + 3, R.arena_dev(0), R.arena_host(0), w.tgt.p,
+                         w.res.p, nullptr, w.wrec.p, w.flen.p, w.fwords.p, w.foff.p, w.part.p, status, w.s, true,
+                         w.fmixed.p);
+        launch_frame_copy(w.wv.p, w.imsc.p, 2, int(m), R.e, w.tgt.p, w.res.p, R.init_ids.p, R.tmpl.p, nullptr, w.wrec.p,
+                          w.flen.p, w.fwords.p, w.foff.p, w.s, true, w.fmixed.p);
     } else {
         launch_size_reserve(w.wv.p, 2, m, R.e, w.sizes.p, w.lb_ctr.p + 3, R.arena_dev(0), R.arena_host(0), w.tgt.p,
                             w.res.p, status, w.s);
@@ -1521,9 +1537,10 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             (rc = w.sizes.alloc(max_batch_blocks)) || (rc = w.lb_state.alloc(max_batch_blocks * nframes)) ||
             (rc = w.part.alloc(max_batch_blocks * nframes)) || (rc = w.hist.alloc(max_batch_blocks * 32)) ||
             (rc = w.pred.alloc(max_batch_blocks)) ||
-            (!persistent && (rc = w.wrec.alloc(max_batch_blocks * nframes * 256))) ||
+            (!persistent && (rc = w.wrec.alloc(max_batch_blocks * nframes * (RC.rel ? kQszrSideBytes : 256)))) ||
             (!persistent && !predict && !raw && (rc = w.imsc.alloc(max_batch_blocks << m))) ||
             (!persistent && (rc = w.fwords.alloc(max_batch_blocks * nframes))) ||
+            (RC.rel && (rc = w.fmixed.alloc(max_batch_blocks * nframes))) ||
             (rc = w.flen.alloc(max_batch_blocks * nframes)) || (rc = w.foff.alloc(max_batch_blocks * nframes)) ||
             (rc = w.lb_ctr.alloc(8))) {
             destroy_streams();
@@ -1620,7 +1637,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
                 pre.gbase = gb_stage + g0;
                 uint32_t *hist = (predict || collect) ? w.hist.p : nullptr;
                 if (hist) CUDA_TRY(cudaMemsetAsync(hist, 0, size_t(nb) * 32 * sizeof(uint32_t), w.s));
-                launch_decode_table(tab_in, ids, nb, m, w.wv.p, hist, status, pre, w.s);
+                launch_decode_table(tab_in, ids, nb, m, w.wv.p, hist, status, pre, w.s, RC.rel);
             }
             prof.end(w.s);
             float *log_ptr = collect ? RC.log_rows.p + RC.log_next * (kMlpIn + 1) : nullptr;
@@ -1667,11 +1684,11 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
                     prof.begin(P_ENCODE, w.s);
                     launch_encode_ip(w.wv.p, w.imsc.p, nb, m, e, w.lb_ctr.p + 3, arena_dev(out_par),
                                      arena_host(out_par), w.tgt.p, w.res.p, acc, w.wrec.p, w.flen.p, w.fwords.p,
-                                     w.foff.p, w.part.p, status, w.s);
+                                     w.foff.p, w.part.p, status, w.s, RC.rel, w.fmixed.p);
                     prof.end(w.s);
                     prof.begin(P_FRAME_COPY, w.s);
                     launch_frame_copy(w.wv.p, w.imsc.p, nb, m, e, w.tgt.p, w.res.p, ids, tab_out, acc, w.wrec.p,
-                                      w.flen.p, w.fwords.p, w.foff.p, w.s);
+                                      w.flen.p, w.fwords.p, w.foff.p, w.s, RC.rel, w.fmixed.p);
                     prof.end(w.s);
                 }
                 if (collect) {
@@ -1821,7 +1838,7 @@ static int decode_state_blocks(const qsim_state *st, uint64_t b0, uint32_t count
     CUDA_TRY(cudaMemcpyAsync(ids_dev, ids.data(), count * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
     launch_gather_refs(st->table, ids_dev, count, refs, s);
     if (st->codec == QSIM_CODEC_NONE) launch_copy_in(refs, count, st->m, dst, status, s);
-    else launch_decode(refs, count, st->m, dst, nullptr, status, s);
+    else launch_decode(refs, count, st->m, dst, nullptr, status, s, st->codec == QSIM_CODEC_QSZR);
     CUDA_TRY(cudaStreamSynchronize(s));
     return QSIM_OK;
 }
@@ -1866,6 +1883,11 @@ void qsim_release_cached_memory(void) {
 size_t qsim_worst_case_bytes(uint32_t m) {
     if (m < uint32_t(kQszMinM) || m > uint32_t(kQszMaxM)) return 0;
     return size_t(qsz_worst_case(int(m)));
+}
+
+size_t qsim_worst_case_bytes_rel(uint32_t m) {
+    if (m < uint32_t(kQszMinM) || m > uint32_t(kQszMaxM)) return 0;
+    return size_t(qszr_worst_case(int(m)));
 }
 
 int qsim_plan_stages(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_config *cfg, qsim_plan **out) {
@@ -2203,7 +2225,7 @@ int qsim_amplitudes(const qsim_state *st, const uint64_t *idx, size_t count, flo
         CUDA_TRY(cudaMemcpyAsync(ids.p, bids.data() + b0, cnt * sizeof(uint32_t), cudaMemcpyHostToDevice, s));
         launch_gather_refs(st->table, ids.p, cnt, refs.p, s);
         if (st->codec == QSIM_CODEC_NONE) launch_copy_in(refs.p, cnt, m, blocks.p, status, s);
-        else launch_decode(refs.p, cnt, m, blocks.p, nullptr, status, s);
+        else launch_decode(refs.p, cnt, m, blocks.p, nullptr, status, s, st->codec == QSIM_CODEC_QSZR);
         std::vector<uint32_t> sel_slot, sel_local;
         std::vector<size_t> sel_pos;
         for (size_t i = 0; i < count; ++i)
@@ -2345,6 +2367,61 @@ int qsim_compress_block(const float *d_amps, uint32_t m, double eb, void *d_out,
     return QSIM_OK;
 }
 
+int qsim_compress_block_rel(const float *d_amps, uint32_t m, double rel, void *d_out, size_t cap,
+                            size_t *out_bytes, void *cuda_stream) {
+    if (!d_amps || !d_out || !out_bytes) return set_error(QSIM_E_INVALID, "null argument");
+    if (m < uint32_t(kQszMinM) || m > uint32_t(kQszMaxM)) return set_error(QSIM_E_INVALID, "m=%u not in 5..26", m);
+    if ((reinterpret_cast<uintptr_t>(d_amps) & 15) || (reinterpret_cast<uintptr_t>(d_out) & 15))
+        return set_error(QSIM_E_INVALID, "device buffers must be 16-byte aligned");
+    int k;
+    if (!qszr_shift(rel, &k)) return set_error(QSIM_E_INVALID, "relative bound out of range");
+    int dev;
+    CUDA_TRY(cudaGetDevice(&dev));
+    DeviceCtx &c = device_ctx(dev);
+    std::lock_guard<std::mutex> lk(c.mu);
+    int rc = ensure_device_ctx(c);
+    if (rc) return rc;
+    cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
+    // scratch layout: block copy (8 B / amplitude), Im words (4 B), side records, then five per-frame arrays
+    const uint64_t N = 1ull << m, nf = qsz_nframes(int(m));
+    const size_t need = size_t(12 * N + nf * (kQszrSideBytes + 4 * 4 + 8));
+    if (need > c.rel_cap) {
+        if (c.rel_buf) CUDA_TRY(cudaFree(c.rel_buf));
+        c.rel_buf = nullptr;
+        c.rel_cap = 0;
+        if (cudaMalloc(&c.rel_buf, need) != cudaSuccess) {
+            cudaGetLastError();
+            return set_error(QSIM_E_NOMEM, "relative-codec scratch of %zu bytes", need);
+        }
+        c.rel_cap = need;
+    }
+    float2 *wv = reinterpret_cast<float2 *>(c.rel_buf);
+    uint32_t *im = reinterpret_cast<uint32_t *>(c.rel_buf + 8 * N);
+    uint8_t *side = c.rel_buf + 12 * N;
+    uint32_t *flen = reinterpret_cast<uint32_t *>(side + nf * kQszrSideBytes);
+    uint32_t *fwords = flen + nf, *fmixed = fwords + nf, *foff = fmixed + nf;
+    float2 *part = reinterpret_cast<float2 *>(foff + nf);
+    CUDA_TRY(cudaMemcpyAsync(wv, d_amps, 8 * N, cudaMemcpyDeviceToDevice, s));
+    EncTarget t{};
+    t.ptr = static_cast<uint8_t *>(d_out);
+    t.cap = cap;
+    EncResult r{};
+    CUDA_TRY(cudaMemcpyAsync(c.tgt, &t, sizeof(t), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c.res, &r, sizeof(r), cudaMemcpyHostToDevice, s));
+    const ArenaDev none{};
+    launch_encode_ip(wv, im, 1, int(m), k, c.lb_ctr + 3, none, none, c.tgt, c.res, nullptr, side, flen, fwords, foff,
+                     part, c.status, s, true, fmixed);
+    launch_frame_copy(wv, im, 1, int(m), k, c.tgt, c.res, nullptr, nullptr, nullptr, side, flen, fwords, foff, s, true,
+                      fmixed);
+    CUDA_TRY(cudaMemcpyAsync(&r, c.res, sizeof(r), cudaMemcpyDeviceToHost, s));
+    int code = read_status(c.status, s);
+    if (code) return set_error(code, "compress_rel: %s", status_text(code));
+    *out_bytes = r.total;
+    if (r.overflow) return set_error(QSIM_E_CAPACITY, "stream needs %llu bytes, cap is %zu",
+                                     (unsigned long long)r.total, cap);
+    return QSIM_OK;
+}
+
 int qsim_decompress_block(const void *d_in, size_t in_bytes, float *d_amps, uint32_t m, void *cuda_stream) {
     if (!d_in || !d_amps) return set_error(QSIM_E_INVALID, "null argument");
     if (m < uint32_t(kQszMinM) || m > uint32_t(kQszMaxM)) return set_error(QSIM_E_INVALID, "m=%u not in 5..26", m);
@@ -2358,8 +2435,13 @@ int qsim_decompress_block(const void *d_in, size_t in_bytes, float *d_amps, uint
     if (rc) return rc;
     cudaStream_t s = static_cast<cudaStream_t>(cuda_stream);
     BlockRef r{static_cast<const uint8_t *>(d_in), in_bytes};
+    uint32_t magic = 0;  // the format: QSZ1 or QSZR (any other value fails the kernel's header check)
+    if (in_bytes >= 4) {
+        CUDA_TRY(cudaMemcpyAsync(&magic, d_in, 4, cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+    }
     CUDA_TRY(cudaMemcpyAsync(c.ref, &r, sizeof(r), cudaMemcpyHostToDevice, s));
-    launch_decode(c.ref, 1, int(m), reinterpret_cast<float2 *>(d_amps), nullptr, c.status, s);
+    launch_decode(c.ref, 1, int(m), reinterpret_cast<float2 *>(d_amps), nullptr, c.status, s, magic == kQszrMagic);
     int code = read_status(c.status, s);
     if (code) return set_error(code, "decompress: %s", status_text(code));
     return QSIM_OK;

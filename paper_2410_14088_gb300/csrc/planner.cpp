@@ -479,6 +479,18 @@ bool qsz_step_exponent(double eb, int *e) {
     return true;
 }
 
+bool qszr_shift(double rel, int *k) {
+    if (!(rel > 0.0) || !(rel < 1.0)) return false;
+    const double r = rel / (1.0 + rel);
+    int x;
+    (void)frexp(std::ldexp(r, 24), &x);  // 2^24 r = f 2^x, f in [0.5, 1)
+    int v = x - 1;
+    while (v >= kQszrKMin && std::ldexp(1.0, v - 24) > r) --v;
+    if (v < kQszrKMin || v > kQszrKMax) return false;
+    *k = v;
+    return true;
+}
+
 int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_config *cfg,
                qsim_plan **out) {
     auto t0 = std::chrono::steady_clock::now();
@@ -492,7 +504,7 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
     if (cfg->mode > QSIM_MODE_PERSISTENT) return set_error(QSIM_E_INVALID, "bad mode %u", cfg->mode);
     if (cfg->mode == QSIM_MODE_PERSISTENT && cfg->k > 5)
         return set_error(QSIM_E_INVALID, "persistent mode fuses at most k = 5 qubits");
-    if (cfg->codec > QSIM_CODEC_NONE) return set_error(QSIM_E_INVALID, "bad codec %u", cfg->codec);
+    if (cfg->codec > QSIM_CODEC_QSZR) return set_error(QSIM_E_INVALID, "bad codec %u", cfg->codec);
     if (cfg->sizing > QSIM_SIZING_PREDICT) return set_error(QSIM_E_INVALID, "bad sizing %u", cfg->sizing);
     if (cfg->mode == QSIM_MODE_STREAMS && (cfg->streams < 1 || cfg->streams > 16))
         return set_error(QSIM_E_INVALID, "streams=%u not in 1..16", cfg->streams);
@@ -501,6 +513,12 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
         int e;
         double eb = cfg->eps * pow(2.0, -double(n) / 2.0);
         if (!qsz_step_exponent(eb, &e)) return set_error(QSIM_E_INVALID, "eps gives an error bound out of range");
+    }
+    if (cfg->codec == QSIM_CODEC_QSZR) {
+        int k;
+        if (!qszr_shift(cfg->eps, &k)) return set_error(QSIM_E_INVALID, "relative bound eps out of range");
+        if (cfg->mode != QSIM_MODE_STREAMS || cfg->sizing != QSIM_SIZING_EXACT)
+            return set_error(QSIM_E_UNSUPPORTED, "the relative-bound codec runs in streams mode with exact sizing");
     }
     if (ngates && !gates) return set_error(QSIM_E_INVALID, "gates is NULL");
 

@@ -42,6 +42,18 @@ inline uint64_t qsz_worst_case(int m) {
 // largest e with 2^e <= 2*eb (frexp, exact); returns false when out of range
 bool qsz_step_exponent(double eb, int *e);
 
+// QSZR: the relative-bound variant (codes = FP32 magnitude bits rounded to multiples of 2^k, sign chunks)
+constexpr uint32_t kQszrMagic = 0x525A5351u;  // "QSZR"
+constexpr int kQszrKMin = 1;
+constexpr int kQszrKMax = 22;
+constexpr uint32_t kQszrSideBytes = 2048;  // per-frame side record of the in-place encoder
+inline uint64_t qszr_worst_case(int m) {
+    uint64_t F = uint64_t(1) << frame_log_for(m), C = F / 32;
+    return qsz_data_start(m) + qsz_nframes(m) * (pad16(2 * C) + pad16((2 * C + 3) / 4) + pad16(8 * C) + 8 * F);
+}
+// largest k with 2^(k-24) <= rel / (1 + rel); returns false when out of range
+bool qszr_shift(double rel, int *k);
+
 // ---------------------------------------------------------------------------
 // plan
 // ---------------------------------------------------------------------------

@@ -26,7 +26,7 @@ ERROR_NAMES = {-1: "INVALID", -2: "NOMEM", -3: "CAPACITY", -4: "CORRUPT", -5: "R
 GATE_DIAG, GATE_PHASEFLIP = 1, 2
 PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2
 MODE_STREAMS, MODE_PERSISTENT = 0, 1
-CODEC_QSZ1, CODEC_NONE = 0, 1
+CODEC_QSZ1, CODEC_NONE, CODEC_QSZR = 0, 1, 2
 SIZING_EXACT, SIZING_PREDICT = 0, 1
 
 
@@ -120,6 +120,8 @@ SIGNATURES = {
     "qsim_compress_block": (ctypes.c_int, [_VP, _U32, ctypes.c_double, _VP, _SZ, ctypes.POINTER(_SZ), _VP]),
     "qsim_compress_block_noalloc": (ctypes.c_int, [_VP, _U32, ctypes.c_double, _VP, _SZ, ctypes.POINTER(_SZ), _VP]),
     "qsim_decompress_block": (ctypes.c_int, [_VP, _SZ, _VP, _U32, _VP]),
+    "qsim_compress_block_rel": (ctypes.c_int, [_VP, _U32, ctypes.c_double, _VP, _SZ, ctypes.POINTER(_SZ), _VP]),
+    "qsim_worst_case_bytes_rel": (_SZ, [_U32]),
     "qsim_mlp_forward": (ctypes.c_int, [_VP, _VP, _SZ, _VP, ctypes.c_int, _VP]),
     "qsim_mlp_loss_grad": (ctypes.c_int, [_VP, _VP, _VP, _SZ, _VP, ctypes.POINTER(ctypes.c_float), _VP]),
     "qsim_adam_step": (ctypes.c_int, [_VP, _VP, _VP, _VP, _SZ, ctypes.c_int, ctypes.c_float, ctypes.c_float,
@@ -422,6 +424,35 @@ def compress_block(amps, m: int, eb: float, out=None, cap: Optional[int] = None,
     _check(lib().qsim_compress_block(ctypes.c_void_p(amps.data_ptr()), m, eb, ctypes.c_void_p(out.data_ptr()), cap,
                                      ctypes.byref(nb), _stream_ptr(stream)), "qsim_compress_block")
     return out, nb.value
+
+
+def qszr_worst_case_bytes(m: int) -> int:
+    """qsim_worst_case_bytes_rel: largest QSZR stream of a 2^m-amplitude block."""
+    return int(lib().qsim_worst_case_bytes_rel(m))
+
+
+def compress_block_rel(amps, m: int, rel: float, out=None, cap: Optional[int] = None, stream=None):
+    """qsim_compress_block_rel: a QSZR stream under the point-wise relative bound rel. Returns
+    (out_tensor_uint8, nbytes)."""
+    import torch
+    if out is None:
+        cap = qszr_worst_case_bytes(m) if cap is None else cap
+        out = torch.empty(max(cap, 16), dtype=torch.uint8, device=amps.device)
+    cap = out.numel() if cap is None else cap
+    nb = ctypes.c_size_t()
+    _check(lib().qsim_compress_block_rel(ctypes.c_void_p(amps.data_ptr()), m, rel, ctypes.c_void_p(out.data_ptr()),
+                                         cap, ctypes.byref(nb), _stream_ptr(stream)), "qsim_compress_block_rel")
+    return out, nb.value
+
+
+def compress_block_rel_rc(amps, m, rel, cap, stream=None):
+    """Returns (rc, needed_bytes) without raising (for capacity and range tests)."""
+    import torch
+    out = torch.empty(max(cap, 16), dtype=torch.uint8, device=amps.device)
+    nb = ctypes.c_size_t()
+    rc = lib().qsim_compress_block_rel(ctypes.c_void_p(amps.data_ptr()), m, rel, ctypes.c_void_p(out.data_ptr()), cap,
+                                       ctypes.byref(nb), _stream_ptr(stream))
+    return rc, nb.value
 
 
 def compress_block_needed(amps, m, eb, cap, stream=None):

@@ -1,0 +1,121 @@
+"""GPU relative-bound codec (QSZR: Sec. 4.3, Eq. 1-2, Algorithm 2) vs the scalar oracle, through the C ABI:
+byte-identical streams and exact decodes for blocks of several sizes and value mixes, the point-wise relative
+bound, range / capacity / corruption errors, and the stage loop storing QSZR blocks that re-encode exactly."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2410_14088_gb300 import inputs, qsim
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def gpu_encode(block, m, rel):
+    out, nb = qsim.compress_block_rel(dev(block), m, rel)
+    torch.cuda.synchronize()
+    return out[:nb].cpu().numpy().tobytes()
+
+
+def gpu_decode(stream, m):
+    buf = torch.zeros(max(16, len(stream) + 16), dtype=torch.uint8, device="cuda")
+    buf[: len(stream)] = torch.frombuffer(bytearray(stream), dtype=torch.uint8).cuda()
+    out = qsim.decompress_block(buf, m, nbytes=len(stream))
+    return out.cpu().numpy().view(np.float32)
+
+
+def block(kind, m, seed):
+    rng = np.random.default_rng(seed)
+    n = 2 << m
+    if kind == "gauss":
+        return (rng.standard_normal(n) * 2.0 ** -8).astype(np.float32)
+    if kind == "binades":  # magnitudes over 40 binades, powers of two and their neighbours, zeros, both signs
+        x = (2.0 ** rng.uniform(-40, 0, n)).astype(np.float32)
+        pw = (2.0 ** rng.integers(-40, 1, n)).astype(np.float32)
+        x[1::5] = pw[1::5]
+        x[2::5] = np.nextafter(pw[2::5], np.float32(0))
+        x[::11] = 0.0
+        x *= np.where(rng.random(n) < 0.5, -1, 1).astype(np.float32)
+        return x
+    if kind == "negative":
+        return -(rng.random(n) * 0.5 + 0.01).astype(np.float32)
+    if kind == "alternating":
+        return (np.where(np.arange(n) % 4 < 2, 1, -1) * (rng.random(n) + 0.5) * 2.0 ** -6).astype(np.float32)
+    if kind == "subnormal":
+        return (rng.integers(-2000, 2000, n) * np.float32(2.0 ** -149)).astype(np.float32)
+    if kind == "zero":
+        return np.zeros(n, np.float32)
+    raise ValueError(kind)
+
+
+@pytest.mark.parametrize("kind", ["gauss", "binades", "negative", "alternating", "subnormal", "zero"])
+@pytest.mark.parametrize("m", [5, 8, 12, 14])
+@pytest.mark.parametrize("rel", [1e-3, 1e-2])
+def test_bit_exact_vs_oracle(kind, m, rel):
+    x = block(kind, m, 100 * m + len(kind))
+    want = oracle.qszr_encode(x, m, rel)
+    got = gpu_encode(x, m, rel)
+    assert got == want
+    y = gpu_decode(got, m)
+    assert np.array_equal(y.view(np.uint32), oracle.qszr_decode(want, m).view(np.uint32))
+    xd, yd = x.astype(np.float64), y.astype(np.float64)
+    normal = np.abs(xd) >= 2.0 ** -126
+    assert np.all(np.abs(yd[normal] - xd[normal]) <= rel * np.abs(xd[normal]))
+
+
+def test_capacity_range_invalid():
+    m, rel = 9, 1e-3
+    x = block("gauss", m, 1)
+    want = oracle.qszr_encode(x, m, rel)
+    rc, needed = qsim.compress_block_rel_rc(dev(x), m, rel, len(want) - 16)
+    assert rc == qsim.E_CAPACITY and needed == len(want)
+    y = x.copy()
+    y[7] = np.float32(2.0 ** 64)
+    assert qsim.compress_block_rel_rc(dev(y), m, rel, 1 << 16)[0] == qsim.E_RANGE
+    y[7] = np.inf
+    assert qsim.compress_block_rel_rc(dev(y), m, rel, 1 << 16)[0] == qsim.E_INVALID
+    assert qsim.compress_block_rel_rc(dev(x), m, 1.5, 1 << 16)[0] == qsim.E_INVALID
+
+
+def test_corrupt_streams_rejected():
+    m, rel = 5, 1e-3
+    x = np.zeros(64, np.float32)
+    x[0::2] = 1.0
+    good = bytearray(oracle.qszr_encode(x, m, rel))
+    bad_type = bytearray(good)
+    bad_type[48 + 16] = 3  # first frame at 48: widths (16 B), then the sign chunk types
+    bad_k = bytearray(good)
+    bad_k[10] = 30
+    for s in (bytes(bad_type), bytes(bad_k), bytes(good[:-16])):
+        buf = torch.zeros(256, dtype=torch.uint8, device="cuda")
+        buf[: len(s)] = torch.frombuffer(bytearray(s), dtype=torch.uint8).cuda()
+        assert qsim.decompress_block_rc(buf, m, len(s)) == qsim.E_CORRUPT
+
+
+@pytest.mark.parametrize("m", [9, 12])
+def test_stage_loop_stores_relative_streams(m):
+    n = 15
+    c = inputs.random_brick(n, 6, 9)
+    st = qsim.run(qsim.plan_stages(c, m=m, inner=2, k=4, eps=1e-3, codec=qsim.CODEC_QSZR))
+    amps = st.decompress().cpu().numpy()
+    f = oracle.fidelity(oracle.simulate(c), amps)
+    assert f >= 0.999
+    flat = amps.view(np.float32)
+    for b in range(1 << (n - m)):
+        blk = flat[(b << (m + 1)):((b + 1) << (m + 1))]
+        assert st.block_stream(b) == oracle.qszr_encode(blk, m, 1e-3), b
+    # the run's statistics come from the same encoder
+    assert st.stats.fidelity_lower_bound >= 0.99 and st.stats.nstages >= 1
+
+
+def test_relative_codec_mode_limits():
+    c = inputs.random_brick(12, 2, 1)
+    for kw in (dict(mode=qsim.MODE_PERSISTENT), dict(sizing=qsim.SIZING_PREDICT)):
+        with pytest.raises(qsim.QsimError) as ei:
+            qsim.plan_stages(c, m=9, inner=2, k=4, eps=1e-3, codec=qsim.CODEC_QSZR, **kw)
+        assert ei.value.code == qsim.E_UNSUPPORTED
