@@ -81,6 +81,9 @@ def parse_args():
     ap.add_argument("--depth", type=int, default=14)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement (long workloads)")
     ap.add_argument("--cap-gib", type=float, default=0.0, help="device tier cap (pinned host holds the rest)")
+    ap.add_argument("--codec", default="abs", choices=["abs", "rel"],
+                    help="abs: point-wise absolute bound eps*2^(-n/2) (QSZ1); rel: point-wise relative bound eps "
+                         "(QSZR, the paper's Sec. 4.3 mode)")
     return ap.parse_args()
 
 
@@ -204,7 +207,9 @@ class OracleSampler:
         self.np, self.oracle = np, oracle
         self.circ = workload(args)
         self.n, self.m = self.circ.n, min(args.m, self.circ.n - 4)
-        self.eb = args.eps * 2.0 ** (-self.n / 2)
+        self.rel = getattr(args, "codec", "abs") == "rel"
+        self.eb = args.eps if self.rel else args.eps * 2.0 ** (-self.n / 2)
+        self.codec = "QSZR" if self.rel else "QSZ1"
         self.stages = partition(self.circ.gates, self.n, self.m, args.inner)
         self.psi = oracle.basis_state(self.n, self.circ.init_basis)
         self.next_gate = 0
@@ -225,7 +230,10 @@ class OracleSampler:
         while time.perf_counter() - t1 < 0.3 * budget_s or b == 0:
             j = self.next_block % nblocks
             blk = self.psi[2 * (j << self.m): 2 * ((j + 1) << self.m)].astype(self.np.float32)
-            self.oracle.qsz_decode(self.oracle.qsz_encode(blk, self.m, self.eb), self.m)
+            if self.rel:
+                self.oracle.qszr_decode(self.oracle.qszr_encode(blk, self.m, self.eb), self.m)
+            else:
+                self.oracle.qsz_decode(self.oracle.qsz_encode(blk, self.m, self.eb), self.m)
             self.next_block += 1
             b += 1
         t2 = time.perf_counter()
@@ -243,7 +251,7 @@ class OracleSampler:
         ups = (1 << self.n) * len(self.circ.gates) / total
         threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
         sample = (f"{self.gates_done} complex128 gate updates of the full 2^{self.n} state "
-                  f"({self.t_gates:.1f} s) and {self.blocks_done} QSZ1 encode+decode of 2^{self.m}-amplitude "
+                  f"({self.t_gates:.1f} s) and {self.blocks_done} {self.codec} encode+decode of 2^{self.m}-amplitude "
                   f"blocks ({self.t_codec:.1f} s); full run modelled as per-gate time x {len(self.circ.gates)} "
                   f"gates + per-block codec time x {nblocks} blocks x {len(self.stages)} stages")
         return ups, sample, threads, total
@@ -287,8 +295,11 @@ def config_dict(args):
             "random": f"random u3+cz brick n={args.n} depth={args.depth}",
             "mirror": f"mirror u3+cz brick n={args.n} depth={args.depth}"}[args.workload]
     raw = 8 << args.n
+    bound = "" if args.codec == "abs" else ", codec=relative (QSZR)"
     return {"workload": f"{name}, m={args.m}, inner={args.inner}, k={args.k}, eps={args.eps:g}, prec={args.prec}, "
-                        f"mode={args.mode}{'+graph' if args.graph else ''}, sizing={args.sizing}",
+                        f"mode={args.mode}{'+graph' if args.graph else ''}, sizing={args.sizing}{bound}",
+            "error_bound": ("absolute eps*2^(-n/2) per component" if args.codec == "abs"
+                            else "relative eps per component"),
             "n_qubits": args.n, "gates": len(workload(args).gates), "block_log2": args.m, "inner": args.inner,
             "k": args.k, "eps": args.eps, "prec": args.prec, "streams": args.streams, "mode": args.mode,
             "graph": bool(args.graph), "sizing": args.sizing, "device_tier_cap_gib": args.cap_gib,
@@ -316,7 +327,8 @@ def run_ours(args, rank, world, dist):
               graph=1 if args.graph else 0,
               sizing=qsim.SIZING_PREDICT if args.sizing == "predict" else qsim.SIZING_EXACT,
               predictor_margin=args.margin, diag_exempt=1 if args.diag_exempt else 0,
-              device_tier_cap_bytes=int(args.cap_gib * (1 << 30)))
+              device_tier_cap_bytes=int(args.cap_gib * (1 << 30)),
+              codec=qsim.CODEC_QSZR if args.codec == "rel" else qsim.CODEC_QSZ1)
     train_info = None
     if args.sizing == "predict":
         # training rows from exact-sizing runs of training seeds (100+) of the same family, not timed
