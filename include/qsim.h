@@ -94,7 +94,11 @@ typedef struct qsim_config {
     uint64_t device_tier_cap_bytes; /* bytes of compressed blocks kept on the device; 0 = no cap */
     uint64_t init_basis;  /* initial basis state |init_basis> (Sec. 4.2 initialisation) */
     double predictor_margin; /* predictor reservation = 2^pred * (1 + margin) */
-    uint64_t reserved[6];    /* zero; reserved[0] bit 0 is a test hook: in persistent mode the
+    uint32_t reorder;        /* 1: commutation-aware partition: a gate may be placed before earlier
+                                gates it commutes with (disjoint qubits, or both diagonal) when that
+                                keeps it in the current stage; 0 = Algorithm 1 in circuit order */
+    uint32_t pad0;           /* zero */
+    uint64_t reserved[5];    /* zero; reserved[0] bit 0 is a test hook: in persistent mode the
                                 first stage's second phase waits for a count that is never
                                 reached, so the run ends with QSIM_E_TIMEOUT after the
                                 bounded wait (0.2 s) instead of hanging */

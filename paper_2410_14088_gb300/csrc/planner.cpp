@@ -89,6 +89,80 @@ int counted_globals(const Gate &g, uint32_t n, uint32_t m, uint32_t thr, bool di
     return QSIM_OK;
 }
 
+// Commutation-aware order for the stage cut. Two gates must keep their
+// circuit order when they share a qubit, unless both are diagonal (diagonal
+// gates commute). List scheduling: repeatedly take the earliest gate whose
+// ordered predecessors are all placed and whose counted global qubits keep the
+// current stage within the threshold; when none fits, the stage is closed and
+// the next one starts empty. Every placed gate follows all the gates it does not
+// commute with, so the reordered circuit is the same unitary; the in-order cut
+// of Algorithm 1 over the new list then yields these stages.
+int reorder_for_stages(std::vector<Gate> &gates, uint32_t n, uint32_t m, uint32_t thr, bool diag_exempt) {
+    const size_t N = gates.size();
+    std::vector<uint64_t> gmask(N);
+    std::vector<std::vector<uint32_t>> succ(N);
+    std::vector<uint32_t> npred(N, 0);
+    {
+        std::vector<int64_t> last_nd(n, -1);             // last non-diagonal gate on each qubit
+        std::vector<std::vector<uint32_t>> diag_since(n);  // diagonal gates on the qubit since then
+        std::vector<uint32_t> preds;
+        for (size_t i = 0; i < N; ++i) {
+            const Gate &g = gates[i];
+            int rc = counted_globals(g, n, m, thr, diag_exempt, &gmask[i]);
+            if (rc) return rc;
+            std::vector<uint32_t> qs;
+            if (g.phaseflip)
+                for (uint32_t q = 0; q < n; ++q) qs.push_back(q);
+            else
+                qs.assign(g.q, g.q + g.nq);
+            const bool d = g.diag || g.phaseflip;
+            preds.clear();
+            for (uint32_t q : qs) {
+                if (last_nd[q] >= 0) preds.push_back(uint32_t(last_nd[q]));
+                if (!d) preds.insert(preds.end(), diag_since[q].begin(), diag_since[q].end());
+            }
+            std::sort(preds.begin(), preds.end());
+            preds.erase(std::unique(preds.begin(), preds.end()), preds.end());
+            for (uint32_t pj : preds) succ[pj].push_back(uint32_t(i));
+            npred[i] = uint32_t(preds.size());
+            for (uint32_t q : qs) {
+                if (d) {
+                    diag_since[q].push_back(uint32_t(i));
+                } else {
+                    last_nd[q] = int64_t(i);
+                    diag_since[q].clear();
+                }
+            }
+        }
+    }
+    std::set<uint32_t> ready;
+    for (size_t i = 0; i < N; ++i)
+        if (!npred[i]) ready.insert(uint32_t(i));
+    std::vector<uint32_t> order;
+    order.reserve(N);
+    uint64_t mask = 0;
+    while (!ready.empty()) {
+        uint32_t pick = UINT32_MAX;
+        for (uint32_t i : ready)
+            if (__builtin_popcountll(mask | gmask[i]) <= int(thr)) { pick = i; break; }
+        if (pick == UINT32_MAX) {  // nothing fits: close the stage
+            mask = 0;
+            continue;
+        }
+        ready.erase(pick);
+        mask |= gmask[pick];
+        order.push_back(pick);
+        for (uint32_t s2 : succ[pick])
+            if (--npred[s2] == 0) ready.insert(s2);
+    }
+    if (order.size() != N) return set_error(QSIM_E_INVALID, "internal: gate order incomplete");
+    std::vector<Gate> out;
+    out.reserve(N);
+    for (uint32_t i : order) out.push_back(std::move(gates[i]));
+    gates.swap(out);
+    return QSIM_OK;
+}
+
 // Embed matrix `u` acting on working bits `bits` (matrix bit j <-> bits[j])
 // into the space of the ascending working-bit set `S`.
 std::vector<cd> embed(const std::vector<cd> &u, const std::vector<uint32_t> &bits,
@@ -539,6 +613,12 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
         }
     }
 
+    // ---- optional commutation-aware order (stages are then cut from the reordered list) ----
+    if (cfg->reorder) {
+        rc = reorder_for_stages(p->gates, n, m, thr, cfg->diag_exempt != 0);
+        if (rc) { delete p; return rc; }
+    }
+
     // ---- Algorithm 1: greedy in-order partition ----
     uint64_t cur_mask = 0;
     size_t cur_first = 0, cur_count = 0;
@@ -578,8 +658,9 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
         for (size_t i = st.first_gate; i < st.first_gate + st.ngates; ++i) fz.add(p->gates[i]);
         fz.flush();
         narrow_csep_ops(st.ops);
+        // leading phase ops go to the decoder of either compressed format (the raw copy-in applies none)
         layout_passes(st, std::max<uint32_t>(tile_bits, std::min<uint32_t>(st.W, 5 + cfg->k)),
-                      cfg->codec == QSIM_CODEC_QSZ1);
+                      cfg->codec != QSIM_CODEC_NONE);
     }
 
     qsim_plan_stats &s = p->stats;

@@ -102,3 +102,39 @@ def test_errors():
     pf = inputs.PHASEFLIP(200, 8)
     p = qsim.plan_stages(8, [inputs.H(7), pf], m=5, inner=2, k=3)
     assert p.nstages == 1
+
+
+@pytest.mark.parametrize("circ,m,inner,k,dx", CASES, ids=lambda x: str(getattr(x, "family", x)))
+def test_reordered_stages_reproduce_the_circuit(circ, m, inner, k, dx):
+    # commutation-aware partition: gates only move past gates they commute with, so replaying the fused ops
+    # of the reordered stages with the oracle gives the circuit's state; never more stages than Algorithm 1
+    p = qsim.plan_stages(circ, m=m, inner=inner, k=k, diag_exempt=dx, reorder=1)
+    base = qsim.plan_stages(circ, m=m, inner=inner, k=k, diag_exempt=dx)
+    n = circ.n
+    psi = oracle.basis_state(n, circ.init_basis)
+    total = 0
+    for s, (f, c, inner_q) in enumerate(p.stages()):
+        assert len(inner_q) <= max(inner, 2)
+        for op in p.stage_ops(s):
+            total += op["ngates"]
+            if op["type"] == 0:
+                assert all(q < m or q in inner_q for q in op["qubits"])
+            apply_op(psi, n, op)
+    assert total == len(circ.gates)
+    assert np.max(np.abs(psi.view(np.complex128) - oracle.simulate(circ))) <= 1e-12
+    assert p.nstages <= base.nstages
+
+
+def test_reorder_cuts_fewer_stages_on_qft_and_qaoa():
+    for c, m in ((inputs.qft_rz_cx(20, 4, 1), 14), (inputs.qaoa_maxcut(20, 3, 2), 14)):
+        a = qsim.plan_stages(c, m=m, inner=4, k=5).nstages
+        b = qsim.plan_stages(c, m=m, inner=4, k=5, reorder=1).nstages
+        assert b < a, (c.family, a, b)
+
+
+def test_reorder_keeps_a_chain_in_order():
+    # a CX ladder up and back down: every gate shares a qubit with the one before, nothing can move
+    c = inputs.Circuit(12, inputs.cx_ladder(12) + inputs.cx_ladder(12)[::-1], 0, "ladder")
+    a = qsim.plan_stages(c, m=7, inner=2, k=2)
+    b = qsim.plan_stages(c, m=7, inner=2, k=2, reorder=1)
+    assert a.stages() == b.stages()
