@@ -66,6 +66,8 @@ def parse_args():
     ap.add_argument("--sizing", default="exact", choices=["exact", "predict"])
     ap.add_argument("--margin", type=float, default=0.25, help="predictor reservation margin")
     ap.add_argument("--diag-exempt", action="store_true", help="diagonal gates never count as global (Algorithm 1)")
+    ap.add_argument("--reorder", action="store_true",
+                    help="commutation-aware partition: gates may move before earlier gates they commute with")
     ap.add_argument("--train-n", type=int, default=0, help="qubits of the predictor's training circuits (0 = n)")
     ap.add_argument("--workload", default="qft", choices=["qft", "qaoa", "random", "mirror", "batch"],
                     help="qft: QFT + 4 x (RZ, CX ladder) on n qubits; qaoa: MaxCut p=3 on a random 3-regular "
@@ -300,6 +302,8 @@ def config_dict(args):
                         f"mode={args.mode}{'+graph' if args.graph else ''}, sizing={args.sizing}{bound}",
             "error_bound": ("absolute eps*2^(-n/2) per component" if args.codec == "abs"
                             else "relative eps per component"),
+            "partition": ("commutation-aware (reorder)" if args.reorder else "Algorithm 1 in circuit order") +
+                         (", diagonal gates exempt" if args.diag_exempt else ""),
             "n_qubits": args.n, "gates": len(workload(args).gates), "block_log2": args.m, "inner": args.inner,
             "k": args.k, "eps": args.eps, "prec": args.prec, "streams": args.streams, "mode": args.mode,
             "graph": bool(args.graph), "sizing": args.sizing, "device_tier_cap_gib": args.cap_gib,
@@ -327,6 +331,7 @@ def run_ours(args, rank, world, dist):
               graph=1 if args.graph else 0,
               sizing=qsim.SIZING_PREDICT if args.sizing == "predict" else qsim.SIZING_EXACT,
               predictor_margin=args.margin, diag_exempt=1 if args.diag_exempt else 0,
+              reorder=1 if args.reorder else 0,
               device_tier_cap_bytes=int(args.cap_gib * (1 << 30)),
               codec=qsim.CODEC_QSZR if args.codec == "rel" else qsim.CODEC_QSZ1)
     train_info = None

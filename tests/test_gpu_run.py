@@ -223,3 +223,18 @@ def test_config1_gate_error_vs_fp64(prec, rel_tol):
     print(f"\ngate error vs FP64, 28-qubit QFT+RZ/CX, prec={prec}: max-abs {err:.3e}, relative to 2^-14: {rel:.3e}")
     assert err <= 1e-5 or prec == qsim.PREC_TF32
     assert rel <= rel_tol
+
+
+@pytest.mark.parametrize("family", ["qft", "qaoa", "random"])
+def test_reordered_partition_runs(family):
+    # the commutation-aware partition: fewer stages, same state up to the codec error, and the persistent
+    # kernel stores the same streams as the streams engine
+    c = {"qft": inputs.qft_rz_cx(16, 2, 5), "qaoa": inputs.qaoa_maxcut(16, 2, 7),
+         "random": inputs.random_brick(16, 6, 8)}[family]
+    kw = dict(m=11, inner=2, k=4, eps=1e-3, reorder=1)
+    st = qsim.run(qsim.plan_stages(c, **kw))
+    assert st.stats.nstages <= qsim.plan_stages(c, m=11, inner=2, k=4, eps=1e-3).nstages
+    assert oracle.fidelity(oracle.simulate(c), state_c64(st)) >= 0.99
+    pst = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, **kw))
+    for b in range(1 << (16 - 11)):
+        assert pst.block_stream(b) == st.block_stream(b)
