@@ -291,6 +291,7 @@ def config_dict(args):
                 "circuits": len(cs), "n_qubits": [min(c.n for c in cs), max(c.n for c in cs)],
                 "gates": sum(len(c.gates) for c in cs), "eps": args.eps, "prec": args.prec,
                 "mode": "persistent (one launch for the batch)", "sizing": args.sizing,
+                "partition": "commutation-aware (reorder)" if args.reorder else "Algorithm 1 in circuit order",
                 "raw_state_gib": sum(8 << c.n for c in cs) / 2**30,
                 "l2_policy": "working set (all circuits' compressed stores) > L2 (129 MB); no flush"}
     name = {"qft": f"qft{args.n}+4x(rz,cx-ladder)", "qaoa": f"qaoa-maxcut p=3, 3-regular n={args.n}",
@@ -539,7 +540,7 @@ def run_batch_bench(args, rank, world, dist):
     circuits = batch_workload(args)
     base = dict(eps=args.eps, prec=prec, mode=qsim.MODE_PERSISTENT,
                 sizing=qsim.SIZING_PREDICT if args.sizing == "predict" else qsim.SIZING_EXACT,
-                predictor_margin=args.margin)
+                predictor_margin=args.margin, reorder=1 if args.reorder else 0)
     train_info = None
     if args.sizing == "predict":
         # training rows from exact-sizing runs of a training batch (seed 100+), not timed
