@@ -119,3 +119,19 @@ def test_relative_codec_mode_limits():
         with pytest.raises(qsim.QsimError) as ei:
             qsim.plan_stages(c, m=9, inner=2, k=4, eps=1e-3, codec=qsim.CODEC_QSZR, **kw)
         assert ei.value.code == qsim.E_UNSUPPORTED
+
+
+def test_relative_streams_in_host_tier_and_readout():
+    # device tier capped: blocks land in pinned host memory, same streams; amplitude readout decodes QSZR
+    c = inputs.qaoa_maxcut(16, 2, 6)
+    kw = dict(m=10, inner=2, k=4, eps=1e-3, codec=qsim.CODEC_QSZR)
+    base = qsim.run(qsim.plan_stages(c, **kw))
+    capped = qsim.run(qsim.plan_stages(c, device_tier_cap_bytes=1 << 16, **kw))
+    assert capped.stats.host_tier_peak_bytes > 0
+    for b in range(0, 1 << 6, 5):
+        assert base.block_stream(b) == capped.block_stream(b)
+    full = base.decompress().cpu().numpy()
+    idx = np.array([0, 3, 999, (1 << 16) - 1, 40000], dtype=np.uint64)
+    np.testing.assert_array_equal(capped.amplitudes(idx), full[idx.astype(np.int64)])
+    ideal = oracle.simulate(c)
+    assert oracle.fidelity(ideal, full) >= 0.999
