@@ -238,3 +238,17 @@ def test_reordered_partition_runs(family):
     pst = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, **kw))
     for b in range(1 << (16 - 11)):
         assert pst.block_stream(b) == st.block_stream(b)
+
+
+@pytest.mark.parametrize("mode,codec", [(qsim.MODE_STREAMS, qsim.CODEC_QSZ1), (qsim.MODE_PERSISTENT, qsim.CODEC_QSZ1),
+                                        (qsim.MODE_STREAMS, qsim.CODEC_QSZR), (qsim.MODE_STREAMS, qsim.CODEC_NONE)])
+def test_empty_circuit_returns_the_initial_state(mode, codec):
+    # no gates: no stage; the stored state is the initial basis state, exactly (1.0 is on both codecs' grids)
+    c = inputs.Circuit(12, [], 1234, "empty")
+    p = qsim.plan_stages(c, m=8, inner=2, k=4, eps=1e-3, mode=mode, codec=codec)
+    assert p.nstages == 0
+    st = qsim.run(p)
+    want = np.zeros(1 << 12, np.complex64)
+    want[1234] = 1.0
+    assert np.array_equal(state_c64(st), want)
+    assert st.stats.nstages == 0
