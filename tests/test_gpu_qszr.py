@@ -135,3 +135,25 @@ def test_relative_streams_in_host_tier_and_readout():
     np.testing.assert_array_equal(capped.amplitudes(idx), full[idx.astype(np.int64)])
     ideal = oracle.simulate(c)
     assert oracle.fidelity(ideal, full) >= 0.999
+
+
+@pytest.mark.parametrize("rel", [None, 1e-3])
+def test_largest_block_both_codecs(rel):
+    # m = 26, the largest block: 2^26 amplitudes (512 MiB), 16384 frames; streams byte-identical to the oracle
+    m = 26
+    rng = np.random.default_rng(26)
+    x = (rng.standard_normal(2 << m, dtype=np.float32) * np.float32(2.0 ** -13))
+    x[: 1 << 20] = 0.0  # a run of zero frames at the start
+    if rel is None:
+        eb = 1e-3 * 2.0 ** -13
+        out, nb = qsim.compress_block(dev(x), m, eb)
+        want = oracle.qsz_encode(x, m, eb)
+    else:
+        out, nb = qsim.compress_block_rel(dev(x), m, rel)
+        want = oracle.qszr_encode(x, m, rel)
+    torch.cuda.synchronize()
+    got = out[:nb].cpu().numpy().tobytes()
+    assert got == want
+    y = qsim.decompress_block(out, m, nbytes=nb).cpu().numpy().view(np.float32)
+    ref = oracle.qsz_decode(want, m) if rel is None else oracle.qszr_decode(want, m)
+    assert np.array_equal(y.view(np.uint32), ref.view(np.uint32))
