@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
                          epoch, tgt[j], res + j, table ? table + ids[j] : nullptr, acc,
                          scr.part ? scr.part + item : nullptr, only_overflowed, s_stage, SE, status);
     // ---- last CTA: reduce the frame partials, reset the ticket counter, advance the epoch ----
+    __syncthreads();  // the frame's writes by every thread of the CTA come before its arrival
     if (tid == 0) {
         __threadfence();
         s_last = atomicAdd(scr.done, 1u) == gridDim.x - 1;
@@ -299,8 +300,12 @@ __global__ void __launch_bounds__(NT, 4) k_encode_ip(float2 *wv, uint32_t *__res
             flen[item] = len;
             fwords[item] = words;
             if (REL) fmixed[item] = mixed;
+            __threadfence();  // the frame's records (and its error partial) before the CTA's arrival below
         }
     }
+    // every warp of the CTA has written its frames' records before the CTA counts as arrived: the last CTA
+    // reads all of them
+    __syncthreads();
     if (tid == 0) {
         __threadfence();
         s_last = atomicAdd(done_ctr, 1u) == gridDim.x - 1;

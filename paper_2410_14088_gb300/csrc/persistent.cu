@@ -183,7 +183,10 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
                 const uint32_t jj = fi / g.nframes, f = fi % g.nframes;
                 const uint32_t len = cdev::size_frame_warp<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g,
                                                                  S.e, L.wrec + uint64_t(sf0 + fi) * 256, L.status);
-                if ((tid & 31) == 0) L.flen[sf0 + fi] = len;
+                if ((tid & 31) == 0) {
+                    L.flen[sf0 + fi] = len;
+                    __threadfence();  // read by the phase's last item on another CTA
+                }
             }
         } else if (type == PH_ENCODE_W) {
             const uint32_t fi = i * (PT / 32) + warp;

@@ -252,3 +252,20 @@ def test_empty_circuit_returns_the_initial_state(mode, codec):
     want[1234] = 1.0
     assert np.array_equal(state_c64(st), want)
     assert st.stats.nstages == 0
+
+
+def test_repeated_runs_store_identical_streams():
+    # every CTA of the in-place encoder must finish its frames' records before it counts as arrived; a run
+    # repeated many times stores the same bytes (collect mode adds the training-row kernels to the stream)
+    circuits = list(inputs.batch_circuits(100, count=6, nmin=18, nmax=21))
+    ref = {}
+    for rep in range(4):
+        for i, c in enumerate(circuits):
+            for collect in (0, 1):
+                p = qsim.plan_stages(c, m=c.n - 4, inner=2, k=5, eps=1e-3, prec=qsim.PREC_TF32, collect=collect)
+                st = qsim.run(p)
+                got = [st.block_stream(b) for b in range(16)]
+                if (i, collect) in ref:
+                    assert got == ref[(i, collect)], (i, collect, rep)
+                else:
+                    ref[(i, collect)] = got
