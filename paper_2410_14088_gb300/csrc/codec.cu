@@ -145,96 +145,6 @@ __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, ui
     }
 }
 
-// Learned-sizing encoder: one warp per frame, frames taken by ticket in
-// block-major order so a frame's predecessors are always already being encoded;
-// the frame offset comes from a warp look-back (epoch-tagged status words). The
-// last CTA folds the frame partials, resets the ticket and advances the epoch.
-__global__ void __launch_bounds__(NT, 4) k_encode_lbw(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
-                                                   EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
-                                                   int only_overflowed, const uint32_t *__restrict__ ids,
-                                                   BlockSlot *__restrict__ table, StageAccum *acc,
-                                                   LookbackScratch scr, ArenaDev dev, ArenaDev host, int *status) {
-    // a re-encode with nothing to redo leaves the ticket, the counters and the epoch alone
-    if (only_overflowed && scr.pending && ld_relaxed_u32(scr.pending) == 0) return;
-    const FrameGeom g = geom(m);
-    __shared__ uint32_t s_wb[NW][64];
-    __shared__ double s_red[2][NW];
-    __shared__ bool s_last;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    uint32_t item = 0, epoch = 0;
-    if (lane == 0) {
-        item = atomicAdd(scr.ticket, 1u);
-        epoch = ld_relaxed_u32(scr.epoch) & kEpochMask;
-    }
-    item = __shfl_sync(kFull, item, 0);
-    epoch = __shfl_sync(kFull, epoch, 0);
-    const uint32_t j = item / g.nframes, f = item % g.nframes;
-    bool skip = j >= nblocks;
-    if (!skip && only_overflowed) skip = __ldcg(&res[j].overflow) == 0;
-    if (!skip)
-        encode_frame_warp_lb(wv + (uint64_t(j) << m) + uint64_t(f) * g.F, g, m, e, f,
-                             scr.state + uint64_t(j) * g.nframes, epoch, tgt[j], res + j,
-                             table ? table + ids[j] : nullptr, acc,
-                             (scr.part && !only_overflowed) ? scr.part + item : nullptr, s_wb[warp], status);
-    __syncthreads();
-    if (tid == 0) {
-        __threadfence();
-        s_last = atomicAdd(scr.done, 1u) == gridDim.x - 1;
-    }
-    __syncthreads();
-    if (!s_last) return;
-    __threadfence();
-    if (scr.part && !only_overflowed) {
-        double ta = 0, tb = 0;
-        for (uint32_t jb = warp; jb < nblocks; jb += NW) {
-            double a = 0, b = 0;
-            for (uint32_t f2 = lane; f2 < g.nframes; f2 += 32) {
-                const float2 p = __ldcg(scr.part + uint64_t(jb) * g.nframes + f2);
-                a += double(p.x);
-                b += double(p.y);
-            }
-#pragma unroll
-            for (int o = 16; o; o >>= 1) {
-                a += __shfl_xor_sync(kFull, a, o);
-                b += __shfl_xor_sync(kFull, b, o);
-            }
-            if (lane == 0) {
-                res[jb].err_sq = a;
-                res[jb].norm_sq = b;
-            }
-            ta += a;
-            tb += b;
-        }
-        if (lane == 0) {
-            s_red[0][warp] = ta;
-            s_red[1][warp] = tb;
-        }
-        __syncthreads();
-        if (tid == 0 && acc) {
-            double a = 0, b = 0;
-            for (int w = 0; w < NW; ++w) { a += s_red[0][w]; b += s_red[1][w]; }
-            atomicAdd(&acc->err_sq, a);
-            atomicAdd(&acc->norm_sq, b);
-        }
-    }
-    if (!only_overflowed && dev.bump) {
-        // blocks whose predicted slot was too small get an exact one now (res.total holds their exact size)
-        for (uint32_t jb = tid; jb < nblocks; jb += NT)
-            if (__ldcg(&res[jb].overflow)) {
-                if (scr.pending) atomicAdd(scr.pending, 1u);
-                reserve_slot(__ldcg(reinterpret_cast<const unsigned long long *>(&res[jb].total)), dev, host,
-                             &tgt[jb], status);
-            }
-        __syncthreads();
-    }
-    if (tid == 0) {
-        *scr.ticket = 0;
-        *scr.done = 0;
-        __threadfence();
-        atomicExch(scr.epoch, (epoch + 1) & kEpochMask);
-    }
-}
-
 // Sizing pass (one CTA per frame) whose last CTA reserves every block's slot
 // from the summed frame lengths; sizes are left zeroed for the next use.
 __global__ void __launch_bounds__(NT, 3) k_encode_size(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
@@ -276,7 +186,9 @@ __global__ void __launch_bounds__(NT, 3) k_encode_size(const float2 *__restrict_
 // offsets, reserves each block's exact slot and folds the frames' error
 // partials into the blocks' and the stage's totals.
 // REL: the relative-bound format (e is the shift k, side records of kQszrSideBytes, mixed sign words counted
-// in fmixed). Without a device arena (dev.bump null) the targets are the caller's and nothing is reserved.
+// in fmixed). Without a device arena (dev.bump null) the targets are the caller's and nothing is reserved; with
+// keep_fitting (learned sizing) a block keeps the slot reserved for it beforehand when its exact size fits, and
+// only a block whose prediction was too small gets an exact slot (counted as an overflowed block).
 template <bool REL>
 __global__ void __launch_bounds__(NT, 4) k_encode_ip(float2 *wv, uint32_t *__restrict__ im, uint32_t nblocks, int m,
                                                   int e, uint32_t *done_ctr, ArenaDev dev, ArenaDev host,
@@ -284,7 +196,7 @@ __global__ void __launch_bounds__(NT, 4) k_encode_ip(float2 *wv, uint32_t *__res
                                                   StageAccum *acc, uint8_t *__restrict__ wrec,
                                                   uint32_t *__restrict__ flen, uint32_t *__restrict__ fwords,
                                                   uint32_t *__restrict__ fmixed, uint32_t *__restrict__ foff,
-                                                  float2 *__restrict__ part, int *status) {
+                                                  float2 *__restrict__ part, int keep_fitting, int *status) {
     const FrameGeom g = geom(m);
     constexpr uint32_t kSide = REL ? kQszrSideBytes : 256u;
     __shared__ bool s_last;
@@ -347,7 +259,14 @@ __global__ void __launch_bounds__(NT, 4) k_encode_ip(float2 *wv, uint32_t *__res
             res[jb].overflow = 0;
             res[jb].err_sq = a;
             res[jb].norm_sq = b;
-            if (dev.bump) reserve_slot(run, dev, host, &tgt[jb], status);
+            if (dev.bump) {
+                if (!keep_fitting) {
+                    reserve_slot(run, dev, host, &tgt[jb], status);
+                } else if (tgt[jb].ptr == nullptr || run > tgt[jb].cap) {
+                    if (acc) atomicAdd(reinterpret_cast<unsigned long long *>(&acc->overflow_blocks), 1ull);
+                    reserve_slot(run, dev, host, &tgt[jb], status);
+                }
+            }
         }
         ta += a;
         tb += b;
@@ -399,14 +318,12 @@ __global__ void __launch_bounds__(NT) k_frame_copy(const float2 *__restrict__ wv
 __global__ void k_reserve(uint32_t nblocks, const uint64_t *__restrict__ need, uint64_t add_const,
                           const float *__restrict__ pred_log2, double margin, uint64_t worst,
                           ArenaDev dev, ArenaDev host, EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
-                          int retry_overflowed, int *status, uint32_t *pending) {
+                          int retry_overflowed, int *status) {
     const uint32_t j = blockIdx.x * blockDim.x + threadIdx.x;
-    if (pending && !retry_overflowed && j == 0) *pending = 0;
     if (j >= nblocks) return;
     uint64_t want;
     if (retry_overflowed) {
         if (res[j].overflow == 0) return;
-        if (pending) atomicAdd(pending, 1u);
         want = res[j].total;
     } else if (pred_log2) {
         double p = double(pred_log2[j]);
@@ -536,30 +453,19 @@ void launch_size_reserve(const float2 *wv, uint32_t nblocks, int m, int e, uint6
     count_launch();
 }
 
-void launch_encode_lbw(const float2 *wv, uint32_t nblocks, int m, int e, EncTarget *tgt, EncResult *res,
-                       int only_overflowed, const uint32_t *ids, BlockSlot *table, StageAccum *acc,
-                       const LookbackScratch &scr, const ArenaDev *fix_dev, const ArenaDev *fix_host, int *status,
-                       cudaStream_t s) {
-    const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
-    ArenaDev none{};
-    k_encode_lbw<<<unsigned((items + NW - 1) / NW), NT, 0, s>>>(wv, nblocks, m, e, tgt, res, only_overflowed, ids,
-                                                                table, acc, scr, fix_dev ? *fix_dev : none,
-                                                                fix_host ? *fix_host : none, status);
-    count_launch();
-}
 
 void launch_encode_ip(float2 *wv, uint32_t *im, uint32_t nblocks, int m, int e, uint32_t *done_ctr,
                       const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, StageAccum *acc,
                       uint8_t *wrec, uint32_t *flen, uint32_t *fwords, uint32_t *foff, float2 *part, int *status,
-                      cudaStream_t s, bool rel, uint32_t *fmixed) {
+                      cudaStream_t s, bool rel, uint32_t *fmixed, bool keep_fitting) {
     const uint64_t items = uint64_t(nblocks) * qsz_nframes(m);
     const unsigned grid = grid_for((items + NW - 1) / NW, 152 * 8);
     if (rel)
         k_encode_ip<true><<<grid, NT, 0, s>>>(wv, im, nblocks, m, e, done_ctr, dev, host, tgt, res, acc, wrec, flen,
-                                              fwords, fmixed, foff, part, status);
+                                              fwords, fmixed, foff, part, keep_fitting ? 1 : 0, status);
     else
         k_encode_ip<false><<<grid, NT, 0, s>>>(wv, im, nblocks, m, e, done_ctr, dev, host, tgt, res, acc, wrec, flen,
-                                               fwords, fmixed, foff, part, status);
+                                               fwords, fmixed, foff, part, keep_fitting ? 1 : 0, status);
     count_launch();
 }
 void launch_frame_copy(const float2 *wv, const uint32_t *im, uint32_t nblocks, int m, int e, const EncTarget *tgt,
@@ -579,9 +485,9 @@ void launch_frame_copy(const float2 *wv, const uint32_t *im, uint32_t nblocks, i
 
 void launch_reserve(uint32_t nblocks, const uint64_t *need, uint64_t add_const, const float *pred_log2,
                     double margin, uint64_t worst, const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt,
-                    EncResult *res, int retry_overflowed, int *status, cudaStream_t s, uint32_t *pending) {
+                    EncResult *res, int retry_overflowed, int *status, cudaStream_t s) {
     k_reserve<<<(nblocks + 127) / 128, 128, 0, s>>>(nblocks, need, add_const, pred_log2, margin, worst, dev, host,
-                                                    tgt, res, retry_overflowed, status, pending);
+                                                    tgt, res, retry_overflowed, status);
     count_launch();
 }
 

@@ -64,7 +64,6 @@ struct LookbackScratch {
     uint32_t *done;
     uint32_t *epoch;
     float2 *part;       // per-frame (err_sq, norm_sq) partials, or null (then per-CTA atomics)
-    uint32_t *pending;  // learned sizing: blocks to re-encode (counted by the exact re-reservation), or null
 };
 
 void count_launch();
@@ -79,22 +78,16 @@ void launch_encode(const float2 *wv, uint32_t nblocks, int m, int e, const EncTa
 void launch_size_reserve(const float2 *wv, uint32_t nblocks, int m, int e, uint64_t *sizes, uint32_t *done_ctr,
                          const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, int *status,
                          cudaStream_t s);
-// learned-sizing encoder (warp per frame, ticket order, warp look-back); only_overflowed: re-encode the blocks
-// whose first pass overflowed its reserved slot. With fix_dev/fix_host the first pass's last CTA reserves exact
-// slots for those blocks (counted in scr.pending).
-void launch_encode_lbw(const float2 *wv, uint32_t nblocks, int m, int e, EncTarget *tgt, EncResult *res,
-                       int only_overflowed, const uint32_t *ids, BlockSlot *table, StageAccum *acc,
-                       const LookbackScratch &scr, const ArenaDev *fix_dev, const ArenaDev *fix_host, int *status,
-                       cudaStream_t s);
 // In-place exact encoder: pass 1 encodes every frame over its own amplitudes (Im-plane words to im, 4 bytes
 // per amplitude), records the frames' lengths, word counts (fwords) and offsets and reserves each block's
 // exact slot; pass 2 (launch_frame_copy) copies the frames into the slots. wv is overwritten.
 // rel: QSZR (e is the shift k, wrec holds kQszrSideBytes per frame, fmixed one word per frame); without a
-// device arena (dev.bump null) tgt is the caller's and nothing is reserved.
+// device arena (dev.bump null) tgt is the caller's and nothing is reserved. keep_fitting: learned sizing, a
+// block keeps its predicted slot (tgt, reserved beforehand) when it fits, else gets an exact one.
 void launch_encode_ip(float2 *wv, uint32_t *im, uint32_t nblocks, int m, int e, uint32_t *done_ctr,
                       const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt, EncResult *res, StageAccum *acc,
                       uint8_t *wrec, uint32_t *flen, uint32_t *fwords, uint32_t *foff, float2 *part, int *status,
-                      cudaStream_t s, bool rel = false, uint32_t *fmixed = nullptr);
+                      cudaStream_t s, bool rel = false, uint32_t *fmixed = nullptr, bool keep_fitting = false);
 void launch_frame_copy(const float2 *wv, const uint32_t *im, uint32_t nblocks, int m, int e, const EncTarget *tgt,
                        EncResult *res, const uint32_t *ids, BlockSlot *table, StageAccum *acc, const uint8_t *wrec,
                        const uint32_t *flen, const uint32_t *fwords, const uint32_t *foff, cudaStream_t s,
@@ -111,10 +104,9 @@ struct PreOps {
 // decode with the block references read from table[ids[j]]
 void launch_decode_table(const BlockSlot *table, const uint32_t *ids, uint32_t nblocks, int m, float2 *wv,
                          uint32_t *hist, int *status, const PreOps &pre, cudaStream_t s, bool rel = false);
-// pending (nullable): zeroed by a first reservation, counts the blocks re-reserved by retry_overflowed
 void launch_reserve(uint32_t nblocks, const uint64_t *need, uint64_t add_const, const float *pred_log2,
                     double margin, uint64_t worst, const ArenaDev &dev, const ArenaDev &host, EncTarget *tgt,
-                    EncResult *res, int retry_overflowed, int *status, cudaStream_t s, uint32_t *pending = nullptr);
+                    EncResult *res, int retry_overflowed, int *status, cudaStream_t s);
 void launch_copy_out(const float2 *wv, uint32_t nblocks, int m, const EncTarget *tgt, const uint32_t *ids,
                      BlockSlot *table, StageAccum *acc, int *status, cudaStream_t s);
 void launch_copy_in(const BlockRef *in, uint32_t nblocks, int m, float2 *wv, int *status, cudaStream_t s);

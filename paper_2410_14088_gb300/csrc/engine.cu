@@ -292,7 +292,6 @@ static int ensure_device_ctx(DeviceCtx &c) {
 static LookbackScratch make_scratch(uint64_t *state, uint32_t *ctr, float2 *part = nullptr) {
     LookbackScratch s{};
     s.part = part;
-    s.pending = nullptr;
     s.state = state;
     s.ticket = ctr;
     s.done = ctr + 1;
@@ -967,8 +966,8 @@ static int prepare_run(RunCtx &R, const qsim_plan *p, const DeviceCtx &dctx) {
     R.nst = p->stages.size();
     R.raw = cfg.codec == QSIM_CODEC_NONE;
     R.rel = cfg.codec == QSIM_CODEC_QSZR;
-    if (R.rel && (R.persistent || cfg.sizing != QSIM_SIZING_EXACT || cfg.collect))
-        return set_error(QSIM_E_UNSUPPORTED, "the relative-bound codec runs in streams mode with exact sizing");
+    if (R.rel && R.persistent)
+        return set_error(QSIM_E_UNSUPPORTED, "the relative-bound codec runs in streams mode");
     if (R.rel ? !qszr_shift(cfg.eps, &R.e)
               : (!R.raw && !qsz_step_exponent(cfg.eps * std::pow(2.0, -double(R.n) / 2.0), &R.e)))
         return set_error(QSIM_E_INVALID, "error bound out of range");
@@ -1414,8 +1413,6 @@ static int finish_run(RunCtx &R, int dev, double ms, Profiler *prof, qsim_stats 
             }
             if (raw) {
                 bytes[P_COPY_OUT] += 8 * amps + out_store;
-            } else if (predict) {
-                bytes[P_ENCODE] += 8 * amps + out_store;
             } else {
                 bytes[P_ENCODE] += 8 * amps + out_store;  // frames written in place
                 bytes[P_FRAME_COPY] += 2 * out_store;
@@ -1538,7 +1535,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             (rc = w.part.alloc(max_batch_blocks * nframes)) || (rc = w.hist.alloc(max_batch_blocks * 32)) ||
             (rc = w.pred.alloc(max_batch_blocks)) ||
             (!persistent && (rc = w.wrec.alloc(max_batch_blocks * nframes * (RC.rel ? kQszrSideBytes : 256)))) ||
-            (!persistent && !predict && !raw && (rc = w.imsc.alloc(max_batch_blocks << m))) ||
+            (!persistent && !raw && (rc = w.imsc.alloc(max_batch_blocks << m))) ||
             (!persistent && (rc = w.fwords.alloc(max_batch_blocks * nframes))) ||
             (RC.rel && (rc = w.fmixed.alloc(max_batch_blocks * nframes))) ||
             (rc = w.flen.alloc(max_batch_blocks * nframes)) || (rc = w.foff.alloc(max_batch_blocks * nframes)) ||
@@ -1662,22 +1659,21 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
                 launch_copy_out(w.wv.p, nb, m, w.tgt.p, ids, tab_out, acc, status, w.s);
                 prof.end(w.s);
             } else {
-                LookbackScratch scr = make_scratch(w.lb_state.p, w.lb_ctr.p, w.part.p);
-                scr.pending = w.lb_ctr.p + 4;
                 if (predict) {
-                    // reserve 2^pred (1 + margin) bytes, encode once, re-encode under-estimated blocks exactly
+                    // reserve 2^pred (1 + margin) bytes per block ahead of the encoder; the in-place encoder keeps
+                    // every slot its block fits and reserves exact slots for under-estimated blocks; copy
                     prof.begin(P_RESERVE, w.s);
                     launch_reserve(nb, nullptr, 0, w.pred.p, cfg.predictor_margin, worst, arena_dev(out_par),
-                                   arena_host(out_par), w.tgt.p, w.res.p, 0, status, w.s, scr.pending);
+                                   arena_host(out_par), w.tgt.p, w.res.p, 0, status, w.s);
                     prof.end(w.s);
                     prof.begin(P_ENCODE, w.s);
-                    const ArenaDev fd = arena_dev(out_par), fh = arena_host(out_par);
-                    launch_encode_lbw(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 0, ids, tab_out, acc, scr, &fd, &fh, status,
-                                      w.s);
+                    launch_encode_ip(w.wv.p, w.imsc.p, nb, m, e, w.lb_ctr.p + 3, arena_dev(out_par),
+                                     arena_host(out_par), w.tgt.p, w.res.p, acc, w.wrec.p, w.flen.p, w.fwords.p,
+                                     w.foff.p, w.part.p, status, w.s, RC.rel, w.fmixed.p, true);
                     prof.end(w.s);
-                    prof.begin(P_REENCODE, w.s);
-                    launch_encode_lbw(w.wv.p, nb, m, e, w.tgt.p, w.res.p, 1, ids, tab_out, acc, scr, nullptr, nullptr,
-                                      status, w.s);
+                    prof.begin(P_FRAME_COPY, w.s);
+                    launch_frame_copy(w.wv.p, w.imsc.p, nb, m, e, w.tgt.p, w.res.p, ids, tab_out, acc, w.wrec.p,
+                                      w.flen.p, w.fwords.p, w.foff.p, w.s, RC.rel, w.fmixed.p);
                     prof.end(w.s);
                 } else {
                     // exact sizing: encode every frame in place, reserve exact slots, copy the frames over

@@ -115,10 +115,26 @@ def test_stage_loop_stores_relative_streams(m):
 
 def test_relative_codec_mode_limits():
     c = inputs.random_brick(12, 2, 1)
-    for kw in (dict(mode=qsim.MODE_PERSISTENT), dict(sizing=qsim.SIZING_PREDICT)):
-        with pytest.raises(qsim.QsimError) as ei:
-            qsim.plan_stages(c, m=9, inner=2, k=4, eps=1e-3, codec=qsim.CODEC_QSZR, **kw)
-        assert ei.value.code == qsim.E_UNSUPPORTED
+    with pytest.raises(qsim.QsimError) as ei:
+        qsim.plan_stages(c, m=9, inner=2, k=4, eps=1e-3, codec=qsim.CODEC_QSZR, mode=qsim.MODE_PERSISTENT)
+    assert ei.value.code == qsim.E_UNSUPPORTED
+
+
+def test_relative_codec_with_learned_sizing():
+    # rows logged by relative-bound runs train the predictor; predicted slots store the same streams as exact
+    # sizing, and a forced under-estimate re-reserves exactly
+    kw = dict(m=10, inner=2, k=4, eps=1e-3, codec=qsim.CODEC_QSZR)
+    rows = np.concatenate([qsim.run(qsim.plan_stages(inputs.random_brick(14, 6, 300 + s), collect=1, **kw))
+                           .training_data() for s in range(3)])
+    qsim.predictor_train(rows, epochs=30, batch=64, lr=3e-3, seed=5)
+    c = inputs.random_brick(14, 8, 4)
+    exact = qsim.run(qsim.plan_stages(c, **kw))
+    for margin in (0.25, -0.9):
+        pred = qsim.run(qsim.plan_stages(c, sizing=qsim.SIZING_PREDICT, predictor_margin=margin, **kw))
+        for b in range(16):
+            assert pred.block_stream(b) == exact.block_stream(b)
+        if margin < 0:
+            assert pred.stats.overflow_blocks > 0
 
 
 def test_relative_streams_in_host_tier_and_readout():
