@@ -939,8 +939,9 @@ __device__ __forceinline__ int32_t quantize_one(float x, float inv_step, uint32_
 // words receives its Re-plane words | Im-plane words << 16 (each at most
 // 4096), mixed (REL) its Re | Im mixed sign chunks << 16. The second pass
 // (copy_frame_warp) moves the pieces to the frame's offset in the block's slot.
-// e is the step exponent (QSZ1) or the shift k (REL).
-template <bool REL = false>
+// e is the step exponent (QSZ1) or the shift k (REL). With CG the amplitudes are read through L2 (written by
+// other CTAs of the same launch).
+template <bool REL = false, bool CG = false>
 __device__ __forceinline__ uint32_t encode_frame_warp_ip(float2 *frame, uint32_t *__restrict__ im,
                                                          const FrameGeom &g, int e, uint8_t *__restrict__ side,
                                                          uint32_t &words, uint32_t &mixed, float2 *part_item,
@@ -957,7 +958,7 @@ __device__ __forceinline__ uint32_t encode_frame_warp_ip(float2 *frame, uint32_t
 #pragma unroll
         for (int t = 0; t < 8; ++t) {
             const uint32_t c = c0 + t;
-            vin[t] = c < g.C ? frame[c * 32 + lane] : make_float2(0.f, 0.f);
+            vin[t] = c < g.C ? (CG ? __ldcg(frame + c * 32 + lane) : frame[c * 32 + lane]) : make_float2(0.f, 0.f);
         }
         __syncwarp();  // every lane's reads of this batch come before the batch's in-place writes
 #pragma unroll

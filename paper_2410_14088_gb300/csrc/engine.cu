@@ -954,8 +954,8 @@ static int prepare_run(RunCtx &R, const qsim_plan *p, const DeviceCtx &dctx) {
     const qsim_config &cfg = p->cfg;
     R.p = p;
     R.persistent = cfg.mode == QSIM_MODE_PERSISTENT;
-    if (R.persistent && cfg.codec != QSIM_CODEC_QSZ1)
-        return set_error(QSIM_E_INVALID, "persistent mode runs the compressed store (codec QSZ1)");
+    if (R.persistent && cfg.codec == QSIM_CODEC_NONE)
+        return set_error(QSIM_E_INVALID, "persistent mode runs the compressed store (codec QSZ1 or QSZR)");
     if (R.persistent && cfg.collect)
         return set_error(QSIM_E_INVALID, "training-row collection runs in streams mode");
     int rc = upload_plan(p, &R.pd);
@@ -966,8 +966,6 @@ static int prepare_run(RunCtx &R, const qsim_plan *p, const DeviceCtx &dctx) {
     R.nst = p->stages.size();
     R.raw = cfg.codec == QSIM_CODEC_NONE;
     R.rel = cfg.codec == QSIM_CODEC_QSZR;
-    if (R.rel && R.persistent)
-        return set_error(QSIM_E_UNSUPPORTED, "the relative-bound codec runs in streams mode");
     if (R.rel ? !qszr_shift(cfg.eps, &R.e)
               : (!R.raw && !qsz_step_exponent(cfg.eps * std::pow(2.0, -double(R.n) / 2.0), &R.e)))
         return set_error(QSIM_E_INVALID, "error bound out of range");
@@ -1163,17 +1161,19 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         }
         if (frames_total >= (1ull << 32)) return set_error(QSIM_E_UNSUPPORTED, "working-vector slot plan too large");
     }
+    const bool rel = rs[0]->rel;  // one codec per launch (the batch entry points check it)
     DevBuf<float2> wv, part;
     DevBuf<uint8_t> wrec;
-    DevBuf<uint32_t> flen, foff;
+    DevBuf<uint32_t> flen, foff, fwords, fmixed, im;
     DevBuf<uint64_t> lb, dg_wv;
     DevBuf<uint32_t> sync, fin, ctr, dg_frame, dg_prev;
     DevBuf<PSeg> dsegs;
     if ((rc = wv.alloc(wv_total)) || (rc = lb.alloc(frames_total)) || (rc = part.alloc(frames_total)) ||
         (rc = sync.alloc(2 * total_groups * kMaxPhases)) || (rc = fin.alloc(2 * nseg)) || (rc = ctr.alloc(4)) ||
         (rc = dsegs.alloc(nseg)) || (rc = dg_wv.alloc(total_groups)) || (rc = dg_frame.alloc(total_groups)) ||
-        (rc = dg_prev.alloc(total_groups)) || (rc = wrec.alloc(frames_total * 256)) ||
-        (rc = flen.alloc(frames_total)) || (rc = foff.alloc(frames_total)))
+        (rc = dg_prev.alloc(total_groups)) || (rc = wrec.alloc(frames_total * (rel ? kQszrSideBytes : 256))) ||
+        (rc = flen.alloc(frames_total)) || (rc = foff.alloc(frames_total)) ||
+        (rel && ((rc = fwords.alloc(frames_total)) || (rc = fmixed.alloc(frames_total)) || (rc = im.alloc(wv_total)))))
         return rc;
     CUDA_TRY(cudaMemcpyAsync(dg_wv.p, g_wv.data(), total_groups * sizeof(uint64_t), cudaMemcpyHostToDevice, main));
     CUDA_TRY(cudaMemcpyAsync(dg_frame.p, g_frame.data(), total_groups * sizeof(uint32_t), cudaMemcpyHostToDevice,
@@ -1218,15 +1218,17 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         add(PH_DECODE, (gframes + 7) / 8, 0);
         if (R.predict) add(PH_PREDICT, 1, 0);
         for (uint32_t pi = 0; pi < sd.npasses; ++pi) add(PH_PASS, 1u << sd.passes_host[pi].nout, pi);
-        if (R.predict) {
+        if (R.rel) {
+            // relative-bound codec: in-place encoder (exact slots, or predicted slots kept when they fit), copy
+            add(PH_ENCODE_IP, (gframes + 7) / 8, 0);
+            add(PH_COPY, (gframes + 7) / 8, 0);
+        } else if (R.predict) {
             add(PH_ENCODE, (gframes + 7) / 8, 0);
+            add(PH_FIX, 1, 0);
+            add(PH_REENCODE, (gframes + 7) / 8, 0);
         } else {
             add(PH_SIZE_W, (gframes + 7) / 8, 0);
             add(PH_ENCODE_W, (gframes + 7) / 8, 0);
-        }
-        if (R.predict) {
-            add(PH_FIX, 1, 0);
-            add(PH_REENCODE, (gframes + 7) / 8, 0);
         }
         // the last phase index is the group's finished flag
         if (nph > uint32_t(kMaxPhases) - 1)
@@ -1285,13 +1287,16 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
     }
     CUDA_TRY(cudaMemcpyAsync(dsegs.p, segs.data(), nseg * sizeof(PSeg), cudaMemcpyHostToDevice, main));
     const size_t smem = persistent_smem_bytes(max_pass_bytes);
-    if ((rc = prepare_stage_persistent(prec, smem))) return set_error(rc, "persistent kernel set-up failed");
+    if ((rc = prepare_stage_persistent(prec, smem, rel))) return set_error(rc, "persistent kernel set-up failed");
 
     PLaunch L{};
     L.wv = wv.p;
     L.wrec = wrec.p;
     L.flen = flen.p;
     L.foff = foff.p;
+    L.im = im.p;
+    L.fwords = fwords.p;
+    L.fmixed = fmixed.p;
     L.lb = lb.p;
     L.part = part.p;
     L.ctr = ctr.p;
@@ -1334,7 +1339,7 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         L.done = sync.p + seg_group_off[k0] * kMaxPhases;
         L.arrive = sync.p + (total_groups + seg_group_off[k0]) * kMaxPhases;
         prof.begin(P_STAGE, cs);
-        rc = launch_stage_persistent(L, prec, smem, cs, nullptr);
+        rc = launch_stage_persistent(L, prec, smem, cs, nullptr, rel);
         prof.end(cs);
         if (rc) {
             end_capture_on_error();
@@ -1534,9 +1539,9 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             (rc = w.sizes.alloc(max_batch_blocks)) || (rc = w.lb_state.alloc(max_batch_blocks * nframes)) ||
             (rc = w.part.alloc(max_batch_blocks * nframes)) || (rc = w.hist.alloc(max_batch_blocks * 32)) ||
             (rc = w.pred.alloc(max_batch_blocks)) ||
-            (!persistent && (rc = w.wrec.alloc(max_batch_blocks * nframes * (RC.rel ? kQszrSideBytes : 256)))) ||
-            (!persistent && !raw && (rc = w.imsc.alloc(max_batch_blocks << m))) ||
-            (!persistent && (rc = w.fwords.alloc(max_batch_blocks * nframes))) ||
+            ((!persistent || RC.rel) && (rc = w.wrec.alloc(max_batch_blocks * nframes * (RC.rel ? kQszrSideBytes : 256)))) ||
+            ((!persistent || RC.rel) && !raw && (rc = w.imsc.alloc(max_batch_blocks << m))) ||
+            ((!persistent || RC.rel) && (rc = w.fwords.alloc(max_batch_blocks * nframes))) ||
             (RC.rel && (rc = w.fmixed.alloc(max_batch_blocks * nframes))) ||
             (rc = w.flen.alloc(max_batch_blocks * nframes)) || (rc = w.foff.alloc(max_batch_blocks * nframes)) ||
             (rc = w.lb_ctr.alloc(8))) {
@@ -1734,9 +1739,11 @@ static int run_batch(const qsim_plan *const *plans, size_t count, cudaStream_t m
         const qsim_plan *p = plans[c];
         if (!p) return set_error(QSIM_E_INVALID, "batch entry %zu is null", c);
         const qsim_config &cfg = p->cfg;
-        if (cfg.codec != QSIM_CODEC_QSZ1 || cfg.collect)
+        if (cfg.codec == QSIM_CODEC_NONE || cfg.collect)
             return set_error(QSIM_E_INVALID, "batch entry %zu: a batch runs the compressed store without row collection",
                              c);
+        if (cfg.codec != plans[0]->cfg.codec)
+            return set_error(QSIM_E_INVALID, "batch entry %zu: every circuit of a batch uses the same codec", c);
         if (cfg.prec != plans[0]->cfg.prec)
             return set_error(QSIM_E_INVALID, "batch entry %zu: every circuit of a batch uses the same precision", c);
         rs[c].reset(new RunCtx());
@@ -1754,7 +1761,9 @@ static int run_batch(const qsim_plan *const *plans, size_t count, cudaStream_t m
     uint64_t ring_amps = 0;
     for (const auto &kv : w_groups)
         ring_amps += std::min<uint64_t>(kv.second, std::max<uint64_t>(2, slot_budget >> kv.first)) << kv.first;
-    const uint64_t work_bytes = ring_amps * 8 * 5 / 4 + (16ull << (mmax + 1));
+    const bool rel = plans[0]->cfg.codec == QSIM_CODEC_QSZR;
+    // 8 B per amplitude and a quarter for the frame scratch; the relative codec adds its 4 B imaginary words
+    const uint64_t work_bytes = ring_amps * (rel ? 12 : 10) + (16ull << (mmax + 1)) * (rel ? 2 : 1);
     const double dev_budget = free_b > work_bytes ? 0.85 * double(free_b - work_bytes) : 0.0;
     const double host_budget = 0.3 * double(host_phys_bytes());
     // each circuit's share of both levels follows its worst-case need
@@ -1765,7 +1774,11 @@ static int run_batch(const qsim_plan *const *plans, size_t count, cudaStream_t m
     StreamWork w;
     const uint64_t nframes_max = qsz_nframes(int(mmax));
     if ((rc = w.wv.alloc(2ull << mmax)) || (rc = w.tgt.alloc(2)) || (rc = w.res.alloc(2)) || (rc = w.sizes.alloc(2)) ||
-        (rc = w.lb_state.alloc(2 * nframes_max)) || (rc = w.lb_ctr.alloc(4)))
+        (rc = w.lb_state.alloc(2 * nframes_max)) || (rc = w.lb_ctr.alloc(4)) ||
+        (rel && ((rc = w.imsc.alloc(2ull << mmax)) || (rc = w.wrec.alloc(2 * nframes_max * kQszrSideBytes)) ||
+                 (rc = w.fwords.alloc(2 * nframes_max)) || (rc = w.fmixed.alloc(2 * nframes_max)) ||
+                 (rc = w.flen.alloc(2 * nframes_max)) || (rc = w.foff.alloc(2 * nframes_max)) ||
+                 (rc = w.part.alloc(2 * nframes_max)))))
         return rc;
     CUDA_TRY(cudaMemsetAsync(w.lb_state.p, 0, 2 * nframes_max * sizeof(uint64_t), main));
     CUDA_TRY(cudaMemsetAsync(w.lb_ctr.p, 0, 4 * sizeof(uint32_t), main));

@@ -53,7 +53,8 @@ __device__ __forceinline__ EncTarget load_target(const EncTarget *t) {
     return r;
 }
 
-template <int PREC>
+// REL: the relative-bound codec (QSZR) in the decode phase and the in-place exact phases
+template <int PREC, bool REL>
 __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
     extern __shared__ float4 dsm[];
     __shared__ gdev::PassSmem PS;
@@ -155,7 +156,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
         const uint64_t bbase = uint64_t(grp) * S.G;  // per-group block arrays
         const uint32_t sf0 = L.g_frame[q];  // the slot's first frame in wrec / flen / foff / part / lb
         bool by_arrival = type == PH_SIZE || type == PH_ENCODE || type == PH_REENCODE || type == PH_SIZE_W ||
-                          type == PH_ENCODE_W;
+                          type == PH_ENCODE_W || type == PH_ENCODE_IP || type == PH_COPY;
         if (abort_item) {
             // skip the work, keep the counts
         } else if (type == PH_DECODE) {
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             if (fi < gframes) {
                 const uint32_t jj = fi / g.nframes, f = fi % g.nframes;
                 const BlockSlot sl = S.tab_in[ids[jj]];
-                cdev::decode_frame_warp<kMaxPreOps>(sl.ptr, sl.bytes, g, int(S.m), f,
+                cdev::decode_frame_warp<kMaxPreOps, false, REL>(sl.ptr, sl.bytes, g, int(S.m), f,
                                                     wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F,
                                                     S.hist ? S.hist + (bbase + jj) * 32 : nullptr, s_hist[warp],
                                                     L.status, s_pre, s_pre_ab, S.npre, S.mats,
@@ -177,6 +178,38 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             const uint32_t len = cdev::size_frame_cta<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g, S.e,
                                                             s_words, L.status);
             if (tid == 0 && len) atomicAdd(reinterpret_cast<unsigned long long *>(&S.sizes[bbase + jj]), uint64_t(len));
+        } else if (REL && type == PH_ENCODE_IP) {
+            if constexpr (REL) {
+                const uint32_t fi = i * (PT / 32) + warp;
+                if (fi < gframes) {
+                    const uint32_t jj = fi / g.nframes, f = fi % g.nframes;
+                    const uint64_t a0 = (uint64_t(jj) << S.m) + uint64_t(f) * g.F;
+                    uint32_t words, mixed;
+                    const uint32_t len = cdev::encode_frame_warp_ip<true, true>(
+                        wv + a0, L.im + L.g_wv[q] + a0, g, S.e, L.wrec + uint64_t(sf0 + fi) * kQszrSideBytes, words,
+                        mixed, part + fi, L.status);
+                    if ((tid & 31) == 0) {
+                        L.flen[sf0 + fi] = len;
+                        L.fwords[sf0 + fi] = words;
+                        L.fmixed[sf0 + fi] = mixed;
+                        __threadfence();  // read by the phase's last item and the copy phase on other CTAs
+                    }
+                }
+            }
+        } else if (REL && type == PH_COPY) {
+            if constexpr (REL) {
+                const uint32_t fi = i * (PT / 32) + warp;
+                if (fi < gframes) {
+                    const uint32_t jj = fi / g.nframes, f = fi % g.nframes;
+                    const uint64_t a0 = (uint64_t(jj) << S.m) + uint64_t(f) * g.F;
+                    cdev::copy_frame_warp<true>(reinterpret_cast<const uint32_t *>(wv + a0), L.im + L.g_wv[q] + a0,
+                                                L.wrec + uint64_t(sf0 + fi) * kQszrSideBytes,
+                                                __ldcg(L.fwords + sf0 + fi), __ldcg(L.fmixed + sf0 + fi),
+                                                __ldcg(L.flen + sf0 + fi), __ldcg(L.foff + sf0 + fi), g, int(S.m),
+                                                S.e, f, load_target(&S.tgt[bbase + jj]), &S.res[bbase + jj],
+                                                S.tab_out + ids[jj], S.acc);
+                }
+            }
         } else if (type == PH_SIZE_W) {
             const uint32_t fi = i * (PT / 32) + warp;
             if (fi < gframes) {
@@ -276,8 +309,9 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
                 rs.norm_sq = 0;
                 cdev::reserve_slot(want_b, S.dev, S.host, &S.tgt[bbase + jj], L.status);
             }
-        } else if (type == PH_SIZE_W) {
-            // the group's frame lengths are complete: frame offsets (warp per block) and the group's slots
+        } else if (type == PH_SIZE_W || type == PH_ENCODE_IP) {
+            // the group's frame lengths are complete: frame offsets (warp per block) and the group's slots (the
+            // in-place phase with learned sizing keeps every predicted slot its block fits)
             const int lane = tid & 31;
             for (uint32_t jj = warp; jj < S.G; jj += PT / 32) {
                 uint32_t run = uint32_t(S.data_start);
@@ -299,10 +333,19 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
                     rs.overflow = 0;
                     rs.err_sq = 0;
                     rs.norm_sq = 0;
-                    cdev::reserve_slot(run, S.dev, S.host, &S.tgt[bbase + jj], L.status);
+                    EncTarget &t = S.tgt[bbase + jj];
+                    if (type == PH_ENCODE_IP && S.pparams) {
+                        if (t.ptr == nullptr || run > t.cap) {
+                            atomicAdd(reinterpret_cast<unsigned long long *>(&S.acc->overflow_blocks), 1ull);
+                            cdev::reserve_slot(run, S.dev, S.host, &t, L.status);
+                        }
+                    } else {
+                        cdev::reserve_slot(run, S.dev, S.host, &t, L.status);
+                    }
                 }
             }
-        } else if (type == PH_ENCODE || type == PH_ENCODE_W) {
+        }
+        if (!abort_item && (type == PH_ENCODE || type == PH_ENCODE_W || type == PH_ENCODE_IP)) {
             // the group's frames are encoded: fold their error partials into the stage totals
             double a = 0, b = 0;
             for (uint32_t t = tid; t < gframes; t += PT) {
@@ -351,42 +394,58 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
     }
 }
 
-template <int PREC>
+template <int PREC, bool REL>
 struct LaunchShape {
     static int grid;
     static size_t attr_smem;
 };
-template <int PREC> int LaunchShape<PREC>::grid = 0;
-template <int PREC> size_t LaunchShape<PREC>::attr_smem = 0;
+template <int PREC, bool REL> int LaunchShape<PREC, REL>::grid = 0;
+template <int PREC, bool REL> size_t LaunchShape<PREC, REL>::attr_smem = 0;
 
 // kernel attributes and the grid (one wave of resident CTAs); done outside any stream capture
-template <int PREC>
+template <int PREC, bool REL>
 int prepare_prec(size_t smem) {
-    if (LaunchShape<PREC>::attr_smem < smem) {
-        if (cudaFuncSetAttribute(k_stage_persistent<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem)) !=
-            cudaSuccess)
+    using Shape = LaunchShape<PREC, REL>;
+    if (Shape::attr_smem < smem) {
+        if (cudaFuncSetAttribute(k_stage_persistent<PREC, REL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 int(smem)) != cudaSuccess)
             return QSIM_E_CUDA;
-        LaunchShape<PREC>::attr_smem = smem;
-        LaunchShape<PREC>::grid = 0;
+        Shape::attr_smem = smem;
+        Shape::grid = 0;
     }
-    if (!LaunchShape<PREC>::grid) {
+    if (!Shape::grid) {
         int dev = 0, sms = 0, per_sm = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_persistent<PREC>, PT, smem);
-        LaunchShape<PREC>::grid = sms * (per_sm > 0 ? per_sm : 1);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_persistent<PREC, REL>, PT, smem);
+        Shape::grid = sms * (per_sm > 0 ? per_sm : 1);
     }
     return QSIM_OK;
 }
 
-template <int PREC>
+template <int PREC, bool REL>
 int launch_stage_prec(const PLaunch &a, size_t smem, cudaStream_t s, int *grid_out) {
-    if (LaunchShape<PREC>::attr_smem < smem || !LaunchShape<PREC>::grid) return QSIM_E_INVALID;
-    const int grid = LaunchShape<PREC>::grid;
-    k_stage_persistent<PREC><<<grid, PT, smem, s>>>(a);
+    using Shape = LaunchShape<PREC, REL>;
+    if (Shape::attr_smem < smem || !Shape::grid) return QSIM_E_INVALID;
+    const int grid = Shape::grid;
+    k_stage_persistent<PREC, REL><<<grid, PT, smem, s>>>(a);
     if (grid_out) *grid_out = grid;
     count_launch();
     return QSIM_OK;
+}
+
+template <bool REL>
+int prepare_codec(int prec, size_t smem) {
+    if (prec == QSIM_PREC_TF32) return prepare_prec<QSIM_PREC_TF32, REL>(smem);
+    if (prec == QSIM_PREC_BF16X3) return prepare_prec<QSIM_PREC_BF16X3, REL>(smem);
+    return prepare_prec<QSIM_PREC_FP32, REL>(smem);
+}
+
+template <bool REL>
+int launch_codec(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid) {
+    if (prec == QSIM_PREC_TF32) return launch_stage_prec<QSIM_PREC_TF32, REL>(a, smem, s, grid);
+    if (prec == QSIM_PREC_BF16X3) return launch_stage_prec<QSIM_PREC_BF16X3, REL>(a, smem, s, grid);
+    return launch_stage_prec<QSIM_PREC_FP32, REL>(a, smem, s, grid);
 }
 
 }  // namespace
@@ -396,16 +455,12 @@ size_t persistent_smem_bytes(size_t pass_bytes) {
     return pass_bytes > mlp ? pass_bytes : mlp;
 }
 
-int prepare_stage_persistent(int prec, size_t smem) {
-    if (prec == QSIM_PREC_TF32) return prepare_prec<QSIM_PREC_TF32>(smem);
-    if (prec == QSIM_PREC_BF16X3) return prepare_prec<QSIM_PREC_BF16X3>(smem);
-    return prepare_prec<QSIM_PREC_FP32>(smem);
+int prepare_stage_persistent(int prec, size_t smem, bool rel) {
+    return rel ? prepare_codec<true>(prec, smem) : prepare_codec<false>(prec, smem);
 }
 
-int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid) {
-    if (prec == QSIM_PREC_TF32) return launch_stage_prec<QSIM_PREC_TF32>(a, smem, s, grid);
-    if (prec == QSIM_PREC_BF16X3) return launch_stage_prec<QSIM_PREC_BF16X3>(a, smem, s, grid);
-    return launch_stage_prec<QSIM_PREC_FP32>(a, smem, s, grid);
+int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid, bool rel) {
+    return rel ? launch_codec<true>(a, prec, smem, s, grid) : launch_codec<false>(a, prec, smem, s, grid);
 }
 
 }  // namespace qsim

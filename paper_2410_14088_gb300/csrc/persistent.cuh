@@ -20,8 +20,13 @@ enum PhaseType : uint32_t {
     PH_REENCODE = 6, // one frame of an overflowed block (others skip)
     PH_SIZE_W = 7,   // exact sizing, eight frames per item (one warp each): widths and frame length;
                      // the last item turns the lengths into frame offsets and reserves the group's slots
-    PH_ENCODE_W = 8  // exact sizing, eight frames per item (one warp each) at the known offsets; the last
+    PH_ENCODE_W = 8, // exact sizing, eight frames per item (one warp each) at the known offsets; the last
                      // item folds the group's error partials into the stage totals
+    PH_ENCODE_IP = 9, // relative-bound codec: eight frames per item (one warp each) encoded over their own
+                      // amplitudes; the last item turns the lengths into frame offsets, reserves the group's
+                      // exact slots (with learned sizing: keeps every predicted slot its block fits) and folds
+                      // the error partials into the stage totals
+    PH_COPY = 10      // relative-bound codec: eight frames per item (one warp each) copied into their slots
 };
 
 struct PPhase {
@@ -84,9 +89,12 @@ struct PLaunch {
     float2 *wv;
     uint64_t *lb;
     float2 *part;
-    uint8_t *wrec;    // per slot frame: chunk widths (256 bytes)
+    uint8_t *wrec;    // per slot frame: chunk widths (256 bytes; relative codec: side record of 2048 bytes)
     uint32_t *flen;   // per slot frame: stream bytes
     uint32_t *foff;   // per slot frame: byte offset in the block's stream
+    uint32_t *im;     // relative codec: Im-plane words of the in-place encoder, laid out like wv
+    uint32_t *fwords; // relative codec, per slot frame: Re words | Im words << 16
+    uint32_t *fmixed; // relative codec, per slot frame: Re | Im mixed sign chunks << 16
     uint32_t *done, *arrive;  // per launch group x kMaxPhases each, zero at launch
     uint32_t *ctr;            // queue head, CTAs finished, look-back epoch
     int *status;
@@ -95,7 +103,7 @@ struct PLaunch {
 
 // pass_bytes: the largest tile + pass blob + matrix area of the launch's passes
 size_t persistent_smem_bytes(size_t pass_bytes);
-int prepare_stage_persistent(int prec, size_t smem);
-int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid);
+int prepare_stage_persistent(int prec, size_t smem, bool rel = false);
+int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid, bool rel = false);
 
 }  // namespace qsim

@@ -591,8 +591,6 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
     if (cfg->codec == QSIM_CODEC_QSZR) {
         int k;
         if (!qszr_shift(cfg->eps, &k)) return set_error(QSIM_E_INVALID, "relative bound eps out of range");
-        if (cfg->mode != QSIM_MODE_STREAMS)
-            return set_error(QSIM_E_UNSUPPORTED, "the relative-bound codec runs in streams mode");
     }
     if (ngates && !gates) return set_error(QSIM_E_INVALID, "gates is NULL");
 

@@ -1,6 +1,7 @@
 """GPU relative-bound codec (QSZR: Sec. 4.3, Eq. 1-2, Algorithm 2) vs the scalar oracle, through the C ABI:
 byte-identical streams and exact decodes for blocks of several sizes and value mixes, the point-wise relative
-bound, range / capacity / corruption errors, and the stage loop storing QSZR blocks that re-encode exactly."""
+bound, range / capacity / corruption errors, and the stage loop (stream engine, persistent kernel, batch)
+storing QSZR blocks that re-encode exactly."""
 import numpy as np
 import pytest
 
@@ -113,11 +114,39 @@ def test_stage_loop_stores_relative_streams(m):
     assert st.stats.fidelity_lower_bound >= 0.99 and st.stats.nstages >= 1
 
 
-def test_relative_codec_mode_limits():
-    c = inputs.random_brick(12, 2, 1)
+@pytest.mark.parametrize("prec", [qsim.PREC_FP32, qsim.PREC_TF32], ids=["fp32", "tf32"])
+@pytest.mark.parametrize("graph", [0, 1])
+def test_relative_codec_persistent_matches_streams(prec, graph):
+    # the persistent stage kernel's in-place encoder and frame copy store the stream engine's bytes
+    c = inputs.random_brick(16, 8, 2)
+    kw = dict(m=10, inner=2, k=5, eps=1e-3, prec=prec, codec=qsim.CODEC_QSZR)
+    ref = qsim.run(qsim.plan_stages(c, **kw))
+    per = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, graph=graph, **kw))
+    for b in range(64):
+        assert per.block_stream(b) == ref.block_stream(b)
+    assert per.fidelity(oracle.simulate(c)) >= 0.999
+
+
+def test_relative_codec_persistent_qft_and_batch():
+    # 2^22-amplitude working vectors with leading phase ops, then a uniform relative-codec batch in one launch
+    c = inputs.qft_rz_cx(24, 2, 5)
+    kw = dict(m=20, inner=2, k=5, eps=1e-3, codec=qsim.CODEC_QSZR)
+    ref = qsim.run(qsim.plan_stages(c, **kw))
+    per = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, graph=1, **kw))
+    for b in range(16):
+        assert per.block_stream(b) == ref.block_stream(b)
+    circuits = [inputs.random_brick(13, 6, 31), inputs.qft_rz_cx(12, 1, 4), inputs.ghz(11)]
+    plans = [qsim.plan_stages(x, m=x.n - 3, inner=2, k=4, eps=1e-3, codec=qsim.CODEC_QSZR) for x in circuits]
+    states, launch = qsim.run_batch(plans)
+    assert launch["launches"] == 1
+    for x, p, st in zip(circuits, plans, states):
+        one = qsim.run(p)
+        for b in range(8):
+            assert st.block_stream(b) == one.block_stream(b), x.family
+    mixed = [plans[0], qsim.plan_stages(circuits[1], m=9, inner=2, k=4, eps=1e-3)]
     with pytest.raises(qsim.QsimError) as ei:
-        qsim.plan_stages(c, m=9, inner=2, k=4, eps=1e-3, codec=qsim.CODEC_QSZR, mode=qsim.MODE_PERSISTENT)
-    assert ei.value.code == qsim.E_UNSUPPORTED
+        qsim.run_batch(mixed)  # one codec per batch
+    assert ei.value.code == qsim.E_INVALID
 
 
 def test_relative_codec_with_learned_sizing():
@@ -135,6 +164,13 @@ def test_relative_codec_with_learned_sizing():
             assert pred.block_stream(b) == exact.block_stream(b)
         if margin < 0:
             assert pred.stats.overflow_blocks > 0
+    for margin in (0.25, -0.9):  # the persistent kernel keeps fitting predicted slots the same way
+        per = qsim.run(qsim.plan_stages(c, sizing=qsim.SIZING_PREDICT, predictor_margin=margin,
+                                        mode=qsim.MODE_PERSISTENT, **kw))
+        for b in range(16):
+            assert per.block_stream(b) == exact.block_stream(b)
+        if margin < 0:
+            assert per.stats.overflow_blocks > 0
 
 
 def test_relative_streams_in_host_tier_and_readout():

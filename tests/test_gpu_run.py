@@ -134,7 +134,7 @@ def test_qft_separable_phase_ops(prec, mode):
     c = inputs.Circuit(n, inputs.qft_gates(n), x)
     p = qsim.plan_stages(c, m=14, inner=4, k=5, codec=qsim.CODEC_NONE, prec=prec, mode=qsim.MODE_STREAMS)
     assert any(o["type"] == 3 for s in range(p.nstages) for o in p.stage_ops(s))
-    if mode == qsim.MODE_PERSISTENT:  # the compressed store (persistent mode runs QSZ1)
+    if mode == qsim.MODE_PERSISTENT:  # persistent mode runs a compressed store
         st = qsim.run(qsim.plan_stages(c, m=14, inner=4, k=5, eps=1e-4, prec=prec, mode=mode))
         assert st.fidelity(cf.qft_basis_state(n, x)) >= 0.999
         return
