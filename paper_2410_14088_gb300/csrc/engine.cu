@@ -525,16 +525,26 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                         od.tq[j] = t;
                     }
                     const uint32_t min_k = p->cfg.prec == QSIM_PREC_TF32 ? 3u : 4u;
+                    // k = 5 TF32 ops of the stream engine's 4096-amplitude passes on tcgen05 when asked for
+                    // (one thread per index group: the complement ordered for that gather)
+                    const bool um = p->cfg.tcgen05 && p->cfg.prec == QSIM_PREC_TF32 && op.k == 5 && ps.T == 12 &&
+                                    p->cfg.mode == QSIM_MODE_STREAMS;
                     order_complement(od, ps.T,
-                                     p->cfg.prec != QSIM_PREC_FP32 && op.k >= min_k && op.k <= 5 && ps.T == 12);
+                                     !um && p->cfg.prec != QSIM_PREC_FP32 && op.k >= min_k && op.k <= 5 &&
+                                         ps.T == 12);
                     od.mat = mats.size();
                     for (const cd &v : op.u) mats.push_back(make_float2(float(v.real()), float(v.imag())));
                     P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << (2 * op.k));
                     if (p->cfg.prec != QSIM_PREC_FP32 && op.k >= 3 && op.k <= 5) {
+                        bfr.resize((bfr.size() + 3) & ~size_t(3));  // 16-byte aligned tables
                         od.bfrag = bfr.size();
                         bfr.resize(bfr.size() + bfrag_words(op.k, int(p->cfg.prec)));
-                        build_bfrag_table(reinterpret_cast<const double *>(op.u.data()), op.k, int(p->cfg.prec),
-                                          bfr.data() + od.bfrag);
+                        if (um)
+                            build_umma_b(reinterpret_cast<const double *>(op.u.data()), bfr.data() + od.bfrag);
+                        else
+                            build_bfrag_table(reinterpret_cast<const double *>(op.u.data()), op.k, int(p->cfg.prec),
+                                              bfr.data() + od.bfrag);
+                        if (um) P.umma = 1;
                     }
                     P.kmax = std::max<uint32_t>(P.kmax, op.k);
                 } else if (op.type == OP_CSEP) {
@@ -1652,7 +1662,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             for (uint32_t pi = 0; pi < sd.npasses; ++pi) {
                 prof.begin(P_PASS, w.s);
                 launch_pass(w.wv.p, sd.W, ng, &sd.passes_host[pi], pd->blob.p, pd->mats.p, pd->bfr.p, gb_stage + g0,
-                            cfg.prec, w.s);
+                            cfg.prec, w.s, status);
                 prof.end(w.s);
             }
             if (raw) {

@@ -34,40 +34,56 @@ constexpr int NT = 128;
 // with two tile buffers per CTA and cp.async prefetch of the next tile ran
 // slower on GB300: fewer resident CTAs, 3.1 against 4.3 TB/s on load/store-only
 // passes.)
-template <int KMAX, int PREC>
+// UM: the pass's k = 5 dense ops run on tcgen05 (a separate instantiation, so that the warp-MMA kernels
+// keep their own register allocation)
+template <int KMAX, int PREC, bool UM>
 __global__ void __launch_bounds__(NT, (KMAX >= 6 ? 2 : (PREC == QSIM_PREC_BF16X3 && KMAX >= 4) ? 3 : 4))
     k_pass(float2 *__restrict__ wv, uint32_t W, const __grid_constant__ PassDev P, const uint4 *__restrict__ blob,
-           const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr, const uint64_t *__restrict__ gbase) {
+           const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr, const uint64_t *__restrict__ gbase,
+           int *status) {
     extern __shared__ float4 dyn_smem[];
     __shared__ PassSmem S;
     float2 *g = wv + (uint64_t(blockIdx.y) << W);
     const uint64_t gb = gbase ? gbase[blockIdx.y] : 0ull;
-    pass_tile<NT, KMAX, PREC, false>(g, P, blob, mats, bfr, blockIdx.x, gb, S, reinterpret_cast<float2 *>(dyn_smem));
+    pass_tile<NT, KMAX, PREC, false, UM>(g, P, blob, mats, bfr, blockIdx.x, gb, S,
+                                         reinterpret_cast<float2 *>(dyn_smem), status);
+}
+
+template <int KMAX, int PREC, bool UM>
+void launch_pass_ku(dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W, const PassDev &P,
+                    const uint4 *blob, const float2 *mats, const uint32_t *bfr, const uint64_t *gbase, int *status) {
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaFuncSetAttribute(k_pass<KMAX, PREC, UM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr_set = true;
+    }
+    k_pass<KMAX, PREC, UM><<<grid, NT, smem, s>>>(wv, W, P, blob, mats, bfr, gbase, status);
 }
 
 template <int KMAX, int PREC>
 void launch_pass_k(dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W, const PassDev &P,
-                   const uint4 *blob, const float2 *mats, const uint32_t *bfr, const uint64_t *gbase) {
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaFuncSetAttribute(k_pass<KMAX, PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr_set = true;
+                   const uint4 *blob, const float2 *mats, const uint32_t *bfr, const uint64_t *gbase, int *status) {
+    if constexpr (PREC == QSIM_PREC_TF32 && KMAX >= 5) {
+        if (P.umma) {
+            launch_pass_ku<KMAX, PREC, true>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status);
+            return;
+        }
     }
-    k_pass<KMAX, PREC><<<grid, NT, smem, s>>>(wv, W, P, blob, mats, bfr, gbase);
+    launch_pass_ku<KMAX, PREC, false>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status);
 }
 
 template <int PREC>
 void launch_pass_prec(uint32_t kmax, dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W,
                       const PassDev &P, const uint4 *blob, const float2 *mats, const uint32_t *bfr,
-                      const uint64_t *gbase) {
+                      const uint64_t *gbase, int *status) {
     switch (kmax) {
-        case 0: launch_pass_k<0, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
-        case 1: launch_pass_k<1, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
-        case 2: launch_pass_k<2, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
-        case 3: launch_pass_k<3, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
-        case 4: launch_pass_k<4, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
-        case 5: launch_pass_k<5, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
-        default: launch_pass_k<6, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase); break;
+        case 0: launch_pass_k<0, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
+        case 1: launch_pass_k<1, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
+        case 2: launch_pass_k<2, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
+        case 3: launch_pass_k<3, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
+        case 4: launch_pass_k<4, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
+        case 5: launch_pass_k<5, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
+        default: launch_pass_k<6, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
     }
 }
 
@@ -144,21 +160,37 @@ void build_bfrag_table(const double *u, uint32_t k, int prec, uint32_t *out) {
             }
 }
 
+size_t pass_smem_bytes(const PassDev &P) {
+    return (size_t(1) << P.T) * sizeof(float2) + (P.umma ? size_t(kUmmaExtraSmem) : 0) + size_t(P.blob_words) * 16 +
+           size_t(P.mat_elems) * sizeof(float2);
+}
+
+void build_umma_b(const double *u, uint32_t *out) {
+    constexpr uint32_t D = 32;
+    for (uint32_t n = 0; n < 2 * D; ++n)
+        for (uint32_t kk = 0; kk < 2 * D; ++kk) {
+            const uint32_t r = n % D, c = kk % D;
+            const double re = u[2 * (size_t(r) * D + c)], im = u[2 * (size_t(r) * D + c) + 1];
+            const double v = n < D ? (kk < D ? re : -im) : (kk < D ? im : re);
+            const uint32_t a = kk / 32, ch = (kk % 32) / 4, w = kk % 4;
+            const size_t byte = size_t(a) * 8192 + (n / 8) * 1024 + (n % 8) * 128 + ((ch ^ (n % 8)) * 16) + w * 4;
+            out[byte / 4] = to_tf32(float(v));
+        }
+}
+
 void launch_pass(float2 *wv, uint32_t W, uint32_t ngroups, const PassDev *pass_host, const uint4 *blob_dev,
                  const float2 *mats_dev, const uint32_t *bfr_dev, const uint64_t *gbase_dev, int prec,
-                 cudaStream_t s) {
+                 cudaStream_t s, int *status) {
     const PassDev &P = *pass_host;
-    // tile, pass blob, matrix area
-    const size_t smem = (size_t(1) << P.T) * sizeof(float2) + size_t(P.blob_words) * 16 +
-                        size_t(P.mat_elems) * sizeof(float2);
+    const size_t smem = pass_smem_bytes(P);
     dim3 grid(1u << P.nout, ngroups);
     const uint32_t kmax = P.kmax;
     if (prec == QSIM_PREC_TF32 && kmax >= 3)
-        launch_pass_prec<QSIM_PREC_TF32>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev);
+        launch_pass_prec<QSIM_PREC_TF32>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev, status);
     else if (prec == QSIM_PREC_BF16X3 && kmax >= 3)
-        launch_pass_prec<QSIM_PREC_BF16X3>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev);
+        launch_pass_prec<QSIM_PREC_BF16X3>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev, status);
     else
-        launch_pass_prec<QSIM_PREC_FP32>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev);
+        launch_pass_prec<QSIM_PREC_FP32>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev, status);
     count_launch();
 }
 

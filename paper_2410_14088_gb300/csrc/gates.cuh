@@ -21,7 +21,7 @@ struct PassDev {
     uint32_t kmax;           // widest dense op of the pass (0 if none)
     uint32_t blob_words;     // 16-byte words of the pass blob: op descriptors, phase tables, small matrices
     uint32_t blob_off;       // its first word in the plan's blob array
-    uint32_t pad0;
+    uint32_t umma;           // 1: the pass's k = 5 TF32 dense ops run on tcgen05 (B operands in 128-byte swizzled form)
     uint64_t out_mask;       // working-index mask of the non-tile bits
     uint32_t tile_pos[16];   // working bit of tile bit t (ascending)
     uint32_t out_pos[32];    // working bit of CTA-index bit t
@@ -66,8 +66,17 @@ constexpr uint32_t kPassBlobMax = 40960;    // bytes of one pass blob (shared me
 void build_bfrag_table(const double *u_interleaved, uint32_t k, int prec, uint32_t *out);
 size_t bfrag_words(uint32_t k, int prec);
 
+// The B operand of a k = 5 dense op for tcgen05 (4096 words, the same count as its TF32 fragment table):
+// B^T = U_r rounded to TF32, row n = output n (Re outputs 0..31, then Im), column = input (Re inputs, then
+// Im), K-major in the 128-byte swizzled layout: column block a = input / 32 at byte 8192 a, row n at
+// 1024 (n / 8) + 128 (n % 8), 16-byte chunk c = (input % 32) / 4 stored at chunk position c ^ (n % 8).
+void build_umma_b(const double *u_interleaved, uint32_t *out);
+
 void launch_pass(float2 *wv, uint32_t W, uint32_t ngroups, const PassDev *pass_host, const uint4 *blob_dev,
                  const float2 *mats_dev, const uint32_t *bfr_dev, const uint64_t *gbase_dev, int prec,
-                 cudaStream_t s);
+                 cudaStream_t s, int *status);
+
+// dynamic shared memory of one tile pass (tile, B operand and alignment when on tcgen05, blob, matrices)
+size_t pass_smem_bytes(const PassDev &P);
 
 }  // namespace qsim

@@ -10,6 +10,7 @@
 #include "codec.cuh"
 #include "device_common.cuh"
 #include "gates.cuh"
+#include "umma.cuh"
 
 namespace qsim {
 namespace gdev {
@@ -44,6 +45,9 @@ struct PassSmem {
     float2 csq[2][64];
     float2 ck[2];
     uint32_t cbconst;           // the branch when the control is outside the tile
+    // passes with tcgen05 dense ops: the MMA-completion mbarrier and the TMEM accumulator's base address
+    uint64_t mbar;
+    uint32_t tmem;
 };
 static_assert(sizeof(OpDev) % 16 == 0, "op descriptors are copied as 16-byte words");
 
@@ -266,6 +270,79 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
     }
 }
 
+// Bytes of shared memory a tcgen05 pass adds: the B operand of one op and the slack that aligns the tile
+// (the A operand while the MMAs run) to 1024 bytes.
+constexpr uint32_t kUmmaBBytes = 16384;
+constexpr uint32_t kUmmaExtraSmem = kUmmaBBytes + 1024;
+constexpr uint32_t kUmmaIdesc = umma::idesc_tf32(128, 64);
+constexpr uint64_t kUmmaWaitNs = 1000000000ull;  // bound on one MMA-completion wait
+
+// Dense op of width 5 (TF32) on a 4096-amplitude tile with the 5th-generation tensor cores: the real form
+// D = A * B with A = 128 index groups x 64 inputs (Re parts of the group's 32 amplitudes in K columns
+// 0..31, Im parts in 32..63), B = the op's 64 x 64 real matrix (host-built, staged at `bsm` in the same
+// K-major 128-byte swizzled layout: B^T row n = output n, Re outputs first), D in TMEM (lane = group,
+// 64 FP32 columns). Thread g owns index group g: it gathers the group's amplitudes into registers; after
+// a barrier the tile's 32 KB, no longer needed as amplitudes, hold A; one thread issues the eight K = 8
+// MMAs and commits them to the mbarrier; every thread waits (bounded), reads its D row from TMEM and
+// writes the group's outputs back to their tile positions, which only it owns in this op.
+// Returns false when the wait ran out (status set; the tile is then left unwritten).
+template <int NT>
+__device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, const PassSmem &S, uint32_t &phase,
+                                                 int *status) {
+    static_assert(NT == 128, "one thread per index group");
+    const uint32_t g = threadIdx.x, warp = g >> 5;
+    const uint32_t base = S.cb[0][g & 63u] ^ S.cb[1][g >> 6];
+    uint32_t re[32], im[32];
+#pragma unroll
+    for (uint32_t j = 0; j < 32; ++j) {
+        const float2 v = tile[base ^ S.offs_sw[j]];
+        re[j] = f32_to_tf32(v.x);
+        im[j] = f32_to_tf32(v.y);
+    }
+    __syncthreads();  // every amplitude of the tile is in registers
+    uint8_t *arow = reinterpret_cast<uint8_t *>(tile) + (g >> 3) * 1024u + (g & 7u) * 128u;
+#pragma unroll
+    for (uint32_t c = 0; c < 8; ++c) {
+        const uint32_t o = (c ^ (g & 7u)) << 4;
+        *reinterpret_cast<uint4 *>(arow + o) = make_uint4(re[4 * c], re[4 * c + 1], re[4 * c + 2], re[4 * c + 3]);
+        *reinterpret_cast<uint4 *>(arow + 16384u + o) =
+            make_uint4(im[4 * c], im[4 * c + 1], im[4 * c + 2], im[4 * c + 3]);
+    }
+    cp_async_wait_all();  // this thread's share of B
+    umma::fence_proxy_async_smem();
+    __syncthreads();
+    const uint32_t bar = umma::smem_addr(&S.mbar);
+    if (g == 0) {
+        umma::fence_after_sync();
+        const uint32_t a0 = umma::smem_addr(tile);
+#pragma unroll
+        for (uint32_t s = 0; s < 8; ++s) {
+            const uint64_t da = umma::desc_kmajor_sw128(a0 + (s >> 2) * 16384u + (s & 3u) * 32u);
+            const uint64_t db = umma::desc_kmajor_sw128(bsm + (s >> 2) * 8192u + (s & 3u) * 32u);
+            umma::mma_tf32_ss(S.tmem, da, db, kUmmaIdesc, s);
+        }
+        umma::commit(bar);
+    }
+    // the outcome of the bounded wait is made uniform so that every thread takes the same path
+    const bool ok = __syncthreads_and(umma::mbar_wait(bar, phase, kUmmaWaitNs));
+    phase ^= 1u;
+    if (!ok) {
+        if (g == 0) raise_status(status, QSIM_E_TIMEOUT);
+        return false;
+    }
+    umma::fence_after_sync();
+    uint32_t d[32];
+    const uint32_t taddr = S.tmem + ((32u * warp) << 16);
+    umma::tmem_ld32(taddr, d);  // Re of outputs 0..31
+#pragma unroll
+    for (uint32_t j = 0; j < 32; ++j) re[j] = d[j];
+    umma::tmem_ld32(taddr + 32u, d);  // Im of outputs 0..31
+#pragma unroll
+    for (uint32_t j = 0; j < 32; ++j) tile[base ^ S.offs_sw[j]] = make_float2(__uint_as_float(re[j]), __uint_as_float(d[j]));
+    umma::fence_before_sync();  // the next op's barrier orders these TMEM reads before its MMAs
+    return true;
+}
+
 // Dense op of width k (<= KMAX) on the shared-memory tile; the tensor-core
 // form needs 4096-amplitude tiles and at least 16 index groups per warp.
 template <int NT, int KMAX, int PREC>
@@ -428,10 +505,12 @@ __device__ __forceinline__ void blob_load(const uint4 *__restrict__ gblob, uint3
 // The pass's ops on a staged tile; blob: the staged pass blob; mat: the matrix
 // area for dense ops whose matrix is not in the blob. Starts with a CTA
 // barrier, so the tile's and blob's loads need only have completed per thread.
-template <int NT, int KMAX, int PREC>
-__device__ __forceinline__ void tile_ops(float2 *tile, const uint4 *blob, float2 *mat,
+template <int NT, int KMAX, int PREC, bool UM = false>
+__device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2 *mat,
                                          const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr,
-                                         uint64_t base, uint64_t gb, PassSmem &S) {
+                                         uint64_t base, uint64_t gb, PassSmem &S, uint4 *bbuf, int *status,
+                                         uint32_t &phase) {
+    // phase: parity of the next MMA-completion phase (tcgen05 dense ops); false after a wait ran out
     const int tid = threadIdx.x;
     const uint32_t T = S.p.T;
     const OpDev *bops = reinterpret_cast<const OpDev *>(blob);
@@ -446,6 +525,15 @@ __device__ __forceinline__ void tile_ops(float2 *tile, const uint4 *blob, float2
             const uint32_t D = 1u << k;
             // the tensor-core form reads the op's B-fragment table; the CUDA-core form its matrix
             const bool tc = PREC != QSIM_PREC_FP32 && k >= (PREC == QSIM_PREC_TF32 ? 3u : 4u) && k <= 5 && T == 12;
+            bool um = false;  // on tcgen05: stage the op's B operand now, under the set-up below
+            if constexpr (UM) {
+                um = S.p.umma && k == 5 && T == 12;
+                if (um) {
+                    const uint4 *src = reinterpret_cast<const uint4 *>(bfr + op.bfrag);
+                    for (uint32_t t = tid; t < kUmmaBBytes / 16; t += NT) cp_async16(bbuf + t, src + t);
+                    cp_async_commit();
+                }
+            }
             const float2 *M = mat;
             if (!tc) {
                 if (op.tab != kNoTab) M = bf2 + op.tab;
@@ -470,6 +558,13 @@ __device__ __forceinline__ void tile_ops(float2 *tile, const uint4 *blob, float2
                 }
             }
             __syncthreads();
+            if constexpr (UM) {
+                if (um) {
+                    if (!apply_dense_umma<NT>(tile, umma::smem_addr(bbuf), S, phase, status)) return false;
+                    oi += adv;
+                    continue;
+                }
+            }
             if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, M, bfr + op.bfrag, S, T);
         } else if (type == OP_DIAG) {
             // a run of r diagonal ops in one sweep; op d's phase index = bits constant over the
@@ -592,6 +687,7 @@ __device__ __forceinline__ void tile_ops(float2 *tile, const uint4 *blob, float2
         }
         oi += adv;
     }
+    return true;
 }
 
 // One tile of one pass: stage the pass blob and the 2^T amplitudes of tile
@@ -599,22 +695,47 @@ __device__ __forceinline__ void tile_ops(float2 *tile, const uint4 *blob, float2
 // then matrix area), apply the pass's ops, store the tile back. CG selects
 // L2-only loads, needed when the working vector was written by other CTAs of
 // the same launch (the persistent stage kernel).
-template <int NT, int KMAX, int PREC, bool CG>
+template <int NT, int KMAX, int PREC, bool CG, bool UM = false>
 __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev &pd, const uint4 *__restrict__ gblob,
                                           const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr,
-                                          uint64_t cta, uint64_t gb, PassSmem &S, float2 *dyn) {
+                                          uint64_t cta, uint64_t gb, PassSmem &S, float2 *dyn, int *status) {
     pass_setup<NT>(pd, S);
     const uint32_t T = S.p.T;
+    // passes with tcgen05 dense ops: the tile 1024-byte aligned (it is the A operand while the MMAs run),
+    // the B operand after it, then the blob; 64 TMEM columns hold the accumulator
+    static_assert(!UM || (PREC == QSIM_PREC_TF32 && NT == 128 && KMAX >= 5), "tcgen05 passes: TF32, k = 5");
+    bool um = false;
+    if constexpr (UM) um = S.p.umma != 0;
     float2 *tile = dyn;
-    uint4 *blob = reinterpret_cast<uint4 *>(dyn + (1u << T));
+    uint4 *bbuf = nullptr;
+    if (um) {
+        const uint32_t pad = (1024u - (umma::smem_addr(dyn) & 1023u)) & 1023u;
+        tile = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(dyn) + pad);
+        bbuf = reinterpret_cast<uint4 *>(tile + 4096);
+        if (threadIdx.x < 32) umma::tmem_alloc(umma::smem_addr(&S.tmem), 64);
+        if (threadIdx.x == 0) umma::mbar_init(umma::smem_addr(&S.mbar), 1);
+        umma::fence_before_sync();
+    }
+    uint4 *blob = reinterpret_cast<uint4 *>(tile + (1u << T)) + (um ? kUmmaBBytes / 16 : 0u);
     float2 *mat = reinterpret_cast<float2 *>(blob + S.p.blob_words);
     const uint64_t base = tile_base(S, cta);
     blob_load<NT>(gblob + S.p.blob_off, S.p.blob_words, blob);
     tile_load<NT, CG>(g, base, S, tile);
     cp_async_wait_all();
-    tile_ops<NT, KMAX, PREC>(tile, blob, mat, mats, bfr, base, gb, S);
+    uint32_t phase = 0;
+    const bool ok = tile_ops<NT, KMAX, PREC, UM>(tile, blob, mat, mats, bfr, base, gb, S, bbuf, status, phase);
     __syncthreads();
     tile_store<NT>(g, base, S, tile);
+    if (um) {
+        // after a wait that ran out, wait (bounded) once more for the MMAs in flight before freeing TMEM
+        if (!ok) umma::mbar_wait(umma::smem_addr(&S.mbar), phase ^ 1u, kUmmaWaitNs);
+        umma::fence_before_sync();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            umma::fence_after_sync();
+            umma::tmem_dealloc(S.tmem, 64);
+        }
+    }
 }
 
 }  // namespace gdev

@@ -172,7 +172,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             }
         } else if (type == PH_PASS) {
             gdev::pass_tile<PT, 5, PREC, true>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr, i, gb, PS,
-                                               reinterpret_cast<float2 *>(dsm));
+                                               reinterpret_cast<float2 *>(dsm), L.status);
         } else if (type == PH_SIZE) {
             const uint32_t jj = i / g.nframes, f = i % g.nframes;
             const uint32_t len = cdev::size_frame_cta<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g, S.e,

@@ -575,6 +575,7 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
         return set_error(QSIM_E_INVALID, "m=%u not in 5..min(26, n)", cfg->m);
     if (cfg->k < 1 || cfg->k > 6) return set_error(QSIM_E_INVALID, "k=%u not in 1..6", cfg->k);
     if (cfg->prec > QSIM_PREC_BF16X3) return set_error(QSIM_E_INVALID, "bad precision %u", cfg->prec);
+    if (cfg->tcgen05 > 1) return set_error(QSIM_E_INVALID, "tcgen05 is 0 or 1");
     if (cfg->mode > QSIM_MODE_PERSISTENT) return set_error(QSIM_E_INVALID, "bad mode %u", cfg->mode);
     if (cfg->mode == QSIM_MODE_PERSISTENT && cfg->k > 5)
         return set_error(QSIM_E_INVALID, "persistent mode fuses at most k = 5 qubits");

@@ -48,7 +48,7 @@ class Config(ctypes.Structure):
                 ("graph", ctypes.c_uint32), ("tile_bits", ctypes.c_uint32), ("collect", ctypes.c_uint32),
                 ("eps", ctypes.c_double), ("device_tier_cap_bytes", ctypes.c_uint64),
                 ("init_basis", ctypes.c_uint64), ("predictor_margin", ctypes.c_double),
-                ("reorder", ctypes.c_uint32), ("pad0", ctypes.c_uint32), ("reserved", ctypes.c_uint64 * 5)]
+                ("reorder", ctypes.c_uint32), ("tcgen05", ctypes.c_uint32), ("reserved", ctypes.c_uint64 * 5)]
 
 
 class PlanStats(ctypes.Structure):

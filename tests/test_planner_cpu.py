@@ -89,6 +89,9 @@ def test_errors():
     with pytest.raises(qsim.QsimError) as ei:
         qsim.plan_stages(inputs.ghz(8), m=6, k=1)  # CX is a non-diagonal 2-qubit gate
     assert ei.value.code == qsim.E_INVALID
+    with pytest.raises(qsim.QsimError) as ei:
+        qsim.plan_stages(c, m=6, tcgen05=2)  # the tensor-core choice is 0 or 1
+    assert ei.value.code == qsim.E_INVALID
     bad = inputs.Gate("bad", (0,), (), np.array([[1, 1], [0, 1]], dtype=np.complex128))
     with pytest.raises(qsim.QsimError) as ei:
         qsim.plan_stages(8, [bad], m=6)
