@@ -544,7 +544,7 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                         else
                             build_bfrag_table(reinterpret_cast<const double *>(op.u.data()), op.k, int(p->cfg.prec),
                                               bfr.data() + od.bfrag);
-                        if (um) P.umma = 1;
+                        if (um) P.umma = (p->cfg.reserved[0] & 2) ? 3u : 1u;  // bit 1: wait-limit test hook
                     }
                     P.kmax = std::max<uint32_t>(P.kmax, op.k);
                 } else if (op.type == OP_CSEP) {

@@ -21,7 +21,8 @@ struct PassDev {
     uint32_t kmax;           // widest dense op of the pass (0 if none)
     uint32_t blob_words;     // 16-byte words of the pass blob: op descriptors, phase tables, small matrices
     uint32_t blob_off;       // its first word in the plan's blob array
-    uint32_t umma;           // 1: the pass's k = 5 TF32 dense ops run on tcgen05 (B operands in 128-byte swizzled form)
+    uint32_t umma;           // bit 0: the pass's k = 5 TF32 dense ops run on tcgen05 (B operands in 128-byte
+                             // swizzled form); bit 1: test hook, the MMAs are not committed to the mbarrier
     uint64_t out_mask;       // working-index mask of the non-tile bits
     uint32_t tile_pos[16];   // working bit of tile bit t (ascending)
     uint32_t out_pos[32];    // working bit of CTA-index bit t

@@ -58,3 +58,20 @@ def test_tcgen05_compressed_runs():
     b = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, **kw))
     for blk in range(64):
         assert a.block_stream(blk) == b.block_stream(blk)
+
+
+def test_tcgen05_bounded_wait_reports_timeout():
+    # test hook: the MMAs are not committed to the mbarrier, so every tile's wait runs out (1 s) and the run
+    # ends with QSIM_E_TIMEOUT instead of hanging; the context stays usable
+    c = inputs.random_brick(12, 4, 1)
+    kw = dict(m=12, inner=2, k=5, prec=qsim.PREC_TF32, tcgen05=1, codec=qsim.CODEC_NONE)
+    cfg = qsim.default_config(**kw)
+    cfg.reserved[0] = 2
+    stalled = qsim.Plan(c.n, c.gates, cfg)
+    assert dense5(stalled) > 0
+    with pytest.raises(qsim.QsimError) as ei:
+        qsim.run(stalled)
+    assert ei.value.code == qsim.E_TIMEOUT
+    got = qsim.run(qsim.plan_stages(c, **kw)).decompress().cpu().numpy()
+    want = oracle.simulate(c)
+    assert np.linalg.norm(got - want) <= stalled.stats()["dense_ops"] * 2.0 ** -10
