@@ -564,6 +564,13 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                     const uint32_t cs = source(op.csep_q[0]);
                     const int32_t ctb = tile_bit(cs);
                     od.cctl = ctb >= 0 ? uint32_t(ctb) : (kCtlConst | cs);
+                    // a branch whose factors are all exactly 1 leaves its amplitudes unchanged: skipped
+                    for (uint32_t b = 0; b < 2; ++b) {
+                        bool id = op.u[b] == cd(1, 0);
+                        for (size_t t = 1; t < op.csep_q.size() && id; ++t)
+                            id = op.u[2 + 4 * (t - 1) + 2 * b] == cd(1, 0) && op.u[2 + 4 * (t - 1) + 2 * b + 1] == cd(1, 0);
+                        if (id) od.cctl |= b ? kCtlId1 : kCtlId0;
+                    }
                 } else {
                     od = diag_opdev(op);
                     if (op.type == OP_DIAG) {

@@ -45,11 +45,15 @@ struct __align__(16) OpDev {
     uint32_t run;            // diag in a pass: ops applied in one sweep from here (0 inside a run)
     uint32_t tab;            // in a pass: float2 offset in the blob of the phases (diag), of the matrix (dense
                              // on CUDA cores) or of the tile-bit tables P_lo[2][128] (csep); kNoTab when not there
-    uint32_t cctl;           // csep: control at tile bit cctl, or kCtlConst | source (working bit < 64 or 64 + qubit)
+    uint32_t cctl;           // csep: control at tile bit cctl, or kCtlConst | source (working bit < 64 or 64 + qubit);
+                             // kCtlId0 / kCtlId1: that branch is the identity
     uint32_t ncst;           // csep: targets outside the tile (records at blob offset `mat`, P_hi[2][64] at `dlut`)
 };
 
 constexpr uint32_t kCtlConst = 0x80000000u;
+constexpr uint32_t kCtlId0 = 0x40000000u;  // csep: branch 0 (control bit clear) is the identity
+constexpr uint32_t kCtlId1 = 0x20000000u;  // csep: branch 1 is the identity
+constexpr uint32_t kCtlFlags = kCtlConst | kCtlId0 | kCtlId1;
 
 constexpr uint32_t kDiagRun = 4;            // diagonal ops applied in one sweep over a tile
 constexpr uint32_t kNoTab = 0xffffffffu;

@@ -639,21 +639,27 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                 }
                 S.ck[tid] = kb;
                 if (tid == 0) {
-                    const uint32_t src = op.cctl & ~kCtlConst;
+                    const uint32_t src = op.cctl & ~kCtlFlags;
                     S.cbconst = (op.cctl & kCtlConst)
                                     ? uint32_t(src < 64 ? (base >> src) & 1ull : (gb >> (src - 64)) & 1ull)
                                     : 0u;
                 }
             }
             __syncthreads();
+            // branches that are the identity (bit b of idm) leave their amplitudes as they are
+            const uint32_t idm = ((op.cctl & kCtlId0) ? 1u : 0u) | ((op.cctl & kCtlId1) ? 2u : 0u);
+            const bool ctile = !(op.cctl & kCtlConst);
+            const uint32_t ct = op.cctl & 31u, bconst = S.cbconst;
+            if (!ctile && ((idm >> bconst) & 1u)) {  // the whole tile takes an identity branch
+                oi += adv;
+                continue;
+            }
             for (uint32_t x = tid; x < 128; x += NT) {
                 const uint32_t b = x >> 6;
                 const float2 h = phi[x], kb = S.ck[b];
                 S.csq[b][x & 63u] = make_float2(h.x * kb.x - h.y * kb.y, h.x * kb.y + h.y * kb.x);
             }
             __syncthreads();
-            const bool ctile = !(op.cctl & kCtlConst);
-            const uint32_t ct = op.cctl & 31u, bconst = S.cbconst;
             if (T == 12) {
                 const uint32_t tq = swz_thread<NT>(tid), lo = uint32_t(tid) & 127u, hib = uint32_t(tid) >> 7;
                 const float2 pl0 = plo[lo], pl1 = plo[128 + lo];
@@ -661,6 +667,7 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                 for (uint32_t u = 0; u < 4096u / NT; ++u) {
                     const uint32_t i = uint32_t(tid) + NT * u, hi = hib + (NT / 128) * u;
                     const uint32_t b = ctile ? (i >> ct) & 1u : bconst;
+                    if ((idm >> b) & 1u) continue;
                     const float2 q = S.csq[b][hi], pl = b ? pl1 : pl0;
                     const float2 ph = make_float2(pl.x * q.x - pl.y * q.y, pl.x * q.y + pl.y * q.x);
                     float2 &a = tile[(tq ^ swz_u<NT>(u)) + NT * u];
@@ -670,6 +677,7 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
             } else {
                 for (uint32_t i = tid; i < (1u << T); i += NT) {
                     const uint32_t b = ctile ? (i >> ct) & 1u : bconst;
+                    if ((idm >> b) & 1u) continue;
                     const float2 q = S.csq[b][i >> 7], pl = plo[128 * b + (i & 127u)];
                     const float2 ph = make_float2(pl.x * q.x - pl.y * q.y, pl.x * q.y + pl.y * q.x);
                     float2 &a = tile[swz(i)];
