@@ -67,7 +67,7 @@ def parse_args():
     ap.add_argument("--margin", type=float, default=0.25, help="predictor reservation margin")
     ap.add_argument("--diag-exempt", action="store_true", help="diagonal gates never count as global (Algorithm 1)")
     ap.add_argument("--mma", default="tcgen05", choices=["warp", "tcgen05"],
-                    help="TF32 dense ops of width 5: warp-level mma.sync, or tcgen05 with the accumulator in TMEM")
+                    help="TF32 / split-BF16 dense ops of width 5: warp-level mma.sync, or tcgen05 with the accumulator in TMEM")
     ap.add_argument("--reorder", action="store_true",
                     help="commutation-aware partition: gates may move before earlier gates they commute with")
     ap.add_argument("--train-n", type=int, default=0, help="qubits of the predictor's training circuits (0 = n)")
@@ -303,15 +303,14 @@ def config_dict(args):
     bound = "" if args.codec == "abs" else ", codec=relative (QSZR)"
     return {"workload": f"{name}, m={args.m}, inner={args.inner}, k={args.k}, eps={args.eps:g}, prec={args.prec}, "
                         f"mode={args.mode}{'+graph' if args.graph else ''}, sizing={args.sizing}{bound}"
-                        f"{', mma=tcgen05' if args.mma == 'tcgen05' and args.prec == 'tf32' and args.mode == 'streams' else ''}",
+                        f"{', mma=tcgen05' if args.mma == 'tcgen05' and args.prec != 'fp32' and args.mode == 'streams' else ''}",
             "error_bound": ("absolute eps*2^(-n/2) per component" if args.codec == "abs"
                             else "relative eps per component"),
             "partition": ("commutation-aware (reorder)" if args.reorder else "Algorithm 1 in circuit order") +
                          (", diagonal gates exempt" if args.diag_exempt else ""),
             "n_qubits": args.n, "gates": len(workload(args).gates), "block_log2": args.m, "inner": args.inner,
             "k": args.k, "eps": args.eps, "prec": args.prec,
-            "mma": ("fp32 cuda cores" if args.prec == "fp32" else
-                    args.mma if args.prec == "tf32" and args.mode == "streams" else "warp"),
+            "mma": ("fp32 cuda cores" if args.prec == "fp32" else args.mma if args.mode == "streams" else "warp"),
             "streams": args.streams,
             "mode": args.mode,
             "graph": bool(args.graph), "sizing": args.sizing, "device_tier_cap_gib": args.cap_gib,

@@ -97,9 +97,9 @@ typedef struct qsim_config {
     uint32_t reorder;        /* 1: commutation-aware partition: a gate may be placed before earlier
                                 gates it commutes with (disjoint qubits, or both diagonal) when that
                                 keeps it in the current stage; 0 = Algorithm 1 in circuit order */
-    uint32_t tcgen05;        /* 1: TF32 dense ops of width 5 on the 5th-generation tensor cores
-                                (tcgen05.mma, accumulator in tensor memory) in streams mode;
-                                0: warp-level mma.sync */
+    uint32_t tcgen05;        /* 1: TF32 and split-BF16 dense ops of width 5 on the 5th-generation
+                                tensor cores (tcgen05.mma, accumulator in tensor memory) in
+                                streams mode; 0: warp-level mma.sync */
     uint64_t reserved[5];    /* zero; reserved[0] bit 0 is a test hook: in persistent mode the
                                 first stage's second phase waits for a count that is never
                                 reached, so the run ends with QSIM_E_TIMEOUT after the

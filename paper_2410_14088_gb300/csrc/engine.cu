@@ -527,8 +527,9 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                     const uint32_t min_k = p->cfg.prec == QSIM_PREC_TF32 ? 3u : 4u;
                     // k = 5 TF32 ops of the stream engine's 4096-amplitude passes on tcgen05 when asked for
                     // (one thread per index group: the complement ordered for that gather)
-                    const bool um = p->cfg.tcgen05 && p->cfg.prec == QSIM_PREC_TF32 && op.k == 5 && ps.T == 12 &&
-                                    p->cfg.mode == QSIM_MODE_STREAMS;
+                    const bool um = p->cfg.tcgen05 &&
+                                    (p->cfg.prec == QSIM_PREC_TF32 || p->cfg.prec == QSIM_PREC_BF16X3) &&
+                                    op.k == 5 && ps.T == 12 && p->cfg.mode == QSIM_MODE_STREAMS;
                     order_complement(od, ps.T,
                                      !um && p->cfg.prec != QSIM_PREC_FP32 && op.k >= min_k && op.k <= 5 &&
                                          ps.T == 12);
@@ -539,12 +540,16 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                         bfr.resize((bfr.size() + 3) & ~size_t(3));  // 16-byte aligned tables
                         od.bfrag = bfr.size();
                         bfr.resize(bfr.size() + bfrag_words(op.k, int(p->cfg.prec)));
-                        if (um)
+                        if (um && p->cfg.prec == QSIM_PREC_BF16X3)
+                            build_umma_b3(reinterpret_cast<const double *>(op.u.data()), bfr.data() + od.bfrag);
+                        else if (um)
                             build_umma_b(reinterpret_cast<const double *>(op.u.data()), bfr.data() + od.bfrag);
                         else
                             build_bfrag_table(reinterpret_cast<const double *>(op.u.data()), op.k, int(p->cfg.prec),
                                               bfr.data() + od.bfrag);
-                        if (um) P.umma = (p->cfg.reserved[0] & 2) ? 3u : 1u;  // bit 1: wait-limit test hook
+                        if (um)  // bit 1: wait-limit test hook; bit 2: split-BF16 operands
+                            P.umma = 1u | ((p->cfg.reserved[0] & 2) ? 2u : 0u) |
+                                     (p->cfg.prec == QSIM_PREC_BF16X3 ? 4u : 0u);
                     }
                     P.kmax = std::max<uint32_t>(P.kmax, op.k);
                 } else if (op.type == OP_CSEP) {

@@ -63,7 +63,7 @@ void launch_pass_ku(dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t
 template <int KMAX, int PREC>
 void launch_pass_k(dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W, const PassDev &P,
                    const uint4 *blob, const float2 *mats, const uint32_t *bfr, const uint64_t *gbase, int *status) {
-    if constexpr (PREC == QSIM_PREC_TF32 && KMAX >= 5) {
+    if constexpr ((PREC == QSIM_PREC_TF32 || PREC == QSIM_PREC_BF16X3) && KMAX >= 5) {
         if (P.umma) {
             launch_pass_ku<KMAX, PREC, true>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status);
             return;
@@ -161,7 +161,10 @@ void build_bfrag_table(const double *u, uint32_t k, int prec, uint32_t *out) {
 }
 
 size_t pass_smem_bytes(const PassDev &P) {
-    return (size_t(1) << P.T) * sizeof(float2) + (P.umma ? size_t(kUmmaExtraSmem) : 0) + size_t(P.blob_words) * 16 +
+    const size_t um = (P.umma & 1u) ? size_t((P.umma & 4u) ? umma_b_bytes<QSIM_PREC_BF16X3>()
+                                                              : umma_b_bytes<QSIM_PREC_TF32>()) + 1024
+                                    : 0;
+    return (size_t(1) << P.T) * sizeof(float2) + um + size_t(P.blob_words) * 16 +
            size_t(P.mat_elems) * sizeof(float2);
 }
 
@@ -175,6 +178,26 @@ void build_umma_b(const double *u, uint32_t *out) {
             const uint32_t a = kk / 32, ch = (kk % 32) / 4, w = kk % 4;
             const size_t byte = size_t(a) * 8192 + (n / 8) * 1024 + (n % 8) * 128 + ((ch ^ (n % 8)) * 16) + w * 4;
             out[byte / 4] = to_tf32(float(v));
+        }
+}
+
+void build_umma_b3(const double *u, uint32_t *out) {
+    constexpr uint32_t D = 32;
+    uint16_t *o16 = reinterpret_cast<uint16_t *>(out);
+    for (uint32_t n = 0; n < 2 * D; ++n)
+        for (uint32_t kk = 0; kk < 2 * D; ++kk) {
+            const uint32_t r = n % D, c = kk % D;
+            const double re = u[2 * (size_t(r) * D + c)], im = u[2 * (size_t(r) * D + c) + 1];
+            const float x = float(n < D ? (kk < D ? re : -im) : (kk < D ? im : re));
+            const uint16_t h = to_bf16(x);
+            const float r1 = x - from_bf16(h);
+            const uint16_t m = to_bf16(r1);
+            const uint16_t l = to_bf16(r1 - from_bf16(m));
+            const uint32_t ch = kk / 8, w = kk % 8;
+            const size_t off = (n / 8) * 1024 + (n % 8) * 128 + ((ch ^ (n % 8)) * 16) + w * 2;  // bytes in a part
+            o16[(0 * 8192 + off) / 2] = h;
+            o16[(1 * 8192 + off) / 2] = m;
+            o16[(2 * 8192 + off) / 2] = l;
         }
 }
 

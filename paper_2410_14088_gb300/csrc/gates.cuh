@@ -22,7 +22,8 @@ struct PassDev {
     uint32_t blob_words;     // 16-byte words of the pass blob: op descriptors, phase tables, small matrices
     uint32_t blob_off;       // its first word in the plan's blob array
     uint32_t umma;           // bit 0: the pass's k = 5 TF32 dense ops run on tcgen05 (B operands in 128-byte
-                             // swizzled form); bit 1: test hook, the MMAs are not committed to the mbarrier
+                             // swizzled form); bit 1: test hook, the MMAs are not committed to the mbarrier;
+                             // bit 2: split-BF16 B operands (three parts, 24 KB)
     uint64_t out_mask;       // working-index mask of the non-tile bits
     uint32_t tile_pos[16];   // working bit of tile bit t (ascending)
     uint32_t out_pos[32];    // working bit of CTA-index bit t
@@ -76,6 +77,10 @@ size_t bfrag_words(uint32_t k, int prec);
 // Im), K-major in the 128-byte swizzled layout: column block a = input / 32 at byte 8192 a, row n at
 // 1024 (n / 8) + 128 (n % 8), 16-byte chunk c = (input % 32) / 4 stored at chunk position c ^ (n % 8).
 void build_umma_b(const double *u_interleaved, uint32_t *out);
+// The split-BF16 form (6144 words, the count of its warp-MMA fragment table): three 8 KB parts hi, mid, lo of
+// U_r (x = hi + mid + lo, each rounded to BF16 nearest-even), each part 64 rows of 64 BF16 inputs in the same
+// swizzled layout (row n at 1024 (n / 8) + 128 (n % 8), 16-byte chunk c = input / 8 at position c ^ (n % 8)).
+void build_umma_b3(const double *u_interleaved, uint32_t *out);
 
 void launch_pass(float2 *wv, uint32_t W, uint32_t ngroups, const PassDev *pass_host, const uint4 *blob_dev,
                  const float2 *mats_dev, const uint32_t *bfr_dev, const uint64_t *gbase_dev, int prec,

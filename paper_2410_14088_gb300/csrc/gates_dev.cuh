@@ -270,12 +270,40 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
     }
 }
 
-// Bytes of shared memory a tcgen05 pass adds: the B operand of one op and the slack that aligns the tile
-// (the A operand while the MMAs run) to 1024 bytes.
-constexpr uint32_t kUmmaBBytes = 16384;
-constexpr uint32_t kUmmaExtraSmem = kUmmaBBytes + 1024;
+// Bytes of shared memory a tcgen05 pass adds: the B operand of one op (TF32 64 x 64, or split BF16 in three
+// 64 x 64 parts) and the slack that aligns the tile (the A operand while the MMAs run) to 1024 bytes.
+template <int PREC>
+__host__ __device__ constexpr uint32_t umma_b_bytes() {
+    return PREC == QSIM_PREC_BF16X3 ? 24576u : 16384u;
+}
 constexpr uint32_t kUmmaIdesc = umma::idesc_tf32(128, 64);
+constexpr uint32_t kUmmaIdescBf16 = umma::idesc_bf16(128, 64);
 constexpr uint64_t kUmmaWaitNs = 1000000000ull;  // bound on one MMA-completion wait
+
+// Commit the MMAs issued by thread 0 (unless the test hook asks otherwise) and wait, bounded, for them; the
+// outcome is made uniform so that every thread takes the same path. False (status set) when the wait ran out.
+__device__ __forceinline__ bool umma_commit_wait(const PassSmem &S, uint32_t &phase, int *status) {
+    const uint32_t bar = umma::smem_addr(&S.mbar);
+    if (threadIdx.x == 0 && !(S.p.umma & 2u)) umma::commit(bar);  // test hook: no arrival, the wait runs out
+    const bool ok = __syncthreads_and(umma::mbar_wait(bar, phase, kUmmaWaitNs));
+    phase ^= 1u;
+    if (!ok && threadIdx.x == 0) raise_status(status, QSIM_E_TIMEOUT);
+    return ok;
+}
+
+// Row g of D (TMEM lane g: Re of the 32 outputs in columns 0..31, Im in 32..63) back to the group's tile
+// positions.
+__device__ __forceinline__ void umma_epilogue(float2 *tile, uint32_t base, const PassSmem &S) {
+    umma::fence_after_sync();
+    const uint32_t taddr = S.tmem + ((32u * (threadIdx.x >> 5)) << 16);
+    uint32_t re[32], im[32];
+    umma::tmem_ld32(taddr, re);
+    umma::tmem_ld32(taddr + 32u, im);
+#pragma unroll
+    for (uint32_t j = 0; j < 32; ++j)
+        tile[base ^ S.offs_sw[j]] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+    umma::fence_before_sync();  // the next op's barrier orders these TMEM reads before its MMAs
+}
 
 // Dense op of width 5 (TF32) on a 4096-amplitude tile with the 5th-generation tensor cores: the real form
 // D = A * B with A = 128 index groups x 64 inputs (Re parts of the group's 32 amplitudes in K columns
@@ -290,7 +318,7 @@ template <int NT>
 __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, const PassSmem &S, uint32_t &phase,
                                                  int *status) {
     static_assert(NT == 128, "one thread per index group");
-    const uint32_t g = threadIdx.x, warp = g >> 5;
+    const uint32_t g = threadIdx.x;
     const uint32_t base = S.cb[0][g & 63u] ^ S.cb[1][g >> 6];
     uint32_t re[32], im[32];
 #pragma unroll
@@ -311,7 +339,6 @@ __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, con
     cp_async_wait_all();  // this thread's share of B
     umma::fence_proxy_async_smem();
     __syncthreads();
-    const uint32_t bar = umma::smem_addr(&S.mbar);
     if (g == 0) {
         umma::fence_after_sync();
         const uint32_t a0 = umma::smem_addr(tile);
@@ -321,25 +348,84 @@ __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, con
             const uint64_t db = umma::desc_kmajor_sw128(bsm + (s >> 2) * 8192u + (s & 3u) * 32u);
             umma::mma_tf32_ss(S.tmem, da, db, kUmmaIdesc, s);
         }
-        if (!(S.p.umma & 2u)) umma::commit(bar);  // test hook: no arrival, so the bounded wait runs out
     }
-    // the outcome of the bounded wait is made uniform so that every thread takes the same path
-    const bool ok = __syncthreads_and(umma::mbar_wait(bar, phase, kUmmaWaitNs));
-    phase ^= 1u;
-    if (!ok) {
-        if (g == 0) raise_status(status, QSIM_E_TIMEOUT);
-        return false;
+    if (!umma_commit_wait(S, phase, status)) return false;
+    umma_epilogue(tile, base, S);
+    return true;
+}
+
+// The same op in split BF16 (x = hi + mid + lo, each part BF16; the six products of order <= 2 accumulated
+// in FP32) on tcgen05 (kind::f16, K = 16 per MMA). A row = 64 BF16 values = one 128-byte row per part, so
+// the tile's two 16 KB halves hold two parts at a time: first A_hi and A_lo for lo x B_hi and hi x B_lo,
+// then A_mid over A_lo for mid x B_mid, mid x B_hi, hi x B_mid, hi x B_hi (small terms first; each thread
+// keeps its A_mid words in registers across the first wait). B: three 8 KB parts (hi, mid, lo) at bsm.
+template <int NT>
+__device__ __forceinline__ bool apply_dense_umma3(float2 *tile, uint32_t bsm, const PassSmem &S, uint32_t &phase,
+                                                  int *status) {
+    static_assert(NT == 128, "one thread per index group");
+    const uint32_t g = threadIdx.x;
+    const uint32_t base = S.cb[0][g & 63u] ^ S.cb[1][g >> 6];
+    float x[64];  // K order: Re parts of inputs 0..31, then Im parts
+#pragma unroll
+    for (uint32_t j = 0; j < 32; ++j) {
+        const float2 v = tile[base ^ S.offs_sw[j]];
+        x[j] = v.x;
+        x[32 + j] = v.y;
     }
-    umma::fence_after_sync();
-    uint32_t d[32];
-    const uint32_t taddr = S.tmem + ((32u * warp) << 16);
-    umma::tmem_ld32(taddr, d);  // Re of outputs 0..31
+    __syncthreads();  // every amplitude of the tile is in registers
+    uint8_t *arow = reinterpret_cast<uint8_t *>(tile) + (g >> 3) * 1024u + (g & 7u) * 128u;
+    uint32_t mid[32];
 #pragma unroll
-    for (uint32_t j = 0; j < 32; ++j) re[j] = d[j];
-    umma::tmem_ld32(taddr + 32u, d);  // Im of outputs 0..31
+    for (uint32_t c = 0; c < 8; ++c) {  // 16-byte chunk c = K elements 8c .. 8c + 7
+        uint32_t h[4], l[4];
 #pragma unroll
-    for (uint32_t j = 0; j < 32; ++j) tile[base ^ S.offs_sw[j]] = make_float2(__uint_as_float(re[j]), __uint_as_float(d[j]));
-    umma::fence_before_sync();  // the next op's barrier orders these TMEM reads before its MMAs
+        for (uint32_t q = 0; q < 4; ++q) {
+            __nv_bfloat16 h0, m0, l0, h1, m1, l1;
+            split3(x[8 * c + 2 * q], h0, m0, l0);
+            split3(x[8 * c + 2 * q + 1], h1, m1, l1);
+            h[q] = pack_bf16(h0, h1);
+            l[q] = pack_bf16(l0, l1);
+            mid[4 * c + q] = pack_bf16(m0, m1);
+        }
+        const uint32_t o = (c ^ (g & 7u)) << 4;
+        *reinterpret_cast<uint4 *>(arow + o) = make_uint4(h[0], h[1], h[2], h[3]);
+        *reinterpret_cast<uint4 *>(arow + 16384u + o) = make_uint4(l[0], l[1], l[2], l[3]);
+    }
+    cp_async_wait_all();  // this thread's share of B
+    umma::fence_proxy_async_smem();
+    __syncthreads();
+    const uint32_t a0 = umma::smem_addr(tile);
+    auto product = [&](uint32_t a_half, uint32_t b_part, uint32_t first) {
+#pragma unroll
+        for (uint32_t s = 0; s < 4; ++s) {
+            const uint64_t da = umma::desc_kmajor_sw128(a0 + a_half * 16384u + s * 32u);
+            const uint64_t db = umma::desc_kmajor_sw128(bsm + b_part * 8192u + s * 32u);
+            umma::mma_bf16_ss(S.tmem, da, db, kUmmaIdescBf16, first && s == 0 ? 0u : 1u);
+        }
+    };
+    if (g == 0) {
+        umma::fence_after_sync();
+        product(1, 0, 1);  // lo x B_hi (the first product overwrites D)
+        product(0, 2, 0);  // hi x B_lo
+    }
+    if (!umma_commit_wait(S, phase, status)) return false;
+#pragma unroll
+    for (uint32_t c = 0; c < 8; ++c) {
+        const uint32_t o = (c ^ (g & 7u)) << 4;
+        *reinterpret_cast<uint4 *>(arow + 16384u + o) =
+            make_uint4(mid[4 * c], mid[4 * c + 1], mid[4 * c + 2], mid[4 * c + 3]);
+    }
+    umma::fence_proxy_async_smem();
+    __syncthreads();
+    if (g == 0) {
+        umma::fence_after_sync();
+        product(1, 1, 0);  // mid x B_mid
+        product(1, 0, 0);  // mid x B_hi
+        product(0, 1, 0);  // hi x B_mid
+        product(0, 0, 0);  // hi x B_hi
+    }
+    if (!umma_commit_wait(S, phase, status)) return false;
+    umma_epilogue(tile, base, S);
     return true;
 }
 
@@ -530,7 +616,7 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                 um = S.p.umma && k == 5 && T == 12;
                 if (um) {
                     const uint4 *src = reinterpret_cast<const uint4 *>(bfr + op.bfrag);
-                    for (uint32_t t = tid; t < kUmmaBBytes / 16; t += NT) cp_async16(bbuf + t, src + t);
+                    for (uint32_t t = tid; t < umma_b_bytes<PREC>() / 16; t += NT) cp_async16(bbuf + t, src + t);
                     cp_async_commit();
                 }
             }
@@ -560,7 +646,10 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
             __syncthreads();
             if constexpr (UM) {
                 if (um) {
-                    if (!apply_dense_umma<NT>(tile, umma::smem_addr(bbuf), S, phase, status)) return false;
+                    const bool done = PREC == QSIM_PREC_BF16X3
+                                          ? apply_dense_umma3<NT>(tile, umma::smem_addr(bbuf), S, phase, status)
+                                          : apply_dense_umma<NT>(tile, umma::smem_addr(bbuf), S, phase, status);
+                    if (!done) return false;
                     oi += adv;
                     continue;
                 }
@@ -711,7 +800,8 @@ __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev 
     const uint32_t T = S.p.T;
     // passes with tcgen05 dense ops: the tile 1024-byte aligned (it is the A operand while the MMAs run),
     // the B operand after it, then the blob; 64 TMEM columns hold the accumulator
-    static_assert(!UM || (PREC == QSIM_PREC_TF32 && NT == 128 && KMAX >= 5), "tcgen05 passes: TF32, k = 5");
+    static_assert(!UM || ((PREC == QSIM_PREC_TF32 || PREC == QSIM_PREC_BF16X3) && NT == 128 && KMAX >= 5),
+                  "tcgen05 passes: TF32 or split BF16, k = 5");
     bool um = false;
     if constexpr (UM) um = S.p.umma != 0;
     float2 *tile = dyn;
@@ -724,7 +814,7 @@ __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev 
         if (threadIdx.x == 0) umma::mbar_init(umma::smem_addr(&S.mbar), 1);
         umma::fence_before_sync();
     }
-    uint4 *blob = reinterpret_cast<uint4 *>(tile + (1u << T)) + (um ? kUmmaBBytes / 16 : 0u);
+    uint4 *blob = reinterpret_cast<uint4 *>(tile + (1u << T)) + (um ? umma_b_bytes<PREC>() / 16 : 0u);
     float2 *mat = reinterpret_cast<float2 *>(blob + S.p.blob_words);
     const uint64_t base = tile_base(S, cta);
     blob_load<NT>(gblob + S.p.blob_off, S.p.blob_words, blob);

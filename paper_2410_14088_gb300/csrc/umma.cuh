@@ -17,7 +17,7 @@ __device__ __forceinline__ uint32_t smem_addr(const void *p) { return uint32_t(_
 // layout: rows of 128 bytes, groups of 8 rows 1024 bytes apart (the stride
 // byte offset), the 16-byte chunk index of row r XOR-ed with r mod 8. The
 // group base must be 1024-byte aligned. The leading byte offset is unused for
-// this layout (the K extent of one MMA, 32 bytes of TF32, stays inside a row).
+// this layout (the K extent of one MMA, 32 bytes: 8 TF32 or 16 BF16 values, stays inside a row).
 __device__ __forceinline__ uint64_t desc_kmajor_sw128(uint32_t saddr) {
     uint64_t d = uint64_t((saddr & 0x3FFFFu) >> 4);  // bits 0-13: start address / 16
     d |= uint64_t(1) << 16;                           // bits 16-29: leading byte offset / 16
@@ -35,6 +35,26 @@ __host__ __device__ constexpr uint32_t idesc_tf32(uint32_t M, uint32_t N) {
            | (2u << 10)           // B format: TF32
            | ((N >> 3) << 17)     // N / 8
            | ((M >> 4) << 24);    // M / 16
+}
+
+// Instruction descriptor of kind::f16 with BF16 operands and an FP32 accumulator, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(uint32_t M, uint32_t N) {
+    return (1u << 4)              // D format: F32
+           | (1u << 7)            // A format: BF16
+           | (1u << 10)           // B format: BF16
+           | ((N >> 3) << 17)     // N / 8
+           | ((M >> 4) << 24);    // M / 16
+}
+
+// D[tmem] (+)= A[smem] * B[smem] with BF16 operands (K = 16 per instruction), issued by one thread
+__device__ __forceinline__ void mma_bf16_ss(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+        "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
 }
 
 // D[tmem] (+)= A[smem] * B[smem], issued by one thread

@@ -1,5 +1,5 @@
-"""TF32 dense ops of width 5 on the 5th-generation tensor cores (tcgen05.mma with both operands in
-shared memory and the FP32 accumulator in tensor memory) against the FP64 oracle and the warp-level
+"""Dense ops of width 5 on the 5th-generation tensor cores (tcgen05.mma in TF32 or split BF16, both operands
+in shared memory, the FP32 accumulator in tensor memory) against the FP64 oracle and the warp-level
 mma.sync path, uncompressed and through the compressed stage loop."""
 import numpy as np
 import pytest
@@ -17,8 +17,9 @@ def dense5(p):
     return sum(1 for s in range(p.nstages) for o in p.stage_ops(s) if o["type"] == 0 and o["nq"] == 5)
 
 
+@pytest.mark.parametrize("prec", [qsim.PREC_TF32, qsim.PREC_BF16X3], ids=["tf32", "bf16x3"])
 @pytest.mark.parametrize("family", ["qft", "brick", "qaoa"])
-def test_tcgen05_matches_fp64_and_warp_mma(family):
+def test_tcgen05_matches_fp64_and_warp_mma(family, prec):
     if family == "qft":
         n = 20
         c = inputs.Circuit(n, inputs.qft_gates(n), 0x5A5A5)
@@ -31,18 +32,24 @@ def test_tcgen05_matches_fp64_and_warp_mma(family):
         n = 18
         c = inputs.qaoa_maxcut(n, 2, 3)
         kw = dict(m=13, inner=2, k=5)
-    plans = [qsim.plan_stages(c, codec=qsim.CODEC_NONE, prec=qsim.PREC_TF32, tcgen05=t, **kw) for t in (0, 1)]
+    plans = [qsim.plan_stages(c, codec=qsim.CODEC_NONE, prec=prec, tcgen05=t, **kw) for t in (0, 1)]
     assert dense5(plans[1]) > 0
     warp, tc = (qsim.run(p).decompress().cpu().numpy() for p in plans)
     want = cf.qft_basis_state(n, 0x5A5A5) if family == "qft" else oracle.simulate(c)
-    # both operands of every dense op rounded to TF32 (unit roundoff 2^-11): the state's relative 2-norm error
-    # grows by at most about 2^-10 per TF32 op; and tcgen05 stays as close to FP64 as the warp-level path
+    # TF32: both operands of every dense op rounded to TF32 (unit roundoff 2^-11), so the state's relative
+    # 2-norm error grows by at most about 2^-10 per op. Split BF16: three parts of 8 bits each and the six
+    # products of order <= 2 leave about 2^-22 per op, below the FP32 rounding of the other ops; bound at 2^-20
+    # per op. Either way tcgen05 stays as close to FP64 as the warp-level path.
     nops = sum(1 for s in range(plans[1].nstages) for o in plans[1].stage_ops(s) if o["type"] == 0)
     err_tc = np.linalg.norm(tc - want) / np.linalg.norm(want)
     err_warp = np.linalg.norm(warp - want) / np.linalg.norm(want)
-    assert err_tc <= nops * 2.0 ** -10
+    per_op = 2.0 ** -10 if prec == qsim.PREC_TF32 else 2.0 ** -20
+    assert err_tc <= nops * per_op
     assert err_tc <= 1.5 * err_warp + 1e-6
-    assert np.max(np.abs(tc - want)) <= 2e-2 * 2 ** (-n / 2)
+    if prec == qsim.PREC_TF32:
+        assert np.max(np.abs(tc - want)) <= 2e-2 * 2 ** (-n / 2)
+    else:
+        assert np.max(np.abs(tc - want)) <= 1e-5  # the FP32 paths' bound
     # the norm drifts with TF32 rounding as much as on the warp-level path
     assert abs(np.vdot(tc, tc).real - np.vdot(warp, warp).real) < 1e-3
 
@@ -50,9 +57,12 @@ def test_tcgen05_matches_fp64_and_warp_mma(family):
 def test_tcgen05_compressed_runs():
     c = inputs.qft_rz_cx(22, 2, 3)
     kw = dict(m=16, inner=4, k=5, eps=1e-3, prec=qsim.PREC_TF32)
+    ideal = oracle.simulate(c)
     for streams in (1, 2):
         st = qsim.run(qsim.plan_stages(c, tcgen05=1, streams=streams, **kw))
-        assert st.fidelity(oracle.simulate(c)) >= 0.999
+        assert st.fidelity(ideal) >= 0.999
+    st = qsim.run(qsim.plan_stages(c, tcgen05=1, **dict(kw, prec=qsim.PREC_BF16X3)))
+    assert st.fidelity(ideal) >= 0.999
     # the persistent stage kernel keeps the warp-level MMAs: the option leaves its streams unchanged
     a = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, tcgen05=1, **kw))
     b = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, **kw))
