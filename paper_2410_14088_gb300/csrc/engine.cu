@@ -519,6 +519,7 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                 od.type = op.type;
                 od.k = op.k;
                 if (op.type == OP_DENSE) {
+                    od.dlut = kNoTab;  // set for tensor-core ops when the pass blob is laid out
                     for (uint32_t j = 0; j < op.k; ++j) {
                         uint32_t t = 0;
                         while (ps.tile_pos[t] != op.wq[j]) ++t;
@@ -685,7 +686,31 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                         for (const float2 &f : recs) put(f);
                     } else if (od.type == OP_DENSE) {
                         const bool tc = p->cfg.prec != QSIM_PREC_FP32 && od.k >= min_k && od.k <= 5 && ps.T == 12;
-                        if (tc) continue;
+                        if (tc) {
+                            // swizzled tile offsets of the op's index groups (128 words: the group bits 0..5 and
+                            // 6.. through the complement) and of its matrix columns (32 words), read by the
+                            // tensor-core forms in place of a per-tile set-up
+                            auto swz = [](uint32_t i) { return i ^ (((i >> 4) ^ (i >> 8) ^ (i >> 12)) & 15u); };
+                            uint32_t t[160] = {};
+                            const uint32_t nc = ps.T - od.k;
+                            for (uint32_t x = 0; x < 128; ++x) {
+                                const uint32_t half = x >> 6, v = x & 63u;
+                                uint32_t bits = 0;
+                                for (uint32_t j = 0; j < 6; ++j)
+                                    if (6 * half + j < nc) bits |= ((v >> j) & 1u) << od.comp[6 * half + j];
+                                t[x] = swz(bits);
+                            }
+                            for (uint32_t c = 0; c < (1u << od.k); ++c) {
+                                uint32_t o = 0;
+                                for (uint32_t j = 0; j < od.k; ++j) o |= ((c >> j) & 1u) << od.tq[j];
+                                t[128 + c] = swz(o);
+                            }
+                            align16();
+                            od.dlut = uint32_t(pb.size() / 4);
+                            const uint8_t *tb = reinterpret_cast<const uint8_t *>(t);
+                            pb.insert(pb.end(), tb, tb + sizeof(t));
+                            continue;
+                        }
                         const size_t mb = size_t(8) << (2 * od.k);
                         if (((pb.size() + 15) & ~size_t(15)) + mb <= kPassBlobMax) {
                             align16();

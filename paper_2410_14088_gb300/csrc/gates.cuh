@@ -34,7 +34,8 @@ struct __align__(16) OpDev {
     uint32_t k;
     uint32_t mat;            // float2 offset of the matrix (dense) or phases (diag) in the plan's matrix array
     uint32_t dlut;           // diag: float2 offset of its phase-index byte tables (pass: in the blob; decoder
-                             // pre-op: in the matrix array)
+                             // pre-op: in the matrix array); dense on tensor cores: word offset in the blob of its
+                             // swizzled group-base (128) and column (32) offsets, else kNoTab
     uint32_t tq[6];          // dense: tile bit of matrix bit j
     uint32_t dsrc[8];        // diag: working bit (< 64) or 64 + full qubit (outer, from group base)
     uint32_t dtile[8];       // diag in a pass: tile bit of qubit j, or 255 when the bit is constant over a tile

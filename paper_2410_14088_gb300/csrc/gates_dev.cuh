@@ -34,9 +34,7 @@ struct PassSmem {
     // 4096-amplitude tiles: element tid + NT u sits at working offset tpart[tid] + off12[u]
     uint32_t off12[32];
     uint32_t tpart[256];
-    uint32_t offs[64];     // dense op: working offsets of its 2^k matrix columns within the tile
-    uint32_t offs_sw[64];  // the same through the swizzle
-    uint32_t comp[16];     // dense op: its complement tile bits
+    uint32_t offs_sw[64];  // dense op: tile offsets of its 2^k matrix columns through the swizzle
     // dense op: swizzled base of index group g = cb[0][g & 63] ^ cb[1][g >> 6] (the swizzle is
     // linear over GF(2), so swz(b | c) = swz(b) ^ swz(c) for disjoint bit sets b, c)
     uint32_t cb[2][64];
@@ -52,14 +50,15 @@ struct PassSmem {
 static_assert(sizeof(OpDev) % 16 == 0, "op descriptors are copied as 16-byte words");
 
 template <int NT, int K>
-__device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const PassSmem &S, uint32_t T) {
+__device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const uint32_t *cb, const uint32_t *osw,
+                                            uint32_t T) {
     constexpr int D = 1 << K;
     const uint32_t ngroups = 1u << (T - K);
     for (uint32_t g = threadIdx.x; g < ngroups; g += NT) {
-        const uint32_t sb = S.cb[0][g & 63u] ^ S.cb[1][g >> 6];
+        const uint32_t sb = cb[g & 63u] ^ cb[64u + (g >> 6)];
         float2 x[D];
 #pragma unroll
-        for (int c = 0; c < D; ++c) x[c] = tile[sb ^ S.offs_sw[c]];
+        for (int c = 0; c < D; ++c) x[c] = tile[sb ^ osw[c]];
 #pragma unroll 1
         for (int r = 0; r < D; ++r) {
             const float4 *row = reinterpret_cast<const float4 *>(U + r * D);
@@ -80,17 +79,18 @@ __device__ __forceinline__ void apply_dense(float2 *tile, const float2 *U, const
                     ai = fmaf(u.z, x[c + 1].y, ai); ai = fmaf(u.w, x[c + 1].x, ai);
                 }
             }
-            tile[sb ^ S.offs_sw[r]] = make_float2(ar, ai);
+            tile[sb ^ osw[r]] = make_float2(ar, ai);
         }
     }
 }
 
 template <int NT>
-__device__ __forceinline__ void apply_dense_k1(float2 *tile, const float2 *U, const PassSmem &S, uint32_t T) {
+__device__ __forceinline__ void apply_dense_k1(float2 *tile, const float2 *U, const uint32_t *cb, const uint32_t *osw,
+                                               uint32_t T) {
     const uint32_t ngroups = 1u << (T - 1);
     const float2 u00 = U[0], u01 = U[1], u10 = U[2], u11 = U[3];
     for (uint32_t g = threadIdx.x; g < ngroups; g += NT) {
-        const uint32_t i0 = S.cb[0][g & 63u] ^ S.cb[1][g >> 6], i1 = i0 ^ S.offs_sw[1];
+        const uint32_t i0 = cb[g & 63u] ^ cb[64u + (g >> 6)], i1 = i0 ^ osw[1];
         const float2 x0 = tile[i0], x1 = tile[i1];
         tile[i0] = make_float2(u00.x * x0.x - u00.y * x0.y + u01.x * x1.x - u01.y * x1.y,
                                u00.x * x0.y + u00.y * x0.x + u01.x * x1.y + u01.y * x1.x);
@@ -162,7 +162,8 @@ __device__ __forceinline__ uint32_t pack_bf16(__nv_bfloat16 lo_half, __nv_bfloat
 }
 
 template <int NT, int K, int PREC>
-__device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__restrict__ bfr, const PassSmem &S,
+__device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__restrict__ bfr, const uint32_t *cb,
+                                                const uint32_t *osw,
                                                 uint32_t T) {
     // tensor-core shape: T = 12 (4096-amplitude tiles), checked by the caller
     constexpr uint32_t D = 1u << K, N2 = 2 * D;
@@ -181,7 +182,7 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const uint32_t g = row0 + mt * 16 + gq + 8 * h;
-            base[mt][h] = S.cb[0][g & 63u] ^ S.cb[1][g >> 6];
+            base[mt][h] = cb[g & 63u] ^ cb[64u + (g >> 6)];
         }
     float acc[MT * NTILES][4];
 #pragma unroll
@@ -192,7 +193,7 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
 #pragma unroll
     for (uint32_t ks = 0; ks < KS / 2; ++ks) {
         if constexpr (PREC == QSIM_PREC_TF32) {
-            const uint32_t c0 = S.offs_sw[ks * 8 + tq], c1 = S.offs_sw[ks * 8 + tq + 4];
+            const uint32_t c0 = osw[ks * 8 + tq], c1 = osw[ks * 8 + tq + 4];
             uint32_t are[MT][4], aim[MT][4];
 #pragma unroll
             for (uint32_t mt = 0; mt < MT; ++mt) {
@@ -216,8 +217,8 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
             }
         } else {
             // columns 2t, 2t+1, 2t+8, 2t+9 of the k-step
-            const uint32_t cc[4] = {S.offs_sw[ks * 16 + 2 * tq], S.offs_sw[ks * 16 + 2 * tq + 1],
-                                    S.offs_sw[ks * 16 + 2 * tq + 8], S.offs_sw[ks * 16 + 2 * tq + 9]};
+            const uint32_t cc[4] = {osw[ks * 16 + 2 * tq], osw[ks * 16 + 2 * tq + 1],
+                                    osw[ks * 16 + 2 * tq + 8], osw[ks * 16 + 2 * tq + 9]};
             constexpr uint32_t PART = KS * NTILES * 32;  // uint2 entries per part
 #pragma unroll
             for (int ri = 0; ri < 2; ++ri) {  // Re inputs with k-step ks, then Im inputs with ks + KS/2
@@ -253,7 +254,7 @@ __device__ __forceinline__ void apply_dense_mma(float2 *tile, const uint32_t *__
         }
     }
     __syncwarp();
-    const uint32_t *offs = S.offs_sw;
+    const uint32_t *offs = osw;
     // outputs: n-tile j < NTILES/2 holds Re of outputs 8j + 2tq (+1), tile j + NTILES/2 the Im parts
 #pragma unroll
     for (uint32_t mt = 0; mt < MT; ++mt) {
@@ -293,7 +294,7 @@ __device__ __forceinline__ bool umma_commit_wait(const PassSmem &S, uint32_t &ph
 
 // Row g of D (TMEM lane g: Re of the 32 outputs in columns 0..31, Im in 32..63) back to the group's tile
 // positions.
-__device__ __forceinline__ void umma_epilogue(float2 *tile, uint32_t base, const PassSmem &S) {
+__device__ __forceinline__ void umma_epilogue(float2 *tile, uint32_t base, const uint32_t *osw, const PassSmem &S) {
     umma::fence_after_sync();
     const uint32_t taddr = S.tmem + ((32u * (threadIdx.x >> 5)) << 16);
     uint32_t re[32], im[32];
@@ -301,7 +302,7 @@ __device__ __forceinline__ void umma_epilogue(float2 *tile, uint32_t base, const
     umma::tmem_ld32(taddr + 32u, im);
 #pragma unroll
     for (uint32_t j = 0; j < 32; ++j)
-        tile[base ^ S.offs_sw[j]] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+        tile[base ^ osw[j]] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
     umma::fence_before_sync();  // the next op's barrier orders these TMEM reads before its MMAs
 }
 
@@ -315,15 +316,16 @@ __device__ __forceinline__ void umma_epilogue(float2 *tile, uint32_t base, const
 // writes the group's outputs back to their tile positions, which only it owns in this op.
 // Returns false when the wait ran out (status set; the tile is then left unwritten).
 template <int NT>
-__device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, const PassSmem &S, uint32_t &phase,
+__device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, const uint32_t *cb, const uint32_t *osw,
+                                                 const PassSmem &S, uint32_t &phase,
                                                  int *status) {
     static_assert(NT == 128, "one thread per index group");
     const uint32_t g = threadIdx.x;
-    const uint32_t base = S.cb[0][g & 63u] ^ S.cb[1][g >> 6];
+    const uint32_t base = cb[g & 63u] ^ cb[64u + (g >> 6)];
     uint32_t re[32], im[32];
 #pragma unroll
     for (uint32_t j = 0; j < 32; ++j) {
-        const float2 v = tile[base ^ S.offs_sw[j]];
+        const float2 v = tile[base ^ osw[j]];
         re[j] = f32_to_tf32(v.x);
         im[j] = f32_to_tf32(v.y);
     }
@@ -350,7 +352,7 @@ __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, con
         }
     }
     if (!umma_commit_wait(S, phase, status)) return false;
-    umma_epilogue(tile, base, S);
+    umma_epilogue(tile, base, osw, S);
     return true;
 }
 
@@ -360,15 +362,16 @@ __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, con
 // then A_mid over A_lo for mid x B_mid, mid x B_hi, hi x B_mid, hi x B_hi (small terms first; each thread
 // keeps its A_mid words in registers across the first wait). B: three 8 KB parts (hi, mid, lo) at bsm.
 template <int NT>
-__device__ __forceinline__ bool apply_dense_umma3(float2 *tile, uint32_t bsm, const PassSmem &S, uint32_t &phase,
+__device__ __forceinline__ bool apply_dense_umma3(float2 *tile, uint32_t bsm, const uint32_t *cb, const uint32_t *osw,
+                                                  const PassSmem &S, uint32_t &phase,
                                                   int *status) {
     static_assert(NT == 128, "one thread per index group");
     const uint32_t g = threadIdx.x;
-    const uint32_t base = S.cb[0][g & 63u] ^ S.cb[1][g >> 6];
+    const uint32_t base = cb[g & 63u] ^ cb[64u + (g >> 6)];
     float x[64];  // K order: Re parts of inputs 0..31, then Im parts
 #pragma unroll
     for (uint32_t j = 0; j < 32; ++j) {
-        const float2 v = tile[base ^ S.offs_sw[j]];
+        const float2 v = tile[base ^ osw[j]];
         x[j] = v.x;
         x[32 + j] = v.y;
     }
@@ -425,7 +428,7 @@ __device__ __forceinline__ bool apply_dense_umma3(float2 *tile, uint32_t bsm, co
         product(0, 0, 0);  // hi x B_hi
     }
     if (!umma_commit_wait(S, phase, status)) return false;
-    umma_epilogue(tile, base, S);
+    umma_epilogue(tile, base, osw, S);
     return true;
 }
 
@@ -433,35 +436,35 @@ __device__ __forceinline__ bool apply_dense_umma3(float2 *tile, uint32_t bsm, co
 // form needs 4096-amplitude tiles and at least 16 index groups per warp.
 template <int NT, int KMAX, int PREC>
 __device__ __forceinline__ void apply_dense_dispatch(uint32_t k, float2 *tile, const float2 *mat, const uint32_t *bfr,
-                                                     const PassSmem &S, uint32_t T) {
+                                                     const uint32_t *cb, const uint32_t *osw, uint32_t T) {
     constexpr bool TC = PREC != QSIM_PREC_FP32;
     const uint32_t min_k = PREC == QSIM_PREC_TF32 ? 3u : 4u;  // an MMA k-step must not straddle Re and Im
     const bool tc_ok = TC && k >= min_k && k <= 5 && T == 12;  // 16+ index groups per warp for NT <= 256
     switch (k) {
-        case 1: apply_dense_k1<NT>(tile, mat, S, T); break;
-        case 2: if constexpr (KMAX >= 2) apply_dense<NT, 2>(tile, mat, S, T); break;
+        case 1: apply_dense_k1<NT>(tile, mat, cb, osw, T); break;
+        case 2: if constexpr (KMAX >= 2) apply_dense<NT, 2>(tile, mat, cb, osw, T); break;
         case 3:
             if constexpr (KMAX >= 3) {
                 if constexpr (PREC == QSIM_PREC_TF32) {
-                    if (tc_ok) { apply_dense_mma<NT, 3, PREC>(tile, bfr, S, T); break; }
+                    if (tc_ok) { apply_dense_mma<NT, 3, PREC>(tile, bfr, cb, osw, T); break; }
                 }
-                apply_dense<NT, 3>(tile, mat, S, T);
+                apply_dense<NT, 3>(tile, mat, cb, osw, T);
             }
             break;
         case 4:
             if constexpr (KMAX >= 4) {
-                if (tc_ok) apply_dense_mma<NT, 4, PREC>(tile, bfr, S, T);
-                else apply_dense<NT, 4>(tile, mat, S, T);
+                if (tc_ok) apply_dense_mma<NT, 4, PREC>(tile, bfr, cb, osw, T);
+                else apply_dense<NT, 4>(tile, mat, cb, osw, T);
             }
             break;
         case 5:
             if constexpr (KMAX >= 5) {
-                if (tc_ok) apply_dense_mma<NT, 5, PREC>(tile, bfr, S, T);
-                else apply_dense<NT, 5>(tile, mat, S, T);
+                if (tc_ok) apply_dense_mma<NT, 5, PREC>(tile, bfr, cb, osw, T);
+                else apply_dense<NT, 5>(tile, mat, cb, osw, T);
             }
             break;
         default:
-            if constexpr (KMAX >= 6) apply_dense<NT, 6>(tile, mat, S, T);
+            if constexpr (KMAX >= 6) apply_dense<NT, 6>(tile, mat, cb, osw, T);
             break;
     }
 }
@@ -620,20 +623,27 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                     cp_async_commit();
                 }
             }
+            // swizzled group bases (cb[g & 63] ^ cb[64 + (g >> 6)]) and column offsets (osw): copied from the
+            // host-built tables in the blob for the tensor-core ops, else built here
+            const uint32_t *cb = &S.cb[0][0], *osw = S.offs_sw;
             const float2 *M = mat;
             if (!tc) {
                 if (op.tab != kNoTab) M = bf2 + op.tab;
                 else
                     for (uint32_t i = tid; i < D * D; i += NT) mat[i] = mats[op.mat + i];
             }
-            if (tid < int(D)) {
-                uint32_t o = 0;
-                for (uint32_t j = 0; j < k; ++j) o |= ((uint32_t(tid) >> j) & 1u) << op.tq[j];
-                S.offs[tid] = o;
-                S.offs_sw[tid] = swz(o);
-            }
-            if (tid < 16) S.comp[tid] = op.comp[tid];
-            {
+            if (op.dlut != kNoTab) {
+                const uint32_t *ht = reinterpret_cast<const uint32_t *>(blob) + op.dlut;
+                for (uint32_t x = tid; x < 128 + D; x += NT) {
+                    if (x < 128) S.cb[x >> 6][x & 63u] = ht[x];
+                    else S.offs_sw[x - 128] = ht[x];
+                }
+            } else {
+                if (tid < int(D)) {
+                    uint32_t o = 0;
+                    for (uint32_t j = 0; j < k; ++j) o |= ((uint32_t(tid) >> j) & 1u) << op.tq[j];
+                    S.offs_sw[tid] = swz(o);
+                }
                 const uint32_t nc = T - k;
                 for (uint32_t x = tid; x < 128; x += NT) {
                     const uint32_t half = x >> 6, v = x & 63u;
@@ -646,15 +656,16 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
             __syncthreads();
             if constexpr (UM) {
                 if (um) {
-                    const bool done = PREC == QSIM_PREC_BF16X3
-                                          ? apply_dense_umma3<NT>(tile, umma::smem_addr(bbuf), S, phase, status)
-                                          : apply_dense_umma<NT>(tile, umma::smem_addr(bbuf), S, phase, status);
+                    const bool done =
+                        PREC == QSIM_PREC_BF16X3
+                            ? apply_dense_umma3<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status)
+                            : apply_dense_umma<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status);
                     if (!done) return false;
                     oi += adv;
                     continue;
                 }
             }
-            if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, M, bfr + op.bfrag, S, T);
+            if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, M, bfr + op.bfrag, cb, osw, T);
         } else if (type == OP_DIAG) {
             // a run of r diagonal ops in one sweep; op d's phase index = bits constant over the
             // tile | lookups over the tile bits 0..6 and 7..12
