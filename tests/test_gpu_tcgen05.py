@@ -85,3 +85,35 @@ def test_tcgen05_bounded_wait_reports_timeout():
     got = qsim.run(qsim.plan_stages(c, **kw)).decompress().cpu().numpy()
     want = oracle.simulate(c)
     assert np.linalg.norm(got - want) <= stalled.stats()["dense_ops"] * 2.0 ** -10
+
+
+def test_bench_configuration_full_size_sampled():
+    # the default bench line's launch configuration: 28-qubit QFT of a random basis state + 4 x (RZ layer, CX
+    # ladder), m = 22, inner 4, k = 5, TF32 on tcgen05, 2 streams, compressed; 4096 sampled amplitudes against
+    # the closed form
+    c = inputs.qft_rz_cx(28, 4, 1)
+    st = qsim.run(qsim.plan_stages(c, m=22, inner=4, k=5, eps=1e-3, prec=qsim.PREC_TF32, tcgen05=1, streams=2))
+    assert st.stats.fidelity_lower_bound >= 0.99
+    idx = (inputs.splitmix64_array(78, 4096) >> np.uint64(36)).astype(np.uint64)
+    got = st.amplitudes(idx).astype(np.complex128)
+    want = cf.qft_rz_cx_amplitudes(28, c.meta["x"], c.meta["rz_angles"], idx)
+    eb = 1e-3 * 2.0 ** -14
+    # codec error <= eb per component per stage, plus the TF32 gate error (2 % of the amplitude scale bound)
+    assert np.max(np.abs(got - want)) <= 2 * eb * st.nstages + 2e-2 * 2.0 ** -14
+    fs = abs(np.vdot(want, got)) / (np.linalg.norm(want) * np.linalg.norm(got))
+    assert fs >= 0.99
+
+
+@pytest.mark.parametrize("prec,rel_tol", [(qsim.PREC_TF32, 2e-2), (qsim.PREC_BF16X3, 1e-4)], ids=["tf32", "bf16x3"])
+def test_full_size_gate_error_vs_fp64(prec, rel_tol):
+    # the 28-qubit workload with the codec off: the tcgen05 gate arithmetic against the exact state, with the
+    # warp-level path's bounds
+    c = inputs.qft_rz_cx(28, 4, 1)
+    st = qsim.run(qsim.plan_stages(c, m=22, inner=4, k=5, codec=qsim.CODEC_NONE, prec=prec, tcgen05=1))
+    idx = (inputs.splitmix64_array(91, 4096) >> np.uint64(36)).astype(np.uint64)
+    got = st.amplitudes(idx).astype(np.complex128)
+    want = cf.qft_rz_cx_amplitudes(28, c.meta["x"], c.meta["rz_angles"], idx)
+    err = float(np.max(np.abs(got - want)))
+    assert err / 2.0 ** -14 <= rel_tol
+    if prec == qsim.PREC_BF16X3:
+        assert err <= 1e-5
