@@ -72,9 +72,12 @@ typedef struct qsim_gate {
 #define QSIM_CODEC_QSZ1 0u /* compressed blocks under a point-wise absolute bound (the method) */
 #define QSIM_CODEC_NONE 1u /* raw complex64 blocks: the no-compression comparison run */
 #define QSIM_CODEC_QSZR 2u /* compressed blocks under a point-wise relative bound eps (Sec. 4.3,
-                              Eq. 1-2, Algorithm 2): streams mode with exact sizing only */
+                              Eq. 1-2, Algorithm 2); both modes, exact or learned sizing */
 
-#define QSIM_SIZING_EXACT 0u   /* a sizing pass computes each block's exact size first */
+#define QSIM_SIZING_EXACT 0u   /* every block gets a slot of its exact size: in streams mode the encoder
+                                  codes the frames in place in one read of the working vector and then
+                                  reserves the exact slots; the persistent kernel sizes the frames in
+                                  one read and encodes at the known offsets in a second */
 #define QSIM_SIZING_PREDICT 1u /* learned size predictor reserves space; overflow re-encodes */
 
 typedef struct qsim_config {
@@ -186,10 +189,17 @@ typedef struct qsim_stats {
 } qsim_stats;
 
 /*
- * Run the plan from |init_basis>. Work is ordered on cuda_stream (and on the
- * library's own streams, joined back to it); the call returns once the run
- * is complete and *stats (nullable) is filled. *out receives a state handle
- * owning the final compressed store.
+ * Run the plan from |init_basis> (Sec. 4.2: the initial store encodes the
+ * block holding the basis state and one zero block, copied to every other
+ * block; then, stage after stage, every SV group — the 2^|inner| blocks that
+ * share their outer index bits — is decompressed, updated by the stage's
+ * gates and compressed again, the groups overlapped on CUDA streams, or in
+ * persistent mode inside one kernel per stage). Blocks live in the device
+ * tier, then in pinned host memory once the device tier is full (Sec. 4.4).
+ * Work is ordered on cuda_stream (and on the library's own streams, joined
+ * back to it); the call returns once the run is complete and *stats
+ * (nullable) is filled. *out receives a state handle owning the final
+ * compressed store (the library's memory until qsim_state_free).
  * Errors: NOMEM (tiers full), RANGE, TIMEOUT, CUDA, INVALID.
  */
 int qsim_run(const qsim_plan *plan, void *cuda_stream, qsim_state **out, qsim_stats *stats);
@@ -201,8 +211,12 @@ int qsim_state_stage_stats(const qsim_state *st, size_t stage, uint64_t *store_b
 
 /* ---- readout -------------------------------------------------------------- */
 
-/* Gather `count` amplitudes by index into out_interleaved (HOST, 2*count
- * floats). Only the blocks holding them are decompressed. */
+/* Read the final state (Sec. 4.2's loop leaves it compressed, block by
+ * block): gather `count` amplitudes, indices idx (host, each < 2^n), into
+ * out_interleaved (HOST, 2*count floats, re then im per amplitude). Only the
+ * blocks holding them are decompressed, into library scratch on the state's
+ * device. Errors: INVALID (null pointer, index out of range), NOMEM, CUDA,
+ * CORRUPT. */
 int qsim_amplitudes(const qsim_state *st, const uint64_t *idx, size_t count, float *out_interleaved);
 
 /* Fidelity |<ref|sim>| / (||ref|| ||sim||) (Sec. 5.3 definition, normalised),
@@ -233,10 +247,14 @@ size_t qsim_worst_case_bytes(uint32_t m);
 size_t qsim_worst_case_bytes_rel(uint32_t m);
 
 /*
- * Compress one block of 2^m complex64 amplitudes (d_amps, device) under the
- * absolute bound eb into d_out (device, cap bytes). The call synchronises
- * cuda_stream and writes the stream size to *out_bytes (host). Every
- * reconstructed component is within eb of the input.
+ * Compress one SV block (Sec. 4.3: error-bounded lossy compression of a
+ * block, here under a point-wise ABSOLUTE bound with this library's QSZ1
+ * format: quantisation to int32 on the grid 2^e with 2^e <= 2 eb, a delta
+ * within 32-value chunks, zigzag and bit-plane packing at each chunk's
+ * width). d_amps: 2^m complex64 amplitudes on the device, interleaved,
+ * 16-byte aligned, not modified; d_out: device, cap bytes. The call
+ * synchronises cuda_stream and writes the stream size to *out_bytes (host).
+ * Every reconstructed component is within eb of the input.
  * Errors: INVALID (m outside 5..26, eb out of range, NaN/Inf input), RANGE,
  * CAPACITY (cap too small; *out_bytes = the size needed), CUDA.
  * Calls from several host threads are serialised inside the library.
@@ -289,8 +307,10 @@ int qsim_compress_block_rel(const float *d_amps, uint32_t m, double rel, void *d
                             size_t *out_bytes, void *cuda_stream);
 
 /*
- * Decompress a QSZ1 or QSZR stream (d_in, device, in_bytes; the format is
- * read from its magic number) into d_amps (device, 2^m complex64).
+ * Decompress one SV block (the inverse of the block codec of Sec. 4.3, run
+ * before every stage's gate updates in Sec. 4.2): a QSZ1 or QSZR stream
+ * (d_in, device, in_bytes; the format is read from its magic number) into
+ * d_amps (device, 2^m complex64, interleaved; the caller's buffer).
  * Synchronises cuda_stream to report the status.
  * Errors: INVALID, CORRUPT (bad magic/header/offsets/widths/sign types), CUDA.
  */

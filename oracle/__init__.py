@@ -24,8 +24,13 @@ Parity status per function (what pins it is in tests/test_oracle_*.py):
                       test, sign-chunk elision lengths, idempotence, corruption.
   partition           pinned: invariants of Algorithm 1 plus hand-worked cases.
   mlp_*               pinned: central finite differences, closed-form linear case,
-                      Adam against its published recurrence on a scalar.
-  simulate_staged     pinned through simulate (no codec) and the point-wise bound.
+                      a closed form whose value needs the ReLU of both hidden
+                      layers (|x| from relu(x) + relu(-x), rows with negative
+                      pre-activations cleared, their gradients zero), Adam
+                      against its published recurrence on a scalar.
+  simulate_staged     pinned: a two-stage 5-qubit case worked by hand (stage cut,
+                      grid step, the state stored after each stage), output on
+                      the 2^e grid and different from simulate, the norm bound.
 """
 from __future__ import annotations
 

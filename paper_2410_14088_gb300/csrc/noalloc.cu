@@ -120,7 +120,10 @@ extern "C" int qsim_compress_block_noalloc(const float *d_amps, uint32_t m, doub
     int h_status = 0;
     ce = cudaMemcpyAsync(&r, res, sizeof(r), cudaMemcpyDeviceToHost, s);
     if (ce == cudaSuccess) ce = cudaMemcpyAsync(&h_status, status, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (ce == cudaSuccess) ce = cudaStreamSynchronize(s);
+    // Once the encoder is queued, wait for the stream on every path, failed copies included: the next call
+    // (possibly on another stream) clears the shared array and must not do so under a running encoder.
+    const cudaError_t se = cudaStreamSynchronize(s);
+    if (ce == cudaSuccess) ce = se;
     if (ce != cudaSuccess) return set_error(QSIM_E_CUDA, "compress (no-alloc): %s", cudaGetErrorString(ce));
     if (h_status) return set_error(h_status, "compress (no-alloc): device status %d", h_status);
     *out_bytes = size_t(r.total);

@@ -472,7 +472,16 @@ def compress_block_noalloc(amps, m: int, eb: float, out, cap: Optional[int] = No
     """qsim_compress_block_noalloc: same stream as compress_block, but the
     library allocates nothing (its scratch is a fixed device array). `out` is
     the caller's uint8 CUDA tensor. Returns (rc, nbytes) without raising."""
+    import torch
+    nfloat = amps.numel() * (2 if amps.dtype == torch.complex64 else 1)
+    if not (amps.is_cuda and amps.dtype in (torch.complex64, torch.float32) and amps.is_contiguous()
+            and nfloat >= (2 << m)):
+        raise ValueError("amps must be a contiguous CUDA tensor of 2^m complex64 (or 2^(m+1) float32) values")
+    if not (out.is_cuda and out.dtype == torch.uint8 and out.is_contiguous()):
+        raise ValueError("out must be a contiguous uint8 CUDA tensor")
     cap = out.numel() if cap is None else cap
+    if cap > out.numel():
+        raise ValueError("cap exceeds the bytes of out")
     nb = ctypes.c_size_t()
     rc = lib().qsim_compress_block_noalloc(ctypes.c_void_p(amps.data_ptr()), m, eb, ctypes.c_void_p(out.data_ptr()),
                                            cap, ctypes.byref(nb), _stream_ptr(stream))

@@ -186,3 +186,35 @@ def test_staged_quantised_simulation_bound():
     bound = len(stages) * math.sqrt(2 * (1 << 12)) * eb
     assert np.linalg.norm(staged - exact) <= bound
     assert oracle.fidelity(exact, staged.astype(np.complex64)) >= 0.99
+
+
+def test_staged_hand_worked_two_stages():
+    # n = 5, m = 2, inner 2: the global qubits are 2, 3, 4 and a stage may hold two of them, so
+    # [U3(pi/3, 0, 0) on 2, H on 3] is stage 1 and [H on 4] stage 2 (Algorithm 1).
+    # eps = 0.5: eb = 0.5 * 2^(-5/2) = 0.0884, 2 eb = 0.177, so e = -3 and the grid step is 1/8.
+    # Stage 1 exact: cos(pi/6)/sqrt2 = 0.61237 at |0>, |8>; sin(pi/6)/sqrt2 = 0.35355 at |4>, |12>;
+    #   stored: rint(4.899)/8 = 0.625 and rint(2.828)/8 = 0.375.
+    # Stage 2 from the stored state: 0.625/sqrt2 * 8 = 3.536 -> 0.5, 0.375/sqrt2 * 8 = 2.121 -> 0.25.
+    # Without the stage-1 quantisation the first value would be rint(3.464)/8 = 0.375, with a step of 1/16
+    # it would be 0.4375 and with none 0.4330, so each of those mistakes changes the result.
+    c = inputs.Circuit(5, [inputs.U3(2, math.pi / 3, 0.0, 0.0), inputs.H(3), inputs.H(4)])
+    staged, stages, e = oracle.simulate_staged(c, m=2, inner_size=2, eps=0.5)
+    assert e == -3
+    assert [s.gate_indices for s in stages] == [[0, 1], [2]]
+    want = np.zeros(32, np.complex128)
+    want[[0, 8, 16, 24]] = 0.5
+    want[[4, 12, 20, 28]] = 0.25
+    assert np.array_equal(staged, want)
+
+
+def test_staged_output_on_grid_and_not_the_exact_state():
+    c = inputs.random_brick(10, 6, 12)
+    staged, stages, e = oracle.simulate_staged(c, m=5, inner_size=2, eps=1e-2)
+    assert len(stages) >= 2
+    q = staged.view(np.float64) / 2.0 ** e
+    assert np.array_equal(q, np.rint(q))
+    exact = oracle.simulate(c)
+    d = np.abs(staged - exact)
+    assert d.max() > 0
+    # each stage moves every component by at most half a step; the unitary stages keep 2-norms
+    assert np.linalg.norm(staged - exact) <= len(stages) * math.sqrt(2 << 10) * 2.0 ** (e - 1)

@@ -5,13 +5,20 @@ block: their framework already owns the device memory through its own pool,
 or they must keep a fixed footprint once started, or they run in a loop
 where an allocation would synchronise the device. The no-alloc entry point
 serves them from a fixed device array. Here it must give the same stream,
-byte for byte, as qsim_compress_block, on two calls in a row (the second
-call finds the first call's leftovers in the shared array), and reject
-blocks larger than its fixed scratch covers. This file is collected last.
+byte for byte, as qsim_compress_block and as the CPU oracle's encoder, on
+two calls in a row (the second call finds the first call's leftovers in the
+shared array), also when it is the first call of the library in a fresh
+process, and reject blocks larger than its fixed scratch covers. This file is
+collected last.
 """
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
+import oracle
 from paper_2410_14088_gb300 import inputs, qsim
 
 pytestmark = pytest.mark.gpu
@@ -32,6 +39,7 @@ def test_noalloc_matches_compress_block_on_consecutive_calls():
             assert rc == qsim.OK, qsim.lib().qsim_last_error()
             assert nb == nref
             assert torch.equal(out[:nb], ref[:nref]), (call, m)
+            assert out[:nb].cpu().numpy().tobytes() == oracle.qsz_encode(x.cpu().numpy(), m, eb), (call, m)
 
 
 def test_noalloc_limits_and_capacity():
@@ -50,3 +58,30 @@ def test_noalloc_limits_and_capacity():
     out = torch.empty(nref, dtype=torch.uint8, device="cuda")
     rc, nb = qsim.compress_block_noalloc(x, m, 1e-6, out)
     assert rc == qsim.OK and nb == nref and torch.equal(out, ref[:nref])
+
+
+CHILD = """
+import sys
+import torch
+sys.path.insert(0, sys.argv[1])
+import oracle
+from paper_2410_14088_gb300 import inputs, qsim
+torch.cuda.set_device(0)
+m, eb = 13, 1e-3 * 2.0 ** -9
+for call in range(2):
+    x = torch.from_numpy(inputs.gaussian_block(m, 18, 70 + call)).cuda()
+    out = torch.zeros(qsim.worst_case_bytes(m), dtype=torch.uint8, device="cuda")
+    rc, nb = qsim.compress_block_noalloc(x, m, eb, out)
+    assert rc == qsim.OK, qsim.lib().qsim_last_error()
+    assert out[:nb].cpu().numpy().tobytes() == oracle.qsz_encode(x.cpu().numpy(), m, eb), call
+print("fresh-process no-alloc ok")
+"""
+
+
+def test_noalloc_first_call_in_a_fresh_process():
+    # the device address of the fixed array is looked up by the first call on a device: run that call as
+    # the first call of the library in a new process, twice in a row, against the oracle's stream
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", CHILD, root], capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stdout + r.stderr
+    assert "fresh-process no-alloc ok" in r.stdout
