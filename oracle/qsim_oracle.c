@@ -496,11 +496,22 @@ int oracle_qsz_decode(const uint8_t *in, uint64_t in_bytes, int m, float *amps)
 /* bit planes). A frame whose codes are all zero has length 0. Otherwise:    */
 /*   u8 widths[2C], padded to 16 B;                                          */
 /*   sign chunk types, 2 bits per chunk t (byte t/4, bits 2(t%4)): 0 = all   */
-/*     32 signs 0, 1 = all 32 signs 1, 2 = mixed (the pre-scan of the sign   */
-/*     bitmap that drops all-0 and all-1 chunks), padded to 16 B;            */
-/*   the sign word (bit j = sign of value j) of every mixed chunk, in t      */
-/*     order, u32 each, padded to 16 B;                                      */
+/*     32 signs 0, 1 = all 32 signs 1 (the pre-scan of the sign bitmap       */
+/*     that drops all-0 and all-1 chunks), 2 = stored word, 3 = run-coded,   */
+/*     padded to 16 B;                                                       */
+/*   the sign section, padded to 16 B as a whole: the sign word (bit j =     */
+/*     sign of value j) of every type-2 chunk, u32 each, in t order; then    */
+/*     one u16 run record per type-3 chunk, in t order;                      */
 /*   the code bit planes as in QSZ1, padded to 16 B.                         */
+/*                                                                           */
+/* Lossless coding of the remaining bitmap (Algorithm 2's last step): a      */
+/* chunk whose 32 signs change between neighbours 1 to 3 times (one to three */
+/* run boundaries; the transition word T = (W ^ (W >> 1)) & 0x7FFFFFFF has   */
+/* 1 to 3 bits set) is type 3 and stores 2 bytes instead of 4: bit 15 = the  */
+/* sign of value 0, bits 0-4, 5-9, 10-14 = the boundaries p1 < p2 < p3 in    */
+/* 1..31 (value p differs from value p - 1; bit p - 1 of T), unused fields   */
+/* zero. Decoding: W = bit 15 ? all ones : 0, then W ^= ~0 << p for every    */
+/* nonzero field. A chunk with 4 or more boundaries keeps its raw word.      */
 /* ====================================================================== */
 
 #define QSZR_MAGIC 0x525A5351u
@@ -560,6 +571,42 @@ int oracle_qszr_quantize(const float *x, int64_t count, int k, int32_t *q, uint8
     return OR_OK;
 }
 
+/* Sign chunk type of sign word w: 0 all clear, 1 all set, 3 run-coded (1..3 boundaries), 2 stored. */
+static uint32_t qszr_sign_type(uint32_t w)
+{
+    if (w == 0u)
+        return 0u;
+    if (w == 0xFFFFFFFFu)
+        return 1u;
+    const uint32_t t = (w ^ (w >> 1)) & 0x7FFFFFFFu;
+    int r = 0;
+    for (int j = 0; j < 31; ++j)
+        r += (int)((t >> j) & 1u);
+    return r <= 3 ? 3u : 2u;
+}
+
+/* Run record of a type-3 sign word: bit 15 = bit 0 of w, then the boundaries in ascending order. */
+static uint16_t qszr_run_record(uint32_t w)
+{
+    uint32_t rec = (w & 1u) << 15, field = 0;
+    for (int j = 0; j < 31; ++j)
+        if ((((w >> j) ^ (w >> (j + 1))) & 1u) != 0u)
+            rec |= (uint32_t)(j + 1) << (5 * field++);
+    return (uint16_t)rec;
+}
+
+/* Sign word of a run record; 0 with *ok = 0 for a record no encoder writes. */
+static uint32_t qszr_run_word(uint32_t rec, int *ok)
+{
+    const uint32_t p[3] = {rec & 31u, (rec >> 5) & 31u, (rec >> 10) & 31u};
+    *ok = p[0] != 0u && (p[1] == 0u ? p[2] == 0u : (p[1] > p[0] && (p[2] == 0u || p[2] > p[1])));
+    uint32_t w = (rec >> 15) ? 0xFFFFFFFFu : 0u;
+    for (int i = 0; i < 3; ++i)
+        if (p[i])
+            w ^= 0xFFFFFFFFu << p[i];
+    return w;
+}
+
 int oracle_qszr_encode(const float *amps, int m, double rel, uint8_t *out, uint64_t cap, uint64_t *out_bytes)
 {
     if (m < QSZ_MIN_M || m > QSZ_MAX_M)
@@ -609,15 +656,17 @@ int oracle_qszr_encode(const float *amps, int m, double rel, uint8_t *out, uint6
     uint64_t pos = data_start;
     for (int64_t f = 0; f < nframes; ++f) {
         offs[f] = pos;
-        uint64_t words = 0, mixed = 0;
+        uint64_t words = 0, mixed = 0, runs = 0;
         for (int plane = 0; plane < 2; ++plane)
             for (int64_t c = 0; c < C; ++c) {
                 const int64_t t = plane * NC + f * C + c;
+                const uint32_t type = qszr_sign_type(sw[t]);
                 words += w[t];
-                mixed += sw[t] != 0 && sw[t] != 0xFFFFFFFFu;
+                mixed += type == 2u;
+                runs += type == 3u;
             }
         if (words)
-            pos += pad16(2 * C) + pad16(tbytes) + pad16(4 * mixed) + pad16(4 * words);
+            pos += pad16(2 * C) + pad16(tbytes) + pad16(4 * mixed + 2 * runs) + pad16(4 * words);
     }
     offs[nframes] = pos;
     *out_bytes = pos;
@@ -647,17 +696,24 @@ int oracle_qszr_encode(const float *amps, int m, double rel, uint8_t *out, uint6
                 fp[plane * C + c] = w[plane * NC + f * C + c];
         uint8_t *tp = fp + pad16(2 * C);
         uint8_t *mp = tp + pad16(tbytes);
-        uint64_t mixed = 0;
+        uint64_t mixed = 0, runs = 0;
+        for (int plane = 0; plane < 2; ++plane)
+            for (int64_t c = 0; c < C; ++c)
+                mixed += qszr_sign_type(sw[plane * NC + f * C + c]) == 2u;
+        uint8_t *rp = mp + 4 * mixed; /* the run records follow the stored words */
+        mixed = 0;
         for (int plane = 0; plane < 2; ++plane)
             for (int64_t c = 0; c < C; ++c) {
                 const int64_t t = plane * C + c;
                 const uint32_t s = sw[plane * NC + f * C + c];
-                const uint32_t type = s == 0 ? 0u : s == 0xFFFFFFFFu ? 1u : 2u;
+                const uint32_t type = qszr_sign_type(s);
                 tp[t / 4] |= (uint8_t)(type << (2 * (t % 4)));
                 if (type == 2)
                     put_u32(mp + 4 * mixed++, s);
+                else if (type == 3)
+                    put_u16(rp + 2 * runs++, qszr_run_record(s));
             }
-        uint8_t *wp = mp + pad16(4 * mixed);
+        uint8_t *wp = mp + pad16(4 * mixed + 2 * runs);
         for (int plane = 0; plane < 2; ++plane)
             for (int64_t c = 0; c < C; ++c) {
                 const int64_t ch = f * C + c;
@@ -713,16 +769,17 @@ int oracle_qszr_decode(const uint8_t *in, uint64_t in_bytes, int m, float *amps)
             words += fp[t];
         }
         const uint8_t *tp = fp + pad16(2 * C);
+        uint64_t runs = 0;
         for (int64_t t = 0; t < 2 * C; ++t) {
             const uint32_t type = (tp[t / 4] >> (2 * (t % 4))) & 3u;
-            if (type == 3)
-                return OR_E_CORRUPT;
             mixed += type == 2;
+            runs += type == 3;
         }
-        if (words == 0 || b - a != pad16(2 * C) + pad16(tbytes) + pad16(4 * mixed) + pad16(4 * words))
+        if (words == 0 || b - a != pad16(2 * C) + pad16(tbytes) + pad16(4 * mixed + 2 * runs) + pad16(4 * words))
             return OR_E_CORRUPT;
         const uint8_t *mp = tp + pad16(tbytes);
-        const uint8_t *wp = mp + pad16(4 * mixed);
+        const uint8_t *rp = mp + 4 * mixed;
+        const uint8_t *wp = mp + pad16(4 * mixed + 2 * runs);
         for (int plane = 0; plane < 2; ++plane)
             for (int64_t c = 0; c < C; ++c) {
                 const int64_t t = plane * C + c;
@@ -731,6 +788,12 @@ int oracle_qszr_decode(const uint8_t *in, uint64_t in_bytes, int m, float *amps)
                 if (type == 2) {
                     s = get_u32(mp);
                     mp += 4;
+                } else if (type == 3) {
+                    int ok;
+                    s = qszr_run_word((uint32_t)rp[0] | ((uint32_t)rp[1] << 8), &ok);
+                    rp += 2;
+                    if (!ok)
+                        return OR_E_CORRUPT;
                 }
                 const int wc = fp[t];
                 uint32_t zc[32];

@@ -43,12 +43,47 @@ __device__ __forceinline__ FrameGeom geom(int m) {
 }
 
 // QSZR (relative bound): per-frame side record of the in-place encoder (widths at 0, sign chunk types at
-// kSideTypes, Re and Im mixed sign words at kSideMixRe / kSideMixIm) and the code range (|x| < 2^64)
-constexpr uint32_t kSideTypes = 256, kSideMixRe = 320, kSideMixIm = 832;
+// kSideTypes, Re and Im stored sign words at kSideMixRe / kSideMixIm, Re and Im run records (u16) at
+// kSideRunRe / kSideRunIm) and the code range (|x| < 2^64)
+constexpr uint32_t kSideTypes = 256, kSideMixRe = 320, kSideMixIm = 832, kSideRunRe = 1344, kSideRunIm = 1600;
 constexpr uint32_t kQszrMaxU = 0x5F800000u;
 
-// sign chunk type: 0 all clear, 1 all set, 2 mixed
-__device__ __forceinline__ uint32_t sign_type(uint32_t w) { return w == 0u ? 0u : (w == 0xFFFFFFFFu ? 1u : 2u); }
+// sign chunk type: 0 all clear, 1 all set (Algorithm 2's pre-scan), 3 run-coded (the signs change 1 to 3 times
+// between neighbours), 2 stored word
+__device__ __forceinline__ uint32_t sign_type(uint32_t w) {
+    if (w == 0u) return 0u;
+    if (w == 0xFFFFFFFFu) return 1u;
+    return __popc((w ^ (w >> 1)) & 0x7FFFFFFFu) <= 3 ? 3u : 2u;
+}
+
+// run record of a run-coded sign word: bit 15 = sign of value 0, bits 0-4 / 5-9 / 10-14 the run boundaries
+// p1 < p2 < p3 (value p differs from value p - 1), unused fields zero
+__device__ __forceinline__ uint32_t sign_run_record(uint32_t w) {
+    uint32_t t = (w ^ (w >> 1)) & 0x7FFFFFFFu;
+    const uint32_t p1 = __ffs(t);
+    t &= t - 1u;
+    const uint32_t p2 = __ffs(t);
+    t &= t - 1u;
+    const uint32_t p3 = __ffs(t);
+    return ((w & 1u) << 15) | p1 | (p2 << 5) | (p3 << 10);
+}
+
+// sign word of a run record; ok false for a record no encoder writes
+__device__ __forceinline__ uint32_t sign_run_word(uint32_t rec, bool &ok) {
+    const uint32_t p1 = rec & 31u, p2 = (rec >> 5) & 31u, p3 = (rec >> 10) & 31u;
+    ok = p1 != 0u && (p2 == 0u ? p3 == 0u : (p2 > p1 && (p3 == 0u || p3 > p2)));
+    uint32_t w = (rec >> 15) ? 0xFFFFFFFFu : 0u;
+    if (p1) w ^= 0xFFFFFFFFu << p1;
+    if (p2) w ^= 0xFFFFFFFFu << p2;
+    if (p3) w ^= 0xFFFFFFFFu << p3;
+    return w;
+}
+
+// packed sign-section counts of a frame: stored words Re | Im << 8, run records Re << 16 | Im << 24
+__device__ __forceinline__ uint32_t sign_section_bytes(uint32_t mixed) {
+    const uint32_t nw = (mixed & 0xffu) + ((mixed >> 8) & 0xffu), nr = ((mixed >> 16) & 0xffu) + (mixed >> 24);
+    return (4u * nw + 2u * nr + 15u) & ~15u;
+}
 
 __device__ __forceinline__ uint32_t zigzag(int32_t d) {
     return (uint32_t(d) << 1) ^ uint32_t(d >> 31);
@@ -173,7 +208,8 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
     uint32_t wsum = 0, wmax = 0;
     uint2 wb = make_uint2(0, 0);
     uint32_t base_off = 0;
-    uint32_t tw = 0, mbase = 0, nmix = 0;  // REL: sign chunk types of chunks 16 lane.., mixed ranks
+    uint32_t tw = 0, mbase = 0, nmix = 0, rbase = 0, nrun = 0;  // REL: sign chunk types of chunks 16 lane..,
+                                                                 // ranks of stored words and run records
     if (ok && fb > fa) {
         // ---- widths: lane l holds chunks 8l .. 8l+7 (Re chunks 0..C-1, then Im chunks) ----
         if (8u * lane < 2u * g.C) wb = *reinterpret_cast<const uint2 *>(sp + fa + 8u * lane);
@@ -192,23 +228,28 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
         base_off = incl - wsum;
         const uint32_t words = __shfl_sync(kFull, incl, 31);
         const uint32_t maxw = __reduce_max_sync(kFull, wmax);
-        bool tok = true;
         if constexpr (REL) {
             if (16u * uint32_t(lane) < 2u * g.C) tw = *reinterpret_cast<const uint32_t *>(sp + fa + padw + 4u * lane);
-            const uint32_t hi = tw & 0xAAAAAAAAu;  // type 2 (mixed) sets the odd bit alone; type 3 is invalid
-            tok = __all_sync(kFull, (hi & (tw << 1)) == 0u);
-            const uint32_t cnt = __popc(hi);
-            uint32_t mi = cnt;
+            // odd bit of each 2-bit type: set for types 2 (stored word) and 3 (run record)
+            const uint32_t hi = tw & 0xAAAAAAAAu, t3 = hi & (tw << 1);
+            const uint32_t c2 = __popc(hi ^ t3), c3 = __popc(t3);
+            uint32_t mi = c2, ri = c3;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
-                const uint32_t t = __shfl_up_sync(kFull, mi, o);
-                if (lane >= o) mi += t;
+                const uint32_t t = __shfl_up_sync(kFull, mi, o), u = __shfl_up_sync(kFull, ri, o);
+                if (lane >= o) {
+                    mi += t;
+                    ri += u;
+                }
             }
-            mbase = mi - cnt;
+            mbase = mi - c2;
+            rbase = ri - c3;
             nmix = __shfl_sync(kFull, mi, 31);
+            nrun = __shfl_sync(kFull, ri, 31);
         }
-        ok = tok && maxw <= 32 && words > 0 &&
-             uint64_t(fb - fa) == padw + tbp + ((4ull * nmix + 15) & ~15ull) + ((4ull * words + 15) & ~15ull);
+        ok = maxw <= 32 && words > 0 &&
+             uint64_t(fb - fa) == padw + tbp + ((4ull * nmix + 2ull * nrun + 15) & ~15ull) +
+                                      ((4ull * words + 15) & ~15ull);
     }
     if (!ok) {
         if (lane == 0) raise_status(status, QSIM_E_CORRUPT);
@@ -220,8 +261,9 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
         return;
     }
     const uint32_t *mixw = reinterpret_cast<const uint32_t *>(sp + fa + padw + tbp);
-    const uint32_t *payload =
-        reinterpret_cast<const uint32_t *>(sp + fa + padw + tbp + (REL ? ((4u * nmix + 15u) & ~15u) : 0u));
+    const uint16_t *runw = reinterpret_cast<const uint16_t *>(sp + fa + padw + tbp + 4u * nmix);
+    const uint32_t *payload = reinterpret_cast<const uint32_t *>(
+        sp + fa + padw + tbp + (REL ? ((4u * nmix + 2u * nrun + 15u) & ~15u) : 0u));
     const float step = REL ? 0.f : exp2i(e);
     bool qbad = false;
     uint32_t pre[NP > 0 ? NP : 1];
@@ -237,12 +279,14 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
         const uint32_t si0 = (g.C + c0) & 7u;
         uint32_t xr[8], xi[8], wr[8], wi[8];
         // REL: sign chunk types of this batch (owners c0/16 and (C+c0)/16) and the mixed ranks before them
-        uint32_t twr = 0, twi = 0, mbr = 0, mbi = 0;
+        uint32_t twr = 0, twi = 0, mbr = 0, mbi = 0, rbr = 0, rbi = 0;
         if constexpr (REL) {
             twr = __shfl_sync(kFull, tw, c0 >> 4);
             mbr = __shfl_sync(kFull, mbase, c0 >> 4);
+            rbr = __shfl_sync(kFull, rbase, c0 >> 4);
             twi = __shfl_sync(kFull, tw, (g.C + c0) >> 4);
             mbi = __shfl_sync(kFull, mbase, (g.C + c0) >> 4);
+            rbi = __shfl_sync(kFull, rbase, (g.C + c0) >> 4);
         }
         {
             uint32_t sr_ = 0, si_ = 0;
@@ -297,12 +341,25 @@ __device__ __forceinline__ void decode_frame_warp(const uint8_t *sp, uint64_t by
             }
             float2 v;
             if constexpr (REL) {
-                // sign words: all clear, all set, or the chunk's stored word (its rank among the mixed chunks)
+                // sign words: all clear, all set, the chunk's stored word (its rank among the type-2 chunks) or
+                // the word of its run record (its rank among the type-3 chunks)
                 const uint32_t pr = 2u * (c & 15u), pi = 2u * ((g.C + c) & 15u);
                 const uint32_t tr = (twr >> pr) & 3u, ti = (twi >> pi) & 3u;
-                uint32_t swr = tr ? 0xFFFFFFFFu : 0u, swi = ti ? 0xFFFFFFFFu : 0u;
-                if (tr == 2u) swr = __ldg(mixw + mbr + __popc(twr & 0xAAAAAAAAu & ((1u << pr) - 1u)));
-                if (ti == 2u) swi = __ldg(mixw + mbi + __popc(twi & 0xAAAAAAAAu & ((1u << pi) - 1u)));
+                const uint32_t t3r = twr & 0xAAAAAAAAu & (twr << 1), t3i = twi & 0xAAAAAAAAu & (twi << 1);
+                const uint32_t t2r = (twr & 0xAAAAAAAAu) ^ t3r, t2i = (twi & 0xAAAAAAAAu) ^ t3i;
+                uint32_t swr = tr == 1u ? 0xFFFFFFFFu : 0u, swi = ti == 1u ? 0xFFFFFFFFu : 0u;
+                if (tr == 2u) swr = __ldg(mixw + mbr + __popc(t2r & ((1u << pr) - 1u)));
+                if (ti == 2u) swi = __ldg(mixw + mbi + __popc(t2i & ((1u << pi) - 1u)));
+                if (tr == 3u) {
+                    bool rok;
+                    swr = sign_run_word(__ldg(runw + rbr + __popc(t3r & ((1u << pr) - 1u))), rok);
+                    qbad |= !rok;
+                }
+                if (ti == 3u) {
+                    bool rok;
+                    swi = sign_run_word(__ldg(runw + rbi + __popc(t3i & ((1u << pi) - 1u))), rok);
+                    qbad |= !rok;
+                }
                 qbad |= qr > (kQszrMaxU >> e) || qi > (kQszrMaxU >> e);
                 const float mr = __uint_as_float(qr << e), mi = __uint_as_float(qi << e);
                 v = make_float2(((swr >> lane) & 1u) ? -mr : mr, ((swi >> lane) & 1u) ? -mi : mi);
@@ -904,8 +961,10 @@ __device__ __forceinline__ void encode_frame_warp_known(const float2 *__restrict
 // a component x is its FP32 magnitude bit pattern U = bits(|x|) (exponent plus
 // linear mantissa: log2|x| up to a scale and offset) rounded to a multiple of
 // 2^k: q = (U + 2^(k-1)) >> k; the sign (1 for x < 0 with q != 0) goes to a
-// per-chunk sign word W = ballot(sign), stored only for chunks whose signs are
-// mixed (2-bit chunk types: 0 all clear, 1 all set, 2 mixed). Reconstruction
+// per-chunk sign word W = ballot(sign): chunks of all clear or all set signs
+// store only their 2-bit type (0, 1: Algorithm 2's pre-scan); the others are
+// coded losslessly, as a 2-byte run record when the signs change 1 to 3 times
+// between neighbours (type 3), else as the raw word (type 2). Reconstruction
 // |x'| = float(bits q << k).
 // ---------------------------------------------------------------------------
 
@@ -935,9 +994,9 @@ __device__ __forceinline__ int32_t quantize_one(float x, float inv_step, uint32_
 // chunk c end at or before byte 128 (c + 1) of the frame, and every chunk up
 // to c has been read by then), the Im-plane words to im (one word per
 // amplitude of scratch), the chunk widths to side (2C bytes; for REL also the
-// sign chunk types and mixed sign words). Returns the frame's stream bytes;
+// sign chunk types, stored sign words and run records). Returns the frame's stream bytes;
 // words receives its Re-plane words | Im-plane words << 16 (each at most
-// 4096), mixed (REL) its Re | Im mixed sign chunks << 16. The second pass
+// 4096), mixed (REL) its stored sign words Re | Im << 8 and run records Re << 16 | Im << 24. The second pass
 // (copy_frame_warp) moves the pieces to the frame's offset in the block's slot.
 // e is the step exponent (QSZ1) or the shift k (REL). With CG the amplitudes are read through L2 (written by
 // other CTAs of the same launch).
@@ -950,7 +1009,7 @@ __device__ __forceinline__ uint32_t encode_frame_warp_ip(float2 *frame, uint32_t
     const float inv_step = REL ? 0.f : exp2i(-e), step = REL ? 0.f : exp2i(e);
     const uint32_t k = uint32_t(e);
     uint32_t *re = reinterpret_cast<uint32_t *>(frame);  // aliases frame: no __restrict__
-    uint32_t ro = 0, io = 0, wre = 0, wim = 0, tw = 0, mr = 0, mi = 0;
+    uint32_t ro = 0, io = 0, wre = 0, wim = 0, tw = 0, mr = 0, mi = 0, rr = 0, ri = 0;
     float err_sq = 0.f, norm_sq = 0.f;
     int bad = 0;
     for (uint32_t c0 = 0; c0 < g.C; c0 += 8) {
@@ -993,9 +1052,13 @@ __device__ __forceinline__ uint32_t encode_frame_warp_ip(float2 *frame, uint32_t
                 if (lane == 0) {
                     if (tr == 2) reinterpret_cast<uint32_t *>(side + kSideMixRe)[mr] = sr;
                     if (ti == 2) reinterpret_cast<uint32_t *>(side + kSideMixIm)[mi] = si;
+                    if (tr == 3) reinterpret_cast<uint16_t *>(side + kSideRunRe)[rr] = uint16_t(sign_run_record(sr));
+                    if (ti == 3) reinterpret_cast<uint16_t *>(side + kSideRunIm)[ri] = uint16_t(sign_run_record(si));
                 }
                 mr += tr == 2;
                 mi += ti == 2;
+                rr += tr == 3;
+                ri += ti == 3;
             }
             const int32_t pr = __shfl_up_sync(kFull, q[0], 1);
             const int32_t pi = __shfl_up_sync(kFull, q[1], 1);
@@ -1043,20 +1106,20 @@ __device__ __forceinline__ uint32_t encode_frame_warp_ip(float2 *frame, uint32_t
     }
     if (lane == 0 && part_item) *part_item = make_float2(err_sq, norm_sq);
     words = ro | (io << 16);
-    mixed = mr | (mi << 16);
+    mixed = mr | (mi << 8) | (rr << 16) | (ri << 24);
     if (ro + io == 0) return 0u;
     uint32_t len = frame_len(g, ro + io);
-    if constexpr (REL) len += uint32_t(pad16d((2u * g.C + 3u) / 4u) + pad16d(4u * (mr + mi)));
+    if constexpr (REL) len += uint32_t(pad16d((2u * g.C + 3u) / 4u)) + sign_section_bytes(mixed);
     return len;
 }
 
 // Second pass of the in-place encoder: frame f's widths (and for REL its sign
-// chunk types and mixed sign words) from side, its Re-plane words (re, 16-byte
+// chunk types, stored sign words and run records) from side, its Re-plane words (re, 16-byte
 // aligned) and Im-plane words (im) are copied to byte offset frame_off of the
 // block's slot and padded to 16 bytes; lane 0 writes the frame's offset-table
 // entry and, for the block's last frame, the header, the block's table slot
-// and the stage totals. words = Re words | Im words << 16, mixed = Re | Im
-// mixed sign chunks << 16. A slot too small (only after a failed reservation
+// and the stage totals. words = Re words | Im words << 16, mixed = the sign-section
+// counts packed as by the first pass. A slot too small (only after a failed reservation
 // or a caller's short buffer) sets the block's overflow flag instead.
 template <bool REL = false>
 __device__ __forceinline__ void copy_frame_warp(const uint32_t *__restrict__ re, const uint32_t *__restrict__ im,
@@ -1076,15 +1139,36 @@ __device__ __forceinline__ void copy_frame_warp(const uint32_t *__restrict__ re,
         if (8u * lane < padw) *reinterpret_cast<uint2 *>(dst + 8u * lane) = wb;
         uint32_t head = padw;
         if constexpr (REL) {
-            // sign chunk types, then the mixed sign words (Re chunks first), each part padded to 16 bytes
-            const uint32_t tb = uint32_t(pad16d((2u * g.C + 3u) / 4u)), mre = mixed & 0xffffu, mim = mixed >> 16;
-            const uint32_t nmw = uint32_t(pad16d(4u * (mre + mim))) / 4u;
+            // sign chunk types, padded to 16 bytes; then the sign section: the stored words (Re chunks first),
+            // then the run records (Re chunks first), padded to 16 bytes as a whole
+            const uint32_t tb = uint32_t(pad16d((2u * g.C + 3u) / 4u));
+            const uint32_t mre = mixed & 0xffu, mim = (mixed >> 8) & 0xffu;
+            const uint32_t rre = (mixed >> 16) & 0xffu, rim = mixed >> 24;
+            const uint32_t nmw = sign_section_bytes(mixed) / 4u;
             uint32_t *tdst = reinterpret_cast<uint32_t *>(dst + padw);
             if (4u * lane < tb) tdst[lane] = 16u * lane < 2u * g.C ? __ldcg(reinterpret_cast<const uint32_t *>(side + kSideTypes) + lane) : 0u;
             uint32_t *mdst = reinterpret_cast<uint32_t *>(dst + padw + tb);
-            for (uint32_t i = lane; i < nmw; i += 32)
-                mdst[i] = i < mre ? __ldcg(reinterpret_cast<const uint32_t *>(side + kSideMixRe) + i)
-                                  : (i < mre + mim ? __ldcg(reinterpret_cast<const uint32_t *>(side + kSideMixIm) + (i - mre)) : 0u);
+            const uint16_t *rrec = reinterpret_cast<const uint16_t *>(side + kSideRunRe);
+            const uint16_t *irec = reinterpret_cast<const uint16_t *>(side + kSideRunIm);
+            for (uint32_t i = lane; i < nmw; i += 32) {
+                uint32_t v;
+                if (i < mre) {
+                    v = __ldcg(reinterpret_cast<const uint32_t *>(side + kSideMixRe) + i);
+                } else if (i < mre + mim) {
+                    v = __ldcg(reinterpret_cast<const uint32_t *>(side + kSideMixIm) + (i - mre));
+                } else {
+                    // run records 2j and 2j + 1 of the section's record list (Re then Im), zero past the end
+                    const uint32_t j = 2u * (i - mre - mim);
+                    uint32_t h[2];
+#pragma unroll
+                    for (uint32_t q = 0; q < 2; ++q) {
+                        const uint32_t r = j + q;
+                        h[q] = r < rre ? uint32_t(__ldcg(rrec + r)) : (r - rre < rim ? uint32_t(__ldcg(irec + (r - rre))) : 0u);
+                    }
+                    v = h[0] | (h[1] << 16);
+                }
+                mdst[i] = v;
+            }
             head = padw + tb + 4u * nmw;
         }
         // payload word i: Re word i (i < nre), Im word i - nre (i - nre < nim), else zero padding; written

@@ -1,5 +1,6 @@
 """GPU relative-bound codec (QSZR: Sec. 4.3, Eq. 1-2, Algorithm 2) vs the scalar oracle, through the C ABI:
-byte-identical streams and exact decodes for blocks of several sizes and value mixes, the point-wise relative
+byte-identical streams and exact decodes for blocks of several sizes and value mixes (run-coded sign chunks
+included), the point-wise relative
 bound, range / capacity / corruption errors, and the stage loop (stream engine, persistent kernel, batch)
 storing QSZR blocks that re-encode exactly."""
 import numpy as np
@@ -51,10 +52,20 @@ def block(kind, m, seed):
         return (rng.integers(-2000, 2000, n) * np.float32(2.0 ** -149)).astype(np.float32)
     if kind == "zero":
         return np.zeros(n, np.float32)
+    if kind == "runs":  # every 32-value chunk of each plane changes sign 0..5 times: run-coded and stored words
+        x = (rng.random(n) * 0.5 + 0.25).astype(np.float32)
+        for plane in range(2):
+            for ch in range(n // 64):
+                nb = int(rng.integers(0, 6))
+                s = np.ones(32, np.float32) * (1 if rng.random() < 0.5 else -1)
+                for p in np.sort(rng.choice(np.arange(1, 32), nb, replace=False)):
+                    s[p:] *= -1
+                x[plane + 64 * ch: plane + 64 * (ch + 1): 2] *= s
+        return x
     raise ValueError(kind)
 
 
-@pytest.mark.parametrize("kind", ["gauss", "binades", "negative", "alternating", "subnormal", "zero"])
+@pytest.mark.parametrize("kind", ["gauss", "binades", "negative", "alternating", "subnormal", "zero", "runs"])
 @pytest.mark.parametrize("m", [5, 8, 12, 14])
 @pytest.mark.parametrize("rel", [1e-3, 1e-2])
 def test_bit_exact_vs_oracle(kind, m, rel):

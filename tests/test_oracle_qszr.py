@@ -1,7 +1,8 @@
 """Pins of the oracle's relative-bound codec (Sec. 4.3, Eq. 1-2, Algorithm 2), all on the CPU: the shift
 against its defining inequality, the point-wise relative bound on every normal value (binade edges
-included), exact zeros and signs, the sign-bitmap pre-scan (all-0 / all-1 chunks stored as a type only),
-streams assembled by hand from the format description, idempotence and corrupt-stream rejection."""
+included), exact zeros and signs, the sign-bitmap pre-scan (all-0 / all-1 chunks stored as a type only), the
+lossless run coding of the remaining sign words, streams assembled by hand from the format description,
+idempotence and corrupt-stream rejection."""
 import math
 import struct
 from fractions import Fraction
@@ -96,11 +97,13 @@ def hand_stream(m, k, frames):
     return hdr + pad(struct.pack("<%dI" % (nframes + 1), *offs)) + b"".join(frames)
 
 
-def unit_frame(widths, types, mixed, planes):
-    """widths: 2 bytes (C = 1); types: 2-bit codes of the Re and Im chunk; planes: u32 words."""
+def unit_frame(widths, types, mixed, planes, runs=()):
+    """widths: 2 bytes (C = 1); types: 2-bit codes of the Re and Im chunk; mixed: stored sign words (u32);
+    runs: run records (u16), after the stored words in the same 16-byte padded section; planes: u32 words."""
     pad = lambda b: b + bytes((-len(b)) % 16)
     t = bytes([types[0] | (types[1] << 2)])
-    return (pad(bytes(widths)) + pad(t) + pad(struct.pack("<%dI" % len(mixed), *mixed)) +
+    return (pad(bytes(widths)) + pad(t) +
+            pad(struct.pack("<%dI" % len(mixed), *mixed) + struct.pack("<%dH" % len(runs), *runs)) +
             pad(struct.pack("<%dI" % len(planes), *planes)))
 
 
@@ -127,6 +130,57 @@ def test_hand_assembled_streams():
     # all-zero block: every frame has length 0
     z = np.zeros(64, np.float32)
     assert oracle.qszr_encode(z, m, rel) == hand_stream(m, k, [b""])
+
+
+def test_hand_assembled_run_coded_signs():
+    # the lossless step on the sign words left by the pre-scan: a chunk whose signs change 1 to 3 times
+    # between neighbours is stored as a 2-byte run record (bit 15 = sign of value 0, 5-bit boundaries)
+    m, rel, k = 5, 1e-3, 14
+    re_planes = [1 if 10 <= b <= 16 else 0 for b in range(17)]  # every |Re| = 1.0 (see above)
+    im_planes = [1 if b == 17 else 0 for b in range(18)]        # every |Im| = 2.0
+    x = np.zeros(64, np.float32)
+    # Re: values 0..9 negative -> word 0x000003FF, one boundary at 10: record 0x8000 | 10
+    x[0::2] = np.where(np.arange(32) < 10, -1.0, 1.0)
+    # Im: values 4..7 and 20..31 negative -> boundaries 4, 8, 20: record 4 | 8 << 5 | 20 << 10 = 0x5104
+    im_neg = ((np.arange(32) >= 4) & (np.arange(32) < 8)) | (np.arange(32) >= 20)
+    x[1::2] = np.where(im_neg, -2.0, 2.0)
+    want = hand_stream(m, k, [unit_frame([17, 18], [3, 3], [], re_planes + im_planes, runs=[0x800A, 0x5104])])
+    assert oracle.qszr_encode(x, m, rel) == want
+    assert np.array_equal(oracle.qszr_decode(want, m), x)
+    # Re alternating (31 boundaries): stored word first, then Im's run record, in one padded section
+    x[0::2] = np.where(np.arange(32) % 2 == 1, -1.0, 1.0)
+    want = hand_stream(m, k, [unit_frame([17, 18], [2, 3], [0xAAAAAAAA], re_planes + im_planes, runs=[0x5104])])
+    assert oracle.qszr_encode(x, m, rel) == want
+    assert np.array_equal(oracle.qszr_decode(want, m), x)
+    # four boundaries are not run-coded: Im negative at 4..7 and 20..23 keeps its raw word
+    im4 = ((np.arange(32) >= 4) & (np.arange(32) < 8)) | ((np.arange(32) >= 20) & (np.arange(32) < 24))
+    x[1::2] = np.where(im4, -2.0, 2.0)
+    want = hand_stream(m, k, [unit_frame([17, 18], [2, 2], [0xAAAAAAAA, 0x00F000F0], re_planes + im_planes)])
+    assert oracle.qszr_encode(x, m, rel) == want
+
+
+@pytest.mark.parametrize("nb", [1, 2, 3, 4, 7])
+def test_run_coding_sizes_and_round_trip(nb):
+    # blocks whose chunks all have nb sign boundaries: 2 bytes per chunk for nb <= 3, 4 bytes otherwise,
+    # against the same magnitudes with constant signs; the signs come back exactly
+    rng = np.random.default_rng(40 + nb)
+    m = 12
+    mag = (rng.random(2 << m) * 0.5 + 0.25).astype(np.float32)
+    sign = np.ones(2 << m, np.float32)
+    for plane in range(2):
+        for ch in range((1 << m) // 32):
+            cuts = np.sort(rng.choice(np.arange(1, 32), nb, replace=False))
+            s = np.ones(32, np.float32)
+            for p in cuts:
+                s[p:] *= -1
+            sign[plane + 2 * 32 * ch: plane + 2 * 32 * (ch + 1): 2] = s
+    x = mag * sign
+    base = len(oracle.qszr_encode(mag, m, 1e-3))
+    got = oracle.qszr_encode(x, m, 1e-3)
+    per_chunk = 2 if nb <= 3 else 4
+    assert len(got) == base + per_chunk * 256  # 2C = 256 chunks per 4096-amplitude frame, one frame
+    y = oracle.qszr_decode(got, m)
+    assert np.array_equal(np.signbit(y), np.signbit(x))
 
 
 def test_sign_chunks_elided():
@@ -172,10 +226,19 @@ def test_corrupt_streams_rejected():
     good = bytearray(oracle.qszr_encode(x, m, rel))
     frame = 48  # data_start for one frame
     bad_type = bytearray(good)
-    bad_type[frame + 16] = 3  # sign type 3 is not defined
+    bad_type[frame + 16] = 3  # a run-coded chunk, but the frame holds no run record: lengths disagree
     bad_magic = bytearray(good)
     bad_magic[0] ^= 1
-    for s in (bytes(bad_type), bytes(bad_magic), bytes(good[:-16])):
+    # run records no encoder writes: no boundary, and boundaries out of order
+    x[0::2] = np.where(np.arange(32) < 10, -1.0, 1.0)
+    runs = bytearray(oracle.qszr_encode(x, m, rel))
+    rec_at = frame + 32  # widths (16) + types (16), then the sign section
+    assert runs[rec_at:rec_at + 2] == bytes([0x0A, 0x80])
+    no_boundary = bytearray(runs)
+    no_boundary[rec_at:rec_at + 2] = bytes([0x00, 0x80])
+    out_of_order = bytearray(runs)
+    out_of_order[rec_at:rec_at + 2] = (10 | (4 << 5) | 0x8000).to_bytes(2, "little")
+    for s in (bytes(bad_type), bytes(bad_magic), bytes(good[:-16]), bytes(no_boundary), bytes(out_of_order)):
         with pytest.raises(oracle.OracleError) as ei:
             oracle.qszr_decode(s, m)
         assert ei.value.code == oracle.E_CORRUPT
