@@ -136,6 +136,24 @@ int qsim_plan_stages(uint32_t n, const qsim_gate *gates, size_t ngates, const qs
  * a mask whose bit j is set when global qubit m + j is an inner index. */
 int qsim_plan_info(const qsim_plan *plan, size_t *nstages, uint32_t *stage_inner_masks);
 
+/*
+ * Group sharding over 2^log2_ranks ranks (Sec. 4.2: the SV groups of a stage
+ * are independent, so they can run on different GPUs; Sec. 5.8 measures the
+ * paper's multi-GPU runs). For every stage s the call picks log2_ranks rank
+ * qubits, global qubits (>= m) outside the stage's inner set, and writes them
+ * to rank_qubits[s * log2_ranks + j] (host, nstages * log2_ranks entries).
+ * Block b (index bits m.. of its amplitudes) belongs during stage s to the
+ * rank whose bit j is the block's bit at rank qubit j, so every SV group of
+ * the stage lies on one rank. A rank qubit keeps its slot j until a stage
+ * takes it as an inner qubit; it is then replaced by the free global qubit
+ * whose next use as an inner qubit is farthest ahead, so blocks change ranks
+ * only at the stage boundaries where a slot changes.
+ * Errors: INVALID (null pointer, log2_ranks > 16, a stage that leaves fewer
+ * than log2_ranks global qubits outside its inner set). log2_ranks = 0 writes
+ * nothing.
+ */
+int qsim_plan_shards(const qsim_plan *plan, uint32_t log2_ranks, uint32_t *rank_qubits);
+
 /* Gates [*first, *first + *count) of the input form stage `stage`. */
 int qsim_plan_stage_gates(const qsim_plan *plan, size_t stage, size_t *first, size_t *count);
 
@@ -209,6 +227,56 @@ int qsim_run(const qsim_plan *plan, void *cuda_stream, qsim_state **out, qsim_st
 int qsim_state_stage_stats(const qsim_state *st, size_t stage, uint64_t *store_bytes,
                            uint64_t *reserved_bytes, double *err_sq);
 
+/* ---- sharded runs: one rank's SV groups on this GPU ---------------------------
+ * Sec. 4.2's groups are independent, so a run can be spread over several GPUs
+ * (the paper's multi-GPU runs, Sec. 5.8): rank k holds the blocks whose bits at
+ * the stage's rank qubits (qsim_plan_shards) spell k and runs the SV groups they
+ * form. Between stages whose rank qubits differ, each rank exports the blocks
+ * that change owner (their compressed streams, packed into a caller's device
+ * buffer) and imports those it receives; the transfer itself (NCCL, or any
+ * copy) is the caller's. Every call is on the current device; work is ordered
+ * on the stream given to qsim_shard_begin, and the export, import and finish
+ * calls synchronise it. The handle is the library's until qsim_shard_free.
+ */
+typedef struct qsim_shard_run qsim_shard_run;
+
+/* Begin rank `rank` of 2^log2_ranks: the compressed store's tiers, the
+ * initial store (Sec. 4.2), and the rank's SV groups of every stage. plan must
+ * be in streams mode; rank_qubits: host, nstages * log2_ranks entries as from
+ * qsim_plan_shards (copied). The rank starts with the blocks it owns under
+ * stage 0's rank qubits. Errors: INVALID (null pointer, persistent mode, rank
+ * out of range, a rank qubit that is inner or not global), NOMEM, CUDA. */
+int qsim_shard_begin(const qsim_plan *plan, const uint32_t *rank_qubits, uint32_t log2_ranks, uint32_t rank,
+                     void *cuda_stream, qsim_shard_run **out);
+
+/* Run stage `stage` (stages in order, from 0) over this rank's SV groups. The
+ * blocks on the rank must be exactly those its rank qubits give it for this
+ * stage (INVALID otherwise). */
+int qsim_shard_stage(qsim_shard_run *run, size_t stage);
+
+/* Stream bytes of `count` blocks on this rank (host lists; each a multiple of
+ * 16), as they are before the next stage. INVALID for a block not on the rank. */
+int qsim_shard_block_bytes(qsim_shard_run *run, const uint64_t *blocks, size_t count, uint64_t *bytes);
+
+/* Pack the streams of `count` blocks on this rank, in list order, into
+ * d_packed (device, 16-byte aligned, cap bytes; block i at the sum of the
+ * sizes before it) and remove them from the rank. CAPACITY when cap is too
+ * small (nothing removed). */
+int qsim_shard_export(qsim_shard_run *run, const uint64_t *blocks, size_t count, void *d_packed, size_t cap);
+
+/* Place `count` received blocks on this rank: block ids and stream bytes
+ * (host), streams packed back to back in d_packed (device, 16-byte aligned),
+ * copied into the rank's current tier (device, then pinned host). Errors:
+ * INVALID (a block already on the rank), CORRUPT (a size not a multiple of
+ * 16), NOMEM (tiers full, reported by the device), CUDA. */
+int qsim_shard_import(qsim_shard_run *run, const uint64_t *blocks, const uint64_t *bytes, size_t count,
+                      const void *d_packed);
+
+/* After the last stage: the state handle of the blocks now on this rank (the
+ * others read as corrupt blocks) and the rank's statistics. */
+int qsim_shard_finish(qsim_shard_run *run, qsim_state **out, qsim_stats *stats);
+void qsim_shard_free(qsim_shard_run *run);
+
 /* ---- readout -------------------------------------------------------------- */
 
 /* Read the final state (Sec. 4.2's loop leaves it compressed, block by
@@ -231,7 +299,8 @@ int qsim_state_norm(const qsim_state *st, double *norm_sq);
 int qsim_state_decompress(const qsim_state *st, float *d_out, void *cuda_stream);
 
 /* Copy block `block`'s compressed stream to host_out (cap bytes); *bytes gets
- * its size (also when cap is too small: CAPACITY). */
+ * its size (also when cap is too small: CAPACITY); 0 bytes for a block the
+ * state does not hold (the other ranks' blocks after a sharded run). */
 int qsim_state_block_stream(const qsim_state *st, uint64_t block, void *host_out, size_t cap,
                             size_t *bytes);
 

@@ -389,6 +389,26 @@ static void order_complement(OpDev &od, uint32_t T, bool mma) {
     for (; i < 16; ++i) od.comp[i] = 0;
 }
 
+// Dense op `op` (width k <= kw, all of its working bits tile bits of pass ps) as a width-kw op: matrix bits
+// k..kw-1 are the lowest tile bits the op does not touch, and the matrix is I (x) U (the identity on those
+// bits): U'[r][c] = U[r mod 2^k][c mod 2^k] when r and c agree above bit k, else 0.
+static Op widen_dense(const Op &op, const Pass &ps, uint32_t kw) {
+    Op w = op;
+    const uint32_t k = op.k, D = 1u << k, DW = 1u << kw;
+    for (uint32_t t = 0, j = k; j < kw && t < ps.T; ++t) {
+        const uint32_t b = ps.tile_pos[t];
+        bool used = false;
+        for (uint32_t i = 0; i < j; ++i) used |= w.wq[i] == b;
+        if (!used) w.wq[j++] = b;
+    }
+    w.k = kw;
+    w.u.assign(size_t(DW) * DW, cd(0, 0));
+    for (uint32_t r = 0; r < DW; ++r)
+        for (uint32_t c = 0; c < DW; ++c)
+            if ((r >> k) == (c >> k)) w.u[size_t(r) * DW + c] = op.u[size_t(r & (D - 1)) * D + (c & (D - 1))];
+    return w;
+}
+
 static int upload_plan(const qsim_plan *p, PlanDev **out) {
     int dev;
     CUDA_TRY(cudaGetDevice(&dev));
@@ -514,7 +534,18 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
             P.op_count = ps.ops.size();
             P.mat_elems = 0;
             for (uint32_t oi : ps.ops) {
-                const Op &op = st.ops[oi];
+                // in passes whose width-5 dense ops run on tcgen05, dense ops of width 3 and 4 run there too,
+                // as width-5 ops: the op's matrix times the identity on the lowest tile bits it does not touch
+                // (the same operator, so the same result up to the FP32 accumulation order)
+                Op wide;
+                const Op *opp = &st.ops[oi];
+                if (opp->type == OP_DENSE && (opp->k == 3 || opp->k == 4) && ps.T == 12 && p->cfg.tcgen05 &&
+                    p->cfg.mode == QSIM_MODE_STREAMS &&
+                    (p->cfg.prec == QSIM_PREC_TF32 || p->cfg.prec == QSIM_PREC_BF16X3)) {
+                    wide = widen_dense(*opp, ps, 5);
+                    opp = &wide;
+                }
+                const Op &op = *opp;
                 OpDev od{};
                 od.type = op.type;
                 od.k = op.k;
@@ -1520,26 +1551,51 @@ static int finish_run(RunCtx &R, int dev, double ms, Profiler *prof, qsim_stats 
     return QSIM_OK;
 }
 
-static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsim_stats *stats) {
-    NvtxRange run_range("qsim_run n=%u", p->n);
+// A streams-mode run between its stages: the compressed store (RunCtx), the per-stream work buffers and the
+// run's events. run_plan drives one through every stage; a sharded run (qsim_shard_*) drives one stage at a
+// time over the SV groups its rank holds and moves blocks between the stages.
+struct StreamsRun {
+    RunCtx RC;
+    DeviceCtx *dctx = nullptr;
+    int dev = 0;
+    cudaStream_t main = nullptr;
+    std::vector<StreamWork> sw;
+    cudaEvent_t ev_start = nullptr, ev_stop = nullptr, ev_fork = nullptr;
+    Profiler prof;
+    int *status = nullptr;
+    uint64_t batch_amps = 0;
+    uint64_t groups_run = 0;  // SV groups processed (all stages)
+    ~StreamsRun() {
+        for (auto &x : sw) {
+            if (x.s) cudaStreamDestroy(x.s);
+            if (x.done) cudaEventDestroy(x.done);
+        }
+        if (ev_start) cudaEventDestroy(ev_start);
+        if (ev_stop) cudaEventDestroy(ev_stop);
+        if (ev_fork) cudaEventDestroy(ev_fork);
+    }
+};
+
+// Validation, the compressed store's tiers, the per-stream buffers and the initial store (Sec. 4.2); the start
+// event is recorded on `main` before the initial store.
+static int streams_begin(StreamsRun &S, const qsim_plan *p, cudaStream_t main) {
     const qsim_config &cfg = p->cfg;
-    int dev;
-    CUDA_TRY(cudaGetDevice(&dev));
-    DeviceCtx &dctx = device_ctx(dev);
+    CUDA_TRY(cudaGetDevice(&S.dev));
+    S.dctx = &device_ctx(S.dev);
+    DeviceCtx &dctx = *S.dctx;
     {
         std::lock_guard<std::mutex> lk(dctx.mu);
         int rc = ensure_device_ctx(dctx);
         if (rc) return rc;
     }
-    RunCtx RC;
+    S.main = main;
+    RunCtx &RC = S.RC;
     int rc = prepare_run(RC, p, dctx);
     if (rc) return rc;
     PlanDev *pd = RC.pd;
-    const bool persistent = RC.persistent, raw = RC.raw, predict = RC.predict, collect = RC.collect;
+    const bool persistent = RC.persistent, raw = RC.raw;
     const uint32_t m = RC.m;
-    const uint64_t nblocks = RC.nblocks, nframes = RC.nframes, worst = RC.worst;
-    const int e = RC.e;
-    const size_t nst = RC.nst;
+    const uint64_t nframes = RC.nframes;
 
     // ---- pool sizing: device arenas first, pinned host for the rest ----
     size_t free_b = 0, total_b = 0;
@@ -1549,18 +1605,15 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
     for (const StageDev &sd : pd->stages) maxW = std::max(maxW, sd.W);
     const uint32_t nstreams = persistent ? 1 : cfg.streams;
     const uint64_t batch_amps = std::max<uint64_t>(1ull << maxW, 1ull << 22);
+    S.batch_amps = batch_amps;
     const uint64_t work_bytes = nstreams * batch_amps * 8 * 2;
     const uint64_t dev_budget = free_b > work_bytes ? uint64_t(0.85 * double(free_b - work_bytes)) : 0;
     // the pinned-host level holds at most 30 % of the host's memory per stage parity
     if ((rc = alloc_run(RC, dev_budget, uint64_t(0.3 * double(host_phys_bytes())), main))) return rc;
-    auto arena_dev = [&](int parity) { return RC.arena_dev(parity); };
-    auto arena_host = [&](int parity) { return RC.arena_host(parity); };
-    BlockSlot *const tables_p = RC.tables.p;
-    StageAccum *const accs_p = RC.accs.p;
-    uint64_t *const bumps_p = RC.bumps.p;
 
     // ---- per-stream work buffers ----
-    std::vector<StreamWork> sw(nstreams);
+    std::vector<StreamWork> &sw = S.sw;
+    sw.resize(nstreams);
     uint64_t max_batch_blocks = 0;
     for (const StageDev &sd : pd->stages) {
         uint64_t gpb = std::min<uint64_t>(std::max<uint64_t>(1, batch_amps >> sd.W), 32768);
@@ -1569,14 +1622,6 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
     }
     max_batch_blocks = std::max<uint64_t>(max_batch_blocks, 2);
     if (persistent) max_batch_blocks = 2;  // the stream buffers only serve the initial store
-    auto destroy_streams = [&]() {
-        for (auto &x : sw) {
-            if (x.s) cudaStreamDestroy(x.s);
-            if (x.done) cudaEventDestroy(x.done);
-            x.s = nullptr;
-            x.done = nullptr;
-        }
-    };
     for (uint32_t i = 0; i < nstreams; ++i) {
         StreamWork &w = sw[i];
         CUDA_TRY(cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking));
@@ -1591,46 +1636,57 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             ((!persistent || RC.rel) && (rc = w.fwords.alloc(max_batch_blocks * nframes))) ||
             (RC.rel && (rc = w.fmixed.alloc(max_batch_blocks * nframes))) ||
             (rc = w.flen.alloc(max_batch_blocks * nframes)) || (rc = w.foff.alloc(max_batch_blocks * nframes)) ||
-            (rc = w.lb_ctr.alloc(8))) {
-            destroy_streams();
+            (rc = w.lb_ctr.alloc(16)))
             return rc;
-        }
         CUDA_TRY(cudaMemsetAsync(w.lb_state.p, 0, max_batch_blocks * nframes * sizeof(uint64_t), main));
-        CUDA_TRY(cudaMemsetAsync(w.lb_ctr.p, 0, 8 * sizeof(uint32_t), main));
+        CUDA_TRY(cudaMemsetAsync(w.lb_ctr.p, 0, 16 * sizeof(uint32_t), main));  // [8], [9]: gate-pass tile counter
         CUDA_TRY(cudaMemsetAsync(w.sizes.p, 0, max_batch_blocks * sizeof(uint64_t), main));
     }
-    cudaEvent_t ev_start, ev_stop, ev_fork;
-    CUDA_TRY(cudaEventCreate(&ev_start));
-    CUDA_TRY(cudaEventCreate(&ev_stop));
-    CUDA_TRY(cudaEventCreateWithFlags(&ev_fork, cudaEventDisableTiming));
-    int *status = dctx.status;
-    Profiler prof;
-    prof.on = g_profile.load() != 0 && !(persistent && cfg.graph);
-    CUDA_TRY(cudaEventRecord(ev_start, main));
+    CUDA_TRY(cudaEventCreate(&S.ev_start));
+    CUDA_TRY(cudaEventCreate(&S.ev_stop));
+    CUDA_TRY(cudaEventCreateWithFlags(&S.ev_fork, cudaEventDisableTiming));
+    S.status = dctx.status;
+    S.prof.on = g_profile.load() != 0 && !(persistent && cfg.graph);
+    CUDA_TRY(cudaEventRecord(S.ev_start, main));
 
     // ---- initial store ----
     {
         StreamWork &w = sw[0];
-        CUDA_TRY(cudaEventRecord(ev_fork, main));
-        CUDA_TRY(cudaStreamWaitEvent(w.s, ev_fork, 0));
-        if ((rc = init_store(RC, w, status))) {
-            destroy_streams();
-            return rc;
-        }
+        CUDA_TRY(cudaEventRecord(S.ev_fork, main));
+        CUDA_TRY(cudaStreamWaitEvent(w.s, S.ev_fork, 0));
+        if ((rc = init_store(RC, w, S.status))) return rc;
         CUDA_TRY(cudaEventRecord(w.done, w.s));
         CUDA_TRY(cudaStreamWaitEvent(main, w.done, 0));
     }
+    return QSIM_OK;
+}
 
-    // ---- stage loop ----
-    if (persistent) {
-        std::vector<RunCtx *> one{&RC};
-        rc = run_persistent(one, false, main, status, prof, dctx, 1ull << 25);
-        if (rc) {
-            destroy_streams();
-            return rc;
-        }
-    }
-    for (size_t si = 0; si < (persistent ? 0 : nst); ++si) {
+// Stage si over `ngroups` SV groups: ids_stage holds their block ids (group-major, G per group), gb_stage their
+// outer bits (device arrays). Work runs on the run's streams, joined back to S.main.
+static int streams_stage(StreamsRun &S, size_t si, const uint32_t *ids_stage, const uint64_t *gb_stage,
+                         uint64_t ngroups) {
+    RunCtx &RC = S.RC;
+    const qsim_plan *p = RC.p;
+    const qsim_config &cfg = p->cfg;
+    PlanDev *pd = RC.pd;
+    DeviceCtx &dctx = *S.dctx;
+    const bool raw = RC.raw, predict = RC.predict, collect = RC.collect;
+    const uint32_t m = RC.m;
+    const uint64_t nblocks = RC.nblocks, worst = RC.worst;
+    const int e = RC.e;
+    const uint32_t nstreams = uint32_t(S.sw.size());
+    std::vector<StreamWork> &sw = S.sw;
+    const uint64_t batch_amps = S.batch_amps;
+    cudaStream_t main = S.main;
+    cudaEvent_t ev_fork = S.ev_fork;
+    Profiler &prof = S.prof;
+    int *status = S.status;
+    auto arena_dev = [&](int parity) { return RC.arena_dev(parity); };
+    auto arena_host = [&](int parity) { return RC.arena_host(parity); };
+    BlockSlot *const tables_p = RC.tables.p;
+    StageAccum *const accs_p = RC.accs.p;
+    uint64_t *const bumps_p = RC.bumps.p;
+    {
         NvtxRange stage_range("stage %zu", si);
         const StageDev &sd = pd->stages[si];
         const int in_par = si & 1, out_par = (si + 1) & 1;
@@ -1640,10 +1696,9 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
         CUDA_TRY(cudaEventRecord(ev_fork, main));
         for (auto &w : sw) CUDA_TRY(cudaStreamWaitEvent(w.s, ev_fork, 0));
         const uint64_t gpb = std::min<uint64_t>(std::min<uint64_t>(std::max<uint64_t>(1, batch_amps >> sd.W), 32768),
-                                                sd.ngroups);
-        const uint64_t nbatches = (sd.ngroups + gpb - 1) / gpb;
-        const uint32_t *ids_stage = pd->ids.p + pd->ids_off[si];
-        const uint64_t *gb_stage = pd->gbase.p + pd->gbase_off[si];
+                                                std::max<uint64_t>(1, ngroups));
+        const uint64_t nbatches = (ngroups + gpb - 1) / gpb;
+        S.groups_run += ngroups;
         StageAccum *acc = accs_p + si;
         StageFeatures sf{};
         {
@@ -1667,7 +1722,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             NvtxRange group_range("groups %llu..", (unsigned long long)(b * gpb));
             StreamWork &w = sw[b % nstreams];
             const uint64_t g0 = b * gpb;
-            const uint32_t ng = uint32_t(std::min<uint64_t>(gpb, sd.ngroups - g0));
+            const uint32_t ng = uint32_t(std::min<uint64_t>(gpb, ngroups - g0));
             const uint32_t nb = ng * sd.G;
             const uint32_t *ids = ids_stage + g0 * sd.G;
             if (raw) {
@@ -1699,7 +1754,7 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             for (uint32_t pi = 0; pi < sd.npasses; ++pi) {
                 prof.begin(P_PASS, w.s);
                 launch_pass(w.wv.p, sd.W, ng, &sd.passes_host[pi], pd->blob.p, pd->mats.p, pd->bfr.p, gb_stage + g0,
-                            cfg.prec, w.s, status);
+                            cfg.prec, w.s, w.lb_ctr.p + 8, status);
                 prof.end(w.s);
             }
             if (raw) {
@@ -1749,18 +1804,38 @@ static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsi
             CUDA_TRY(cudaEventRecord(w.done, w.s));
             CUDA_TRY(cudaStreamWaitEvent(main, w.done, 0));
         }
-    }
-    CUDA_TRY(cudaEventRecord(ev_stop, main));
-    CUDA_TRY(cudaEventSynchronize(ev_stop));
+        }
+    return QSIM_OK;
+}
+
+// The run's end: stop event, status, and the state handle with the statistics.
+static int streams_finish(StreamsRun &S, qsim_state **out, qsim_stats *stats) {
+    CUDA_TRY(cudaEventRecord(S.ev_stop, S.main));
+    CUDA_TRY(cudaEventSynchronize(S.ev_stop));
     float ms = 0;
-    CUDA_TRY(cudaEventElapsedTime(&ms, ev_start, ev_stop));
-    cudaEventDestroy(ev_start);
-    cudaEventDestroy(ev_stop);
-    cudaEventDestroy(ev_fork);
-    destroy_streams();
-    int st_code = read_status(status, main);
+    CUDA_TRY(cudaEventElapsedTime(&ms, S.ev_start, S.ev_stop));
+    int st_code = read_status(S.status, S.main);
     if (st_code) return set_error(st_code, "qsim_run: %s", status_text(st_code));
-    return finish_run(RC, dev, ms, &prof, stats, out);
+    return finish_run(S.RC, S.dev, ms, &S.prof, stats, out);
+}
+
+static int run_plan(const qsim_plan *p, cudaStream_t main, qsim_state **out, qsim_stats *stats) {
+    NvtxRange run_range("qsim_run n=%u", p->n);
+    StreamsRun S;
+    int rc = streams_begin(S, p, main);
+    if (rc) return rc;
+    PlanDev *pd = S.RC.pd;
+    if (S.RC.persistent) {
+        std::vector<RunCtx *> one{&S.RC};
+        if ((rc = run_persistent(one, false, main, S.status, S.prof, *S.dctx, 1ull << 25))) return rc;
+    } else {
+        for (size_t si = 0; si < S.RC.nst; ++si) {
+            const StageDev &sd = pd->stages[si];
+            if ((rc = streams_stage(S, si, pd->ids.p + pd->ids_off[si], pd->gbase.p + pd->gbase_off[si], sd.ngroups)))
+                return rc;
+        }
+    }
+    return streams_finish(S, out, stats);
 }
 
 // A batch of circuits: initial stores, then one persistent launch over every
@@ -1968,6 +2043,10 @@ int qsim_plan_info(const qsim_plan *plan, size_t *nstages, uint32_t *stage_inner
     return QSIM_OK;
 }
 
+int qsim_plan_shards(const qsim_plan *plan, uint32_t log2_ranks, uint32_t *rank_qubits) {
+    return plan_shards(plan, log2_ranks, rank_qubits);
+}
+
 int qsim_plan_stage_gates(const qsim_plan *plan, size_t stage, size_t *first, size_t *count) {
     if (!plan || !first || !count) return set_error(QSIM_E_INVALID, "null argument");
     if (stage >= plan->stages.size()) return set_error(QSIM_E_INVALID, "stage index out of range");
@@ -2035,6 +2114,282 @@ int qsim_run(const qsim_plan *plan, void *cuda_stream, qsim_state **out, qsim_st
         return set_error(QSIM_E_CUDA, "run failed");
     }
 }
+
+// ---------------------------------------------------------------------------
+// sharded runs: one rank's SV groups, stage by stage, blocks moved between stages by the caller
+// ---------------------------------------------------------------------------
+}  // extern "C"
+
+namespace qsim {
+
+// the streams of `count` blocks (table entries of `tab`) packed at byte offsets dst_off of dst, 16-byte words;
+// each copied entry is then cleared (the block has left this rank)
+__global__ void k_export_streams(BlockSlot *tab, const uint64_t *__restrict__ ids, const uint64_t *__restrict__ dst_off,
+                                 uint32_t count, uint8_t *__restrict__ dst) {
+    for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+        const BlockSlot sl = tab[ids[i]];
+        const uint4 *src = reinterpret_cast<const uint4 *>(sl.ptr);
+        uint4 *d = reinterpret_cast<uint4 *>(dst + dst_off[i]);
+        for (uint64_t k = threadIdx.x; k < sl.bytes / 16; k += blockDim.x) d[k] = src[k];
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            tab[ids[i]].ptr = nullptr;
+            tab[ids[i]].bytes = 0;
+        }
+    }
+}
+
+// received streams (at byte offsets src_off of src, sizes bytes[i]) placed in slots of the current arena
+// (device tier, then pinned host), their table entries set
+__global__ void k_import_streams(BlockSlot *tab, const uint64_t *__restrict__ ids, const uint64_t *__restrict__ src_off,
+                                 const uint64_t *__restrict__ bytes, uint32_t count, const uint8_t *__restrict__ src,
+                                 ArenaDev dev, ArenaDev host, int *status) {
+    __shared__ uint8_t *dst;
+    __shared__ uint32_t tier;
+    for (uint32_t i = blockIdx.x; i < count; i += gridDim.x) {
+        const uint64_t nb = bytes[i];
+        if (threadIdx.x == 0) {
+            const uint64_t sz = (nb + 255) & ~255ull;
+            uint64_t off = atomicAdd(reinterpret_cast<unsigned long long *>(dev.bump), sz);
+            dst = nullptr;
+            tier = 0;
+            if (off + sz <= dev.cap) {
+                dst = dev.base + off;
+            } else if (host.base) {
+                off = atomicAdd(reinterpret_cast<unsigned long long *>(host.bump), sz);
+                if (off + sz <= host.cap) {
+                    dst = host.base + off;
+                    tier = 1;
+                }
+            }
+            if (!dst) raise_status(status, QSIM_E_NOMEM);
+            tab[ids[i]].ptr = dst;
+            tab[ids[i]].bytes = dst ? nb : 0;
+            tab[ids[i]].tier = tier;
+        }
+        __syncthreads();
+        if (dst) {
+            const uint4 *s4 = reinterpret_cast<const uint4 *>(src + src_off[i]);
+            uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+            for (uint64_t k = threadIdx.x; k < nb / 16; k += blockDim.x) d4[k] = s4[k];
+        }
+        __syncthreads();
+    }
+}
+
+__global__ void k_clear_slots(BlockSlot *tab, const uint8_t *__restrict__ held, uint64_t nblocks) {
+    for (uint64_t b = blockIdx.x * uint64_t(blockDim.x) + threadIdx.x; b < nblocks; b += uint64_t(gridDim.x) * blockDim.x)
+        if (!held[b]) {
+            tab[b].ptr = nullptr;
+            tab[b].bytes = 0;
+        }
+}
+
+}  // namespace qsim
+
+struct qsim_shard_run {
+    qsim::StreamsRun S;
+    uint32_t r = 0, rank = 0;
+    std::vector<uint32_t> rq;         // nstages x r rank qubits
+    std::vector<uint8_t> held;        // blocks this rank holds now
+    qsim::DevBuf<uint32_t> ids;       // per stage: the rank's groups' block ids, group-major
+    qsim::DevBuf<uint64_t> gb;        // per stage: their outer bits
+    std::vector<size_t> ids_off, gb_off;
+    std::vector<uint64_t> ngroups;
+    size_t next = 0;                  // the next stage to run
+    qsim::DevBuf<uint64_t> xbuf;      // export/import lists
+    bool failed = false;
+};
+
+using namespace qsim;
+
+static uint32_t shard_owner(const qsim_shard_run *R, size_t stage, uint64_t block) {
+    const uint32_t m = R->S.RC.m;
+    uint32_t o = 0;
+    for (uint32_t j = 0; j < R->r; ++j) o |= uint32_t((block >> (R->rq[stage * R->r + j] - m)) & 1ull) << j;
+    return o;
+}
+
+extern "C" {
+
+int qsim_shard_begin(const qsim_plan *plan, const uint32_t *rank_qubits, uint32_t log2_ranks, uint32_t rank,
+                     void *cuda_stream, qsim_shard_run **out) {
+    if (!plan || !out || (log2_ranks && !rank_qubits)) return set_error(QSIM_E_INVALID, "null argument");
+    *out = nullptr;
+    if (plan->cfg.mode != QSIM_MODE_STREAMS) return set_error(QSIM_E_INVALID, "sharded runs use streams mode");
+    if (log2_ranks > 16 || rank >= (1u << log2_ranks)) return set_error(QSIM_E_INVALID, "rank out of range");
+    const size_t nst = plan->stages.size();
+    const uint32_t n = plan->n, m = plan->cfg.m;
+    for (size_t s = 0; s < nst; ++s)
+        for (uint32_t j = 0; j < log2_ranks; ++j) {
+            const uint32_t q = rank_qubits[s * log2_ranks + j];
+            const auto &in = plan->stages[s].inner;
+            if (q < m || q >= n || std::find(in.begin(), in.end(), q) != in.end())
+                return set_error(QSIM_E_INVALID, "stage %zu: rank qubit %u is not an outer qubit", s, q);
+            for (uint32_t k = 0; k < j; ++k)
+                if (rank_qubits[s * log2_ranks + k] == q)
+                    return set_error(QSIM_E_INVALID, "stage %zu: rank qubit %u repeated", s, q);
+        }
+    try {
+        std::unique_ptr<qsim_shard_run> R(new qsim_shard_run());
+        R->r = log2_ranks;
+        R->rank = rank;
+        R->rq.assign(rank_qubits, rank_qubits + nst * log2_ranks);
+        int rc = streams_begin(R->S, plan, static_cast<cudaStream_t>(cuda_stream));
+        if (rc) return rc;
+        const uint64_t nblocks = R->S.RC.nblocks;
+        R->held.assign(nblocks, 0);
+        if (nst)
+            for (uint64_t b = 0; b < nblocks; ++b) R->held[b] = shard_owner(R.get(), 0, b) == rank;
+        else
+            for (uint64_t b = 0; b < nblocks; ++b) R->held[b] = rank == 0;
+        // the rank's groups of every stage, in the plan's group order
+        PlanDev *pd = R->S.RC.pd;
+        std::vector<uint32_t> hid, sub_ids;
+        std::vector<uint64_t> hgb, sub_gb;
+        for (size_t s = 0; s < nst; ++s) {
+            const StageDev &sd = pd->stages[s];
+            hid.resize(size_t(sd.ngroups) * sd.G);
+            hgb.resize(sd.ngroups);
+            CUDA_TRY(cudaMemcpy(hid.data(), pd->ids.p + pd->ids_off[s], hid.size() * 4, cudaMemcpyDeviceToHost));
+            CUDA_TRY(cudaMemcpy(hgb.data(), pd->gbase.p + pd->gbase_off[s], hgb.size() * 8, cudaMemcpyDeviceToHost));
+            R->ids_off.push_back(sub_ids.size());
+            R->gb_off.push_back(sub_gb.size());
+            uint64_t ng = 0;
+            for (uint32_t g = 0; g < sd.ngroups; ++g) {
+                if (shard_owner(R.get(), s, hid[size_t(g) * sd.G]) != rank) continue;
+                sub_ids.insert(sub_ids.end(), hid.begin() + size_t(g) * sd.G, hid.begin() + size_t(g + 1) * sd.G);
+                sub_gb.push_back(hgb[g]);
+                ++ng;
+            }
+            R->ngroups.push_back(ng);
+        }
+        if ((rc = R->ids.alloc(std::max<size_t>(1, sub_ids.size()))) || (rc = R->gb.alloc(std::max<size_t>(1, sub_gb.size()))))
+            return rc;
+        if (!sub_ids.empty())
+            CUDA_TRY(cudaMemcpy(R->ids.p, sub_ids.data(), sub_ids.size() * 4, cudaMemcpyHostToDevice));
+        if (!sub_gb.empty())
+            CUDA_TRY(cudaMemcpy(R->gb.p, sub_gb.data(), sub_gb.size() * 8, cudaMemcpyHostToDevice));
+        *out = R.release();
+        return QSIM_OK;
+    } catch (const std::bad_alloc &) {
+        return set_error(QSIM_E_NOMEM, "host allocation failed");
+    }
+}
+
+int qsim_shard_stage(qsim_shard_run *R, size_t stage) {
+    if (!R) return set_error(QSIM_E_INVALID, "null argument");
+    if (R->failed) return set_error(QSIM_E_INVALID, "the sharded run failed earlier");
+    if (stage != R->next || stage >= R->S.RC.nst)
+        return set_error(QSIM_E_INVALID, "stage %zu: the next stage to run is %zu", stage, R->next);
+    for (uint64_t b = 0; b < R->S.RC.nblocks; ++b)
+        if (bool(R->held[b]) != (shard_owner(R, stage, b) == R->rank))
+            return set_error(QSIM_E_INVALID, "stage %zu: block %llu is %s this rank, the rank qubits say otherwise",
+                             stage, (unsigned long long)b, R->held[b] ? "on" : "not on");
+    int rc = streams_stage(R->S, stage, R->ids.p + R->ids_off[stage], R->gb.p + R->gb_off[stage], R->ngroups[stage]);
+    if (rc) {
+        R->failed = true;
+        return rc;
+    }
+    ++R->next;
+    return QSIM_OK;
+}
+
+int qsim_shard_block_bytes(qsim_shard_run *R, const uint64_t *blocks, size_t count, uint64_t *bytes) {
+    if (!R || (count && (!blocks || !bytes))) return set_error(QSIM_E_INVALID, "null argument");
+    const uint64_t nblocks = R->S.RC.nblocks;
+    for (size_t i = 0; i < count; ++i)
+        if (blocks[i] >= nblocks || !R->held[blocks[i]])
+            return set_error(QSIM_E_INVALID, "block %llu is not on this rank", (unsigned long long)blocks[i]);
+    CUDA_TRY(cudaStreamSynchronize(R->S.main));
+    std::vector<BlockSlot> tab(nblocks);
+    const BlockSlot *cur = R->S.RC.tables.p + (R->next & 1) * nblocks;
+    CUDA_TRY(cudaMemcpy(tab.data(), cur, nblocks * sizeof(BlockSlot), cudaMemcpyDeviceToHost));
+    for (size_t i = 0; i < count; ++i) bytes[i] = tab[blocks[i]].bytes;
+    return QSIM_OK;
+}
+
+int qsim_shard_export(qsim_shard_run *R, const uint64_t *blocks, size_t count, void *d_packed, size_t cap) {
+    if (!R || (count && (!blocks || !d_packed))) return set_error(QSIM_E_INVALID, "null argument");
+    if (reinterpret_cast<uintptr_t>(d_packed) & 15) return set_error(QSIM_E_INVALID, "d_packed must be 16-byte aligned");
+    if (!count) return QSIM_OK;
+    std::vector<uint64_t> bytes(count);
+    int rc = qsim_shard_block_bytes(R, blocks, count, bytes.data());
+    if (rc) return rc;
+    std::vector<uint64_t> lists(2 * count);
+    uint64_t off = 0;
+    for (size_t i = 0; i < count; ++i) {
+        lists[i] = blocks[i];
+        lists[count + i] = off;
+        off += bytes[i];
+    }
+    if (off > cap) return set_error(QSIM_E_CAPACITY, "the blocks need %llu bytes, cap is %zu", (unsigned long long)off, cap);
+    if ((rc = R->xbuf.alloc(3 * count))) return rc;
+    cudaStream_t s = R->S.main;
+    CUDA_TRY(cudaMemcpyAsync(R->xbuf.p, lists.data(), 2 * count * 8, cudaMemcpyHostToDevice, s));
+    BlockSlot *cur = R->S.RC.tables.p + (R->next & 1) * R->S.RC.nblocks;
+    k_export_streams<<<unsigned(std::min<size_t>(count, 152 * 8)), 256, 0, s>>>(cur, R->xbuf.p, R->xbuf.p + count,
+                                                                               uint32_t(count), static_cast<uint8_t *>(d_packed));
+    count_launch();
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < count; ++i) R->held[blocks[i]] = 0;
+    return QSIM_OK;
+}
+
+int qsim_shard_import(qsim_shard_run *R, const uint64_t *blocks, const uint64_t *bytes, size_t count,
+                      const void *d_packed) {
+    if (!R || (count && (!blocks || !bytes || !d_packed))) return set_error(QSIM_E_INVALID, "null argument");
+    if (reinterpret_cast<uintptr_t>(d_packed) & 15) return set_error(QSIM_E_INVALID, "d_packed must be 16-byte aligned");
+    if (!count) return QSIM_OK;
+    const uint64_t nblocks = R->S.RC.nblocks;
+    std::vector<uint64_t> lists(3 * count);
+    uint64_t off = 0;
+    for (size_t i = 0; i < count; ++i) {
+        if (blocks[i] >= nblocks || R->held[blocks[i]])
+            return set_error(QSIM_E_INVALID, "block %llu: out of range or already on this rank", (unsigned long long)blocks[i]);
+        if (bytes[i] & 15) return set_error(QSIM_E_CORRUPT, "block %llu: stream size not a multiple of 16", (unsigned long long)blocks[i]);
+        lists[i] = blocks[i];
+        lists[count + i] = off;
+        lists[2 * count + i] = bytes[i];
+        off += bytes[i];
+    }
+    int rc;
+    if ((rc = R->xbuf.alloc(3 * count))) return rc;
+    cudaStream_t s = R->S.main;
+    CUDA_TRY(cudaMemcpyAsync(R->xbuf.p, lists.data(), 3 * count * 8, cudaMemcpyHostToDevice, s));
+    const int par = int(R->next & 1);
+    BlockSlot *cur = R->S.RC.tables.p + par * nblocks;
+    k_import_streams<<<unsigned(std::min<size_t>(count, 152 * 8)), 256, 0, s>>>(
+        cur, R->xbuf.p, R->xbuf.p + count, R->xbuf.p + 2 * count, uint32_t(count),
+        static_cast<const uint8_t *>(d_packed), R->S.RC.arena_dev(par), R->S.RC.arena_host(par), R->S.status);
+    count_launch();
+    CUDA_TRY(cudaStreamSynchronize(s));
+    for (size_t i = 0; i < count; ++i) R->held[blocks[i]] = 1;
+    return QSIM_OK;
+}
+
+int qsim_shard_finish(qsim_shard_run *R, qsim_state **out, qsim_stats *stats) {
+    if (!R || !out) return set_error(QSIM_E_INVALID, "null argument");
+    *out = nullptr;
+    if (R->failed) return set_error(QSIM_E_INVALID, "the sharded run failed earlier");
+    if (R->next != R->S.RC.nst) return set_error(QSIM_E_INVALID, "%zu of %zu stages run", R->next, R->S.RC.nst);
+    // blocks not on this rank: clear their final table entries (readout of them reports a corrupt block)
+    const uint64_t nblocks = R->S.RC.nblocks;
+    DevBuf<uint8_t> held;
+    int rc = held.alloc(nblocks);
+    if (rc) return rc;
+    CUDA_TRY(cudaMemcpyAsync(held.p, R->held.data(), nblocks, cudaMemcpyHostToDevice, R->S.main));
+    k_clear_slots<<<64, 256, 0, R->S.main>>>(R->S.RC.tables.p + (R->next & 1) * nblocks, held.p, nblocks);
+    count_launch();
+    CUDA_TRY(cudaStreamSynchronize(R->S.main));
+    try {
+        return streams_finish(R->S, out, stats);
+    } catch (const std::bad_alloc &) {
+        return set_error(QSIM_E_NOMEM, "host allocation failed");
+    }
+}
+
+void qsim_shard_free(qsim_shard_run *R) { delete R; }
 
 int qsim_run_batch(const qsim_plan *const *plans, size_t count, void *cuda_stream, qsim_state **states,
                    qsim_stats *stats, qsim_kernel_stat *launch) {
@@ -2386,6 +2741,7 @@ int qsim_state_block_stream(const qsim_state *st, uint64_t block, void *host_out
     *bytes = slot.bytes;
     if (cap < slot.bytes) return set_error(QSIM_E_CAPACITY, "buffer of %zu bytes < stream of %llu", cap,
                                            (unsigned long long)slot.bytes);
+    if (!slot.bytes) return QSIM_OK;  // a block this state does not hold (a sharded rank's)
     if (!host_out) return set_error(QSIM_E_INVALID, "null output");
     CUDA_TRY(cudaMemcpy(host_out, slot.ptr, slot.bytes, cudaMemcpyDefault));
     return QSIM_OK;

@@ -17,6 +17,9 @@
 #include <stdint.h>
 #include <string.h>
 
+#include <map>
+#include <mutex>
+
 #include "codec.cuh"
 #include "device_common.cuh"
 #include "gates.cuh"
@@ -29,61 +32,107 @@ namespace {
 using namespace gdev;
 constexpr int NT = 128;
 
-// One CTA per tile (grid: tiles x groups); several resident CTAs per SM keep
-// loads, ops and stores of different tiles in flight. (A persistent variant
-// with two tile buffers per CTA and cp.async prefetch of the next tile ran
-// slower on GB300: fewer resident CTAs, 3.1 against 4.3 TB/s on load/store-only
-// passes.)
+// One wave of resident CTAs, each looping over tiles of all the launch's groups
+// (one tile buffer per CTA; several resident CTAs per SM keep loads, ops and
+// stores of different tiles in flight). The pass set-up, the pass blob, TMEM
+// and a single tcgen05 op's B operand are staged once per CTA rather than once
+// per tile. (A variant with two tile buffers per CTA and cp.async prefetch of
+// the next tile ran slower on GB300: fewer resident CTAs, 3.1 against 4.3 TB/s
+// on load/store-only passes.)
 // UM: the pass's k = 5 dense ops run on tcgen05 (a separate instantiation, so that the warp-MMA kernels
 // keep their own register allocation)
 template <int KMAX, int PREC, bool UM>
 __global__ void __launch_bounds__(NT, (KMAX >= 6 ? 2 : (PREC == QSIM_PREC_BF16X3 && KMAX >= 4) ? 3 : 4))
-    k_pass(float2 *__restrict__ wv, uint32_t W, const __grid_constant__ PassDev P, const uint4 *__restrict__ blob,
-           const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr, const uint64_t *__restrict__ gbase,
-           int *status) {
+    k_pass(float2 *__restrict__ wv, uint32_t W, uint64_t ntiles, const __grid_constant__ PassDev P,
+           const uint4 *__restrict__ blob, const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr,
+           const uint64_t *__restrict__ gbase, uint32_t *ctr, int *status) {
     extern __shared__ float4 dyn_smem[];
     __shared__ PassSmem S;
-    float2 *g = wv + (uint64_t(blockIdx.y) << W);
-    const uint64_t gb = gbase ? gbase[blockIdx.y] : 0ull;
-    pass_tile<NT, KMAX, PREC, false, UM>(g, P, blob, mats, bfr, blockIdx.x, gb, S,
-                                         reinterpret_cast<float2 *>(dyn_smem), status);
+    pass_tiles<NT, KMAX, PREC, UM>(wv, W, ntiles, P, blob, mats, bfr, gbase, S, reinterpret_cast<float2 *>(dyn_smem),
+                                   ctr, status);
+}
+
+// Resident CTAs per SM of one k_pass instantiation at a given dynamic shared memory size (cached), from the
+// kernel's registers and static shared memory and the SM's limits (65536 registers, 2048 threads, 32 CTAs,
+// 228 KB of shared memory with 1 KB reserved per CTA). (The runtime's occupancy query answered 1 here where
+// 4 CTAs per SM were resident.)
+template <int KMAX, int PREC, bool UM>
+int pass_blocks_per_sm(size_t smem) {
+    static std::mutex mu;
+    static std::map<size_t, int> cache;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(smem);
+    if (it != cache.end()) return it->second;
+    cudaFuncAttributes fa{};
+    int nb = 1;
+    if (cudaFuncGetAttributes(&fa, k_pass<KMAX, PREC, UM>) == cudaSuccess) {
+        const int regs = ((fa.numRegs > 0 ? fa.numRegs : 255) + 7) & ~7;
+        const int by_regs = 65536 / (regs * NT);
+        const int by_smem = int((228u * 1024u) / (smem + fa.sharedSizeBytes + 1024u));
+        nb = std::max(1, std::min(std::min(by_regs, by_smem), std::min(2048 / NT, 32)));
+    }
+    cache[smem] = nb;
+    return nb;
+}
+
+int num_sms() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        n = v > 0 ? v : 1;
+    }
+    return n;
 }
 
 template <int KMAX, int PREC, bool UM>
 void launch_pass_ku(dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W, const PassDev &P,
-                    const uint4 *blob, const float2 *mats, const uint32_t *bfr, const uint64_t *gbase, int *status) {
+                    const uint4 *blob, const float2 *mats, const uint32_t *bfr, const uint64_t *gbase, uint32_t *ctr,
+                    int *status) {
     static bool attr_set = false;
     if (!attr_set) {
         cudaFuncSetAttribute(k_pass<KMAX, PREC, UM>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        // the whole unified L1/shared array as shared memory: the resident CTAs are limited by their tiles
+        cudaFuncSetAttribute(k_pass<KMAX, PREC, UM>, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             int(cudaSharedmemCarveoutMaxShared));
         attr_set = true;
     }
-    k_pass<KMAX, PREC, UM><<<grid, NT, smem, s>>>(wv, W, P, blob, mats, bfr, gbase, status);
+    // grid.x tiles per group, grid.y groups: the resident CTAs loop over all of them. The grid is twice the
+    // resident count so that an underestimate of it cannot leave SMs short of CTAs (measured on the 32-qubit
+    // QAOA passes: one CTA per SM 0.85 ms, one resident wave 0.41 ms, two 0.41 ms, one tile per CTA 0.46 ms);
+    // CTAs that start after the tiles have run out leave at once.
+    const uint64_t ntiles = uint64_t(grid.x) * grid.y;
+    const uint64_t resident = 2ull * uint64_t(pass_blocks_per_sm<KMAX, PREC, UM>(smem)) * num_sms();
+    const uint32_t nctas = uint32_t(ntiles < resident ? ntiles : resident);
+    k_pass<KMAX, PREC, UM><<<nctas, NT, smem, s>>>(wv, W, ntiles, P, blob, mats, bfr, gbase, ctr, status);
 }
 
 template <int KMAX, int PREC>
 void launch_pass_k(dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W, const PassDev &P,
-                   const uint4 *blob, const float2 *mats, const uint32_t *bfr, const uint64_t *gbase, int *status) {
+                   const uint4 *blob, const float2 *mats, const uint32_t *bfr, const uint64_t *gbase, uint32_t *ctr,
+                   int *status) {
     if constexpr ((PREC == QSIM_PREC_TF32 || PREC == QSIM_PREC_BF16X3) && KMAX >= 5) {
         if (P.umma) {
-            launch_pass_ku<KMAX, PREC, true>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status);
+            launch_pass_ku<KMAX, PREC, true>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, ctr, status);
             return;
         }
     }
-    launch_pass_ku<KMAX, PREC, false>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status);
+    launch_pass_ku<KMAX, PREC, false>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, ctr, status);
 }
 
 template <int PREC>
 void launch_pass_prec(uint32_t kmax, dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t W,
                       const PassDev &P, const uint4 *blob, const float2 *mats, const uint32_t *bfr,
-                      const uint64_t *gbase, int *status) {
+                      const uint64_t *gbase, uint32_t *ctr, int *status) {
     switch (kmax) {
-        case 0: launch_pass_k<0, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
-        case 1: launch_pass_k<1, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
-        case 2: launch_pass_k<2, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
-        case 3: launch_pass_k<3, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
-        case 4: launch_pass_k<4, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
-        case 5: launch_pass_k<5, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
-        default: launch_pass_k<6, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, status); break;
+        case 0: launch_pass_k<0, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, ctr, status); break;
+        case 1: launch_pass_k<1, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, ctr, status); break;
+        case 2: launch_pass_k<2, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, ctr, status); break;
+        case 3: launch_pass_k<3, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, ctr, status); break;
+        case 4: launch_pass_k<4, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, ctr, status); break;
+        case 5: launch_pass_k<5, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, ctr, status); break;
+        default: launch_pass_k<6, PREC>(grid, smem, s, wv, W, P, blob, mats, bfr, gbase, ctr, status); break;
     }
 }
 
@@ -203,17 +252,17 @@ void build_umma_b3(const double *u, uint32_t *out) {
 
 void launch_pass(float2 *wv, uint32_t W, uint32_t ngroups, const PassDev *pass_host, const uint4 *blob_dev,
                  const float2 *mats_dev, const uint32_t *bfr_dev, const uint64_t *gbase_dev, int prec,
-                 cudaStream_t s, int *status) {
+                 cudaStream_t s, uint32_t *ctr, int *status) {
     const PassDev &P = *pass_host;
     const size_t smem = pass_smem_bytes(P);
     dim3 grid(1u << P.nout, ngroups);
     const uint32_t kmax = P.kmax;
     if (prec == QSIM_PREC_TF32 && kmax >= 3)
-        launch_pass_prec<QSIM_PREC_TF32>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev, status);
+        launch_pass_prec<QSIM_PREC_TF32>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev, ctr, status);
     else if (prec == QSIM_PREC_BF16X3 && kmax >= 3)
-        launch_pass_prec<QSIM_PREC_BF16X3>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev, status);
+        launch_pass_prec<QSIM_PREC_BF16X3>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev, ctr, status);
     else
-        launch_pass_prec<QSIM_PREC_FP32>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev, status);
+        launch_pass_prec<QSIM_PREC_FP32>(kmax, grid, smem, s, wv, W, P, blob_dev, mats_dev, bfr_dev, gbase_dev, ctr, status);
     count_launch();
 }
 

@@ -83,9 +83,12 @@ void build_umma_b(const double *u_interleaved, uint32_t *out);
 // swizzled layout (row n at 1024 (n / 8) + 128 (n % 8), 16-byte chunk c = input / 8 at position c ^ (n % 8)).
 void build_umma_b3(const double *u_interleaved, uint32_t *out);
 
+// One pass over ngroups consecutive working vectors of 2^W amplitudes. ctr: two words of device memory, zero
+// before the first launch on a stream, that the launch leaves zero again; launches that overlap on the GPU
+// (other streams) need their own.
 void launch_pass(float2 *wv, uint32_t W, uint32_t ngroups, const PassDev *pass_host, const uint4 *blob_dev,
                  const float2 *mats_dev, const uint32_t *bfr_dev, const uint64_t *gbase_dev, int prec,
-                 cudaStream_t s, int *status);
+                 cudaStream_t s, uint32_t *ctr, int *status);
 
 // dynamic shared memory of one tile pass (tile, B operand and alignment when on tcgen05, blob, matrices)
 size_t pass_smem_bytes(const PassDev &P);

@@ -598,7 +598,8 @@ template <int NT, int KMAX, int PREC, bool UM = false>
 __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2 *mat,
                                          const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr,
                                          uint64_t base, uint64_t gb, PassSmem &S, uint4 *bbuf, int *status,
-                                         uint32_t &phase) {
+                                         uint32_t &phase, bool b_resident = false) {
+    // b_resident: the pass's only tcgen05 op has its B operand in bbuf already (staged once per CTA)
     // phase: parity of the next MMA-completion phase (tcgen05 dense ops); false after a wait ran out
     const int tid = threadIdx.x;
     const uint32_t T = S.p.T;
@@ -617,7 +618,7 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
             bool um = false;  // on tcgen05: stage the op's B operand now, under the set-up below
             if constexpr (UM) {
                 um = S.p.umma && k == 5 && T == 12;
-                if (um) {
+                if (um && !b_resident) {
                     const uint4 *src = reinterpret_cast<const uint4 *>(bfr + op.bfrag);
                     for (uint32_t t = tid; t < umma_b_bytes<PREC>() / 16; t += NT) cp_async16(bbuf + t, src + t);
                     cp_async_commit();
@@ -835,6 +836,96 @@ __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev 
     const bool ok = tile_ops<NT, KMAX, PREC, UM>(tile, blob, mat, mats, bfr, base, gb, S, bbuf, status, phase);
     __syncthreads();
     tile_store<NT>(g, base, S, tile);
+    if (um) {
+        // after a wait that ran out, wait (bounded) once more for the MMAs in flight before freeing TMEM
+        if (!ok) umma::mbar_wait(umma::smem_addr(&S.mbar), phase ^ 1u, kUmmaWaitNs);
+        umma::fence_before_sync();
+        __syncthreads();
+        if (threadIdx.x < 32) {
+            umma::fence_after_sync();
+            umma::tmem_dealloc(S.tmem, 64);
+        }
+    }
+}
+
+// One pass over many tiles (streams mode): CTA c takes tiles c, c + gridDim.x, ... of the launch's groups
+// (tile t: group t >> nout, tile index t & (2^nout - 1)). The pass descriptor, the pass blob, the TMEM
+// accumulator and the MMA mbarrier are set up once per CTA instead of once per tile, and when the pass has a
+// single tcgen05 op its B operand is staged once too; each tile is then loaded, updated and stored as in
+// pass_tile, with several CTAs per SM keeping loads, ops and stores of different tiles in flight.
+// Tiles are handed out in launch order from a counter (ctr[0]; ctr[1] counts the CTAs that finished, and the last
+// one zeroes both for the next launch on the stream), so the tiles in flight stay a narrow window of the working
+// vector: its 64-byte rows that share DRAM pages are read and written close together in time.
+template <int NT, int KMAX, int PREC, bool UM = false>
+__device__ __forceinline__ void pass_tiles(float2 *__restrict__ wv, uint32_t W, uint64_t ntiles, const PassDev &pd,
+                                           const uint4 *__restrict__ gblob, const float2 *__restrict__ mats,
+                                           const uint32_t *__restrict__ bfr, const uint64_t *__restrict__ gbase,
+                                           PassSmem &S, float2 *dyn, uint32_t *ctr, int *status) {
+    __shared__ uint32_t s_next;
+    pass_setup<NT>(pd, S);
+    const uint32_t T = S.p.T;
+    static_assert(!UM || ((PREC == QSIM_PREC_TF32 || PREC == QSIM_PREC_BF16X3) && NT == 128 && KMAX >= 5),
+                  "tcgen05 passes: TF32 or split BF16, k = 5");
+    bool um = false;
+    if constexpr (UM) um = S.p.umma != 0;
+    float2 *tile = dyn;
+    uint4 *bbuf = nullptr;
+    if (um) {
+        const uint32_t pad = (1024u - (umma::smem_addr(dyn) & 1023u)) & 1023u;
+        tile = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(dyn) + pad);
+        bbuf = reinterpret_cast<uint4 *>(tile + 4096);
+        if (threadIdx.x < 32) umma::tmem_alloc(umma::smem_addr(&S.tmem), 64);
+        if (threadIdx.x == 0) umma::mbar_init(umma::smem_addr(&S.mbar), 1);
+        umma::fence_before_sync();
+    }
+    uint4 *blob = reinterpret_cast<uint4 *>(tile + (1u << T)) + (um ? umma_b_bytes<PREC>() / 16 : 0u);
+    float2 *mat = reinterpret_cast<float2 *>(blob + S.p.blob_words);
+    blob_load<NT>(gblob + S.p.blob_off, S.p.blob_words, blob);
+    cp_async_wait_all();
+    __syncthreads();
+    // a single tcgen05 op: its B operand stays in bbuf for every tile of this CTA
+    bool b_res = false;
+    if (um && T == 12) {
+        const OpDev *bops = reinterpret_cast<const OpDev *>(blob);
+        uint32_t n5 = 0, first = 0;
+        for (uint32_t oi = 0; oi < S.p.op_count; ++oi)
+            if (bops[oi].type == OP_DENSE && bops[oi].k == 5) {
+                if (!n5) first = oi;
+                ++n5;
+            }
+        if (n5 == 1) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(bfr + bops[first].bfrag);
+            for (uint32_t t = threadIdx.x; t < umma_b_bytes<PREC>() / 16; t += NT) cp_async16(bbuf + t, src + t);
+            cp_async_commit();
+            b_res = true;
+        }
+    }
+    uint32_t phase = 0;
+    bool ok = true;
+    const uint64_t tmask = (1ull << S.p.nout) - 1;
+    for (uint64_t t = blockIdx.x; t < ntiles;) {
+        if (threadIdx.x == 0) s_next = gridDim.x + atomicAdd(ctr, 1u);  // this CTA's next tile, read below
+        const uint64_t grp = t >> S.p.nout, cta = t & tmask;
+        float2 *g = wv + (grp << W);
+        const uint64_t gb = gbase ? gbase[grp] : 0ull;
+        const uint64_t base = tile_base(S, cta);
+        tile_load<NT, false>(g, base, S, tile);
+        cp_async_wait_all();
+        ok = tile_ops<NT, KMAX, PREC, UM>(tile, blob, mat, mats, bfr, base, gb, S, bbuf, status, phase, b_res);
+        __syncthreads();
+        tile_store<NT>(g, base, S, tile);
+        __syncthreads();  // the next tile's loads overwrite the tile; s_next is visible
+        if (!ok) break;   // uniform: the MMA wait ran out (status set)
+        t = s_next;
+    }
+    if (threadIdx.x == 0) {
+        // every tile counter increment of this CTA precedes its arrival; the last CTA to arrive resets both
+        __threadfence();
+        if (atomicAdd(ctr + 1, 1u) == gridDim.x - 1) {
+            atomicExch(ctr, 0u);
+            atomicExch(ctr + 1, 0u);
+        }
+    }
     if (um) {
         // after a wait that ran out, wait (bounded) once more for the MMAs in flight before freeing TMEM
         if (!ok) umma::mbar_wait(umma::smem_addr(&S.mbar), phase ^ 1u, kUmmaWaitNs);

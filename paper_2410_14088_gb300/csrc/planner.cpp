@@ -680,4 +680,53 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
     return QSIM_OK;
 }
 
+// Group sharding over 2^r ranks (Sec. 4.2: the SV groups of a stage are independent; Sec. 5.8 runs them on
+// several GPUs). Stage s deals its groups by r rank qubits, global qubits outside the stage's inner set, so each
+// group, and each of its blocks, sits on the rank numbered by the block's bits at those qubits (rank bit j = the
+// bit of rank qubit j). A rank qubit keeps its slot until a stage takes it as an inner qubit; it is then replaced
+// by the free global qubit whose next use as an inner qubit is farthest away (never used: farthest of all), so
+// blocks move between ranks only at the stage boundaries that need it, and only over the replaced bits.
+int plan_shards(const qsim_plan *p, uint32_t r, uint32_t *rank_qubits) {
+    if (!p || (r && !rank_qubits)) return set_error(QSIM_E_INVALID, "null argument");
+    const uint32_t n = p->n, m = p->cfg.m, ns = uint32_t(p->stages.size());
+    if (r == 0 || ns == 0) return QSIM_OK;
+    if (r > 16) return set_error(QSIM_E_INVALID, "at most 2^16 ranks");
+    auto inner_of = [&](uint32_t s, uint32_t q) {
+        const std::vector<uint32_t> &in = p->stages[s].inner;
+        return std::find(in.begin(), in.end(), q) != in.end();
+    };
+    // next stage >= s that takes q as an inner qubit (ns: none)
+    auto next_use = [&](uint32_t s, uint32_t q) {
+        for (uint32_t t = s; t < ns; ++t)
+            if (inner_of(t, q)) return t;
+        return ns;
+    };
+    std::vector<uint32_t> cur;
+    for (uint32_t s = 0; s < ns; ++s) {
+        if (n - m < r + uint32_t(p->stages[s].inner.size()))
+            return set_error(QSIM_E_INVALID, "stage %u: %u global qubits, %zu inner, too few left for %u rank qubits",
+                             s, n - m, p->stages[s].inner.size(), r);
+        std::vector<uint32_t> next(cur);
+        if (next.empty()) next.assign(r, ~0u);
+        for (uint32_t j = 0; j < r; ++j) {
+            if (next[j] != ~0u && !inner_of(s, next[j])) continue;
+            // the free global qubit (not inner now, not held by another slot) used as inner farthest ahead;
+            // ties go to the lowest qubit
+            uint32_t best = ~0u, best_use = 0;
+            for (uint32_t q = m; q < n; ++q) {
+                if (inner_of(s, q) || std::find(next.begin(), next.end(), q) != next.end()) continue;
+                const uint32_t u = next_use(s, q);
+                if (best == ~0u || u > best_use) {
+                    best = q;
+                    best_use = u;
+                }
+            }
+            next[j] = best;
+        }
+        for (uint32_t j = 0; j < r; ++j) rank_qubits[size_t(s) * r + j] = next[j];
+        cur = next;
+    }
+    return QSIM_OK;
+}
+
 }  // namespace qsim

@@ -116,4 +116,5 @@ namespace qsim {
 // planner.cpp
 int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_config *cfg,
                qsim_plan **out);
+int plan_shards(const qsim_plan *p, uint32_t log2_ranks, uint32_t *rank_qubits);
 }  // namespace qsim

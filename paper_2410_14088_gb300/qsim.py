@@ -118,6 +118,14 @@ SIGNATURES = {
     "qsim_state_free": (None, [_VP]),
     "qsim_worst_case_bytes": (_SZ, [_U32]),
     "qsim_compress_block": (ctypes.c_int, [_VP, _U32, ctypes.c_double, _VP, _SZ, ctypes.POINTER(_SZ), _VP]),
+    "qsim_plan_shards": (ctypes.c_int, [_VP, _U32, ctypes.POINTER(_U32)]),
+    "qsim_shard_begin": (ctypes.c_int, [_VP, ctypes.POINTER(_U32), _U32, _U32, _VP, ctypes.POINTER(_VP)]),
+    "qsim_shard_stage": (ctypes.c_int, [_VP, _SZ]),
+    "qsim_shard_block_bytes": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), _SZ, ctypes.POINTER(_U64)]),
+    "qsim_shard_export": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), _SZ, _VP, _SZ]),
+    "qsim_shard_import": (ctypes.c_int, [_VP, ctypes.POINTER(_U64), ctypes.POINTER(_U64), _SZ, _VP]),
+    "qsim_shard_finish": (ctypes.c_int, [_VP, ctypes.POINTER(_VP), ctypes.POINTER(Stats)]),
+    "qsim_shard_free": (None, [_VP]),
     "qsim_compress_block_noalloc": (ctypes.c_int, [_VP, _U32, ctypes.c_double, _VP, _SZ, ctypes.POINTER(_SZ), _VP]),
     "qsim_decompress_block": (ctypes.c_int, [_VP, _SZ, _VP, _U32, _VP]),
     "qsim_compress_block_rel": (ctypes.c_int, [_VP, _U32, ctypes.c_double, _VP, _SZ, ctypes.POINTER(_SZ), _VP]),
@@ -282,6 +290,14 @@ class Plan:
             ops.append(d)
         return ops
 
+    def shards(self, log2_ranks: int) -> np.ndarray:
+        """qsim_plan_shards: rank qubits per stage, shape (nstages, log2_ranks)."""
+        ns = self.nstages
+        out = np.zeros((max(1, ns), max(1, log2_ranks)), dtype=np.uint32)
+        _check(lib().qsim_plan_shards(self.handle, log2_ranks, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))),
+               "qsim_plan_shards")
+        return out[:ns, :log2_ranks]
+
     def stats(self) -> dict:
         s = PlanStats()
         _check(lib().qsim_plan_get_stats(self.handle, ctypes.byref(s)), "qsim_plan_get_stats")
@@ -406,6 +422,65 @@ def run_batch(plans, stream=None):
     launch = {"name": ks.name.decode(), "launches": ks.launches, "seconds": ks.seconds, "alg_bytes": ks.alg_bytes,
               "alg_flops": ks.alg_flops}
     return states, launch
+
+
+# --------------------------------------------------------------------------
+# sharded runs (one rank's SV groups)
+# --------------------------------------------------------------------------
+
+class ShardRun:
+    """qsim_shard_*: rank `rank` of 2^log2_ranks running its SV groups stage by stage; blocks move between
+    ranks through export (packed into a uint8 CUDA tensor) and import."""
+
+    def __init__(self, plan: Plan, rank_qubits, log2_ranks: int, rank: int, stream=None):
+        self.plan = plan
+        rq = np.ascontiguousarray(rank_qubits, dtype=np.uint32).reshape(-1)
+        h = ctypes.c_void_p()
+        _check(lib().qsim_shard_begin(plan.handle, rq.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), log2_ranks,
+                                      rank, _stream_ptr(stream), ctypes.byref(h)), "qsim_shard_begin")
+        self.handle = h
+
+    def __del__(self):
+        if getattr(self, "handle", None):
+            lib().qsim_shard_free(self.handle)
+            self.handle = None
+
+    def stage(self, s: int):
+        _check(lib().qsim_shard_stage(self.handle, s), "qsim_shard_stage")
+
+    def block_bytes(self, blocks) -> np.ndarray:
+        b = np.ascontiguousarray(blocks, dtype=np.uint64)
+        out = np.zeros(max(1, b.size), dtype=np.uint64)
+        _check(lib().qsim_shard_block_bytes(self.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), b.size,
+                                            out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))),
+               "qsim_shard_block_bytes")
+        return out[: b.size]
+
+    def export(self, blocks):
+        """(sizes, packed uint8 CUDA tensor) of the blocks, which leave this rank."""
+        import torch
+        b = np.ascontiguousarray(blocks, dtype=np.uint64)
+        sizes = self.block_bytes(b)
+        buf = torch.empty(max(16, int(sizes.sum())), dtype=torch.uint8, device="cuda")
+        _check(lib().qsim_shard_export(self.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), b.size,
+                                       ctypes.c_void_p(buf.data_ptr()), buf.numel()), "qsim_shard_export")
+        return sizes, buf[: int(sizes.sum())]
+
+    def import_(self, blocks, sizes, packed):
+        b = np.ascontiguousarray(blocks, dtype=np.uint64)
+        sz = np.ascontiguousarray(sizes, dtype=np.uint64)
+        if b.size == 0:
+            return
+        packed = packed.contiguous()
+        _check(lib().qsim_shard_import(self.handle, b.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                       sz.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), b.size,
+                                       ctypes.c_void_p(packed.data_ptr())), "qsim_shard_import")
+
+    def finish(self) -> "State":
+        h = ctypes.c_void_p()
+        st = Stats()
+        _check(lib().qsim_shard_finish(self.handle, ctypes.byref(h), ctypes.byref(st)), "qsim_shard_finish")
+        return State(h, self.plan.n, self.plan.cfg.m, st, self.plan.nstages)
 
 
 # --------------------------------------------------------------------------

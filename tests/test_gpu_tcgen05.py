@@ -1,6 +1,7 @@
-"""Dense ops of width 5 on the 5th-generation tensor cores (tcgen05.mma in TF32 or split BF16, both operands
-in shared memory, the FP32 accumulator in tensor memory) against the FP64 oracle and the warp-level
-mma.sync path, uncompressed and through the compressed stage loop."""
+"""Dense ops on the 5th-generation tensor cores (tcgen05.mma in TF32 or split BF16, both operands in shared
+memory, the FP32 accumulator in tensor memory) against the FP64 oracle and the warp-level mma.sync path,
+uncompressed and through the compressed stage loop: width 5 natively, widths 3 and 4 as width-5 ops (the
+matrix times the identity on tile bits the op does not touch)."""
 import numpy as np
 import pytest
 
@@ -117,3 +118,28 @@ def test_full_size_gate_error_vs_fp64(prec, rel_tol):
     assert err / 2.0 ** -14 <= rel_tol
     if prec == qsim.PREC_BF16X3:
         assert err <= 1e-5
+
+
+@pytest.mark.parametrize("prec", [qsim.PREC_TF32, qsim.PREC_BF16X3], ids=["tf32", "bf16x3"])
+@pytest.mark.parametrize("k", [3, 4])
+def test_tcgen05_widths_3_and_4(k, prec):
+    # fused to at most k qubits: every dense op of width 3 or 4 in a 4096-amplitude tile pass runs on tcgen05
+    # as a width-5 op; against FP64 with the per-op bounds above, and no worse than the warp-level path
+    cases = [(inputs.qft_rz_cx(14, 2, 7), dict(m=9, inner=3)), (inputs.random_brick(16, 8, 2), dict(m=10, inner=2))]
+    for c, kw in cases:
+        plans = [qsim.plan_stages(c, codec=qsim.CODEC_NONE, prec=prec, k=k, tcgen05=t, **kw) for t in (0, 1)]
+        nk = sum(1 for s in range(plans[1].nstages) for o in plans[1].stage_ops(s) if o["type"] == 0 and o["nq"] == k)
+        assert nk > 0
+        warp, tc = (qsim.run(p).decompress().cpu().numpy() for p in plans)
+        want = oracle.simulate(c)
+        nops = sum(1 for s in range(plans[1].nstages) for o in plans[1].stage_ops(s) if o["type"] == 0)
+        err_tc = np.linalg.norm(tc - want) / np.linalg.norm(want)
+        err_warp = np.linalg.norm(warp - want) / np.linalg.norm(want)
+        per_op = 2.0 ** -10 if prec == qsim.PREC_TF32 else 2.0 ** -20
+        print(f"\nk={k} prec={prec} n={c.n}: tcgen05 {err_tc:.3e}, warp/cuda-core {err_warp:.3e}, {nops} dense ops")
+        assert err_tc <= nops * per_op
+        assert err_tc <= 1.5 * err_warp + 1e-6
+        if prec == qsim.PREC_BF16X3:
+            assert np.max(np.abs(tc - want)) <= 1e-5
+        else:
+            assert np.max(np.abs(tc - want)) <= 2e-2 * 2 ** (-c.n / 2)
