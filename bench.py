@@ -1,10 +1,16 @@
 #!/usr/bin/env python
 """Benchmark of the compressed staged state-vector loop on GB300.
 
-Workload (default): 28-qubit QFT of a seeded random basis state followed by
-4 x (RZ on every qubit, CX ladder) — 626 gates, complex64 state (2 GiB raw),
-SV blocks of 2^22 amplitudes, inner size 2, gates fused to k = 5 qubits,
-eps = 1e-3 (eb = eps * 2^-14 per real/imaginary part).
+Workload (default): QAOA MaxCut with p = 3 on a seeded random 3-regular graph
+of 32 vertices — an H layer, then 3 x (RZZ(gamma) on all 48 edges, RX(beta) on
+every qubit), 272 gates, complex64 state (32 GiB raw), eps = 1e-3
+(eb = eps * 2^-16 per real/imaginary part), SV blocks of 2^22 amplitudes,
+inner size 4, gates fused to k = 5, commutation-aware partition with diagonal
+gates exempt. The timed form is the tensor-core one with learned sizing: fused
+k-qubit gates as TF32 GEMMs on tcgen05, slots reserved by the trained size
+predictor. Beside it, on the same circuit ("forms"): the plain FP32 form
+(CUDA-core gates, exact sizing), the tensor-core form with exact sizing, and
+the tensor-core form with Algorithm 1 over the gates in circuit order.
 
 One step = one qsim_run of the whole circuit through the C ABI: initial
 store, then per stage decompress -> fused gate passes -> sizing ->
@@ -18,7 +24,7 @@ beside it.
   e2e    — K steps from host data through the public API: plan from the host
            gate list (matrices uploaded), run, read sampled amplitudes and
            the statistics back to the host.
-The working set (2 GiB state, ~1 GB compressed) is larger than L2 (129 MB),
+The working set (32 GiB state, ~12 GB compressed) is larger than L2 (129 MB),
 so no explicit flush is done between steps.
 
 `--impl reference` times the CPU oracle (complex128 staged simulation + scalar
@@ -51,7 +57,7 @@ def parse_args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32", "bf16x3"])
-    ap.add_argument("--n", type=int, default=28)
+    ap.add_argument("--n", type=int, default=32)
     ap.add_argument("--m", type=int, default=22)
     ap.add_argument("--inner", type=int, default=4)
     ap.add_argument("--k", type=int, default=5)
@@ -63,15 +69,18 @@ def parse_args():
     ap.add_argument("--no-profile", action="store_true")
     ap.add_argument("--mode", default="streams", choices=["streams", "persistent"])
     ap.add_argument("--graph", action="store_true", help="persistent mode: capture the stage loop in a CUDA graph")
-    ap.add_argument("--sizing", default="exact", choices=["exact", "predict"])
+    ap.add_argument("--sizing", default="predict", choices=["exact", "predict"])
     ap.add_argument("--margin", type=float, default=0.25, help="predictor reservation margin")
-    ap.add_argument("--diag-exempt", action="store_true", help="diagonal gates never count as global (Algorithm 1)")
+    ap.add_argument("--diag-exempt", action=argparse.BooleanOptionalAction, default=True,
+                    help="diagonal gates never count as global qubits in the partition (Algorithm 1's option for "
+                         "QAOA and Grover; --no-diag-exempt counts them as the paper does)")
     ap.add_argument("--mma", default="tcgen05", choices=["warp", "tcgen05"],
                     help="TF32 / split-BF16 dense ops of width 5: warp-level mma.sync, or tcgen05 with the accumulator in TMEM")
-    ap.add_argument("--reorder", action="store_true",
-                    help="commutation-aware partition: gates may move before earlier gates they commute with")
+    ap.add_argument("--reorder", action=argparse.BooleanOptionalAction, default=True,
+                    help="commutation-aware partition: gates may move before earlier gates they commute with "
+                         "(--no-reorder: Algorithm 1 in circuit order)")
     ap.add_argument("--train-n", type=int, default=0, help="qubits of the predictor's training circuits (0 = n)")
-    ap.add_argument("--workload", default="qft", choices=["qft", "qaoa", "random", "mirror", "batch"],
+    ap.add_argument("--workload", default="qaoa", choices=["qft", "qaoa", "random", "mirror", "batch"],
                     help="qft: QFT + 4 x (RZ, CX ladder) on n qubits; qaoa: MaxCut p=3 on a random 3-regular "
                          "graph of n vertices; random: U3 + CZ brick of depth --depth; mirror: depth/2 random "
                          "layers then their inverse (ideal final state |0...0>); batch: --batch independent "
@@ -85,6 +94,13 @@ def parse_args():
     ap.add_argument("--depth", type=int, default=14)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement (long workloads)")
     ap.add_argument("--cap-gib", type=float, default=0.0, help="device tier cap (pinned host holds the rest)")
+    ap.add_argument("--forms", type=int, default=3,
+                    help="timed runs of each comparison form (plain FP32 + exact sizing; the timed precision with "
+                         "exact sizing); 0 skips them")
+    ap.add_argument("--shard", action="store_true",
+                    help="run the circuit sharded over the ranks (qsim_shard_*: each rank runs its SV groups, "
+                         "compressed blocks exchanged between stages); the default for N > 1, and at N = 1 a "
+                         "single-rank sharded run")
     ap.add_argument("--codec", default="abs", choices=["abs", "rel"],
                     help="abs: point-wise absolute bound eps*2^(-n/2) (QSZ1); rel: point-wise relative bound eps "
                          "(QSZR, the paper's Sec. 4.3 mode)")
@@ -127,6 +143,26 @@ def job_rate(world, steps, units_per_step, max_ms):
     """Whole-job throughput: every rank runs `steps` steps of `units_per_step` units (weak scaling), timed by the
     slowest rank."""
     return world * steps * units_per_step / (max_ms * 1e-3)
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu on Arm, /proc/cpuinfo on x86), for the CPU baseline's record."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().startswith("Model name:"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    import platform
+    return platform.machine()
 
 
 def load_peaks():
@@ -202,6 +238,8 @@ class OracleSampler:
     calls), plus QSZ1 encode + decode of SV blocks. The full-run time is
     modelled as (time per gate) x gates + (time per block) x blocks x stages."""
 
+    MAX_SAMPLE_QUBITS = 28  # a 2^28 complex128 state is 4 GiB of host memory; 32 qubits would need 64 GiB
+
     def __init__(self, args):
         import numpy as np
 
@@ -209,13 +247,22 @@ class OracleSampler:
         from oracle.partition import partition
 
         self.np, self.oracle = np, oracle
-        self.circ = workload(args)
-        self.n, self.m = self.circ.n, min(args.m, self.circ.n - 4)
+        full = workload(args)
+        self.n, self.m = full.n, min(args.m, full.n - 4)
+        # gates are timed on the same family's circuit at min(n, 28) qubits (same seed) and scaled by
+        # 2^(n - n_sample): the per-gate work of the plain update is proportional to the state size
+        self.n_sample = min(self.n, self.MAX_SAMPLE_QUBITS)
+        if args.workload == "batch" or self.n_sample == self.n:
+            self.n_sample = self.n
+            self.circ = full
+        else:
+            self.circ = workload(args, n=self.n_sample)
+        self.full_gates = len(full.gates)
         self.rel = getattr(args, "codec", "abs") == "rel"
         self.eb = args.eps if self.rel else args.eps * 2.0 ** (-self.n / 2)
         self.codec = "QSZR" if self.rel else "QSZ1"
-        self.stages = partition(self.circ.gates, self.n, self.m, args.inner)
-        self.psi = oracle.basis_state(self.n, self.circ.init_basis)
+        self.stages = partition(full.gates, self.n, self.m, args.inner)
+        self.psi = oracle.basis_state(self.n_sample, self.circ.init_basis)
         self.next_gate = 0
         self.next_block = 0
         self.t_gates = self.t_codec = 0.0
@@ -226,11 +273,11 @@ class OracleSampler:
         g = b = 0
         while time.perf_counter() - t0 < 0.7 * budget_s or g == 0:
             gi = self.next_gate % len(self.circ.gates)
-            self.oracle.apply_gate(self.psi, self.n, self.circ.gates[gi])
+            self.oracle.apply_gate(self.psi, self.n_sample, self.circ.gates[gi])
             self.next_gate += 1
             g += 1
         t1 = time.perf_counter()
-        nblocks = 1 << (self.n - self.m)
+        nblocks = 1 << (self.n_sample - self.m)
         while time.perf_counter() - t1 < 0.3 * budget_s or b == 0:
             j = self.next_block % nblocks
             blk = self.psi[2 * (j << self.m): 2 * ((j + 1) << self.m)].astype(self.np.float32)
@@ -248,15 +295,19 @@ class OracleSampler:
             self.blocks_done += b
 
     def result(self):
-        per_gate = self.t_gates / max(1, self.gates_done)
+        scale = float(1 << (self.n - self.n_sample))
+        per_gate = self.t_gates / max(1, self.gates_done) * scale
         per_block = self.t_codec / max(1, self.blocks_done)
         nblocks = 1 << (self.n - self.m)
-        total = per_gate * len(self.circ.gates) + per_block * nblocks * len(self.stages)
-        ups = (1 << self.n) * len(self.circ.gates) / total
+        total = per_gate * self.full_gates + per_block * nblocks * len(self.stages)
+        ups = (1 << self.n) * self.full_gates / total
         threads = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-        sample = (f"{self.gates_done} complex128 gate updates of the full 2^{self.n} state "
+        where = (f"the full 2^{self.n} state" if self.n_sample == self.n else
+                 f"a 2^{self.n_sample} state of the same circuit family and seed (per-gate time x "
+                 f"2^{self.n - self.n_sample} for 2^{self.n} amplitudes)")
+        sample = (f"{self.gates_done} complex128 gate updates of {where} "
                   f"({self.t_gates:.1f} s) and {self.blocks_done} {self.codec} encode+decode of 2^{self.m}-amplitude "
-                  f"blocks ({self.t_codec:.1f} s); full run modelled as per-gate time x {len(self.circ.gates)} "
+                  f"blocks ({self.t_codec:.1f} s); full run modelled as per-gate time x {self.full_gates} "
                   f"gates + per-block codec time x {nblocks} blocks x {len(self.stages)} stages")
         return ups, sample, threads, total
 
@@ -277,7 +328,8 @@ def run_reference(args, rank, world):
         "ms_per_step": total * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": config_dict(args),
-        "cpu_baseline": {"value": ups, "unit": "updates/s", "cores": threads, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": ups, "unit": "updates/s", "cores": threads, "cpu_model": cpu_model(),
+                         "nproc": os.cpu_count(), "kind": "oracle", "sample": sample},
         "e2e": {"value": ups, "unit": "updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -370,6 +422,19 @@ def run_ours(args, rank, world, dist):
                      "m": best.m, "k": best.k, "inner": best.inner, "streams": best.streams}
     plan = qsim.plan_stages(circ, **kw)
     stream = torch.cuda.current_stream()
+    # sharded over the ranks (strong scaling: one circuit, its SV groups dealt to the ranks, compressed blocks
+    # exchanged between stages), or one replica of the whole circuit per rank (weak scaling)
+    sharded = args.shard or world > 1
+    log2w = world.bit_length() - 1
+    if sharded and world != 1 << log2w:
+        raise SystemExit("sharded runs need a power-of-two number of ranks")
+    jobs = 1 if sharded else world  # circuits the job runs per step
+
+    def run_once():
+        if sharded:
+            from paper_2410_14088_gb300 import shard
+            return shard.run_sharded(plan, log2w, dist)[0]
+        return qsim.run(plan)
 
     def barrier():
         if dist is not None:
@@ -378,7 +443,7 @@ def run_ours(args, rank, world, dist):
 
     # ---- warm-up ----
     for _ in range(args.warmup):
-        st = qsim.run(plan)
+        st = run_once()
         del st
     barrier()
 
@@ -394,7 +459,7 @@ def run_ours(args, rank, world, dist):
     kstats_acc = {}
     stats = []
     for _ in range(args.steps):
-        st = qsim.run(plan)
+        st = run_once()
         stats.append(st.stats.as_dict())
         for k, v in st.kernel_stats().items():
             a = kstats_acc.setdefault(k, {"launches": 0, "seconds": 0.0, "alg_bytes": 0.0, "alg_flops": 0.0})
@@ -408,10 +473,16 @@ def run_ours(args, rank, world, dist):
     launches = qsim.launch_count() - launches0
     t_ms = ev0.elapsed_time(ev1)
     t_max = max_over_ranks(t_ms, dist)
-    ups = job_rate(world, args.steps, (1 << n) * G, t_max)
+    ups = job_rate(jobs, args.steps, (1 << n) * G, t_max)
 
     # ---- timed: e2e through the public API from host data ----
     idx = np.arange(0, 1 << n, (1 << n) // 4096, dtype=np.uint64)[:4096]
+    if sharded and plan.nstages:
+        # each rank reads the sampled amplitudes that lie in the blocks it holds after the last stage
+        from paper_2410_14088_gb300 import shard
+        last_q = plan.shards(log2w)[-1] if log2w else []
+        own = shard.block_owner(idx >> np.uint64(args.m), last_q, args.m) == rank
+        idx = idx[own]
     barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
@@ -419,7 +490,11 @@ def run_ours(args, rank, world, dist):
     h2d = d2h = 0
     for _ in range(0 if args.no_e2e else args.steps):
         p2 = qsim.plan_stages(circ, **kw)
-        st = qsim.run(p2)
+        if sharded:
+            from paper_2410_14088_gb300 import shard
+            st = shard.run_sharded(p2, log2w, dist)[0]
+        else:
+            st = qsim.run(p2)
         amps = st.amplitudes(idx)
         h2d += st.stats.h2d_bytes + idx.nbytes
         d2h += st.stats.d2h_bytes + amps.nbytes
@@ -427,11 +502,11 @@ def run_ours(args, rank, world, dist):
     e1.record(stream)
     barrier()
     te_ms = max_over_ranks(e0.elapsed_time(e1), dist)
-    e2e = job_rate(world, args.steps, (1 << n) * G, te_ms) if not args.no_e2e else None
+    e2e = job_rate(jobs, args.steps, (1 << n) * G, te_ms) if not args.no_e2e else None
 
     # ---- per-kernel times without the other stream's kernels beside them (roofline context) ----
     kstats_serial = None
-    if not args.no_profile and args.mode == "streams" and args.streams > 1:
+    if not args.no_profile and args.mode == "streams" and args.streams > 1 and not sharded:
         plan1 = qsim.plan_stages(circ, **dict(kw, streams=1))
         st = qsim.run(plan1)
         del st
@@ -440,6 +515,48 @@ def run_ours(args, rank, world, dist):
         kstats_serial = st.kernel_stats()
         qsim.profile_enable(False)
         del st, plan1
+
+    # ---- the comparison forms on the same circuit and partition: plain FP32 CUDA-core gates with exact sizing
+    # (the method without either addition), and the timed precision with exact sizing (without the predictor) ----
+    forms = None
+    if args.forms > 0 and args.codec == "abs" and not sharded:
+        headline = f"{args.prec}{'_tcgen05' if args.mma == 'tcgen05' and args.prec != 'fp32' else ''}_{args.sizing}_sizing"
+        forms = {headline: {"value": ups, "ms_per_step": t_max / args.steps, "steps": args.steps,
+                            "stages": stats[-1]["nstages"], "fidelity_lower_bound": stats[-1]["fidelity_lower_bound"],
+                            "timed_form": True}}
+        variants = []
+        if not (args.prec == "fp32" and args.sizing == "exact"):
+            variants.append(("fp32_exact_sizing", dict(kw, prec=qsim.PREC_FP32, sizing=qsim.SIZING_EXACT, tcgen05=0)))
+        if args.sizing == "predict":
+            variants.append((headline.replace("_predict_sizing", "_exact_sizing"), dict(kw, sizing=qsim.SIZING_EXACT)))
+        if args.reorder or args.diag_exempt:
+            # the paper's partition: Algorithm 1 over the gates in circuit order, every gate counted
+            variants.append((headline.replace("_predict_sizing", "_exact_sizing") + "_algorithm1_in_order",
+                             dict(kw, sizing=qsim.SIZING_EXACT, reorder=0, diag_exempt=0)))
+        for name, fk in variants:
+            pl = qsim.plan_stages(circ, **fk)
+            del_st = qsim.run(pl)  # warm-up (plan upload, arenas)
+            del del_st
+            barrier()
+            f0 = torch.cuda.Event(enable_timing=True)
+            f1 = torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            fst = None
+            for _ in range(args.forms):
+                st = qsim.run(pl)
+                fst = st.stats.as_dict()
+                del st
+            f1.record(stream)
+            barrier()
+            fms = max_over_ranks(f0.elapsed_time(f1), dist)
+            forms[name] = {"value": job_rate(world, args.forms, (1 << n) * G, fms), "ms_per_step": fms / args.forms,
+                           "steps": args.forms, "stages": fst["nstages"],
+                           "fidelity_lower_bound": fst["fidelity_lower_bound"],
+                           "compression_ratio": 8.0 * (1 << n) / max(1, fst["peak_store_bytes"]),
+                           "overflow_blocks": fst["overflow_blocks"]}
+            del pl
+        if "fp32_exact_sizing" in forms:
+            forms["speedup_vs_fp32_exact_sizing"] = ups / forms["fp32_exact_sizing"]["value"]
 
     if rank != 0:
         return
@@ -503,10 +620,13 @@ def run_ours(args, rank, world, dist):
     line = {
         "metric": "amplitude-gate updates/s incl. codec & compression ratio at fidelity>=0.99",
         "value": ups, "unit": "updates/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": t_max / args.steps, "higher_is_better": True, "scaling": "strong" if sharded else "weak",
+        "vs_baseline": None,
         "dtype": {"fp32": "f32", "tf32": "tf32", "bf16x3": "bf16x3"}[args.prec],
         "data": "synthetic",
-        "config": config_dict(args),
+        "config": dict(config_dict(args), parallelism=(f"sharded over {world} rank(s): SV groups dealt by rank "
+                                                     f"qubits, compressed blocks exchanged between stages")
+                       if sharded else f"{world} independent replica(s)"),
         "compression_ratio": cr, "compression_ratio_vs_complex128": 2 * cr,
         "fidelity_lower_bound": last["fidelity_lower_bound"], "norm_sq": last["norm_sq"],
         "stages": last["nstages"], "plan_seconds": plan.stats()["plan_seconds"],
@@ -514,9 +634,11 @@ def run_ours(args, rank, world, dist):
         "host_tier_peak_bytes": last["host_tier_peak_bytes"], "predictor_training": train_info,
         "autotune": tune_info,
         "mirror_fidelity": mirror_fidelity,
+        "forms": forms,
         "e2e": {"value": e2e, "unit": "updates/s", "h2d_bytes_per_step": h2d // args.steps,
                 "d2h_bytes_per_step": d2h // args.steps} if e2e is not None else None,
         "gpu_launches": launches,
+        "launches_before_timed": launches0,
         "roofline": roofline,
         "kernels": kernels,
         "clocks": clocks,
@@ -528,7 +650,8 @@ def run_ours(args, rank, world, dist):
         for _ in range(3):
             smp.step(args.cpu_seconds / 3)
         cups, sample, threads, _ = smp.result()
-        line["cpu_baseline"] = {"value": cups, "unit": "updates/s", "cores": threads, "kind": "oracle",
+        line["cpu_baseline"] = {"value": cups, "unit": "updates/s", "cores": threads, "cpu_model": cpu_model(),
+                                "nproc": os.cpu_count(), "kind": "oracle",
                                 "sample": sample}
     print(json.dumps(line), flush=True)
 
@@ -668,7 +791,8 @@ def run_batch_bench(args, rank, world, dist):
         for _ in range(3):
             smp.step(args.cpu_seconds / 3)
         cups, sample, threads, _ = smp.result()
-        line["cpu_baseline"] = {"value": cups, "unit": "updates/s", "cores": threads, "kind": "oracle",
+        line["cpu_baseline"] = {"value": cups, "unit": "updates/s", "cores": threads, "cpu_model": cpu_model(),
+                                "nproc": os.cpu_count(), "kind": "oracle",
                                 "sample": "per-amplitude-gate rate of the batch's first random circuit: " + sample}
     print(json.dumps(line), flush=True)
 

@@ -42,14 +42,23 @@ constexpr int NT = 128;
 // UM: the pass's k = 5 dense ops run on tcgen05 (a separate instantiation, so that the warp-MMA kernels
 // keep their own register allocation)
 template <int KMAX, int PREC, bool UM>
-__global__ void __launch_bounds__(NT, (KMAX >= 6 ? 2 : (PREC == QSIM_PREC_BF16X3 && KMAX >= 4) ? 3 : 4))
+__host__ __device__ constexpr int pass_threads() {
+    return NT;
+}
+template <int KMAX, int PREC, bool UM>
+__host__ __device__ constexpr int pass_min_blocks() {
+    return KMAX >= 6 ? 2 : (PREC == QSIM_PREC_BF16X3 && KMAX >= 4) ? 3 : 4;
+}
+
+template <int KMAX, int PREC, bool UM>
+__global__ void __launch_bounds__(pass_threads<KMAX, PREC, UM>(), pass_min_blocks<KMAX, PREC, UM>())
     k_pass(float2 *__restrict__ wv, uint32_t W, uint64_t ntiles, const __grid_constant__ PassDev P,
            const uint4 *__restrict__ blob, const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr,
            const uint64_t *__restrict__ gbase, uint32_t *ctr, int *status) {
     extern __shared__ float4 dyn_smem[];
     __shared__ PassSmem S;
-    pass_tiles<NT, KMAX, PREC, UM>(wv, W, ntiles, P, blob, mats, bfr, gbase, S, reinterpret_cast<float2 *>(dyn_smem),
-                                   ctr, status);
+    pass_tiles<pass_threads<KMAX, PREC, UM>(), KMAX, PREC, UM>(wv, W, ntiles, P, blob, mats, bfr, gbase, S,
+                                                                reinterpret_cast<float2 *>(dyn_smem), ctr, status);
 }
 
 // Resident CTAs per SM of one k_pass instantiation at a given dynamic shared memory size (cached), from the
@@ -65,11 +74,12 @@ int pass_blocks_per_sm(size_t smem) {
     if (it != cache.end()) return it->second;
     cudaFuncAttributes fa{};
     int nb = 1;
+    constexpr int nt = pass_threads<KMAX, PREC, UM>();
     if (cudaFuncGetAttributes(&fa, k_pass<KMAX, PREC, UM>) == cudaSuccess) {
         const int regs = ((fa.numRegs > 0 ? fa.numRegs : 255) + 7) & ~7;
-        const int by_regs = 65536 / (regs * NT);
+        const int by_regs = 65536 / (regs * nt);
         const int by_smem = int((228u * 1024u) / (smem + fa.sharedSizeBytes + 1024u));
-        nb = std::max(1, std::min(std::min(by_regs, by_smem), std::min(2048 / NT, 32)));
+        nb = std::max(1, std::min(std::min(by_regs, by_smem), std::min(2048 / nt, 32)));
     }
     cache[smem] = nb;
     return nb;
@@ -105,7 +115,8 @@ void launch_pass_ku(dim3 grid, size_t smem, cudaStream_t s, float2 *wv, uint32_t
     const uint64_t ntiles = uint64_t(grid.x) * grid.y;
     const uint64_t resident = 2ull * uint64_t(pass_blocks_per_sm<KMAX, PREC, UM>(smem)) * num_sms();
     const uint32_t nctas = uint32_t(ntiles < resident ? ntiles : resident);
-    k_pass<KMAX, PREC, UM><<<nctas, NT, smem, s>>>(wv, W, ntiles, P, blob, mats, bfr, gbase, ctr, status);
+    k_pass<KMAX, PREC, UM><<<nctas, pass_threads<KMAX, PREC, UM>(), smem, s>>>(wv, W, ntiles, P, blob, mats, bfr,
+                                                                              gbase, ctr, status);
 }
 
 template <int KMAX, int PREC>

@@ -634,11 +634,10 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                     for (uint32_t i = tid; i < D * D; i += NT) mat[i] = mats[op.mat + i];
             }
             if (op.dlut != kNoTab) {
+                // read in place from the staged blob (shared memory for the whole pass): no copy, no barrier
                 const uint32_t *ht = reinterpret_cast<const uint32_t *>(blob) + op.dlut;
-                for (uint32_t x = tid; x < 128 + D; x += NT) {
-                    if (x < 128) S.cb[x >> 6][x & 63u] = ht[x];
-                    else S.offs_sw[x - 128] = ht[x];
-                }
+                cb = ht;
+                osw = ht + 128;
             } else {
                 if (tid < int(D)) {
                     uint32_t o = 0;
@@ -654,19 +653,27 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                     S.cb[half][v] = swz(b);
                 }
             }
-            __syncthreads();
+            if (op.dlut == kNoTab || !tc) __syncthreads();  // tables built above, or the matrix area filled
             if constexpr (UM) {
                 if (um) {
-                    const bool done =
-                        PREC == QSIM_PREC_BF16X3
-                            ? apply_dense_umma3<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status)
-                            : apply_dense_umma<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status);
+                    bool done;
+                    if constexpr (PREC == QSIM_PREC_BF16X3)
+                        done = apply_dense_umma3<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status);
+                    else
+                        done = apply_dense_umma<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status);
                     if (!done) return false;
                     oi += adv;
                     continue;
                 }
             }
-            if constexpr (KMAX >= 1) apply_dense_dispatch<NT, KMAX, PREC>(k, tile, M, bfr + op.bfrag, cb, osw, T);
+            if constexpr (UM) {
+                // a tcgen05 pass (T = 12) runs every dense op of width 3 to 5 above (widths 3 and 4 come widened
+                // to 5); what is left here is width 1, 2 or 6 on CUDA cores, so no other dense form is compiled in
+                if (k <= 2) apply_dense_dispatch<NT, 2, PREC>(k, tile, M, bfr + op.bfrag, cb, osw, T);
+                else if constexpr (KMAX >= 6) apply_dense<NT, 6>(tile, M, cb, osw, T);
+            } else if constexpr (KMAX >= 1) {
+                apply_dense_dispatch<NT, KMAX, PREC>(k, tile, M, bfr + op.bfrag, cb, osw, T);
+            }
         } else if (type == OP_DIAG) {
             // a run of r diagonal ops in one sweep; op d's phase index = bits constant over the
             // tile | lookups over the tile bits 0..6 and 7..12
