@@ -107,8 +107,9 @@ typedef struct qsim_config {
                                 first stage's second phase waits for a count that is never
                                 reached, so the run ends with QSIM_E_TIMEOUT after the
                                 bounded wait (0.2 s) instead of hanging; bit 1 likewise for
-                                the tcgen05 dense ops: their MMAs are not committed to the
-                                mbarrier, so each tile's wait runs out after 1 s */
+                                the tcgen05 dense ops: their MMAs are neither issued nor
+                                committed to the mbarrier, so each tile's wait runs out after
+                                1 s with no MMA in flight */
 } qsim_config;
 
 /* Fill *cfg with defaults: m 20, inner 2, k 4, FP32, streams mode, 2 streams,

@@ -540,8 +540,8 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                 Op wide;
                 const Op *opp = &st.ops[oi];
                 if (opp->type == OP_DENSE && (opp->k == 3 || opp->k == 4) && ps.T == 12 && p->cfg.tcgen05 &&
-                    p->cfg.mode == QSIM_MODE_STREAMS &&
-                    (p->cfg.prec == QSIM_PREC_TF32 || p->cfg.prec == QSIM_PREC_BF16X3)) {
+                    (p->cfg.prec == QSIM_PREC_TF32 ||
+                     (p->cfg.prec == QSIM_PREC_BF16X3 && p->cfg.mode == QSIM_MODE_STREAMS))) {
                     wide = widen_dense(*opp, ps, 5);
                     opp = &wide;
                 }
@@ -559,29 +559,35 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                     const uint32_t min_k = p->cfg.prec == QSIM_PREC_TF32 ? 3u : 4u;
                     // k = 5 TF32 ops of the stream engine's 4096-amplitude passes on tcgen05 when asked for
                     // (one thread per index group: the complement ordered for that gather)
-                    const bool um = p->cfg.tcgen05 &&
-                                    (p->cfg.prec == QSIM_PREC_TF32 || p->cfg.prec == QSIM_PREC_BF16X3) &&
-                                    op.k == 5 && ps.T == 12 && p->cfg.mode == QSIM_MODE_STREAMS;
+                    const bool um6 = p->cfg.tcgen05 && p->cfg.prec == QSIM_PREC_TF32 && op.k == 6 && ps.T == 12 &&
+                                     p->cfg.mode == QSIM_MODE_STREAMS;
+                    // width 5 (and the widened 3 and 4): TF32 in both modes, split BF16 in streams mode (its form
+                    // needs the stream engine's 128-thread CTAs); width 6: TF32 in streams mode
+                    const bool um = um6 || (p->cfg.tcgen05 && op.k == 5 && ps.T == 12 &&
+                                            (p->cfg.prec == QSIM_PREC_TF32 ||
+                                             (p->cfg.prec == QSIM_PREC_BF16X3 && p->cfg.mode == QSIM_MODE_STREAMS)));
                     order_complement(od, ps.T,
                                      !um && p->cfg.prec != QSIM_PREC_FP32 && op.k >= min_k && op.k <= 5 &&
                                          ps.T == 12);
                     od.mat = mats.size();
                     for (const cd &v : op.u) mats.push_back(make_float2(float(v.real()), float(v.imag())));
                     P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << (2 * op.k));
-                    if (p->cfg.prec != QSIM_PREC_FP32 && op.k >= 3 && op.k <= 5) {
+                    if (p->cfg.prec != QSIM_PREC_FP32 && ((op.k >= 3 && op.k <= 5) || um6)) {
                         bfr.resize((bfr.size() + 3) & ~size_t(3));  // 16-byte aligned tables
                         od.bfrag = bfr.size();
                         bfr.resize(bfr.size() + bfrag_words(op.k, int(p->cfg.prec)));
-                        if (um && p->cfg.prec == QSIM_PREC_BF16X3)
+                        if (um6)
+                            build_umma_b6(reinterpret_cast<const double *>(op.u.data()), bfr.data() + od.bfrag);
+                        else if (um && p->cfg.prec == QSIM_PREC_BF16X3)
                             build_umma_b3(reinterpret_cast<const double *>(op.u.data()), bfr.data() + od.bfrag);
                         else if (um)
                             build_umma_b(reinterpret_cast<const double *>(op.u.data()), bfr.data() + od.bfrag);
                         else
                             build_bfrag_table(reinterpret_cast<const double *>(op.u.data()), op.k, int(p->cfg.prec),
                                               bfr.data() + od.bfrag);
-                        if (um)  // bit 1: wait-limit test hook; bit 2: split-BF16 operands
-                            P.umma = 1u | ((p->cfg.reserved[0] & 2) ? 2u : 0u) |
-                                     (p->cfg.prec == QSIM_PREC_BF16X3 ? 4u : 0u);
+                        if (um)  // bit 1: wait-limit test hook; bit 2: split-BF16 operands; bit 3: a width-6 op
+                            P.umma |= 1u | ((p->cfg.reserved[0] & 2) ? 2u : 0u) |
+                                      (p->cfg.prec == QSIM_PREC_BF16X3 ? 4u : 0u) | (um6 ? 8u : 0u);
                     }
                     P.kmax = std::max<uint32_t>(P.kmax, op.k);
                 } else if (op.type == OP_CSEP) {
@@ -716,13 +722,15 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                         od.ncst = uint32_t(recs.size() / 5);
                         for (const float2 &f : recs) put(f);
                     } else if (od.type == OP_DENSE) {
-                        const bool tc = p->cfg.prec != QSIM_PREC_FP32 && od.k >= min_k && od.k <= 5 && ps.T == 12;
+                        const bool tc6 = od.k == 6 && (P.umma & 8u) && p->cfg.prec == QSIM_PREC_TF32;
+                        const bool tc = (p->cfg.prec != QSIM_PREC_FP32 && od.k >= min_k && od.k <= 5 && ps.T == 12) ||
+                                        tc6;
                         if (tc) {
                             // swizzled tile offsets of the op's index groups (128 words: the group bits 0..5 and
-                            // 6.. through the complement) and of its matrix columns (32 words), read by the
+                            // 6.. through the complement) and of its matrix columns (2^k words), read by the
                             // tensor-core forms in place of a per-tile set-up
                             auto swz = [](uint32_t i) { return i ^ (((i >> 4) ^ (i >> 8) ^ (i >> 12)) & 15u); };
-                            uint32_t t[160] = {};
+                            uint32_t t[192] = {};
                             const uint32_t nc = ps.T - od.k;
                             for (uint32_t x = 0; x < 128; ++x) {
                                 const uint32_t half = x >> 6, v = x & 63u;
@@ -739,7 +747,7 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                             align16();
                             od.dlut = uint32_t(pb.size() / 4);
                             const uint8_t *tb = reinterpret_cast<const uint8_t *>(t);
-                            pb.insert(pb.end(), tb, tb + sizeof(t));
+                            pb.insert(pb.end(), tb, tb + 4 * (128 + (1u << od.k)));
                             continue;
                         }
                         const size_t mb = size_t(8) << (2 * od.k);
@@ -1165,16 +1173,21 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
 
     uint64_t total_groups = 0;
     size_t max_pass_bytes = 0;
+    bool um_any = false;  // tcgen05 passes in the launch (TF32): the kernel holds TMEM and an MMA mbarrier
     for (const SegRef &sr : order) {
         const RunCtx &R = *rs[sr.c];
         const StageDev &sd = R.pd->stages[sr.si];
         total_groups += sd.ngroups;
         for (const PassDev &ps : sd.passes_host) {
             max_pass_bytes = std::max(max_pass_bytes, (size_t(1) << ps.T) * sizeof(float2) + size_t(ps.blob_words) * 16 +
-                                                          size_t(ps.mat_elems) * sizeof(float2));
+                                                          size_t(ps.mat_elems) * sizeof(float2) +
+                                                          umma_pass_smem(ps.umma));
+            um_any |= (ps.umma & 1u) != 0;
             if (ps.kmax > 5) return set_error(QSIM_E_INVALID, "persistent mode fuses at most k = 5 qubits");
         }
     }
+    if (um_any && prec != QSIM_PREC_TF32)
+        return set_error(QSIM_E_INVALID, "internal: tcgen05 passes in the persistent kernel need TF32");
     std::vector<std::unique_ptr<PBlockBufs>> bb(rs.size());
     int rc;
     for (size_t c = 0; c < rs.size(); ++c) {
@@ -1365,7 +1378,7 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
     }
     CUDA_TRY(cudaMemcpyAsync(dsegs.p, segs.data(), nseg * sizeof(PSeg), cudaMemcpyHostToDevice, main));
     const size_t smem = persistent_smem_bytes(max_pass_bytes);
-    if ((rc = prepare_stage_persistent(prec, smem, rel))) return set_error(rc, "persistent kernel set-up failed");
+    if ((rc = prepare_stage_persistent(prec, smem, rel, um_any))) return set_error(rc, "persistent kernel set-up failed");
 
     PLaunch L{};
     L.wv = wv.p;
@@ -1417,7 +1430,7 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         L.done = sync.p + seg_group_off[k0] * kMaxPhases;
         L.arrive = sync.p + (total_groups + seg_group_off[k0]) * kMaxPhases;
         prof.begin(P_STAGE, cs);
-        rc = launch_stage_persistent(L, prec, smem, cs, nullptr, rel);
+        rc = launch_stage_persistent(L, prec, smem, cs, nullptr, rel, um_any);
         prof.end(cs);
         if (rc) {
             end_capture_on_error();

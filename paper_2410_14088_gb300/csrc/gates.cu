@@ -220,10 +220,12 @@ void build_bfrag_table(const double *u, uint32_t k, int prec, uint32_t *out) {
             }
 }
 
+size_t umma_pass_smem(uint32_t umma_bits) {
+    return (umma_bits & 1u) ? size_t(umma_pass_b_bytes(umma_bits)) + 1024 : 0;
+}
+
 size_t pass_smem_bytes(const PassDev &P) {
-    const size_t um = (P.umma & 1u) ? size_t((P.umma & 4u) ? umma_b_bytes<QSIM_PREC_BF16X3>()
-                                                              : umma_b_bytes<QSIM_PREC_TF32>()) + 1024
-                                    : 0;
+    const size_t um = umma_pass_smem(P.umma);
     return (size_t(1) << P.T) * sizeof(float2) + um + size_t(P.blob_words) * 16 +
            size_t(P.mat_elems) * sizeof(float2);
 }
@@ -237,6 +239,19 @@ void build_umma_b(const double *u, uint32_t *out) {
             const double v = n < D ? (kk < D ? re : -im) : (kk < D ? im : re);
             const uint32_t a = kk / 32, ch = (kk % 32) / 4, w = kk % 4;
             const size_t byte = size_t(a) * 8192 + (n / 8) * 1024 + (n % 8) * 128 + ((ch ^ (n % 8)) * 16) + w * 4;
+            out[byte / 4] = to_tf32(float(v));
+        }
+}
+
+void build_umma_b6(const double *u, uint32_t *out) {
+    constexpr uint32_t D = 64;
+    for (uint32_t n = 0; n < 2 * D; ++n)
+        for (uint32_t kk = 0; kk < 2 * D; ++kk) {
+            const uint32_t r = n % D, c = kk % D;
+            const double re = u[2 * (size_t(r) * D + c)], im = u[2 * (size_t(r) * D + c) + 1];
+            const double v = n < D ? (kk < D ? re : -im) : (kk < D ? im : re);
+            const uint32_t a = kk / 32, ch = (kk % 32) / 4, w = kk % 4;
+            const size_t byte = size_t(a) * 16384 + (n / 8) * 1024 + (n % 8) * 128 + ((ch ^ (n % 8)) * 16) + w * 4;
             out[byte / 4] = to_tf32(float(v));
         }
 }

@@ -22,8 +22,9 @@ struct PassDev {
     uint32_t blob_words;     // 16-byte words of the pass blob: op descriptors, phase tables, small matrices
     uint32_t blob_off;       // its first word in the plan's blob array
     uint32_t umma;           // bit 0: the pass's k = 5 TF32 dense ops run on tcgen05 (B operands in 128-byte
-                             // swizzled form); bit 1: test hook, the MMAs are not committed to the mbarrier;
-                             // bit 2: split-BF16 B operands (three parts, 24 KB)
+                             // swizzled form); bit 1: test hook, no MMA is issued or committed to the mbarrier;
+                             // bit 2: split-BF16 B operands (three parts, 24 KB); bit 3: a TF32 width-6 op
+                             // (B operand 64 KB, 128 TMEM columns)
     uint64_t out_mask;       // working-index mask of the non-tile bits
     uint32_t tile_pos[16];   // working bit of tile bit t (ascending)
     uint32_t out_pos[32];    // working bit of CTA-index bit t
@@ -77,7 +78,13 @@ size_t bfrag_words(uint32_t k, int prec);
 // B^T = U_r rounded to TF32, row n = output n (Re outputs 0..31, then Im), column = input (Re inputs, then
 // Im), K-major in the 128-byte swizzled layout: column block a = input / 32 at byte 8192 a, row n at
 // 1024 (n / 8) + 128 (n % 8), 16-byte chunk c = (input % 32) / 4 stored at chunk position c ^ (n % 8).
+// Shared memory a tcgen05 pass adds (its B buffer and 1024 bytes of alignment slack) from PassDev::umma; 0 for
+// a pass without tcgen05 ops.
+size_t umma_pass_smem(uint32_t umma_bits);
 void build_umma_b(const double *u_interleaved, uint32_t *out);
+// The TF32 B operand of a width-6 op for tcgen05 (16384 words, 64 KB): U_r^T (128 x 128) K-major in four 128-byte
+// K-chunks of 128 rows (16 KB each, chunk a holding inputs 32a .. 32a + 31), rows n swizzled as in build_umma_b.
+void build_umma_b6(const double *u_interleaved, uint32_t *out);
 // The split-BF16 form (6144 words, the count of its warp-MMA fragment table): three 8 KB parts hi, mid, lo of
 // U_r (x = hi + mid + lo, each rounded to BF16 nearest-even), each part 64 rows of 64 BF16 inputs in the same
 // swizzled layout (row n at 1024 (n / 8) + 128 (n % 8), 16-byte chunk c = input / 8 at position c ^ (n % 8)).

@@ -277,7 +277,13 @@ template <int PREC>
 __host__ __device__ constexpr uint32_t umma_b_bytes() {
     return PREC == QSIM_PREC_BF16X3 ? 24576u : 16384u;
 }
+// B buffer of a tcgen05 pass from its PassDev::umma bits: 64 KB with a width-6 op, else the width-5 operand's size
+__host__ __device__ constexpr uint32_t umma_pass_b_bytes(uint32_t umma_bits) {
+    return (umma_bits & 8u) ? 65536u : (umma_bits & 4u) ? umma_b_bytes<QSIM_PREC_BF16X3>() : umma_b_bytes<QSIM_PREC_TF32>();
+}
+__host__ __device__ constexpr uint32_t umma_pass_tmem_cols(uint32_t umma_bits) { return (umma_bits & 8u) ? 128u : 64u; }
 constexpr uint32_t kUmmaIdesc = umma::idesc_tf32(128, 64);
+constexpr uint32_t kUmmaIdesc6 = umma::idesc_tf32(128, 128);
 constexpr uint32_t kUmmaIdescBf16 = umma::idesc_bf16(128, 64);
 constexpr uint64_t kUmmaWaitNs = 1000000000ull;  // bound on one MMA-completion wait
 
@@ -285,7 +291,8 @@ constexpr uint64_t kUmmaWaitNs = 1000000000ull;  // bound on one MMA-completion 
 // outcome is made uniform so that every thread takes the same path. False (status set) when the wait ran out.
 __device__ __forceinline__ bool umma_commit_wait(const PassSmem &S, uint32_t &phase, int *status) {
     const uint32_t bar = umma::smem_addr(&S.mbar);
-    if (threadIdx.x == 0 && !(S.p.umma & 2u)) umma::commit(bar);  // test hook: no arrival, the wait runs out
+    // test hook (bit 1): no MMA was issued and nothing is committed, so the wait runs out with no MMA in flight
+    if (threadIdx.x == 0 && !(S.p.umma & 2u)) umma::commit(bar);
     const bool ok = __syncthreads_and(umma::mbar_wait(bar, phase, kUmmaWaitNs));
     phase ^= 1u;
     if (!ok && threadIdx.x == 0) raise_status(status, QSIM_E_TIMEOUT);
@@ -318,6 +325,63 @@ __device__ __forceinline__ void umma_epilogue(float2 *tile, uint32_t base, const
 template <int NT>
 __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, const uint32_t *cb, const uint32_t *osw,
                                                  const PassSmem &S, uint32_t &phase,
+                                                 int *status);
+
+// The TF32 op for 256-thread CTAs (the persistent stage kernel): threads g and g + 128 share index group g, each
+// gathering, writing into A and taking back from TMEM 16 of the group's 32 amplitudes; warps w and w + 4 read
+// the same TMEM lanes (w's quarter of the 128 rows) in different columns. The MMAs are those of the 128-thread
+// form, so both give the same results bit for bit.
+template <>
+__device__ __forceinline__ bool apply_dense_umma<256>(float2 *tile, uint32_t bsm, const uint32_t *cb,
+                                                      const uint32_t *osw, const PassSmem &S, uint32_t &phase,
+                                                      int *status) {
+    const uint32_t g = threadIdx.x & 127u, h = threadIdx.x >> 7;  // group, half (amplitudes 16h .. 16h + 15)
+    const uint32_t base = cb[g & 63u] ^ cb[64u + (g >> 6)];
+    uint32_t re[16], im[16];
+#pragma unroll
+    for (uint32_t j = 0; j < 16; ++j) {
+        const float2 v = tile[base ^ osw[16u * h + j]];
+        re[j] = f32_to_tf32(v.x);
+        im[j] = f32_to_tf32(v.y);
+    }
+    __syncthreads();  // every amplitude of the tile is in registers
+    uint8_t *arow = reinterpret_cast<uint8_t *>(tile) + (g >> 3) * 1024u + (g & 7u) * 128u;
+#pragma unroll
+    for (uint32_t cc = 0; cc < 4; ++cc) {  // 16-byte chunks 4h .. 4h + 3 of the Re and Im halves of the row
+        const uint32_t o = ((4u * h + cc) ^ (g & 7u)) << 4;
+        *reinterpret_cast<uint4 *>(arow + o) = make_uint4(re[4 * cc], re[4 * cc + 1], re[4 * cc + 2], re[4 * cc + 3]);
+        *reinterpret_cast<uint4 *>(arow + 16384u + o) =
+            make_uint4(im[4 * cc], im[4 * cc + 1], im[4 * cc + 2], im[4 * cc + 3]);
+    }
+    cp_async_wait_all();  // this thread's share of B
+    umma::fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0 && !(S.p.umma & 2u)) {  // the test hook issues nothing
+        umma::fence_after_sync();
+        const uint32_t a0 = umma::smem_addr(tile);
+#pragma unroll
+        for (uint32_t s = 0; s < 8; ++s) {
+            const uint64_t da = umma::desc_kmajor_sw128(a0 + (s >> 2) * 16384u + (s & 3u) * 32u);
+            const uint64_t db = umma::desc_kmajor_sw128(bsm + (s >> 2) * 8192u + (s & 3u) * 32u);
+            umma::mma_tf32_ss(S.tmem, da, db, kUmmaIdesc, s);
+        }
+    }
+    if (!umma_commit_wait(S, phase, status)) return false;
+    umma::fence_after_sync();
+    const uint32_t taddr = S.tmem + ((32u * ((threadIdx.x >> 5) & 3u)) << 16) + 16u * h;
+    uint32_t dre[16], dim[16];
+    umma::tmem_ld16(taddr, dre);
+    umma::tmem_ld16(taddr + 32u, dim);
+#pragma unroll
+    for (uint32_t j = 0; j < 16; ++j)
+        tile[base ^ osw[16u * h + j]] = make_float2(__uint_as_float(dre[j]), __uint_as_float(dim[j]));
+    umma::fence_before_sync();  // the next op's barrier orders these TMEM reads before its MMAs
+    return true;
+}
+
+template <int NT>
+__device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, const uint32_t *cb, const uint32_t *osw,
+                                                 const PassSmem &S, uint32_t &phase,
                                                  int *status) {
     static_assert(NT == 128, "one thread per index group");
     const uint32_t g = threadIdx.x;
@@ -341,7 +405,7 @@ __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, con
     cp_async_wait_all();  // this thread's share of B
     umma::fence_proxy_async_smem();
     __syncthreads();
-    if (g == 0) {
+    if (g == 0 && !(S.p.umma & 2u)) {  // the test hook issues nothing
         umma::fence_after_sync();
         const uint32_t a0 = umma::smem_addr(tile);
 #pragma unroll
@@ -353,6 +417,69 @@ __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, con
     }
     if (!umma_commit_wait(S, phase, status)) return false;
     umma_epilogue(tile, base, osw, S);
+    return true;
+}
+
+// Dense op of width 6 (TF32) on a 4096-amplitude tile with tcgen05: 64 index groups, K = 128 inputs (Re parts of
+// the group's 64 amplitudes, then Im parts) in four 128-byte K-chunks of 8 KB (64 rows each), N = 128 outputs, B
+// (64 KB, from build_umma_b6) at `bsm`. Threads g and g + 64 share group g, each gathering 32 of its amplitudes
+// into K-chunks h and 2 + h. The MMAs run at M = 128: the descriptor's rows 64..127 read the next K-chunk (the
+// last one's read the B buffer after the tile), valid shared memory whose results land in TMEM lanes 64..127 and
+// are never read. Warps 0 and 1 (TMEM lanes 0..63) take the 64 rows of D back, two halves of 32 outputs each.
+template <int NT>
+__device__ __forceinline__ bool apply_dense_umma6(float2 *tile, uint32_t bsm, const uint32_t *cb, const uint32_t *osw,
+                                                  const PassSmem &S, uint32_t &phase, int *status) {
+    static_assert(NT == 128, "two threads per index group");
+    const uint32_t g = threadIdx.x & 63u, h = threadIdx.x >> 6;
+    const uint32_t base = cb[g] ^ cb[64];
+    {
+        uint32_t re[32], im[32];
+#pragma unroll
+        for (uint32_t j = 0; j < 32; ++j) {
+            const float2 v = tile[base ^ osw[32u * h + j]];
+            re[j] = f32_to_tf32(v.x);
+            im[j] = f32_to_tf32(v.y);
+        }
+        __syncthreads();  // every amplitude of the tile is in registers
+        uint8_t *row = reinterpret_cast<uint8_t *>(tile) + (g >> 3) * 1024u + (g & 7u) * 128u;
+#pragma unroll
+        for (uint32_t c = 0; c < 8; ++c) {
+            const uint32_t o = (c ^ (g & 7u)) << 4;
+            *reinterpret_cast<uint4 *>(row + h * 8192u + o) =
+                make_uint4(re[4 * c], re[4 * c + 1], re[4 * c + 2], re[4 * c + 3]);
+            *reinterpret_cast<uint4 *>(row + (2u + h) * 8192u + o) =
+                make_uint4(im[4 * c], im[4 * c + 1], im[4 * c + 2], im[4 * c + 3]);
+        }
+    }
+    cp_async_wait_all();  // this thread's share of B
+    umma::fence_proxy_async_smem();
+    __syncthreads();
+    if (threadIdx.x == 0 && !(S.p.umma & 2u)) {  // the test hook issues nothing
+        umma::fence_after_sync();
+        const uint32_t a0 = umma::smem_addr(tile);
+#pragma unroll
+        for (uint32_t s = 0; s < 16; ++s) {
+            const uint64_t da = umma::desc_kmajor_sw128(a0 + (s >> 2) * 8192u + (s & 3u) * 32u);
+            const uint64_t db = umma::desc_kmajor_sw128(bsm + (s >> 2) * 16384u + (s & 3u) * 32u);
+            umma::mma_tf32_ss(S.tmem, da, db, kUmmaIdesc6, s);
+        }
+    }
+    if (!umma_commit_wait(S, phase, status)) return false;
+    umma::fence_after_sync();
+    if (threadIdx.x < 64) {
+        // row g = threadIdx.x of D: Re of output j in column j, Im in column 64 + j
+        const uint32_t taddr = S.tmem + ((32u * (threadIdx.x >> 5)) << 16);
+#pragma unroll
+        for (uint32_t half = 0; half < 2; ++half) {
+            uint32_t re[32], im[32];
+            umma::tmem_ld32(taddr + 32u * half, re);
+            umma::tmem_ld32(taddr + 64u + 32u * half, im);
+#pragma unroll
+            for (uint32_t j = 0; j < 32; ++j)
+                tile[base ^ osw[32u * half + j]] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+        }
+    }
+    umma::fence_before_sync();  // the next op's barrier orders these TMEM reads before its MMAs
     return true;
 }
 
@@ -406,7 +533,7 @@ __device__ __forceinline__ bool apply_dense_umma3(float2 *tile, uint32_t bsm, co
             umma::mma_bf16_ss(S.tmem, da, db, kUmmaIdescBf16, first && s == 0 ? 0u : 1u);
         }
     };
-    if (g == 0) {
+    if (g == 0 && !(S.p.umma & 2u)) {  // the test hook issues nothing
         umma::fence_after_sync();
         product(1, 0, 1);  // lo x B_hi (the first product overwrites D)
         product(0, 2, 0);  // hi x B_lo
@@ -420,7 +547,7 @@ __device__ __forceinline__ bool apply_dense_umma3(float2 *tile, uint32_t bsm, co
     }
     umma::fence_proxy_async_smem();
     __syncthreads();
-    if (g == 0) {
+    if (g == 0 && !(S.p.umma & 2u)) {
         umma::fence_after_sync();
         product(1, 1, 0);  // mid x B_mid
         product(1, 0, 0);  // mid x B_hi
@@ -614,13 +741,17 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
         if (type == OP_DENSE) {
             const uint32_t D = 1u << k;
             // the tensor-core form reads the op's B-fragment table; the CUDA-core form its matrix
-            const bool tc = PREC != QSIM_PREC_FP32 && k >= (PREC == QSIM_PREC_TF32 ? 3u : 4u) && k <= 5 && T == 12;
+            // width 6 runs on tcgen05 too in TF32 passes that carry one (PassDev::umma bit 3)
+            const bool um6 = UM && PREC == QSIM_PREC_TF32 && k == 6 && T == 12 && (S.p.umma & 8u);
+            const bool tc =
+                (PREC != QSIM_PREC_FP32 && k >= (PREC == QSIM_PREC_TF32 ? 3u : 4u) && k <= 5 && T == 12) || um6;
             bool um = false;  // on tcgen05: stage the op's B operand now, under the set-up below
             if constexpr (UM) {
-                um = S.p.umma && k == 5 && T == 12;
+                um = S.p.umma && (k == 5 || um6) && T == 12;
                 if (um && !b_resident) {
                     const uint4 *src = reinterpret_cast<const uint4 *>(bfr + op.bfrag);
-                    for (uint32_t t = tid; t < umma_b_bytes<PREC>() / 16; t += NT) cp_async16(bbuf + t, src + t);
+                    const uint32_t bw = (k == 6 ? 65536u : umma_b_bytes<PREC>()) / 16;
+                    for (uint32_t t = tid; t < bw; t += NT) cp_async16(bbuf + t, src + t);
                     cp_async_commit();
                 }
             }
@@ -659,6 +790,12 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                     bool done;
                     if constexpr (PREC == QSIM_PREC_BF16X3)
                         done = apply_dense_umma3<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status);
+                    else if (k == 6) {
+                        if constexpr (NT == 128)
+                            done = apply_dense_umma6<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status);
+                        else
+                            done = false;  // not uploaded for 256-thread kernels
+                    }
                     else
                         done = apply_dense_umma<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status);
                     if (!done) return false;
@@ -668,7 +805,8 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
             }
             if constexpr (UM) {
                 // a tcgen05 pass (T = 12) runs every dense op of width 3 to 5 above (widths 3 and 4 come widened
-                // to 5); what is left here is width 1, 2 or 6 on CUDA cores, so no other dense form is compiled in
+                // to 5), and width 6 in TF32; what is left here is width 1 or 2, or 6 in split BF16, on CUDA cores,
+                // so no other dense form is compiled in
                 if (k <= 2) apply_dense_dispatch<NT, 2, PREC>(k, tile, M, bfr + op.bfrag, cb, osw, T);
                 else if constexpr (KMAX >= 6) apply_dense<NT, 6>(tile, M, cb, osw, T);
             } else if constexpr (KMAX >= 1) {
@@ -811,16 +949,20 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
 // then matrix area), apply the pass's ops, store the tile back. CG selects
 // L2-only loads, needed when the working vector was written by other CTAs of
 // the same launch (the persistent stage kernel).
+// With phase_io the caller owns the TMEM accumulator (S.tmem, 64 columns) and the MMA mbarrier (S.mbar) across
+// calls and keeps the mbarrier's phase parity in *phase_io; returns false when an MMA wait ran out.
 template <int NT, int KMAX, int PREC, bool CG, bool UM = false>
-__device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev &pd, const uint4 *__restrict__ gblob,
+__device__ __forceinline__ bool pass_tile(float2 *__restrict__ g, const PassDev &pd, const uint4 *__restrict__ gblob,
                                           const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr,
-                                          uint64_t cta, uint64_t gb, PassSmem &S, float2 *dyn, int *status) {
-    pass_setup<NT>(pd, S);
+                                          uint64_t cta, uint64_t gb, PassSmem &S, float2 *dyn, int *status,
+                                          uint32_t *phase_io = nullptr) {
+    pass_setup<NT>(pd, S);  // copies the descriptor only: a caller-owned S.tmem and S.mbar stay as they are
     const uint32_t T = S.p.T;
     // passes with tcgen05 dense ops: the tile 1024-byte aligned (it is the A operand while the MMAs run),
     // the B operand after it, then the blob; 64 TMEM columns hold the accumulator
-    static_assert(!UM || ((PREC == QSIM_PREC_TF32 || PREC == QSIM_PREC_BF16X3) && NT == 128 && KMAX >= 5),
-                  "tcgen05 passes: TF32 or split BF16, k = 5");
+    static_assert(!UM || (((PREC == QSIM_PREC_TF32 && (NT == 128 || NT == 256)) ||
+                           (PREC == QSIM_PREC_BF16X3 && NT == 128)) && KMAX >= 5),
+                  "tcgen05 passes: TF32 (128 or 256 threads) or split BF16 (128 threads), k = 5");
     bool um = false;
     if constexpr (UM) um = S.p.umma != 0;
     float2 *tile = dyn;
@@ -829,20 +971,26 @@ __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev 
         const uint32_t pad = (1024u - (umma::smem_addr(dyn) & 1023u)) & 1023u;
         tile = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(dyn) + pad);
         bbuf = reinterpret_cast<uint4 *>(tile + 4096);
-        if (threadIdx.x < 32) umma::tmem_alloc(umma::smem_addr(&S.tmem), 64);
-        if (threadIdx.x == 0) umma::mbar_init(umma::smem_addr(&S.mbar), 1);
+        if (!phase_io) {
+            if (threadIdx.x < 32) umma::tmem_alloc(umma::smem_addr(&S.tmem), umma_pass_tmem_cols(S.p.umma));
+            if (threadIdx.x == 0) umma::mbar_init(umma::smem_addr(&S.mbar), 1);
+        }
         umma::fence_before_sync();
     }
-    uint4 *blob = reinterpret_cast<uint4 *>(tile + (1u << T)) + (um ? umma_b_bytes<PREC>() / 16 : 0u);
+    uint4 *blob = reinterpret_cast<uint4 *>(tile + (1u << T)) + (um ? umma_pass_b_bytes(S.p.umma) / 16 : 0u);
     float2 *mat = reinterpret_cast<float2 *>(blob + S.p.blob_words);
     const uint64_t base = tile_base(S, cta);
     blob_load<NT>(gblob + S.p.blob_off, S.p.blob_words, blob);
     tile_load<NT, CG>(g, base, S, tile);
     cp_async_wait_all();
-    uint32_t phase = 0;
+    uint32_t phase = phase_io ? *phase_io : 0u;
     const bool ok = tile_ops<NT, KMAX, PREC, UM>(tile, blob, mat, mats, bfr, base, gb, S, bbuf, status, phase);
     __syncthreads();
     tile_store<NT>(g, base, S, tile);
+    if (phase_io) {
+        *phase_io = phase;
+        return ok;
+    }
     if (um) {
         // after a wait that ran out, wait (bounded) once more for the MMAs in flight before freeing TMEM
         if (!ok) umma::mbar_wait(umma::smem_addr(&S.mbar), phase ^ 1u, kUmmaWaitNs);
@@ -850,9 +998,10 @@ __device__ __forceinline__ void pass_tile(float2 *__restrict__ g, const PassDev 
         __syncthreads();
         if (threadIdx.x < 32) {
             umma::fence_after_sync();
-            umma::tmem_dealloc(S.tmem, 64);
+            umma::tmem_dealloc(S.tmem, umma_pass_tmem_cols(S.p.umma));
         }
     }
+    return ok;
 }
 
 // One pass over many tiles (streams mode): CTA c takes tiles c, c + gridDim.x, ... of the launch's groups
@@ -881,11 +1030,11 @@ __device__ __forceinline__ void pass_tiles(float2 *__restrict__ wv, uint32_t W, 
         const uint32_t pad = (1024u - (umma::smem_addr(dyn) & 1023u)) & 1023u;
         tile = reinterpret_cast<float2 *>(reinterpret_cast<uint8_t *>(dyn) + pad);
         bbuf = reinterpret_cast<uint4 *>(tile + 4096);
-        if (threadIdx.x < 32) umma::tmem_alloc(umma::smem_addr(&S.tmem), 64);
+        if (threadIdx.x < 32) umma::tmem_alloc(umma::smem_addr(&S.tmem), umma_pass_tmem_cols(S.p.umma));
         if (threadIdx.x == 0) umma::mbar_init(umma::smem_addr(&S.mbar), 1);
         umma::fence_before_sync();
     }
-    uint4 *blob = reinterpret_cast<uint4 *>(tile + (1u << T)) + (um ? umma_b_bytes<PREC>() / 16 : 0u);
+    uint4 *blob = reinterpret_cast<uint4 *>(tile + (1u << T)) + (um ? umma_pass_b_bytes(S.p.umma) / 16 : 0u);
     float2 *mat = reinterpret_cast<float2 *>(blob + S.p.blob_words);
     blob_load<NT>(gblob + S.p.blob_off, S.p.blob_words, blob);
     cp_async_wait_all();
@@ -896,13 +1045,15 @@ __device__ __forceinline__ void pass_tiles(float2 *__restrict__ wv, uint32_t W, 
         const OpDev *bops = reinterpret_cast<const OpDev *>(blob);
         uint32_t n5 = 0, first = 0;
         for (uint32_t oi = 0; oi < S.p.op_count; ++oi)
-            if (bops[oi].type == OP_DENSE && bops[oi].k == 5) {
+            if (bops[oi].type == OP_DENSE &&
+                (bops[oi].k == 5 || (bops[oi].k == 6 && PREC == QSIM_PREC_TF32 && (S.p.umma & 8u)))) {
                 if (!n5) first = oi;
                 ++n5;
             }
         if (n5 == 1) {
             const uint4 *src = reinterpret_cast<const uint4 *>(bfr + bops[first].bfrag);
-            for (uint32_t t = threadIdx.x; t < umma_b_bytes<PREC>() / 16; t += NT) cp_async16(bbuf + t, src + t);
+            const uint32_t bw = (bops[first].k == 6 ? 65536u : umma_b_bytes<PREC>()) / 16;
+            for (uint32_t t = threadIdx.x; t < bw; t += NT) cp_async16(bbuf + t, src + t);
             cp_async_commit();
             b_res = true;
         }
@@ -940,7 +1091,7 @@ __device__ __forceinline__ void pass_tiles(float2 *__restrict__ wv, uint32_t W, 
         __syncthreads();
         if (threadIdx.x < 32) {
             umma::fence_after_sync();
-            umma::tmem_dealloc(S.tmem, 64);
+            umma::tmem_dealloc(S.tmem, umma_pass_tmem_cols(S.p.umma));
         }
     }
 }

@@ -53,8 +53,9 @@ __device__ __forceinline__ EncTarget load_target(const EncTarget *t) {
     return r;
 }
 
-// REL: the relative-bound codec (QSZR) in the decode phase and the in-place exact phases
-template <int PREC, bool REL>
+// REL: the relative-bound codec (QSZR) in the decode phase and the in-place exact phases. UM: the plan's TF32
+// dense ops of width 3 to 5 run on tcgen05 (TMEM accumulator and MMA mbarrier held by each CTA for the launch).
+template <int PREC, bool REL, bool UM>
 __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
     extern __shared__ float4 dsm[];
     __shared__ gdev::PassSmem PS;
@@ -71,7 +72,15 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
         s_epoch = ld_relaxed_u32(L.ctr + 2) & cdev::kEpochMask;
         s_seg = ~0u;
     }
+    uint32_t mphase = 0;     // parity of the MMA mbarrier's next phase (UM)
+    bool mma_ok = true;      // false after an MMA wait ran out (then a last bounded wait before TMEM is freed)
+    if constexpr (UM) {
+        if (warp == 0) umma::tmem_alloc(umma::smem_addr(&PS.tmem), 64);
+        if (tid == 0) umma::mbar_init(umma::smem_addr(&PS.mbar), 1);
+        umma::fence_before_sync();
+    }
     __syncthreads();
+    if constexpr (UM) umma::fence_after_sync();
 
     while (true) {
         if (tid == 0) {
@@ -171,8 +180,14 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
                                                     uint64_t(jj) << S.m, gb);
             }
         } else if (type == PH_PASS) {
-            gdev::pass_tile<PT, 5, PREC, true>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr, i, gb, PS,
-                                               reinterpret_cast<float2 *>(dsm), L.status);
+            if constexpr (UM) {
+                mma_ok &= gdev::pass_tile<PT, 5, PREC, true, true>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr,
+                                                                   i, gb, PS, reinterpret_cast<float2 *>(dsm),
+                                                                   L.status, &mphase);
+            } else {
+                gdev::pass_tile<PT, 5, PREC, true>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr, i, gb, PS,
+                                                   reinterpret_cast<float2 *>(dsm), L.status);
+            }
         } else if (type == PH_SIZE) {
             const uint32_t jj = i / g.nframes, f = i % g.nframes;
             const uint32_t len = cdev::size_frame_cta<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g, S.e,
@@ -382,6 +397,16 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             }
         }
     }
+    if constexpr (UM) {
+        // after an MMA wait that ran out, wait (bounded) once more for that op's MMAs before TMEM is freed
+        if (!mma_ok) umma::mbar_wait(umma::smem_addr(&PS.mbar), mphase ^ 1u, gdev::kUmmaWaitNs);
+        umma::fence_before_sync();
+        __syncthreads();
+        if (warp == 0) {
+            umma::fence_after_sync();
+            umma::tmem_dealloc(PS.tmem, 64);
+        }
+    }
     // the last CTA out resets the queue and advances the look-back epoch
     if (tid == 0) {
         __threadfence();
@@ -394,58 +419,73 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
     }
 }
 
-template <int PREC, bool REL>
+template <int PREC, bool REL, bool UM>
 struct LaunchShape {
     static int grid;
     static size_t attr_smem;
 };
-template <int PREC, bool REL> int LaunchShape<PREC, REL>::grid = 0;
-template <int PREC, bool REL> size_t LaunchShape<PREC, REL>::attr_smem = 0;
+template <int PREC, bool REL, bool UM> int LaunchShape<PREC, REL, UM>::grid = 0;
+template <int PREC, bool REL, bool UM> size_t LaunchShape<PREC, REL, UM>::attr_smem = 0;
 
 // kernel attributes and the grid (one wave of resident CTAs); done outside any stream capture
-template <int PREC, bool REL>
+template <int PREC, bool REL, bool UM>
 int prepare_prec(size_t smem) {
-    using Shape = LaunchShape<PREC, REL>;
+    using Shape = LaunchShape<PREC, REL, UM>;
     if (Shape::attr_smem < smem) {
-        if (cudaFuncSetAttribute(k_stage_persistent<PREC, REL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        if (cudaFuncSetAttribute(k_stage_persistent<PREC, REL, UM>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  int(smem)) != cudaSuccess)
             return QSIM_E_CUDA;
         Shape::attr_smem = smem;
         Shape::grid = 0;
     }
     if (!Shape::grid) {
-        int dev = 0, sms = 0, per_sm = 0;
+        // resident CTAs per SM from the kernel's registers and shared memory and the SM's limits (65536 registers,
+        // 2048 threads, 228 KB of shared memory with 1 KB reserved per CTA); the runtime's occupancy query was
+        // seen to answer 1 where more CTAs were resident
+        int dev = 0, sms = 0, per_sm = 1;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_stage_persistent<PREC, REL>, PT, smem);
-        Shape::grid = sms * (per_sm > 0 ? per_sm : 1);
+        cudaFuncAttributes fa{};
+        if (cudaFuncGetAttributes(&fa, k_stage_persistent<PREC, REL, UM>) == cudaSuccess) {
+            const int regs = ((fa.numRegs > 0 ? fa.numRegs : 255) + 7) & ~7;
+            const int by_regs = 65536 / (regs * PT);
+            const int by_smem = int((228u * 1024u) / (smem + fa.sharedSizeBytes + 1024u));
+            per_sm = by_regs < by_smem ? by_regs : by_smem;
+            if (per_sm > 2048 / PT) per_sm = 2048 / PT;
+            if (per_sm < 1) per_sm = 1;
+        }
+        Shape::grid = (sms > 0 ? sms : 1) * per_sm;
     }
     return QSIM_OK;
 }
 
-template <int PREC, bool REL>
+template <int PREC, bool REL, bool UM>
 int launch_stage_prec(const PLaunch &a, size_t smem, cudaStream_t s, int *grid_out) {
-    using Shape = LaunchShape<PREC, REL>;
+    using Shape = LaunchShape<PREC, REL, UM>;
     if (Shape::attr_smem < smem || !Shape::grid) return QSIM_E_INVALID;
     const int grid = Shape::grid;
-    k_stage_persistent<PREC, REL><<<grid, PT, smem, s>>>(a);
+    k_stage_persistent<PREC, REL, UM><<<grid, PT, smem, s>>>(a);
     if (grid_out) *grid_out = grid;
     count_launch();
     return QSIM_OK;
 }
 
+// tcgen05 (um) only for TF32: the split-BF16 form keeps 128-thread CTAs, which this kernel does not have
 template <bool REL>
-int prepare_codec(int prec, size_t smem) {
-    if (prec == QSIM_PREC_TF32) return prepare_prec<QSIM_PREC_TF32, REL>(smem);
-    if (prec == QSIM_PREC_BF16X3) return prepare_prec<QSIM_PREC_BF16X3, REL>(smem);
-    return prepare_prec<QSIM_PREC_FP32, REL>(smem);
+int prepare_codec(int prec, size_t smem, bool um) {
+    if (prec == QSIM_PREC_TF32)
+        return um ? prepare_prec<QSIM_PREC_TF32, REL, true>(smem) : prepare_prec<QSIM_PREC_TF32, REL, false>(smem);
+    if (prec == QSIM_PREC_BF16X3) return prepare_prec<QSIM_PREC_BF16X3, REL, false>(smem);
+    return prepare_prec<QSIM_PREC_FP32, REL, false>(smem);
 }
 
 template <bool REL>
-int launch_codec(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid) {
-    if (prec == QSIM_PREC_TF32) return launch_stage_prec<QSIM_PREC_TF32, REL>(a, smem, s, grid);
-    if (prec == QSIM_PREC_BF16X3) return launch_stage_prec<QSIM_PREC_BF16X3, REL>(a, smem, s, grid);
-    return launch_stage_prec<QSIM_PREC_FP32, REL>(a, smem, s, grid);
+int launch_codec(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid, bool um) {
+    if (prec == QSIM_PREC_TF32)
+        return um ? launch_stage_prec<QSIM_PREC_TF32, REL, true>(a, smem, s, grid)
+                  : launch_stage_prec<QSIM_PREC_TF32, REL, false>(a, smem, s, grid);
+    if (prec == QSIM_PREC_BF16X3) return launch_stage_prec<QSIM_PREC_BF16X3, REL, false>(a, smem, s, grid);
+    return launch_stage_prec<QSIM_PREC_FP32, REL, false>(a, smem, s, grid);
 }
 
 }  // namespace
@@ -455,12 +495,12 @@ size_t persistent_smem_bytes(size_t pass_bytes) {
     return pass_bytes > mlp ? pass_bytes : mlp;
 }
 
-int prepare_stage_persistent(int prec, size_t smem, bool rel) {
-    return rel ? prepare_codec<true>(prec, smem) : prepare_codec<false>(prec, smem);
+int prepare_stage_persistent(int prec, size_t smem, bool rel, bool um) {
+    return rel ? prepare_codec<true>(prec, smem, um) : prepare_codec<false>(prec, smem, um);
 }
 
-int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid, bool rel) {
-    return rel ? launch_codec<true>(a, prec, smem, s, grid) : launch_codec<false>(a, prec, smem, s, grid);
+int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid, bool rel, bool um) {
+    return rel ? launch_codec<true>(a, prec, smem, s, grid, um) : launch_codec<false>(a, prec, smem, s, grid, um);
 }
 
 }  // namespace qsim

@@ -103,7 +103,9 @@ struct PLaunch {
 
 // pass_bytes: the largest tile + pass blob + matrix area of the launch's passes
 size_t persistent_smem_bytes(size_t pass_bytes);
-int prepare_stage_persistent(int prec, size_t smem, bool rel = false);
-int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid, bool rel = false);
+// um: the launch's passes carry tcgen05 dense ops (TF32 only)
+int prepare_stage_persistent(int prec, size_t smem, bool rel = false, bool um = false);
+int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid, bool rel = false,
+                            bool um = false);
 
 }  // namespace qsim

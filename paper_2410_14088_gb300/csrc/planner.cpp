@@ -514,7 +514,8 @@ void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
     // shared-memory bytes of the pass's op data (descriptor, and for a diagonal op its tables)
     auto op_bytes = [&](const Op &op) -> size_t {
         if (op.type == OP_CSEP) return kOpDescBytes + kCsepTableBytes + 48 * size_t(op.k);
-        if (op.type == OP_DENSE && op.k >= 3 && op.k <= 5) return kOpDescBytes + 640;  // tensor-core offset tables
+        if (op.type == OP_DENSE && op.k >= 3 && op.k <= 6)  // tensor-core offset tables: 128 + 2^k words
+            return kOpDescBytes + 4 * (128 + (size_t(1) << op.k));
         return kOpDescBytes + (op.type == OP_DIAG ? 192 + 16 + (size_t(8) << op.k) : 0);
     };
     size_t bytes = 0;

@@ -1,8 +1,8 @@
 """Persistent stage kernel (one launch per stage over a queue of work items,
 optionally the stage loop captured into one CUDA graph): byte-identical
 compressed state to the stream engine, with exact and learned sizing, all
-gate precisions, and a bounded dependency wait that ends the run with
-QSIM_E_TIMEOUT instead of hanging."""
+gate precisions, TF32 dense ops of width 3-5 on tcgen05, and a bounded
+dependency wait that ends the run with QSIM_E_TIMEOUT instead of hanging."""
 import numpy as np
 import pytest
 
@@ -68,3 +68,19 @@ def test_persistent_rejects_k6():
     with pytest.raises(qsim.QsimError) as ei:
         qsim.plan_stages(c, m=10, k=6, mode=qsim.MODE_PERSISTENT)
     assert ei.value.code == qsim.E_INVALID
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_persistent_tcgen05_matches_streams(k):
+    # TF32 dense ops of width 3..5 on tcgen05 inside the persistent kernel (TMEM and the MMA mbarrier held per CTA
+    # for the launch): the same MMAs as the stream engine's tcgen05 form, so the same streams byte for byte
+    c = inputs.random_brick(18, 8, 2)
+    kw = dict(m=11, inner=2, k=k, eps=1e-3, prec=qsim.PREC_TF32, tcgen05=1)
+    ref = qsim.run(qsim.plan_stages(c, **kw))
+    for graph in (0, 1):
+        per = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, graph=graph, **kw))
+        assert streams_of(ref, 128) == streams_of(per, 128)
+        assert per.fidelity(oracle.simulate(c)) >= 0.99
+    # and it differs from the warp-level MMA run only by TF32 rounding (both within the codec's grid of each other)
+    warp = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, **dict(kw, tcgen05=0)))
+    assert abs(warp.fidelity(oracle.simulate(c)) - per.fidelity(oracle.simulate(c))) < 1e-3

@@ -1,7 +1,7 @@
 """Dense ops on the 5th-generation tensor cores (tcgen05.mma in TF32 or split BF16, both operands in shared
 memory, the FP32 accumulator in tensor memory) against the FP64 oracle and the warp-level mma.sync path,
 uncompressed and through the compressed stage loop: width 5 natively, widths 3 and 4 as width-5 ops (the
-matrix times the identity on tile bits the op does not touch)."""
+matrix times the identity on tile bits the op does not touch), width 6 in TF32 with a 64 KB B operand."""
 import numpy as np
 import pytest
 
@@ -64,15 +64,16 @@ def test_tcgen05_compressed_runs():
         assert st.fidelity(ideal) >= 0.999
     st = qsim.run(qsim.plan_stages(c, tcgen05=1, **dict(kw, prec=qsim.PREC_BF16X3)))
     assert st.fidelity(ideal) >= 0.999
-    # the persistent stage kernel keeps the warp-level MMAs: the option leaves its streams unchanged
+    # the persistent stage kernel runs the same TF32 MMAs on tcgen05 (two threads per index group in its 256-thread
+    # CTAs): the same streams as the stream engine, byte for byte
     a = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, tcgen05=1, **kw))
-    b = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, **kw))
+    b = qsim.run(qsim.plan_stages(c, tcgen05=1, **kw))
     for blk in range(64):
         assert a.block_stream(blk) == b.block_stream(blk)
 
 
 def test_tcgen05_bounded_wait_reports_timeout():
-    # test hook: the MMAs are not committed to the mbarrier, so every tile's wait runs out (1 s) and the run
+    # test hook: no MMA is issued or committed to the mbarrier, so every tile's wait runs out (1 s) and the run
     # ends with QSIM_E_TIMEOUT instead of hanging; the context stays usable
     c = inputs.random_brick(12, 4, 1)
     kw = dict(m=12, inner=2, k=5, prec=qsim.PREC_TF32, tcgen05=1, codec=qsim.CODEC_NONE)
@@ -143,3 +144,25 @@ def test_tcgen05_widths_3_and_4(k, prec):
             assert np.max(np.abs(tc - want)) <= 1e-5
         else:
             assert np.max(np.abs(tc - want)) <= 2e-2 * 2 ** (-c.n / 2)
+
+
+def test_tcgen05_width_6_tf32():
+    # fused to 6 qubits: width-6 dense ops run on tcgen05 in TF32 (M = 128 with 64 live rows, K = N = 128);
+    # against the FP32 CUDA-core run of the same plan the tcgen05 run shows TF32-sized errors (the tensor-core
+    # path ran), within the per-op bound, and stays close to FP64
+    cases = [(inputs.qft_rz_cx(14, 2, 7), dict(m=9, inner=3)), (inputs.random_brick(16, 8, 2), dict(m=10, inner=2))]
+    for c, kw in cases:
+        plans = [qsim.plan_stages(c, codec=qsim.CODEC_NONE, k=6, **kw),
+                 qsim.plan_stages(c, codec=qsim.CODEC_NONE, prec=qsim.PREC_TF32, k=6, tcgen05=1, **kw)]
+        n6 = sum(1 for s in range(plans[1].nstages) for o in plans[1].stage_ops(s) if o["type"] == 0 and o["nq"] == 6)
+        assert n6 > 0
+        fp32, tc = (qsim.run(p).decompress().cpu().numpy() for p in plans)  # FP32 CUDA cores, TF32 tcgen05
+        want = oracle.simulate(c)
+        nops = sum(1 for s in range(plans[1].nstages) for o in plans[1].stage_ops(s) if o["type"] == 0)
+        err_tc = np.linalg.norm(tc - want) / np.linalg.norm(want)
+        err_fp32 = np.linalg.norm(fp32 - want) / np.linalg.norm(want)
+        print(f"\nk=6 tf32 n={c.n}: tcgen05 {err_tc:.3e}, cuda cores {err_fp32:.3e}, {n6} width-6 of {nops} dense ops")
+        assert err_tc <= nops * 2.0 ** -10
+        assert err_tc > 10 * err_fp32  # TF32 operands: the tensor-core path ran
+        assert np.max(np.abs(tc - want)) <= 2e-2 * 2 ** (-c.n / 2)
+        assert oracle.fidelity(want, tc) >= 0.9999
