@@ -281,7 +281,10 @@ __host__ __device__ constexpr uint32_t umma_b_bytes() {
 __host__ __device__ constexpr uint32_t umma_pass_b_bytes(uint32_t umma_bits) {
     return (umma_bits & 8u) ? 65536u : (umma_bits & 4u) ? umma_b_bytes<QSIM_PREC_BF16X3>() : umma_b_bytes<QSIM_PREC_TF32>();
 }
-__host__ __device__ constexpr uint32_t umma_pass_tmem_cols(uint32_t umma_bits) { return (umma_bits & 8u) ? 128u : 64u; }
+// TMEM columns of a tcgen05 pass: D in columns 0..63 (0..127 for width 6) and, for the width-5 TF32 form, A in
+// columns kUmmaACol .. kUmmaACol + 63; 128 in every case (four resident CTAs fill the SM's 512)
+__host__ __device__ constexpr uint32_t umma_pass_tmem_cols(uint32_t) { return 128u; }
+constexpr uint32_t kUmmaACol = 64;
 constexpr uint32_t kUmmaIdesc = umma::idesc_tf32(128, 64);
 constexpr uint32_t kUmmaIdesc6 = umma::idesc_tf32(128, 128);
 constexpr uint32_t kUmmaIdescBf16 = umma::idesc_bf16(128, 64);
@@ -315,12 +318,13 @@ __device__ __forceinline__ void umma_epilogue(float2 *tile, uint32_t base, const
 
 // Dense op of width 5 (TF32) on a 4096-amplitude tile with the 5th-generation tensor cores: the real form
 // D = A * B with A = 128 index groups x 64 inputs (Re parts of the group's 32 amplitudes in K columns
-// 0..31, Im parts in 32..63), B = the op's 64 x 64 real matrix (host-built, staged at `bsm` in the same
-// K-major 128-byte swizzled layout: B^T row n = output n, Re outputs first), D in TMEM (lane = group,
-// 64 FP32 columns). Thread g owns index group g: it gathers the group's amplitudes into registers; after
-// a barrier the tile's 32 KB, no longer needed as amplitudes, hold A; one thread issues the eight K = 8
-// MMAs and commits them to the mbarrier; every thread waits (bounded), reads its D row from TMEM and
-// writes the group's outputs back to their tile positions, which only it owns in this op.
+// 0..31, Im parts in 32..63), B = the op's 64 x 64 real matrix (host-built, staged at `bsm` in the K-major
+// 128-byte swizzled layout: B^T row n = output n, Re outputs first), D in TMEM (lane = group, 64 FP32
+// columns). Thread g owns index group g: it gathers the group's amplitudes into registers and stores them,
+// rounded to TF32, as row g of A in TMEM (lane g, from column kUmmaACol), so A never passes through shared
+// memory; one thread issues the eight K = 8 MMAs (A from TMEM, B from shared memory) and commits them to the
+// mbarrier; every thread waits (bounded), reads its D row from TMEM and writes the group's outputs back to
+// their tile positions, which only it owns in this op.
 // Returns false when the wait ran out (status set; the tile is then left unwritten).
 template <int NT>
 __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, const uint32_t *cb, const uint32_t *osw,
@@ -337,33 +341,31 @@ __device__ __forceinline__ bool apply_dense_umma<256>(float2 *tile, uint32_t bsm
                                                       int *status) {
     const uint32_t g = threadIdx.x & 127u, h = threadIdx.x >> 7;  // group, half (amplitudes 16h .. 16h + 15)
     const uint32_t base = cb[g & 63u] ^ cb[64u + (g >> 6)];
-    uint32_t re[16], im[16];
+    {
+        uint32_t re[16], im[16];
 #pragma unroll
-    for (uint32_t j = 0; j < 16; ++j) {
-        const float2 v = tile[base ^ osw[16u * h + j]];
-        re[j] = f32_to_tf32(v.x);
-        im[j] = f32_to_tf32(v.y);
-    }
-    __syncthreads();  // every amplitude of the tile is in registers
-    uint8_t *arow = reinterpret_cast<uint8_t *>(tile) + (g >> 3) * 1024u + (g & 7u) * 128u;
-#pragma unroll
-    for (uint32_t cc = 0; cc < 4; ++cc) {  // 16-byte chunks 4h .. 4h + 3 of the Re and Im halves of the row
-        const uint32_t o = ((4u * h + cc) ^ (g & 7u)) << 4;
-        *reinterpret_cast<uint4 *>(arow + o) = make_uint4(re[4 * cc], re[4 * cc + 1], re[4 * cc + 2], re[4 * cc + 3]);
-        *reinterpret_cast<uint4 *>(arow + 16384u + o) =
-            make_uint4(im[4 * cc], im[4 * cc + 1], im[4 * cc + 2], im[4 * cc + 3]);
+        for (uint32_t j = 0; j < 16; ++j) {
+            const float2 v = tile[base ^ osw[16u * h + j]];
+            re[j] = f32_to_tf32(v.x);
+            im[j] = f32_to_tf32(v.y);
+        }
+        // row g of A is TMEM lane g (lane quarter = warp mod 4): this thread's 16 Re parts at columns
+        // kUmmaACol + 16h.., its 16 Im parts 32 further
+        const uint32_t ta = S.tmem + ((32u * ((threadIdx.x >> 5) & 3u)) << 16) + kUmmaACol + 16u * h;
+        umma::tmem_st16(ta, re);
+        umma::tmem_st16(ta + 32u, im);
+        umma::tmem_wait_st();
     }
     cp_async_wait_all();  // this thread's share of B
     umma::fence_proxy_async_smem();
+    umma::fence_before_sync();
     __syncthreads();
     if (threadIdx.x == 0 && !(S.p.umma & 2u)) {  // the test hook issues nothing
         umma::fence_after_sync();
-        const uint32_t a0 = umma::smem_addr(tile);
 #pragma unroll
         for (uint32_t s = 0; s < 8; ++s) {
-            const uint64_t da = umma::desc_kmajor_sw128(a0 + (s >> 2) * 16384u + (s & 3u) * 32u);
             const uint64_t db = umma::desc_kmajor_sw128(bsm + (s >> 2) * 8192u + (s & 3u) * 32u);
-            umma::mma_tf32_ss(S.tmem, da, db, kUmmaIdesc, s);
+            umma::mma_tf32_ts(S.tmem, S.tmem + kUmmaACol + 8u * s, db, kUmmaIdesc, s);
         }
     }
     if (!umma_commit_wait(S, phase, status)) return false;
@@ -386,33 +388,30 @@ __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, con
     static_assert(NT == 128, "one thread per index group");
     const uint32_t g = threadIdx.x;
     const uint32_t base = cb[g & 63u] ^ cb[64u + (g >> 6)];
-    uint32_t re[32], im[32];
+    {
+        uint32_t re[32], im[32];
 #pragma unroll
-    for (uint32_t j = 0; j < 32; ++j) {
-        const float2 v = tile[base ^ osw[j]];
-        re[j] = f32_to_tf32(v.x);
-        im[j] = f32_to_tf32(v.y);
-    }
-    __syncthreads();  // every amplitude of the tile is in registers
-    uint8_t *arow = reinterpret_cast<uint8_t *>(tile) + (g >> 3) * 1024u + (g & 7u) * 128u;
-#pragma unroll
-    for (uint32_t c = 0; c < 8; ++c) {
-        const uint32_t o = (c ^ (g & 7u)) << 4;
-        *reinterpret_cast<uint4 *>(arow + o) = make_uint4(re[4 * c], re[4 * c + 1], re[4 * c + 2], re[4 * c + 3]);
-        *reinterpret_cast<uint4 *>(arow + 16384u + o) =
-            make_uint4(im[4 * c], im[4 * c + 1], im[4 * c + 2], im[4 * c + 3]);
+        for (uint32_t j = 0; j < 32; ++j) {
+            const float2 v = tile[base ^ osw[j]];
+            re[j] = f32_to_tf32(v.x);
+            im[j] = f32_to_tf32(v.y);
+        }
+        // row g of A is TMEM lane g: Re parts in columns kUmmaACol.., Im parts 32 further (the tile stays as it is)
+        const uint32_t ta = S.tmem + ((32u * (g >> 5)) << 16) + kUmmaACol;
+        umma::tmem_st32(ta, re);
+        umma::tmem_st32(ta + 32u, im);
+        umma::tmem_wait_st();
     }
     cp_async_wait_all();  // this thread's share of B
     umma::fence_proxy_async_smem();
+    umma::fence_before_sync();
     __syncthreads();
     if (g == 0 && !(S.p.umma & 2u)) {  // the test hook issues nothing
         umma::fence_after_sync();
-        const uint32_t a0 = umma::smem_addr(tile);
 #pragma unroll
         for (uint32_t s = 0; s < 8; ++s) {
-            const uint64_t da = umma::desc_kmajor_sw128(a0 + (s >> 2) * 16384u + (s & 3u) * 32u);
             const uint64_t db = umma::desc_kmajor_sw128(bsm + (s >> 2) * 8192u + (s & 3u) * 32u);
-            umma::mma_tf32_ss(S.tmem, da, db, kUmmaIdesc, s);
+            umma::mma_tf32_ts(S.tmem, S.tmem + kUmmaACol + 8u * s, db, kUmmaIdesc, s);
         }
     }
     if (!umma_commit_wait(S, phase, status)) return false;

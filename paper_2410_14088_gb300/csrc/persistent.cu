@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
     uint32_t mphase = 0;     // parity of the MMA mbarrier's next phase (UM)
     bool mma_ok = true;      // false after an MMA wait ran out (then a last bounded wait before TMEM is freed)
     if constexpr (UM) {
-        if (warp == 0) umma::tmem_alloc(umma::smem_addr(&PS.tmem), 64);
+        if (warp == 0) umma::tmem_alloc(umma::smem_addr(&PS.tmem), gdev::umma_pass_tmem_cols(0));
         if (tid == 0) umma::mbar_init(umma::smem_addr(&PS.mbar), 1);
         umma::fence_before_sync();
     }
@@ -404,7 +404,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
         __syncthreads();
         if (warp == 0) {
             umma::fence_after_sync();
-            umma::tmem_dealloc(PS.tmem, 64);
+            umma::tmem_dealloc(PS.tmem, gdev::umma_pass_tmem_cols(0));
         }
     }
     // the last CTA out resets the queue and advances the look-back epoch
