@@ -350,7 +350,7 @@ int qsim_compress_block(const float *d_amps, uint32_t m, double eb, void *d_out,
  * Arguments, output and errors are those of qsim_compress_block; in
  * addition m > QSIM_NOALLOC_MAX_M is rejected with QSIM_E_INVALID. The first
  * call on a device looks up the array's device address (once per device,
- * with that device current); make that first call before any stream capture.
+ * with that device current).
  * All calls share the one array and each call clears the parts it uses, so
  * calls must not overlap on the GPU: this call synchronises cuda_stream
  * before it returns, and calls from several host threads are serialised.

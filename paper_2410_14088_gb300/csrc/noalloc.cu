@@ -44,8 +44,7 @@ std::mutex g_noalloc_mu;
 DeviceScratch g_noalloc_dev[64];
 
 // Once per device, with that device current: look up the array's device
-// address. The first call on a device does this; make it before any stream
-// capture.
+// address. The first call on a device does this.
 int scratch_for_current_device(unsigned char **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
