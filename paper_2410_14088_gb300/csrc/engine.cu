@@ -1298,6 +1298,7 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
         a.pbf16 = uint32_t(dctx.pred_bf16);
         uint32_t nph = 0;
         const uint32_t gframes = sd.G * uint32_t(R.nframes);
+        const uint32_t fpi = persistent_frames_per_item(um_any);
         auto add = [&](uint32_t type, uint32_t count, uint32_t arg) {
             if (nph < uint32_t(kMaxPhases)) {
                 a.ph[nph].type = type;
@@ -1306,20 +1307,20 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
             }
             ++nph;
         };
-        add(PH_DECODE, (gframes + 7) / 8, 0);
+        add(PH_DECODE, (gframes + fpi - 1) / fpi, 0);
         if (R.predict) add(PH_PREDICT, 1, 0);
         for (uint32_t pi = 0; pi < sd.npasses; ++pi) add(PH_PASS, 1u << sd.passes_host[pi].nout, pi);
         if (R.rel) {
             // relative-bound codec: in-place encoder (exact slots, or predicted slots kept when they fit), copy
-            add(PH_ENCODE_IP, (gframes + 7) / 8, 0);
-            add(PH_COPY, (gframes + 7) / 8, 0);
+            add(PH_ENCODE_IP, (gframes + fpi - 1) / fpi, 0);
+            add(PH_COPY, (gframes + fpi - 1) / fpi, 0);
         } else if (R.predict) {
-            add(PH_ENCODE, (gframes + 7) / 8, 0);
+            add(PH_ENCODE, (gframes + fpi - 1) / fpi, 0);
             add(PH_FIX, 1, 0);
-            add(PH_REENCODE, (gframes + 7) / 8, 0);
+            add(PH_REENCODE, (gframes + fpi - 1) / fpi, 0);
         } else {
-            add(PH_SIZE_W, (gframes + 7) / 8, 0);
-            add(PH_ENCODE_W, (gframes + 7) / 8, 0);
+            add(PH_SIZE_W, (gframes + fpi - 1) / fpi, 0);
+            add(PH_ENCODE_W, (gframes + fpi - 1) / fpi, 0);
         }
         // the last phase index is the group's finished flag
         if (nph > uint32_t(kMaxPhases) - 1)

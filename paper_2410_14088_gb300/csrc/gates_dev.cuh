@@ -331,56 +331,6 @@ __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, con
                                                  const PassSmem &S, uint32_t &phase,
                                                  int *status);
 
-// The TF32 op for 256-thread CTAs (the persistent stage kernel): threads g and g + 128 share index group g, each
-// gathering, writing into A and taking back from TMEM 16 of the group's 32 amplitudes; warps w and w + 4 read
-// the same TMEM lanes (w's quarter of the 128 rows) in different columns. The MMAs are those of the 128-thread
-// form, so both give the same results bit for bit.
-template <>
-__device__ __forceinline__ bool apply_dense_umma<256>(float2 *tile, uint32_t bsm, const uint32_t *cb,
-                                                      const uint32_t *osw, const PassSmem &S, uint32_t &phase,
-                                                      int *status) {
-    const uint32_t g = threadIdx.x & 127u, h = threadIdx.x >> 7;  // group, half (amplitudes 16h .. 16h + 15)
-    const uint32_t base = cb[g & 63u] ^ cb[64u + (g >> 6)];
-    {
-        uint32_t re[16], im[16];
-#pragma unroll
-        for (uint32_t j = 0; j < 16; ++j) {
-            const float2 v = tile[base ^ osw[16u * h + j]];
-            re[j] = f32_to_tf32(v.x);
-            im[j] = f32_to_tf32(v.y);
-        }
-        // row g of A is TMEM lane g (lane quarter = warp mod 4): this thread's 16 Re parts at columns
-        // kUmmaACol + 16h.., its 16 Im parts 32 further
-        const uint32_t ta = S.tmem + ((32u * ((threadIdx.x >> 5) & 3u)) << 16) + kUmmaACol + 16u * h;
-        umma::tmem_st16(ta, re);
-        umma::tmem_st16(ta + 32u, im);
-        umma::tmem_wait_st();
-    }
-    cp_async_wait_all();  // this thread's share of B
-    umma::fence_proxy_async_smem();
-    umma::fence_before_sync();
-    __syncthreads();
-    if (threadIdx.x == 0 && !(S.p.umma & 2u)) {  // the test hook issues nothing
-        umma::fence_after_sync();
-#pragma unroll
-        for (uint32_t s = 0; s < 8; ++s) {
-            const uint64_t db = umma::desc_kmajor_sw128(bsm + (s >> 2) * 8192u + (s & 3u) * 32u);
-            umma::mma_tf32_ts(S.tmem, S.tmem + kUmmaACol + 8u * s, db, kUmmaIdesc, s);
-        }
-    }
-    if (!umma_commit_wait(S, phase, status)) return false;
-    umma::fence_after_sync();
-    const uint32_t taddr = S.tmem + ((32u * ((threadIdx.x >> 5) & 3u)) << 16) + 16u * h;
-    uint32_t dre[16], dim[16];
-    umma::tmem_ld16(taddr, dre);
-    umma::tmem_ld16(taddr + 32u, dim);
-#pragma unroll
-    for (uint32_t j = 0; j < 16; ++j)
-        tile[base ^ osw[16u * h + j]] = make_float2(__uint_as_float(dre[j]), __uint_as_float(dim[j]));
-    umma::fence_before_sync();  // the next op's barrier orders these TMEM reads before its MMAs
-    return true;
-}
-
 template <int NT>
 __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, const uint32_t *cb, const uint32_t *osw,
                                                  const PassSmem &S, uint32_t &phase,
@@ -789,12 +739,8 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                     bool done;
                     if constexpr (PREC == QSIM_PREC_BF16X3)
                         done = apply_dense_umma3<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status);
-                    else if (k == 6) {
-                        if constexpr (NT == 128)
-                            done = apply_dense_umma6<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status);
-                        else
-                            done = false;  // not uploaded for 256-thread kernels
-                    }
+                    else if (k == 6)
+                        done = apply_dense_umma6<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status);
                     else
                         done = apply_dense_umma<NT>(tile, umma::smem_addr(bbuf), cb, osw, S, phase, status);
                     if (!done) return false;
@@ -948,20 +894,25 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
 // then matrix area), apply the pass's ops, store the tile back. CG selects
 // L2-only loads, needed when the working vector was written by other CTAs of
 // the same launch (the persistent stage kernel).
-// With phase_io the caller owns the TMEM accumulator (S.tmem, 64 columns) and the MMA mbarrier (S.mbar) across
+// With phase_io the caller owns the TMEM accumulator (S.tmem, 128 columns) and the MMA mbarrier (S.mbar) across
 // calls and keeps the mbarrier's phase parity in *phase_io; returns false when an MMA wait ran out.
+// With cache (shared memory: cache[0] the key of the pass staged in dyn, cache[1] whether its single tcgen05
+// op's B operand is staged too) a call whose key matches reuses the staged descriptor, blob and B operand; the
+// caller sets cache[0] to a key no pass uses whenever something else writes dyn.
 template <int NT, int KMAX, int PREC, bool CG, bool UM = false>
 __device__ __forceinline__ bool pass_tile(float2 *__restrict__ g, const PassDev &pd, const uint4 *__restrict__ gblob,
                                           const float2 *__restrict__ mats, const uint32_t *__restrict__ bfr,
                                           uint64_t cta, uint64_t gb, PassSmem &S, float2 *dyn, int *status,
-                                          uint32_t *phase_io = nullptr) {
-    pass_setup<NT>(pd, S);  // copies the descriptor only: a caller-owned S.tmem and S.mbar stay as they are
+                                          uint32_t *phase_io = nullptr, uint32_t *cache = nullptr,
+                                          uint32_t key = 0) {
+    const bool hit = cache && cache[0] == key;
+    // copies the descriptor only: a caller-owned S.tmem and S.mbar stay as they are
+    if (!hit) pass_setup<NT>(pd, S);
     const uint32_t T = S.p.T;
     // passes with tcgen05 dense ops: the tile 1024-byte aligned (it is the A operand while the MMAs run),
     // the B operand after it, then the blob; 64 TMEM columns hold the accumulator
-    static_assert(!UM || (((PREC == QSIM_PREC_TF32 && (NT == 128 || NT == 256)) ||
-                           (PREC == QSIM_PREC_BF16X3 && NT == 128)) && KMAX >= 5),
-                  "tcgen05 passes: TF32 (128 or 256 threads) or split BF16 (128 threads), k = 5");
+    static_assert(!UM || ((PREC == QSIM_PREC_TF32 || PREC == QSIM_PREC_BF16X3) && NT == 128 && KMAX >= 5),
+                  "tcgen05 passes: TF32 or split BF16, 128 threads, k = 5");
     bool um = false;
     if constexpr (UM) um = S.p.umma != 0;
     float2 *tile = dyn;
@@ -979,11 +930,44 @@ __device__ __forceinline__ bool pass_tile(float2 *__restrict__ g, const PassDev 
     uint4 *blob = reinterpret_cast<uint4 *>(tile + (1u << T)) + (um ? umma_pass_b_bytes(S.p.umma) / 16 : 0u);
     float2 *mat = reinterpret_cast<float2 *>(blob + S.p.blob_words);
     const uint64_t base = tile_base(S, cta);
-    blob_load<NT>(gblob + S.p.blob_off, S.p.blob_words, blob);
+    bool b_res = false;
+    if (hit) {
+        b_res = cache[1] != 0;
+    } else {
+        blob_load<NT>(gblob + S.p.blob_off, S.p.blob_words, blob);
+        if (cache) {
+            // a pass with a single tcgen05 op keeps that op's B operand staged for the calls that hit the cache
+            if constexpr (UM) {
+                if (um && T == 12) {
+                    const OpDev *gops = reinterpret_cast<const OpDev *>(gblob + S.p.blob_off);
+                    uint32_t n5 = 0, first = 0;
+                    for (uint32_t oi = 0; oi < S.p.op_count; ++oi) {
+                        const uint32_t ty = __ldg(&gops[oi].type), k = __ldg(&gops[oi].k);
+                        if (ty == OP_DENSE && (k == 5 || (k == 6 && PREC == QSIM_PREC_TF32 && (S.p.umma & 8u)))) {
+                            if (!n5) first = oi;
+                            ++n5;
+                        }
+                    }
+                    if (n5 == 1) {
+                        const uint32_t k1 = __ldg(&gops[first].k);
+                        const uint4 *src = reinterpret_cast<const uint4 *>(bfr + __ldg(&gops[first].bfrag));
+                        const uint32_t bw = (k1 == 6 ? 65536u : umma_b_bytes<PREC>()) / 16;
+                        for (uint32_t t = threadIdx.x; t < bw; t += NT) cp_async16(bbuf + t, src + t);
+                        b_res = true;
+                    }
+                }
+            }
+            if (threadIdx.x == 0) {  // every thread read cache[0] before pass_setup's barriers
+                cache[0] = key;
+                cache[1] = b_res ? 1u : 0u;
+            }
+        }
+    }
     tile_load<NT, CG>(g, base, S, tile);
     cp_async_wait_all();
     uint32_t phase = phase_io ? *phase_io : 0u;
-    const bool ok = tile_ops<NT, KMAX, PREC, UM>(tile, blob, mat, mats, bfr, base, gb, S, bbuf, status, phase);
+    const bool ok =
+        tile_ops<NT, KMAX, PREC, UM>(tile, blob, mat, mats, bfr, base, gb, S, bbuf, status, phase, b_res);
     __syncthreads();
     tile_store<NT>(g, base, S, tile);
     if (phase_io) {
@@ -1016,7 +1000,9 @@ __device__ __forceinline__ void pass_tiles(float2 *__restrict__ wv, uint32_t W, 
                                            const uint4 *__restrict__ gblob, const float2 *__restrict__ mats,
                                            const uint32_t *__restrict__ bfr, const uint64_t *__restrict__ gbase,
                                            PassSmem &S, float2 *dyn, uint32_t *ctr, int *status) {
-    __shared__ uint32_t s_next;
+    // the CTA's next tile, in a slot by iteration parity: thread 0 writes slot (it + 1) & 1 while a slower warp may
+    // still be reading slot it & 1 after the end-of-iteration barrier; that slot is next written two barriers later
+    __shared__ uint32_t s_next[2];
     pass_setup<NT>(pd, S);
     const uint32_t T = S.p.T;
     static_assert(!UM || ((PREC == QSIM_PREC_TF32 || PREC == QSIM_PREC_BF16X3) && NT == 128 && KMAX >= 5),
@@ -1060,8 +1046,9 @@ __device__ __forceinline__ void pass_tiles(float2 *__restrict__ wv, uint32_t W, 
     uint32_t phase = 0;
     bool ok = true;
     const uint64_t tmask = (1ull << S.p.nout) - 1;
-    for (uint64_t t = blockIdx.x; t < ntiles;) {
-        if (threadIdx.x == 0) s_next = gridDim.x + atomicAdd(ctr, 1u);  // this CTA's next tile, read below
+    uint32_t it = 0;
+    for (uint64_t t = blockIdx.x; t < ntiles; ++it) {
+        if (threadIdx.x == 0) s_next[it & 1u] = gridDim.x + atomicAdd(ctr, 1u);  // read after the barrier below
         const uint64_t grp = t >> S.p.nout, cta = t & tmask;
         float2 *g = wv + (grp << W);
         const uint64_t gb = gbase ? gbase[grp] : 0ull;
@@ -1071,9 +1058,9 @@ __device__ __forceinline__ void pass_tiles(float2 *__restrict__ wv, uint32_t W, 
         ok = tile_ops<NT, KMAX, PREC, UM>(tile, blob, mat, mats, bfr, base, gb, S, bbuf, status, phase, b_res);
         __syncthreads();
         tile_store<NT>(g, base, S, tile);
-        __syncthreads();  // the next tile's loads overwrite the tile; s_next is visible
+        __syncthreads();  // the next tile's loads overwrite the tile; s_next[it & 1] is visible
         if (!ok) break;   // uniform: the MMA wait ran out (status set)
-        t = s_next;
+        t = s_next[it & 1u];
     }
     if (threadIdx.x == 0) {
         // every tile counter increment of this CTA precedes its arrival; the last CTA to arrive resets both

@@ -36,7 +36,9 @@ namespace {
 using cdev::FrameGeom;
 using cdev::geom;
 
-constexpr int PT = 256;  // threads per CTA
+// threads per CTA: one warp per frame of a frame-parallel item
+template <bool UM>
+constexpr int kPT = 32 * int(persistent_frames_per_item(UM));
 
 __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     uint32_t v;
@@ -56,7 +58,8 @@ __device__ __forceinline__ EncTarget load_target(const EncTarget *t) {
 // REL: the relative-bound codec (QSZR) in the decode phase and the in-place exact phases. UM: the plan's TF32
 // dense ops of width 3 to 5 run on tcgen05 (TMEM accumulator and MMA mbarrier held by each CTA for the launch).
 template <int PREC, bool REL, bool UM>
-__global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
+__global__ void __launch_bounds__(kPT<UM>, 512 / kPT<UM>) k_stage_persistent(PLaunch L) {
+    constexpr int PT = kPT<UM>;
     extern __shared__ float4 dsm[];
     __shared__ gdev::PassSmem PS;
     __shared__ uint32_t s_wb[PT / 32][64];
@@ -64,13 +67,15 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
     __shared__ uint2 s_pre_ab[kMaxPreOps];
     __shared__ __align__(16) PSeg S;
     __shared__ uint32_t s_hist[PT / 32][32];
-    __shared__ uint32_t s_words[PT / 32];
     __shared__ uint32_t s_item, s_epoch, s_seg, s_next;
-    __shared__ int s_flag;
+    __shared__ uint32_t s_pcache[2];  // key (segment x 256 + pass) of the pass staged in dsm; its B resident
+    __shared__ int s_flag, s_abort;
     const int tid = threadIdx.x, warp = tid >> 5;
     if (tid == 0) {
         s_epoch = ld_relaxed_u32(L.ctr + 2) & cdev::kEpochMask;
         s_seg = ~0u;
+        s_pcache[0] = ~0u;
+        s_pcache[1] = 0;
     }
     uint32_t mphase = 0;     // parity of the MMA mbarrier's next phase (UM)
     bool mma_ok = true;      // false after an MMA wait ran out (then a last bounded wait before TMEM is freed)
@@ -82,28 +87,82 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
     __syncthreads();
     if constexpr (UM) umma::fence_after_sync();
 
+    // thread 0: the next item, claimed one item ahead so that the claim's latency hides under the current item
+    // (every dependency points to an earlier item, and the grid is one wave of resident CTAs, so the smallest
+    // unfinished item is always some CTA's current item and the queue keeps moving)
+    uint32_t nx_item = 0;
+    // thread 0: the (launch group, phase) whose dependencies this CTA last saw met; later items of the same
+    // phase of the same group skip the wait (the counters only grow within a launch)
+    uint64_t dep_key = ~0ull;
+    if (tid == 0) nx_item = atomicAdd(L.ctr, 1u);
+    // thread 0: wait for the item's dependencies (the group's previous phase; for its first phase the slot's
+    // previous group and the circuit's previous stage); returns 1 when the item must skip its work (a device
+    // error, or a wait that ran out)
+    auto deps = [&](uint32_t it) -> int {
+        const uint32_t rel = uint32_t(it - S.item_begin);
+        const uint32_t grp = rel / S.per_group, r = rel % S.per_group;
+        const uint32_t q = S.group_begin + grp;
+        uint32_t p = 0;
+        while (p + 1 < S.nphases && r >= S.ph_start[p + 1]) ++p;
+        const uint64_t key = uint64_t(q) * kMaxPhases + p;
+        if (key == dep_key) return ld_relaxed_u32(reinterpret_cast<const uint32_t *>(L.status)) != 0;
+        const uint32_t *flag = nullptr, *flag2 = nullptr;
+        uint32_t need = 0;
+        if (p > 0) {
+            flag = L.done + uint64_t(q) * kMaxPhases + p - 1;
+            need = S.ph[p - 1].count;
+        } else {
+            const uint32_t prev = L.g_prev[q];
+            if (prev != kNoGroup) {  // the slot's previous group must have finished
+                flag = L.done + uint64_t(prev) * kMaxPhases + kMaxPhases - 1;
+                need = 1;
+            }
+            flag2 = S.prev_flag;
+        }
+        if (S.stall_test && grp == 0 && p == 1) ++need;  // never reached: exercises the time limit
+        bool met = true;
+        if (flag || flag2) {
+            const uint64_t t0 = global_ns();
+            while ((flag && ld_acquire_u32(flag) < need) || (flag2 && ld_acquire_u32(flag2) == 0)) {
+                if (global_ns() - t0 > L.wait_ns) {
+                    raise_status(L.status, QSIM_E_TIMEOUT);
+                    met = false;
+                    break;
+                }
+                __nanosleep(256);
+            }
+        }
+        if (met) dep_key = key;
+        // after any device error the remaining items only keep the schedule going
+        return (!met || ld_relaxed_u32(reinterpret_cast<const uint32_t *>(L.status)) != 0) ? 1 : 0;
+    };
+
     while (true) {
         if (tid == 0) {
-            s_item = atomicAdd(L.ctr, 1u);
+            const uint32_t it = nx_item;
+            s_item = it;
             // the segment holding the item: last one with item_begin <= item
-            uint32_t lo = 0, hi = L.nseg - 1;
-            if (s_item < L.total_items) {
+            uint32_t lo = 0;
+            if (it < L.total_items) {
+                nx_item = atomicAdd(L.ctr, 1u);
+                uint32_t hi = L.nseg - 1;
                 while (lo < hi) {
                     const uint32_t mid = (lo + hi + 1) >> 1;
-                    if (__ldg(reinterpret_cast<const unsigned long long *>(&L.segs[mid].item_begin)) <= s_item)
+                    if (__ldg(reinterpret_cast<const unsigned long long *>(&L.segs[mid].item_begin)) <= it)
                         lo = mid;
                     else
                         hi = mid - 1;
                 }
             }
             s_next = lo;
+            // the current segment's descriptor is in S: check the dependencies before the barrier
+            if (it < L.total_items && lo == s_seg) s_abort = deps(it);
         }
         __syncthreads();
         const uint32_t item = s_item;
         if (item >= L.total_items) break;
         const uint32_t want = s_next;
         if (want != s_seg) {  // uniform: a new segment, load its descriptor and leading phase ops
-            __syncthreads();
             const unsigned long long *src = reinterpret_cast<const unsigned long long *>(L.segs + want);
             unsigned long long *dst = reinterpret_cast<unsigned long long *>(&S);
             for (int t = tid; t < int(sizeof(PSeg) / 8); t += PT) dst[t] = __ldg(src + t);
@@ -112,7 +171,10 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
                 s_pre[tid] = S.ops[S.pre_begin + tid];
                 s_pre_ab[tid] = cdev::pre_setup(S.ops[S.pre_begin + tid]);
             }
-            if (tid == 0) s_seg = want;
+            if (tid == 0) {
+                s_seg = want;
+                s_abort = deps(item);
+            }
             __syncthreads();
         }
         const FrameGeom g = geom(int(S.m));
@@ -125,46 +187,14 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
         while (p + 1 < nph && r >= S.ph_start[p + 1]) ++p;
         const uint32_t i = r - S.ph_start[p];
         const uint32_t type = S.ph[p].type;
-        // ---- dependencies: the group's previous phase; for its first phase the
-        // slot's previous group and the circuit's previous stage ----
-        if (tid == 0) {
-            const uint32_t *flag = nullptr, *flag2 = nullptr;
-            uint32_t need = 0;
-            if (p > 0) {
-                flag = L.done + uint64_t(q) * kMaxPhases + p - 1;
-                need = S.ph[p - 1].count;
-            } else {
-                const uint32_t prev = L.g_prev[q];
-                if (prev != kNoGroup) {  // the slot's previous group must have finished
-                    flag = L.done + uint64_t(prev) * kMaxPhases + kMaxPhases - 1;
-                    need = 1;
-                }
-                flag2 = S.prev_flag;
-            }
-            if (S.stall_test && grp == 0 && p == 1) ++need;  // never reached: exercises the time limit
-            if (flag || flag2) {
-                const uint64_t t0 = global_ns();
-                while ((flag && ld_acquire_u32(flag) < need) || (flag2 && ld_acquire_u32(flag2) == 0)) {
-                    if (global_ns() - t0 > L.wait_ns) {
-                        raise_status(L.status, QSIM_E_TIMEOUT);
-                        break;
-                    }
-                    __nanosleep(256);
-                }
-            }
-            // after any device error the remaining items only keep the schedule going
-            s_flag = ld_relaxed_u32(reinterpret_cast<const uint32_t *>(L.status)) != 0;
-        }
-        __syncthreads();
-        const bool abort_item = s_flag != 0;
-        __syncthreads();
+        const bool abort_item = s_abort != 0;
         float2 *wv = L.wv + L.g_wv[q];
         float2 *part = L.part + L.g_frame[q];
         const uint32_t *ids = S.ids + uint64_t(grp) * S.G;
         const uint64_t gb = S.gbase[grp];
         const uint64_t bbase = uint64_t(grp) * S.G;  // per-group block arrays
         const uint32_t sf0 = L.g_frame[q];  // the slot's first frame in wrec / flen / foff / part / lb
-        bool by_arrival = type == PH_SIZE || type == PH_ENCODE || type == PH_REENCODE || type == PH_SIZE_W ||
+        bool by_arrival = type == PH_ENCODE || type == PH_REENCODE || type == PH_SIZE_W ||
                           type == PH_ENCODE_W || type == PH_ENCODE_IP || type == PH_COPY;
         if (abort_item) {
             // skip the work, keep the counts
@@ -183,16 +213,13 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             if constexpr (UM) {
                 mma_ok &= gdev::pass_tile<PT, 5, PREC, true, true>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr,
                                                                    i, gb, PS, reinterpret_cast<float2 *>(dsm),
-                                                                   L.status, &mphase);
+                                                                   L.status, &mphase, s_pcache,
+                                                                   s_seg * 256u + S.ph[p].arg);
             } else {
                 gdev::pass_tile<PT, 5, PREC, true>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr, i, gb, PS,
-                                                   reinterpret_cast<float2 *>(dsm), L.status);
+                                                   reinterpret_cast<float2 *>(dsm), L.status, nullptr, s_pcache,
+                                                   s_seg * 256u + S.ph[p].arg);
             }
-        } else if (type == PH_SIZE) {
-            const uint32_t jj = i / g.nframes, f = i % g.nframes;
-            const uint32_t len = cdev::size_frame_cta<true>(wv + (uint64_t(jj) << S.m) + uint64_t(f) * g.F, g, S.e,
-                                                            s_words, L.status);
-            if (tid == 0 && len) atomicAdd(reinterpret_cast<unsigned long long *>(&S.sizes[bbase + jj]), uint64_t(len));
         } else if (REL && type == PH_ENCODE_IP) {
             if constexpr (REL) {
                 const uint32_t fi = i * (PT / 32) + warp;
@@ -248,6 +275,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             }
         } else if (type == PH_PREDICT) {
             float *w = reinterpret_cast<float *>(dsm);
+            if (tid == 0) s_pcache[0] = ~0u;  // dsm is overwritten: no pass stays staged
             for (int t = tid; t < kMlpParams; t += PT) {
                 const float v = S.pparams[t];
                 w[t] = S.pbf16 ? __bfloat162float(__float2bfloat16_rn(v)) : v;
@@ -271,7 +299,7 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
             // the group's histograms are consumed: leave them zero for the next stage
             for (uint32_t t = tid; t < S.G * 32; t += PT) S.hist[bbase * 32 + t] = 0;
         } else if (type == PH_ENCODE || type == PH_REENCODE) {
-            // learned sizing: eight frames per item, one warp each, offsets by warp look-back
+            // learned sizing: one frame per warp, offsets by warp look-back
             const uint32_t fi = i * (PT / 32) + warp;
             const bool retry = type == PH_REENCODE;
             if (fi < gframes) {
@@ -312,18 +340,6 @@ __global__ void __launch_bounds__(PT, 2) k_stage_persistent(PLaunch L) {
         __threadfence();
         if (abort_item) {
             // no reservation or statistics after an error
-        } else if (type == PH_SIZE) {
-            // the group's exact sizes are complete: reserve its slots (and clear the sums for the next stage)
-            for (uint32_t jj = tid; jj < S.G; jj += PT) {
-                const uint64_t want_b =
-                    atomicExch(reinterpret_cast<unsigned long long *>(&S.sizes[bbase + jj]), 0ull) + S.data_start;
-                EncResult &rs = S.res[bbase + jj];
-                rs.total = 0;
-                rs.overflow = 0;
-                rs.err_sq = 0;
-                rs.norm_sq = 0;
-                cdev::reserve_slot(want_b, S.dev, S.host, &S.tgt[bbase + jj], L.status);
-            }
         } else if (type == PH_SIZE_W || type == PH_ENCODE_IP) {
             // the group's frame lengths are complete: frame offsets (warp per block) and the group's slots (the
             // in-place phase with learned sizing keeps every predicted slot its block fits)
@@ -448,10 +464,13 @@ int prepare_prec(size_t smem) {
         cudaFuncAttributes fa{};
         if (cudaFuncGetAttributes(&fa, k_stage_persistent<PREC, REL, UM>) == cudaSuccess) {
             const int regs = ((fa.numRegs > 0 ? fa.numRegs : 255) + 7) & ~7;
+            constexpr int PT = kPT<UM>;
             const int by_regs = 65536 / (regs * PT);
             const int by_smem = int((228u * 1024u) / (smem + fa.sharedSizeBytes + 1024u));
             per_sm = by_regs < by_smem ? by_regs : by_smem;
             if (per_sm > 2048 / PT) per_sm = 2048 / PT;
+            // each CTA of a tcgen05 launch holds its TMEM columns for the launch: no more than the SM's 512
+            if (UM && per_sm > int(512u / gdev::umma_pass_tmem_cols(0))) per_sm = int(512u / gdev::umma_pass_tmem_cols(0));
             if (per_sm < 1) per_sm = 1;
         }
         Shape::grid = (sms > 0 ? sms : 1) * per_sm;
@@ -464,7 +483,7 @@ int launch_stage_prec(const PLaunch &a, size_t smem, cudaStream_t s, int *grid_o
     using Shape = LaunchShape<PREC, REL, UM>;
     if (Shape::attr_smem < smem || !Shape::grid) return QSIM_E_INVALID;
     const int grid = Shape::grid;
-    k_stage_persistent<PREC, REL, UM><<<grid, PT, smem, s>>>(a);
+    k_stage_persistent<PREC, REL, UM><<<grid, kPT<UM>, smem, s>>>(a);
     if (grid_out) *grid_out = grid;
     count_launch();
     return QSIM_OK;

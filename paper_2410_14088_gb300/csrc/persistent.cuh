@@ -11,22 +11,22 @@
 namespace qsim {
 
 enum PhaseType : uint32_t {
-    PH_DECODE = 0,   // eight frames per item (one warp each), leading phase ops applied
+    PH_DECODE = 0,   // persistent_frames_per_item(um) frames per item (one warp each), leading phase ops applied
     PH_PASS = 1,     // one tile of gate pass `arg`
-    PH_SIZE = 2,     // one frame's exact size; the last item reserves the group's slots
+    PH_SIZE = 2,     // (not emitted: exact sizing uses PH_SIZE_W)
     PH_PREDICT = 3,  // one item: predicted sizes and slot reservation for the group
     PH_ENCODE = 4,   // one frame; the last item folds the group's error partials into the stage totals
     PH_FIX = 5,      // one item: exact slots for blocks whose prediction was too small
     PH_REENCODE = 6, // one frame of an overflowed block (others skip)
-    PH_SIZE_W = 7,   // exact sizing, eight frames per item (one warp each): widths and frame length;
+    PH_SIZE_W = 7,   // exact sizing, persistent_frames_per_item(um) frames per item (one warp each): widths and frame length;
                      // the last item turns the lengths into frame offsets and reserves the group's slots
-    PH_ENCODE_W = 8, // exact sizing, eight frames per item (one warp each) at the known offsets; the last
+    PH_ENCODE_W = 8, // exact sizing, persistent_frames_per_item(um) frames per item (one warp each) at the known offsets; the last
                      // item folds the group's error partials into the stage totals
-    PH_ENCODE_IP = 9, // relative-bound codec: eight frames per item (one warp each) encoded over their own
+    PH_ENCODE_IP = 9, // relative-bound codec: persistent_frames_per_item(um) frames per item (one warp each) encoded over their own
                       // amplitudes; the last item turns the lengths into frame offsets, reserves the group's
                       // exact slots (with learned sizing: keeps every predicted slot its block fits) and folds
                       // the error partials into the stage totals
-    PH_COPY = 10      // relative-bound codec: eight frames per item (one warp each) copied into their slots
+    PH_COPY = 10      // relative-bound codec: persistent_frames_per_item(um) frames per item (one warp each) copied into their slots
 };
 
 struct PPhase {
@@ -34,6 +34,10 @@ struct PPhase {
 };
 
 constexpr int kMaxPhases = 128;
+// frames per work item of the frame-parallel phases (one warp each; the kernel's CTAs have 32 x this many threads):
+// 4 in launches whose dense ops run on tcgen05 (128-thread CTAs, one thread per index group of a width-5 op, four
+// CTAs per SM filling its TMEM), else 8 (256-thread CTAs, two per SM)
+constexpr uint32_t persistent_frames_per_item(bool um) { return um ? 4u : 8u; }
 constexpr uint32_t kNoGroup = 0xffffffffu;
 
 // One segment of the work queue: one stage of one circuit. The queue holds

@@ -64,8 +64,8 @@ def test_tcgen05_compressed_runs():
         assert st.fidelity(ideal) >= 0.999
     st = qsim.run(qsim.plan_stages(c, tcgen05=1, **dict(kw, prec=qsim.PREC_BF16X3)))
     assert st.fidelity(ideal) >= 0.999
-    # the persistent stage kernel runs the same TF32 MMAs on tcgen05 (two threads per index group in its 256-thread
-    # CTAs): the same streams as the stream engine, byte for byte
+    # the persistent stage kernel runs the same TF32 MMAs on tcgen05 (128-thread CTAs, one thread per index group):
+    # the same streams as the stream engine, byte for byte
     a = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, tcgen05=1, **kw))
     b = qsim.run(qsim.plan_stages(c, tcgen05=1, **kw))
     for blk in range(64):
