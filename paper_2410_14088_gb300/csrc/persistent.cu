@@ -95,6 +95,18 @@ __global__ void __launch_bounds__(kPT<UM>, 512 / kPT<UM>) k_stage_persistent(PLa
     // phase of the same group skip the wait (the counters only grow within a launch)
     uint64_t dep_key = ~0ull;
     if (tid == 0) nx_item = atomicAdd(L.ctr, 1u);
+    // thread 0: a done counter of a per-item phase whose increments this CTA holds back, and their number; they are
+    // added (after a fence) when the CTA completes an item of another phase, before it waits on any dependency and
+    // when it leaves, so a CTA that waits never holds counts another CTA waits for
+    uint32_t *pend_done = nullptr;
+    uint32_t pend_cnt = 0;
+    auto flush = [&]() {
+        if (pend_cnt) {
+            __threadfence();
+            atomicAdd(pend_done, pend_cnt);
+            pend_cnt = 0;
+        }
+    };
     // thread 0: wait for the item's dependencies (the group's previous phase; for its first phase the slot's
     // previous group and the circuit's previous stage); returns 1 when the item must skip its work (a device
     // error, or a wait that ran out)
@@ -106,6 +118,7 @@ __global__ void __launch_bounds__(kPT<UM>, 512 / kPT<UM>) k_stage_persistent(PLa
         while (p + 1 < S.nphases && r >= S.ph_start[p + 1]) ++p;
         const uint64_t key = uint64_t(q) * kMaxPhases + p;
         if (key == dep_key) return ld_relaxed_u32(reinterpret_cast<const uint32_t *>(L.status)) != 0;
+        flush();
         const uint32_t *flag = nullptr, *flag2 = nullptr;
         uint32_t need = 0;
         if (p > 0) {
@@ -146,6 +159,8 @@ __global__ void __launch_bounds__(kPT<UM>, 512 / kPT<UM>) k_stage_persistent(PLa
             if (it < L.total_items) {
                 nx_item = atomicAdd(L.ctr, 1u);
                 uint32_t hi = L.nseg - 1;
+                if (s_seg != ~0u && it >= S.item_begin && it - S.item_begin < uint64_t(S.ngroups) * S.per_group)
+                    lo = hi = s_seg;  // still in the segment whose descriptor is staged
                 while (lo < hi) {
                     const uint32_t mid = (lo + hi + 1) >> 1;
                     if (__ldg(reinterpret_cast<const unsigned long long *>(&L.segs[mid].item_begin)) <= it)
@@ -326,8 +341,11 @@ __global__ void __launch_bounds__(kPT<UM>, 512 / kPT<UM>) k_stage_persistent(PLa
         uint32_t *done = L.done + uint64_t(q) * kMaxPhases + p;
         if (!by_arrival) {
             if (tid == 0) {
-                __threadfence();
-                atomicAdd(done, 1u);
+                if (done != pend_done) {
+                    flush();
+                    pend_done = done;
+                }
+                ++pend_cnt;
             }
             continue;
         }
@@ -413,6 +431,7 @@ __global__ void __launch_bounds__(kPT<UM>, 512 / kPT<UM>) k_stage_persistent(PLa
             }
         }
     }
+    if (tid == 0) flush();
     if constexpr (UM) {
         // after an MMA wait that ran out, wait (bounded) once more for that op's MMAs before TMEM is freed
         if (!mma_ok) umma::mbar_wait(umma::smem_addr(&PS.mbar), mphase ^ 1u, gdev::kUmmaWaitNs);
