@@ -90,7 +90,7 @@ def parse_args():
     ap.add_argument("--no-tune", action="store_true", help="batch workload: fixed m, k instead of the autotuner")
     ap.add_argument("--tune", action="store_true",
                     help="single-circuit workloads: pick m, k, inner (and streams) with the autotuner first "
-                         "(not timed; m in 18..24, k in 3..5 in persistent mode, 3..6 otherwise)")
+                         "(not timed; m in 18..24, k in 3..6: 3..5 in persistent mode unless TF32 on tcgen05)")
     ap.add_argument("--depth", type=int, default=14)
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end measurement (long workloads)")
     ap.add_argument("--cap-gib", type=float, default=0.0, help="device tier cap (pinned host holds the rest)")
@@ -416,7 +416,8 @@ def run_ours(args, rank, world, dist):
     if args.tune:
         t0 = time.perf_counter()
         base = qsim.default_config(init_basis=circ.init_basis, **kw)
-        kmax = 5 if args.mode == "persistent" else 6
+        # the persistent kernel fuses width 6 only as TF32 on tcgen05
+        kmax = 6 if args.mode == "streams" or (args.prec == "tf32" and args.mma == "tcgen05") else 5
         best, secs, cand = qsim.autotune(circ, base, m=(18, min(24, n - 2)), k=(3, kmax), inner=(2, 5),
                                          streams=(1, 2) if args.mode == "streams" else (1,),
                                          prefix_gates=min(len(circ.gates), 160), reps=1, max_working_log2=n - 2)

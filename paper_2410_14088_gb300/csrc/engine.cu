@@ -540,8 +540,7 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                 Op wide;
                 const Op *opp = &st.ops[oi];
                 if (opp->type == OP_DENSE && (opp->k == 3 || opp->k == 4) && ps.T == 12 && p->cfg.tcgen05 &&
-                    (p->cfg.prec == QSIM_PREC_TF32 ||
-                     (p->cfg.prec == QSIM_PREC_BF16X3 && p->cfg.mode == QSIM_MODE_STREAMS))) {
+                    (p->cfg.prec == QSIM_PREC_TF32 || p->cfg.prec == QSIM_PREC_BF16X3)) {
                     wide = widen_dense(*opp, ps, 5);
                     opp = &wide;
                 }
@@ -557,21 +556,20 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                         od.tq[j] = t;
                     }
                     const uint32_t min_k = p->cfg.prec == QSIM_PREC_TF32 ? 3u : 4u;
-                    // k = 5 TF32 ops of the stream engine's 4096-amplitude passes on tcgen05 when asked for
-                    // (one thread per index group: the complement ordered for that gather)
-                    const bool um6 = p->cfg.tcgen05 && p->cfg.prec == QSIM_PREC_TF32 && op.k == 6 && ps.T == 12 &&
-                                     p->cfg.mode == QSIM_MODE_STREAMS;
-                    // width 5 (and the widened 3 and 4): TF32 in both modes, split BF16 in streams mode (its form
-                    // needs the stream engine's 128-thread CTAs); width 6: TF32 in streams mode
+                    // dense ops of 4096-amplitude passes on tcgen05 when asked for (one thread per index group of a
+                    // 128-thread CTA, in both modes: the complement ordered for that gather): width 5 (and the
+                    // widened 3 and 4) in TF32 or split BF16, width 6 in TF32
+                    const bool um6 = p->cfg.tcgen05 && p->cfg.prec == QSIM_PREC_TF32 && op.k == 6 && ps.T == 12;
                     const bool um = um6 || (p->cfg.tcgen05 && op.k == 5 && ps.T == 12 &&
-                                            (p->cfg.prec == QSIM_PREC_TF32 ||
-                                             (p->cfg.prec == QSIM_PREC_BF16X3 && p->cfg.mode == QSIM_MODE_STREAMS)));
+                                            (p->cfg.prec == QSIM_PREC_TF32 || p->cfg.prec == QSIM_PREC_BF16X3));
                     order_complement(od, ps.T,
                                      !um && p->cfg.prec != QSIM_PREC_FP32 && op.k >= min_k && op.k <= 5 &&
                                          ps.T == 12);
                     od.mat = mats.size();
                     for (const cd &v : op.u) mats.push_back(make_float2(float(v.real()), float(v.imag())));
-                    P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << (2 * op.k));
+                    // the matrix area serves the CUDA-core form only (the tensor-core forms read B tables)
+                    if (!um && !(p->cfg.prec != QSIM_PREC_FP32 && op.k >= min_k && op.k <= 5 && ps.T == 12))
+                        P.mat_elems = std::max<uint32_t>(P.mat_elems, 1u << (2 * op.k));
                     if (p->cfg.prec != QSIM_PREC_FP32 && ((op.k >= 3 && op.k <= 5) || um6)) {
                         bfr.resize((bfr.size() + 3) & ~size_t(3));  // 16-byte aligned tables
                         od.bfrag = bfr.size();
@@ -1173,7 +1171,7 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
 
     uint64_t total_groups = 0;
     size_t max_pass_bytes = 0;
-    bool um_any = false;  // tcgen05 passes in the launch (TF32): the kernel holds TMEM and an MMA mbarrier
+    bool um_any = false;  // tcgen05 passes in the launch: the kernel holds TMEM and an MMA mbarrier
     for (const SegRef &sr : order) {
         const RunCtx &R = *rs[sr.c];
         const StageDev &sd = R.pd->stages[sr.si];
@@ -1183,11 +1181,12 @@ static int run_persistent(const std::vector<RunCtx *> &rs, bool one_launch, cuda
                                                           size_t(ps.mat_elems) * sizeof(float2) +
                                                           umma_pass_smem(ps.umma));
             um_any |= (ps.umma & 1u) != 0;
-            if (ps.kmax > 5) return set_error(QSIM_E_INVALID, "persistent mode fuses at most k = 5 qubits");
+            if (ps.kmax > 5 && !(ps.umma & 8u))
+                return set_error(QSIM_E_INVALID, "persistent mode fuses k = 6 only as TF32 on tcgen05");
         }
     }
-    if (um_any && prec != QSIM_PREC_TF32)
-        return set_error(QSIM_E_INVALID, "internal: tcgen05 passes in the persistent kernel need TF32");
+    if (um_any && prec == QSIM_PREC_FP32)
+        return set_error(QSIM_E_INVALID, "internal: tcgen05 passes in an FP32 plan");
     std::vector<std::unique_ptr<PBlockBufs>> bb(rs.size());
     int rc;
     for (size_t c = 0; c < rs.size(); ++c) {

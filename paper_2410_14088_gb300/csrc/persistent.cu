@@ -55,8 +55,9 @@ __device__ __forceinline__ EncTarget load_target(const EncTarget *t) {
     return r;
 }
 
-// REL: the relative-bound codec (QSZR) in the decode phase and the in-place exact phases. UM: the plan's TF32
-// dense ops of width 3 to 5 run on tcgen05 (TMEM accumulator and MMA mbarrier held by each CTA for the launch).
+// REL: the relative-bound codec (QSZR) in the decode phase and the in-place exact phases. UM: the plan's dense ops
+// of width 3 to 5 (TF32 or split BF16) and 6 (TF32) run on tcgen05 (TMEM accumulator and MMA mbarrier held by each
+// CTA for the launch).
 template <int PREC, bool REL, bool UM>
 __global__ void __launch_bounds__(kPT<UM>, 512 / kPT<UM>) k_stage_persistent(PLaunch L) {
     constexpr int PT = kPT<UM>;
@@ -513,7 +514,8 @@ template <bool REL>
 int prepare_codec(int prec, size_t smem, bool um) {
     if (prec == QSIM_PREC_TF32)
         return um ? prepare_prec<QSIM_PREC_TF32, REL, true>(smem) : prepare_prec<QSIM_PREC_TF32, REL, false>(smem);
-    if (prec == QSIM_PREC_BF16X3) return prepare_prec<QSIM_PREC_BF16X3, REL, false>(smem);
+    if (prec == QSIM_PREC_BF16X3)
+        return um ? prepare_prec<QSIM_PREC_BF16X3, REL, true>(smem) : prepare_prec<QSIM_PREC_BF16X3, REL, false>(smem);
     return prepare_prec<QSIM_PREC_FP32, REL, false>(smem);
 }
 
@@ -522,7 +524,9 @@ int launch_codec(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *g
     if (prec == QSIM_PREC_TF32)
         return um ? launch_stage_prec<QSIM_PREC_TF32, REL, true>(a, smem, s, grid)
                   : launch_stage_prec<QSIM_PREC_TF32, REL, false>(a, smem, s, grid);
-    if (prec == QSIM_PREC_BF16X3) return launch_stage_prec<QSIM_PREC_BF16X3, REL, false>(a, smem, s, grid);
+    if (prec == QSIM_PREC_BF16X3)
+        return um ? launch_stage_prec<QSIM_PREC_BF16X3, REL, true>(a, smem, s, grid)
+                  : launch_stage_prec<QSIM_PREC_BF16X3, REL, false>(a, smem, s, grid);
     return launch_stage_prec<QSIM_PREC_FP32, REL, false>(a, smem, s, grid);
 }
 

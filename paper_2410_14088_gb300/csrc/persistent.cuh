@@ -107,7 +107,7 @@ struct PLaunch {
 
 // pass_bytes: the largest tile + pass blob + matrix area of the launch's passes
 size_t persistent_smem_bytes(size_t pass_bytes);
-// um: the launch's passes carry tcgen05 dense ops (TF32 only)
+// um: the launch's passes carry tcgen05 dense ops (TF32 widths 3 to 6, or split BF16 widths 3 to 5)
 int prepare_stage_persistent(int prec, size_t smem, bool rel = false, bool um = false);
 int launch_stage_persistent(const PLaunch &a, int prec, size_t smem, cudaStream_t s, int *grid, bool rel = false,
                             bool um = false);

@@ -579,8 +579,8 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
     if (cfg->prec > QSIM_PREC_BF16X3) return set_error(QSIM_E_INVALID, "bad precision %u", cfg->prec);
     if (cfg->tcgen05 > 1) return set_error(QSIM_E_INVALID, "tcgen05 is 0 or 1");
     if (cfg->mode > QSIM_MODE_PERSISTENT) return set_error(QSIM_E_INVALID, "bad mode %u", cfg->mode);
-    if (cfg->mode == QSIM_MODE_PERSISTENT && cfg->k > 5)
-        return set_error(QSIM_E_INVALID, "persistent mode fuses at most k = 5 qubits");
+    if (cfg->mode == QSIM_MODE_PERSISTENT && cfg->k > 5 && !(cfg->tcgen05 && cfg->prec == QSIM_PREC_TF32))
+        return set_error(QSIM_E_INVALID, "persistent mode fuses k = 6 only as TF32 on tcgen05");
     if (cfg->codec > QSIM_CODEC_QSZR) return set_error(QSIM_E_INVALID, "bad codec %u", cfg->codec);
     if (cfg->sizing > QSIM_SIZING_PREDICT) return set_error(QSIM_E_INVALID, "bad sizing %u", cfg->sizing);
     if (cfg->mode == QSIM_MODE_STREAMS && (cfg->streams < 1 || cfg->streams > 16))

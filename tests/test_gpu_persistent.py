@@ -1,7 +1,8 @@
 """Persistent stage kernel (one launch per stage over a queue of work items,
 optionally the stage loop captured into one CUDA graph): byte-identical
 compressed state to the stream engine, with exact and learned sizing, all
-gate precisions, TF32 dense ops of width 3-5 on tcgen05, and a bounded
+gate precisions, dense ops on tcgen05 (TF32 widths 3-6, split BF16 widths
+3-5), and a bounded
 dependency wait that ends the run with QSIM_E_TIMEOUT instead of hanging."""
 import numpy as np
 import pytest
@@ -63,11 +64,38 @@ def test_persistent_bounded_wait_reports_timeout():
     assert st.fidelity(oracle.simulate(c)) >= 0.99
 
 
-def test_persistent_rejects_k6():
+def test_persistent_k6_only_on_tcgen05_tf32():
+    # width-6 ops in the persistent kernel exist only in the TF32 tcgen05 form; the others are rejected at planning
     c = inputs.random_brick(16, 2, 1)
-    with pytest.raises(qsim.QsimError) as ei:
-        qsim.plan_stages(c, m=10, k=6, mode=qsim.MODE_PERSISTENT)
-    assert ei.value.code == qsim.E_INVALID
+    for kw in (dict(), dict(prec=qsim.PREC_TF32), dict(prec=qsim.PREC_BF16X3, tcgen05=1)):
+        with pytest.raises(qsim.QsimError) as ei:
+            qsim.plan_stages(c, m=10, k=6, mode=qsim.MODE_PERSISTENT, **kw)
+        assert ei.value.code == qsim.E_INVALID
+    qsim.plan_stages(c, m=10, k=6, mode=qsim.MODE_PERSISTENT, prec=qsim.PREC_TF32, tcgen05=1)
+
+
+def test_persistent_tcgen05_width6_matches_streams():
+    # TF32 width-6 ops on tcgen05 inside the persistent kernel: the stream engine's MMAs, the same streams
+    c = inputs.random_brick(18, 8, 3)
+    kw = dict(m=12, inner=2, k=6, eps=1e-3, prec=qsim.PREC_TF32, tcgen05=1)
+    plan = qsim.plan_stages(c, **kw)
+    assert any(op["type"] == 0 and op["nq"] == 6 for s in range(plan.nstages) for op in plan.stage_ops(s))
+    ref = qsim.run(plan)
+    for graph in (0, 1):
+        per = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, graph=graph, **kw))
+        assert streams_of(ref, 64) == streams_of(per, 64)
+    assert per.fidelity(oracle.simulate(c)) >= 0.99
+
+
+@pytest.mark.parametrize("k", [3, 4, 5])
+def test_persistent_tcgen05_bf16x3_matches_streams(k):
+    # split-BF16 dense ops (widths 3-5) on tcgen05 inside the persistent kernel: the same streams as the stream engine
+    c = inputs.random_brick(18, 8, 4)
+    kw = dict(m=11, inner=2, k=k, eps=1e-3, prec=qsim.PREC_BF16X3, tcgen05=1)
+    ref = qsim.run(qsim.plan_stages(c, **kw))
+    per = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, graph=1, **kw))
+    assert streams_of(ref, 128) == streams_of(per, 128)
+    assert per.fidelity(oracle.simulate(c)) >= 0.99
 
 
 @pytest.mark.parametrize("k", [3, 4, 5])
