@@ -304,6 +304,25 @@ __device__ __forceinline__ bool umma_commit_wait(const PassSmem &S, uint32_t &ph
 
 // Row g of D (TMEM lane g: Re of the 32 outputs in columns 0..31, Im in 32..63) back to the group's tile
 // positions.
+// The swizzled tile offsets of a width-5 op's 32 columns from its five basis columns: the column map and the
+// swizzle are linear over GF(2), so osw[j] is the XOR of osw[2^b] over the set bits b of j (osw[0] = 0). Five
+// shared-memory reads per thread instead of 32.
+struct ColBasis {
+    uint32_t b[5];
+};
+__device__ __forceinline__ ColBasis col_basis(const uint32_t *osw) {
+    ColBasis c;
+#pragma unroll
+    for (uint32_t t = 0; t < 5; ++t) c.b[t] = osw[1u << t];
+    return c;
+}
+// Step i of a walk over the 32 columns in Gray-code order: column gray(i) = i ^ (i >> 1), whose offset differs from
+// the previous step's by basis column ctz(i) (one XOR into a running address)
+__device__ __forceinline__ constexpr uint32_t gray5(uint32_t i) { return i ^ (i >> 1); }
+__device__ __forceinline__ constexpr uint32_t ctz5(uint32_t i) {
+    return (i & 1u) ? 0u : (i & 2u) ? 1u : (i & 4u) ? 2u : (i & 8u) ? 3u : 4u;
+}
+
 __device__ __forceinline__ void umma_epilogue(float2 *tile, uint32_t base, const uint32_t *osw, const PassSmem &S) {
     umma::fence_after_sync();
     const uint32_t taddr = S.tmem + ((32u * (threadIdx.x >> 5)) << 16);
@@ -339,12 +358,15 @@ __device__ __forceinline__ bool apply_dense_umma(float2 *tile, uint32_t bsm, con
     const uint32_t g = threadIdx.x;
     const uint32_t base = cb[g & 63u] ^ cb[64u + (g >> 6)];
     {
+        const ColBasis cbs = col_basis(osw);
         uint32_t re[32], im[32];
+        uint32_t a = base;
 #pragma unroll
-        for (uint32_t j = 0; j < 32; ++j) {
-            const float2 v = tile[base ^ osw[j]];
-            re[j] = f32_to_tf32(v.x);
-            im[j] = f32_to_tf32(v.y);
+        for (uint32_t i = 0; i < 32; ++i) {
+            if (i) a ^= cbs.b[ctz5(i)];
+            const float2 v = tile[a];
+            re[gray5(i)] = f32_to_tf32(v.x);
+            im[gray5(i)] = f32_to_tf32(v.y);
         }
         // row g of A is TMEM lane g: Re parts in columns kUmmaACol.., Im parts 32 further (the tile stays as it is)
         const uint32_t ta = S.tmem + ((32u * (g >> 5)) << 16) + kUmmaACol;
@@ -444,12 +466,15 @@ __device__ __forceinline__ bool apply_dense_umma3(float2 *tile, uint32_t bsm, co
     static_assert(NT == 128, "one thread per index group");
     const uint32_t g = threadIdx.x;
     const uint32_t base = cb[g & 63u] ^ cb[64u + (g >> 6)];
+    const ColBasis cbs = col_basis(osw);
     float x[64];  // K order: Re parts of inputs 0..31, then Im parts
+    uint32_t a = base;
 #pragma unroll
-    for (uint32_t j = 0; j < 32; ++j) {
-        const float2 v = tile[base ^ osw[j]];
-        x[j] = v.x;
-        x[32 + j] = v.y;
+    for (uint32_t i = 0; i < 32; ++i) {
+        if (i) a ^= cbs.b[ctz5(i)];
+        const float2 v = tile[a];
+        x[gray5(i)] = v.x;
+        x[32 + gray5(i)] = v.y;
     }
     __syncthreads();  // every amplitude of the tile is in registers
     uint8_t *arow = reinterpret_cast<uint8_t *>(tile) + (g >> 3) * 1024u + (g & 7u) * 128u;
