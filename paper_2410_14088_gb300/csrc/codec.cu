@@ -68,6 +68,23 @@ __global__ void __launch_bounds__(NT, 3) k_decode(const BlockRef *__restrict__ i
     }
 }
 
+// Random access: frame frames[i].y of block frames[i].x (slot table entry) decoded into out + i * F, one warp per
+// frame; no leading phase ops, no histogram.
+template <bool REL>
+__global__ void __launch_bounds__(NT, 3) k_decode_frames(const BlockSlot *__restrict__ table,
+                                                      const uint2 *__restrict__ frames, uint32_t nitems, int m,
+                                                      float2 *__restrict__ out, int *status) {
+    const FrameGeom g = geom(m);
+    __shared__ uint32_t s_hist[NW][32];
+    const int warp = threadIdx.x >> 5;
+    for (uint64_t item = uint64_t(blockIdx.x) * NW + warp; item < nitems; item += uint64_t(gridDim.x) * NW) {
+        const uint2 bf = frames[item];
+        const BlockSlot sl = table[bf.x];
+        decode_frame_warp<0, false, REL>(sl.ptr, sl.bytes, g, m, bf.y, out + item * g.F, nullptr, s_hist[warp],
+                                         status, nullptr, nullptr, 0, nullptr, 0, 0);
+    }
+}
+
 __global__ void __launch_bounds__(NT) k_encode(const float2 *__restrict__ wv, uint32_t nblocks, int m, int e,
                                                const EncTarget *__restrict__ tgt, EncResult *__restrict__ res,
                                                int only_overflowed, const uint32_t *__restrict__ ids,
@@ -423,6 +440,16 @@ static void decode_table(const BlockSlot *table, const uint32_t *ids, uint32_t n
         k_decode<2, REL><<<grid, NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist, status, pre);
     else
         k_decode<kMaxPreOps, REL><<<grid, NT, 0, s>>>(nullptr, table, ids, nblocks, m, wv, hist, status, pre);
+}
+
+void launch_decode_frames(const BlockSlot *table, const uint2 *frames, uint32_t nitems, int m, float2 *out,
+                          int *status, cudaStream_t s, bool rel) {
+    const unsigned grid = grid_for((uint64_t(nitems) + NW - 1) / NW, 152 * 8);
+    if (rel)
+        k_decode_frames<true><<<grid, NT, 0, s>>>(table, frames, nitems, m, out, status);
+    else
+        k_decode_frames<false><<<grid, NT, 0, s>>>(table, frames, nitems, m, out, status);
+    count_launch();
 }
 
 void launch_decode_table(const BlockSlot *table, const uint32_t *ids, uint32_t nblocks, int m, float2 *wv,

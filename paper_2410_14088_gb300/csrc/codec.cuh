@@ -110,6 +110,10 @@ void launch_reserve(uint32_t nblocks, const uint64_t *need, uint64_t add_const, 
 void launch_copy_out(const float2 *wv, uint32_t nblocks, int m, const EncTarget *tgt, const uint32_t *ids,
                      BlockSlot *table, StageAccum *acc, int *status, cudaStream_t s);
 void launch_copy_in(const BlockRef *in, uint32_t nblocks, int m, float2 *wv, int *status, cudaStream_t s);
+// Frames frames[i] = (block id in table, frame index) decoded into out + i * min(2^m, 4096) (random access through
+// the stream's frame offsets)
+void launch_decode_frames(const BlockSlot *table, const uint2 *frames, uint32_t nitems, int m, float2 *out,
+                          int *status, cudaStream_t s, bool rel);
 void launch_gather_refs(const BlockSlot *table, const uint32_t *ids, uint32_t count, BlockRef *out,
                         cudaStream_t s);
 

@@ -2608,11 +2608,72 @@ int qsim_state_decompress(const qsim_state *st, float *d_out, void *cuda_stream)
     return QSIM_OK;
 }
 
+// Compressed states: only the frames (4096 amplitudes, or the whole block below 2^12) holding the requested
+// amplitudes are decoded, through the streams' frame offsets.
+static int amplitudes_by_frame(const qsim_state *st, const uint64_t *idx, size_t count, float *out) {
+    const uint32_t m = st->m, fl = m < 12 ? m : 12;
+    std::map<uint64_t, uint32_t> item;  // global frame number -> position in the decode list
+    for (size_t i = 0; i < count; ++i) item.emplace(idx[i] >> fl, 0);
+    std::vector<uint2> frames;
+    frames.reserve(item.size());
+    for (auto &kv : item) {
+        kv.second = uint32_t(frames.size());
+        frames.push_back(make_uint2(uint32_t(kv.first >> (m - fl)), uint32_t(kv.first & ((1ull << (m - fl)) - 1))));
+    }
+    const uint32_t chunk = uint32_t(std::min<size_t>(frames.size(), size_t(1) << (24 - fl)));  // 2^24 amplitudes
+    cudaStream_t s = nullptr;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    DevBuf<uint2> d_frames;
+    DevBuf<uint32_t> d_slot, d_local;
+    DevBuf<float2> buf, d_out;
+    int rc;
+    if ((rc = d_frames.alloc(frames.size())) || (rc = buf.alloc(uint64_t(chunk) << fl)) ||
+        (rc = d_slot.alloc(count)) || (rc = d_local.alloc(count)) || (rc = d_out.alloc(count))) {
+        cudaStreamDestroy(s);
+        return rc;
+    }
+    int *status = device_ctx(st->device).status;
+    CUDA_TRY(cudaMemcpyAsync(d_frames.p, frames.data(), frames.size() * sizeof(uint2), cudaMemcpyHostToDevice, s));
+    std::vector<float2> host(count);
+    for (size_t f0 = 0; f0 < frames.size(); f0 += chunk) {
+        const uint32_t cnt = uint32_t(std::min<size_t>(chunk, frames.size() - f0));
+        launch_decode_frames(st->table, d_frames.p + f0, cnt, int(m), buf.p, status, s,
+                             st->codec == QSIM_CODEC_QSZR);
+        std::vector<uint32_t> sel_slot, sel_local;
+        std::vector<size_t> sel_pos;
+        for (size_t i = 0; i < count; ++i) {
+            const uint32_t it = item[idx[i] >> fl];
+            if (it >= f0 && it < f0 + cnt) {
+                sel_slot.push_back(uint32_t(it - f0));
+                sel_local.push_back(uint32_t(idx[i] & ((1ull << fl) - 1)));
+                sel_pos.push_back(i);
+            }
+        }
+        CUDA_TRY(cudaMemcpyAsync(d_slot.p, sel_slot.data(), sel_slot.size() * 4, cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(d_local.p, sel_local.data(), sel_local.size() * 4, cudaMemcpyHostToDevice, s));
+        k_gather_amps<<<unsigned((sel_pos.size() + 255) / 256), 256, 0, s>>>(buf.p, d_slot.p, d_local.p,
+                                                                            sel_pos.size(), int(fl), d_out.p);
+        count_launch();
+        std::vector<float2> tmp(sel_pos.size());
+        CUDA_TRY(cudaMemcpyAsync(tmp.data(), d_out.p, tmp.size() * sizeof(float2), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        for (size_t t = 0; t < sel_pos.size(); ++t) host[sel_pos[t]] = tmp[t];
+    }
+    int code = read_status(status, s);
+    cudaStreamDestroy(s);
+    if (code) return set_error(code, "amplitudes: %s", status_text(code));
+    memcpy(out, host.data(), count * sizeof(float2));
+    return QSIM_OK;
+}
+
 int qsim_amplitudes(const qsim_state *st, const uint64_t *idx, size_t count, float *out) {
     if (!st || (count && (!idx || !out))) return set_error(QSIM_E_INVALID, "null argument");
     if (!count) return QSIM_OK;
     const uint32_t m = st->m;
     const uint64_t N = 1ull << st->n;
+    for (size_t i = 0; i < count; ++i)
+        if (idx[i] >= N) return set_error(QSIM_E_INVALID, "amplitude index out of range");
+    if (st->codec != QSIM_CODEC_NONE) return amplitudes_by_frame(st, idx, count, out);
     std::map<uint64_t, uint32_t> slot;
     for (size_t i = 0; i < count; ++i) {
         if (idx[i] >= N) return set_error(QSIM_E_INVALID, "amplitude index out of range");

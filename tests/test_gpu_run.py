@@ -169,6 +169,20 @@ def test_amplitudes_and_host_tier():
     np.testing.assert_array_equal(capped.amplitudes(idx), full[idx.astype(np.int64)])
 
 
+@pytest.mark.parametrize("m,codec", [(13, qsim.CODEC_QSZ1), (14, qsim.CODEC_QSZR), (9, qsim.CODEC_QSZ1),
+                                     (15, qsim.CODEC_NONE)])
+def test_amplitudes_equal_full_decompress(m, codec):
+    # the readout decodes only the frames (4096 amplitudes, or the whole block below 2^12) holding the requested
+    # indices: bit-equal to the same amplitudes of the fully decompressed state, repeated and unsorted indices included
+    c = inputs.random_brick(18, 6, 4)
+    st = qsim.run(qsim.plan_stages(c, m=m, inner=2, k=4, codec=codec))
+    full = state_c64(st)
+    rng = np.random.default_rng(5)
+    idx = rng.integers(0, 1 << 18, size=3000).astype(np.uint64)
+    idx = np.concatenate([idx, idx[:100], np.array([0, (1 << 18) - 1, 4095, 4096], dtype=np.uint64)])
+    np.testing.assert_array_equal(st.amplitudes(idx), full[idx.astype(np.int64)])
+
+
 def test_single_block_and_phaseflip_edges():
     # m = n: one block, no global qubits; phase flips on several blocks
     n = 12
