@@ -227,12 +227,15 @@ __global__ void __launch_bounds__(kPT<UM>, 512 / kPT<UM>) k_stage_persistent(PLa
             }
         } else if (type == PH_PASS) {
             if constexpr (UM) {
-                mma_ok &= gdev::pass_tile<PT, 5, PREC, true, true>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr,
+                // tile loads by cp.async (L1-cached): the item's dependencies were acquired by thread 0 (for this
+                // group and phase, in this item or an earlier one of this CTA) before the CTA barrier above, so the
+                // memory model orders them after the previous phase's writes; L1 starts empty at the launch
+                mma_ok &= gdev::pass_tile<PT, 5, PREC, false, true>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr,
                                                                    i, gb, PS, reinterpret_cast<float2 *>(dsm),
                                                                    L.status, &mphase, s_pcache,
                                                                    s_seg * 256u + S.ph[p].arg);
             } else {
-                gdev::pass_tile<PT, 5, PREC, true>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr, i, gb, PS,
+                gdev::pass_tile<PT, 5, PREC, false>(wv, S.passes[S.ph[p].arg], S.blob, S.mats, S.bfr, i, gb, PS,
                                                    reinterpret_cast<float2 *>(dsm), L.status, nullptr, s_pcache,
                                                    s_seg * 256u + S.ph[p].arg);
             }
