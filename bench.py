@@ -803,13 +803,26 @@ def run_batch_bench(args, rank, world, dist):
     print(json.dumps(line), flush=True)
 
 
+def code_digest(path):
+    """sha256[:16] of a source file's code: // comments, trailing blanks and
+    empty lines removed, so that a comment edit keeps a capture valid."""
+    import hashlib
+    import re
+    lines = []
+    with open(path) as f:
+        for line in f:
+            line = re.sub(r"//.*$", "", line.rstrip("\n")).rstrip()
+            if line:
+                lines.append(line)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()[:16]
+
+
 def traffic_for(kernel, alg_bytes_per_launch):
     """DRAM bytes per launch from the committed ncu summary, scaled to this
-    launch size; None when no capture matches the kernel's current source."""
+    launch size; None when no capture matches the kernel's current code."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
     if not os.path.exists(path):
         return None
-    import hashlib
     with open(path) as f:
         for line in f:
             if line.startswith("#") or not line.strip():
@@ -821,7 +834,7 @@ def traffic_for(kernel, alg_bytes_per_launch):
             sp = os.path.join(ROOT, src)
             if not os.path.exists(sp):
                 return None
-            if hashlib.sha256(open(sp, "rb").read()).hexdigest()[:16] != digest:
+            if code_digest(sp) != digest:
                 return None  # kernel changed since the counters were taken
             return dram_bytes / alg_bytes * alg_bytes_per_launch
     return None

@@ -917,8 +917,10 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
 // One tile of one pass: stage the pass blob and the 2^T amplitudes of tile
 // `cta` of the group's working vector g in shared memory (dyn: tile, then blob,
 // then matrix area), apply the pass's ops, store the tile back. CG selects
-// L2-only loads, needed when the working vector was written by other CTAs of
-// the same launch (the persistent stage kernel).
+// L2-only loads in registers instead of cp.async into shared memory (L1-cached);
+// a caller whose working vector was written by other CTAs of the same launch
+// may still take cp.async when a gpu-scope acquire of those writes' release,
+// followed by a CTA barrier, precedes the call (the persistent stage kernel).
 // With phase_io the caller owns the TMEM accumulator (S.tmem, 128 columns) and the MMA mbarrier (S.mbar) across
 // calls and keeps the mbarrier's phase parity in *phase_io; returns false when an MMA wait ran out.
 // With cache (shared memory: cache[0] the key of the pass staged in dyn, cache[1] whether its single tcgen05
