@@ -4,8 +4,8 @@
 Workload (default): QAOA MaxCut with p = 3 on a seeded random 3-regular graph
 of 32 vertices — an H layer, then 3 x (RZZ(gamma) on all 48 edges, RX(beta) on
 every qubit), 272 gates, complex64 state (32 GiB raw), eps = 1e-3
-(eb = eps * 2^-16 per real/imaginary part), SV blocks of 2^23 amplitudes,
-inner size 4 (working vectors of 2^27 amplitudes), gates fused to k = 5, commutation-aware partition with diagonal
+(eb = eps * 2^-16 per real/imaginary part), SV blocks of 2^25 amplitudes,
+inner size 3 (working vectors of 2^28 amplitudes), gates fused to k = 5, commutation-aware partition with diagonal
 gates exempt. The timed form is the tensor-core one with learned sizing: fused
 k-qubit gates as TF32 GEMMs on tcgen05, slots reserved by the trained size
 predictor. Beside it, on the same circuit ("forms"): the plain FP32 form
@@ -58,8 +58,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="tf32", choices=["fp32", "tf32", "bf16x3"])
     ap.add_argument("--n", type=int, default=32)
-    ap.add_argument("--m", type=int, default=23)
-    ap.add_argument("--inner", type=int, default=4)
+    ap.add_argument("--m", type=int, default=25)
+    ap.add_argument("--inner", type=int, default=3)
     ap.add_argument("--k", type=int, default=5)
     ap.add_argument("--streams", type=int, default=2)
     ap.add_argument("--eps", type=float, default=1e-3)

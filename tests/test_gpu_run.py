@@ -300,12 +300,12 @@ def test_repeated_runs_store_identical_streams():
 
 
 def test_bench_configuration_qaoa32_mirror():
-    # the default bench line's launch configuration at its full size (32 qubits, m = 23, inner 4, k = 5, TF32 on
+    # the default bench line's launch configuration at its full size (32 qubits, m = 25, inner 3, k = 5, TF32 on
     # tcgen05, commutation-aware partition with diagonal gates exempt, 2 streams, compressed), on the QAOA circuit
     # followed by its inverse: the ideal final state is |0...0>, so the simulated fidelity is |a_0| / ||b||
     c = inputs.qaoa_maxcut(32, 3, 1)
     mirror = inputs.Circuit(32, list(c.gates) + [inputs.dagger(g) for g in reversed(c.gates)], 0, "qaoa-mirror")
-    st = qsim.run(qsim.plan_stages(mirror, m=23, inner=4, k=5, eps=1e-3, prec=qsim.PREC_TF32, tcgen05=1,
+    st = qsim.run(qsim.plan_stages(mirror, m=25, inner=3, k=5, eps=1e-3, prec=qsim.PREC_TF32, tcgen05=1,
                                    reorder=1, diag_exempt=1, streams=2))
     assert st.stats.fidelity_lower_bound >= 0.99
     a0 = complex(st.amplitudes(np.array([0], dtype=np.uint64))[0])
@@ -320,6 +320,6 @@ def test_bench_configuration_qaoa32_mirror():
     assert np.max(rest) <= st.stats.err_norm_sum + 1e-6
     # sampled stored blocks re-encode byte for byte with the oracle (decoded values lie on the grid)
     eb = 1e-3 * 2.0 ** -16
-    for b in (0, 1, 200, 511):
+    for b in (0, 1, 77, 127):
         s_ = st.block_stream(b)
-        assert s_ == oracle.qsz_encode(oracle.qsz_decode(s_, 23), 23, eb), b
+        assert s_ == oracle.qsz_encode(oracle.qsz_decode(s_, 25), 25, eb), b
