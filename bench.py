@@ -79,6 +79,9 @@ def parse_args():
     ap.add_argument("--reorder", action=argparse.BooleanOptionalAction, default=True,
                     help="commutation-aware partition: gates may move before earlier gates they commute with "
                          "(--no-reorder: Algorithm 1 in circuit order)")
+    ap.add_argument("--pack", action=argparse.BooleanOptionalAction, default=True,
+                    help="with --reorder: each stage's gates gathered into tile passes and fused pass by pass "
+                         "(reorder mode 2; --no-pack keeps each stage's gates in partition order)")
     ap.add_argument("--train-n", type=int, default=0, help="qubits of the predictor's training circuits (0 = n)")
     ap.add_argument("--workload", default="qaoa", choices=["qft", "qaoa", "random", "mirror", "batch"],
                     help="qft: QFT + 4 x (RZ, CX ladder) on n qubits; qaoa: MaxCut p=3 on a random 3-regular "
@@ -340,6 +343,17 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def reorder_mode(args):
+    """qsim_config.reorder: 0 Algorithm 1 in circuit order, 1 commutation-aware stages, 2 and pass-aware order."""
+    return 2 if args.reorder and args.pack else 1 if args.reorder else 0
+
+
+def partition_name(args):
+    return ("Algorithm 1 in circuit order" if not args.reorder else
+            "commutation-aware (reorder), pass-aware order in each stage" if args.pack else
+            "commutation-aware (reorder)")
+
+
 def config_dict(args):
     if args.workload == "batch":
         cs = batch_workload(args)
@@ -350,7 +364,7 @@ def config_dict(args):
                 "circuits": len(cs), "n_qubits": [min(c.n for c in cs), max(c.n for c in cs)],
                 "gates": sum(len(c.gates) for c in cs), "eps": args.eps, "prec": args.prec,
                 "mode": "persistent (one launch for the batch)", "sizing": args.sizing,
-                "partition": "commutation-aware (reorder)" if args.reorder else "Algorithm 1 in circuit order",
+                "partition": partition_name(args),
                 "raw_state_gib": sum(8 << c.n for c in cs) / 2**30,
                 "l2_policy": "working set (all circuits' compressed stores) > L2 (129 MB); no flush"}
     name = {"qft": f"qft{args.n}+4x(rz,cx-ladder)", "qaoa": f"qaoa-maxcut p=3, 3-regular n={args.n}",
@@ -363,7 +377,7 @@ def config_dict(args):
                         f"{', mma=tcgen05' if args.mma == 'tcgen05' and args.prec != 'fp32' and args.mode == 'streams' else ''}",
             "error_bound": ("absolute eps*2^(-n/2) per component" if args.codec == "abs"
                             else "relative eps per component"),
-            "partition": ("commutation-aware (reorder)" if args.reorder else "Algorithm 1 in circuit order") +
+            "partition": partition_name(args) +
                          (", diagonal gates exempt" if args.diag_exempt else ""),
             "n_qubits": args.n, "gates": len(workload(args).gates), "block_log2": args.m, "inner": args.inner,
             "k": args.k, "eps": args.eps, "prec": args.prec,
@@ -395,7 +409,7 @@ def run_ours(args, rank, world, dist):
               graph=1 if args.graph else 0,
               sizing=qsim.SIZING_PREDICT if args.sizing == "predict" else qsim.SIZING_EXACT,
               predictor_margin=args.margin, diag_exempt=1 if args.diag_exempt else 0,
-              reorder=1 if args.reorder else 0, tcgen05=1 if args.mma == "tcgen05" else 0,
+              reorder=reorder_mode(args), tcgen05=1 if args.mma == "tcgen05" else 0,
               device_tier_cap_bytes=int(args.cap_gib * (1 << 30)),
               codec=qsim.CODEC_QSZR if args.codec == "rel" else qsim.CODEC_QSZ1)
     train_info = None
@@ -535,6 +549,10 @@ def run_ours(args, rank, world, dist):
             variants.append(("fp32_exact_sizing", dict(kw, prec=qsim.PREC_FP32, sizing=qsim.SIZING_EXACT, tcgen05=0)))
         if args.sizing == "predict":
             variants.append((headline.replace("_predict_sizing", "_exact_sizing"), dict(kw, sizing=qsim.SIZING_EXACT)))
+        if args.reorder and args.pack:
+            # the same partition with each stage's gates fused and laid out in partition order
+            variants.append((headline.replace("_predict_sizing", "_exact_sizing") + "_without_pass_order",
+                             dict(kw, sizing=qsim.SIZING_EXACT, reorder=1)))
         if args.reorder or args.diag_exempt:
             # the paper's partition: Algorithm 1 over the gates in circuit order, every gate counted
             variants.append((headline.replace("_predict_sizing", "_exact_sizing") + "_algorithm1_in_order",
@@ -675,7 +693,7 @@ def run_batch_bench(args, rank, world, dist):
     circuits = batch_workload(args)
     base = dict(eps=args.eps, prec=prec, mode=qsim.MODE_PERSISTENT,
                 sizing=qsim.SIZING_PREDICT if args.sizing == "predict" else qsim.SIZING_EXACT,
-                predictor_margin=args.margin, reorder=1 if args.reorder else 0)
+                predictor_margin=args.margin, reorder=reorder_mode(args))
     train_info = None
     if args.sizing == "predict":
         # training rows from exact-sizing runs of a training batch (seed 100+), not timed

@@ -80,6 +80,10 @@ typedef struct qsim_gate {
                                   one read and encodes at the known offsets in a second */
 #define QSIM_SIZING_PREDICT 1u /* learned size predictor reserves space; overflow re-encodes */
 
+#define QSIM_REORDER_NONE 0u   /* Algorithm 1 over the gates in circuit order */
+#define QSIM_REORDER_STAGES 1u /* commutation-aware stage partition */
+#define QSIM_REORDER_PASSES 2u /* commutation-aware stages + pass-aware order within each stage */
+
 typedef struct qsim_config {
     uint32_t m;           /* log2 amplitudes per SV block (the paper's b), 5..26 */
     uint32_t inner;       /* inner size i (Sec. 4.1); threshold = max(i, 2) */
@@ -97,9 +101,13 @@ typedef struct qsim_config {
     uint64_t device_tier_cap_bytes; /* bytes of compressed blocks kept on the device; 0 = no cap */
     uint64_t init_basis;  /* initial basis state |init_basis> (Sec. 4.2 initialisation) */
     double predictor_margin; /* predictor reservation = 2^pred * (1 + margin) */
-    uint32_t reorder;        /* 1: commutation-aware partition: a gate may be placed before earlier
-                                gates it commutes with (disjoint qubits, or both diagonal) when that
-                                keeps it in the current stage; 0 = Algorithm 1 in circuit order */
+    uint32_t reorder;        /* QSIM_REORDER_*: 0 = Algorithm 1 in circuit order; 1 = commutation-
+                                aware partition: a gate may be placed before earlier gates it
+                                commutes with (disjoint qubits, or both diagonal) when that keeps
+                                it in the current stage; 2 = that partition, and inside each stage
+                                a pass-aware order: gates are gathered into shared-memory tile
+                                passes (a non-diagonal gate joins a pass while the tile bits it
+                                needs fit, diagonal gates join any pass) and fused pass by pass */
     uint32_t tcgen05;        /* 1: TF32 and split-BF16 dense ops of width 5 on the 5th-generation
                                 tensor cores (tcgen05.mma, accumulator in tensor memory) in
                                 streams mode; 0: warp-level mma.sync */

@@ -163,6 +163,177 @@ int reorder_for_stages(std::vector<Gate> &gates, uint32_t n, uint32_t m, uint32_
     return QSIM_OK;
 }
 
+// Pass-aware order of one stage's gates (QSIM_REORDER_PASSES). Every tile
+// pass holds the low L working bits and at most T bits in all; a non-diagonal
+// gate needs its qubits among them, a diagonal gate needs none (its phase
+// index comes from any bits). List scheduling over the stage's commutation
+// order (two gates keep their order when they share a qubit, unless both are
+// diagonal), which also shapes the fusion that follows: the next gate is
+//   1. a ready non-diagonal gate that joins the dense op being built (the union
+//      of their qubits within k, and within the pass's T bits), fewest new op
+//      bits first, then fewest new tile bits;
+//   2. else a ready diagonal gate inside that op (the fuser folds it in);
+//   3. else every ready diagonal gate, placed together (the fuser gathers them
+//      into few diagonal ops); the dense op being built ends;
+//   4. else a ready non-diagonal gate that starts a new dense op, the one
+//      adding the fewest new tile bits;
+//   5. else the pass closes and the next one starts from the low L bits.
+// Ties go to the gate earliest in the stage. Gates [first, first + count) are
+// permuted in place (each gate still follows every gate it does not commute
+// with, so the stage is the same unitary); `breaks` receives the
+// stage-relative positions where a new pass starts and `masks` the tile bits of
+// each pass (breaks.size() + 1 entries). Returns false, leaving the gates as
+// they are, if a non-diagonal gate has a qubit outside the working vector
+// (which Algorithm 1's cut excludes).
+bool pack_stage_passes(std::vector<Gate> &gates, size_t first, size_t count, const std::vector<uint32_t> &inner,
+                       uint32_t n, uint32_t m, uint32_t T, uint32_t L, uint32_t k, std::vector<size_t> *breaks,
+                       std::vector<uint64_t> *masks) {
+    breaks->clear();
+    masks->clear();
+    auto wbit = [&](uint32_t q) -> int32_t {
+        if (q < m) return int32_t(q);
+        auto it = std::find(inner.begin(), inner.end(), q);
+        return it == inner.end() ? -1 : int32_t(m + (it - inner.begin()));
+    };
+    if (T > 63 || L > T) return false;
+    const uint64_t low = (1ull << L) - 1;
+    // need: working bits of a non-diagonal gate; dneed: those of a diagonal gate whose qubits are all
+    // working bits (one that a dense op can absorb), else 0
+    std::vector<uint64_t> need(count, 0), dneed(count, 0);
+    std::vector<char> isdiag(count, 0);
+    std::vector<std::vector<uint32_t>> succ(count);
+    std::vector<uint32_t> npred(count, 0);
+    {
+        std::vector<int64_t> last_nd(n, -1);
+        std::vector<std::vector<uint32_t>> diag_since(n);
+        std::vector<uint32_t> preds, qs;
+        for (size_t i = 0; i < count; ++i) {
+            const Gate &g = gates[first + i];
+            qs.clear();
+            if (g.phaseflip)
+                for (uint32_t q = 0; q < n; ++q) qs.push_back(q);
+            else
+                qs.assign(g.q, g.q + g.nq);
+            const bool d = g.diag || g.phaseflip;
+            isdiag[i] = d;
+            if (!d) {
+                for (uint32_t q : qs) {
+                    const int32_t w = wbit(q);
+                    if (w < 0 || w >= 64) return false;
+                    need[i] |= 1ull << w;
+                }
+            } else if (!g.phaseflip) {
+                uint64_t dm = 0;
+                bool all = true;
+                for (uint32_t q : qs) {
+                    const int32_t w = wbit(q);
+                    if (w < 0 || w >= 64) all = false;
+                    else dm |= 1ull << w;
+                }
+                dneed[i] = all ? dm : 0;
+            }
+            preds.clear();
+            for (uint32_t q : qs) {
+                if (last_nd[q] >= 0) preds.push_back(uint32_t(last_nd[q]));
+                if (!d) preds.insert(preds.end(), diag_since[q].begin(), diag_since[q].end());
+            }
+            std::sort(preds.begin(), preds.end());
+            preds.erase(std::unique(preds.begin(), preds.end()), preds.end());
+            for (uint32_t pj : preds) succ[pj].push_back(uint32_t(i));
+            npred[i] = uint32_t(preds.size());
+            for (uint32_t q : qs) {
+                if (d) {
+                    diag_since[q].push_back(uint32_t(i));
+                } else {
+                    last_nd[q] = int64_t(i);
+                    diag_since[q].clear();
+                }
+            }
+        }
+    }
+    std::set<uint32_t> ready_d, ready_n;
+    for (size_t i = 0; i < count; ++i)
+        if (!npred[i]) (isdiag[i] ? ready_d : ready_n).insert(uint32_t(i));
+    std::vector<uint32_t> order;
+    order.reserve(count);
+    uint64_t P = low;  // tile bits of the pass being filled
+    uint64_t act = 0;  // working bits of the dense op being built
+    auto place = [&](uint32_t i) {
+        order.push_back(i);
+        P |= need[i];
+        for (uint32_t s2 : succ[i])
+            if (--npred[s2] == 0) (isdiag[s2] ? ready_d : ready_n).insert(s2);
+    };
+    auto fits = [&](uint32_t i) { return __builtin_popcountll(P | need[i]) <= int(T); };
+    while (order.size() < count) {
+        uint32_t pick = UINT32_MAX;
+        if (act) {
+            int best = INT32_MAX;
+            for (uint32_t i : ready_n) {  // 1
+                if (__builtin_popcountll(act | need[i]) > int(k) || !fits(i)) continue;
+                const int cost = 64 * __builtin_popcountll(need[i] & ~act) + __builtin_popcountll(need[i] & ~P);
+                if (cost < best) {
+                    best = cost;
+                    pick = i;
+                    if (!cost) break;
+                }
+            }
+            if (pick != UINT32_MAX) {
+                ready_n.erase(pick);
+                act |= need[pick];
+                place(pick);
+                continue;
+            }
+            for (uint32_t i : ready_d)  // 2
+                if (dneed[i] && !(dneed[i] & ~act)) {
+                    pick = i;
+                    break;
+                }
+            if (pick != UINT32_MAX) {
+                ready_d.erase(pick);
+                place(pick);
+                continue;
+            }
+        }
+        if (!ready_d.empty()) {  // 3
+            while (!ready_d.empty()) {
+                const uint32_t i = *ready_d.begin();
+                ready_d.erase(ready_d.begin());
+                place(i);
+            }
+            act = 0;
+            continue;
+        }
+        int best = INT32_MAX;
+        for (uint32_t i : ready_n) {  // 4
+            const int add = __builtin_popcountll(need[i] & ~P);
+            if (add < best && fits(i)) {
+                best = add;
+                pick = i;
+                if (!add) break;
+            }
+        }
+        if (pick != UINT32_MAX) {
+            ready_n.erase(pick);
+            act = need[pick];
+            place(pick);
+            continue;
+        }
+        // 5; a DAG always has a ready gate, and every gate fits a fresh pass (k + L <= T)
+        if (ready_n.empty() || P == low) return false;
+        breaks->push_back(order.size());
+        masks->push_back(P);
+        P = low;
+        act = 0;
+    }
+    masks->push_back(P);
+    std::vector<Gate> out;
+    out.reserve(count);
+    for (uint32_t i : order) out.push_back(std::move(gates[first + i]));
+    for (size_t i = 0; i < count; ++i) gates[first + i] = std::move(out[i]);
+    return true;
+}
+
 // Embed matrix `u` acting on working bits `bits` (matrix bit j <-> bits[j])
 // into the space of the ascending working-bit set `S`.
 std::vector<cd> embed(const std::vector<cd> &u, const std::vector<uint32_t> &bits,
@@ -227,6 +398,7 @@ struct Fuser {
     std::set<uint32_t> csep_blockers;
     uint32_t last2[2] = {0, 0};    // qubits of the last two-qubit diagonal gate seen
     bool have_last2 = false;
+    uint64_t allowed = ~0ull;      // working bits a dense op may take (pass-aware mode: the pass's tile bits)
 
     int32_t working_bit(uint32_t q) const {
         if (q < m) return int32_t(q);
@@ -355,6 +527,8 @@ struct Fuser {
         std::set<uint32_t> uni(S.begin(), S.end());
         uni.insert(wb.begin(), wb.end());
         if (!active || uni.size() > k) return false;
+        for (uint32_t w : uni)
+            if (w >= 64 || !((allowed >> w) & 1ull)) return false;
         std::vector<uint32_t> NS(uni.begin(), uni.end());
         std::vector<cd> cur = embed(U, S, NS);
         std::vector<cd> gm = embed(g.u, wb, NS);
@@ -482,6 +656,14 @@ void narrow_csep_ops(std::vector<Op> &ops) {
     }
 }
 
+// shared-memory bytes of an op's data in its pass (descriptor, and for a diagonal op its tables)
+size_t pass_op_bytes(const Op &op) {
+    if (op.type == OP_CSEP) return kOpDescBytes + kCsepTableBytes + 48 * size_t(op.k);
+    if (op.type == OP_DENSE && op.k >= 3 && op.k <= 6)  // tensor-core offset tables: 128 + 2^k words
+        return kOpDescBytes + 4 * (128 + (size_t(1) << op.k));
+    return kOpDescBytes + (op.type == OP_DIAG ? 192 + 16 + (size_t(8) << op.k) : 0);
+}
+
 void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
     const uint32_t W = st.W;
     st.pre_ops.clear();
@@ -511,17 +693,10 @@ void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
     std::set<uint32_t> P;
     for (uint32_t b = 0; b < L; ++b) P.insert(b);
     std::vector<uint32_t> cur;
-    // shared-memory bytes of the pass's op data (descriptor, and for a diagonal op its tables)
-    auto op_bytes = [&](const Op &op) -> size_t {
-        if (op.type == OP_CSEP) return kOpDescBytes + kCsepTableBytes + 48 * size_t(op.k);
-        if (op.type == OP_DENSE && op.k >= 3 && op.k <= 6)  // tensor-core offset tables: 128 + 2^k words
-            return kOpDescBytes + 4 * (128 + (size_t(1) << op.k));
-        return kOpDescBytes + (op.type == OP_DIAG ? 192 + 16 + (size_t(8) << op.k) : 0);
-    };
     size_t bytes = 0;
     for (uint32_t i = first; i < st.ops.size(); ++i) {
         const Op &op = st.ops[i];
-        bool fresh = bytes + op_bytes(op) > kPassOpBytes;
+        bool fresh = bytes + pass_op_bytes(op) > kPassOpBytes;
         std::set<uint32_t> need(P);
         if (op.type == OP_DENSE) {
             for (uint32_t j = 0; j < op.k; ++j) need.insert(op.wq[j]);
@@ -537,10 +712,61 @@ void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
         } else if (op.type == OP_DENSE) {
             P = need;
         }
-        bytes += op_bytes(op);
+        bytes += pass_op_bytes(op);
         cur.push_back(i);
     }
     close(P, cur);
+}
+
+// Modelled time of a stage's tile passes, to choose between two layouts of the same stage (relative units:
+// one pass over 2^28 amplitudes, in ms on GB300). A pass costs its load and store plus its ops; the
+// coefficients are the k_pass times the ncu launch list gave for 28-qubit QAOA passes of every composition
+// (TF32 dense ops of width 3 to 5 on tcgen05; the warp-level MMA form runs these passes at about the same rate):
+// with 4 resident CTAs per SM 0.54 per pass and 0.284 per tensor-core dense op,
+// with 3 (a pass whose op data pushes a CTA's shared memory past a quarter of the SM's) 0.65, 0.42 and 0.17 per
+// diagonal op; 0.13 per diagonal op with 4 CTAs (scaled by 3/4, not measured); dense ops outside the tensor
+// cores 0.57 (width 1 or 2, measured) or, at width 3 or more, their FP32 arithmetic at the CUDA cores' rate
+// (8 * 2^k flops per amplitude at 80 TFLOP/s).
+double stage_pass_cost(const Stage &st, const qsim_config *cfg) {
+    constexpr double kSmemPerSm = 233472, kStatic = 3300, kReserved = 1024;
+    double total = 0;
+    for (const Pass &ps : st.passes) {
+        const bool tc = cfg->tcgen05 && ps.T == 12 &&
+                        (cfg->prec == QSIM_PREC_TF32 || cfg->prec == QSIM_PREC_BF16X3);
+        size_t blob = 0, mat = 0, bbytes = 0;
+        double d_tc = 0, d_cc = 0, ccw = 0, g = 0;
+        for (uint32_t oi : ps.ops) {
+            const Op &op = st.ops[oi];
+            blob += pass_op_bytes(op);
+            if (op.type == OP_DENSE) {
+                // tcgen05 (widths 3 to 5, TF32 also 6), or warp-level MMAs (TF32 widths 3 to 5, split BF16 4
+                // and 5), which run these passes at about the same rate
+                const uint32_t min_k = cfg->prec == QSIM_PREC_TF32 ? 3u : 4u;
+                const bool on_tc = (tc && op.k >= 3 && (op.k <= 5 || cfg->prec == QSIM_PREC_TF32)) ||
+                                   (cfg->prec != QSIM_PREC_FP32 && ps.T == 12 && op.k >= min_k && op.k <= 5);
+                if (on_tc) {
+                    d_tc += 1;
+                    bbytes = std::max<size_t>(bbytes, op.k == 6 ? 65536 : cfg->prec == QSIM_PREC_BF16X3 ? 24576 : 16384);
+                } else if (op.k <= 2) {
+                    d_cc += 1;
+                    mat = std::max<size_t>(mat, size_t(8) << (2 * op.k));
+                } else {
+                    ccw += double(uint64_t(8) << op.k) * double(1ull << 28) / 80e12 * 1e3;
+                    mat = std::max<size_t>(mat, size_t(8) << (2 * op.k));
+                }
+            } else if (op.type == OP_DIAG || op.type == OP_CSEP) {
+                g += 1;
+            }
+        }
+        const double smem = double(size_t(8) << ps.T) + (bbytes ? double(bbytes) + 1024 : 0) + double(blob + mat) +
+                            kStatic + kReserved;
+        const int ctas = std::max(1, std::min(4, int(kSmemPerSm / smem)));
+        if (ctas >= 4)
+            total += 0.54 + 0.284 * d_tc + 0.13 * g + 0.57 * d_cc + ccw;
+        else
+            total += (0.65 + 0.42 * d_tc + 0.17 * g + 0.57 * d_cc + ccw) * (3.0 / ctas);
+    }
+    return total;
 }
 
 }  // namespace
@@ -578,6 +804,7 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
     if (cfg->k < 1 || cfg->k > 6) return set_error(QSIM_E_INVALID, "k=%u not in 1..6", cfg->k);
     if (cfg->prec > QSIM_PREC_BF16X3) return set_error(QSIM_E_INVALID, "bad precision %u", cfg->prec);
     if (cfg->tcgen05 > 1) return set_error(QSIM_E_INVALID, "tcgen05 is 0 or 1");
+    if (cfg->reorder > QSIM_REORDER_PASSES) return set_error(QSIM_E_INVALID, "reorder is 0, 1 or 2");
     if (cfg->mode > QSIM_MODE_PERSISTENT) return set_error(QSIM_E_INVALID, "bad mode %u", cfg->mode);
     if (cfg->mode == QSIM_MODE_PERSISTENT && cfg->k > 5 && !(cfg->tcgen05 && cfg->prec == QSIM_PREC_TF32))
         return set_error(QSIM_E_INVALID, "persistent mode fuses k = 6 only as TF32 on tcgen05");
@@ -650,18 +877,50 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
     // ---- fusion and tile passes per stage ----
     const uint32_t tile_bits = cfg->tile_bits ? cfg->tile_bits : 12;
     if (tile_bits < 6 || tile_bits > 13) { delete p; return set_error(QSIM_E_INVALID, "tile_bits must be 6..13"); }
-    for (Stage &st : p->stages) {
+    // the stage's gates fused into ops (greedily, in the given order) and laid out in tile passes; with breaks,
+    // the fuser closes its dense op at each pass boundary and builds dense ops only from that pass's tile bits
+    auto fuse_layout = [&](Stage &st, uint32_t T, const std::vector<size_t> *breaks,
+                           const std::vector<uint64_t> *masks) {
+        st.ops.clear();
         Fuser fz;
         fz.inner = &st.inner;
         fz.m = m;
         fz.k = cfg->k;
         fz.ops = &st.ops;
-        for (size_t i = st.first_gate; i < st.first_gate + st.ngates; ++i) fz.add(p->gates[i]);
+        size_t nb = 0;
+        if (breaks) fz.allowed = (*masks)[0];
+        for (size_t i = 0; i < st.ngates; ++i) {
+            if (breaks && nb < breaks->size() && i == (*breaks)[nb]) {
+                fz.flush();
+                fz.allowed = (*masks)[++nb];
+            }
+            fz.add(p->gates[st.first_gate + i]);
+        }
         fz.flush();
         narrow_csep_ops(st.ops);
         // leading phase ops go to the decoder of either compressed format (the raw copy-in applies none)
-        layout_passes(st, std::max<uint32_t>(tile_bits, std::min<uint32_t>(st.W, 5 + cfg->k)),
-                      cfg->codec != QSIM_CODEC_NONE);
+        layout_passes(st, T, cfg->codec != QSIM_CODEC_NONE);
+    };
+    for (Stage &st : p->stages) {
+        const uint32_t T = std::max<uint32_t>(tile_bits, std::min<uint32_t>(st.W, 5 + cfg->k));
+        fuse_layout(st, T, nullptr, nullptr);
+        if (cfg->reorder != QSIM_REORDER_PASSES) continue;
+        // pass-aware order: kept when its modelled pass time is at least 10 % below that of the partition order's
+        // layout (the model is within about 5 % of most measured passes; closer calls keep the partition order)
+        const std::vector<Gate> keep(p->gates.begin() + st.first_gate, p->gates.begin() + st.first_gate + st.ngates);
+        std::vector<size_t> breaks;
+        std::vector<uint64_t> masks;
+        if (!pack_stage_passes(p->gates, st.first_gate, st.ngates, st.inner, n, m, std::min(T, st.W),
+                               std::min(kCoalesceBits, std::min(T, st.W)), cfg->k, &breaks, &masks))
+            continue;
+        Stage packed = st;
+        fuse_layout(packed, T, &breaks, &masks);
+        if (stage_pass_cost(packed, cfg) < 0.9 * stage_pass_cost(st, cfg)) {
+            st = std::move(packed);
+            st.pass_order = true;
+        } else {
+            std::copy(keep.begin(), keep.end(), p->gates.begin() + st.first_gate);
+        }
     }
 
     qsim_plan_stats &s = p->stats;

@@ -85,6 +85,7 @@ struct Stage {
     std::vector<Op> ops;
     std::vector<uint32_t> pre_ops;  // leading diagonal ops applied while decoding (no pass needed)
     std::vector<Pass> passes;
+    bool pass_order = false;  // the stage's gates were reordered pass by pass (QSIM_REORDER_PASSES)
 };
 
 constexpr uint32_t kMaxPreOps = 8;

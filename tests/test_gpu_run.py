@@ -323,3 +323,36 @@ def test_bench_configuration_qaoa32_mirror():
     for b in (0, 1, 77, 127):
         s_ = st.block_stream(b)
         assert s_ == oracle.qsz_encode(oracle.qsz_decode(s_, 25), 25, eb), b
+
+
+@pytest.mark.parametrize("prec,tc", [(qsim.PREC_FP32, 0), (qsim.PREC_TF32, 1)], ids=["fp32", "tf32-tcgen05"])
+@pytest.mark.parametrize("family", ["qft", "qaoa", "random"])
+def test_pass_aware_order_runs(family, prec, tc):
+    # reorder = 2 (each stage's gates gathered into tile passes and fused pass by pass): 20 qubits, working
+    # vectors of 2^17 amplitudes, so every stage takes several 4096-amplitude passes. Uncompressed, the final state
+    # against FP64 element by element: FP32 within 1e-5; TF32 within its per-op bound (relative 2-norm error
+    # 2^-10 per dense op) and, element by element, within twice the TF32 error of the same stages fused in
+    # partition order (reorder = 1), so the pass-aware order costs no accuracy; compressed, fidelity >= 0.99 and the
+    # persistent kernel stores the same streams as the stream engine
+    n = 20
+    c = {"qft": inputs.qft_rz_cx(n, 2, 5), "qaoa": inputs.qaoa_maxcut(n, 3, 7),
+         "random": inputs.random_brick(n, 8, 8)}[family]
+    kw = dict(m=14, inner=3, k=5, eps=1e-3, prec=prec, tcgen05=tc, reorder=2, diag_exempt=1)
+    want = oracle.simulate(c)
+    p = qsim.plan_stages(c, codec=qsim.CODEC_NONE, **kw)
+    assert p.stats()["passes"] > p.nstages
+    raw = state_c64(qsim.run(p))
+    if prec == qsim.PREC_FP32:
+        assert np.max(np.abs(raw - want)) <= 1e-5
+    else:
+        nops = sum(1 for s in range(p.nstages) for o in p.stage_ops(s) if o["type"] == 0)
+        assert np.linalg.norm(raw - want) / np.linalg.norm(want) <= nops * 2.0 ** -10
+        inorder = state_c64(qsim.run(qsim.plan_stages(c, codec=qsim.CODEC_NONE, **dict(kw, reorder=1))))
+        err, err_inorder = np.max(np.abs(raw - want)), np.max(np.abs(inorder - want))
+        print(f"\nTF32 max-abs error vs FP64, {family}: pass-aware {err:.3e}, partition order {err_inorder:.3e}")
+        assert err <= 2.0 * err_inorder
+    st = qsim.run(qsim.plan_stages(c, **kw))
+    assert oracle.fidelity(want, state_c64(st)) >= 0.99
+    pst = qsim.run(qsim.plan_stages(c, mode=qsim.MODE_PERSISTENT, **kw))
+    for b in range(1 << (n - 14)):
+        assert pst.block_stream(b) == st.block_stream(b)
