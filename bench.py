@@ -80,8 +80,11 @@ def parse_args():
                     help="commutation-aware partition: gates may move before earlier gates they commute with "
                          "(--no-reorder: Algorithm 1 in circuit order)")
     ap.add_argument("--pack", action=argparse.BooleanOptionalAction, default=True,
-                    help="with --reorder: each stage's gates gathered into tile passes and fused pass by pass "
-                         "(reorder mode 2; --no-pack keeps each stage's gates in partition order)")
+                    help="with --reorder: each stage's gates gathered into tile passes and fused pass by pass where "
+                         "the planner's pass-time model gains 10 %% (reorder mode 2; --no-pack keeps each stage's "
+                         "gates in partition order)")
+    ap.add_argument("--pack-all", action="store_true",
+                    help="with --reorder: the pass-aware order in every stage, without the model (reorder mode 3)")
     ap.add_argument("--train-n", type=int, default=0, help="qubits of the predictor's training circuits (0 = n)")
     ap.add_argument("--workload", default="qaoa", choices=["qft", "qaoa", "random", "mirror", "batch"],
                     help="qft: QFT + 4 x (RZ, CX ladder) on n qubits; qaoa: MaxCut p=3 on a random 3-regular "
@@ -344,13 +347,15 @@ def run_reference(args, rank, world):
 
 
 def reorder_mode(args):
-    """qsim_config.reorder: 0 Algorithm 1 in circuit order, 1 commutation-aware stages, 2 and pass-aware order."""
-    return 2 if args.reorder and args.pack else 1 if args.reorder else 0
+    """qsim_config.reorder: 0 Algorithm 1 in circuit order, 1 commutation-aware stages, 2 and the pass-aware order
+    where the planner's model gains, 3 the pass-aware order in every stage."""
+    return (3 if args.pack_all else 2) if args.reorder and (args.pack or args.pack_all) else 1 if args.reorder else 0
 
 
 def partition_name(args):
     return ("Algorithm 1 in circuit order" if not args.reorder else
-            "commutation-aware (reorder), pass-aware order in each stage" if args.pack else
+            "commutation-aware (reorder), pass-aware order in every stage" if args.pack_all else
+            "commutation-aware (reorder), pass-aware order where modelled faster" if args.pack else
             "commutation-aware (reorder)")
 
 
@@ -549,7 +554,7 @@ def run_ours(args, rank, world, dist):
             variants.append(("fp32_exact_sizing", dict(kw, prec=qsim.PREC_FP32, sizing=qsim.SIZING_EXACT, tcgen05=0)))
         if args.sizing == "predict":
             variants.append((headline.replace("_predict_sizing", "_exact_sizing"), dict(kw, sizing=qsim.SIZING_EXACT)))
-        if args.reorder and args.pack:
+        if args.reorder and (args.pack or args.pack_all):
             # the same partition with each stage's gates fused and laid out in partition order
             variants.append((headline.replace("_predict_sizing", "_exact_sizing") + "_without_pass_order",
                              dict(kw, sizing=qsim.SIZING_EXACT, reorder=1)))

@@ -804,7 +804,7 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
     if (cfg->k < 1 || cfg->k > 6) return set_error(QSIM_E_INVALID, "k=%u not in 1..6", cfg->k);
     if (cfg->prec > QSIM_PREC_BF16X3) return set_error(QSIM_E_INVALID, "bad precision %u", cfg->prec);
     if (cfg->tcgen05 > 1) return set_error(QSIM_E_INVALID, "tcgen05 is 0 or 1");
-    if (cfg->reorder > QSIM_REORDER_PASSES) return set_error(QSIM_E_INVALID, "reorder is 0, 1 or 2");
+    if (cfg->reorder > QSIM_REORDER_PASSES_ALL) return set_error(QSIM_E_INVALID, "reorder is 0 to 3");
     if (cfg->mode > QSIM_MODE_PERSISTENT) return set_error(QSIM_E_INVALID, "bad mode %u", cfg->mode);
     if (cfg->mode == QSIM_MODE_PERSISTENT && cfg->k > 5 && !(cfg->tcgen05 && cfg->prec == QSIM_PREC_TF32))
         return set_error(QSIM_E_INVALID, "persistent mode fuses k = 6 only as TF32 on tcgen05");
@@ -904,9 +904,10 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
     for (Stage &st : p->stages) {
         const uint32_t T = std::max<uint32_t>(tile_bits, std::min<uint32_t>(st.W, 5 + cfg->k));
         fuse_layout(st, T, nullptr, nullptr);
-        if (cfg->reorder != QSIM_REORDER_PASSES) continue;
+        if (cfg->reorder < QSIM_REORDER_PASSES) continue;
         // pass-aware order: kept when its modelled pass time is at least 10 % below that of the partition order's
-        // layout (the model is within about 5 % of most measured passes; closer calls keep the partition order)
+        // layout (the model is within about 5 % of most measured passes; closer calls keep the partition order),
+        // or in every stage with QSIM_REORDER_PASSES_ALL
         const std::vector<Gate> keep(p->gates.begin() + st.first_gate, p->gates.begin() + st.first_gate + st.ngates);
         std::vector<size_t> breaks;
         std::vector<uint64_t> masks;
@@ -915,7 +916,7 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
             continue;
         Stage packed = st;
         fuse_layout(packed, T, &breaks, &masks);
-        if (stage_pass_cost(packed, cfg) < 0.9 * stage_pass_cost(st, cfg)) {
+        if (cfg->reorder == QSIM_REORDER_PASSES_ALL || stage_pass_cost(packed, cfg) < 0.9 * stage_pass_cost(st, cfg)) {
             st = std::move(packed);
             st.pass_order = true;
         } else {

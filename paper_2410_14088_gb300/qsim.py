@@ -28,7 +28,7 @@ PREC_FP32, PREC_TF32, PREC_BF16X3 = 0, 1, 2
 MODE_STREAMS, MODE_PERSISTENT = 0, 1
 CODEC_QSZ1, CODEC_NONE, CODEC_QSZR = 0, 1, 2
 SIZING_EXACT, SIZING_PREDICT = 0, 1
-REORDER_NONE, REORDER_STAGES, REORDER_PASSES = 0, 1, 2
+REORDER_NONE, REORDER_STAGES, REORDER_PASSES, REORDER_PASSES_ALL = 0, 1, 2, 3
 
 
 class QsimError(RuntimeError):

@@ -328,7 +328,8 @@ def test_bench_configuration_qaoa32_mirror():
 @pytest.mark.parametrize("prec,tc", [(qsim.PREC_FP32, 0), (qsim.PREC_TF32, 1)], ids=["fp32", "tf32-tcgen05"])
 @pytest.mark.parametrize("family", ["qft", "qaoa", "random"])
 def test_pass_aware_order_runs(family, prec, tc):
-    # reorder = 2 (each stage's gates gathered into tile passes and fused pass by pass): 20 qubits, working
+    # reorder = 3 (each stage's gates gathered into tile passes and fused pass by pass, in every stage; mode 2 picks
+    # per stage between this layout and the partition order's, which the other tests cover): 20 qubits, working
     # vectors of 2^17 amplitudes, so every stage takes several 4096-amplitude passes. Uncompressed, the final state
     # against FP64 element by element: FP32 within 1e-5; TF32 within its per-op bound (relative 2-norm error
     # 2^-10 per dense op) and, element by element, within twice the TF32 error of the same stages fused in
@@ -337,10 +338,11 @@ def test_pass_aware_order_runs(family, prec, tc):
     n = 20
     c = {"qft": inputs.qft_rz_cx(n, 2, 5), "qaoa": inputs.qaoa_maxcut(n, 3, 7),
          "random": inputs.random_brick(n, 8, 8)}[family]
-    kw = dict(m=14, inner=3, k=5, eps=1e-3, prec=prec, tcgen05=tc, reorder=2, diag_exempt=1)
+    kw = dict(m=14, inner=3, k=5, eps=1e-3, prec=prec, tcgen05=tc, reorder=3, diag_exempt=1)
     want = oracle.simulate(c)
     p = qsim.plan_stages(c, codec=qsim.CODEC_NONE, **kw)
     assert p.stats()["passes"] > p.nstages
+    assert p.stats()["passes"] < qsim.plan_stages(c, codec=qsim.CODEC_NONE, **dict(kw, reorder=1)).stats()["passes"]
     raw = state_c64(qsim.run(p))
     if prec == qsim.PREC_FP32:
         assert np.max(np.abs(raw - want)) <= 1e-5

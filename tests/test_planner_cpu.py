@@ -156,15 +156,17 @@ def working_bit(q, m, inner_q):
     return q if q < m else m + inner_q.index(q)
 
 
+@pytest.mark.parametrize("reorder", [2, 3])
 @pytest.mark.parametrize("circ", PACK_CASES, ids=lambda c: c.family)
-def test_pass_aware_order_reproduces_the_circuit(circ):
-    # reorder = 2: the stages of the commutation-aware partition, with each stage's gates reordered pass by pass
+def test_pass_aware_order_reproduces_the_circuit(circ, reorder):
+    # reorder = 2 (where the pass-time model gains) and 3 (every stage): the stages of the commutation-aware
+    # partition, with each stage's gates reordered pass by pass
     # (a gate only moves past gates it commutes with) and fused pass by pass; replaying the fused ops with the
     # oracle gives the circuit's state, and every pass's dense ops fit its tile (the 3 low working bits and at
     # most T bits in all; tile_bits 6 and k 3 give T = max(6, min(W, 5 + k)) = 8, several passes per stage)
     m, inner, k, T = 9, 3, 3, 8
     kw = dict(m=m, inner=inner, k=k, tile_bits=6, diag_exempt=1)
-    p = qsim.plan_stages(circ, reorder=2, **kw)
+    p = qsim.plan_stages(circ, reorder=reorder, **kw)
     staged = qsim.plan_stages(circ, reorder=1, **kw)
     assert [(c, inn) for _, c, inn in p.stages()] == [(c, inn) for _, c, inn in staged.stages()]
     n = circ.n
@@ -202,4 +204,4 @@ def test_pass_aware_order_needs_fewer_passes():
 
 def test_reorder_values_checked():
     with pytest.raises(qsim.QsimError):
-        qsim.plan_stages(inputs.ghz(8), m=5, inner=2, k=2, reorder=3)
+        qsim.plan_stages(inputs.ghz(8), m=5, inner=2, k=2, reorder=4)
