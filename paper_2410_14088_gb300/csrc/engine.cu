@@ -671,6 +671,7 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                             pb.insert(pb.end(), fb, fb + 8);
                         }
                     } else if (od.type == OP_CSEP) {
+                        P.mat_elems = std::max<uint32_t>(P.mat_elems, 128u);  // the per-tile branch table
                         // P_lo[b][x] over tile bits 0..6, P_hi[b][y] over tile bits 7.. (with K[b]), and the
                         // records {source, D[0][0], D[0][1], D[1][0], D[1][1]} of the targets outside the tile
                         auto source = [&](uint32_t q) -> uint32_t {

@@ -31,16 +31,13 @@ __device__ __forceinline__ void coop_copy(T &dst, const T &src) {
 
 struct PassSmem {
     PassDev p;
-    // 4096-amplitude tiles: element tid + NT u sits at working offset tpart[tid] + off12[u]
+    // 4096-amplitude tiles: element tid + NT u sits at working offset thread_tile_offset(tid) + off12[u]
     uint32_t off12[32];
-    uint32_t tpart[256];
     uint32_t offs_sw[64];  // dense op: tile offsets of its 2^k matrix columns through the swizzle
     // dense op: swizzled base of index group g = cb[0][g & 63] ^ cb[1][g >> 6] (the swizzle is
     // linear over GF(2), so swz(b | c) = swz(b) ^ swz(c) for disjoint bit sets b, c)
     uint32_t cb[2][64];
     uint32_t dconst[kDiagRun];  // diagonal op d of a run: phase-index bits constant over the tile
-    // controlled-separable op: per branch b, csq[b][h] = P_hi[b][h] * (factors of the targets outside the tile)
-    float2 csq[2][64];
     float2 ck[2];
     uint32_t cbconst;           // the branch when the control is outside the tile
     // passes with tcgen05 dense ops: the MMA-completion mbarrier and the TMEM accumulator's base address
@@ -579,11 +576,9 @@ __device__ __forceinline__ void pass_setup(const PassDev &pd, PassSmem &S) {
     const uint32_t T = S.p.T;
     constexpr uint32_t A = NT == 256 ? 8 : 7;
     if (T == 12) {
-        // element i = tid + NT u: tile bits 0..A-1 from tid, A..11 from u (disjoint working bits)
+        // element i = tid + NT u: tile bits 0..A-1 from tid (thread_tile_offset), A..11 from u (disjoint working
+        // bits)
         const uint32_t x = threadIdx.x;
-        uint32_t o = 0;
-        for (uint32_t t = 0; t < A; ++t) o |= ((x >> t) & 1u) << S.p.tile_pos[t];
-        S.tpart[x] = o;
         if (x < (4096u / NT)) {
             uint32_t h = 0;
             for (uint32_t t = A; t < 12; ++t) h |= ((x >> (t - A)) & 1u) << S.p.tile_pos[t];
@@ -594,6 +589,18 @@ __device__ __forceinline__ void pass_setup(const PassDev &pd, PassSmem &S) {
 }
 
 constexpr uint32_t kCgBatch = 16;
+
+// Working offset of tile bits 0..A-1 taken from this thread's index (A = 7 for 128 threads, 8 for 256): the
+// thread-dependent part of the 4096-amplitude tile addressing, computed where it is used rather than kept in a
+// shared table
+template <int NT>
+__device__ __forceinline__ uint32_t thread_tile_offset(const PassSmem &S) {
+    constexpr uint32_t A = NT == 256 ? 8 : 7;
+    uint32_t o = 0;
+#pragma unroll
+    for (uint32_t t = 0; t < A; ++t) o |= ((uint32_t(threadIdx.x) >> t) & 1u) << S.p.tile_pos[t];
+    return o;
+}
 
 // Fast tile addressing for T = 12: element i = tid + NT u sits at working
 // offset tpart[tid] + off12[u] and at shared index (tid ^ xt) ^ xu(u) + NT u,
@@ -634,7 +641,7 @@ __device__ __forceinline__ void tile_load(const float2 *__restrict__ g, uint64_t
     const uint32_t T = S.p.T, L = S.p.L, lmask = (1u << L) - 1;
     const int tid = threadIdx.x;
     if (fast12<NT>(S)) {
-        const float2 *gt = g + (base | uint64_t(S.tpart[tid]));
+        const float2 *gt = g + (base | uint64_t(thread_tile_offset<NT>(S)));
         const uint32_t tq = swz_thread<NT>(tid);
         if constexpr (CG) {
             constexpr uint32_t B = kCgBatch;  // L2 loads in flight per thread
@@ -677,7 +684,7 @@ __device__ __forceinline__ void tile_store(float2 *__restrict__ g, uint64_t base
     const uint32_t T = S.p.T, L = S.p.L, lmask = (1u << L) - 1;
     if (fast12<NT>(S)) {
         const uint32_t tid = threadIdx.x, tq = swz_thread<NT>(tid);
-        float2 *gt = g + (base | uint64_t(S.tpart[tid]));
+        float2 *gt = g + (base | uint64_t(thread_tile_offset<NT>(S)));
 #pragma unroll
         for (uint32_t u = 0; u < 4096u / NT; ++u) gt[S.off12[u]] = tile[(tq ^ swz_u<NT>(u)) + NT * u];
         return;
@@ -870,10 +877,13 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                 oi += adv;
                 continue;
             }
+            // per branch b, csq[64 b + h] = P_hi[b][h] * (factors of the targets outside the tile), in the pass's
+            // matrix area (128 entries whenever the pass has a controlled-separable op)
+            float2 *csq = mat;
             for (uint32_t x = tid; x < 128; x += NT) {
                 const uint32_t b = x >> 6;
                 const float2 h = phi[x], kb = S.ck[b];
-                S.csq[b][x & 63u] = make_float2(h.x * kb.x - h.y * kb.y, h.x * kb.y + h.y * kb.x);
+                csq[x] = make_float2(h.x * kb.x - h.y * kb.y, h.x * kb.y + h.y * kb.x);
             }
             __syncthreads();
             if (T == 12) {
@@ -884,7 +894,7 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                     const uint32_t i = uint32_t(tid) + NT * u, hi = hib + (NT / 128) * u;
                     const uint32_t b = ctile ? (i >> ct) & 1u : bconst;
                     if ((idm >> b) & 1u) continue;
-                    const float2 q = S.csq[b][hi], pl = b ? pl1 : pl0;
+                    const float2 q = csq[64u * b + hi], pl = b ? pl1 : pl0;
                     const float2 ph = make_float2(pl.x * q.x - pl.y * q.y, pl.x * q.y + pl.y * q.x);
                     float2 &a = tile[(tq ^ swz_u<NT>(u)) + NT * u];
                     const float2 v = a;
@@ -894,7 +904,7 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                 for (uint32_t i = tid; i < (1u << T); i += NT) {
                     const uint32_t b = ctile ? (i >> ct) & 1u : bconst;
                     if ((idm >> b) & 1u) continue;
-                    const float2 q = S.csq[b][i >> 7], pl = plo[128 * b + (i & 127u)];
+                    const float2 q = csq[64u * b + (i >> 7)], pl = plo[128 * b + (i & 127u)];
                     const float2 ph = make_float2(pl.x * q.x - pl.y * q.y, pl.x * q.y + pl.y * q.x);
                     float2 &a = tile[swz(i)];
                     const float2 v = a;

@@ -656,9 +656,10 @@ void narrow_csep_ops(std::vector<Op> &ops) {
     }
 }
 
-// shared-memory bytes of an op's data in its pass (descriptor, and for a diagonal op its tables)
+// shared-memory bytes of an op's data in its pass: its descriptor; a diagonal op's index tables and phases; a
+// controlled-separable op's tile-bit tables, records and per-tile branch table
 size_t pass_op_bytes(const Op &op) {
-    if (op.type == OP_CSEP) return kOpDescBytes + kCsepTableBytes + 48 * size_t(op.k);
+    if (op.type == OP_CSEP) return kOpDescBytes + kCsepTableBytes + 48 * size_t(op.k) + 1024;
     if (op.type == OP_DENSE && op.k >= 3 && op.k <= 6)  // tensor-core offset tables: 128 + 2^k words
         return kOpDescBytes + 4 * (128 + (size_t(1) << op.k));
     return kOpDescBytes + (op.type == OP_DIAG ? 192 + 16 + (size_t(8) << op.k) : 0);
@@ -728,7 +729,7 @@ void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
 // cores 0.57 (width 1 or 2, measured) or, at width 3 or more, their FP32 arithmetic at the CUDA cores' rate
 // (8 * 2^k flops per amplitude at 80 TFLOP/s).
 double stage_pass_cost(const Stage &st, const qsim_config *cfg) {
-    constexpr double kSmemPerSm = 233472, kStatic = 3300, kReserved = 1024;
+    constexpr double kSmemPerSm = 233472, kStatic = 1250, kReserved = 1024;
     double total = 0;
     for (const Pass &ps : st.passes) {
         const bool tc = cfg->tcgen05 && ps.T == 12 &&
