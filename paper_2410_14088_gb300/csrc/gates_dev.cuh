@@ -299,8 +299,6 @@ __device__ __forceinline__ bool umma_commit_wait(const PassSmem &S, uint32_t &ph
     return ok;
 }
 
-// Row g of D (TMEM lane g: Re of the 32 outputs in columns 0..31, Im in 32..63) back to the group's tile
-// positions.
 // The swizzled tile offsets of a width-5 op's 32 columns from its five basis columns: the column map and the
 // swizzle are linear over GF(2), so osw[j] is the XOR of osw[2^b] over the set bits b of j (osw[0] = 0). Five
 // shared-memory reads per thread instead of 32.
@@ -320,15 +318,26 @@ __device__ __forceinline__ constexpr uint32_t ctz5(uint32_t i) {
     return (i & 1u) ? 0u : (i & 2u) ? 1u : (i & 4u) ? 2u : (i & 8u) ? 3u : 4u;
 }
 
+// Row g of D (TMEM lane g: Re of the 32 outputs in columns 0..31, Im in 32..63) back to the group's tile
+// positions, in the gather's Gray-code order (one XOR into a running address per step, from the five basis
+// offsets, instead of a table read per output) and in two halves of 16 columns: the first 16 steps of the walk
+// visit columns 0..15, the last 16 columns 16..31, so each half needs only its 16 Re and 16 Im columns of D.
 __device__ __forceinline__ void umma_epilogue(float2 *tile, uint32_t base, const uint32_t *osw, const PassSmem &S) {
     umma::fence_after_sync();
     const uint32_t taddr = S.tmem + ((32u * (threadIdx.x >> 5)) << 16);
-    uint32_t re[32], im[32];
-    umma::tmem_ld32(taddr, re);
-    umma::tmem_ld32(taddr + 32u, im);
+    const ColBasis cbs = col_basis(osw);
+    uint32_t a = base;
 #pragma unroll
-    for (uint32_t j = 0; j < 32; ++j)
-        tile[base ^ osw[j]] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+    for (uint32_t h = 0; h < 2; ++h) {
+        uint32_t re[16], im[16];
+        umma::tmem_ld16x2(taddr + 16u * h, re, taddr + 32u + 16u * h, im);
+#pragma unroll
+        for (uint32_t i = 16u * h; i < 16u * h + 16u; ++i) {
+            if (i) a ^= cbs.b[ctz5(i)];
+            const uint32_t j = gray5(i) - 16u * h;
+            tile[a] = make_float2(__uint_as_float(re[j]), __uint_as_float(im[j]));
+        }
+    }
     umma::fence_before_sync();  // the next op's barrier orders these TMEM reads before its MMAs
 }
 
