@@ -81,7 +81,7 @@ def parse_args():
                          "(--no-reorder: Algorithm 1 in circuit order)")
     ap.add_argument("--pack", action=argparse.BooleanOptionalAction, default=True,
                     help="with --reorder: each stage's gates gathered into tile passes and fused pass by pass where "
-                         "the planner's pass-time model gains 10 %% (reorder mode 2; --no-pack keeps each stage's "
+                         "the planner's pass-time model gains 5 %% (reorder mode 2; --no-pack keeps each stage's "
                          "gates in partition order)")
     ap.add_argument("--pack-all", action="store_true",
                     help="with --reorder: the pass-aware order in every stage, without the model (reorder mode 3)")

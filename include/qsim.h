@@ -83,7 +83,7 @@ typedef struct qsim_gate {
 #define QSIM_REORDER_NONE 0u   /* Algorithm 1 over the gates in circuit order */
 #define QSIM_REORDER_STAGES 1u /* commutation-aware stage partition */
 #define QSIM_REORDER_PASSES 2u /* commutation-aware stages + pass-aware order within each stage, kept per
-                                  stage where a model of the passes' time puts it at least 10 % lower */
+                                  stage where a model of the passes' time puts it at least 5 % lower */
 #define QSIM_REORDER_PASSES_ALL 3u /* as 2, in every stage (no model; for measurements) */
 
 typedef struct qsim_config {
@@ -111,7 +111,7 @@ typedef struct qsim_config {
                                 passes (a non-diagonal gate joins a pass while the tile bits it
                                 needs fit, diagonal gates join any pass) and fused pass by pass,
                                 kept per stage where a model of the passes' time puts it at least
-                                10 % lower; 3 = the pass-aware order in every stage */
+                                5 % lower; 3 = the pass-aware order in every stage */
     uint32_t tcgen05;        /* 1: TF32 and split-BF16 dense ops of width 5 on the 5th-generation
                                 tensor cores (tcgen05.mma, accumulator in tensor memory) in
                                 streams mode; 0: warp-level mma.sync */

@@ -22,6 +22,7 @@
 #include <unistd.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cmath>
@@ -626,15 +627,26 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                 }
                 ops.push_back(od);
             }
-            // runs of consecutive diagonal ops applied in one sweep
+            // diagonal ops whose phase is a polynomial of degree <= 2 in their bits (4096-amplitude tiles only)
+            std::vector<char> quad(P.op_count, 0);
+            std::vector<DiagPoly> qpoly(P.op_count);
+            if (ps.T == 12)
+                for (uint32_t a = 0; a < P.op_count; ++a)
+                    if (ops[P.op_begin + a].type == OP_DIAG) quad[a] = diag_quadratic(st.ops[ps.ops[a]], &qpoly[a]);
+            // runs of consecutive diagonal ops applied in one sweep: up to kDiagRun table ops, or any number of
+            // polynomial ops (one phase per amplitude for the whole run; the head becomes an OP_POLY descriptor)
             for (uint32_t a = P.op_begin; a < P.op_begin + P.op_count;) {
                 if (ops[a].type != OP_DIAG) {
                     ++a;
                     continue;
                 }
+                const bool pq = quad[a - P.op_begin];
                 uint32_t b = a;
-                while (b < P.op_begin + P.op_count && b - a < kDiagRun && ops[b].type == OP_DIAG) ops[b++].run = 0;
+                while (b < P.op_begin + P.op_count && ops[b].type == OP_DIAG && bool(quad[b - P.op_begin]) == pq &&
+                       (pq || b - a < kDiagRun))
+                    ops[b++].run = 0;
                 ops[a].run = b - a;
+                if (pq) ops[a].type = OP_POLY;
                 a = b;
             }
             // the pass blob: descriptors, then per diagonal op its index tables (tile bits 0..6 and
@@ -648,7 +660,68 @@ static int upload_plan(const qsim_plan *p, PlanDev **out) {
                     OpDev &od = ops[P.op_begin + a];
                     const Op &op = st.ops[ps.ops[a]];
                     od.tab = kNoTab;
-                    if (od.type == OP_DIAG) {
+                    if (od.type == OP_POLY) {
+                        // the run's summed phase polynomial (angles in turns, 32-bit fixed point) over the tile bits t (the bits of a
+                        // 4096-amplitude tile): G[t][t'] (t < t'), the run's quadratic part over tile bits 7..11
+                        // (Q7, 32 values) and 8..11 (Q8, 16), the linear coefficients A0[t], the constant C0, then
+                        // records {t or -1, source, source or kNoSrc, coefficient} of the terms with bits constant
+                        // over the tile (a working bit outside the tile, or 64 + an outer qubit): tile bit t's linear
+                        // coefficient, or (t = -1) the constant, gains the coefficient when those bits are 1
+                        const uint32_t r = od.run;
+                        double G[12][12] = {}, A0[12] = {}, C0 = 0;
+                        std::map<std::array<uint32_t, 3>, double> terms;
+                        for (uint32_t d = 0; d < r; ++d) {
+                            const OpDev &rd = ops[P.op_begin + a + d];
+                            const DiagPoly &q = qpoly[a + d];
+                            C0 += q.c;
+                            for (uint32_t j = 0; j < rd.k; ++j) {
+                                if (rd.dtile[j] != 255) A0[rd.dtile[j]] += q.a[j];
+                                else terms[{kPolyConst, rd.dsrc[j], kNoSrc}] += q.a[j];
+                                for (uint32_t l = j + 1; l < rd.k; ++l) {
+                                    const uint32_t tj = rd.dtile[j], tl = rd.dtile[l];
+                                    if (tj != 255 && tl != 255) G[std::min(tj, tl)][std::max(tj, tl)] += q.g[j][l];
+                                    else if (tj != 255) terms[{tj, rd.dsrc[l], kNoSrc}] += q.g[j][l];
+                                    else if (tl != 255) terms[{tl, rd.dsrc[j], kNoSrc}] += q.g[j][l];
+                                    else
+                                        terms[{kPolyConst, std::min(rd.dsrc[j], rd.dsrc[l]),
+                                               std::max(rd.dsrc[j], rd.dsrc[l])}] += q.g[j][l];
+                                }
+                            }
+                        }
+                        // angles as 32-bit fixed point in turns (2^32 = one turn): sums wrap exactly modulo a turn
+                        auto red = [](double t) {
+                            const double f = t - std::floor(t);
+                            return uint32_t(uint64_t(std::llround(f * 4294967296.0)) & 0xffffffffull);
+                        };
+                        std::vector<uint32_t> w(kPolyHeadWords, 0u);
+                        for (uint32_t t = 0; t < 12; ++t)
+                            for (uint32_t t2 = t + 1; t2 < 12; ++t2) w[12 * t + t2] = red(G[t][t2]);
+                        for (uint32_t u = 0; u < 32; ++u) {
+                            double qv = 0, qv8 = 0;
+                            for (uint32_t b = 7; b < 12; ++b)
+                                for (uint32_t b2 = b + 1; b2 < 12; ++b2) {
+                                    const bool on = ((u >> (b - 7)) & 1u) && ((u >> (b2 - 7)) & 1u);
+                                    if (on) qv += G[b][b2];
+                                    if (b >= 8 && u < 16 && ((u >> (b - 8)) & 1u) && ((u >> (b2 - 8)) & 1u)) qv8 += G[b][b2];
+                                }
+                            w[144 + u] = red(qv);
+                            if (u < 16) w[176 + u] = red(qv8);
+                        }
+                        for (uint32_t t = 0; t < 12; ++t) w[192 + t] = red(A0[t]);
+                        w[204] = red(C0);
+                        align16();
+                        od.tab = uint32_t(pb.size() / 4);
+                        od.ncst = uint32_t(terms.size());
+                        const uint8_t *wb = reinterpret_cast<const uint8_t *>(w.data());
+                        pb.insert(pb.end(), wb, wb + 4 * w.size());
+                        for (const auto &kv : terms) {
+                            const uint32_t rec[4] = {kv.first[0], kv.first[1], kv.first[2], red(kv.second)};
+                            const uint8_t *rb = reinterpret_cast<const uint8_t *>(rec);
+                            pb.insert(pb.end(), rb, rb + 16);
+                        }
+                    } else if (od.type == OP_DIAG && quad[a]) {
+                        // inside a polynomial run: nothing of its own in the blob
+                    } else if (od.type == OP_DIAG) {
                         align16();
                         od.dlut = uint32_t(pb.size() / 8);
                         for (uint32_t v = 0; v < 192; ++v) {

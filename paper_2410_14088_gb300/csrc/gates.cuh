@@ -31,7 +31,7 @@ struct PassDev {
 };
 
 struct __align__(16) OpDev {
-    uint32_t type;           // 0 dense, 1 diagonal, 2 phase flip
+    uint32_t type;           // 0 dense, 1 diagonal, 2 phase flip, 3 controlled-separable, OP_POLY (4)
     uint32_t k;
     uint32_t mat;            // float2 offset of the matrix (dense) or phases (diag) in the plan's matrix array
     uint32_t dlut;           // diag: float2 offset of its phase-index byte tables (pass: in the blob; decoder
@@ -50,7 +50,8 @@ struct __align__(16) OpDev {
                              // on CUDA cores) or of the tile-bit tables P_lo[2][128] (csep); kNoTab when not there
     uint32_t cctl;           // csep: control at tile bit cctl, or kCtlConst | source (working bit < 64 or 64 + qubit);
                              // kCtlId0 / kCtlId1: that branch is the identity
-    uint32_t ncst;           // csep: targets outside the tile (records at blob offset `mat`, P_hi[2][64] at `dlut`)
+    uint32_t ncst;           // csep: targets outside the tile (records at blob offset `mat`, P_hi[2][64] at `dlut`);
+                             // OP_POLY: number of term records
 };
 
 constexpr uint32_t kCtlConst = 0x80000000u;
@@ -59,6 +60,14 @@ constexpr uint32_t kCtlId1 = 0x20000000u;  // csep: branch 1 is the identity
 constexpr uint32_t kCtlFlags = kCtlConst | kCtlId0 | kCtlId1;
 
 constexpr uint32_t kDiagRun = 4;            // diagonal ops applied in one sweep over a tile
+// An OpDev of type OP_POLY heads a run of diagonal ops whose phases are polynomials of degree <= 2 in the index bits
+// (4096-amplitude tiles): `tab` is the word offset in the pass blob of the run's summed polynomial (kPolyHeadWords
+// words: G[12][12], Q7[32], Q8[16], A0[12], C0, padding; every coefficient an angle in turns as 32-bit fixed point,
+// 2^32 = one turn) followed by `ncst` term records of 4 words
+constexpr uint32_t OP_POLY = 4;
+constexpr uint32_t kPolyHeadWords = 208;
+constexpr uint32_t kPolyConst = 0xffffffffu;  // term record: adds to the constant, not to a tile bit's coefficient
+constexpr uint32_t kNoSrc = 0xffffffffu;      // term record: no second source bit
 constexpr uint32_t kNoTab = 0xffffffffu;
 constexpr uint32_t kPassBlobMax = 40960;    // bytes of one pass blob (shared memory next to the tile)
 

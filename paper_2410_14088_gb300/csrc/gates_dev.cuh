@@ -38,6 +38,8 @@ struct PassSmem {
     // linear over GF(2), so swz(b | c) = swz(b) ^ swz(c) for disjoint bit sets b, c)
     uint32_t cb[2][64];
     uint32_t dconst[kDiagRun];  // diagonal op d of a run: phase-index bits constant over the tile
+    uint32_t pA[13];            // polynomial run: tile bit t's linear coefficient (t < 12) and the constant (12),
+                                // angles in turns as 32-bit fixed point
     float2 ck[2];
     uint32_t cbconst;           // the branch when the control is outside the tile
     // passes with tcgen05 dense ops: the MMA-completion mbarrier and the TMEM accumulator's base address
@@ -854,6 +856,60 @@ __device__ __forceinline__ bool tile_ops(float2 *tile, const uint4 *blob, float2
                         }
                     }
                     a = v;
+                }
+            }
+        } else if (type == OP_POLY) {
+            // a run of diagonal ops whose summed phase angle is a polynomial of degree <= 2 in the tile's bits:
+            // P(x) = C + sum_t A_t x_t + sum_{t < t'} G_tt' x_t x_t', where C and A_t take the terms with bits
+            // constant over the tile; one phase exp(2 pi i P) per amplitude for the whole run. Angles are turns in
+            // 32-bit fixed point, so every sum wraps exactly modulo a turn; only the final angle is rounded (to FP32,
+            // within 2^-26 turns) before __sincosf
+            const uint32_t r = op.run;
+            adv = r;
+            const uint32_t *pw = reinterpret_cast<const uint32_t *>(blob) + op.tab;
+            // this tile's A_t and C: the pass constants, then every term whose constant bits are 1 over this tile,
+            // the records shared out over the CTA (shared atomic adds, exact modulo 2^32)
+            if (tid < 13) S.pA[tid] = pw[tid < 12 ? 192 + tid : 204];
+            __syncthreads();
+            {
+                const uint32_t *tr = pw + kPolyHeadWords;
+                for (uint32_t i = tid; i < op.ncst; i += NT) {
+                    const uint32_t t = tr[4 * i], s1 = tr[4 * i + 1], s2 = tr[4 * i + 2];
+                    const uint64_t b1 = s1 < 64 ? (base >> s1) & 1ull : (gb >> (s1 - 64)) & 1ull;
+                    const uint64_t b2 = s2 == kNoSrc ? 1ull : s2 < 64 ? (base >> s2) & 1ull : (gb >> (s2 - 64)) & 1ull;
+                    if (b1 & b2) atomicAdd(&S.pA[t == kPolyConst ? 12u : t], tr[4 * i + 3]);
+                }
+            }
+            __syncthreads();
+            if (T == 12) {
+                // element i = tid + NT u: tile bits 0..LB-1 from tid, LB..11 from u
+                constexpr uint32_t LB = NT == 256 ? 8 : 7, HB = 12 - LB;
+                const uint32_t tq = swz_thread<NT>(tid);
+                uint32_t th = S.pA[12], beta[HB];
+#pragma unroll
+                for (uint32_t b = 0; b < HB; ++b) beta[b] = S.pA[LB + b];
+#pragma unroll
+                for (uint32_t t = 0; t < LB; ++t) {
+                    if (!((uint32_t(tid) >> t) & 1u)) continue;
+                    th += S.pA[t];
+#pragma unroll
+                    for (uint32_t t2 = t + 1; t2 < LB; ++t2)
+                        if ((uint32_t(tid) >> t2) & 1u) th += pw[12 * t + t2];
+#pragma unroll
+                    for (uint32_t b = 0; b < HB; ++b) beta[b] += pw[12 * t + LB + b];
+                }
+                const uint32_t *q = pw + (LB == 7 ? 144 : 176);
+#pragma unroll
+                for (uint32_t u = 0; u < 4096u / NT; ++u) {
+                    uint32_t ang = th + q[u];
+#pragma unroll
+                    for (uint32_t b = 0; b < HB; ++b)
+                        if ((u >> b) & 1u) ang += beta[b];
+                    float sn, cs;
+                    __sincosf(6.28318530717958648f * 2.3283064365386963e-10f * float(int32_t(ang)), &sn, &cs);
+                    float2 &a = tile[(tq ^ swz_u<NT>(u)) + NT * u];
+                    const float2 v = a;
+                    a = make_float2(cs * v.x - sn * v.y, cs * v.y + sn * v.x);
                 }
             }
         } else if (type == OP_CSEP) {

@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <cmath>
 #include <chrono>
 #include <set>
 
@@ -656,12 +657,14 @@ void narrow_csep_ops(std::vector<Op> &ops) {
     }
 }
 
-// shared-memory bytes of an op's data in its pass: its descriptor; a diagonal op's index tables and phases; a
-// controlled-separable op's tile-bit tables, records and per-tile branch table
-size_t pass_op_bytes(const Op &op) {
+// shared-memory bytes of an op's data in a pass of 2^T-amplitude tiles: its descriptor; a diagonal op's index
+// tables and phases, or, for a polynomial one in a 4096-amplitude tile, its share of the run's summed polynomial
+// (832 bytes per run) and term records; a controlled-separable op's tile-bit tables, records and per-tile branch table
+size_t pass_op_bytes(const Op &op, uint32_t T) {
     if (op.type == OP_CSEP) return kOpDescBytes + kCsepTableBytes + 48 * size_t(op.k) + 1024;
     if (op.type == OP_DENSE && op.k >= 3 && op.k <= 6)  // tensor-core offset tables: 128 + 2^k words
         return kOpDescBytes + 4 * (128 + (size_t(1) << op.k));
+    if (op.type == OP_DIAG && op.quad && T == 12) return kOpDescBytes + 128 + 16 * size_t(op.k);
     return kOpDescBytes + (op.type == OP_DIAG ? 192 + 16 + (size_t(8) << op.k) : 0);
 }
 
@@ -697,7 +700,7 @@ void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
     size_t bytes = 0;
     for (uint32_t i = first; i < st.ops.size(); ++i) {
         const Op &op = st.ops[i];
-        bool fresh = bytes + pass_op_bytes(op) > kPassOpBytes;
+        bool fresh = bytes + pass_op_bytes(op, T) > kPassOpBytes;
         std::set<uint32_t> need(P);
         if (op.type == OP_DENSE) {
             for (uint32_t j = 0; j < op.k; ++j) need.insert(op.wq[j]);
@@ -713,7 +716,7 @@ void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
         } else if (op.type == OP_DENSE) {
             P = need;
         }
-        bytes += pass_op_bytes(op);
+        bytes += pass_op_bytes(op, T);
         cur.push_back(i);
     }
     close(P, cur);
@@ -723,11 +726,12 @@ void layout_passes(Stage &st, uint32_t tile_bits, bool fold_leading_diag) {
 // one pass over 2^28 amplitudes, in ms on GB300). A pass costs its load and store plus its ops; the
 // coefficients are the k_pass times the ncu launch list gave for 28-qubit QAOA passes of every composition
 // (TF32 dense ops of width 3 to 5 on tcgen05; the warp-level MMA form runs these passes at about the same rate):
-// with 4 resident CTAs per SM 0.54 per pass and 0.284 per tensor-core dense op,
-// with 3 (a pass whose op data pushes a CTA's shared memory past a quarter of the SM's) 0.65, 0.42 and 0.17 per
-// diagonal op; 0.13 per diagonal op with 4 CTAs (scaled by 3/4, not measured); dense ops outside the tensor
-// cores 0.57 (width 1 or 2, measured) or, at width 3 or more, their FP32 arithmetic at the CUDA cores' rate
-// (8 * 2^k flops per amplitude at 80 TFLOP/s).
+// with 4 resident CTAs per SM 0.61 per pass and 0.213 per tensor-core dense op; with 3 (a pass whose op data
+// pushes a CTA's shared memory past a quarter of the SM's) 0.72 and 0.315 (scaled by the ratio measured before
+// the epilogue of the tcgen05 ops changed) and 0.17 per diagonal op applied from a phase table (0.13 with 4
+// CTAs, scaled by 3/4); a run of diagonal ops applied as one phase polynomial 0.25 plus 0.055 per op; dense ops
+// outside the tensor cores 0.57 (width 1 or 2, measured) or, at width 3 or more, their FP32 arithmetic at the
+// CUDA cores' rate (8 * 2^k flops per amplitude at 80 TFLOP/s).
 double stage_pass_cost(const Stage &st, const qsim_config *cfg) {
     constexpr double kSmemPerSm = 233472, kStatic = 1250, kReserved = 1024;
     double total = 0;
@@ -735,10 +739,19 @@ double stage_pass_cost(const Stage &st, const qsim_config *cfg) {
         const bool tc = cfg->tcgen05 && ps.T == 12 &&
                         (cfg->prec == QSIM_PREC_TF32 || cfg->prec == QSIM_PREC_BF16X3);
         size_t blob = 0, mat = 0, bbytes = 0;
-        double d_tc = 0, d_cc = 0, ccw = 0, g = 0;
+        double d_tc = 0, d_cc = 0, ccw = 0, g = 0, pr = 0, po = 0;
+        bool in_poly = false;  // inside a run of polynomial diagonal ops (one sweep for the whole run)
         for (uint32_t oi : ps.ops) {
             const Op &op = st.ops[oi];
-            blob += pass_op_bytes(op);
+            blob += pass_op_bytes(op, ps.T);
+            const bool poly = op.type == OP_DIAG && op.quad && ps.T == 12;
+            if (poly) {
+                if (!in_poly) pr += 1;
+                po += 1;
+                in_poly = true;
+                continue;
+            }
+            in_poly = false;
             if (op.type == OP_DENSE) {
                 // tcgen05 (widths 3 to 5, TF32 also 6), or warp-level MMAs (TF32 widths 3 to 5, split BF16 4
                 // and 5), which run these passes at about the same rate
@@ -762,15 +775,47 @@ double stage_pass_cost(const Stage &st, const qsim_config *cfg) {
         const double smem = double(size_t(8) << ps.T) + (bbytes ? double(bbytes) + 1024 : 0) + double(blob + mat) +
                             kStatic + kReserved;
         const int ctas = std::max(1, std::min(4, int(kSmemPerSm / smem)));
+        const double polys = 0.25 * pr + 0.055 * po;
         if (ctas >= 4)
-            total += 0.54 + 0.284 * d_tc + 0.13 * g + 0.57 * d_cc + ccw;
+            total += 0.61 + 0.213 * d_tc + 0.13 * g + 0.57 * d_cc + ccw + polys;
         else
-            total += (0.65 + 0.42 * d_tc + 0.17 * g + 0.57 * d_cc + ccw) * (3.0 / ctas);
+            total += (0.72 + 0.315 * d_tc + 0.17 * g + 0.57 * d_cc + ccw) * (3.0 / ctas) + polys;
     }
     return total;
 }
 
 }  // namespace
+
+bool diag_quadratic(const Op &op, DiagPoly *out) {
+    if (op.type != OP_DIAG || op.k > 8 || op.u.size() != (size_t(1) << op.k)) return false;
+    const uint32_t K = op.k, D = 1u << K;
+    const double two_pi = 6.283185307179586476925286766559;
+    auto red = [](double t) { return t - std::floor(t + 0.5); };  // to [-1/2, 1/2)
+    std::vector<double> ph(D);
+    for (uint32_t x = 0; x < D; ++x) {
+        if (std::fabs(std::abs(op.u[x]) - 1.0) > 1e-9) return false;
+        ph[x] = std::arg(op.u[x]) / two_pi;
+    }
+    DiagPoly q;
+    q.c = ph[0];
+    for (uint32_t j = 0; j < K; ++j) q.a[j] = red(ph[1u << j] - q.c);
+    for (uint32_t j = 0; j < K; ++j)
+        for (uint32_t l = j + 1; l < K; ++l)
+            q.g[j][l] = red(ph[(1u << j) | (1u << l)] - ph[1u << j] - ph[1u << l] + q.c);
+    for (uint32_t x = 0; x < D; ++x) {
+        double t = q.c;
+        for (uint32_t j = 0; j < K; ++j) {
+            if (!((x >> j) & 1u)) continue;
+            t += q.a[j];
+            for (uint32_t l = j + 1; l < K; ++l)
+                if ((x >> l) & 1u) t += q.g[j][l];
+        }
+        if (std::fabs(red(ph[x] - t)) > 1e-9) return false;
+    }
+    q.c = red(q.c);
+    *out = q;
+    return true;
+}
 
 bool qsz_step_exponent(double eb, int *e) {
     if (!(eb > 0.0) || !isfinite(eb)) return false;
@@ -899,6 +944,10 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
         }
         fz.flush();
         narrow_csep_ops(st.ops);
+        for (Op &op : st.ops) {
+            DiagPoly q;
+            op.quad = op.type == OP_DIAG && diag_quadratic(op, &q);
+        }
         // leading phase ops go to the decoder of either compressed format (the raw copy-in applies none)
         layout_passes(st, T, cfg->codec != QSIM_CODEC_NONE);
     };
@@ -906,7 +955,7 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
         const uint32_t T = std::max<uint32_t>(tile_bits, std::min<uint32_t>(st.W, 5 + cfg->k));
         fuse_layout(st, T, nullptr, nullptr);
         if (cfg->reorder < QSIM_REORDER_PASSES) continue;
-        // pass-aware order: kept when its modelled pass time is at least 10 % below that of the partition order's
+        // pass-aware order: kept when its modelled pass time is at least 5 % below that of the partition order's
         // layout (the model is within about 5 % of most measured passes; closer calls keep the partition order),
         // or in every stage with QSIM_REORDER_PASSES_ALL
         const std::vector<Gate> keep(p->gates.begin() + st.first_gate, p->gates.begin() + st.first_gate + st.ngates);
@@ -917,7 +966,7 @@ int build_plan(uint32_t n, const qsim_gate *gates, size_t ngates, const qsim_con
             continue;
         Stage packed = st;
         fuse_layout(packed, T, &breaks, &masks);
-        if (cfg->reorder == QSIM_REORDER_PASSES_ALL || stage_pass_cost(packed, cfg) < 0.9 * stage_pass_cost(st, cfg)) {
+        if (cfg->reorder == QSIM_REORDER_PASSES_ALL || stage_pass_cost(packed, cfg) < 0.95 * stage_pass_cost(st, cfg)) {
             st = std::move(packed);
             st.pass_order = true;
         } else {

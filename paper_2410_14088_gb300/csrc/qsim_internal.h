@@ -70,7 +70,20 @@ struct Op {
     // csep (controlled-separable diagonal): phase(x) = K[b] * prod_t D_t[b][x_t] with b = x_c;
     // csep_q = {c, t_1, t_2, ...} (full qubits), u = {K[0], K[1], then per target D[0][0], D[0][1], D[1][0], D[1][1]}
     std::vector<uint32_t> csep_q;
+    bool quad = false;      // diag: its phase is a polynomial of degree <= 2 in its bits (diag_quadratic)
 };
+
+// A diagonal op whose phase angle is a polynomial of degree at most 2 in its qubits' bits, which every product
+// of one- and two-qubit diagonal gates is: phase(x) = exp(2 pi i (c + sum_j a[j] x_j + sum_{j<l} g[j][l] x_j x_l))
+// with x_j the bit of qubit j of the op; angles in turns, each reduced to [-1/2, 1/2).
+struct DiagPoly {
+    double c = 0;
+    double a[8] = {};
+    double g[8][8] = {};
+};
+// true (and *out filled) when op is an OP_DIAG op of unit-modulus phases whose angles match such a polynomial to
+// 1e-9 turns at every one of its 2^k indices
+bool diag_quadratic(const Op &op, DiagPoly *out);
 
 struct Pass {
     uint32_t T;                   // tile bits
