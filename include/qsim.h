@@ -185,6 +185,10 @@ typedef struct qsim_op_info {
                            type 3: the first 8 of qlist) */
     uint32_t ngates;    /* input gates folded into the op */
     uint32_t pass;      /* index of the shared-memory tile pass within the stage */
+    uint32_t quadratic; /* diagonal op whose phase angle is a polynomial of degree <= 2 in its qubits' bits
+                           (every product of one- and two-qubit diagonal gates): in passes of 4096-amplitude
+                           tiles a run of such ops is applied as one phase per amplitude; else 0 */
+    uint32_t reserved_; /* zero */
     uint64_t basis;     /* phase flip: the flipped basis state */
     const double *u;    /* dense: 2^nq x 2^nq complex128 row-major; diagonal: 2^nq complex128;
                            type 3: K[0], K[1], then per target D[0][0], D[0][1], D[1][0], D[1][1]

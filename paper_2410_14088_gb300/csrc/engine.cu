@@ -2170,6 +2170,7 @@ int qsim_plan_stage_ops(const qsim_plan *plan, size_t stage, size_t *count, qsim
         } else if (op.type == OP_DIAG) {
             o.nq = op.k;
             for (uint32_t j = 0; j < op.k; ++j) o.qubits[j] = op.fq[j];
+            o.quadratic = op.quad ? 1u : 0u;
         } else if (op.type == OP_CSEP) {
             o.nq = uint32_t(op.csep_q.size());
             for (uint32_t j = 0; j < o.nq && j < 8; ++j) o.qubits[j] = op.csep_q[j];

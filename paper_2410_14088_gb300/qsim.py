@@ -60,7 +60,8 @@ class PlanStats(ctypes.Structure):
 
 class OpInfo(ctypes.Structure):
     _fields_ = [("type", ctypes.c_uint32), ("nq", ctypes.c_uint32), ("qubits", ctypes.c_uint32 * 8),
-                ("ngates", ctypes.c_uint32), ("pass_", ctypes.c_uint32), ("basis", ctypes.c_uint64),
+                ("ngates", ctypes.c_uint32), ("pass_", ctypes.c_uint32), ("quadratic", ctypes.c_uint32),
+                ("reserved_", ctypes.c_uint32), ("basis", ctypes.c_uint64),
                 ("u", ctypes.POINTER(ctypes.c_double)), ("qlist", ctypes.POINTER(ctypes.c_uint32))]
 
 
@@ -278,7 +279,7 @@ class Plan:
         ops = []
         for o in arr[: cnt.value]:
             d = {"type": o.type, "nq": o.nq, "qubits": tuple(o.qubits[: o.nq]), "ngates": o.ngates,
-                 "pass": o.pass_, "basis": o.basis, "u": None}
+                 "pass": o.pass_, "quadratic": bool(o.quadratic), "basis": o.basis, "u": None}
             if o.type == 0:
                 D = 1 << o.nq
                 d["u"] = np.ctypeslib.as_array(o.u, shape=(2 * D * D,)).copy().view(np.complex128).reshape(D, D)

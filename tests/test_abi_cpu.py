@@ -31,7 +31,7 @@ def test_struct_sizes_match_header():
     assert ctypes.sizeof(qsim.Gate) == 48
     assert ctypes.sizeof(qsim.Config) == 4 * 12 + 8 * 4 + 8 * 6
     assert ctypes.sizeof(qsim.Stats) == 8 * 16
-    assert ctypes.sizeof(qsim.OpInfo) == 4 * 12 + 8 + 8 + 8
+    assert ctypes.sizeof(qsim.OpInfo) == 4 * 14 + 8 + 8 + 8
     assert ctypes.sizeof(qsim.TrainConfig) == 24
 
 

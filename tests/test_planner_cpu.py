@@ -205,3 +205,46 @@ def test_pass_aware_order_needs_fewer_passes():
 def test_reorder_values_checked():
     with pytest.raises(qsim.QsimError):
         qsim.plan_stages(inputs.ghz(8), m=5, inner=2, k=2, reorder=4)
+
+
+def third_differences_vanish(phases, k):
+    """A function on {0,1}^k has degree <= 2 exactly when every third-order difference
+    sum_{S subset {j,l,m}} (-1)^(3-|S|) f(x + e_S), over x with bits j, l, m clear, vanishes; here f is the phase
+    angle in turns, so the differences are taken modulo 1."""
+    th = np.angle(phases) / (2 * np.pi)
+    for j in range(k):
+        for l in range(j + 1, k):
+            for m_ in range(l + 1, k):
+                mask = (1 << j) | (1 << l) | (1 << m_)
+                for x in range(1 << k):
+                    if x & mask:
+                        continue
+                    s = 0.0
+                    for sub in range(8):
+                        y = x | (((sub >> 0) & 1) << j) | (((sub >> 1) & 1) << l) | (((sub >> 2) & 1) << m_)
+                        s += (-1) ** (3 - bin(sub).count("1")) * th[y]
+                    if abs(s - np.round(s)) > 1e-9:
+                        return False
+    return True
+
+
+def test_quadratic_diagonal_ops_flagged():
+    # the planner flags the diagonal ops that the passes apply as phase polynomials: exactly those whose phase angle
+    # has degree <= 2 in the op's bits, checked here by the vanishing of every third-order difference (mod 1 turn);
+    # products of RZZ / RZ / CZ / CP gates are, a doubly controlled Z (or a phase on three qubits' product) is not
+    ccz = np.diag([1, 1, 1, 1, 1, 1, 1, -1]).astype(complex)
+    gates = [inputs.H(q) for q in range(10)]
+    for t in range(6):
+        gates += [inputs.RZZ(t, t + 3, 0.3 + t), inputs.Gate("ccz", (t, t + 1, t + 4), (), ccz), inputs.CP(t + 2, t, 1.1)]
+    mixed = inputs.Circuit(10, gates + [inputs.H(q) for q in range(10)], 0, "ccz-mix")
+    seen = {True: 0, False: 0}
+    for c, m, inner in ((inputs.qaoa_maxcut(14, 2, 5), 9, 3), (mixed, 6, 2), (inputs.qft_rz_cx(12, 2, 9), 8, 2)):
+        p = qsim.plan_stages(c, m=m, inner=inner, k=4, diag_exempt=1)
+        for s in range(p.nstages):
+            for op in p.stage_ops(s):
+                if op["type"] != 1:
+                    assert not op["quadratic"]
+                    continue
+                assert op["quadratic"] == third_differences_vanish(op["u"], op["nq"]), (c.family, op["qubits"])
+                seen[op["quadratic"]] += 1
+    assert seen[True] > 0 and seen[False] > 0, seen
