@@ -531,6 +531,11 @@ const char *qsim_last_error(void);
 /* Number of kernels this library launched in this process so far. */
 uint64_t qsim_kernel_launch_count(void);
 
+/* Number of device (cudaMalloc) and pinned-host (cudaHostAlloc) allocations this
+ * library made in this process so far; buffers it reuses from its own cache are
+ * not counted again. qsim_compress_block_noalloc leaves it unchanged. */
+uint64_t qsim_alloc_count(void);
+
 /* Release cached device/pinned buffers held by the library for reuse. */
 void qsim_release_cached_memory(void);
 

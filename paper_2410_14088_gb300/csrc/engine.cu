@@ -47,6 +47,7 @@ namespace qsim {
 // ---------------------------------------------------------------------------
 static thread_local char g_err[512] = "";
 static std::atomic<uint64_t> g_launches{0};
+static std::atomic<uint64_t> g_allocs{0};  // successful cudaMalloc / cudaHostAlloc calls of the library
 
 int set_error(int code, const char *fmt, ...) {
     va_list ap;
@@ -172,6 +173,7 @@ static int dev_alloc(void **p, size_t bytes) {
             return set_error(QSIM_E_NOMEM, "cudaMalloc(%zu) failed", bytes);
         }
     }
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     std::lock_guard<std::mutex> lk(c.mu);
     c.dev_live[*p] = bytes;
     return QSIM_OK;
@@ -214,6 +216,7 @@ static int host_alloc(void **p, size_t bytes) {
         cudaGetLastError();
         return set_error(QSIM_E_NOMEM, "cudaHostAlloc(%zu) failed", bytes);
     }
+    g_allocs.fetch_add(1, std::memory_order_relaxed);
     std::lock_guard<std::mutex> lk(c.mu);
     c.host_live[*p] = bytes;
     return QSIM_OK;
@@ -276,13 +279,18 @@ static DeviceCtx &device_ctx(int dev) {
 static int ensure_device_ctx(DeviceCtx &c) {
     if (c.ready) return QSIM_OK;
     const size_t max_frames = size_t(1) << (kQszMaxM - kQszMaxFrameLog);
-    CUDA_TRY(cudaMalloc(&c.status, 256));
-    CUDA_TRY(cudaMalloc(&c.lb_state, max_frames * sizeof(uint64_t)));
-    CUDA_TRY(cudaMalloc(&c.lb_ctr, 256));
-    CUDA_TRY(cudaMalloc(&c.tgt, sizeof(EncTarget)));
-    CUDA_TRY(cudaMalloc(&c.res, sizeof(EncResult)));
-    CUDA_TRY(cudaMalloc(&c.ref, sizeof(BlockRef)));
-    CUDA_TRY(cudaMalloc(&c.pred_params, kMlpParams * sizeof(float)));
+    auto alloc = [](auto **p, size_t bytes) {
+        const cudaError_t e = cudaMalloc(reinterpret_cast<void **>(p), bytes);
+        if (e == cudaSuccess) g_allocs.fetch_add(1, std::memory_order_relaxed);
+        return e;
+    };
+    CUDA_TRY(alloc(&c.status, 256));
+    CUDA_TRY(alloc(&c.lb_state, max_frames * sizeof(uint64_t)));
+    CUDA_TRY(alloc(&c.lb_ctr, 256));
+    CUDA_TRY(alloc(&c.tgt, sizeof(EncTarget)));
+    CUDA_TRY(alloc(&c.res, sizeof(EncResult)));
+    CUDA_TRY(alloc(&c.ref, sizeof(BlockRef)));
+    CUDA_TRY(alloc(&c.pred_params, kMlpParams * sizeof(float)));
     CUDA_TRY(cudaMemset(c.status, 0, 256));
     CUDA_TRY(cudaMemset(c.lb_state, 0, max_frames * sizeof(uint64_t)));
     CUDA_TRY(cudaMemset(c.lb_ctr, 0, 256));
@@ -2087,6 +2095,7 @@ void qsim_config_default(qsim_config *cfg) {
 
 const char *qsim_last_error(void) { return g_err; }
 
+uint64_t qsim_alloc_count(void) { return g_allocs.load(); }
 uint64_t qsim_kernel_launch_count(void) { return g_launches.load(); }
 
 void qsim_release_cached_memory(void) {
@@ -2954,6 +2963,7 @@ int qsim_compress_block_rel(const float *d_amps, uint32_t m, double rel, void *d
             cudaGetLastError();
             return set_error(QSIM_E_NOMEM, "relative-codec scratch of %zu bytes", need);
         }
+        g_allocs.fetch_add(1, std::memory_order_relaxed);
         c.rel_cap = need;
     }
     float2 *wv = reinterpret_cast<float2 *>(c.rel_buf);

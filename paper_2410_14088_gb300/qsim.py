@@ -149,6 +149,7 @@ SIGNATURES = {
                                       ctypes.POINTER(KernelStat)]),
     "qsim_last_error": (ctypes.c_char_p, []),
     "qsim_kernel_launch_count": (_U64, []),
+    "qsim_alloc_count": (_U64, []),
     "qsim_release_cached_memory": (None, []),
 }
 
@@ -188,6 +189,11 @@ def profile_enable(on: bool = True):
 
 def launch_count() -> int:
     return int(lib().qsim_kernel_launch_count())
+
+
+def alloc_count() -> int:
+    """qsim_alloc_count: the library's device and pinned-host allocations in this process so far."""
+    return int(lib().qsim_alloc_count())
 
 
 def worst_case_bytes(m: int) -> int:

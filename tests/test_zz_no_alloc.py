@@ -8,8 +8,9 @@ serves them from a fixed device array. Here it must give the same stream,
 byte for byte, as qsim_compress_block and as the CPU oracle's encoder, on
 two calls in a row (the second call finds the first call's leftovers in the
 shared array), also when it is the first call of the library in a fresh
-process, and reject blocks larger than its fixed scratch covers. This file is
-collected last.
+process, and reject blocks larger than its fixed scratch covers; the library's
+own allocation count (qsim_alloc_count) must not move across these calls. This
+file is collected last.
 """
 import os
 import subprocess
@@ -35,7 +36,9 @@ def test_noalloc_matches_compress_block_on_consecutive_calls():
             eb = eps * 2.0 ** (-n_equiv / 2)
             ref, nref = qsim.compress_block(x, m, eb)
             out = torch.full((qsim.worst_case_bytes(m),), 0xAB, dtype=torch.uint8, device="cuda")
+            allocs = qsim.alloc_count()
             rc, nb = qsim.compress_block_noalloc(x, m, eb, out)
+            assert qsim.alloc_count() == allocs  # nothing allocated by the library for this call
             assert rc == qsim.OK, qsim.lib().qsim_last_error()
             assert nb == nref
             assert torch.equal(out[:nb], ref[:nref]), (call, m)
@@ -68,12 +71,15 @@ import oracle
 from paper_2410_14088_gb300 import inputs, qsim
 torch.cuda.set_device(0)
 m, eb = 13, 1e-3 * 2.0 ** -9
+allocs = qsim.alloc_count()
 for call in range(2):
     x = torch.from_numpy(inputs.gaussian_block(m, 18, 70 + call)).cuda()
     out = torch.zeros(qsim.worst_case_bytes(m), dtype=torch.uint8, device="cuda")
     rc, nb = qsim.compress_block_noalloc(x, m, eb, out)
     assert rc == qsim.OK, qsim.lib().qsim_last_error()
     assert out[:nb].cpu().numpy().tobytes() == oracle.qsz_encode(x.cpu().numpy(), m, eb), call
+# the library made no allocation of its own for these calls (torch allocated the tensors)
+assert qsim.alloc_count() == allocs, (allocs, qsim.alloc_count())
 print("fresh-process no-alloc ok")
 """
 
