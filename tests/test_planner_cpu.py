@@ -248,3 +248,65 @@ def test_quadratic_diagonal_ops_flagged():
                 assert op["quadratic"] == third_differences_vanish(op["u"], op["nq"]), (c.family, op["qubits"])
                 seen[op["quadratic"]] += 1
     assert seen[True] > 0 and seen[False] > 0, seen
+
+
+def random_mixed_circuit(n: int, ngates: int, seed: int) -> inputs.Circuit:
+    """Seeded mix of one-, two- and three-qubit gates, dense and diagonal (H, U3, CX, RZZ, CP, CZ, a CCZ and a
+    random dense three-qubit unitary), on random qubits, with an occasional phase flip: a scheduler stress case."""
+    rng = inputs.SplitMix64(seed)
+    ccz = np.diag([1, 1, 1, 1, 1, 1, 1, -1]).astype(complex)
+    gates = []
+    for _ in range(ngates):
+        kind = rng.below(9)
+        qs = []
+        while len(qs) < 3:
+            q = rng.below(n)
+            if q not in qs:
+                qs.append(q)
+        a, b, c3 = qs
+        th = 2 * np.pi * rng.uniform()
+        if kind == 0:
+            gates.append(inputs.H(a))
+        elif kind == 1:
+            gates.append(inputs.U3(a, th, 0.5 * th, 0.25 * th))
+        elif kind == 2:
+            gates.append(inputs.CX(a, b))
+        elif kind == 3:
+            gates.append(inputs.RZZ(a, b, th))
+        elif kind == 4:
+            gates.append(inputs.CP(a, b, th))
+        elif kind == 5:
+            gates.append(inputs.CZ(a, b))
+        elif kind == 6:
+            gates.append(inputs.Gate("ccz", (a, b, c3), (), ccz))
+        elif kind == 7:
+            z = np.array([[rng.uniform() - 0.5 + 1j * (rng.uniform() - 0.5) for _ in range(8)] for _ in range(8)])
+            q_, _ = np.linalg.qr(z)
+            gates.append(inputs.Gate("u8", (a, b, c3), (), q_))
+        else:
+            gates.append(inputs.PHASEFLIP(rng.below(1 << n), n) if rng.below(4) == 0 else inputs.RZ(a, th))
+    return inputs.Circuit(n, gates, 0, "mixed", {"seed": seed})
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_pass_aware_order_random_circuits(seed):
+    # seeded mixed circuits, several tile sizes and fusion widths, every stage in the pass-aware order (mode 3):
+    # the fused ops replayed with the oracle give the circuit's state, and every pass's dense ops fit its tile
+    n = 12
+    c = random_mixed_circuit(n, 120, 1000 + seed)
+    tile_bits, k = [(6, 3), (7, 4), (8, 3), (6, 5)][seed % 4]
+    m, inner = 8, 3 + seed % 2  # three-qubit dense gates may touch three global qubits: threshold >= 3
+    T = max(tile_bits, min(m + inner, 5 + k))
+    p = qsim.plan_stages(c, m=m, inner=inner, k=k, tile_bits=tile_bits, diag_exempt=seed % 2, reorder=3)
+    psi = oracle.basis_state(n, c.init_basis)
+    total = 0
+    for s, (f, cnt, inner_q) in enumerate(p.stages()):
+        tile = {}
+        for op in p.stage_ops(s):
+            total += op["ngates"]
+            if op["type"] == 0:
+                tile.setdefault(op["pass"], {0, 1, 2}).update(working_bit(q, m, inner_q) for q in op["qubits"])
+            apply_op(psi, n, op)
+        assert all(len(b) <= min(T, m + len(inner_q)) for b in tile.values()), tile
+    assert total == len(c.gates)
+    assert np.max(np.abs(psi.view(np.complex128) - oracle.simulate(c))) <= 1e-11
