@@ -310,3 +310,24 @@ def test_pass_aware_order_random_circuits(seed):
         assert all(len(b) <= min(T, m + len(inner_q)) for b in tile.values()), tile
     assert total == len(c.gates)
     assert np.max(np.abs(psi.view(np.complex128) - oracle.simulate(c))) <= 1e-11
+
+
+@pytest.mark.parametrize("degree", [1, 2, 3])
+def test_quadratic_flag_on_random_phase_polynomials(degree):
+    # a four-qubit diagonal gate whose phase angle is a random polynomial in its bits: flagged exactly when the
+    # polynomial's degree is at most 2 (a random cubic coefficient makes the third-order differences nonzero)
+    rng = np.random.default_rng(40 + degree)
+    x = np.arange(16)
+    bits = [(x >> j) & 1 for j in range(4)]
+    ang = rng.uniform() + sum(rng.uniform() * b for b in bits)
+    if degree >= 2:
+        ang = ang + sum(rng.uniform() * bits[j] * bits[l] for j in range(4) for l in range(j + 1, 4))
+    if degree >= 3:
+        ang = ang + (0.1 + rng.uniform()) * bits[0] * bits[1] * bits[2]
+    g = inputs.Gate("poly", (1, 3, 4, 6), (), np.diag(np.exp(2j * np.pi * ang)))
+    c = inputs.Circuit(8, [inputs.H(q) for q in range(8)] + [g] + [inputs.H(q) for q in range(8)], 0, "poly")
+    p = qsim.plan_stages(c, m=6, inner=2, k=4, diag_exempt=1)
+    ops = [o for s in range(p.nstages) for o in p.stage_ops(s) if o["type"] == 1]
+    assert ops
+    for o in ops:
+        assert o["quadratic"] == (degree <= 2) == third_differences_vanish(o["u"], o["nq"])
